@@ -1,0 +1,254 @@
+"""ORACLE -- test infrastructure only.
+
+Plain FP64 CPU restatement of "A Sparse Stress Model" (Ortmann, Klimenta,
+Brandes; arxiv 1608.08909) in ``oracle.c``, wrapped with ctypes.  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares no code with the CUDA library.
+
+Every function takes and returns numpy arrays; see ``oracle.c`` for the
+paper passage each one follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", -1: "bad argument", -2: "bad graph", -3: "disconnected",
+          -4: "distance above 65534", -5: "out of memory", -8: "numerical failure"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (strict IEEE: no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            v, i32, i64, u64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            sig = {
+                "orc_build_csr": [i32, i64, v, v, v, v, v],
+                "orc_bfs": [i32, v, v, i32, v],
+                "orc_maxmin": [i32, v, v, i32, i32, v],
+                "orc_pivot_dist": [i32, v, v, i32, v, v],
+                "orc_regions": [i32, i32, v, v],
+                "orc_histograms": [i32, i32, v, v, v, v, v, i64],
+                "orc_adapted_weights": [i32, i32, v, v, v],
+                "orc_pivotmds": [i32, i32, v, v, v, v],
+                "orc_rescale": [i32, v, v, v],
+                "orc_sweep_jacobi": [i32, v, v, i32, v, v, v, v, v, v],
+                "orc_sweep_gs": [i32, v, v, i32, v, v, v, v],
+                "orc_splitmix64": [u64, i64, v],
+                "orc_sample_pairs": [i32, i32, i32, u64, v, v],
+                "orc_full_stress": [i32, v, v, v, i32, i32, u64, v, v],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _chk(rc: int, what: str):
+    if rc != 0:
+        raise OracleError(rc, what)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Graph:
+    """CSR of a simple undirected graph: rowptr[n+1], colidx[2m], sorted rows."""
+
+    def __init__(self, n: int, rowptr: np.ndarray, colidx: np.ndarray, m: int):
+        self.n, self.rowptr, self.colidx, self.m = n, rowptr, colidx, m
+
+
+def build_csr(n: int, src, dst) -> Graph:
+    src, dst = _i32(src), _i32(dst)
+    rowptr = np.zeros(n + 1, np.int32)
+    colidx = np.zeros(max(2 * len(src), 1), np.int32)
+    m = ctypes.c_int64(0)
+    _chk(_load().orc_build_csr(n, len(src), _p(src), _p(dst), _p(rowptr), _p(colidx), ctypes.byref(m)),
+         "build_csr")
+    return Graph(n, rowptr, colidx[: 2 * m.value].copy(), m.value)
+
+
+def bfs(g: Graph, s: int) -> np.ndarray:
+    dist = np.zeros(g.n, np.int32)
+    _chk(_load().orc_bfs(g.n, _p(g.rowptr), _p(g.colidx), s, _p(dist)), "bfs")
+    return dist
+
+
+def maxmin(g: Graph, k: int, start: int = 0) -> np.ndarray:
+    piv = np.zeros(k, np.int32)
+    _chk(_load().orc_maxmin(g.n, _p(g.rowptr), _p(g.colidx), k, start, _p(piv)), "maxmin")
+    return piv
+
+
+def pivot_dist(g: Graph, pivots) -> np.ndarray:
+    pivots = _i32(pivots)
+    k = len(pivots)
+    dip = np.zeros((k, g.n), np.uint16)
+    _chk(_load().orc_pivot_dist(g.n, _p(g.rowptr), _p(g.colidx), k, _p(pivots), _p(dip)), "pivot_dist")
+    return dip
+
+
+def regions(dip: np.ndarray) -> np.ndarray:
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    k, n = dip.shape
+    reg = np.zeros(n, np.int32)
+    _chk(_load().orc_regions(n, k, _p(dip), _p(reg)), "regions")
+    return reg
+
+
+def histograms(dip: np.ndarray, region: np.ndarray):
+    """Returns (ecc[k], cnt_off[k+1] int64, cnt[cnt_off[k]] uint32)."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    region = _i32(region)
+    k, n = dip.shape
+    ecc = np.zeros(k, np.int32)
+    lib = _load()
+    _chk(lib.orc_histograms(n, k, _p(dip), _p(region), _p(ecc), None, None, 0), "histograms")
+    cap = int((ecc.astype(np.int64) + 1).sum())
+    off = np.zeros(k + 1, np.int64)
+    cnt = np.zeros(max(cap, 1), np.uint32)
+    _chk(lib.orc_histograms(n, k, _p(dip), _p(region), _p(ecc), _p(off), _p(cnt), cap), "histograms")
+    return ecc, off, cnt[:cap]
+
+
+def adapted_weights(dip: np.ndarray, region: np.ndarray) -> np.ndarray:
+    """w[a][i] = s/d_ia^2 (0 where the pivot term is skipped), by direct count."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    region = _i32(region)
+    k, n = dip.shape
+    w = np.zeros((k, n), np.float64)
+    _chk(_load().orc_adapted_weights(n, k, _p(dip), _p(region), _p(w)), "adapted_weights")
+    return w
+
+
+def pivotmds(dip: np.ndarray, return_b: bool = False):
+    """PivotMDS layout [n][2] and the two eigenvalues (and B = C^T C if asked)."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    k, n = dip.shape
+    pos = np.zeros((n, 2), np.float64)
+    eig = np.zeros(2, np.float64)
+    B = np.zeros((k, k), np.float64) if return_b else None
+    _chk(_load().orc_pivotmds(n, k, _p(dip), _p(pos), _p(eig), _p(B) if return_b else None), "pivotmds")
+    return (pos, eig, B) if return_b else (pos, eig)
+
+
+def rescale(g: Graph, pos: np.ndarray) -> np.ndarray:
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    _chk(_load().orc_rescale(g.n, _p(g.rowptr), _p(g.colidx), _p(pos)), "rescale")
+    return pos
+
+
+def sweep_jacobi(g: Graph, pivots, dip, w, pos):
+    """One Jacobi update of Eq. 4; returns (new positions, relative change)."""
+    pivots = _i32(pivots)
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros_like(pos)
+    rel = ctypes.c_double(0.0)
+    _chk(_load().orc_sweep_jacobi(g.n, _p(g.rowptr), _p(g.colidx), len(pivots), _p(pivots), _p(dip), _p(w),
+                                  _p(pos), _p(out), ctypes.byref(rel)), "sweep_jacobi")
+    return out, rel.value
+
+
+def sweep_gs(g: Graph, pivots, dip, w, pos):
+    """One in-place (node by node, ascending) update of Eq. 4; returns new positions."""
+    pivots = _i32(pivots)
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    _chk(_load().orc_sweep_gs(g.n, _p(g.rowptr), _p(g.colidx), len(pivots), _p(pivots), _p(dip), _p(w),
+                              _p(pos)), "sweep_gs")
+    return pos
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    out = np.zeros(count, np.uint64)
+    _chk(_load().orc_splitmix64(ctypes.c_uint64(seed), count, _p(out)), "splitmix64")
+    return out
+
+
+def sample_pairs(n: int, S: int, T: int, seed: int):
+    srcs = np.zeros(S, np.int32)
+    tgts = np.zeros((S, T), np.int32)
+    _chk(_load().orc_sample_pairs(n, S, T, ctypes.c_uint64(seed), _p(srcs), _p(tgts)), "sample_pairs")
+    return srcs, tgts
+
+
+def full_stress(g: Graph, pos, S: int = 0, T: int = 0, seed: int = 0, return_sums: bool = False):
+    """{raw, alpha*, scaled, normalized} of Eq. 1; S=0 exhaustive, else S*T sampled pairs."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros(4, np.float64)
+    sums = np.zeros(4, np.float64)
+    _chk(_load().orc_full_stress(g.n, _p(g.rowptr), _p(g.colidx), _p(pos), S, T, ctypes.c_uint64(seed),
+                                 _p(out), _p(sums)), "full_stress")
+    return (out, sums) if return_sums else out
+
+
+# ---------------------------------------------------------------------------
+# Whole pipeline (Algorithm 1 with the Jacobi schedule), for tests and the
+# CPU baseline.
+# ---------------------------------------------------------------------------
+
+class Prepared:
+    """Everything Algorithm 1 lines 1-4 produce for one graph."""
+
+    def __init__(self, g, pivots, dip, region, ecc, cnt_off, cnt, w, pos0, eig):
+        self.g, self.pivots, self.dip, self.region = g, pivots, dip, region
+        self.ecc, self.cnt_off, self.cnt, self.w, self.pos0, self.eig = ecc, cnt_off, cnt, w, pos0, eig
+
+
+def prepare(n: int, src, dst, k: int, start: int = 0) -> Prepared:
+    g = build_csr(n, src, dst)
+    piv = maxmin(g, k, start)
+    dip = pivot_dist(g, piv)
+    reg = regions(dip)
+    ecc, off, cnt = histograms(dip, reg)
+    w = adapted_weights(dip, reg)
+    pos, eig = pivotmds(dip)
+    pos = rescale(g, pos)
+    return Prepared(g, piv, dip, reg, ecc, off, cnt, w, pos, eig)
+
+
+def iterate(p: Prepared, pos, iters: int):
+    """`iters` Jacobi updates from pos; returns (positions, last relative change)."""
+    rel = 0.0
+    for _ in range(iters):
+        pos, rel = sweep_jacobi(p.g, p.pivots, p.dip, p.w, pos)
+    return pos, rel

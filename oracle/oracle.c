@@ -1,0 +1,540 @@
+/*
+ * ORACLE -- test infrastructure only.
+ *
+ * A plain, slow, FP64 CPU restatement of the sparse stress model of
+ * Ortmann, Klimenta and Brandes, "A Sparse Stress Model" (arxiv 1608.08909).
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg use
+ * it; the product library never calls it, and it shares no code, header,
+ * table or constant with the CUDA path.
+ *
+ * Every function follows the paper's definitions step by step, in the
+ * paper's order, with no blocking, fusion or reordering:
+ *   orc_build_csr        simple undirected graph G=(V,E)            (Section 1)
+ *   orc_bfs              graph-theoretic distances d_ij, plain queue (Section 1, Eq. 1)
+ *   orc_maxmin           "max/min sp" pivot sampling                 (Section 4.1)
+ *   orc_pivot_dist       d_ip for all pivots, one BFS per pivot      (Algorithm 1, line 2)
+ *   orc_regions          regions R(p): closest pivot                 (Section 3)
+ *   orc_histograms       per-pivot distance counts over R(p)         (Section 3, w'_ip)
+ *   orc_adapted_weights  w'_ip = s / d_ip^2 by direct count          (Section 3, after Eq. 4)
+ *   orc_pivotmds         PivotMDS initial layout                     (Algorithm 1, line 3)
+ *   orc_rescale          edge-length rescale                          (Algorithm 1, line 4)
+ *   orc_sweep_jacobi     one update of Eq. 4 for all nodes from X^t  (Eq. 4)
+ *   orc_sweep_gs         the same, in place node by node              (Algorithm 1, lines 6-10)
+ *   orc_full_stress      Eq. 1 over all pairs, or over sampled pairs  (Eq. 1, Section 4)
+ *
+ * Readings taken where the paper is silent (each is listed with its reason
+ * in the design notes of the repository):
+ *   - region ties go to the lowest pivot index (selection order);
+ *   - the pivot sum skips p = i (d = 0) and pivots adjacent to i (d = 1);
+ *   - s counts j in R(p) with 2*d_jp <= d_ip (exact integer form of d_jp <= d_ip/2);
+ *   - a term with ||x_i - x_j|| == 0 contributes w*x_j only;
+ *   - the update is applied Jacobi-style (all nodes from X^t) in
+ *     orc_sweep_jacobi; orc_sweep_gs keeps the paper's in-place order;
+ *   - relative positional change is ||X^{t+1}-X^t||_F / ||X^t||_F;
+ *   - the rescale target is the sum of edge lengths, i.e. m for unit edges;
+ *   - stress is reported with the optimal scale alpha* = S1/S2.
+ *
+ * Status codes: 0 ok, -1 bad argument, -2 bad graph (id out of range),
+ * -3 disconnected, -4 distance above 65534, -5 out of memory,
+ * -8 numerical failure.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_E_ARG -1
+#define ORC_E_GRAPH -2
+#define ORC_E_DISCONNECTED -3
+#define ORC_E_DIST_OVERFLOW -4
+#define ORC_E_NOMEM -5
+#define ORC_E_NUMERIC -8
+
+/* ------------------------------------------------------------------ */
+/* graph                                                               */
+/* ------------------------------------------------------------------ */
+
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* Simple undirected graph from an edge list: self-loops and repeated edges
+ * are dropped, both directions are stored, each adjacency list is sorted
+ * ascending.  colidx must hold 2*m_in entries; *m_out receives |E|. */
+int orc_build_csr(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst,
+                  int32_t *rowptr, int32_t *colidx, int64_t *m_out) {
+  if (n < 1 || m_in < 0) return ORC_E_ARG;
+  for (int64_t e = 0; e < m_in; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return ORC_E_GRAPH;
+  int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t *tmp = (int32_t *)malloc((size_t)(2 * m_in + 1) * sizeof(int32_t));
+  if (!deg || !fill || !tmp) { free(deg); free(fill); free(tmp); return ORC_E_NOMEM; }
+  for (int64_t e = 0; e < m_in; ++e)
+    if (src[e] != dst[e]) { deg[src[e] + 1]++; deg[dst[e] + 1]++; }
+  for (int32_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  memcpy(fill, deg, ((size_t)n + 1) * sizeof(int64_t));
+  for (int64_t e = 0; e < m_in; ++e)
+    if (src[e] != dst[e]) {
+      tmp[fill[src[e]]++] = dst[e];
+      tmp[fill[dst[e]]++] = src[e];
+    }
+  int64_t out = 0;
+  rowptr[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t b = deg[i], e = deg[i + 1];
+    qsort(tmp + b, (size_t)(e - b), sizeof(int32_t), cmp_i32);
+    for (int64_t t = b; t < e; ++t)
+      if (t == b || tmp[t] != tmp[t - 1]) colidx[out++] = tmp[t];
+    rowptr[i + 1] = (int32_t)out;
+  }
+  free(deg); free(fill); free(tmp);
+  *m_out = out / 2;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* breadth-first search: d_ij for unit edges                           */
+/* ------------------------------------------------------------------ */
+
+/* dist[v] = number of edges on a shortest s-v path, -1 if unreachable */
+int orc_bfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t s, int32_t *dist) {
+  if (s < 0 || s >= n) return ORC_E_ARG;
+  int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!queue) return ORC_E_NOMEM;
+  for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+  int32_t head = 0, tail = 0;
+  dist[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (int32_t t = rowptr[u]; t < rowptr[u + 1]; ++t) {
+      int32_t v = colidx[t];
+      if (dist[v] < 0) { dist[v] = dist[u] + 1; queue[tail++] = v; }
+    }
+  }
+  free(queue);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* pivot sampling: max/min sp (Section 4.1)                            */
+/* ------------------------------------------------------------------ */
+
+/* P = [start]; mind = BFS(start); then k-1 times: p = smallest i with
+ * mind[i] = max(mind); append p; mind = min(mind, BFS(p)).  Each BFS is a
+ * full, unpruned queue BFS. */
+int orc_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+               int32_t start, int32_t *pivots) {
+  if (k < 1 || k > n || start < 0 || start >= n) return ORC_E_ARG;
+  int32_t *mind = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *d = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!mind || !d) { free(mind); free(d); return ORC_E_NOMEM; }
+  int rc = orc_bfs(n, rowptr, colidx, start, mind);
+  for (int32_t v = 0; rc == ORC_OK && v < n; ++v)
+    if (mind[v] < 0) rc = ORC_E_DISCONNECTED;
+  if (rc == ORC_OK) pivots[0] = start;
+  for (int32_t j = 1; rc == ORC_OK && j < k; ++j) {
+    int32_t best = 0;
+    for (int32_t v = 1; v < n; ++v)
+      if (mind[v] > mind[best]) best = v;
+    pivots[j] = best;
+    rc = orc_bfs(n, rowptr, colidx, best, d);
+    for (int32_t v = 0; v < n; ++v)
+      if (d[v] < mind[v]) mind[v] = d[v];
+  }
+  free(mind); free(d);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* d_ip table (Algorithm 1 line 2), pivot-major [k][n] uint16          */
+/* ------------------------------------------------------------------ */
+
+int orc_pivot_dist(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                   const int32_t *pivots, uint16_t *dip) {
+  if (k < 1 || k > 65535) return ORC_E_ARG;
+  int32_t *d = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!d) return ORC_E_NOMEM;
+  int rc = ORC_OK;
+  for (int32_t a = 0; rc == ORC_OK && a < k; ++a) {
+    rc = orc_bfs(n, rowptr, colidx, pivots[a], d);
+    for (int32_t v = 0; rc == ORC_OK && v < n; ++v) {
+      if (d[v] < 0) rc = ORC_E_DISCONNECTED;
+      else if (d[v] > 65534) rc = ORC_E_DIST_OVERFLOW;
+      else dip[(int64_t)a * n + v] = (uint16_t)d[v];
+    }
+  }
+  free(d);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* regions R(p) (Section 3)                                            */
+/* ------------------------------------------------------------------ */
+
+/* region[i] = the smallest pivot index a minimising d_ia */
+int orc_regions(int32_t n, int32_t k, const uint16_t *dip, int32_t *region) {
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t best = 0;
+    for (int32_t a = 1; a < k; ++a)
+      if (dip[(int64_t)a * n + i] < dip[(int64_t)best * n + i]) best = a;
+    region[i] = best;
+  }
+  return ORC_OK;
+}
+
+/* ecc[a] = max_{j in R(a)} d_ja;  cnt[cnt_off[a] + t] = #{j in R(a): d_ja <= t}
+ * for t = 0..ecc[a].  With cnt_off == NULL only ecc is written. */
+int orc_histograms(int32_t n, int32_t k, const uint16_t *dip, const int32_t *region,
+                   int32_t *ecc, int64_t *cnt_off, uint32_t *cnt, int64_t cnt_cap) {
+  for (int32_t a = 0; a < k; ++a) ecc[a] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t a = region[i], d = dip[(int64_t)a * n + i];
+    if (d > ecc[a]) ecc[a] = d;
+  }
+  if (!cnt_off) return ORC_OK;
+  cnt_off[0] = 0;
+  for (int32_t a = 0; a < k; ++a) cnt_off[a + 1] = cnt_off[a] + ecc[a] + 1;
+  if (cnt_off[k] > cnt_cap) return ORC_E_ARG;
+  memset(cnt, 0, (size_t)cnt_off[k] * sizeof(uint32_t));
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t a = region[i];
+    cnt[cnt_off[a] + dip[(int64_t)a * n + i]] += 1; /* histogram H[a][t] */
+  }
+  for (int32_t a = 0; a < k; ++a) /* prefix sums over t */
+    for (int64_t t = cnt_off[a] + 1; t < cnt_off[a + 1]; ++t) cnt[t] += cnt[t - 1];
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* adapted weights w'_ip = s / d_ip^2,  s = #{j in R(p): d_jp <= d_ip/2} */
+/* ------------------------------------------------------------------ */
+
+static int cmp_u16(const void *a, const void *b) {
+  uint16_t x = *(const uint16_t *)a, y = *(const uint16_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* w[a][i] for every pivot index a and node i, by counting the members of
+ * R(a) directly (a sorted list of their distances to p_a and a binary
+ * search), independent of orc_histograms.  w = 0 where the pivot term is
+ * skipped: d_ia <= 1 (i is p_a, or p_a is a neighbour of i). */
+int orc_adapted_weights(int32_t n, int32_t k, const uint16_t *dip, const int32_t *region,
+                        double *w) {
+  uint16_t *lst = (uint16_t *)malloc((size_t)n * sizeof(uint16_t));
+  if (!lst) return ORC_E_NOMEM;
+  for (int32_t a = 0; a < k; ++a) {
+    int32_t len = 0;
+    for (int32_t j = 0; j < n; ++j)
+      if (region[j] == a) lst[len++] = dip[(int64_t)a * n + j];
+    qsort(lst, (size_t)len, sizeof(uint16_t), cmp_u16);
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t d = dip[(int64_t)a * n + i];
+      double wi = 0.0;
+      if (d >= 2) {
+        /* s = number of list entries e with 2*e <= d */
+        int32_t lo = 0, hi = len;
+        while (lo < hi) {
+          int32_t mid = lo + (hi - lo) / 2;
+          if (2 * (int32_t)lst[mid] <= d) lo = mid + 1; else hi = mid;
+        }
+        wi = (double)lo / ((double)d * (double)d);
+      }
+      w[(int64_t)a * n + i] = wi;
+    }
+  }
+  free(lst);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* PivotMDS (Algorithm 1 line 3; Brandes and Pich 2007)                */
+/* ------------------------------------------------------------------ */
+
+/* cyclic Jacobi eigenvalue method for a symmetric k x k matrix A (row-major,
+ * destroyed): on return diag(A) holds the eigenvalues and the columns of V
+ * the eigenvectors.  Sweeps rotate every off-diagonal pair (p,q), p<q, in
+ * row order, with the rotation angle chosen to zero A[p][q]. */
+static int jacobi_eigen(int32_t k, double *A, double *V) {
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < k; ++j) V[i * k + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int32_t i = 0; i < k; ++i)
+      for (int32_t j = 0; j < k; ++j) {
+        tot += A[i * k + j] * A[i * k + j];
+        if (i != j) off += A[i * k + j] * A[i * k + j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) return ORC_OK;
+    for (int32_t p = 0; p < k; ++p)
+      for (int32_t q = p + 1; q < k; ++q) {
+        double apq = A[p * k + q];
+        if (apq == 0.0) continue;
+        double app = A[p * k + p], aqq = A[q * k + q];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int32_t r = 0; r < k; ++r) { /* A <- A J (columns p, q) */
+          double arp = A[r * k + p], arq = A[r * k + q];
+          A[r * k + p] = c * arp - s * arq;
+          A[r * k + q] = s * arp + c * arq;
+        }
+        for (int32_t r = 0; r < k; ++r) { /* A <- J^T A (rows p, q) */
+          double apr = A[p * k + r], aqr = A[q * k + r];
+          A[p * k + r] = c * apr - s * aqr;
+          A[q * k + r] = s * apr + c * aqr;
+        }
+        for (int32_t r = 0; r < k; ++r) { /* V <- V J */
+          double vrp = V[r * k + p], vrq = V[r * k + q];
+          V[r * k + p] = c * vrp - s * vrq;
+          V[r * k + q] = s * vrp + c * vrq;
+        }
+      }
+  }
+  return ORC_E_NUMERIC;
+}
+
+/* PivotMDS from the k x n pivot distances:
+ *   delta_ia = d_ia^2;
+ *   c_ia = -1/2 (delta_ia - rowmean_i - colmean_a + grandmean);
+ *   B = C^T C (k x k);  v1, v2 = eigenvectors of the two largest eigenvalues;
+ *   each v is signed so that its largest-magnitude entry (lowest index on a
+ *   tie) is positive;  x_i = ((C v1)_i, (C v2)_i).
+ * pos is [n][2]; eig (optional) receives the two eigenvalues, B (optional,
+ * k*k) receives C^T C before the eigen-solve. */
+int orc_pivotmds(int32_t n, int32_t k, const uint16_t *dip, double *pos, double *eig, double *Bout) {
+  if (k < 2) return ORC_E_ARG;
+  double *C = (double *)malloc((size_t)n * k * sizeof(double));
+  double *rowm = (double *)calloc((size_t)n, sizeof(double));
+  double *colm = (double *)calloc((size_t)k, sizeof(double));
+  double *B = (double *)calloc((size_t)k * k, sizeof(double));
+  double *V = (double *)malloc((size_t)k * k * sizeof(double));
+  if (!C || !rowm || !colm || !B || !V) { free(C); free(rowm); free(colm); free(B); free(V); return ORC_E_NOMEM; }
+  double grand = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t a = 0; a < k; ++a) {
+      double d = (double)dip[(int64_t)a * n + i];
+      double delta = d * d;
+      C[(int64_t)i * k + a] = delta;
+      rowm[i] += delta;
+      colm[a] += delta;
+      grand += delta;
+    }
+  for (int32_t i = 0; i < n; ++i) rowm[i] /= (double)k;
+  for (int32_t a = 0; a < k; ++a) colm[a] /= (double)n;
+  grand /= (double)n * (double)k;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t a = 0; a < k; ++a)
+      C[(int64_t)i * k + a] = -0.5 * (C[(int64_t)i * k + a] - rowm[i] - colm[a] + grand);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b) {
+      double s = 0.0;
+      for (int32_t i = 0; i < n; ++i) s += C[(int64_t)i * k + a] * C[(int64_t)i * k + b];
+      B[a * k + b] = s;
+    }
+  if (Bout) memcpy(Bout, B, (size_t)k * k * sizeof(double));
+  int rc = jacobi_eigen(k, B, V);
+  if (rc == ORC_OK) {
+    int32_t top[2] = {-1, -1};
+    for (int r = 0; r < 2; ++r)
+      for (int32_t a = 0; a < k; ++a) {
+        if (a == top[0]) continue;
+        if (top[r] < 0 || B[a * k + a] > B[top[r] * k + top[r]]) top[r] = a;
+      }
+    for (int r = 0; r < 2; ++r) {
+      int32_t c = top[r], big = 0;
+      for (int32_t a = 1; a < k; ++a)
+        if (fabs(V[a * k + c]) > fabs(V[big * k + c])) big = a;
+      double sg = V[big * k + c] < 0 ? -1.0 : 1.0;
+      if (eig) eig[r] = B[c * k + c];
+      for (int32_t i = 0; i < n; ++i) {
+        double x = 0.0;
+        for (int32_t a = 0; a < k; ++a) x += C[(int64_t)i * k + a] * sg * V[a * k + c];
+        pos[2 * (int64_t)i + r] = x;
+      }
+    }
+  }
+  free(C); free(rowm); free(colm); free(B); free(V);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* rescale (Algorithm 1 line 4): sum_E ||x_i - x_j|| = sum_E l_ij = m   */
+/* ------------------------------------------------------------------ */
+
+int orc_rescale(int32_t n, const int32_t *rowptr, const int32_t *colidx, double *pos) {
+  double len = 0.0;
+  int64_t m2 = 0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+      int32_t j = colidx[t];
+      if (j <= i) continue;
+      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
+      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
+      len += sqrt(dx * dx + dy * dy);
+      ++m2;
+    }
+  if (!(len > 0.0)) return ORC_E_NUMERIC;
+  double s = (double)m2 / len;
+  for (int64_t t = 0; t < 2 * (int64_t)n; ++t) pos[t] *= s;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* the update of Eq. 4                                                 */
+/* ------------------------------------------------------------------ */
+
+/* new position of node i from the positions X (Eq. 4): neighbour terms with
+ * w_ij = 1, d_ij = 1 (CSR order), then pivot terms a = 0..k-1 with
+ * d = d_ia >= 2 and weight w[a][i]. */
+static void eq4_update(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                       const int32_t *pivots, const uint16_t *dip, const double *w,
+                       const double *X, int32_t i, double *out) {
+  double xi = X[2 * (int64_t)i], yi = X[2 * (int64_t)i + 1];
+  double nx = 0.0, ny = 0.0, den = 0.0;
+  for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+    int32_t j = colidx[t];
+    double xj = X[2 * (int64_t)j], yj = X[2 * (int64_t)j + 1];
+    double dx = xi - xj, dy = yi - yj;
+    double r = sqrt(dx * dx + dy * dy);
+    if (r > 0.0) { nx += xj + dx / r; ny += yj + dy / r; }
+    else { nx += xj; ny += yj; }
+    den += 1.0;
+  }
+  for (int32_t a = 0; a < k; ++a) {
+    int32_t d = dip[(int64_t)a * n + i];
+    if (d < 2) continue;
+    int32_t p = pivots[a];
+    double wa = w[(int64_t)a * n + i];
+    double xp = X[2 * (int64_t)p], yp = X[2 * (int64_t)p + 1];
+    double dx = xi - xp, dy = yi - yp;
+    double r = sqrt(dx * dx + dy * dy);
+    if (r > 0.0) { nx += wa * (xp + d * dx / r); ny += wa * (yp + d * dy / r); }
+    else { nx += wa * xp; ny += wa * yp; }
+    den += wa;
+  }
+  if (den > 0.0) { out[0] = nx / den; out[1] = ny / den; }
+  else { out[0] = xi; out[1] = yi; }
+}
+
+/* Jacobi: X^{t+1}_i from X^t for every i; relchange (optional) receives
+ * ||X^{t+1} - X^t||_F / ||X^t||_F. */
+int orc_sweep_jacobi(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                     const int32_t *pivots, const uint16_t *dip, const double *w,
+                     const double *pos_in, double *pos_out, double *relchange) {
+  for (int32_t i = 0; i < n; ++i)
+    eq4_update(n, rowptr, colidx, k, pivots, dip, w, pos_in, i, pos_out + 2 * (int64_t)i);
+  if (relchange) {
+    double num = 0.0, den = 0.0;
+    for (int64_t t = 0; t < 2 * (int64_t)n; ++t) {
+      double dd = pos_out[t] - pos_in[t];
+      num += dd * dd;
+      den += pos_in[t] * pos_in[t];
+    }
+    *relchange = den > 0.0 ? sqrt(num) / sqrt(den) : 0.0;
+  }
+  return ORC_OK;
+}
+
+/* Gauss-Seidel, the paper's order: x_i <- Eq. 4 for i = 0..n-1, in place */
+int orc_sweep_gs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                 const int32_t *pivots, const uint16_t *dip, const double *w, double *pos) {
+  double t[2];
+  for (int32_t i = 0; i < n; ++i) {
+    eq4_update(n, rowptr, colidx, k, pivots, dip, w, pos, i, t);
+    pos[2 * (int64_t)i] = t[0];
+    pos[2 * (int64_t)i + 1] = t[1];
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* stress (Eq. 1) with optimal scaling                                 */
+/* ------------------------------------------------------------------ */
+
+/* splitmix64 as a counter-based generator: value c of stream `seed` is the
+ * output mix of state seed + (c+1)*0x9E3779B97F4A7C15 (Steele, Lea, Flood 2014) */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+int orc_splitmix64(uint64_t seed, int64_t count, uint64_t *out) {
+  for (int64_t c = 0; c < count; ++c) out[c] = splitmix64_at(seed, (uint64_t)c);
+  return ORC_OK;
+}
+
+/* The sampled pair list: source j (0 <= j < S) is node
+ * (hi32(u_j) * n) >> 32 with u_j = value j of the stream; target l of
+ * source j uses u = value S + j*T + l, t' = (hi32(u) * (n-1)) >> 32 and
+ * t = t' + (t' >= source), i.e. uniform over the other n-1 nodes. */
+int orc_sample_pairs(int32_t n, int32_t S, int32_t T, uint64_t seed, int32_t *srcs, int32_t *tgts) {
+  if (n < 2 || S < 1 || T < 1) return ORC_E_ARG;
+  for (int32_t j = 0; j < S; ++j)
+    srcs[j] = (int32_t)(((splitmix64_at(seed, (uint64_t)j) >> 32) * (uint64_t)n) >> 32);
+  for (int32_t j = 0; j < S; ++j)
+    for (int32_t l = 0; l < T; ++l) {
+      uint64_t u = splitmix64_at(seed, (uint64_t)S + (uint64_t)j * T + l);
+      int32_t t = (int32_t)(((u >> 32) * (uint64_t)(n - 1)) >> 32);
+      tgts[(int64_t)j * T + l] = t + (t >= srcs[j]);
+    }
+  return ORC_OK;
+}
+
+/* Full stress of the layout pos.
+ * S == 0: exhaustive, every pair i < j (a BFS from every node).
+ * S > 0:  the S*T sampled pairs of orc_sample_pairs (a BFS from every source).
+ * sums (optional) receives {sum (r-d)^2/d^2, S1 = sum r/d, S2 = sum r^2/d^2, N}.
+ * out = {raw, alpha*, scaled, normalized}: raw = sum (r-d)^2/d^2 (sampled:
+ * scaled to C(n,2) pairs by C(n,2)/N); alpha* = S1/S2 minimises
+ * sum (alpha r - d)^2 / d^2; scaled = N - S1^2/S2 (sampled: times C(n,2)/N);
+ * normalized = scaled / C(n,2). */
+int orc_full_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *pos,
+                    int32_t S, int32_t T, uint64_t seed, double *out, double *sums) {
+  if (n < 2 || S < 0 || (S > 0 && T < 1)) return ORC_E_ARG;
+  int32_t *dist = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *srcs = NULL, *tgts = NULL;
+  if (!dist) return ORC_E_NOMEM;
+  if (S > 0) {
+    srcs = (int32_t *)malloc((size_t)S * sizeof(int32_t));
+    tgts = (int32_t *)malloc((size_t)S * T * sizeof(int32_t));
+    if (!srcs || !tgts) { free(dist); free(srcs); free(tgts); return ORC_E_NOMEM; }
+    orc_sample_pairs(n, S, T, seed, srcs, tgts);
+  }
+  double raw = 0.0, s1 = 0.0, s2 = 0.0, np = 0.0;
+  int rc = ORC_OK;
+  int32_t nsrc = S > 0 ? S : n;
+  for (int32_t q = 0; rc == ORC_OK && q < nsrc; ++q) {
+    int32_t i = S > 0 ? srcs[q] : q;
+    rc = orc_bfs(n, rowptr, colidx, i, dist);
+    int32_t cnt = S > 0 ? T : n;
+    for (int32_t l = 0; rc == ORC_OK && l < cnt; ++l) {
+      int32_t j = S > 0 ? tgts[(int64_t)q * T + l] : l;
+      if (S == 0 && j <= i) continue;
+      if (dist[j] < 0) { rc = ORC_E_DISCONNECTED; break; }
+      double d = (double)dist[j];
+      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
+      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
+      double r = sqrt(dx * dx + dy * dy);
+      raw += (r - d) * (r - d) / (d * d);
+      s1 += r / d;
+      s2 += r * r / (d * d);
+      np += 1.0;
+    }
+  }
+  free(dist); free(srcs); free(tgts);
+  if (rc != ORC_OK) return rc;
+  double pairs = 0.5 * (double)n * (double)(n - 1);
+  double f = S > 0 ? pairs / np : 1.0;
+  if (sums) { sums[0] = raw; sums[1] = s1; sums[2] = s2; sums[3] = np; }
+  out[0] = raw * f;
+  out[1] = s2 > 0.0 ? s1 / s2 : 0.0;
+  out[2] = (s2 > 0.0 ? np - s1 * s1 / s2 : np) * f;
+  out[3] = out[2] / pairs;
+  return ORC_OK;
+}

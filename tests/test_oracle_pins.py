@@ -1,0 +1,416 @@
+"""Pins of the CPU oracle to what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a library
+routine (scipy shortest paths, numpy eigh), a closed form, an exact special
+case, a hand derivation stored under tests/golden/, or an invariant the paper
+states.  A plausible slip in the oracle (a dropped term, a wrong index or
+sign, a transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+from scipy.optimize import minimize_scalar
+
+import oracle as O
+from paper_1608_08909_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _apsp(g):
+    A = sp.csr_matrix((np.ones(len(g.colidx)), g.colidx, g.rowptr), shape=(g.n, g.n))
+    D = csg.shortest_path(A, method="D", unweighted=True)
+    return D
+
+
+def _rand_graph(rng, n, p):
+    # connected: random spanning tree plus random extra edges
+    src, dst = [], []
+    for v in range(1, n):
+        src.append(int(rng.integers(0, v)))
+        dst.append(v)
+    extra = rng.random((n, n)) < p
+    for i, j in zip(*np.nonzero(np.triu(extra, 1))):
+        src.append(int(i))
+        dst.append(int(j))
+    return n, np.array(src, np.int32), np.array(dst, np.int32)
+
+
+# ---------------------------------------------------------------- graph / BFS
+
+def test_build_csr_matches_scipy_structure():
+    rng = np.random.default_rng(3)
+    n = 37
+    src = rng.integers(0, n, 300).astype(np.int32)
+    dst = rng.integers(0, n, 300).astype(np.int32)
+    g = O.build_csr(n, src, dst)
+    keep = src != dst
+    A = sp.coo_matrix((np.ones(keep.sum()), (src[keep], dst[keep])), shape=(n, n)).tocsr()
+    A = ((A + A.T) > 0).astype(np.int8).tocsr()
+    A.sort_indices()
+    assert np.array_equal(g.rowptr, A.indptr)
+    assert np.array_equal(g.colidx, A.indices)
+    assert g.m == A.nnz // 2
+
+
+def test_build_csr_rejects_out_of_range():
+    with pytest.raises(O.OracleError) as e:
+        O.build_csr(3, [0, 1], [1, 3])
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bfs_matches_library_apsp(seed):
+    rng = np.random.default_rng(seed)
+    n, s, d = _rand_graph(rng, int(rng.integers(2, 40)), 0.08)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    for v in range(n):
+        assert np.array_equal(O.bfs(g, v), D[v].astype(np.int32))
+
+
+def test_bfs_closed_forms():
+    n, s, d = I.grid(7, 9)
+    g = O.build_csr(n, s, d)
+    for v in (0, 13, 62):
+        r, c = divmod(np.arange(n), 9)
+        rv, cv = divmod(v, 9)
+        assert np.array_equal(O.bfs(g, v), np.abs(r - rv) + np.abs(c - cv))
+    n, s, d = I.path(50)
+    g = O.build_csr(n, s, d)
+    assert np.array_equal(O.bfs(g, 17), np.abs(np.arange(50) - 17))
+    n, s, d = I.complete_btree(6)
+    g = O.build_csr(n, s, d)
+
+    def depth(i):
+        return int(math.floor(math.log2(i + 1)))
+
+    def lca_dist(i, j):
+        di, dj = depth(i), depth(j)
+        a, b = i, j
+        while a != b:
+            if a > b:
+                a = (a - 1) // 2
+            else:
+                b = (b - 1) // 2
+        return di + dj - 2 * depth(a)
+
+    for v in (0, 5, 100):
+        assert np.array_equal(O.bfs(g, v), [lca_dist(v, j) for j in range(n)])
+
+
+# ---------------------------------------------------------------- pivots
+
+def test_maxmin_grid_golden():
+    want = [int(x) for x in open(os.path.join(GOLD, "grid32_maxmin.txt")) if x.strip() and x[0] != "#"]
+    n, s, d = I.grid(32, 32)
+    g = O.build_csr(n, s, d)
+    assert O.maxmin(g, 5).tolist() == want
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_maxmin_matches_definition_on_library_apsp(seed):
+    rng = np.random.default_rng(100 + seed)
+    n, s, d = _rand_graph(rng, int(rng.integers(5, 60)), 0.05)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    k = int(rng.integers(1, n + 1))
+    start = int(rng.integers(0, n))
+    P = [start]
+    while len(P) < k:
+        mind = D[P].min(axis=0)
+        P.append(int(np.argmax(mind)))  # first maximum = lowest node id
+    assert O.maxmin(g, k, start).tolist() == P
+
+
+def test_maxmin_rejects_disconnected():
+    with pytest.raises(O.OracleError) as e:
+        g = O.build_csr(4, [0, 2], [1, 3])
+        O.maxmin(g, 2)
+    assert e.value.code == -3
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_pivot_dist_regions_histograms(seed):
+    rng = np.random.default_rng(200 + seed)
+    n, s, d = _rand_graph(rng, int(rng.integers(10, 80)), 0.04)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    k = int(rng.integers(1, min(n, 12) + 1))
+    piv = rng.choice(n, k, replace=False).astype(np.int32)
+    dip = O.pivot_dist(g, piv)
+    assert np.array_equal(dip, D[piv].astype(np.uint16))
+    reg = O.regions(dip)
+    assert np.array_equal(reg, np.argmin(D[piv], axis=0))  # first minimum = lowest pivot index
+    # R is a partition with p in R(p) (Section 3)
+    assert np.array_equal(reg[piv], np.arange(k))
+    ecc, off, cnt = O.histograms(dip, reg)
+    for a in range(k):
+        members = np.nonzero(reg == a)[0]
+        dm = dip[a, members].astype(int)
+        assert ecc[a] == dm.max()
+        row = cnt[off[a]:off[a + 1]]
+        assert len(row) == ecc[a] + 1
+        assert np.array_equal(row, [(dm <= t).sum() for t in range(ecc[a] + 1)])
+    assert sum(cnt[off[a + 1] - 1] for a in range(k)) == n
+
+
+# ---------------------------------------------------------------- adapted weights
+
+def test_adapted_weights_path_golden():
+    n, s, d = I.path(7)
+    g = O.build_csr(n, s, d)
+    dip = O.pivot_dist(g, [0, 6])
+    reg = O.regions(dip)
+    assert reg.tolist() == [0, 0, 0, 0, 1, 1, 1]
+    w = O.adapted_weights(dip, reg)
+    for line in open(os.path.join(GOLD, "path7_weights.txt")):
+        if not line.strip() or line[0] == "#":
+            continue
+        f = line.split()
+        a, i = int(f[0]), int(f[1])
+        want = 0.0 if f[2] == "skip" else int(f[2]) / int(f[3])
+        assert w[a, i] == pytest.approx(want, rel=0, abs=0), (a, i)
+    # asymmetry (Section 3): w'(0 -> 6) != w'(6 -> 0)
+    assert w[1, 0] != w[0, 6]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adapted_weights_match_histogram_route(seed):
+    """Direct count (sorted region lists) against the cumulative counts."""
+    rng = np.random.default_rng(300 + seed)
+    n, s, d = _rand_graph(rng, int(rng.integers(20, 120)), 0.02)
+    g = O.build_csr(n, s, d)
+    k = int(rng.integers(2, 16))
+    piv = O.maxmin(g, k, int(rng.integers(0, n)))
+    dip = O.pivot_dist(g, piv)
+    reg = O.regions(dip)
+    ecc, off, cnt = O.histograms(dip, reg)
+    w = O.adapted_weights(dip, reg)
+    for a in range(k):
+        for i in range(n):
+            dd = int(dip[a, i])
+            if dd < 2:
+                assert w[a, i] == 0.0
+                continue
+            s_ = int(cnt[off[a] + min(dd // 2, ecc[a])])
+            assert s_ >= 1
+            assert w[a, i] == s_ / (dd * dd)
+
+
+def test_weights_reduce_to_full_stress_when_k_equals_n():
+    """k = n: every node is its own region, s = 1, w' = 1/d^2 (Section 3)."""
+    n, s, d = I.grid(5, 6)
+    g = O.build_csr(n, s, d)
+    piv = np.arange(n, dtype=np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    D = _apsp(g)
+    want = np.where(D >= 2, 1.0 / np.maximum(D, 1) ** 2, 0.0)
+    assert np.array_equal(w, want)
+
+
+# ---------------------------------------------------------------- sweep
+
+def _full_stress_jacobi_update(D, X):
+    """GKN localized update (Section 3, the full-stress update before Eq. 4), all i from X."""
+    n = len(X)
+    out = np.zeros_like(X)
+    for i in range(n):
+        num = np.zeros(2)
+        den = 0.0
+        for j in range(n):
+            if j == i:
+                continue
+            w = 1.0 / D[i, j] ** 2
+            diff = X[i] - X[j]
+            r = np.hypot(*diff)
+            num += w * (X[j] + D[i, j] * diff / r)
+            den += w
+        out[i] = num / den
+    return out
+
+
+def test_sweep_k_equals_n_is_full_stress_update():
+    n, s, d = I.grid(4, 5)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    piv = np.arange(n, dtype=np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    X = np.random.default_rng(0).normal(size=(n, 2))
+    got, _ = O.sweep_jacobi(g, piv, dip, w, X)
+    np.testing.assert_allclose(got, _full_stress_jacobi_update(D, X), rtol=1e-13, atol=1e-13)
+
+
+def _stress_eq1(D, X):
+    n = len(X)
+    iu = np.triu_indices(n, 1)
+    r = np.hypot(*(X[iu[0]] - X[iu[1]]).T)
+    dd = D[iu]
+    return np.sum((r - dd) ** 2 / dd ** 2)
+
+
+def test_gauss_seidel_full_stress_is_monotone():
+    """Node-at-a-time majorization of full stress never increases it (Section 3, [gkn-sm-04])."""
+    n, s, d = I.random_btree(40, 5)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    piv = np.arange(n, dtype=np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    X = np.random.default_rng(1).normal(size=(n, 2)) * 3
+    prev = _stress_eq1(D, X)
+    for _ in range(30):
+        X = O.sweep_gs(g, piv, dip, w, X)
+        cur = _stress_eq1(D, X)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
+def test_sweep_equivariance():
+    """Eq. 4 commutes with rotations, reflections and translations of the layout."""
+    n, s, d = I.rgg(300, 7.0, 11)
+    p = O.prepare(n, s, d, 12)
+    X = p.pos0
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]]) @ np.diag([1, -1])
+    t = np.array([3.5, -1.25])
+    a, _ = O.sweep_jacobi(p.g, p.pivots, p.dip, p.w, X)
+    b, _ = O.sweep_jacobi(p.g, p.pivots, p.dip, p.w, X @ R.T + t)
+    np.testing.assert_allclose(b, a @ R.T + t, rtol=0, atol=1e-10 * np.abs(a).max())
+
+
+def test_two_node_jacobi_oscillation():
+    """Two nodes at distance r (edge, d=1): Eq. 4 moves each to x_j + (x_i - x_j)/r,
+    so from r = 0.4 Jacobi maps the distance to 1 exactly (both move)."""
+    g = O.build_csr(2, [0], [1])
+    X = np.array([[0.0, 0.0], [0.4, 0.0]])
+    piv = np.array([0], np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    Y, rel = O.sweep_jacobi(g, piv, dip, w, X)
+    # node 0 -> x1 + (x0-x1)/0.4 = 0.4 - 1 = -0.6 ; node 1 -> x0 + (x1-x0)/0.4 = 1.0
+    np.testing.assert_allclose(Y, [[-0.6, 0.0], [1.0, 0.0]], rtol=0, atol=1e-15)
+    assert rel == pytest.approx(math.hypot(0.6, 0.6) / 0.4)
+
+
+def test_coincident_nodes_rule():
+    """r = 0: the term contributes w * x_j only."""
+    g = O.build_csr(2, [0], [1])
+    X = np.array([[1.0, 2.0], [1.0, 2.0]])
+    piv = np.array([0], np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    Y, _ = O.sweep_jacobi(g, piv, dip, w, X)
+    np.testing.assert_array_equal(Y, X)
+
+
+# ---------------------------------------------------------------- PivotMDS
+
+def test_pivotmds_eigs_match_library():
+    n, s, d = I.rgg(400, 8.0, 3)
+    g = O.build_csr(n, s, d)
+    piv = O.maxmin(g, 20)
+    dip = O.pivot_dist(g, piv)
+    pos, eig, B = O.pivotmds(dip, return_b=True)
+    # B = C^T C with C the double-centred -1/2 d^2 (numpy route)
+    Dl = dip.T.astype(np.float64) ** 2
+    C = -0.5 * (Dl - Dl.mean(1, keepdims=True) - Dl.mean(0, keepdims=True) + Dl.mean())
+    np.testing.assert_allclose(B, C.T @ C, rtol=1e-12, atol=1e-9 * np.abs(B).max())
+    lam, V = np.linalg.eigh(C.T @ C)
+    np.testing.assert_allclose(eig, lam[::-1][:2], rtol=1e-10)
+    for r in range(2):
+        v = V[:, -1 - r]
+        v = v * np.sign(v[np.argmax(np.abs(v))])
+        np.testing.assert_allclose(pos[:, r], C @ v, rtol=1e-8, atol=1e-8 * np.abs(pos).max())
+
+
+def test_pivotmds_path_is_exact_1d():
+    """On a path d_ij = |i-j| is Euclidean in 1-D, so classical MDS is exact:
+    x_i is proportional to i - mean(i) and the second eigenvalue vanishes."""
+    n, s, d = I.path(60)
+    g = O.build_csr(n, s, d)
+    dip = O.pivot_dist(g, O.maxmin(g, 7))
+    pos, eig = O.pivotmds(dip)
+    assert eig[1] <= 1e-9 * eig[0]
+    i = np.arange(n) - (n - 1) / 2
+    c = np.dot(pos[:, 0], i) / np.dot(i, i)
+    np.testing.assert_allclose(pos[:, 0], c * i, rtol=0, atol=1e-9 * abs(c) * n)
+    assert np.abs(pos[:, 1]).max() <= 1e-6 * np.abs(pos[:, 0]).max()
+
+
+def test_rescale_sets_mean_edge_length_one():
+    n, s, d = I.grid(9, 11)
+    p = O.prepare(n, s, d, 8)
+    X = p.pos0
+    e = [(i, j) for i in range(n) for j in p.g.colidx[p.g.rowptr[i]:p.g.rowptr[i + 1]] if j > i]
+    tot = sum(np.hypot(*(X[i] - X[j])) for i, j in e)
+    assert tot == pytest.approx(p.g.m, rel=1e-12)
+
+
+# ---------------------------------------------------------------- stress
+
+def test_stress_unit_square_closed_form():
+    """4-cycle on the unit square: edges r=d=1, diagonals r=sqrt2, d=2."""
+    g = O.build_csr(4, [0, 1, 2, 3], [1, 2, 3, 0])
+    X = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float64)
+    out = O.full_stress(g, X)
+    r2 = math.sqrt(2.0)
+    assert out[0] == pytest.approx(3 - 2 * r2, rel=1e-14)
+    assert out[1] == pytest.approx((4 + r2) / 5, rel=1e-14)
+    assert out[2] == pytest.approx((12 - 8 * r2) / 5, rel=1e-13)
+    assert out[3] == pytest.approx((12 - 8 * r2) / 5 / 6, rel=1e-13)
+
+
+def test_stress_zero_for_exact_path_layout():
+    n, s, d = I.path(25)
+    g = O.build_csr(n, s, d)
+    X = np.stack([np.arange(n) * 2.0, np.zeros(n)], 1)  # twice the right scale
+    out = O.full_stress(g, X)
+    assert out[0] > 0
+    assert out[1] == pytest.approx(0.5, rel=1e-14)
+    assert abs(out[2]) < 1e-9
+
+
+def test_optimal_scale_against_numerical_minimum():
+    n, s, d = I.random_btree(30, 2)
+    g = O.build_csr(n, s, d)
+    D = _apsp(g)
+    X = np.random.default_rng(4).normal(size=(n, 2))
+    out = O.full_stress(g, X)
+    f = lambda a: _stress_eq1(D, a * X)  # noqa: E731
+    res = minimize_scalar(f, bracket=(0.1, 10.0), tol=1e-12)
+    assert out[1] == pytest.approx(res.x, rel=1e-6)
+    assert out[2] == pytest.approx(res.fun, rel=1e-9)
+    assert out[0] == pytest.approx(f(1.0), rel=1e-12)
+
+
+def test_splitmix64_reference_values():
+    want = [int(x, 16) for x in open(os.path.join(GOLD, "splitmix64_seed0.txt")) if x.startswith("0x")]
+    assert O.splitmix64(0, 3).tolist() == want
+
+
+def test_sample_pairs_valid_and_uniform():
+    n, S, T = 50, 64, 512
+    srcs, tgts = O.sample_pairs(n, S, T, 9)
+    assert srcs.min() >= 0 and srcs.max() < n
+    assert tgts.min() >= 0 and tgts.max() < n
+    assert not np.any(tgts == srcs[:, None])
+    counts = np.bincount(tgts.ravel(), minlength=n)
+    exp = S * T / n
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 2 * n  # loose: mean n-1, sd ~ sqrt(2n)
+
+
+def test_sampled_stress_unbiased():
+    """The sampled estimator averages to the exhaustive stress."""
+    n, s, d = I.rgg(120, 7.0, 5)
+    p = O.prepare(n, s, d, 10)
+    ex = O.full_stress(p.g, p.pos0)
+    est = np.mean([O.full_stress(p.g, p.pos0, 16, 64, seed)[0] for seed in range(60)])
+    assert est == pytest.approx(ex[0], rel=0.03)
