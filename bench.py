@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the whole sparse stress pipeline (Algorithm 1, Jacobi schedule).
+
+One step = every stage of the hot path on one synthetic graph:
+  CSR build -> max/min-sp pivots -> multi-source BFS (d_ip) -> regions and
+  counts -> PivotMDS + rescale -> `iters` Jacobi sweeps (Eq. 4) -> sampled
+  (or exhaustive) stress.
+Metric: node-term updates per second, with iters * (k*n + 2m) node-term
+updates per step (each sweep touches k pivot terms and deg(i) edge terms per
+node: O(kn + m) per iteration, Section 3).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rgg256k|ba1m|grid32]
+  python bench.py --impl reference ...   # the CPU oracle on the same workload
+
+Multi-GPU: the path for one graph does not shard here; N ranks run N
+independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator args, k, iters, stress sources, targets per source, description)
+    "rgg256k": dict(k=200, iters=100, S=1024, T=1024, seed=1,
+                    desc="random geometric graph, 262144 uniform points in the unit square (seed 1), "
+                         "radius for mean degree 8, largest component kept"),
+    "ba1m": dict(k=200, iters=100, S=1024, T=1024, seed=1,
+                 desc="Barabasi-Albert graph, n=2^20, 4 edges per new node (seed 1)"),
+    "grid32": dict(k=50, iters=200, S=0, T=0, seed=1, desc="32x32 grid, exhaustive stress"),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def launches_per_step(iters: int, exhaustive_batches: int) -> int:
+    """Kernels of this library launched by one step (memsets not counted):
+    build graph 13 (degree count, 2 scans of 3, scatter, 2 row sorts, flags,
+    compaction, connectivity BFS), pivots 1, d_ip BFS 1, aggregate size 2,
+    aggregate 4, PivotMDS 8, sweeps iters + 1 copy-back, stress 2 + 3 per batch."""
+    return 13 + 1 + 1 + 2 + 4 + 8 + (iters + 1) + 1 + 3 * exhaustive_batches
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1608_08909_gb300 as ssm
+    from paper_1608_08909_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    W = WORKLOADS[args.workload]
+    n, src, dst, _, _ = I.workload(args.workload, W["seed"])
+    k, iters, S, T = W["k"], args.iters or W["iters"], W["S"], W["T"]
+    src_d = torch.from_numpy(src).to(dev)
+    dst_d = torch.from_numpy(dst).to(dev)
+    src_h = torch.from_numpy(src).pin_memory()
+    dst_h = torch.from_numpy(dst).pin_memory()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(s_d, d_d, sweep_ev=None):
+        g = ssm.ssm_build_graph(n, s_d, d_d)
+        piv = ssm.ssm_select_pivots(g, k, 0, check=False)
+        dip = ssm.ssm_pivot_bfs(g, piv, check=False)
+        cnt_len = ssm.ssm_aggregate_size(dip)
+        region, off, cnt = ssm.ssm_aggregate(dip, cnt_len, check=False)
+        pos, _ = ssm.ssm_pivotmds(g, dip, 32, True, check=False)
+        P = ssm.Pivots(k, piv, dip, region, off, cnt)
+        if sweep_ev is not None:
+            sweep_ev[0].record(stream)
+        ssm.ssm_iterate(g, P, pos, iters, check=False)
+        if sweep_ev is not None:
+            sweep_ev[1].record(stream)
+        out, _ = ssm.ssm_stress(g, pos, S, T, W["seed"], check=False)
+        return g, P, pos, out
+
+    # correctness of the device status words is checked once, outside timing
+    g, P, pos, out = step(src_d, dst_d)
+    torch.cuda.synchronize()
+    m = g.m
+    terms_per_step = iters * (k * n + 2 * m)
+    batches = 0 if S > 0 else (n + 1023) // 1024
+
+    for _ in range(args.warmup):
+        step(src_d, dst_d)
+    torch.cuda.synchronize()
+
+    step_ms, sweep_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            _, _, _, out = step(src_d, dst_d, sweep_ev=(ev[2], ev[3]))
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+            sweep_ms.append(ev[2].elapsed_time(ev[3]))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * terms_per_step * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # end to end through the public API: host edge list in, host positions and stress out
+    e2e_ms = []
+    for t_ in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s_d = src_h.to(dev, non_blocking=True)
+        d_d = dst_h.to(dev, non_blocking=True)
+        _, _, pos_d, out_d = step(s_d, d_d)
+        pos_h = pos_d.cpu()
+        out_h = out_d.cpu()
+        torch.cuda.synchronize()
+        if t_ > 0:  # first iteration warms the pinned paths
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * terms_per_step * args.steps / (e2e_total / 1e3)
+    h2d = int(src.nbytes + dst.nbytes)
+    d2h = int(pos_h.numel() * pos_h.element_size() + out_h.numel() * out_h.element_size())
+
+    # roofline of the sweep kernel (one launch = one Jacobi iteration)
+    peak, peak_kind = _peaks()
+    bytes_per_launch = 2 * k * n + 4 * (n + 1) + 8 * m + 8 * n + 8 * n
+    launch_s = (sum(sweep_ms) / 1e3) / (args.steps * iters)
+    achieved = bytes_per_launch / launch_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"sweep_{args.workload}_traffic.json")
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get("dram_bytes_per_launch")
+
+    result = {
+        "metric": "sparse-stress node-updates/s",
+        "value": value,
+        "unit": "node-term updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "description": W["desc"],
+            "n": n, "m": m, "k": k, "iters": iters,
+            "stress_pairs": (f"{S} sources x {T} targets" if S > 0 else "exhaustive"),
+            "node_term_updates_per_step": terms_per_step,
+            "parallelism": f"replicas{world}",
+            "l2": "flushed between steps (256 MB write outside the timed events)",
+            "sweep_ms_per_step": sum(sweep_ms) / args.steps,
+        },
+        "roofline": {
+            "kernel": "k_sweep_f32 (one Jacobi iteration)",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "peak_kind": peak_kind,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "launch_us": launch_s * 1e6,
+        },
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "node-term updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": launches_per_step(iters, batches) * args.steps,
+        "stress_normalized": float(out.cpu()[3]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.workload)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+
+SAMPLE_K = 50
+SAMPLE_ITERS = 2
+SAMPLE_PMDS_N = 8192
+SAMPLE_SOURCES = 16
+
+
+def oracle_sample(workload: str):
+    """Times the CPU oracle on a bounded sample of the workload and scales each
+    stage to the full step by its cost model (Section 3 complexities):
+    max/min pivots, d_ip BFS, counts and weights ~ k (one O(m) BFS or O(n) pass
+    per pivot); PivotMDS ~ n k^2 (C^T C); sweeps ~ k * iters; stress ~ sources.
+    Returns (estimated seconds for one full step, per-stage dict)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1608_08909_gb300 import inputs as I
+
+    W = WORKLOADS[workload]
+    n, src, dst, k, iters = I.workload(workload, W["seed"])
+    S = W["S"]
+    ks = min(SAMPLE_K, k)
+    st = {}
+    t = time.perf_counter(); g = O.build_csr(n, src, dst); st["csr"] = time.perf_counter() - t
+    t = time.perf_counter(); piv = O.maxmin(g, ks); st["maxmin"] = (time.perf_counter() - t) * k / ks
+    t = time.perf_counter(); dip = O.pivot_dist(g, piv); st["pivot_dist"] = (time.perf_counter() - t) * k / ks
+    t = time.perf_counter()
+    reg = O.regions(dip)
+    O.histograms(dip, reg)
+    w = O.adapted_weights(dip, reg)
+    st["aggregate"] = (time.perf_counter() - t) * k / ks
+    nn = min(n, SAMPLE_PMDS_N)
+    t = time.perf_counter(); pos, _ = O.pivotmds(np.ascontiguousarray(dip[:, :nn]))
+    st["pivotmds"] = (time.perf_counter() - t) * (n / nn) * (k / ks) ** 2
+    pos0 = np.random.default_rng(0).normal(size=(n, 2))
+    t = time.perf_counter()
+    x = pos0
+    for _ in range(SAMPLE_ITERS):
+        x, _ = O.sweep_jacobi(g, piv, dip, w, x)
+    st["sweeps"] = (time.perf_counter() - t) * (k / ks) * iters / SAMPLE_ITERS
+    if S > 0:
+        t = time.perf_counter(); O.full_stress(g, x, SAMPLE_SOURCES, W["T"], W["seed"])
+        st["stress"] = (time.perf_counter() - t) * S / SAMPLE_SOURCES
+    else:
+        t = time.perf_counter(); O.full_stress(g, x); st["stress"] = time.perf_counter() - t
+    return sum(st.values()), st, (n, g.m, k, iters)
+
+
+def cpu_baseline(workload: str):
+    est, st, (n, m, k, iters) = oracle_sample(workload)
+    terms = iters * (k * n + 2 * m)
+    return {"value": terms / est, "unit": "node-term updates/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 C oracle, one thread, on the full {workload} graph with {min(SAMPLE_K, k)} of {k} "
+                       f"pivots, PivotMDS on {SAMPLE_PMDS_N} nodes, {SAMPLE_ITERS} of {iters} sweeps, "
+                       f"{SAMPLE_SOURCES} stress sources; stages scaled to the full step by their cost model"),
+            "est_step_s": est, "stage_s": {k_: round(v, 3) for k_, v in st.items()}}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.workload)
+    ests = []
+    for _ in range(args.steps):
+        est, st, (n, m, k, iters) = oracle_sample(args.workload)
+        ests.append(est)
+    terms = iters * (k * n + 2 * m)
+    total = sum(ests)
+    value = terms * args.steps / total
+    cb = cpu_baseline_from(value, args.workload, k, iters)
+    print(json.dumps({
+        "impl": "reference", "metric": "sparse-stress node-updates/s", "value": value,
+        "unit": "node-term updates/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"], "n": n, "m": m,
+                   "k": k, "iters": iters},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "node-term updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline_from(value, workload, k, iters):
+    return {"value": value, "unit": "node-term updates/s", "cores": 1, "kind": "oracle",
+            "sample": (f"each step: FP64 C oracle, one thread, full {workload} graph with {min(SAMPLE_K, k)} of {k} "
+                       f"pivots, PivotMDS on {SAMPLE_PMDS_N} nodes, {SAMPLE_ITERS} of {iters} sweeps, "
+                       f"{SAMPLE_SOURCES} stress sources; stages scaled by their cost model")}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rgg256k")
+    ap.add_argument("--iters", type=int, default=0, help="override the sweep count (0: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * ssm.h -- C ABI of the GB300 sparse stress layout library (libssm.so).
+ *
+ * The library computes the sparse stress model of Ortmann, Klimenta and
+ * Brandes, "A Sparse Stress Model" (arxiv 1608.08909): Algorithm 1 with the
+ * update of Eq. 4 applied Jacobi-style (every node from the previous
+ * iterate), on one GPU.  Call order for one layout:
+ *
+ *   ssm_build_graph -> ssm_select_pivots -> ssm_pivot_bfs -> ssm_aggregate_size
+ *   -> ssm_aggregate -> ssm_pivotmds -> ssm_iterate (repeatable) -> ssm_stress
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller unless the
+ *     comment says "host".  The library never allocates device memory: each
+ *     call that needs scratch takes a caller-allocated device workspace
+ *     (ws, ws_bytes) whose size comes from the matching *_workspace query;
+ *     it must be 256-byte aligned and is not used after the call's work on
+ *     `stream` completes.
+ *   - Calls are asynchronous on `stream` unless marked "synchronous".
+ *   - The return value reports argument and launch errors found on the host
+ *     (SSM_OK or a negative code; ssm_last_error() gives details).  Errors
+ *     found by a kernel are written to the caller's device word `status`
+ *     (first error wins; 0 means none) and read with ssm_check().  `status`
+ *     must be zeroed by the caller before first use.
+ *   - Graphs are simple and undirected, stored as CSR: rowptr[n+1] int32,
+ *     colidx[2m] int32, every row sorted ascending, no self-loops, no
+ *     repeated entries (as produced by ssm_build_graph).  Node ids are 0..n-1.
+ *   - Positions are interleaved (x, y) pairs: float[2n] for precision 32,
+ *     double[2n] for precision 64.
+ *   - The pivot-distance table d_ip is pivot-major uint16: dip[a*n + i] is the
+ *     hop distance between pivot a (the a-th selected pivot) and node i.
+ */
+#ifndef SSM_H
+#define SSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SSM_OK 0
+#define SSM_E_ARG (-1)           /* null pointer, size out of range, k > n ... */
+#define SSM_E_GRAPH (-2)         /* an edge endpoint outside 0..n-1 */
+#define SSM_E_DISCONNECTED (-3)  /* the graph has more than one component */
+#define SSM_E_DIST_OVERFLOW (-4) /* a hop distance above 65534 (uint16 table) */
+#define SSM_E_NOMEM (-5)         /* workspace smaller than its query */
+#define SSM_E_CUDA (-6)          /* a CUDA runtime call failed */
+#define SSM_E_TIMEOUT (-7)       /* a device-wide wait gave up (see each call) */
+#define SSM_E_NUMERIC (-8)       /* non-finite value or a failed eigen-solve */
+
+/* Text for a status code (static storage). */
+const char *ssm_status_string(int code);
+
+/* Detail of the last failing call on this host thread (thread-local; static
+ * storage valid until the next failing call on the same thread). */
+const char *ssm_last_error(void);
+
+/* Synchronous: waits for `stream`, then returns the device status word
+ * (SSM_OK if it is 0), or SSM_E_CUDA if the stream reported a CUDA error. */
+int ssm_check(const int32_t *status, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Graph.  Section 1: G = (V, E) simple and undirected, n = |V|, m = |E|.
+ * Builds the CSR from an undirected edge list (src[e], dst[e]), e < m_in:
+ * both directions stored, self-loops and repeated edges dropped, rows
+ * sorted ascending, then checks that G is connected (the paper keeps only
+ * the largest component, Section 4 "Data"; callers pass that component).
+ * rowptr has n+1 entries, colidx room for 2*m_in.  *m_out (host) receives m.
+ * Synchronous.  Errors are returned directly: SSM_E_GRAPH for an endpoint
+ * outside 0..n-1, SSM_E_DISCONNECTED if some node is unreachable from node 0.
+ * Requires 1 <= n, 0 <= m_in, 2*m_in < 2^31.
+ * ------------------------------------------------------------------- */
+size_t ssm_build_graph_workspace(int32_t n, int64_t m_in);
+int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst,
+                    int32_t *rowptr, int32_t *colidx, int64_t *m_out,
+                    void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Pivot sampling, "max/min sp" (Section 4.1; Algorithm 1 line 1):
+ * pivots[0] = start, then repeatedly the node maximising the hop distance to
+ * its closest chosen pivot, ties to the lowest node id.  Writes pivots[k]
+ * (int32, selection order).  1 <= k <= n.  Device errors: SSM_E_DISCONNECTED,
+ * SSM_E_TIMEOUT (a device-wide barrier waited longer than 2 s).
+ * ------------------------------------------------------------------- */
+size_t ssm_select_pivots_workspace(int32_t n);
+int ssm_select_pivots(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                      int32_t start, int32_t *pivots, int32_t *status,
+                      void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Pivot distances d_ip (Algorithm 1 line 2, unit edge lengths): one
+ * multi-source BFS from all k pivots at once.  Writes dip[k*n] (uint16,
+ * pivot-major).  1 <= k <= 65535, n*ceil(k/32) < 2^31.  Pivots need not be
+ * distinct.  Device errors: SSM_E_DISCONNECTED, SSM_E_DIST_OVERFLOW,
+ * SSM_E_TIMEOUT.
+ * ------------------------------------------------------------------- */
+size_t ssm_pivot_bfs_workspace(int32_t n, int32_t k);
+int ssm_pivot_bfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                  const int32_t *pivots, uint16_t *dip, int32_t *status,
+                  void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Regions and distance counts behind the adapted weights (Section 3):
+ *   region[i] = the lowest pivot index a minimising d_ia   (R(p) of the paper);
+ *   ecc_a     = max over i in R(a) of d_ia;
+ *   cnt[cnt_off[a] + t] = |{ i in R(a) : d_ia <= t }|, t = 0..ecc_a,
+ * so that w'_ia = s / d_ia^2 with s = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)].
+ * ssm_aggregate_size (synchronous) returns in *cnt_len (host) the table length
+ * sum_a (ecc_a + 1); ssm_aggregate fills region[n] int32, cnt_off[k+1] int32,
+ * cnt[cnt_len] uint32.  Workspace: ssm_aggregate_workspace(k) bytes for both.
+ * Device error SSM_E_ARG if cnt_len does not match the table.
+ * ------------------------------------------------------------------- */
+size_t ssm_aggregate_workspace(int32_t k);
+int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len,
+                       void *ws, size_t ws_bytes, cudaStream_t stream);
+int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *cnt_off,
+                  uint32_t *cnt, int64_t cnt_len, int32_t *status,
+                  void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Initial layout (Algorithm 1 lines 3-4): PivotMDS over the k pivots
+ * (Brandes and Pich 2007), then, if rescale != 0, a uniform scale so that the
+ * edge lengths of the layout sum to m (unit edge lengths).
+ *   delta_ia = d_ia^2, C = -1/2 J_n Delta J_k (double centring),
+ *   v1, v2 = eigenvectors of the two largest eigenvalues of C^T C (k x k, FP64),
+ *   each signed so its largest-magnitude entry (lowest index on a tie) is positive,
+ *   x_i = ((C v1)_i, (C v2)_i).
+ * Writes pos[2n] (float or double by precision 32/64) and, if eig is not NULL,
+ * the two eigenvalues to eig[2] (device, double).  2 <= k <= 1024.
+ * Device errors: SSM_E_NUMERIC (eigen-solve did not converge or zero layout).
+ * ------------------------------------------------------------------- */
+size_t ssm_pivotmds_workspace(int32_t n, int32_t k);
+int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                 const uint16_t *dip, void *pos, int32_t precision, int32_t rescale,
+                 double *eig, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Stress majorization (Eq. 4; Algorithm 1 lines 5-10), Jacobi schedule:
+ * each iteration computes every x_i^{t+1} from X^t,
+ *   x_i^{t+1} = [ sum_{j in N(i)} (x_j + (x_i - x_j)/r_ij)
+ *               + sum_{a: d_ia >= 2} w'_ia (x_pa + d_ia (x_i - x_pa)/r_ia) ]
+ *             / [ deg(i) + sum_{a: d_ia >= 2} w'_ia ],
+ *   w'_ia = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)] / d_ia^2,
+ * where r = ||x_i - x_j|| and a term with r == 0 contributes w * x_j only.
+ * Runs `iters` iterations on pos in place (precision 32: float, 64: double).
+ * After each iteration the relative change ||X^{t+1}-X^t||_F / ||X^t||_F is
+ * reduced in FP64; if tol > 0 the remaining iterations are skipped on the
+ * device once it falls below tol.  Writes *iters_done (device int32) and
+ * *rel_change (device double, the last computed change).  cnt_off and cnt are
+ * the tables of ssm_aggregate, cnt_len = cnt_off[k] (from ssm_aggregate_size).
+ * 1 <= iters, 1 <= k <= 4096.
+ * ------------------------------------------------------------------- */
+size_t ssm_iterate_workspace(int32_t n, int32_t k, int32_t precision);
+int ssm_iterate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off,
+                const uint32_t *cnt, int64_t cnt_len, void *pos, int32_t precision, int32_t iters,
+                double tol, int32_t *iters_done, double *rel_change, int32_t *status,
+                void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Full stress of a layout (Eq. 1, w_ij = d_ij^-2) with optimal scaling
+ * (Section 4: drawings are rescaled to their lowest stress).
+ * nsources == 0: exhaustive over all pairs i < j (a BFS from every node).
+ * nsources  > 0: nsources * ntargets sampled pairs: source j is node
+ *   (hi32(u) * n) >> 32 for u = splitmix64 value j of stream `seed`, and
+ *   target l of source j is t' + (t' >= source) with t' = (hi32(u) * (n-1)) >> 32
+ *   for u = value nsources + j*ntargets + l (value c of the stream is the
+ *   splitmix64 output for state seed + (c+1) * 0x9E3779B97F4A7C15).
+ * Writes out[4] (device double): {raw, alpha*, scaled, normalized}, with
+ *   raw = sum (r-d)^2/d^2, alpha* = S1/S2 (S1 = sum r/d, S2 = sum r^2/d^2),
+ *   scaled = N - S1^2/S2 (N pairs), normalized = scaled / C(n,2);
+ *   sampled sums are scaled by C(n,2)/N.  sums[4] (optional, device double)
+ *   receives {sum (r-d)^2/d^2, S1, S2, N} before scaling.
+ * All sums are FP64 in a fixed order.  Device errors: SSM_E_DISCONNECTED,
+ * SSM_E_DIST_OVERFLOW, SSM_E_TIMEOUT.  2 <= n.
+ * ------------------------------------------------------------------- */
+size_t ssm_stress_workspace(int32_t n, int32_t nsources, int32_t ntargets);
+int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const void *pos,
+               int32_t precision, int32_t nsources, int32_t ntargets, uint64_t seed,
+               double *out, double *sums, int32_t *status,
+               void *ws, size_t ws_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSM_H */

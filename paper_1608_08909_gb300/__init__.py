@@ -1,0 +1,289 @@
+"""GB300 sparse stress layout: Python binding of libssm (include/ssm.h).
+
+Argument marshalling only.  Every step runs in the CUDA kernels of
+``csrc/``; PyTorch provides device memory and streams.  There is no CPU
+fallback: if the compiled library is missing or no CUDA device is present,
+every call raises.
+
+The functions mirror the C ABI names (``ssm_build_graph`` ... ``ssm_stress``)
+and take / return torch tensors on the current CUDA device.  ``layout()`` runs
+the whole Algorithm 1 pipeline.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
+    "ssm_aggregate", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+]
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
+          -4: "hop distance above 65534", -5: "workspace too small", -6: "CUDA error", -7: "device wait timed out",
+          -8: "numerical failure"}
+
+
+class SSMError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        msg = f"{what}: status {code} ({STATUS.get(code, '?')})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libssm.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            v, i32, i64, u64, d, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_double, ctypes.c_size_t)
+            sig = {
+                "ssm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+                "ssm_last_error": (ctypes.c_char_p, []),
+                "ssm_check": (ctypes.c_int, [v, v]),
+                "ssm_build_graph_workspace": (sz, [i32, i64]),
+                "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, sz, v]),
+                "ssm_select_pivots_workspace": (sz, [i32]),
+                "ssm_select_pivots": (ctypes.c_int, [i32, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_pivot_bfs_workspace": (sz, [i32, i32]),
+                "ssm_pivot_bfs": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, sz, v]),
+                "ssm_aggregate_workspace": (sz, [i32]),
+                "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
+                "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
+                "ssm_pivotmds_workspace": (sz, [i32, i32]),
+                "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_iterate_workspace": (sz, [i32, i32, i32]),
+                "ssm_iterate": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
+                "ssm_stress_workspace": (sz, [i32, i32, i32]),
+                "ssm_stress": (ctypes.c_int, [i32, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("libssm needs a CUDA device; there is no CPU path")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _rc(code: int, what: str):
+    if code != 0:
+        raise SSMError(code, what, lib().ssm_last_error().decode(errors="replace"))
+
+
+def _ws(nbytes: int, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _status(device):
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def ssm_check(status: torch.Tensor, what: str = "device", stream=None):
+    """Synchronise and raise SSMError if the device status word is set."""
+    _rc(lib().ssm_check(_ptr(status), _stream(stream)), what)
+
+
+@dataclass
+class Graph:
+    n: int
+    m: int
+    rowptr: torch.Tensor  # int32 [n+1]
+    colidx: torch.Tensor  # int32 [2m]
+
+
+@dataclass
+class Pivots:
+    k: int
+    pivots: torch.Tensor   # int32 [k]
+    dip: torch.Tensor      # uint16 [k, n]
+    region: torch.Tensor   # int32 [n]
+    cnt_off: torch.Tensor  # int32 [k+1]
+    cnt: torch.Tensor      # uint32 [cnt_off[k]]
+
+
+def ssm_build_graph(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> Graph:
+    """CSR of the simple undirected graph on the edge list (device int32 tensors)."""
+    _require_cuda()
+    L = lib()
+    dev = src.device
+    src = src.contiguous().to(torch.int32)
+    dst = dst.contiguous().to(torch.int32)
+    m_in = src.numel()
+    rowptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    colidx = torch.empty(max(2 * m_in, 1), dtype=torch.int32, device=dev)
+    ws = _ws(L.ssm_build_graph_workspace(n, m_in), dev)
+    m = ctypes.c_int64(0)
+    _rc(L.ssm_build_graph(n, m_in, _ptr(src), _ptr(dst), _ptr(rowptr), _ptr(colidx), ctypes.byref(m), _ptr(ws),
+                          ws.numel(), _stream(stream)), "ssm_build_graph")
+    return Graph(n, int(m.value), rowptr, colidx[: 2 * m.value])
+
+
+def ssm_select_pivots(g: Graph, k: int, start: int = 0, stream=None, check: bool = True) -> torch.Tensor:
+    L = lib()
+    dev = g.rowptr.device
+    piv = torch.empty(k, dtype=torch.int32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_select_pivots_workspace(g.n), dev)
+    _rc(L.ssm_select_pivots(g.n, _ptr(g.rowptr), _ptr(g.colidx), k, start, _ptr(piv), _ptr(st), _ptr(ws), ws.numel(),
+                            _stream(stream)), "ssm_select_pivots")
+    if check:
+        ssm_check(st, "ssm_select_pivots", stream)
+    return piv
+
+
+def ssm_pivot_bfs(g: Graph, pivots: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
+    L = lib()
+    dev = g.rowptr.device
+    k = pivots.numel()
+    dip = torch.empty((k, g.n), dtype=torch.uint16, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_pivot_bfs_workspace(g.n, k), dev)
+    _rc(L.ssm_pivot_bfs(g.n, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(pivots.contiguous()), _ptr(dip), _ptr(st),
+                        _ptr(ws), ws.numel(), _stream(stream)), "ssm_pivot_bfs")
+    if check:
+        ssm_check(st, "ssm_pivot_bfs", stream)
+    return dip
+
+
+def ssm_aggregate_size(dip: torch.Tensor, stream=None) -> int:
+    L = lib()
+    k, n = dip.shape
+    ws = _ws(L.ssm_aggregate_workspace(k), dip.device)
+    out = ctypes.c_int64(0)
+    _rc(L.ssm_aggregate_size(n, k, _ptr(dip), ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_aggregate_size")
+    return int(out.value)
+
+
+def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, check: bool = True):
+    """Returns (region[n] int32, cnt_off[k+1] int32, cnt[cnt_len] uint32)."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    if cnt_len is None:
+        cnt_len = ssm_aggregate_size(dip, stream)
+    region = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(k + 1, dtype=torch.int32, device=dev)
+    cnt = torch.empty(cnt_len, dtype=torch.uint32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_aggregate_workspace(k), dev)
+    _rc(L.ssm_aggregate(n, k, _ptr(dip), _ptr(region), _ptr(off), _ptr(cnt), cnt_len, _ptr(st), _ptr(ws), ws.numel(),
+                        _stream(stream)), "ssm_aggregate")
+    if check:
+        ssm_check(st, "ssm_aggregate", stream)
+    return region, off, cnt
+
+
+def ssm_pivotmds(g: Graph, dip: torch.Tensor, precision: int = 32, rescale: bool = True, stream=None,
+                 check: bool = True):
+    """Returns (pos [n,2] float32/float64, eigenvalues [2] float64)."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    pos = torch.empty((n, 2), dtype=torch.float64 if precision == 64 else torch.float32, device=dev)
+    eig = torch.empty(2, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_pivotmds_workspace(n, k), dev)
+    _rc(L.ssm_pivotmds(n, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(dip), _ptr(pos), precision, int(bool(rescale)),
+                       _ptr(eig), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_pivotmds")
+    if check:
+        ssm_check(st, "ssm_pivotmds", stream)
+    return pos, eig
+
+
+class IterateWorkspace:
+    """Reusable device buffers for ssm_iterate (so timed loops allocate nothing)."""
+
+    def __init__(self, n: int, k: int, precision: int, device):
+        self.ws = _ws(lib().ssm_iterate_workspace(n, k, precision), device)
+        self.iters_done = torch.zeros(1, dtype=torch.int32, device=device)
+        self.rel = torch.zeros(1, dtype=torch.float64, device=device)
+        self.status = _status(device)
+
+
+def ssm_iterate(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, tol: float = 0.0, stream=None,
+                work: IterateWorkspace | None = None, check: bool = True):
+    """Runs `iters` Jacobi sweeps of Eq. 4 on pos in place; returns (iters_done, rel_change) tensors."""
+    L = lib()
+    precision = 64 if pos.dtype == torch.float64 else 32
+    if work is None:
+        work = IterateWorkspace(g.n, p.k, precision, pos.device)
+    _rc(L.ssm_iterate(g.n, _ptr(g.rowptr), _ptr(g.colidx), p.k, _ptr(p.pivots), _ptr(p.dip), _ptr(p.cnt_off),
+                      _ptr(p.cnt), p.cnt.numel(), _ptr(pos), precision, iters, float(tol), _ptr(work.iters_done), _ptr(work.rel),
+                      _ptr(work.status), _ptr(work.ws), work.ws.numel(), _stream(stream)), "ssm_iterate")
+    if check:
+        ssm_check(work.status, "ssm_iterate", stream)
+    return work.iters_done, work.rel
+
+
+class StressWorkspace:
+    def __init__(self, n: int, nsources: int, ntargets: int, device):
+        self.ws = _ws(lib().ssm_stress_workspace(n, nsources, ntargets), device)
+        self.out = torch.zeros(4, dtype=torch.float64, device=device)
+        self.sums = torch.zeros(4, dtype=torch.float64, device=device)
+        self.status = _status(device)
+
+
+def ssm_stress(g: Graph, pos: torch.Tensor, nsources: int = 0, ntargets: int = 0, seed: int = 0, stream=None,
+               work: StressWorkspace | None = None, check: bool = True):
+    """Returns (out[4], sums[4]) float64 device tensors: {raw, alpha*, scaled, normalized}."""
+    L = lib()
+    precision = 64 if pos.dtype == torch.float64 else 32
+    if work is None:
+        work = StressWorkspace(g.n, nsources, ntargets, pos.device)
+    _rc(L.ssm_stress(g.n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(pos), precision, nsources, ntargets,
+                     ctypes.c_uint64(seed), _ptr(work.out), _ptr(work.sums), _ptr(work.status), _ptr(work.ws),
+                     work.ws.numel(), _stream(stream)), "ssm_stress")
+    if check:
+        ssm_check(work.status, "ssm_stress", stream)
+    return work.out, work.sums
+
+
+def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, device="cuda", stream=None):
+    """Algorithm 1 lines 1-4 on the GPU: returns (Graph, Pivots, initial positions, eigenvalues)."""
+    _require_cuda()
+    src = torch.as_tensor(src, dtype=torch.int32).to(device, non_blocking=True)
+    dst = torch.as_tensor(dst, dtype=torch.int32).to(device, non_blocking=True)
+    g = ssm_build_graph(n, src, dst, stream)
+    piv = ssm_select_pivots(g, k, start, stream)
+    dip = ssm_pivot_bfs(g, piv, stream)
+    region, off, cnt = ssm_aggregate(dip, stream=stream)
+    pos, eig = ssm_pivotmds(g, dip, precision, True, stream)
+    return g, Pivots(k, piv, dip, region, off, cnt), pos, eig
+
+
+def layout(n: int, src, dst, k: int = 200, iters: int = 100, tol: float = 0.0, start: int = 0,
+           precision: int = 32, device="cuda"):
+    """Whole pipeline (Algorithm 1, Jacobi schedule); returns positions [n,2] on the device."""
+    g, p, pos, _ = prepare(n, src, dst, k, start, precision, device)
+    ssm_iterate(g, p, pos, iters, tol)
+    return pos

@@ -1,0 +1,144 @@
+// Regions R(p) and the per-pivot cumulative distance counts behind the
+// adapted weights w'_ip = s / d_ip^2 (Section 3, after Eq. 4):
+//   region[i] = lowest pivot index a minimising d_ia,
+//   ecc_a     = max_{i in R(a)} d_ia,
+//   cnt[cnt_off[a] + t] = |{ i in R(a) : d_ia <= t }|.
+// The sweep then reads s = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)]
+// instead of a stored k x n weight table.
+#include "common.cuh"
+
+namespace ssm {
+
+constexpr int kAggThreads = 256;
+
+// one thread per node: nearest pivot (ties to the lowest index) and the
+// per-pivot maximum distance over its region
+__global__ void __launch_bounds__(kAggThreads) k_region_ecc(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                                            int32_t *__restrict__ region, unsigned *__restrict__ ecc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned best = 0xFFFFFFFFu;
+    int32_t arg = 0;
+    const uint16_t *col = dip + i;
+    for (int32_t a = 0; a < k; ++a) {
+      const unsigned d = __ldg(col + (size_t)a * n);
+      if (d < best) { best = d; arg = a; }
+    }
+    if (region) region[i] = arg;
+    atomicMax(ecc + arg, best);
+  }
+}
+
+__global__ void k_table_len(int32_t k, const unsigned *__restrict__ ecc, long long *__restrict__ len) {
+  __shared__ long long part[32];
+  long long s = 0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) s += (long long)ecc[a] + 1;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += part[w];
+    *len = t;
+  }
+}
+
+// one block: cnt_off = exclusive scan of (ecc + 1); flags a length mismatch
+__global__ void k_cnt_off(int32_t k, const unsigned *__restrict__ ecc, int32_t *__restrict__ cnt_off,
+                          long long expect, int32_t *__restrict__ status) {
+  if (threadIdx.x != 0) return;
+  long long acc = 0;
+  for (int a = 0; a < k; ++a) {
+    cnt_off[a] = (int32_t)acc;
+    acc += (long long)ecc[a] + 1;
+  }
+  cnt_off[k] = (int32_t)acc;
+  if (acc != expect) dev_fail(status, SSM_E_ARG);
+}
+
+__global__ void __launch_bounds__(kAggThreads) k_histogram(int32_t n, const uint16_t *__restrict__ dip,
+                                                           const int32_t *__restrict__ region,
+                                                           const int32_t *__restrict__ cnt_off, int64_t cnt_len,
+                                                           unsigned *__restrict__ cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = region[i];
+    const int64_t slot = (int64_t)cnt_off[a] + __ldg(dip + (size_t)a * n + i);
+    if (slot < cnt_len) atomicAdd(cnt + slot, 1u);
+  }
+}
+
+// one warp per pivot: inclusive prefix over t of the histogram row
+__global__ void k_row_prefix(int32_t k, const int32_t *__restrict__ cnt_off, int64_t cnt_len,
+                             unsigned *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = warp; a < k; a += nwarps) {
+    const int64_t b = cnt_off[a], e = cnt_off[a + 1] < cnt_len ? cnt_off[a + 1] : cnt_len;
+    unsigned carry = 0;
+    for (int64_t base = b; base < e; base += 32) {
+      const int64_t t = base + lane;
+      unsigned v = t < e ? cnt[t] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      v += carry;
+      if (t < e) cnt[t] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+}
+
+static int grid_for(int64_t items, int threads) {
+  int64_t b = (items + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * 8;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace ssm
+
+SSM_API size_t ssm_aggregate_workspace(int32_t k) {
+  ssm::Carver c(nullptr, 0);
+  c.take<unsigned>(k > 0 ? k : 1);
+  c.take<long long>(1);
+  return c.size();
+}
+
+SSM_API int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len, void *ws,
+                               size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || k < 1 || !dip || !cnt_len || !ws) return fail(SSM_E_ARG, "ssm_aggregate_size: bad argument");
+  Carver c(ws, ws_bytes);
+  unsigned *ecc = c.take<unsigned>(k);
+  long long *len = c.take<long long>(1);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate_size: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
+  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc);
+  k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
+  long long h = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  *cnt_len = h;
+  return SSM_OK;
+}
+
+SSM_API int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *cnt_off, uint32_t *cnt,
+                          int64_t cnt_len, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || k < 1 || !dip || !region || !cnt_off || !cnt || !status || !ws || cnt_len < k)
+    return fail(SSM_E_ARG, "ssm_aggregate: bad argument");
+  if (cnt_len >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_aggregate: table length must be below 2^31");
+  Carver c(ws, ws_bytes);
+  unsigned *ecc = c.take<unsigned>(k);
+  c.take<long long>(1);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)cnt_len * sizeof(uint32_t), s));
+  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
+  k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
+  k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}

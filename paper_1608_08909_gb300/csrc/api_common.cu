@@ -1,0 +1,64 @@
+// Status strings, per-thread error text, device queries.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+namespace ssm {
+
+static thread_local char g_last_error[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return SSM_OK;
+  return fail(SSM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+int cooperative_blocks(const void *kernel, int threads, size_t smem, int max_per_sm) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) return 0;
+  if (per_sm > max_per_sm) per_sm = max_per_sm;
+  return per_sm * num_sms();
+}
+
+}  // namespace ssm
+
+SSM_API const char *ssm_status_string(int code) {
+  switch (code) {
+    case SSM_OK: return "ok";
+    case SSM_E_ARG: return "invalid argument";
+    case SSM_E_GRAPH: return "edge endpoint out of range";
+    case SSM_E_DISCONNECTED: return "graph is disconnected";
+    case SSM_E_DIST_OVERFLOW: return "hop distance above 65534";
+    case SSM_E_NOMEM: return "workspace too small";
+    case SSM_E_CUDA: return "CUDA error";
+    case SSM_E_TIMEOUT: return "device-wide wait timed out";
+    case SSM_E_NUMERIC: return "numerical failure";
+    default: return "unknown status";
+  }
+}
+
+SSM_API const char *ssm_last_error(void) { return ssm::g_last_error; }
+
+SSM_API int ssm_check(const int32_t *status, cudaStream_t stream) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, status, sizeof h, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return ssm::cuda_status(e, "ssm_check");
+  if (h != 0) return ssm::fail(h, "device reported: %s", ssm_status_string(h));
+  return SSM_OK;
+}

@@ -1,0 +1,341 @@
+// Breadth-first searches on the device:
+//   * ssm_select_pivots: max/min-sp pivot sampling (Section 4.1), one pruned
+//     level-synchronous BFS per new pivot inside one persistent kernel;
+//   * ssm_pivot_bfs:     all k pivot distances d_ip (Algorithm 1 line 2) in one
+//     multi-source BFS over per-node bitsets (one bit per source), frontier
+//     compacted with warp ballots.
+// Both run as cooperative persistent grids with a device-wide barrier per BFS
+// level; every barrier wait is bounded (SSM_E_TIMEOUT).
+#include "bfs.cuh"
+
+namespace ssm {
+
+constexpr int kBfsThreads = 512;
+constexpr unsigned kInf = 0xFFFFFFFFu;
+
+// --------------------------------------------------------------------------
+// max/min sp
+// --------------------------------------------------------------------------
+struct MaxMinArgs {
+  int32_t n;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  int32_t k;
+  int32_t start;
+  int32_t *pivots;
+  int32_t *status;
+  unsigned *mind;  // [n] hop distance to the closest chosen pivot
+  unsigned *q0, *q1;  // [n] frontier queues (alternate by level parity)
+  unsigned *qcnt;     // [3] queue lengths, rotated by level
+  unsigned long long *best;  // [2] packed (mind << 32 | ~node) maxima, by pivot parity
+  BarrierState *bar;
+};
+
+// Pruned BFS from the newest pivot p: node v is expanded at level L+1 only
+// if L+1 < mind[v].  Since mind (a minimum of distance functions) changes by
+// at most 1 along an edge, every node whose distance to p is below its old
+// mind is reached along a shortest path of such nodes, so the result is
+// exactly mind = min(mind, d(p, .)).
+__global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
+  const unsigned n = (unsigned)A.n;
+
+  for (unsigned v = gtid; v < n; v += nthreads) A.mind[v] = kInf;
+  if (!grid_barrier(A.bar, A.status)) return;
+
+  unsigned p = (unsigned)A.start;
+  for (int j = 0; j < A.k; ++j) {
+    if (gtid == 0) {
+      A.pivots[j] = (int32_t)p;
+      A.mind[p] = 0;
+      A.q0[0] = p;
+      A.qcnt[0] = 1;
+      A.qcnt[1] = 0;
+      A.qcnt[2] = 0;
+    }
+    const bool last = (j == A.k - 1);
+    if (last && j > 0) break;  // the final pivot needs no search
+    if (!grid_barrier(A.bar, A.status)) return;
+
+    for (unsigned L = 0;; ++L) {
+      const unsigned c = __ldcg(A.qcnt + L % 3);
+      if (c == 0) break;
+      if (gtid == 0) A.qcnt[(L + 2) % 3] = 0;
+      const unsigned *qin = (L & 1) ? A.q1 : A.q0;
+      unsigned *qout = (L & 1) ? A.q0 : A.q1;
+      unsigned *cout = A.qcnt + (L + 1) % 3;
+      const unsigned nd = L + 1;
+      for (unsigned base = gwarp * 32u; base < c; base += nwarps * 32u) {
+        const unsigned e = base + lane;
+        int beg = 0, end = 0;
+        if (e < c) {
+          const unsigned u = __ldcg(qin + e);
+          beg = __ldg(A.rowptr + u);
+          end = __ldg(A.rowptr + u + 1);
+        }
+        warp_for_each_neighbor(beg, end, A.colidx, [&](int, bool act, int v) {
+          bool push = false;
+          if (act && nd < __ldcg(A.mind + v)) {
+            const unsigned old = atomicMin(A.mind + v, nd);
+            push = old > nd;
+          }
+          warp_append(push, (unsigned)v, qout, cout);
+        });
+      }
+      if (!grid_barrier(A.bar, A.status)) return;
+    }
+
+    // argmax of mind, ties to the lowest node id
+    unsigned long long key = 0;
+    for (unsigned v = gtid; v < n; v += nthreads) {
+      const unsigned long long kk = ((unsigned long long)__ldcg(A.mind + v) << 32) | (unsigned long long)(~v);
+      key = kk > key ? kk : key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, key, o);
+      key = t > key ? t : key;
+    }
+    if (lane == 0) atomicMax(A.best + (j & 1), key);
+    if (!grid_barrier(A.bar, A.status)) return;
+    key = __ldcg(A.best + (j & 1));
+    if (gtid == 0) A.best[(j + 1) & 1] = 0;
+    if ((unsigned)(key >> 32) == kInf) {  // some node was never reached
+      if (gtid == 0) dev_fail(A.status, SSM_E_DISCONNECTED);
+      return;
+    }
+    if (last) break;
+    p = ~(unsigned)key;
+  }
+}
+
+int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+                  int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Carver c(ws, ws_bytes);
+  MaxMinArgs A;
+  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
+  A.pivots = pivots; A.status = status;
+  A.mind = c.take<unsigned>(n);
+  A.q0 = c.take<unsigned>(n);
+  A.q1 = c.take<unsigned>(n);
+  A.qcnt = c.take<unsigned>(4);
+  A.best = c.take<unsigned long long>(2);
+  A.bar = c.take<BarrierState>(1);
+  if (!ws) return (int)c.size();
+  if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+  const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, 0, 2);
+  if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: kernel cannot be resident");
+  void *args[] = {&A};
+  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_maxmin, dim3(blocks), dim3(kBfsThreads), args, 0, s));
+  return SSM_OK;
+}
+
+size_t maxmin_workspace(int32_t n) {
+  Carver c(nullptr, 0);
+  c.take<unsigned>(n);
+  c.take<unsigned>(n);
+  c.take<unsigned>(n);
+  c.take<unsigned>(4);
+  c.take<unsigned long long>(2);
+  c.take<BarrierState>(1);
+  return c.size();
+}
+
+// --------------------------------------------------------------------------
+// multi-source bitset BFS
+// --------------------------------------------------------------------------
+struct MsBfsArgs {
+  int32_t n;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  int32_t k;
+  int32_t W;  // 32-bit words per node = ceil(k/32)
+  const int32_t *sources;
+  uint16_t *dist;  // [k][n]
+  int32_t *status;
+  unsigned *seen;  // [n*W] sources that have reached each node
+  unsigned *F[3];  // [n*W] frontier bits of levels L, L+1, L+2 (rotated)
+  unsigned *Q[3];  // [n*W] queue of (node*W + word) entries with nonzero frontier bits
+  unsigned *qcnt;  // [4] queue lengths, rotated by level
+  unsigned long long *ndisc;  // total (source, node) discoveries
+  BarrierState *bar;
+};
+
+// Level L expands every queued (u, w) entry: the sources in frontier word
+// F_L[u][w] are pushed to each neighbour v.  New bits are claimed with one
+// atomicOr on seen[v][w] (so each (source, node) pair is discovered exactly
+// once, at its BFS level), merged into F_{L+1}[v][w], and the first claimant
+// of a word appends (v, w) to the next queue.  Entries of F_{L-1} are cleared
+// through their queue so the three frontier arrays can rotate.
+__global__ void __launch_bounds__(kBfsThreads) k_msbfs(MsBfsArgs A) {
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
+  const unsigned n = (unsigned)A.n, W = (unsigned)A.W, k = (unsigned)A.k;
+  unsigned long long found = 0;
+
+  // level 0: the sources themselves (warp-uniform loop so appends stay converged)
+  for (unsigned base = gwarp * 32u; base < k; base += nwarps * 32u) {
+    const unsigned a = base + lane;
+    bool push = false;
+    unsigned idx = 0;
+    if (a < k) {
+      const unsigned v = (unsigned)__ldg(A.sources + a);
+      const unsigned w = a >> 5, bit = 1u << (a & 31u);
+      idx = v * W + w;
+      const unsigned old = atomicOr(A.seen + idx, bit);
+      if (!(old & bit)) {
+        A.dist[(size_t)a * n + v] = 0;
+        ++found;
+        push = atomicOr(A.F[0] + idx, bit) == 0u;
+      }
+    }
+    warp_append(push, idx, A.Q[0], A.qcnt + 0);
+  }
+  if (!grid_barrier(A.bar, A.status)) return;
+
+  for (unsigned L = 0;; ++L) {
+    const unsigned c = __ldcg(A.qcnt + (L & 3u));
+    if (c == 0) break;
+    if (L + 1 > 65534u) {
+      if (gtid == 0) dev_fail(A.status, SSM_E_DIST_OVERFLOW);
+      break;
+    }
+    if (gtid == 0) A.qcnt[(L + 2) & 3u] = 0;
+    // clear F_{L-1} (its array becomes F_{L+2})
+    {
+      const unsigned cprev = __ldcg(A.qcnt + ((L + 3) & 3u));
+      const unsigned *qprev = A.Q[(L + 2) % 3];
+      unsigned *fprev = A.F[(L + 2) % 3];
+      for (unsigned e = gtid; e < cprev; e += nthreads) fprev[__ldcg(qprev + e)] = 0u;
+    }
+    const unsigned *qin = A.Q[L % 3];
+    const unsigned *fin = A.F[L % 3];
+    unsigned *fout = A.F[(L + 1) % 3];
+    unsigned *qout = A.Q[(L + 1) % 3];
+    unsigned *cout = A.qcnt + ((L + 1) & 3u);
+    const uint16_t nd = (uint16_t)(L + 1);
+    for (unsigned base = gwarp * 32u; base < c; base += nwarps * 32u) {
+      const unsigned e = base + lane;
+      int beg = 0, end = 0;
+      unsigned w = 0, f = 0;
+      if (e < c) {
+        const unsigned idx = __ldcg(qin + e);
+        const unsigned u = idx / W;
+        w = idx - u * W;
+        f = __ldcg(fin + idx);
+        beg = __ldg(A.rowptr + u);
+        end = __ldg(A.rowptr + u + 1);
+      }
+      warp_for_each_neighbor(beg, end, A.colidx, [&](int owner, bool act, int v) {
+        const unsigned wo = __shfl_sync(0xffffffffu, w, owner);
+        const unsigned fo = __shfl_sync(0xffffffffu, f, owner);
+        const unsigned nidx = (unsigned)v * W + wo;
+        bool push = false;
+        if (act) {
+          unsigned nb = fo & ~__ldcg(A.seen + nidx);
+          if (nb) {
+            nb &= ~atomicOr(A.seen + nidx, nb);
+            if (nb) {
+              push = atomicOr(fout + nidx, nb) == 0u;
+              found += (unsigned)__popc(nb);
+              uint16_t *col = A.dist + (size_t)(wo * 32u) * n + (unsigned)v;
+              while (nb) {
+                const unsigned b = (unsigned)__ffs(nb) - 1u;
+                col[(size_t)b * n] = nd;
+                nb &= nb - 1u;
+              }
+            }
+          }
+        }
+        warp_append(push, nidx, qout, cout);
+      });
+    }
+    if (!grid_barrier(A.bar, A.status)) return;
+  }
+
+  // every (source, node) pair must have been discovered
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
+  if (lane == 0 && found) atomicAdd(A.ndisc, found);
+  if (!grid_barrier(A.bar, A.status)) return;
+  if (gtid == 0 && __ldcg(A.ndisc) != (unsigned long long)k * n) {
+    int32_t cur = __ldcg(A.status);
+    if (cur == 0) dev_fail(A.status, SSM_E_DISCONNECTED);
+  }
+}
+
+static void msbfs_carve(Carver &c, MsBfsArgs &A, int32_t n, int32_t k) {
+  const size_t nw = (size_t)n * (size_t)((k + 31) / 32);
+  A.seen = c.take<unsigned>(nw);
+  for (int i = 0; i < 3; ++i) A.F[i] = c.take<unsigned>(nw);
+  for (int i = 0; i < 3; ++i) A.Q[i] = c.take<unsigned>(nw);
+  A.qcnt = c.take<unsigned>(4);
+  A.ndisc = c.take<unsigned long long>(1);
+  A.bar = c.take<BarrierState>(1);
+}
+
+size_t msbfs_workspace(int32_t n, int32_t k) {
+  Carver c(nullptr, 0);
+  MsBfsArgs A;
+  msbfs_carve(c, A, n, k);
+  return c.size();
+}
+
+int launch_msbfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
+                 uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Carver c(ws, ws_bytes);
+  MsBfsArgs A;
+  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.W = (k + 31) / 32;
+  A.sources = sources; A.dist = dist; A.status = status;
+  msbfs_carve(c, A, n, k);
+  if (!c.ok) return fail(SSM_E_NOMEM, "multi-source BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const size_t nw = (size_t)n * (size_t)A.W;
+  // seen, F[0..2] are contiguous carve-outs of equal size; clear each
+  SSM_TRY_CUDA(cudaMemsetAsync(A.seen, 0, nw * sizeof(unsigned), s));
+  for (int i = 0; i < 3; ++i) SSM_TRY_CUDA(cudaMemsetAsync(A.F[i], 0, nw * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.ndisc, 0, sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
+  const int blocks = cooperative_blocks((const void *)k_msbfs, kBfsThreads, 0, 2);
+  if (blocks < 1) return fail(SSM_E_CUDA, "multi-source BFS: kernel cannot be resident");
+  void *args[] = {&A};
+  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs, dim3(blocks), dim3(kBfsThreads), args, 0, s));
+  return SSM_OK;
+}
+
+}  // namespace ssm
+
+// ---------------------------------------------------------------- C ABI
+SSM_API size_t ssm_select_pivots_workspace(int32_t n) { return n > 0 ? ssm::maxmin_workspace(n) : 0; }
+
+SSM_API int ssm_select_pivots(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+                              int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (n < 1 || !rowptr || !colidx || !pivots || !status || !ws)
+    return ssm::fail(SSM_E_ARG, "ssm_select_pivots: null pointer or n < 1");
+  if (k < 1 || k > n) return ssm::fail(SSM_E_ARG, "ssm_select_pivots: need 1 <= k <= n (k=%d, n=%d)", k, n);
+  if (start < 0 || start >= n) return ssm::fail(SSM_E_ARG, "ssm_select_pivots: start %d outside 0..n-1", start);
+  return ssm::launch_maxmin(n, rowptr, colidx, k, start, pivots, status, ws, ws_bytes, stream);
+}
+
+SSM_API size_t ssm_pivot_bfs_workspace(int32_t n, int32_t k) {
+  return (n > 0 && k > 0) ? ssm::msbfs_workspace(n, k) : 0;
+}
+
+SSM_API int ssm_pivot_bfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *pivots,
+                          uint16_t *dip, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (n < 1 || !rowptr || !colidx || !pivots || !dip || !status || !ws)
+    return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: null pointer or n < 1");
+  if (k < 1 || k > 65535) return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: need 1 <= k <= 65535 (k=%d)", k);
+  if ((int64_t)n * ((k + 31) / 32) >= (int64_t)1 << 31)
+    return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: n*ceil(k/32) must be below 2^31");
+  return ssm::launch_msbfs(n, rowptr, colidx, k, pivots, dip, status, ws, ws_bytes, stream);
+}

@@ -1,0 +1,226 @@
+// Graph construction (Section 1: a simple undirected graph G = (V, E)):
+// edge list -> CSR with both directions, rows sorted ascending, self-loops and
+// repeated edges dropped, followed by a connectivity check (one BFS).
+//
+//   count degrees (atomics) -> exclusive scan -> scatter both directions
+//   -> sort every row (warp bitonic in registers for rows <= 32, block bitonic
+//      in shared memory up to kSmemSortCap, block bitonic in global memory
+//      beyond) -> flag first occurrences -> scan flags -> compact.
+#include <algorithm>
+
+#include "bfs.cuh"
+#include "scan.cuh"
+
+namespace ssm {
+
+constexpr int kSmemSortCap = 8192;  // ints sorted in shared memory by one block
+constexpr int kSortBlock = 512;
+constexpr int32_t kPad = 0x7fffffff;
+
+__global__ void k_count_degrees(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                int32_t n, int *__restrict__ deg, int32_t *__restrict__ status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = src[e], v = dst[e];
+    if (u < 0 || u >= n || v < 0 || v >= n) {
+      dev_fail(status, SSM_E_GRAPH);
+      continue;
+    }
+    if (u == v) continue;
+    atomicAdd(deg + u, 1);
+    atomicAdd(deg + v, 1);
+  }
+}
+
+__global__ void k_scatter(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int32_t n,
+                          const int *__restrict__ off, int *__restrict__ cursor, int32_t *__restrict__ tmp) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = src[e], v = dst[e];
+    if (u < 0 || u >= n || v < 0 || v >= n || u == v) continue;
+    tmp[off[u] + atomicAdd(cursor + u, 1)] = v;
+    tmp[off[v] + atomicAdd(cursor + v, 1)] = u;
+  }
+}
+
+// Bitonic sorting network in the variant whose comparators all point
+// upwards: for block size b, first compare i with its mirror i ^ (b-1), then
+// half-cleaners i ^ j for j = b/4 .. 1.  Virtual +inf padding at positions
+// >= len never has to move, so comparisons touching it can be skipped.
+
+// rows of length <= 32: one warp per row, values in registers
+__global__ void k_sort_small_rows(int32_t n, const int *__restrict__ off, int32_t *__restrict__ tmp,
+                                  unsigned *__restrict__ big_rows, unsigned *__restrict__ big_count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = warp; row < n; row += nwarps) {
+    const int b = off[row], len = off[row + 1] - b;
+    if (len > 32) {
+      if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = (unsigned)row;
+      continue;
+    }
+    int32_t x = (int)lane < len ? tmp[b + lane] : kPad;
+#pragma unroll
+    for (int bs = 2; bs <= 32; bs <<= 1) {
+      int32_t y = __shfl_xor_sync(0xffffffffu, x, bs - 1);
+      x = (lane & (bs >> 1)) ? max(x, y) : min(x, y);
+#pragma unroll
+      for (int j = bs >> 2; j >= 1; j >>= 1) {
+        y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? max(x, y) : min(x, y);
+      }
+    }
+    if ((int)lane < len) tmp[b + lane] = x;
+  }
+}
+
+template <class Get, class Put>
+__device__ void block_bitonic(int len, Get get, Put put) {
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int bs = 2; bs <= P; bs <<= 1) {
+    for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+      // pair index i -> (lo, hi) in the mirror stage
+      const int blk = i / (bs >> 1), r = i % (bs >> 1);
+      const int lo = blk * bs + r, hi = blk * bs + bs - 1 - r;
+      if (hi < len) {
+        const int32_t a = get(lo), c = get(hi);
+        if (a > c) { put(lo, c); put(hi, a); }
+      }
+    }
+    __syncthreads();
+    for (int j = bs >> 2; j >= 1; j >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        const int lo = (i / j) * 2 * j + (i % j), hi = lo + j;
+        if (hi < len) {
+          const int32_t a = get(lo), c = get(hi);
+          if (a > c) { put(lo, c); put(hi, a); }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// rows longer than 32: one block per row
+__global__ void __launch_bounds__(kSortBlock) k_sort_big_rows(const int *__restrict__ off, int32_t *__restrict__ tmp,
+                                                               const unsigned *__restrict__ big_rows,
+                                                               const unsigned *__restrict__ big_count) {
+  __shared__ int32_t sbuf[kSmemSortCap];
+  const unsigned cnt = *big_count;
+  for (unsigned t = blockIdx.x; t < cnt; t += gridDim.x) {
+    const unsigned row = big_rows[t];
+    const int b = off[row], len = off[row + 1] - b;
+    int32_t *g = tmp + b;
+    if (len <= kSmemSortCap) {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) sbuf[i] = g[i];
+      __syncthreads();
+      block_bitonic(len, [&](int i) { return sbuf[i]; }, [&](int i, int32_t v) { sbuf[i] = v; });
+      for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = sbuf[i];
+    } else {
+      block_bitonic(len, [&](int i) { return __ldcg(g + i); }, [&](int i, int32_t v) { __stcg(g + i, v); });
+    }
+    __syncthreads();
+  }
+}
+
+// flag[t] = 1 for the first occurrence of a value within its (sorted) row
+__global__ void k_flag_unique(int32_t n, const int *__restrict__ off, const int32_t *__restrict__ tmp,
+                              int *__restrict__ flag) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+    const int b = off[row], e = off[row + 1];
+    for (int t = b; t < e; ++t) flag[t] = (t == b || tmp[t] != tmp[t - 1]) ? 1 : 0;
+  }
+}
+
+__global__ void k_compact(int32_t n, int64_t total, const int *__restrict__ off, const int32_t *__restrict__ tmp,
+                          const int *__restrict__ flag, const int *__restrict__ pos, int32_t *__restrict__ rowptr,
+                          int32_t *__restrict__ colidx) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride)
+    if (flag[t]) colidx[pos[t]] = tmp[t];
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row <= n; row += stride)
+    rowptr[row] = pos[off[row]];
+}
+
+struct BuildWs {
+  int *deg, *off, *cursor, *flag, *pos, *tiles;
+  int32_t *tmp;
+  unsigned *big_rows, *big_count;
+  int32_t *status;
+  void *bfs_ws;
+  size_t bfs_bytes;
+};
+
+static size_t carve_build(Carver &c, BuildWs &w, int32_t n, int64_t m_in) {
+  const int64_t e2 = 2 * m_in;
+  w.deg = c.take<int>(n);
+  w.off = c.take<int>((size_t)n + 1);
+  w.cursor = c.take<int>(n);
+  w.tmp = c.take<int32_t>((size_t)(e2 > 0 ? e2 : 1));
+  w.flag = c.take<int>((size_t)(e2 > 0 ? e2 : 1));
+  w.pos = c.take<int>((size_t)e2 + 1);
+  int64_t tiles = scan_tiles(e2 > n ? e2 : n);
+  w.tiles = c.take<int>((size_t)(tiles > 0 ? tiles : 1));
+  w.big_rows = c.take<unsigned>(n);
+  w.big_count = c.take<unsigned>(1);
+  w.status = c.take<int32_t>(2);
+  w.bfs_bytes = maxmin_workspace(n);
+  w.bfs_ws = c.take<char>(w.bfs_bytes);
+  return c.size();
+}
+
+}  // namespace ssm
+
+SSM_API size_t ssm_build_graph_workspace(int32_t n, int64_t m_in) {
+  if (n < 1 || m_in < 0) return 0;
+  ssm::Carver c(nullptr, 0);
+  ssm::BuildWs w;
+  return ssm::carve_build(c, w, n, m_in);
+}
+
+SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst, int32_t *rowptr,
+                            int32_t *colidx, int64_t *m_out, void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || m_in < 0 || !rowptr || !colidx || !m_out || !ws || (m_in > 0 && (!src || !dst)))
+    return fail(SSM_E_ARG, "ssm_build_graph: null pointer or bad size (n=%d, m_in=%lld)", n, (long long)m_in);
+  if (2 * m_in >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_build_graph: 2*m_in must be below 2^31");
+  Carver c(ws, ws_bytes);
+  BuildWs w;
+  carve_build(c, w, n, m_in);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_build_graph: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const int sms = num_sms();
+  const int eblocks = (int)std::min<int64_t>((m_in + 255) / 256 + 1, (int64_t)sms * 16);
+  const int nblocks = (int)std::min<int64_t>(((int64_t)n + 255) / 256 + 1, (int64_t)sms * 16);
+  SSM_TRY_CUDA(cudaMemsetAsync(w.deg, 0, (size_t)n * sizeof(int), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.cursor, 0, (size_t)n * sizeof(int), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.big_count, 0, sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.status, 0, 2 * sizeof(int32_t), s));
+  k_count_degrees<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.deg, w.status);
+  int rc = exclusive_scan(w.deg, w.off, n, w.tiles, s);
+  if (rc) return rc;
+  k_scatter<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.off, w.cursor, w.tmp);
+  k_sort_small_rows<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.big_rows, w.big_count);
+  k_sort_big_rows<<<sms * 2, kSortBlock, 0, s>>>(w.off, w.tmp, w.big_rows, w.big_count);
+  k_flag_unique<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.flag);
+  // total directed entries before dedupe = off[n]; read it to size the scan
+  int total = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&total, w.off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int32_t hstatus = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&hstatus, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hstatus) return fail(hstatus, "ssm_build_graph: %s", ssm_status_string(hstatus));
+  rc = exclusive_scan(w.flag, w.pos, total, w.tiles, s);
+  if (rc) return rc;
+  k_compact<<<std::max(eblocks, nblocks), 256, 0, s>>>(n, total, w.off, w.tmp, w.flag, w.pos, rowptr, colidx);
+  SSM_TRY_CUDA(cudaGetLastError());
+  // connectivity: one BFS from node 0 (status[1] receives its pivot slot)
+  rc = launch_maxmin(n, rowptr, colidx, 1, 0, w.status + 1, w.status, w.bfs_ws, w.bfs_bytes, s);
+  if (rc) return rc;
+  int32_t uniq = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&uniq, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaMemcpyAsync(&hstatus, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  *m_out = uniq / 2;
+  if (hstatus) return fail(hstatus, "ssm_build_graph: %s", ssm_status_string(hstatus));
+  return SSM_OK;
+}

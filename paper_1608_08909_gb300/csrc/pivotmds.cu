@@ -1,0 +1,655 @@
+// Initial layout (Algorithm 1 lines 3-4): PivotMDS over the k pivots
+// (Brandes and Pich 2007, cited by the paper) and the edge-length rescale.
+//
+// With Delta = [d_ia^2] (n x k) and C = -1/2 J_n Delta J_k (double centring),
+//   C^T C = 1/4 J_k (Delta^T Delta - s s^T / n) J_k,   s_a = sum_i d_ia^2,
+// so the only O(n k^2) work is the integer Gram matrix G = Delta^T Delta.
+// G is accumulated exactly (128-bit integers), which makes it independent of
+// summation order; everything after it is k x k FP64:
+//   k_gram      G = Delta^T Delta (upper tiles, 64x64 per block, node chunks)
+//   k_colsum    s_a
+//   k_prepare_b B = 1/4 J (G - s s^T/n) J
+//   k_eigen     top-2 eigenpairs of B, FP64 subspace iteration with
+//               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (one block)
+//   k_project   x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa),
+//               the sum in compensated (two-float) FP32 arithmetic
+//   k_edge_sum / k_rescale: scale so that sum_E ||x_i - x_j|| = m.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ssm {
+
+constexpr int kGT = 64;          // Gram tile edge
+constexpr int kGStage = 32;      // nodes per shared-memory stage
+constexpr int kGChunk = 8192;    // nodes per block
+constexpr int kGPad = kGT + 4;   // padded row (keeps 16-byte alignment)
+constexpr int kEigP = 8;         // subspace dimension
+constexpr int kEigThreads = 256;
+constexpr int kMaxPivotsMds = 1024;
+constexpr int kEigScratch = (kEigThreads / 32) * (kEigP * (kEigP + 1) / 2);  // doubles for block_sum
+
+// ------------------------------------------------------------- Gram matrix
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long v) {
+  lo += v;
+  hi += (lo < v) ? 1ull : 0ull;
+}
+
+__global__ void __launch_bounds__(256) k_gram(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                              unsigned long long *__restrict__ Glo,
+                                              unsigned long long *__restrict__ Ghi) {
+  __shared__ __align__(16) unsigned sA[kGStage][kGPad];
+  __shared__ __align__(16) unsigned sB[kGStage][kGPad];
+  __shared__ unsigned s_dmax;
+  const int T = (k + kGT - 1) / kGT;
+  int p = blockIdx.x, ta = 0;
+  while (p >= T - ta) { p -= T - ta; ++ta; }
+  const int tb = ta + p;
+  const int i_begin = blockIdx.y * kGChunk;
+  const int i_end = min(n, i_begin + kGChunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+  unsigned long long lo[4][4], hi[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) lo[r][c] = hi[r][c] = 0ull;
+
+  for (int i0 = i_begin; i0 < i_end; i0 += kGStage) {
+    if (threadIdx.x == 0) s_dmax = 0;
+    __syncthreads();
+    unsigned dm = 0;
+    for (int q = threadIdx.x; q < kGStage * kGT; q += blockDim.x) {
+      const int c = q % kGStage, r = q / kGStage;  // consecutive threads: consecutive nodes
+      const int i = i0 + c;
+      const int a = ta * kGT + r, b = tb * kGT + r;
+      const unsigned da = (a < k && i < i_end) ? __ldg(dip + (size_t)a * n + i) : 0u;
+      const unsigned db = (b < k && i < i_end) ? __ldg(dip + (size_t)b * n + i) : 0u;
+      sA[c][r] = da * da;
+      sB[c][r] = db * db;
+      dm = max(dm, max(da, db));
+    }
+    atomicMax(&s_dmax, dm);
+    __syncthreads();
+    if (s_dmax <= 23170u) {
+      // 32 products of values below 2^29 stay below 2^64: accumulate the
+      // stage with plain 64-bit multiply-adds, then fold into 128 bits
+      unsigned long long st[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) st[r][c] = 0ull;
+#pragma unroll 4
+      for (int c = 0; c < kGStage; ++c) {
+        const uint4 av = *reinterpret_cast<const uint4 *>(&sA[c][ty * 4]);
+        const uint4 bv = *reinterpret_cast<const uint4 *>(&sB[c][tx * 4]);
+        const unsigned a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) st[r][q] += (unsigned long long)a4[r] * b4[q];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) add128(lo[r][q], hi[r][q], st[r][q]);
+    } else {
+      for (int c = 0; c < kGStage; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            add128(lo[r][q], hi[r][q], (unsigned long long)sA[c][ty * 4 + r] * sB[c][tx * 4 + q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = ta * kGT + ty * 4 + r, b = tb * kGT + tx * 4 + q;
+      if (a >= k || b >= k || a > b) continue;
+      const size_t o = (size_t)a * k + b;
+      const unsigned long long old = atomicAdd(Glo + o, lo[r][q]);
+      const unsigned long long carry = (old + lo[r][q] < old) ? 1ull : 0ull;
+      if (hi[r][q] + carry) atomicAdd(Ghi + o, hi[r][q] + carry);
+    }
+}
+
+// s_a = sum_i d_ia^2 (exact: below 2^63 for n < 2^31)
+__global__ void k_colsum(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                         unsigned long long *__restrict__ s) {
+  __shared__ unsigned long long part[32];
+  for (int a = blockIdx.x; a < k; a += gridDim.x) {
+    unsigned long long acc = 0;
+    const uint16_t *row = dip + (size_t)a * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned long long d = __ldg(row + i);
+      acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)blockDim.x / 32; ++w) t += part[w];
+      s[a] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// B = 1/4 J_k (G - s s^T / n) J_k  (one block, FP64)
+__global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__restrict__ Glo,
+                            const unsigned long long *__restrict__ Ghi, const unsigned long long *__restrict__ s,
+                            double *__restrict__ B, double *__restrict__ rowmean) {
+  __shared__ double red[32];
+  const double two64 = 18446744073709551616.0;
+  const double inv_n = 1.0 / (double)n;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int a = t / k, b = t % k;
+    const int lo_ = min(a, b), hi_ = max(a, b);
+    const size_t o = (size_t)lo_ * k + hi_;
+    const double g = (double)Ghi[o] * two64 + (double)Glo[o];
+    B[t] = g - ((double)s[a] * (double)s[b]) * inv_n;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < k; ++b) acc += B[(size_t)a * k + b];
+    rowmean[a] = acc / (double)k;
+  }
+  __syncthreads();
+  double g = 0.0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) g += rowmean[a];
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+    red[0] = t / (double)k;
+  }
+  __syncthreads();
+  const double gm = red[0];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int a = t / k, b = t % k;
+    B[t] = 0.25 * (B[t] - rowmean[a] - rowmean[b] + gm);
+  }
+}
+
+// ------------------------------------------------------------- eigen-solve
+// block-wide sum of N doubles per thread (result broadcast to all threads)
+template <int N>
+__device__ void block_sum(double (&v)[N], double *scratch /* [warps*N] */) {
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < N; ++j) scratch[w * N + j] = v[j];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += scratch[q * N + j];
+    v[j] = t;
+  }
+  __syncthreads();
+}
+
+// cyclic Jacobi on a tiny symmetric P x P matrix (one thread); eigenvalues
+// on the diagonal of H, eigenvectors in the columns of Q, sorted descending
+__device__ void tiny_jacobi(int P, double *H, double *Q) {
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) Q[i * P + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) {
+        tot += H[i * P + j] * H[i * P + j];
+        if (i != j) off += H[i * P + j] * H[i * P + j];
+      }
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int p = 0; p < P; ++p)
+      for (int q = p + 1; q < P; ++q) {
+        const double apq = H[p * P + q];
+        if (apq == 0.0) continue;
+        const double theta = (H[q * P + q] - H[p * P + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < P; ++r) {
+          const double hp = H[r * P + p], hq = H[r * P + q];
+          H[r * P + p] = c * hp - s * hq;
+          H[r * P + q] = s * hp + c * hq;
+        }
+        for (int r = 0; r < P; ++r) {
+          const double hp = H[p * P + r], hq = H[q * P + r];
+          H[p * P + r] = c * hp - s * hq;
+          H[q * P + r] = s * hp + c * hq;
+        }
+        for (int r = 0; r < P; ++r) {
+          const double qp = Q[r * P + p], qq = Q[r * P + q];
+          Q[r * P + p] = c * qp - s * qq;
+          Q[r * P + q] = s * qp + c * qq;
+        }
+      }
+  }
+  // selection sort, descending eigenvalues
+  for (int i = 0; i < P; ++i) {
+    int m = i;
+    for (int j = i + 1; j < P; ++j)
+      if (H[j * P + j] > H[m * P + m]) m = j;
+    if (m != i) {
+      const double t = H[i * P + i];
+      H[i * P + i] = H[m * P + m];
+      H[m * P + m] = t;
+      for (int r = 0; r < P; ++r) {
+        const double u = Q[r * P + i];
+        Q[r * P + i] = Q[r * P + m];
+        Q[r * P + m] = u;
+      }
+    }
+  }
+}
+
+// orthonormalise the P columns of V (k x P, row-major in shared memory) by
+// Gram-Schmidt applied twice per column; a column that vanishes is replaced
+// by a fixed pseudo-random vector
+__device__ void orthonormalise(int k, int P, double *V, double *scratch, unsigned long long salt) {
+  for (int j = 0; j < P; ++j) {
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      double nrm0[1] = {0.0};
+      for (int r = threadIdx.x; r < k; r += blockDim.x) nrm0[0] += V[r * P + j] * V[r * P + j];
+      block_sum<1>(nrm0, scratch);
+      for (int pass = 0; pass < 2; ++pass) {
+        double dots[kEigP];
+#pragma unroll
+        for (int q = 0; q < kEigP; ++q) dots[q] = 0.0;
+        for (int r = threadIdx.x; r < k; r += blockDim.x)
+#pragma unroll
+          for (int q = 0; q < kEigP; ++q)
+            if (q < j) dots[q] += V[r * P + q] * V[r * P + j];
+        block_sum<kEigP>(dots, scratch);
+        for (int r = threadIdx.x; r < k; r += blockDim.x)
+#pragma unroll
+          for (int q = 0; q < kEigP; ++q)
+            if (q < j) V[r * P + j] -= dots[q] * V[r * P + q];
+        __syncthreads();
+      }
+      double nrm[1] = {0.0};
+      for (int r = threadIdx.x; r < k; r += blockDim.x) nrm[0] += V[r * P + j] * V[r * P + j];
+      block_sum<1>(nrm, scratch);
+      if (nrm[0] > 1e-24 * nrm0[0] && nrm[0] > 0.0) {
+        const double inv = 1.0 / sqrt(nrm[0]);
+        for (int r = threadIdx.x; r < k; r += blockDim.x) V[r * P + j] *= inv;
+        __syncthreads();
+        break;
+      }
+      for (int r = threadIdx.x; r < k; r += blockDim.x)
+        V[r * P + j] = (double)(int64_t)(splitmix64_at(salt + 1000003ull * j + 7919ull * attempt, r) >> 11) *
+                           (1.0 / 4503599627370496.0) - 1.0;
+      __syncthreads();
+    }
+  }
+}
+
+struct EigOut {
+  double lam[2];
+  double sigma[2];  // sum_a v_a
+  double kappa[2];  // sum_a cbar_a v_a - gbar * sigma
+  int32_t iters;
+  int32_t converged;
+};
+
+// top-2 eigenpairs of B (k x k, FP64) by subspace iteration of dimension P
+__global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, const double *__restrict__ B,
+                                                       const unsigned long long *__restrict__ s,
+                                                       double *__restrict__ vout /* [2][k] */,
+                                                       EigOut *__restrict__ out, double *__restrict__ eig_user,
+                                                       int32_t *__restrict__ status, int maxit, double tol) {
+  extern __shared__ __align__(16) double sm[];
+  const int P = min(kEigP, k);
+  double *V = sm;               // k x P
+  double *Y = V + (size_t)k * P;  // k x P
+  double *scratch = Y + (size_t)k * P;  // kEigScratch doubles
+  __shared__ double H[kEigP * kEigP], Q[kEigP * kEigP];
+  __shared__ int s_done;
+
+  for (int t = threadIdx.x; t < k * P; t += blockDim.x)
+    V[t] = (double)(splitmix64_at(0x5eed5eedull, (unsigned long long)t) >> 11) * (1.0 / 4503599627370496.0) - 1.0;
+  __syncthreads();
+  orthonormalise(k, P, V, scratch, 0x1234ull);
+  if (threadIdx.x == 0) s_done = 0;
+  __syncthreads();
+
+  int it = 0;
+  for (; it < maxit; ++it) {
+    // Y = B V (one warp per row, lanes over columns)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = warp; r < k; r += nwarp) {
+      double acc[kEigP];
+#pragma unroll
+      for (int q = 0; q < kEigP; ++q) acc[q] = 0.0;
+      const double *brow = B + (size_t)r * k;
+      for (int c = lane; c < k; c += 32) {
+        const double bv = __ldg(brow + c);
+#pragma unroll
+        for (int q = 0; q < kEigP; ++q)
+          if (q < P) acc[q] += bv * V[c * P + q];
+      }
+#pragma unroll
+      for (int q = 0; q < kEigP; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < kEigP; ++q)
+          if (q < P) Y[r * P + q] = acc[q];
+    }
+    __syncthreads();
+    // H = V^T Y (symmetric P x P)
+    double h[kEigP * (kEigP + 1) / 2];
+#pragma unroll
+    for (int q = 0; q < kEigP * (kEigP + 1) / 2; ++q) h[q] = 0.0;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      int q = 0;
+#pragma unroll
+      for (int i = 0; i < kEigP; ++i)
+#pragma unroll
+        for (int j = i; j < kEigP; ++j, ++q)
+          if (j < P) h[q] += V[r * P + i] * Y[r * P + j];
+    }
+    block_sum<kEigP * (kEigP + 1) / 2>(h, scratch);
+    if (threadIdx.x == 0) {
+      int q = 0;
+      for (int i = 0; i < kEigP; ++i)
+        for (int j = i; j < kEigP; ++j, ++q)
+          if (j < P) {
+            // symmetrise V^T B V from both triangles' estimates
+            H[i * P + j] = h[q];
+            H[j * P + i] = h[q];
+          }
+      tiny_jacobi(P, H, Q);
+    }
+    __syncthreads();
+    // Ritz vectors W = V Q (into V) and B W = Y Q (into Y); residuals of the top two
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      double wv[kEigP], yv[kEigP];
+#pragma unroll
+      for (int j = 0; j < kEigP; ++j) {
+        wv[j] = 0.0;
+        yv[j] = 0.0;
+        if (j < P)
+          for (int l = 0; l < P; ++l) {
+            wv[j] += V[r * P + l] * Q[l * P + j];
+            yv[j] += Y[r * P + l] * Q[l * P + j];
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < kEigP; ++j)
+        if (j < P) {
+          V[r * P + j] = wv[j];
+          Y[r * P + j] = yv[j];
+        }
+    }
+    __syncthreads();
+    double res[2] = {0.0, 0.0};
+    for (int r = threadIdx.x; r < k; r += blockDim.x)
+      for (int j = 0; j < 2 && j < P; ++j) {
+        const double e = Y[r * P + j] - H[j * P + j] * V[r * P + j];
+        res[j] += e * e;
+      }
+    block_sum<2>(res, scratch);
+    const double lam0 = fabs(H[0]);
+    if (threadIdx.x == 0) s_done = (sqrt(res[0]) <= tol * lam0 && sqrt(res[1]) <= tol * lam0) ? 1 : 0;
+    __syncthreads();
+    if (s_done) break;
+    // next basis: orthonormalised B W
+    for (int t = threadIdx.x; t < k * P; t += blockDim.x) V[t] = Y[t];
+    __syncthreads();
+    orthonormalise(k, P, V, scratch, 0x9e37ull + (unsigned long long)it);
+  }
+  // top-2 Ritz vectors are columns 0, 1 of V; sign: largest |entry| positive
+  __shared__ int s_big[2];
+  if (threadIdx.x < 2) {
+    const int j = threadIdx.x;
+    int big = 0;
+    for (int r = 1; r < k; ++r)
+      if (fabs(V[r * P + j]) > fabs(V[big * P + j])) big = r;
+    s_big[j] = big;
+  }
+  __syncthreads();
+  const double sg0 = V[s_big[0] * P + 0] < 0 ? -1.0 : 1.0;
+  const double sg1 = V[s_big[1] * P + 1] < 0 ? -1.0 : 1.0;
+  double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const double inv_n = 1.0 / (double)n;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    const double v0 = sg0 * V[r * P + 0], v1 = sg1 * V[r * P + 1];
+    vout[r] = v0;
+    vout[k + r] = v1;
+    const double cbar = (double)s[r] * inv_n;
+    sums[0] += v0;
+    sums[1] += v1;
+    sums[2] += cbar * v0;
+    sums[3] += cbar * v1;
+    sums[4] += cbar;
+  }
+  block_sum<5>(sums, scratch);
+  if (threadIdx.x == 0) {
+    const double gbar = sums[4] / (double)k;
+    out->lam[0] = H[0];
+    out->lam[1] = P > 1 ? H[1 * P + 1] : 0.0;
+    out->sigma[0] = sums[0];
+    out->sigma[1] = sums[1];
+    out->kappa[0] = sums[2] - gbar * sums[0];
+    out->kappa[1] = sums[3] - gbar * sums[1];
+    out->iters = it;
+    out->converged = s_done;
+    if (eig_user) {
+      eig_user[0] = out->lam[0];
+      eig_user[1] = out->lam[1];
+    }
+    if (!s_done || !(H[0] > 0.0)) dev_fail(status, SSM_E_NUMERIC);
+  }
+}
+
+// ------------------------------------------------------------- projection
+// two-float accumulation: (hi, lo) += a * (bh + bl), a exact in FP32
+__device__ __forceinline__ void ff_madd(float &hi, float &lo, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float pe = fmaf(a, bh, -p);  // exact rounding error of the product
+  const float s = hi + p;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (p - bp);  // exact rounding error of the sum
+  lo += e + fmaf(a, bl, pe);
+  hi = s;
+}
+
+// BIG (read on the device): some d_ia^2 is not exact in FP32 (d > 4095), so
+// it is split into two exact parts
+__global__ void __launch_bounds__(256) k_project(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                                 const double *__restrict__ vv, const EigOut *__restrict__ eo,
+                                                 const unsigned *__restrict__ dmax, void *__restrict__ pos,
+                                                 int precision) {
+  extern __shared__ __align__(16) float4 sv[];  // per pivot: v0 hi, v0 lo, v1 hi, v1 lo
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    const double v0 = vv[a], v1 = vv[k + a];
+    const float h0 = (float)v0, h1 = (float)v1;
+    sv[a] = make_float4(h0, (float)(v0 - (double)h0), h1, (float)(v1 - (double)h1));
+  }
+  __syncthreads();
+  const double sig0 = eo->sigma[0], sig1 = eo->sigma[1], kap0 = eo->kappa[0], kap1 = eo->kappa[1];
+  const bool BIG = (unsigned long long)(*dmax) * (*dmax) >= (1ull << 24);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+    unsigned long long rs = 0;
+    const uint16_t *col = dip + i;
+    for (int a = 0; a < k; ++a) {
+      const unsigned d = __ldg(col + (size_t)a * n);
+      const unsigned dd = d * d;
+      rs += dd;
+      const float4 v = sv[a];
+      if (!BIG) {
+        const float df = (float)dd;  // exact below 2^24
+        ff_madd(xh, xl, df, v.x, v.y);
+        ff_madd(yh, yl, df, v.z, v.w);
+      } else {
+        const float dh = (float)(dd & 0xFFFFF000u), dl = (float)(dd & 0xFFFu);  // both exact
+        ff_madd(xh, xl, dh, v.x, v.y);
+        ff_madd(xh, xl, dl, v.x, v.y);
+        ff_madd(yh, yl, dh, v.z, v.w);
+        ff_madd(yh, yl, dl, v.z, v.w);
+      }
+    }
+    const double rbar = (double)rs / (double)k;
+    const double x = -0.5 * (((double)xh + (double)xl) - rbar * sig0 - kap0);
+    const double y = -0.5 * (((double)yh + (double)yl) - rbar * sig1 - kap1);
+    if (precision == 64) reinterpret_cast<double2 *>(pos)[i] = make_double2(x, y);
+    else reinterpret_cast<float2 *>(pos)[i] = make_float2((float)x, (float)y);
+  }
+}
+
+__global__ void k_dmax(int64_t count, const uint16_t *__restrict__ dip, unsigned *__restrict__ out) {
+  unsigned m = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned)__ldg(dip + t));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ------------------------------------------------------------- rescale
+template <class T2>
+__global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
+                                                  double *__restrict__ part, unsigned *__restrict__ done,
+                                                  double *__restrict__ scale, int32_t *__restrict__ status) {
+  __shared__ double red[8];
+  __shared__ unsigned s_ticket;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T2 xi = pos[i];
+    for (int t = __ldg(rowptr + i); t < __ldg(rowptr + i + 1); ++t) {
+      const int j = __ldg(colidx + t);
+      if (j <= i) continue;
+      const T2 xj = pos[j];
+      const double dx = (double)xi.x - (double)xj.x, dy = (double)xi.y - (double)xj.y;
+      acc += sqrt(dx * dx + dy * dy);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+    part[blockIdx.x] = t;
+    __threadfence();
+    s_ticket = atomicAdd(done, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1 || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(part + b);
+  const double m = (double)__ldg(rowptr + n) * 0.5;
+  if (!(tot > 0.0) || !isfinite(tot)) {
+    dev_fail(status, SSM_E_NUMERIC);
+    *scale = 1.0;
+  } else {
+    *scale = m / tot;
+  }
+}
+
+template <class T2>
+__global__ void k_rescale(int32_t n, T2 *__restrict__ pos, const double *__restrict__ scale) {
+  const double sc = *scale;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T2 x = pos[i];
+    x.x = (decltype(x.x))((double)x.x * sc);
+    x.y = (decltype(x.y))((double)x.y * sc);
+    pos[i] = x;
+  }
+}
+
+struct MdsWs {
+  unsigned long long *Glo, *Ghi, *s;
+  double *B, *rowmean, *vv, *part, *scale;
+  EigOut *eo;
+  unsigned *done, *dmax;
+};
+
+static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
+  (void)n;
+  const size_t kk = (size_t)k * k;
+  w.Glo = c.take<unsigned long long>(kk);
+  w.Ghi = c.take<unsigned long long>(kk);
+  w.s = c.take<unsigned long long>(k);
+  w.B = c.take<double>(kk);
+  w.rowmean = c.take<double>(k);
+  w.vv = c.take<double>(2 * (size_t)k);
+  w.part = c.take<double>(4096);
+  w.scale = c.take<double>(1);
+  w.eo = c.take<EigOut>(1);
+  w.done = c.take<unsigned>(1);
+  w.dmax = c.take<unsigned>(1);
+  return c.size();
+}
+
+}  // namespace ssm
+
+SSM_API size_t ssm_pivotmds_workspace(int32_t n, int32_t k) {
+  if (n < 1 || k < 1) return 0;
+  ssm::Carver c(nullptr, 0);
+  ssm::MdsWs w;
+  return ssm::carve_mds(c, w, n, k);
+}
+
+SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const uint16_t *dip,
+                         void *pos, int32_t precision, int32_t rescale, double *eig, int32_t *status, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || !dip || !pos || !status || !ws || (rescale && (!rowptr || !colidx)))
+    return fail(SSM_E_ARG, "ssm_pivotmds: null pointer or n < 1");
+  if (k < 2 || k > kMaxPivotsMds || k > n) return fail(SSM_E_ARG, "ssm_pivotmds: need 2 <= k <= min(n, %d)", kMaxPivotsMds);
+  if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_pivotmds: precision must be 32 or 64");
+  Carver c(ws, ws_bytes);
+  MdsWs w;
+  carve_mds(c, w, n, k);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_pivotmds: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const size_t kk = (size_t)k * k;
+  const int sms = num_sms();
+  SSM_TRY_CUDA(cudaMemsetAsync(w.Glo, 0, kk * sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.Ghi, 0, kk * sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.done, 0, sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), s));
+  const int T = (k + kGT - 1) / kGT;
+  dim3 ggrid((unsigned)(T * (T + 1) / 2), (unsigned)((n + kGChunk - 1) / kGChunk));
+  k_gram<<<ggrid, 256, 0, s>>>(n, k, dip, w.Glo, w.Ghi);
+  k_colsum<<<std::min(k, sms * 4), 256, 0, s>>>(n, k, dip, w.s);
+  k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
+  const int P = std::min(kEigP, (int)k);
+  const size_t esm = (2 * (size_t)k * P + kEigScratch) * sizeof(double);
+  SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
+  const int64_t cnt = (int64_t)k * n;
+  k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
+  const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
+  const size_t psm = (size_t)k * sizeof(float4);
+  k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);
+  if (rescale) {
+    const int eb = std::min(pb, 4096);
+    if (precision == 64) {
+      k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, w.part, w.done, w.scale, status);
+      k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
+    } else {
+      k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, w.part, w.done, w.scale, status);
+      k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
+    }
+  }
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}

@@ -1,0 +1,222 @@
+// Full stress of a layout (Eq. 1, w_ij = d_ij^-2) with the optimal scale
+// (Section 4: every drawing is rescaled to its lowest stress before it is
+// reported), exhaustive over all pairs or over sampled pairs.
+//
+// Pair distances come from the multi-source bitset BFS (bfs.cu) run from a
+// batch of sources into a [sources][n] uint16 table; a pair kernel then
+// accumulates, in FP64 and in a fixed order,
+//   sum (r/d - 1)^2 = sum (r-d)^2/d^2,  S1 = sum r/d,  S2 = sum r^2/d^2,  N,
+// and the final kernel forms {raw, alpha* = S1/S2, N - S1^2/S2, normalized}.
+#include <algorithm>
+
+#include "bfs.cuh"
+
+namespace ssm {
+
+constexpr int kPairThreads = 256;
+constexpr int kExhaustiveBatch = 1024;  // sources per BFS batch (32 bitset words)
+
+__global__ void k_sample_sources(int32_t n, int32_t S, uint64_t seed, int32_t *__restrict__ src) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S; j += gridDim.x * blockDim.x)
+    src[j] = (int32_t)(((splitmix64_at(seed, (uint64_t)j) >> 32) * (uint64_t)n) >> 32);
+}
+
+__global__ void k_batch_sources(int32_t base, int32_t B, int32_t *__restrict__ src) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x) src[j] = base + j;
+}
+
+template <class T2>
+__device__ __forceinline__ void pair_terms(const T2 *__restrict__ pos, int i, int j, unsigned d, double (&acc)[4]) {
+  const T2 a = pos[i], b = pos[j];
+  const double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y;
+  const double r = sqrt(dx * dx + dy * dy);
+  const double t = r / (double)d;
+  acc[0] += (t - 1.0) * (t - 1.0);
+  acc[1] += t;
+  acc[2] += t * t;
+  acc[3] += 1.0;
+}
+
+__device__ __forceinline__ void block_store_sums(double (&acc)[4], double *__restrict__ part) {
+  __shared__ double red[kPairThreads / 32][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[threadIdx.x >> 5][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kPairThreads / 32; ++w) t += red[w][threadIdx.x];
+    part[4 * (size_t)blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// exhaustive batch: sources base..base+B-1, pairs (base+a, v) with v > base+a
+template <class T2>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_exhaustive(int32_t n, int32_t base, int32_t B,
+                                                                    const uint16_t *__restrict__ dist,
+                                                                    const T2 *__restrict__ pos,
+                                                                    double *__restrict__ part,
+                                                                    int32_t *__restrict__ status) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t total = (int64_t)B * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / n), v = (int)(t - (int64_t)a * n);
+    const int i = base + a;
+    if (v <= i) continue;
+    const unsigned d = __ldg(dist + t);
+    if (d == 0xFFFFu || d == 0u) {
+      dev_fail(status, SSM_E_DISCONNECTED);
+      continue;
+    }
+    pair_terms(pos, i, v, d, acc);
+  }
+  block_store_sums(acc, part);
+}
+
+// sampled: source j (src[j]), targets l = 0..T-1 from the splitmix64 stream
+template <class T2>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_sampled(int32_t n, int32_t S, int32_t T, uint64_t seed,
+                                                                 const int32_t *__restrict__ src,
+                                                                 const uint16_t *__restrict__ dist,
+                                                                 const T2 *__restrict__ pos,
+                                                                 double *__restrict__ part,
+                                                                 int32_t *__restrict__ status) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t total = (int64_t)S * T;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / T);
+    const int s = __ldg(src + j);
+    const uint64_t u = splitmix64_at(seed, (uint64_t)S + (uint64_t)t);
+    int v = (int)(((u >> 32) * (uint64_t)(n - 1)) >> 32);
+    v += (v >= s) ? 1 : 0;
+    const unsigned d = __ldg(dist + (size_t)j * n + v);
+    if (d == 0xFFFFu || d == 0u) {
+      dev_fail(status, SSM_E_DISCONNECTED);
+      continue;
+    }
+    pair_terms(pos, s, v, d, acc);
+  }
+  block_store_sums(acc, part);
+}
+
+// fixed-order sum of all block partials, then the stress values
+__global__ void k_stress_final(int32_t n, int64_t nparts, const double *__restrict__ part, int sampled,
+                               double *__restrict__ out, double *__restrict__ sums) {
+  __shared__ double red[32][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t b = threadIdx.x; b < nparts; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += part[4 * b + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[threadIdx.x >> 5][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int w = 0; w < (int)blockDim.x / 32; ++w)
+    for (int q = 0; q < 4; ++q) s[q] += red[w][q];
+  const double pairs = 0.5 * (double)n * (double)(n - 1);
+  const double f = sampled ? pairs / s[3] : 1.0;
+  if (sums)
+    for (int q = 0; q < 4; ++q) sums[q] = s[q];
+  out[0] = s[0] * f;
+  out[1] = s[2] > 0.0 ? s[1] / s[2] : 0.0;
+  out[2] = (s[2] > 0.0 ? s[3] - s[1] * s[1] / s[2] : s[3]) * f;
+  out[3] = out[2] / pairs;
+}
+
+static int pair_blocks() { return num_sms() * 8; }
+
+struct StressWs {
+  int32_t *src;
+  uint16_t *dist;
+  double *part;
+  void *bfs;
+  size_t bfs_bytes;
+};
+
+static size_t carve_stress(Carver &c, StressWs &w, int32_t n, int32_t S, int32_t nbatches) {
+  w.src = c.take<int32_t>(S);
+  w.dist = c.take<uint16_t>((size_t)S * n);
+  w.part = c.take<double>(4 * (size_t)pair_blocks() * (size_t)nbatches);
+  w.bfs_bytes = msbfs_workspace(n, S);
+  w.bfs = c.take<char>(w.bfs_bytes);
+  return c.size();
+}
+
+static void stress_shape(int32_t n, int32_t nsources, int32_t *S, int32_t *nbatches) {
+  if (nsources > 0) {
+    *S = nsources;
+    *nbatches = 1;
+  } else {
+    *S = std::min<int32_t>(n, kExhaustiveBatch);
+    *nbatches = (n + *S - 1) / *S;
+  }
+}
+
+}  // namespace ssm
+
+SSM_API size_t ssm_stress_workspace(int32_t n, int32_t nsources, int32_t ntargets) {
+  (void)ntargets;
+  if (n < 2 || nsources < 0) return 0;
+  int32_t S, nb;
+  ssm::stress_shape(n, nsources, &S, &nb);
+  ssm::Carver c(nullptr, 0);
+  ssm::StressWs w;
+  return ssm::carve_stress(c, w, n, S, nb);
+}
+
+SSM_API int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const void *pos, int32_t precision,
+                       int32_t nsources, int32_t ntargets, uint64_t seed, double *out, double *sums, int32_t *status,
+                       void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 2 || !rowptr || !colidx || !pos || !out || !status || !ws)
+    return fail(SSM_E_ARG, "ssm_stress: null pointer or n < 2");
+  if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_stress: precision must be 32 or 64");
+  if (nsources < 0 || nsources > 65535 || (nsources > 0 && ntargets < 1))
+    return fail(SSM_E_ARG, "ssm_stress: need 0 <= nsources <= 65535 and ntargets >= 1 when sampling");
+  int32_t S, nb;
+  stress_shape(n, nsources, &S, &nb);
+  if ((int64_t)n * ((S + 31) / 32) >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_stress: n*ceil(S/32) too large");
+  Carver c(ws, ws_bytes);
+  StressWs w;
+  carve_stress(c, w, n, S, nb);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_stress: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const int pb = pair_blocks();
+  if (nsources > 0) {
+    k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
+    int rc = launch_msbfs(n, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
+    if (rc) return rc;
+    if (precision == 64)
+      k_pairs_sampled<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+                                                           (const double2 *)pos, w.part, status);
+    else
+      k_pairs_sampled<float2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+                                                          (const float2 *)pos, w.part, status);
+  } else {
+    for (int b = 0; b < nb; ++b) {
+      const int32_t base = b * S, B = std::min<int32_t>(S, n - base);
+      k_batch_sources<<<std::max(1, (B + 255) / 256), 256, 0, s>>>(base, B, w.src);
+      int rc = launch_msbfs(n, rowptr, colidx, B, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
+      if (rc) return rc;
+      double *part = w.part + 4 * (size_t)pb * b;
+      if (precision == 64)
+        k_pairs_exhaustive<double2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const double2 *)pos, part,
+                                                                status);
+      else
+        k_pairs_exhaustive<float2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const float2 *)pos, part,
+                                                               status);
+    }
+  }
+  k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}

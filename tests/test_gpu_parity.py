@@ -1,0 +1,350 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Integer stages (CSR, pivots, d_ip, regions, counts) must match bit for bit;
+floating-point stages within the tolerances stated in each test:
+  * positions: max_i ||x_i^gpu - x_i^orc|| / RMS_i ||x_i^orc - mean|| <= 1e-5
+    for the FP32 sweep at equal input (FP64 sweep: 1e-10);
+  * stress: relative error <= 1e-9 at equal positions (FP64 sums);
+  * PivotMDS eigenvalues: relative error <= 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1608_08909_gb300 as ssm
+from paper_1608_08909_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _rand_graph(seed, n, extra):
+    rng = np.random.default_rng(seed)
+    src = [int(rng.integers(0, v)) for v in range(1, n)]
+    dst = list(range(1, n))
+    e = rng.integers(0, n, (extra, 2))
+    src += e[:, 0].tolist()  # includes self-loops and repeats
+    dst += e[:, 1].tolist()
+    return n, np.array(src, np.int32), np.array(dst, np.int32)
+
+
+GRAPHS = {
+    "grid32": lambda: I.grid(32, 32),
+    "grid_ragged": lambda: I.grid(17, 45),
+    "path": lambda: I.path(300),
+    "btree": lambda: I.complete_btree(9),
+    "rbtree": lambda: I.random_btree(3001, 4),
+    "rgg": lambda: I.rgg(6000, 8.0, 7),
+    "ba": lambda: I.ba(20000, 4, 3),
+    "messy": lambda: _rand_graph(5, 2500, 9000),
+}
+
+
+def _gpu_graph(n, s, d):
+    return ssm.ssm_build_graph(n, torch.from_numpy(s).to(DEV), torch.from_numpy(d).to(DEV))
+
+
+def _norm_err(a, b):
+    b = np.asarray(b, np.float64)
+    a = np.asarray(a, np.float64)
+    c = b - b.mean(0)
+    rms = np.sqrt((c ** 2).sum(1).mean())
+    return np.sqrt(((a - b) ** 2).sum(1)).max() / rms
+
+
+# ------------------------------------------------------------------ a0 graph
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_build_graph_bit_exact(name):
+    n, s, d = GRAPHS[name]()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    assert g.m == og.m
+    assert np.array_equal(g.rowptr.cpu().numpy(), og.rowptr)
+    assert np.array_equal(g.colidx.cpu().numpy(), og.colidx)
+
+
+def test_build_graph_hub_row():
+    # a star with 20000 leaves (row longer than the shared-memory sort) plus repeats
+    n = 20001
+    leaves = np.arange(1, n, dtype=np.int32)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(leaves)
+    s = np.concatenate([np.zeros(n - 1, np.int32), perm[:500]])
+    d = np.concatenate([perm, np.zeros(500, np.int32)])
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    assert np.array_equal(g.colidx.cpu().numpy(), og.colidx)
+
+
+def test_build_graph_errors():
+    with pytest.raises(ssm.SSMError) as e:
+        _gpu_graph(4, np.array([0, 1], np.int32), np.array([1, 4], np.int32))
+    assert e.value.code == -2
+    with pytest.raises(ssm.SSMError) as e:
+        _gpu_graph(4, np.array([0, 2], np.int32), np.array([1, 3], np.int32))
+    assert e.value.code == -3
+
+
+# ------------------------------------------------------------------ a1 pivots
+
+@pytest.mark.parametrize("name,k,start", [("grid32", 50, 0), ("grid_ragged", 33, 5), ("path", 7, 150),
+                                          ("btree", 40, 0), ("rbtree", 64, 17), ("rgg", 100, 0), ("ba", 100, 0),
+                                          ("messy", 1, 3), ("messy", 65, 0)])
+def test_select_pivots_bit_exact(name, k, start):
+    n, s, d = GRAPHS[name]()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, k, start).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, k, start))
+
+
+def test_select_pivots_k_equals_n():
+    n, s, d = I.grid(5, 7)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, n, 0).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, n, 0))
+    assert sorted(got.tolist()) == list(range(n))
+
+
+# ------------------------------------------------------------------ a2 d_ip
+
+@pytest.mark.parametrize("name,k", [("grid32", 50), ("path", 7), ("btree", 33), ("rgg", 100), ("ba", 64),
+                                    ("messy", 1), ("messy", 95)])
+def test_pivot_bfs_bit_exact(name, k):
+    n, s, d = GRAPHS[name]()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    piv = O.maxmin(og, k, 0)
+    dip = ssm.ssm_pivot_bfs(g, torch.from_numpy(piv).to(DEV)).cpu().numpy()
+    assert np.array_equal(dip, O.pivot_dist(og, piv))
+
+
+def test_pivot_bfs_repeated_pivots():
+    n, s, d = GRAPHS["rbtree"]()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    piv = np.array([5, 5, 0, 17, 5, 2999] * 7, np.int32)
+    dip = ssm.ssm_pivot_bfs(g, torch.from_numpy(piv).to(DEV)).cpu().numpy()
+    assert np.array_equal(dip, O.pivot_dist(og, piv))
+
+
+def test_pivot_bfs_disconnected():
+    n = 40
+    s = np.array(list(range(0, 19)) + list(range(20, 39)), np.int32)
+    d = s + 1
+    og = O.build_csr(n, s, d)
+    g = ssm.Graph(n, og.m, torch.from_numpy(og.rowptr).to(DEV), torch.from_numpy(og.colidx).to(DEV))
+    with pytest.raises(ssm.SSMError) as e:
+        ssm.ssm_pivot_bfs(g, torch.tensor([0, 25], dtype=torch.int32, device=DEV))
+    assert e.value.code == -3
+
+
+# ------------------------------------------------------------------ a3 regions and counts
+
+@pytest.mark.parametrize("name,k", [("grid32", 50), ("path", 7), ("btree", 33), ("rgg", 100), ("ba", 64),
+                                    ("messy", 95)])
+def test_aggregate_bit_exact(name, k):
+    n, s, d = GRAPHS[name]()
+    og = O.build_csr(n, s, d)
+    piv = O.maxmin(og, k, 0)
+    dip = O.pivot_dist(og, piv)
+    reg, (ecc, off, cnt) = O.regions(dip), O.histograms(dip, O.regions(dip))
+    gd = torch.from_numpy(dip).to(DEV)
+    assert ssm.ssm_aggregate_size(gd) == len(cnt)
+    greg, goff, gcnt = ssm.ssm_aggregate(gd)
+    assert np.array_equal(greg.cpu().numpy(), reg)
+    assert np.array_equal(goff.cpu().numpy().astype(np.int64), off)
+    assert np.array_equal(gcnt.cpu().numpy(), cnt)
+
+
+# ------------------------------------------------------------------ a4/a5 PivotMDS
+
+@pytest.mark.parametrize("name,k", [("grid32", 50), ("rgg", 100), ("ba", 64), ("btree", 33), ("path", 7)])
+def test_pivotmds_matches_oracle(name, k):
+    """Eigenvalues to 1e-10; positions to FP32 rounding where the eigenvector is
+    unique.  Where lambda_2 is degenerate (the complete binary tree is
+    symmetric, lambda_2 = lambda_3) any unit vector of the eigenspace is a
+    valid second axis, so the test checks what is unique: the first axis, and
+    that the second axis y = C v has ||y||^2 = lambda_2 and y . x = 0."""
+    n, s, d = GRAPHS[name]()
+    og = O.build_csr(n, s, d)
+    piv = O.maxmin(og, k, 0)
+    dip = O.pivot_dist(og, piv)
+    opos, oeig, B = O.pivotmds(dip, return_b=True)
+    lam = np.linalg.eigvalsh(B)[::-1]
+    unique2 = (lam[1] - lam[2]) > 1e-6 * lam[0] and oeig[1] > 1e-6 * oeig[0]
+    g = _gpu_graph(n, s, d)
+    for prec in (32, 64):
+        pos, eig = ssm.ssm_pivotmds(g, torch.from_numpy(dip).to(DEV), precision=prec, rescale=False)
+        eig = eig.cpu().numpy()
+        np.testing.assert_allclose(eig[0], oeig[0], rtol=1e-10)
+        if oeig[1] > 1e-9 * oeig[0]:
+            np.testing.assert_allclose(eig[1], oeig[1], rtol=1e-10)
+        p = pos.cpu().numpy().astype(np.float64)
+        tol = 2e-6 if prec == 32 else 1e-9
+        if unique2:
+            assert _norm_err(p, opos) < tol
+        else:
+            assert _norm_err(p[:, :1], opos[:, :1]) < tol
+            if oeig[1] > 1e-6 * oeig[0]:
+                y = p[:, 1] - p[:, 1].mean()
+                x = p[:, 0] - p[:, 0].mean()
+                assert np.dot(y, y) == pytest.approx(oeig[1], rel=1e-5)
+                assert abs(np.dot(x, y)) <= 1e-5 * np.sqrt(oeig[0] * oeig[1])
+    # with the rescale of Algorithm 1 line 4
+    pos, _ = ssm.ssm_pivotmds(g, torch.from_numpy(dip).to(DEV), precision=64, rescale=True)
+    if unique2:
+        assert _norm_err(pos.cpu().numpy(), O.rescale(og, opos)) < 1e-9
+
+
+# ------------------------------------------------------------------ a6/a7 sweep
+
+def _gpu_pivots(k, prep):
+    return ssm.Pivots(k, torch.from_numpy(prep.pivots).to(DEV), torch.from_numpy(prep.dip).to(DEV),
+                      torch.from_numpy(prep.region).to(DEV),
+                      torch.from_numpy(prep.cnt_off.astype(np.int32)).to(DEV), torch.from_numpy(prep.cnt).to(DEV))
+
+
+@pytest.mark.parametrize("name,k", [("grid32", 50), ("rgg", 100), ("ba", 64), ("btree", 33), ("messy", 95)])
+def test_sweep_fp64_matches_oracle(name, k):
+    """The FP64 sweep rounds every operation as the oracle does, in the same
+    order, so the trajectories agree bit for bit even where the Jacobi
+    dynamics amplify rounding differences (near-coincident nodes of the
+    PivotMDS start: a 1e-15 perturbation grows to 1e-2 within 5 iterations
+    on the RGG and to 0.4 on the binary tree)."""
+    n, s, d = GRAPHS[name]()
+    prep = O.prepare(n, s, d, k)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(k, prep)
+    pos = torch.from_numpy(prep.pos0.copy()).to(DEV)
+    iters = 20
+    done, rel = ssm.ssm_iterate(g, P, pos, iters)
+    opos, orel = O.iterate(prep, prep.pos0, iters)
+    assert int(done.item()) == iters
+    assert np.array_equal(pos.cpu().numpy(), opos)
+    assert rel.item() == pytest.approx(orel, rel=1e-12)
+
+
+@pytest.mark.parametrize("name,k", [("grid32", 50), ("grid_ragged", 33), ("rgg", 100), ("ba", 64), ("btree", 33),
+                                    ("messy", 95), ("rbtree", 64)])
+def test_sweep_fp32_single_step(name, k):
+    n, s, d = GRAPHS[name]()
+    prep = O.prepare(n, s, d, k)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(k, prep)
+    x0 = prep.pos0.astype(np.float32)
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    done, rel = ssm.ssm_iterate(g, P, pos, 1)
+    opos, orel = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x0.astype(np.float64))
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+    assert rel.item() == pytest.approx(orel, rel=1e-4)
+
+
+@pytest.mark.parametrize("name,k", [("rgg", 100), ("ba", 64), ("btree", 33)])
+def test_sweep_fp32_along_oracle_trajectory(name, k):
+    """FP32 step error along the oracle's FP64 trajectory: at every iteration t
+    the GPU computes X^{t+1} from the oracle's X^t (rounded to FP32)."""
+    n, s, d = GRAPHS[name]()
+    prep = O.prepare(n, s, d, k)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(k, prep)
+    x = prep.pos0
+    worst = 0.0
+    for _ in range(25):
+        pos = torch.from_numpy(x.astype(np.float32)).to(DEV)
+        ssm.ssm_iterate(g, P, pos, 1)
+        x_next, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x.astype(np.float32).astype(np.float64))
+        worst = max(worst, _norm_err(pos.cpu().numpy(), x_next))
+        x, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x)
+    assert worst < 1e-5
+
+
+def test_sweep_fp32_grid_200_iterations():
+    """The small plain configuration: 32x32 grid, k=50, 200 Jacobi iterations."""
+    n, s, d = I.grid(32, 32)
+    prep = O.prepare(n, s, d, 50)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(50, prep)
+    x0 = prep.pos0.astype(np.float32)
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_iterate(g, P, pos, 200)
+    opos, _ = O.iterate(prep, x0.astype(np.float64), 200)
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+
+
+def test_sweep_early_stop():
+    """tol > 0 stops on the device at the first iteration whose relative change
+    is below tol (43 on this grid; the Jacobi change then plateaus near 5.7e-5)."""
+    n, s, d = I.grid(32, 32)
+    prep = O.prepare(n, s, d, 50)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(50, prep)
+    pos = torch.from_numpy(prep.pos0.copy()).to(DEV)
+    done, rel = ssm.ssm_iterate(g, P, pos, 500, tol=1e-4)
+    t = int(done.item())
+    assert 1 <= t < 500
+    opos, orel = O.iterate(prep, prep.pos0, t)
+    assert orel < 1e-4
+    _, prev = O.iterate(prep, prep.pos0, t - 1) if t > 1 else (None, 1.0)
+    assert prev >= 1e-4
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-10
+
+
+def test_sweep_odd_n_and_tail():
+    n, s, d = I.grid(13, 13)  # n = 169 (odd) -> one-node-per-thread path with a ragged tile
+    prep = O.prepare(n, s, d, 9)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(9, prep)
+    x0 = prep.pos0.astype(np.float32)
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_iterate(g, P, pos, 3)
+    opos, _ = O.iterate(prep, x0.astype(np.float64), 3)
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+
+
+# ------------------------------------------------------------------ a8 stress
+
+@pytest.mark.parametrize("name", ["grid32", "btree", "messy"])
+def test_stress_exhaustive(name):
+    n, s, d = GRAPHS[name]()
+    prep = O.prepare(n, s, d, 20)
+    g = _gpu_graph(n, s, d)
+    for prec in (32, 64):
+        x = prep.pos0.astype(np.float32).astype(np.float64) if prec == 32 else prep.pos0
+        pos = torch.from_numpy(x.astype(np.float32) if prec == 32 else x).to(DEV)
+        out, sums = ssm.ssm_stress(g, pos)
+        want, wsums = O.full_stress(prep.g, x, return_sums=True)
+        np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-9)
+        assert sums[3].item() == wsums[3] == n * (n - 1) / 2
+
+
+@pytest.mark.parametrize("S,T,seed", [(64, 256, 1), (100, 37, 9)])
+def test_stress_sampled(S, T, seed):
+    n, s, d = GRAPHS["rgg"]()
+    prep = O.prepare(n, s, d, 30)
+    g = _gpu_graph(n, s, d)
+    x = prep.pos0.astype(np.float32)
+    out, sums = ssm.ssm_stress(g, torch.from_numpy(x).to(DEV), S, T, seed)
+    want, wsums = O.full_stress(prep.g, x.astype(np.float64), S, T, seed, return_sums=True)
+    np.testing.assert_allclose(sums.cpu().numpy(), wsums, rtol=1e-9)
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-9)
+
+
+# ------------------------------------------------------------------ whole pipeline
+
+def test_pipeline_grid32_end_to_end():
+    """All rows on the small plain configuration, GPU pipeline vs oracle pipeline."""
+    n, s, d = I.grid(32, 32)
+    prep = O.prepare(n, s, d, 50)
+    g, P, pos, eig = ssm.prepare(n, s, d, 50, precision=64)
+    assert np.array_equal(P.pivots.cpu().numpy(), prep.pivots)
+    assert np.array_equal(P.dip.cpu().numpy(), prep.dip)
+    assert _norm_err(pos.cpu().numpy(), prep.pos0) < 1e-9
+    ssm.ssm_iterate(g, P, pos, 200)
+    opos, _ = O.iterate(prep, prep.pos0, 200)
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-8
+    out, _ = ssm.ssm_stress(g, pos)
+    np.testing.assert_allclose(out.cpu().numpy(), O.full_stress(prep.g, opos), rtol=1e-8)
