@@ -138,20 +138,28 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step(s_d, d_d, sweep_ev=None):
+    STAGES = ["graph", "pivots", "pivot_bfs", "aggregate", "pivotmds", "sweeps", "stress"]
+
+    def step(s_d, d_d, ev=None):
+        """One pass of every stage; ev (optional) = len(STAGES)+1 events recorded between stages."""
+        mark = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        mark(0)
         g = ssm.ssm_build_graph(n, s_d, d_d)
+        mark(1)
         piv = ssm.ssm_select_pivots(g, k, 0, check=False)
+        mark(2)
         dip = ssm.ssm_pivot_bfs(g, piv, check=False)
+        mark(3)
         cnt_len = ssm.ssm_aggregate_size(dip)
         region, off, cnt = ssm.ssm_aggregate(dip, cnt_len, check=False)
+        mark(4)
         pos, _ = ssm.ssm_pivotmds(g, dip, 32, True, check=False)
         P = ssm.Pivots(k, piv, dip, region, off, cnt)
-        if sweep_ev is not None:
-            sweep_ev[0].record(stream)
+        mark(5)
         ssm.ssm_iterate(g, P, pos, iters, check=False)
-        if sweep_ev is not None:
-            sweep_ev[1].record(stream)
+        mark(6)
         out, _ = ssm.ssm_stress(g, pos, S, T, W["seed"], check=False)
+        mark(7)
         return g, P, pos, out
 
     # correctness of the device status words is checked once, outside timing
@@ -166,19 +174,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     step_ms, sweep_ms = [], []
+    stage_ms = {st: 0.0 for st in STAGES}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            _, _, _, out = step(src_d, dst_d, sweep_ev=(ev[2], ev[3]))
-            ev[1].record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+            _, _, _, out = step(src_d, dst_d, ev)
             torch.cuda.synchronize()
-            step_ms.append(ev[0].elapsed_time(ev[1]))
-            sweep_ms.append(ev[2].elapsed_time(ev[3]))
+            step_ms.append(ev[0].elapsed_time(ev[-1]))
+            for i, st in enumerate(STAGES):
+                stage_ms[st] += ev[i].elapsed_time(ev[i + 1]) / args.steps
+            sweep_ms.append(ev[5].elapsed_time(ev[6]))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -245,6 +254,7 @@ def run_gpu(args):
             "parallelism": f"replicas{world}",
             "l2": "flushed between steps (256 MB write outside the timed events)",
             "sweep_ms_per_step": sum(sweep_ms) / args.steps,
+            "stage_ms": {st: round(v, 3) for st, v in stage_ms.items()},
         },
         "roofline": {
             "kernel": "k_sweep_f32 (one Jacobi iteration)",

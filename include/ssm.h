@@ -151,11 +151,14 @@ int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
  * reduced in FP64; if tol > 0 the remaining iterations are skipped on the
  * device once it falls below tol.  Writes *iters_done (device int32) and
  * *rel_change (device double, the last computed change).  cnt_off and cnt are
- * the tables of ssm_aggregate, cnt_len = cnt_off[k] (from ssm_aggregate_size).
- * 1 <= iters, 1 <= k <= 4096.
+ * the tables of ssm_aggregate, cnt_len = cnt_off[k] (from ssm_aggregate_size);
+ * m is the edge count (colidx has 2m entries).  1 <= iters, 1 <= k <= 4096.
+ * Device error SSM_E_TIMEOUT if a node's neighbour-chunk partial sums were
+ * not published within 20 ms (rows longer than 128 are split into chunks that
+ * other warps of the same launch sum).
  * ------------------------------------------------------------------- */
-size_t ssm_iterate_workspace(int32_t n, int32_t k, int32_t precision);
-int ssm_iterate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision);
+int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                 const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off,
                 const uint32_t *cnt, int64_t cnt_len, void *pos, int32_t precision, int32_t iters,
                 double tol, int32_t *iters_done, double *rel_change, int32_t *status,

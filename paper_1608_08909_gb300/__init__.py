@@ -67,8 +67,8 @@ def lib():
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
-                "ssm_iterate_workspace": (sz, [i32, i32, i32]),
-                "ssm_iterate": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
+                "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
+                "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
                 "ssm_stress_workspace": (sz, [i32, i32, i32]),
                 "ssm_stress": (ctypes.c_int, [i32, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
             }
@@ -223,8 +223,8 @@ def ssm_pivotmds(g: Graph, dip: torch.Tensor, precision: int = 32, rescale: bool
 class IterateWorkspace:
     """Reusable device buffers for ssm_iterate (so timed loops allocate nothing)."""
 
-    def __init__(self, n: int, k: int, precision: int, device):
-        self.ws = _ws(lib().ssm_iterate_workspace(n, k, precision), device)
+    def __init__(self, n: int, m: int, k: int, cnt_len: int, precision: int, device):
+        self.ws = _ws(lib().ssm_iterate_workspace(n, m, k, cnt_len, precision), device)
         self.iters_done = torch.zeros(1, dtype=torch.int32, device=device)
         self.rel = torch.zeros(1, dtype=torch.float64, device=device)
         self.status = _status(device)
@@ -236,8 +236,8 @@ def ssm_iterate(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, tol: float =
     L = lib()
     precision = 64 if pos.dtype == torch.float64 else 32
     if work is None:
-        work = IterateWorkspace(g.n, p.k, precision, pos.device)
-    _rc(L.ssm_iterate(g.n, _ptr(g.rowptr), _ptr(g.colidx), p.k, _ptr(p.pivots), _ptr(p.dip), _ptr(p.cnt_off),
+        work = IterateWorkspace(g.n, g.m, p.k, p.cnt.numel(), precision, pos.device)
+    _rc(L.ssm_iterate(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), p.k, _ptr(p.pivots), _ptr(p.dip), _ptr(p.cnt_off),
                       _ptr(p.cnt), p.cnt.numel(), _ptr(pos), precision, iters, float(tol), _ptr(work.iters_done), _ptr(work.rel),
                       _ptr(work.status), _ptr(work.ws), work.ws.numel(), _stream(stream)), "ssm_iterate")
     if check:

@@ -1,11 +1,16 @@
 // Breadth-first searches on the device:
 //   * ssm_select_pivots: max/min-sp pivot sampling (Section 4.1), one pruned
-//     level-synchronous BFS per new pivot inside one persistent kernel;
-//   * ssm_pivot_bfs:     all k pivot distances d_ip (Algorithm 1 line 2) in one
-//     multi-source BFS over per-node bitsets (one bit per source), frontier
-//     compacted with warp ballots.
-// Both run as cooperative persistent grids with a device-wide barrier per BFS
-// level; every barrier wait is bounded (SSM_E_TIMEOUT).
+//     level-synchronous BFS per new pivot inside one cooperative persistent
+//     kernel; small frontiers are expanded by one block without device-wide
+//     barriers, large ones by the whole grid;
+//   * ssm_pivot_bfs:     all k pivot distances d_ip (Algorithm 1 line 2): one
+//     block per source with the visited set as a bitmap in shared memory
+//     (k_bfs_cta), or, for graphs whose bitmap does not fit, one multi-source
+//     BFS over per-node bitsets with one bit per source (k_msbfs).
+// Frontier appends are compacted with warp ballots; every device-wide wait is
+// bounded (SSM_E_TIMEOUT).
+#include <algorithm>
+
 #include "bfs.cuh"
 
 namespace ssm {
@@ -16,6 +21,9 @@ constexpr unsigned kInf = 0xFFFFFFFFu;
 // --------------------------------------------------------------------------
 // max/min sp
 // --------------------------------------------------------------------------
+constexpr int kSoloMax = 2048;       // frontiers up to this size are expanded by block 0 alone
+constexpr int kSoloLevels = 4096;    // block 0 hands back to the grid at least this often
+
 struct MaxMinArgs {
   int32_t n;
   const int32_t *rowptr;
@@ -27,9 +35,67 @@ struct MaxMinArgs {
   unsigned *mind;  // [n] hop distance to the closest chosen pivot
   unsigned *q0, *q1;  // [n] frontier queues (alternate by level parity)
   unsigned *qcnt;     // [3] queue lengths, rotated by level
+  unsigned *level;    // level reached by a solo phase of block 0
   unsigned long long *best;  // [2] packed (mind << 32 | ~node) maxima, by pivot parity
   BarrierState *bar;
 };
+
+// Block 0 alone expands levels L, L+1, ... while the frontier has at most
+// kSoloMax nodes: row ranges of the frontier stay in shared memory and the
+// levels are separated by __syncthreads instead of device-wide barriers.
+// Every new frontier is also written to the global queue, so the grid can
+// take over when it grows.  Returns with qcnt and *level describing the
+// frontier it stopped at.
+__device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*sq)[kSoloMax], unsigned *s_cnt) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned *qin0 = (L & 1) ? A.q1 : A.q0;
+  for (unsigned e = threadIdx.x; e < c; e += blockDim.x) {
+    const unsigned u = __ldcg(qin0 + e);
+    sq[0][e] = make_int2(__ldg(A.rowptr + u), __ldg(A.rowptr + u + 1));
+  }
+  if (threadIdx.x == 0) {
+    s_cnt[0] = c;
+    s_cnt[1] = 0;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int steps = 0; steps < kSoloLevels; ++steps) {
+    const unsigned cc = s_cnt[cur];
+    if (cc == 0 || cc > (unsigned)kSoloMax) break;
+    const int nxt = cur ^ 1;
+    unsigned *qout = ((L + 1) & 1) ? A.q1 : A.q0;
+    const unsigned nd = L + 1;
+    for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
+      const unsigned e = base + lane;
+      const int2 r = e < cc ? sq[cur][e] : make_int2(0, 0);
+      warp_for_each_neighbor(r.x, r.y, A.colidx, [&](int, bool act, int v) {
+        bool push = false;
+        if (act && nd < __ldcg(A.mind + v)) push = atomicMin(A.mind + v, nd) > nd;
+        const unsigned mask = __ballot_sync(0xffffffffu, push);
+        if (!mask) return;
+        unsigned pos = 0;
+        const int leader = __ffs(mask) - 1;
+        if ((int)lane == leader) pos = atomicAdd(s_cnt + nxt, (unsigned)__popc(mask));
+        pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+        if (push) {
+          qout[pos] = (unsigned)v;
+          if (pos < (unsigned)kSoloMax) sq[nxt][pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
+        }
+      });
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_cnt[cur] = 0;
+    __syncthreads();
+    cur = nxt;
+    ++L;
+  }
+  if (threadIdx.x == 0) {
+    A.qcnt[L % 3] = s_cnt[cur];
+    A.qcnt[(L + 1) % 3] = 0;
+    A.qcnt[(L + 2) % 3] = 0;
+    *A.level = L;
+  }
+}
 
 // Pruned BFS from the newest pivot p: node v is expanded at level L+1 only
 // if L+1 < mind[v].  Since mind (a minimum of distance functions) changes by
@@ -37,6 +103,8 @@ struct MaxMinArgs {
 // mind is reached along a shortest path of such nodes, so the result is
 // exactly mind = min(mind, d(p, .)).
 __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
+  __shared__ int2 sq[2][kSoloMax];
+  __shared__ unsigned s_cnt[2];
   const unsigned nthreads = gridDim.x * blockDim.x;
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -60,9 +128,15 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
     if (last && j > 0) break;  // the final pivot needs no search
     if (!grid_barrier(A.bar, A.status)) return;
 
-    for (unsigned L = 0;; ++L) {
+    for (unsigned L = 0;;) {
       const unsigned c = __ldcg(A.qcnt + L % 3);
       if (c == 0) break;
+      if (c <= (unsigned)kSoloMax) {
+        if (blockIdx.x == 0) maxmin_solo(A, L, c, sq, s_cnt);
+        if (!grid_barrier(A.bar, A.status)) return;
+        L = __ldcg(A.level);
+        continue;
+      }
       if (gtid == 0) A.qcnt[(L + 2) % 3] = 0;
       const unsigned *qin = (L & 1) ? A.q1 : A.q0;
       unsigned *qout = (L & 1) ? A.q0 : A.q1;
@@ -86,6 +160,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
         });
       }
       if (!grid_barrier(A.bar, A.status)) return;
+      ++L;
     }
 
     // argmax of mind, ties to the lowest node id
@@ -122,14 +197,14 @@ int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32
   A.q0 = c.take<unsigned>(n);
   A.q1 = c.take<unsigned>(n);
   A.qcnt = c.take<unsigned>(4);
+  A.level = c.take<unsigned>(1);
   A.best = c.take<unsigned long long>(2);
   A.bar = c.take<BarrierState>(1);
-  if (!ws) return (int)c.size();
   if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
-  const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, 0, 2);
+  const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, 0, 1);
   if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: kernel cannot be resident");
   void *args[] = {&A};
   SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_maxmin, dim3(blocks), dim3(kBfsThreads), args, 0, s));
@@ -142,10 +217,105 @@ size_t maxmin_workspace(int32_t n) {
   c.take<unsigned>(n);
   c.take<unsigned>(n);
   c.take<unsigned>(4);
+  c.take<unsigned>(1);
   c.take<unsigned long long>(2);
   c.take<BarrierState>(1);
   return c.size();
 }
+
+// --------------------------------------------------------------------------
+// one source per block: visited bitmap in shared memory
+// --------------------------------------------------------------------------
+constexpr int kCtaThreads = 512;
+constexpr int kCtaSlotsPerSm = 2;
+constexpr size_t kCtaBitmapMax = 200 * 1024;  // bytes of shared memory for the visited bitmap
+
+struct CtaBfsArgs {
+  int32_t n;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  int32_t nsrc;
+  const int32_t *sources;
+  uint16_t *dist;  // [nsrc][n]
+  int32_t *status;
+  int2 *queues;    // [slots][2][n] row ranges of the frontier
+};
+
+// Each block owns sources blockIdx.x, blockIdx.x + gridDim.x, ...; per source
+// a level-synchronous BFS whose visited set is a bitmap in shared memory
+// (claimed with shared atomicOr), whose frontier holds the row ranges of the
+// nodes (fetched when a node is appended) and whose levels are separated by
+// __syncthreads.  Appends are compacted with warp ballots.
+__global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
+  extern __shared__ unsigned vis[];
+  __shared__ unsigned s_cnt[2];
+  __shared__ unsigned s_total;
+  const unsigned n = (unsigned)A.n, nwords = (n + 31u) / 32u;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int2 *qa = A.queues + (size_t)blockIdx.x * 2 * n, *qb = qa + n;
+  for (int si = blockIdx.x; si < A.nsrc; si += gridDim.x) {
+    for (unsigned w = threadIdx.x; w < nwords; w += blockDim.x) vis[w] = 0u;
+    __syncthreads();
+    uint16_t *row = A.dist + (size_t)si * n;
+    if (threadIdx.x == 0) {
+      const unsigned s = (unsigned)__ldg(A.sources + si);
+      vis[s >> 5] |= 1u << (s & 31u);
+      qa[0] = make_int2(__ldg(A.rowptr + s), __ldg(A.rowptr + s + 1));
+      row[s] = 0;
+      s_cnt[0] = 1;
+      s_cnt[1] = 0;
+      s_total = 1;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (unsigned L = 0;; ++L) {
+      const unsigned cc = s_cnt[cur];
+      if (cc == 0) break;
+      if (L + 1 > 65534u) {
+        if (threadIdx.x == 0) dev_fail(A.status, SSM_E_DIST_OVERFLOW);
+        break;
+      }
+      const int nxt = cur ^ 1;
+      const int2 *qin = cur ? qb : qa;
+      int2 *qout = cur ? qa : qb;
+      const uint16_t nd = (uint16_t)(L + 1);
+      for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
+        const unsigned e = base + lane;
+        const int2 r = e < cc ? __ldcg(qin + e) : make_int2(0, 0);
+        warp_for_each_neighbor(r.x, r.y, A.colidx, [&](int, bool act, int v) {
+          bool push = false;
+          if (act) {
+            const unsigned bit = 1u << ((unsigned)v & 31u);
+            unsigned *wp = vis + ((unsigned)v >> 5);
+            if (!(*wp & bit)) push = !(atomicOr(wp, bit) & bit);
+          }
+          const unsigned mask = __ballot_sync(0xffffffffu, push);
+          if (!mask) return;
+          unsigned pos = 0;
+          const int leader = __ffs(mask) - 1;
+          if ((int)lane == leader) pos = atomicAdd(s_cnt + nxt, (unsigned)__popc(mask));
+          pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+          if (push) {
+            row[v] = nd;
+            qout[pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
+          }
+        });
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_total += s_cnt[nxt];
+        s_cnt[cur] = 0;
+      }
+      __syncthreads();
+      cur = nxt;
+    }
+    if (threadIdx.x == 0 && s_total != n) dev_fail(A.status, SSM_E_DISCONNECTED);
+    __syncthreads();
+  }
+}
+
+static bool cta_bfs_fits(int32_t n) { return (size_t)((n + 31) / 32) * 4 <= kCtaBitmapMax; }
+static int cta_bfs_slots(int32_t nsrc) { return std::max(1, std::min(nsrc, num_sms() * kCtaSlotsPerSm)); }
 
 // --------------------------------------------------------------------------
 // multi-source bitset BFS
@@ -284,6 +454,10 @@ static void msbfs_carve(Carver &c, MsBfsArgs &A, int32_t n, int32_t k) {
 
 size_t msbfs_workspace(int32_t n, int32_t k) {
   Carver c(nullptr, 0);
+  if (cta_bfs_fits(n)) {
+    c.take<int2>((size_t)cta_bfs_slots(k) * 2 * (size_t)n);
+    return c.size();
+  }
   MsBfsArgs A;
   msbfs_carve(c, A, n, k);
   return c.size();
@@ -292,6 +466,20 @@ size_t msbfs_workspace(int32_t n, int32_t k) {
 int launch_msbfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
                  uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   Carver c(ws, ws_bytes);
+  if (cta_bfs_fits(n)) {
+    CtaBfsArgs B;
+    B.n = n; B.rowptr = rowptr; B.colidx = colidx; B.nsrc = k; B.sources = sources; B.dist = dist;
+    B.status = status;
+    const int slots = cta_bfs_slots(k);
+    B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
+    if (!c.ok) return fail(SSM_E_NOMEM, "BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
+    const size_t smem = (size_t)((n + 31) / 32) * 4;
+    SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_bfs_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
+    k_bfs_cta<<<slots, kCtaThreads, smem, s>>>(B);
+    SSM_TRY_CUDA(cudaGetLastError());
+    return SSM_OK;
+  }
   MsBfsArgs A;
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.W = (k + 31) / 32;
   A.sources = sources; A.dist = dist; A.status = status;

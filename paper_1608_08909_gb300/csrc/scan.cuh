@@ -9,10 +9,10 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-inline int64_t scan_tiles(int64_t count) { return (count + kScanTile - 1) / kScanTile; }
+static inline int64_t scan_tiles(int64_t count) { return (count + kScanTile - 1) / kScanTile; }
 
 // block-wide exclusive scan of one value per thread; returns the block total in *total
-__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+static __device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
   __shared__ int warp_tot[kScanThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = v;
@@ -40,7 +40,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
   return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
+static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
                                                                int *__restrict__ tile_sums, int64_t count) {
   __shared__ int s_total;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restri
 }
 
 // one block: exclusive scan of the tile totals in place; grand total to *total_out
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *__restrict__ tile_sums, int64_t ntiles,
+static __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *__restrict__ tile_sums, int64_t ntiles,
                                                               int *__restrict__ total_out) {
   __shared__ int s_total;
   int carry = 0;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *__restrict__ ti
   if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(int *__restrict__ out, const int *__restrict__ tile_sums,
+static __global__ void __launch_bounds__(kScanThreads) k_scan_add(int *__restrict__ out, const int *__restrict__ tile_sums,
                                                              int64_t count) {
   const int add = tile_sums[blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int *__restrict__ out
 
 // out[0..count-1] = exclusive scan of in; out[count] = total (out has count+1 slots).
 // tile_ws needs scan_tiles(count) ints.
-inline int exclusive_scan(const int *in, int *out, int64_t count, int *tile_ws, cudaStream_t s) {
+static inline int exclusive_scan(const int *in, int *out, int64_t count, int *tile_ws, cudaStream_t s) {
   int64_t tiles = scan_tiles(count);
   if (tiles == 0) {
     SSM_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));

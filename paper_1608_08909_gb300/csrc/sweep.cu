@@ -10,23 +10,42 @@
 // A term with r == 0 contributes w * x_j only.  d_ia <= 1 skips the pivot
 // (the pivot itself, or a neighbour already counted as an edge term).
 //
-// GB300 layout: the k pivot positions and the count tables sit in shared
-// memory (loaded once per persistent block), d_ip is streamed from HBM with
-// one coalesced row segment per pivot per warp, neighbour positions are
-// gathered from L2.  Warps take 32*NPT-node tiles from an atomic counter so
-// uneven rows balance across the 152 SMs; nodes of very high degree are
-// processed by the whole warp.  The relative change ||X^{t+1}-X^t||/||X^t||
-// is reduced in FP64 in a fixed order by the last block to finish.
+// FP32 kernel, GB300 layout:
+//  * a lane owns two consecutive nodes; their d_ia for one pivot arrive in one
+//    32-bit load, so a warp streams a contiguous 128-byte segment of the
+//    pivot-major d_ip row per pivot;
+//  * the pivot term is evaluated for the node pair with packed FP32x2
+//    arithmetic and one rsqrt per node: with q = d^2 r^2, u = q^{-1/2},
+//    B = s u = w d / r and W = B u r^2 = s / d^2 = w, the term adds
+//    W x_p + B (x_i - x_p) to the numerator and W to the denominator;
+//    r^2 is floored at 1e-24 so coincident points (r == 0) add w x_p, as
+//    the r == 0 rule says, and q gets + 1e-36 so it stays positive at d = 0
+//    (relative change of a valid term below 1e-12);
+//  * s comes from a per-pivot table indexed directly by d (0 for d < 2,
+//    cnt[min(d/2, ecc)] up to d = 2 ecc + 1, then |R(a)|), held in shared
+//    memory with the pivot positions and loaded once per persistent block;
+//  * warps take 64-node tiles from an atomic counter; rows longer than
+//    kChunkDeg are cut into kChunk-neighbour tasks handed out first, whose
+//    partial sums the owning tile adds in chunk order (results do not depend
+//    on scheduling).
+// The relative change ||X^{t+1}-X^t||/||X^t|| is reduced in FP64 in a fixed
+// order by the last block to finish.
 #include <algorithm>
 
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace ssm {
 
 constexpr int kSweepThreads = 256;
-constexpr int kHeavyDegree = 64;  // rows longer than this are walked by the whole warp
-constexpr size_t kSmemBudget = 160 * 1024;
+constexpr int kLightDeg = 32;   // rows up to this length: one lane walks the row
+constexpr int kChunkDeg = 128;  // rows longer than this: cut into chunk tasks
+constexpr int kChunk = 256;     // neighbours per chunk task
+constexpr size_t kSmemBudget = 200 * 1024;
 constexpr int kMaxPivotsSweep = 4096;
+constexpr float kR2Floor = 1e-24f;
+constexpr int kPrefetch = 16;  // pivots whose d words are loaded ahead
+constexpr unsigned long long kChunkWaitNs = 20000000ull;  // 20 ms
 
 struct SweepArgs {
   int32_t n, k;
@@ -34,14 +53,21 @@ struct SweepArgs {
   const uint16_t *dip;
   const uint32_t *cnt;
   int32_t cnt_len;
-  int32_t cnt_in_smem;
-  unsigned *tile_ctr;    // next tile to hand out
-  unsigned *done_ctr;    // blocks finished
-  double *tile_part;     // [ntiles][2] (sum dx^2, sum x^2) per tile
-  int32_t *stop;         // set when the relative change fell below tol
+  int32_t stab_len;       // 2 * cnt_len
+  const float *stab;      // [stab_len] s by d, per pivot (global copy)
+  const int32_t *cfirst;  // [n+1] first chunk task of each node; cfirst[n] = chunks
+  const int32_t *cnode;   // [chunks] node of each chunk task
+  float2 *cpart;          // [chunks] neighbour partial sums
+  unsigned *cflag;        // [chunks] stamp of the launch that wrote cpart
+  unsigned stamp;         // this launch's stamp
+  unsigned *tile_ctr;     // next task to hand out
+  unsigned *done_ctr;     // blocks finished
+  double *tile_part;      // [ntiles][2] (sum dx^2, sum x^2) per tile
+  int32_t *stop;          // set when the relative change fell below tol
   int32_t *iters_done;
   double *rel_change;
   double tol;
+  int32_t *status;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -52,6 +78,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float lds_f32(unsigned addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
   return v;
 }
 
@@ -93,144 +131,249 @@ __device__ void finish_iteration(const SweepArgs &A, unsigned ntiles) {
   }
 }
 
+// neighbour term x_j + (x_i - x_j)/r (r == 0: x_j)
+__device__ __forceinline__ void edge_term(float xi, float yi, float2 q, float &sx, float &sy) {
+  const float dx = xi - q.x, dy = yi - q.y;
+  const float r2 = fmaf(dx, dx, dy * dy);
+  const float inv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+  sx += fmaf(dx, inv, q.x);
+  sy += fmaf(dy, inv, q.y);
+}
+
+// one lane walks a short row, four independent gathers in flight
+__device__ __forceinline__ void light_row(const float2 *__restrict__ pin, const int32_t *__restrict__ colidx, int beg,
+                                          int end, float xi, float yi, float &sx, float &sy) {
+  int t = beg;
+  for (; t + 4 <= end; t += 4) {
+    const int j0 = __ldg(colidx + t), j1 = __ldg(colidx + t + 1), j2 = __ldg(colidx + t + 2),
+              j3 = __ldg(colidx + t + 3);
+    const float2 q0 = pin[j0], q1 = pin[j1], q2 = pin[j2], q3 = pin[j3];
+    edge_term(xi, yi, q0, sx, sy);
+    edge_term(xi, yi, q1, sx, sy);
+    edge_term(xi, yi, q2, sx, sy);
+    edge_term(xi, yi, q3, sx, sy);
+  }
+  for (; t < end; ++t) edge_term(xi, yi, pin[__ldg(colidx + t)], sx, sy);
+}
+
+// the whole warp walks one row segment [b, e) around (hx, hy); the sums land in every lane
+__device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const int32_t *__restrict__ colidx, int b,
+                                         int e, float hx, float hy, float &sx, float &sy) {
+  const int lane = threadIdx.x & 31;
+  sx = 0.f;
+  sy = 0.f;
+  int t = b + lane;
+  for (; t + 32 < e; t += 64) {
+    const float2 q0 = pin[__ldg(colidx + t)], q1 = pin[__ldg(colidx + t + 32)];
+    edge_term(hx, hy, q0, sx, sy);
+    edge_term(hx, hy, q1, sx, sy);
+  }
+  for (; t < e; t += 32) edge_term(hx, hy, pin[__ldg(colidx + t)], sx, sy);
+  sx = warp_sumf(sx);
+  sy = warp_sumf(sy);
+}
+
 // ----------------------------------------------------------------- FP32
-template <int NPT>
+template <bool VEC, bool SMEM>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
                                                               float2 *__restrict__ pout) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float4 *piv = reinterpret_cast<float4 *>(smem);  // x, y, cnt_off (bits), ecc (bits)
-  float *cntf = reinterpret_cast<float *>(piv + A.k);
+  float4 *pxy = reinterpret_cast<float4 *>(smem);       // (x, x, y, y) per pivot
+  uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
+  float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
   if (__ldcg(A.stop)) return;
   const int n = A.n, k = A.k;
+  // Table address of node distance d for pivot a: with c = bits(2^23 + min(d, D_a))
+  // (a float whose low bits are the integer), addr = 4 c + base_a where
+  // base_a = table start + 4 offset_a - 4 * 0x4B000000 (mod 2^32).
+  const unsigned tab0 = SMEM ? (unsigned)__cvta_generic_to_shared(stab) : 0u;
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     const int p = __ldg(A.pivots + a);
     const float2 xy = pin[p];
-    const int o = __ldg(A.cnt_off + a);
-    const int e = __ldg(A.cnt_off + a + 1) - o - 1;
-    piv[a] = make_float4(xy.x, xy.y, __int_as_float(o), __int_as_float(e));
+    const int o = __ldg(A.cnt_off + a), e = __ldg(A.cnt_off + a + 1);
+    const unsigned soff = 2u * (unsigned)o, dcap = 2u * (unsigned)(e - o) - 1u;  // D_a = 2 ecc_a + 1
+    pxy[a] = make_float4(xy.x, xy.x, xy.y, xy.y);
+    pidx[a] = make_uint2(tab0 + 4u * soff - 4u * 0x4B000000u, 0x4B000000u | dcap);
   }
-  if (A.cnt_in_smem)
-    for (int t = threadIdx.x; t < A.cnt_len; t += blockDim.x) cntf[t] = (float)__ldg(A.cnt + t);
+  if (SMEM)
+    for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned ntiles = (unsigned)((n + 32 * NPT - 1) / (32 * NPT));
-  const bool vec = (n % NPT) == 0;
+  const unsigned ntiles = (unsigned)((n + 63) / 64);
+  const unsigned nchunks = (unsigned)__ldg(A.cfirst + n);
+  const float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
   for (;;) {
-    unsigned tile = 0;
-    if (lane == 0) tile = atomicAdd(A.tile_ctr, 1u);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(A.tile_ctr, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+
+    if (task < nchunks) {  // ---- a chunk of a long row
+      const int node = __ldg(A.cnode + task);
+      const int rb = __ldg(A.rowptr + node), re = __ldg(A.rowptr + node + 1);
+      const int b = rb + ((int)task - __ldg(A.cfirst + node)) * kChunk;
+      const int e = min(b + kChunk, re);
+      const float2 xi = pin[node];
+      float sx, sy;
+      warp_row(pin, A.colidx, b, e, xi.x, xi.y, sx, sy);
+      if (lane == 0) {
+        A.cpart[task] = make_float2(sx, sy);
+        __threadfence();
+        st_release_u32(A.cflag + task, A.stamp);
+      }
+      continue;
+    }
+    const unsigned tile = task - nchunks;
     if (tile >= ntiles) break;
-    const int i0 = (int)(tile * 32u * NPT + lane * NPT);
 
-    float xi[NPT], yi[NPT], nx[NPT], ny[NPT], den[NPT];
-    int beg[NPT], end[NPT];
-    bool live[NPT];
+    // ---- a tile of 64 nodes: this lane owns i0 and i0 + 1
+    const int i0 = (int)(tile * 64u + 2u * lane);
+    const bool live0 = i0 < n, live1 = i0 + 1 < n;
+    const float2 x0 = live0 ? pin[i0] : make_float2(0.f, 0.f);
+    const float2 x1 = live1 ? pin[i0 + 1] : make_float2(0.f, 0.f);
+    const int b0 = live0 ? __ldg(A.rowptr + i0) : 0, e0 = live0 ? __ldg(A.rowptr + i0 + 1) : 0;
+    const int b1 = live1 ? __ldg(A.rowptr + i0 + 1) : 0, e1 = live1 ? __ldg(A.rowptr + i0 + 2) : 0;
+    const float2 xi2 = make_float2(x0.x, x1.x), yi2 = make_float2(x0.y, x1.y);
+
+    // pivot terms, a = 0..k-1; the d words of the next kPrefetch pivots are
+    // always in flight (one 32-bit load per lane per pivot)
+    float2 nx2 = make_float2(0.f, 0.f), ny2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
+    const uint16_t *row = A.dip + i0;
+    auto load_pair = [&](int a) -> unsigned {
+      if (a >= k || !live0) return 0u;
+      const uint16_t *r = row + (size_t)a * n;
+      if (VEC) return __ldg(reinterpret_cast<const unsigned *>(r));
+      const unsigned lo = (unsigned)__ldg(r), hi = live1 ? (unsigned)__ldg(r + 1) : 0u;
+      return lo | (hi << 16);
+    };
+    unsigned buf[kPrefetch];
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int i = i0 + j;
-      live[j] = i < n;
-      float2 x = live[j] ? pin[i] : make_float2(0.f, 0.f);
-      xi[j] = x.x;
-      yi[j] = x.y;
-      nx[j] = 0.f;
-      ny[j] = 0.f;
-      beg[j] = live[j] ? __ldg(A.rowptr + i) : 0;
-      end[j] = live[j] ? __ldg(A.rowptr + i + 1) : 0;
-      den[j] = (float)(end[j] - beg[j]);
+    for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(t);
+    for (int a0 = 0; a0 < k; a0 += kPrefetch) {
+#pragma unroll
+      for (int t = 0; t < kPrefetch; ++t) {
+        const int a = a0 + t;
+        const unsigned pk = buf[t];
+        buf[t] = load_pair(a + kPrefetch);
+        if (a >= k) break;
+        const float4 P = pxy[a];
+        const uint2 I = pidx[a];
+        // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
+        const float f0 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
+        const float f1 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
+        const float c0 = fminf(f0, __uint_as_float(I.y)), c1 = fminf(f1, __uint_as_float(I.y));
+        float2 s2;
+        if (SMEM) {
+          s2.x = lds_f32(4u * __float_as_uint(c0) + I.x);
+          s2.y = lds_f32(4u * __float_as_uint(c1) + I.x);
+        } else {
+          const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
+          s2.x = __ldg(A.stab + soff + (__float_as_uint(c0) - 0x4B000000u));
+          s2.y = __ldg(A.stab + soff + (__float_as_uint(c1) - 0x4B000000u));
+        }
+        const float2 d2 = __fadd2_rn(make_float2(f0, f1), kMagic2);
+        const float2 dx2 = __fadd2_rn(xi2, make_float2(-P.x, -P.y));
+        const float2 dy2 = __fadd2_rn(yi2, make_float2(-P.z, -P.w));
+        float2 r2 = __ffma2_rn(dy2, dy2, __fmul2_rn(dx2, dx2));
+        r2 = make_float2(fmaxf(r2.x, kR2Floor), fmaxf(r2.y, kR2Floor));
+        // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
+        const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, make_float2(1e-36f, 1e-36f));
+        const float2 u2 = make_float2(rsqrt_approx(q2.x), rsqrt_approx(q2.y));
+        const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
+        const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
+        nx2 = __ffma2_rn(B2, dx2, __ffma2_rn(W2, make_float2(P.x, P.y), nx2));
+        ny2 = __ffma2_rn(B2, dy2, __ffma2_rn(W2, make_float2(P.z, P.w), ny2));
+        den2 = __fadd2_rn(den2, W2);
+      }
     }
 
-    // ---- neighbour terms (w = 1, d = 1), CSR order
+    // neighbour terms (w = 1, d = 1)
+    float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
+    const int deg0 = e0 - b0, deg1 = e1 - b1;
+    if (deg0 <= kLightDeg) light_row(pin, A.colidx, b0, e0, x0.x, x0.y, sx0, sy0);
+    if (deg1 <= kLightDeg) light_row(pin, A.colidx, b1, e1, x1.x, x1.y, sx1, sy1);
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      if (end[j] - beg[j] <= kHeavyDegree) {
-        for (int t = beg[j]; t < end[j]; ++t) {
-          const float2 q = pin[__ldg(A.colidx + t)];
-          const float dx = xi[j] - q.x, dy = yi[j] - q.y;
-          const float r2 = fmaf(dx, dx, dy * dy);
-          const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-          nx[j] += fmaf(dx, inv, q.x);
-          ny[j] += fmaf(dy, inv, q.y);
-        }
-      }
-      unsigned heavy = __ballot_sync(0xffffffffu, end[j] - beg[j] > kHeavyDegree);
-      while (heavy) {
-        const int src = __ffs(heavy) - 1;
-        heavy &= heavy - 1u;
-        const int hb = __shfl_sync(0xffffffffu, beg[j], src), he = __shfl_sync(0xffffffffu, end[j], src);
-        const float hx = __shfl_sync(0xffffffffu, xi[j], src), hy = __shfl_sync(0xffffffffu, yi[j], src);
-        float sx = 0.f, sy = 0.f;
-        for (int t = hb + (int)lane; t < he; t += 32) {
-          const float2 q = pin[__ldg(A.colidx + t)];
-          const float dx = hx - q.x, dy = hy - q.y;
-          const float r2 = fmaf(dx, dx, dy * dy);
-          const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-          sx += fmaf(dx, inv, q.x);
-          sy += fmaf(dy, inv, q.y);
-        }
-        sx = warp_sumf(sx);
-        sy = warp_sumf(sy);
+    for (int j = 0; j < 2; ++j) {
+      const int bj = j ? b1 : b0, ej = j ? e1 : e0, dj = ej - bj;
+      unsigned mid = __ballot_sync(0xffffffffu, dj > kLightDeg && dj <= kChunkDeg);
+      while (mid) {  // medium rows: the whole warp, one row at a time
+        const int src = __ffs(mid) - 1;
+        mid &= mid - 1u;
+        const int hb = __shfl_sync(0xffffffffu, bj, src), he = __shfl_sync(0xffffffffu, ej, src);
+        const float hx = __shfl_sync(0xffffffffu, j ? x1.x : x0.x, src);
+        const float hy = __shfl_sync(0xffffffffu, j ? x1.y : x0.y, src);
+        float sx, sy;
+        warp_row(pin, A.colidx, hb, he, hx, hy, sx, sy);
         if ((int)lane == src) {
-          nx[j] += sx;
-          ny[j] += sy;
+          if (j) { sx1 += sx; sy1 += sy; } else { sx0 += sx; sy0 += sy; }
         }
       }
-    }
-
-    // ---- pivot terms a = 0..k-1, d_ia streamed from HBM
-    const uint16_t *col = A.dip + i0;
-#pragma unroll 4
-    for (int a = 0; a < k; ++a) {
-      const float4 P = piv[a];
-      const int off = __float_as_int(P.z), ecc = __float_as_int(P.w);
-      unsigned d[NPT];
-      const uint16_t *row = col + (size_t)a * n;
-      if (NPT == 2 && vec) {
-        const unsigned pk = live[0] ? __ldcs(reinterpret_cast<const unsigned *>(row)) : 0u;
-        d[0] = pk & 0xFFFFu;
-        d[NPT - 1] = pk >> 16;
-      } else {
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) d[j] = live[j] ? (unsigned)__ldcs(row + j) : 0u;
-      }
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const bool valid = d[j] >= 2u;
-        const int h = min((int)(d[j] >> 1), ecc);
-        const float s = valid ? (A.cnt_in_smem ? cntf[off + h] : (float)__ldg(A.cnt + off + h)) : 0.f;
-        const float dx = xi[j] - P.x, dy = yi[j] - P.y;
-        const float r2 = fmaf(dx, dx, dy * dy);
-        const float df = (float)d[j];
-        const bool ok = valid && r2 > 0.f;
-        const float u = rsqrtf(ok ? df * df * r2 : 1.f);  // 1/(d r)
-        const float B = ok ? s * u : 0.f;                 // w d / r = s/(d r)
-        float Aw = B * u * r2;                            // w = s/d^2
-        if (valid && !(r2 > 0.f)) Aw = s / (df * df);
-        nx[j] = fmaf(Aw, P.x, fmaf(B, dx, nx[j]));
-        ny[j] = fmaf(Aw, P.y, fmaf(B, dy, ny[j]));
-        den[j] += Aw;
+      if (dj > kChunkDeg) {  // long row: its chunk partials, in chunk order
+        const int c0 = __ldg(A.cfirst + i0 + j), c1 = __ldg(A.cfirst + i0 + j + 1);
+        float ax = 0.f, ay = 0.f;
+        for (int c = c0; c < c1; ++c) {
+          // the chunk was handed out before this tile and its warp is running
+          const unsigned long long t0 = globaltimer_ns();
+          bool ready = ld_acquire_u32(A.cflag + c) == A.stamp;
+          while (!ready && globaltimer_ns() - t0 < kChunkWaitNs) ready = ld_acquire_u32(A.cflag + c) == A.stamp;
+          if (!ready) dev_fail(A.status, SSM_E_TIMEOUT);
+          const float2 part = ready ? __ldcg(A.cpart + c) : make_float2(0.f, 0.f);
+          ax += part.x;
+          ay += part.y;
+        }
+        if (j) { sx1 += ax; sy1 += ay; } else { sx0 += ax; sy0 += ay; }
       }
     }
 
-    // ---- write X^{t+1}, accumulate the change of this tile
+    // X^{t+1} and this tile's share of the relative change
     float cn = 0.f, cd = 0.f;
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      if (!live[j]) continue;
-      const float x1 = den[j] > 0.f ? nx[j] / den[j] : xi[j];
-      const float y1 = den[j] > 0.f ? ny[j] / den[j] : yi[j];
-      pout[i0 + j] = make_float2(x1, y1);
-      const float ex = x1 - xi[j], ey = y1 - yi[j];
-      cn = fmaf(ex, ex, fmaf(ey, ey, cn));
-      cd = fmaf(xi[j], xi[j], fmaf(yi[j], yi[j], cd));
+    if ((live0 && !(den2.x == den2.x)) || (live1 && !(den2.y == den2.y))) dev_fail(A.status, SSM_E_NUMERIC);
+    if (live0) {
+      const float dn = den2.x + (float)deg0;
+      const float xn = dn > 0.f ? (nx2.x + sx0) / dn : x0.x, yn = dn > 0.f ? (ny2.x + sy0) / dn : x0.y;
+      pout[i0] = make_float2(xn, yn);
+      const float ex = xn - x0.x, ey = yn - x0.y;
+      cn = fmaf(ex, ex, ey * ey);
+      cd = fmaf(x0.x, x0.x, x0.y * x0.y);
     }
-    double tn = warp_sum((double)cn), td = warp_sum((double)cd);
+    if (live1) {
+      const float dn = den2.y + (float)deg1;
+      const float xn = dn > 0.f ? (nx2.y + sx1) / dn : x1.x, yn = dn > 0.f ? (ny2.y + sy1) / dn : x1.y;
+      pout[i0 + 1] = make_float2(xn, yn);
+      const float ex = xn - x1.x, ey = yn - x1.y;
+      cn = fmaf(ex, ex, fmaf(ey, ey, cn));
+      cd = fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, cd));
+    }
+    const double tn = warp_sum((double)cn), td = warp_sum((double)cd);
     if (lane == 0) {
       A.tile_part[2 * (size_t)tile] = tn;
       A.tile_part[2 * (size_t)tile + 1] = td;
     }
   }
   finish_iteration(A, ntiles);
+}
+
+// ----------------------------------------------------------------- setup (once per ssm_iterate)
+// s-by-d table: stab[2 off_a + d] = (d >= 2) ? cnt[off_a + min(d/2, ecc_a)] : 0, d = 0..2 ecc_a + 1
+__global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, const uint32_t *__restrict__ cnt,
+                             float *__restrict__ stab) {
+  for (int a = blockIdx.x; a < k; a += gridDim.x) {
+    const int o = cnt_off[a], ecc = cnt_off[a + 1] - o - 1;
+    for (int d = threadIdx.x; d <= 2 * ecc + 1; d += blockDim.x)
+      stab[2 * o + d] = d >= 2 ? (float)cnt[o + min(d >> 1, ecc)] : 0.f;
+  }
+}
+
+__global__ void k_chunk_count(int32_t n, const int32_t *__restrict__ rowptr, int *__restrict__ nch) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int deg = rowptr[i + 1] - rowptr[i];
+    nch[i] = deg > kChunkDeg ? (deg + kChunk - 1) / kChunk : 0;
+  }
+}
+
+__global__ void k_chunk_nodes(int32_t n, const int32_t *__restrict__ cfirst, int32_t *__restrict__ cnode) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) cnode[c] = (int32_t)i;
 }
 
 // ----------------------------------------------------------------- FP64
@@ -248,6 +391,7 @@ __device__ __forceinline__ double dist_rn(double dx, double dy) {
   return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
 }
 
+template <bool CNT_SMEM>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(SweepArgs A, const double2 *__restrict__ pin,
                                                               double2 *__restrict__ pout) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -261,7 +405,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(SweepArgs A, const 
     const int o = __ldg(A.cnt_off + a);
     piv[a] = PivD{xy.x, xy.y, o, __ldg(A.cnt_off + a + 1) - o - 1};
   }
-  if (A.cnt_in_smem)
+  if (CNT_SMEM)
     for (int t = threadIdx.x; t < A.cnt_len; t += blockDim.x) cntd[t] = (double)__ldg(A.cnt + t);
   __syncthreads();
 
@@ -297,7 +441,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(SweepArgs A, const 
         if (d < 2) continue;
         const PivD P = piv[a];
         const int h = min(d >> 1, P.ecc);
-        const double s = A.cnt_in_smem ? cntd[P.off + h] : (double)__ldg(A.cnt + P.off + h);
+        const double s = CNT_SMEM ? cntd[P.off + h] : (double)__ldg(A.cnt + P.off + h);
         const double dd = (double)d;
         const double w = __ddiv_rn(s, __dmul_rn(dd, dd));
         const double dx = __dsub_rn(x.x, P.x), dy = __dsub_rn(x.y, P.y);
@@ -340,91 +484,119 @@ __global__ void k_copy_back_if_odd(int64_t count, const int32_t *__restrict__ it
 
 struct IterWs {
   void *tmp;
-  unsigned *ctr;  // [0] tile counter, [1] done counter
+  unsigned *ctr;  // [0] task counter, [1] done counter
   int32_t *stop;
   double *tile_part;
+  float *stab;
+  int *nch;       // [n] chunk counts
+  int32_t *cfirst;  // [n+1]
+  int32_t *cnode;
+  float2 *cpart;
+  unsigned *cflag;
+  int *tiles;     // scan workspace
 };
 
-static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int32_t precision) {
+// a row of deg > kChunkDeg yields ceil(deg / kChunk) <= 0.0116 deg chunks, below deg / 64
+static size_t max_chunks(int64_t m2) { return (size_t)(m2 / 64 + 1); }
+
+static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int64_t cnt_len, int32_t precision) {
   const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
   w.tmp = c.take<char>((size_t)n * elem);
   w.ctr = c.take<unsigned>(2);
   w.stop = c.take<int32_t>(1);
   w.tile_part = c.take<double>(2 * ((size_t)n / 32 + 2));
+  w.stab = c.take<float>((size_t)(2 * cnt_len));
+  w.nch = c.take<int>((size_t)n);
+  w.cfirst = c.take<int32_t>((size_t)n + 1);
+  const size_t mc = max_chunks(m2);
+  w.cnode = c.take<int32_t>(mc);
+  w.cpart = c.take<float2>(mc);
+  w.cflag = c.take<unsigned>(mc);
+  w.tiles = c.take<int>((size_t)scan_tiles(n) + 1);
   return c.size();
 }
 
 }  // namespace ssm
 
-SSM_API size_t ssm_iterate_workspace(int32_t n, int32_t k, int32_t precision) {
+SSM_API size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision) {
   (void)k;
-  if (n < 1) return 0;
+  if (n < 1 || m < 0 || cnt_len < 0) return 0;
   ssm::Carver c(nullptr, 0);
   ssm::IterWs w;
-  return ssm::carve_iterate(c, w, n, precision);
+  return ssm::carve_iterate(c, w, n, 2 * m, cnt_len, precision);
 }
 
-SSM_API int ssm_iterate(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *pivots,
-                        const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt, int64_t cnt_len,
-                        void *pos, int32_t precision, int32_t iters, double tol, int32_t *iters_done,
-                        double *rel_change, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                        const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
+                        int64_t cnt_len, void *pos, int32_t precision, int32_t iters, double tol,
+                        int32_t *iters_done, double *rel_change, int32_t *status, void *ws, size_t ws_bytes,
+                        cudaStream_t s) {
   using namespace ssm;
-  if (n < 1 || !rowptr || !colidx || !pivots || !dip || !cnt_off || !cnt || !pos || !iters_done || !rel_change ||
-      !status || !ws)
-    return fail(SSM_E_ARG, "ssm_iterate: null pointer or n < 1");
+  if (n < 1 || m < 0 || !rowptr || !colidx || !pivots || !dip || !cnt_off || !cnt || !pos || !iters_done ||
+      !rel_change || !status || !ws)
+    return fail(SSM_E_ARG, "ssm_iterate: null pointer or bad size");
   if (k < 1 || k > kMaxPivotsSweep) return fail(SSM_E_ARG, "ssm_iterate: need 1 <= k <= %d", kMaxPivotsSweep);
   if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_iterate: precision must be 32 or 64");
   if (iters < 1) return fail(SSM_E_ARG, "ssm_iterate: iters must be >= 1");
-  if (cnt_len < k || cnt_len >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_iterate: bad count-table length");
+  if (cnt_len < k || cnt_len >= ((int64_t)1 << 30)) return fail(SSM_E_ARG, "ssm_iterate: bad count-table length");
   Carver c(ws, ws_bytes);
   IterWs w;
-  carve_iterate(c, w, n, precision);
+  carve_iterate(c, w, n, 2 * m, cnt_len, precision);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_iterate: workspace %zu bytes, need %zu", ws_bytes, c.size());
 
   SweepArgs A;
   A.n = n; A.k = k; A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.cnt_off = cnt_off;
-  A.dip = dip; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len;
+  A.dip = dip; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
+  A.stab = w.stab; A.cfirst = w.cfirst; A.cnode = w.cnode; A.cpart = w.cpart; A.cflag = w.cflag; A.stamp = 0;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
-  A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol;
+  A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol; A.status = status;
 
-  const size_t piv_bytes = (size_t)k * (precision == 64 ? sizeof(PivD) : sizeof(float4));
-  const size_t tab_bytes = (size_t)cnt_len * (precision == 64 ? sizeof(double) : sizeof(float));
-  A.cnt_in_smem = piv_bytes + tab_bytes <= kSmemBudget;
-  const size_t smem = piv_bytes + (A.cnt_in_smem ? tab_bytes : 0);
-
-  const void *kern;
-  if (precision == 64) kern = (const void *)k_sweep_f64;
-  else if (n % 2 == 0) kern = (const void *)k_sweep_f32<2>;
-  else kern = (const void *)k_sweep_f32<1>;
-  SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
-  if (per_sm < 1) return fail(SSM_E_ARG, "ssm_iterate: %zu bytes of shared memory do not fit", smem);
-  const int64_t tiles = precision == 64 ? (n + 31) / 32 : (n + 63) / 64;
-  const int64_t want = (tiles + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * num_sms(), want));
-
+  const int sms = num_sms();
+  const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   SSM_TRY_CUDA(cudaMemsetAsync(w.ctr, 0, 2 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(w.stop, 0, sizeof(int32_t), s));
   SSM_TRY_CUDA(cudaMemsetAsync(iters_done, 0, sizeof(int32_t), s));
   SSM_TRY_CUDA(cudaMemsetAsync(rel_change, 0, sizeof(double), s));
+
+  const void *kern;
+  size_t smem;
+  int64_t tiles;
+  bool vec = (n % 2) == 0, tsm = true;
+  if (precision == 64) {
+    const size_t piv = (size_t)k * sizeof(PivD), tab = (size_t)cnt_len * sizeof(double);
+    tsm = piv + tab <= kSmemBudget;
+    smem = piv + (tsm ? tab : 0);
+    kern = tsm ? (const void *)k_sweep_f64<true> : (const void *)k_sweep_f64<false>;
+    tiles = (n + 31) / 32;
+  } else {
+    k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
+    k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
+    int rc = exclusive_scan(w.nch, w.cfirst, n, w.tiles, s);
+    if (rc) return rc;
+    k_chunk_nodes<<<nb, 256, 0, s>>>(n, w.cfirst, w.cnode);
+    SSM_TRY_CUDA(cudaMemsetAsync(w.cflag, 0, max_chunks(2 * m) * sizeof(unsigned), s));
+    const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2)), tab = (size_t)(2 * cnt_len) * sizeof(float);
+    tsm = piv + tab <= kSmemBudget;
+    smem = piv + (tsm ? tab : 0);
+    kern = vec ? (tsm ? (const void *)k_sweep_f32<true, true> : (const void *)k_sweep_f32<true, false>)
+               : (tsm ? (const void *)k_sweep_f32<false, true> : (const void *)k_sweep_f32<false, false>);
+    tiles = (n + 63) / 64;
+  }
+  SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
+  if (per_sm < 1) return fail(SSM_E_ARG, "ssm_iterate: %zu bytes of shared memory do not fit", smem);
+  const int64_t want = (tiles + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+
   for (int t = 0; t < iters; ++t) {
     const bool even = (t & 1) == 0;
-    if (precision == 64) {
-      const double2 *pin = (const double2 *)(even ? pos : w.tmp);
-      double2 *pout = (double2 *)(even ? w.tmp : pos);
-      k_sweep_f64<<<blocks, kSweepThreads, smem, s>>>(A, pin, pout);
-    } else if (n % 2 == 0) {
-      const float2 *pin = (const float2 *)(even ? pos : w.tmp);
-      float2 *pout = (float2 *)(even ? w.tmp : pos);
-      k_sweep_f32<2><<<blocks, kSweepThreads, smem, s>>>(A, pin, pout);
-    } else {
-      const float2 *pin = (const float2 *)(even ? pos : w.tmp);
-      float2 *pout = (float2 *)(even ? w.tmp : pos);
-      k_sweep_f32<1><<<blocks, kSweepThreads, smem, s>>>(A, pin, pout);
-    }
+    A.stamp = (unsigned)t + 1u;
+    void *pin = even ? pos : w.tmp, *pout = even ? w.tmp : pos;
+    void *args[] = {&A, &pin, &pout};
+    SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(blocks), dim3(kSweepThreads), args, smem, s));
   }
-  const int cb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)num_sms() * 8);
+  const int cb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   if (precision == 64)
     k_copy_back_if_odd<double2><<<cb, 256, 0, s>>>(n, iters_done, (const double2 *)w.tmp, (double2 *)pos);
   else
