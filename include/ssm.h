@@ -25,6 +25,7 @@
  *   - Graphs are simple and undirected, stored as CSR: rowptr[n+1] int32,
  *     colidx[2m] int32, every row sorted ascending, no self-loops, no
  *     repeated entries (as produced by ssm_build_graph).  Node ids are 0..n-1.
+ *     Calls that take a graph take (n, m, rowptr, colidx) with m = |E|.
  *   - Positions are interleaved (x, y) pairs: float[2n] for precision 32,
  *     double[2n] for precision 64.
  *   - The pivot-distance table d_ip is pivot-major uint16: dip[a*n + i] is the
@@ -86,8 +87,8 @@ int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const int32_t *
  * (int32, selection order).  1 <= k <= n.  Device errors: SSM_E_DISCONNECTED,
  * SSM_E_TIMEOUT (a device-wide barrier waited longer than 2 s).
  * ------------------------------------------------------------------- */
-size_t ssm_select_pivots_workspace(int32_t n);
-int ssm_select_pivots(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+size_t ssm_select_pivots_workspace(int32_t n, int64_t m);
+int ssm_select_pivots(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                       int32_t start, int32_t *pivots, int32_t *status,
                       void *ws, size_t ws_bytes, cudaStream_t stream);
 
@@ -98,8 +99,8 @@ int ssm_select_pivots(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
  * distinct.  Device errors: SSM_E_DISCONNECTED, SSM_E_DIST_OVERFLOW,
  * SSM_E_TIMEOUT.
  * ------------------------------------------------------------------- */
-size_t ssm_pivot_bfs_workspace(int32_t n, int32_t k);
-int ssm_pivot_bfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+size_t ssm_pivot_bfs_workspace(int32_t n, int64_t m, int32_t k);
+int ssm_pivot_bfs(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                   const int32_t *pivots, uint16_t *dip, int32_t *status,
                   void *ws, size_t ws_bytes, cudaStream_t stream);
 
@@ -130,7 +131,9 @@ int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, in
  *   each signed so its largest-magnitude entry (lowest index on a tie) is positive,
  *   x_i = ((C v1)_i, (C v2)_i).
  * Writes pos[2n] (float or double by precision 32/64) and, if eig is not NULL,
- * the two eigenvalues to eig[2] (device, double).  2 <= k <= 1024.
+ * eig[4] (device, double): the two eigenvalues, the number of subspace
+ * iterations used and the final relative residual max_j ||B v_j - l_j v_j|| / l_1.
+ * 2 <= k <= 1024.
  * Device errors: SSM_E_NUMERIC (eigen-solve did not converge or zero layout).
  * ------------------------------------------------------------------- */
 size_t ssm_pivotmds_workspace(int32_t n, int32_t k);
@@ -181,8 +184,8 @@ int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *coli
  * All sums are FP64 in a fixed order.  Device errors: SSM_E_DISCONNECTED,
  * SSM_E_DIST_OVERFLOW, SSM_E_TIMEOUT.  2 <= n.
  * ------------------------------------------------------------------- */
-size_t ssm_stress_workspace(int32_t n, int32_t nsources, int32_t ntargets);
-int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const void *pos,
+size_t ssm_stress_workspace(int32_t n, int64_t m, int32_t nsources, int32_t ntargets);
+int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, const void *pos,
                int32_t precision, int32_t nsources, int32_t ntargets, uint64_t seed,
                double *out, double *sums, int32_t *status,
                void *ws, size_t ws_bytes, cudaStream_t stream);

@@ -58,10 +58,10 @@ def lib():
                 "ssm_check": (ctypes.c_int, [v, v]),
                 "ssm_build_graph_workspace": (sz, [i32, i64]),
                 "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, sz, v]),
-                "ssm_select_pivots_workspace": (sz, [i32]),
-                "ssm_select_pivots": (ctypes.c_int, [i32, v, v, i32, i32, v, v, v, sz, v]),
-                "ssm_pivot_bfs_workspace": (sz, [i32, i32]),
-                "ssm_pivot_bfs": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, sz, v]),
+                "ssm_select_pivots_workspace": (sz, [i32, i64]),
+                "ssm_select_pivots": (ctypes.c_int, [i32, i64, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_pivot_bfs_workspace": (sz, [i32, i64, i32]),
+                "ssm_pivot_bfs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, sz, v]),
                 "ssm_aggregate_workspace": (sz, [i32]),
                 "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
@@ -69,8 +69,8 @@ def lib():
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
                 "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
-                "ssm_stress_workspace": (sz, [i32, i32, i32]),
-                "ssm_stress": (ctypes.c_int, [i32, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
+                "ssm_stress_workspace": (sz, [i32, i64, i32, i32]),
+                "ssm_stress": (ctypes.c_int, [i32, i64, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -152,8 +152,8 @@ def ssm_select_pivots(g: Graph, k: int, start: int = 0, stream=None, check: bool
     dev = g.rowptr.device
     piv = torch.empty(k, dtype=torch.int32, device=dev)
     st = _status(dev)
-    ws = _ws(L.ssm_select_pivots_workspace(g.n), dev)
-    _rc(L.ssm_select_pivots(g.n, _ptr(g.rowptr), _ptr(g.colidx), k, start, _ptr(piv), _ptr(st), _ptr(ws), ws.numel(),
+    ws = _ws(L.ssm_select_pivots_workspace(g.n, g.m), dev)
+    _rc(L.ssm_select_pivots(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), k, start, _ptr(piv), _ptr(st), _ptr(ws), ws.numel(),
                             _stream(stream)), "ssm_select_pivots")
     if check:
         ssm_check(st, "ssm_select_pivots", stream)
@@ -166,8 +166,8 @@ def ssm_pivot_bfs(g: Graph, pivots: torch.Tensor, stream=None, check: bool = Tru
     k = pivots.numel()
     dip = torch.empty((k, g.n), dtype=torch.uint16, device=dev)
     st = _status(dev)
-    ws = _ws(L.ssm_pivot_bfs_workspace(g.n, k), dev)
-    _rc(L.ssm_pivot_bfs(g.n, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(pivots.contiguous()), _ptr(dip), _ptr(st),
+    ws = _ws(L.ssm_pivot_bfs_workspace(g.n, g.m, k), dev)
+    _rc(L.ssm_pivot_bfs(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(pivots.contiguous()), _ptr(dip), _ptr(st),
                         _ptr(ws), ws.numel(), _stream(stream)), "ssm_pivot_bfs")
     if check:
         ssm_check(st, "ssm_pivot_bfs", stream)
@@ -205,12 +205,13 @@ def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, ch
 
 def ssm_pivotmds(g: Graph, dip: torch.Tensor, precision: int = 32, rescale: bool = True, stream=None,
                  check: bool = True):
-    """Returns (pos [n,2] float32/float64, eigenvalues [2] float64)."""
+    """Returns (pos [n,2] float32/float64, eig [4] float64: the two eigenvalues,
+    subspace iterations used, final relative residual)."""
     L = lib()
     k, n = dip.shape
     dev = dip.device
     pos = torch.empty((n, 2), dtype=torch.float64 if precision == 64 else torch.float32, device=dev)
-    eig = torch.empty(2, dtype=torch.float64, device=dev)
+    eig = torch.empty(4, dtype=torch.float64, device=dev)
     st = _status(dev)
     ws = _ws(L.ssm_pivotmds_workspace(n, k), dev)
     _rc(L.ssm_pivotmds(n, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(dip), _ptr(pos), precision, int(bool(rescale)),
@@ -246,8 +247,8 @@ def ssm_iterate(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, tol: float =
 
 
 class StressWorkspace:
-    def __init__(self, n: int, nsources: int, ntargets: int, device):
-        self.ws = _ws(lib().ssm_stress_workspace(n, nsources, ntargets), device)
+    def __init__(self, n: int, m: int, nsources: int, ntargets: int, device):
+        self.ws = _ws(lib().ssm_stress_workspace(n, m, nsources, ntargets), device)
         self.out = torch.zeros(4, dtype=torch.float64, device=device)
         self.sums = torch.zeros(4, dtype=torch.float64, device=device)
         self.status = _status(device)
@@ -259,8 +260,8 @@ def ssm_stress(g: Graph, pos: torch.Tensor, nsources: int = 0, ntargets: int = 0
     L = lib()
     precision = 64 if pos.dtype == torch.float64 else 32
     if work is None:
-        work = StressWorkspace(g.n, nsources, ntargets, pos.device)
-    _rc(L.ssm_stress(g.n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(pos), precision, nsources, ntargets,
+        work = StressWorkspace(g.n, g.m, nsources, ntargets, pos.device)
+    _rc(L.ssm_stress(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), _ptr(pos), precision, nsources, ntargets,
                      ctypes.c_uint64(seed), _ptr(work.out), _ptr(work.sums), _ptr(work.status), _ptr(work.ws),
                      work.ws.numel(), _stream(stream)), "ssm_stress")
     if check:

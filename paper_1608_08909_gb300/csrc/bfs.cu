@@ -32,6 +32,7 @@ struct MaxMinArgs {
   int32_t start;
   int32_t *pivots;
   int32_t *status;
+  const int4 *adj;  // [2m] edge-expanded adjacency (v, rowptr[v], rowptr[v+1], 0)
   unsigned *mind;  // [n] hop distance to the closest chosen pivot
   unsigned *q0, *q1;  // [n] frontier queues (alternate by level parity)
   unsigned *qcnt;     // [3] queue lengths, rotated by level
@@ -68,20 +69,15 @@ __device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*
     for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
       const unsigned e = base + lane;
       const int2 r = e < cc ? sq[cur][e] : make_int2(0, 0);
-      warp_for_each_neighbor(r.x, r.y, A.colidx, [&](int, bool act, int v) {
-        bool push = false;
-        if (act && nd < __ldcg(A.mind + v)) push = atomicMin(A.mind + v, nd) > nd;
-        const unsigned mask = __ballot_sync(0xffffffffu, push);
-        if (!mask) return;
-        unsigned pos = 0;
-        const int leader = __ffs(mask) - 1;
-        if ((int)lane == leader) pos = atomicAdd(s_cnt + nxt, (unsigned)__popc(mask));
-        pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
-        if (push) {
-          qout[pos] = (unsigned)v;
-          if (pos < (unsigned)kSoloMax) sq[nxt][pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
-        }
-      });
+      warp_for_each_edge4_batched<8>(
+          r.x, r.y, A.adj, [&](int, int4 ed) { return atomicMin(A.mind + ed.x, nd) > nd; },
+          [&](int, int4 ed, bool push) {
+            const unsigned pos = warp_slot(push, s_cnt + nxt);
+            if (push) {
+              qout[pos] = (unsigned)ed.x;
+              if (pos < (unsigned)kSoloMax) sq[nxt][pos] = make_int2(ed.y, ed.z);
+            }
+          });
     }
     __syncthreads();
     if (threadIdx.x == 0) s_cnt[cur] = 0;
@@ -187,12 +183,31 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
   }
 }
 
-int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+// adj[t] = (colidx[t], rowptr[colidx[t]], rowptr[colidx[t] + 1], 0)
+__global__ void k_expand_adj(int64_t m2, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                             int4 *__restrict__ adj) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = __ldg(colidx + t);
+    adj[t] = make_int4(v, __ldg(rowptr + v), __ldg(rowptr + v + 1), 0);
+  }
+}
+
+static int expand_adj(int64_t m2, const int32_t *rowptr, const int32_t *colidx, int4 *adj, cudaStream_t s) {
+  if (m2 <= 0) return SSM_OK;
+  const int blocks = (int)std::min<int64_t>((m2 + 255) / 256, (int64_t)num_sms() * 8);
+  k_expand_adj<<<blocks, 256, 0, s>>>(m2, rowptr, colidx, adj);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
                   int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   Carver c(ws, ws_bytes);
   MaxMinArgs A;
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
   A.pivots = pivots; A.status = status;
+  int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
+  A.adj = adj;
   A.mind = c.take<unsigned>(n);
   A.q0 = c.take<unsigned>(n);
   A.q1 = c.take<unsigned>(n);
@@ -201,6 +216,8 @@ int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32
   A.best = c.take<unsigned long long>(2);
   A.bar = c.take<BarrierState>(1);
   if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  int rc = expand_adj(m2, rowptr, colidx, adj, s);
+  if (rc) return rc;
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
@@ -211,8 +228,9 @@ int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32
   return SSM_OK;
 }
 
-size_t maxmin_workspace(int32_t n) {
+size_t maxmin_workspace(int32_t n, int64_t m2) {
   Carver c(nullptr, 0);
+  c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
   c.take<unsigned>(n);
   c.take<unsigned>(n);
   c.take<unsigned>(n);
@@ -238,6 +256,7 @@ struct CtaBfsArgs {
   const int32_t *sources;
   uint16_t *dist;  // [nsrc][n]
   int32_t *status;
+  const int4 *adj; // [2m] edge-expanded adjacency
   int2 *queues;    // [slots][2][n] row ranges of the frontier
 };
 
@@ -282,24 +301,20 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
       for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
         const unsigned e = base + lane;
         const int2 r = e < cc ? __ldcg(qin + e) : make_int2(0, 0);
-        warp_for_each_neighbor(r.x, r.y, A.colidx, [&](int, bool act, int v) {
-          bool push = false;
-          if (act) {
-            const unsigned bit = 1u << ((unsigned)v & 31u);
-            unsigned *wp = vis + ((unsigned)v >> 5);
-            if (!(*wp & bit)) push = !(atomicOr(wp, bit) & bit);
-          }
-          const unsigned mask = __ballot_sync(0xffffffffu, push);
-          if (!mask) return;
-          unsigned pos = 0;
-          const int leader = __ffs(mask) - 1;
-          if ((int)lane == leader) pos = atomicAdd(s_cnt + nxt, (unsigned)__popc(mask));
-          pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
-          if (push) {
-            row[v] = nd;
-            qout[pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
-          }
-        });
+        warp_for_each_edge4_batched<4>(
+            r.x, r.y, A.adj,
+            [&](int, int4 ed) {
+              const unsigned bit = 1u << ((unsigned)ed.x & 31u);
+              unsigned *wp = vis + ((unsigned)ed.x >> 5);
+              return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
+            },
+            [&](int, int4 ed, bool push) {
+              const unsigned pos = warp_slot(push, s_cnt + nxt);
+              if (push) {
+                row[ed.x] = nd;
+                qout[pos] = make_int2(ed.y, ed.z);
+              }
+            });
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -452,9 +467,10 @@ static void msbfs_carve(Carver &c, MsBfsArgs &A, int32_t n, int32_t k) {
   A.bar = c.take<BarrierState>(1);
 }
 
-size_t msbfs_workspace(int32_t n, int32_t k) {
+size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   Carver c(nullptr, 0);
   if (cta_bfs_fits(n)) {
+    c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
     c.take<int2>((size_t)cta_bfs_slots(k) * 2 * (size_t)n);
     return c.size();
   }
@@ -463,16 +479,20 @@ size_t msbfs_workspace(int32_t n, int32_t k) {
   return c.size();
 }
 
-int launch_msbfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
-                 uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                 const int32_t *sources, uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   Carver c(ws, ws_bytes);
   if (cta_bfs_fits(n)) {
     CtaBfsArgs B;
     B.n = n; B.rowptr = rowptr; B.colidx = colidx; B.nsrc = k; B.sources = sources; B.dist = dist;
     B.status = status;
     const int slots = cta_bfs_slots(k);
+    int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
+    B.adj = adj;
     B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
     if (!c.ok) return fail(SSM_E_NOMEM, "BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
+    int rc = expand_adj(m2, rowptr, colidx, adj, s);
+    if (rc) return rc;
     const size_t smem = (size_t)((n + 31) / 32) * 4;
     SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_bfs_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
@@ -503,27 +523,31 @@ int launch_msbfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
 }  // namespace ssm
 
 // ---------------------------------------------------------------- C ABI
-SSM_API size_t ssm_select_pivots_workspace(int32_t n) { return n > 0 ? ssm::maxmin_workspace(n) : 0; }
+SSM_API size_t ssm_select_pivots_workspace(int32_t n, int64_t m) {
+  return (n > 0 && m >= 0) ? ssm::maxmin_workspace(n, 2 * m) : 0;
+}
 
-SSM_API int ssm_select_pivots(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
-                              int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream) {
-  if (n < 1 || !rowptr || !colidx || !pivots || !status || !ws)
-    return ssm::fail(SSM_E_ARG, "ssm_select_pivots: null pointer or n < 1");
+SSM_API int ssm_select_pivots(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                              int32_t start, int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes,
+                              cudaStream_t stream) {
+  if (n < 1 || m < 0 || !rowptr || !colidx || !pivots || !status || !ws)
+    return ssm::fail(SSM_E_ARG, "ssm_select_pivots: null pointer or bad size");
   if (k < 1 || k > n) return ssm::fail(SSM_E_ARG, "ssm_select_pivots: need 1 <= k <= n (k=%d, n=%d)", k, n);
   if (start < 0 || start >= n) return ssm::fail(SSM_E_ARG, "ssm_select_pivots: start %d outside 0..n-1", start);
-  return ssm::launch_maxmin(n, rowptr, colidx, k, start, pivots, status, ws, ws_bytes, stream);
+  return ssm::launch_maxmin(n, 2 * m, rowptr, colidx, k, start, pivots, status, ws, ws_bytes, stream);
 }
 
-SSM_API size_t ssm_pivot_bfs_workspace(int32_t n, int32_t k) {
-  return (n > 0 && k > 0) ? ssm::msbfs_workspace(n, k) : 0;
+SSM_API size_t ssm_pivot_bfs_workspace(int32_t n, int64_t m, int32_t k) {
+  return (n > 0 && m >= 0 && k > 0) ? ssm::msbfs_workspace(n, 2 * m, k) : 0;
 }
 
-SSM_API int ssm_pivot_bfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *pivots,
-                          uint16_t *dip, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream) {
-  if (n < 1 || !rowptr || !colidx || !pivots || !dip || !status || !ws)
-    return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: null pointer or n < 1");
+SSM_API int ssm_pivot_bfs(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                          const int32_t *pivots, uint16_t *dip, int32_t *status, void *ws, size_t ws_bytes,
+                          cudaStream_t stream) {
+  if (n < 1 || m < 0 || !rowptr || !colidx || !pivots || !dip || !status || !ws)
+    return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: null pointer or bad size");
   if (k < 1 || k > 65535) return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: need 1 <= k <= 65535 (k=%d)", k);
   if ((int64_t)n * ((k + 31) / 32) >= (int64_t)1 << 31)
     return ssm::fail(SSM_E_ARG, "ssm_pivot_bfs: n*ceil(k/32) must be below 2^31");
-  return ssm::launch_msbfs(n, rowptr, colidx, k, pivots, dip, status, ws, ws_bytes, stream);
+  return ssm::launch_msbfs(n, 2 * m, rowptr, colidx, k, pivots, dip, status, ws, ws_bytes, stream);
 }

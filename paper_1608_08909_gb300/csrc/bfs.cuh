@@ -6,15 +6,16 @@
 
 namespace ssm {
 
-size_t maxmin_workspace(int32_t n);
+// m2 = number of directed edges (colidx entries) in all of these.
+size_t maxmin_workspace(int32_t n, int64_t m2);
 // max/min-sp pivots; with k == 1 it is a single BFS from `start` that flags
 // SSM_E_DISCONNECTED in *status if some node is unreachable.
-int launch_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
                   int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s);
 
-size_t msbfs_workspace(int32_t n, int32_t k);
+size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k);
 // dist[a*n + v] = hop distance from sources[a] to v, for a < k
-int launch_msbfs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
-                 uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s);
+int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                 const int32_t *sources, uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s);
 
 }  // namespace ssm

@@ -164,7 +164,7 @@ static size_t carve_build(Carver &c, BuildWs &w, int32_t n, int64_t m_in) {
   w.big_rows = c.take<unsigned>(n);
   w.big_count = c.take<unsigned>(1);
   w.status = c.take<int32_t>(2);
-  w.bfs_bytes = maxmin_workspace(n);
+  w.bfs_bytes = maxmin_workspace(n, 2 * m_in);
   w.bfs_ws = c.take<char>(w.bfs_bytes);
   return c.size();
 }
@@ -213,14 +213,15 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   if (rc) return rc;
   k_compact<<<std::max(eblocks, nblocks), 256, 0, s>>>(n, total, w.off, w.tmp, w.flag, w.pos, rowptr, colidx);
   SSM_TRY_CUDA(cudaGetLastError());
-  // connectivity: one BFS from node 0 (status[1] receives its pivot slot)
-  rc = launch_maxmin(n, rowptr, colidx, 1, 0, w.status + 1, w.status, w.bfs_ws, w.bfs_bytes, s);
-  if (rc) return rc;
   int32_t uniq = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&uniq, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  SSM_TRY_CUDA(cudaMemcpyAsync(&hstatus, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
   *m_out = uniq / 2;
+  // connectivity: one BFS from node 0 over the final CSR (status[1] receives its pivot slot)
+  rc = launch_maxmin(n, (int64_t)uniq, rowptr, colidx, 1, 0, w.status + 1, w.status, w.bfs_ws, w.bfs_bytes, s);
+  if (rc) return rc;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&hstatus, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
   if (hstatus) return fail(hstatus, "ssm_build_graph: %s", ssm_status_string(hstatus));
   return SSM_OK;
 }

@@ -9,8 +9,10 @@
 //   k_gram      G = Delta^T Delta (upper tiles, 64x64 per block, node chunks)
 //   k_colsum    s_a
 //   k_prepare_b B = 1/4 J (G - s s^T/n) J
-//   k_eigen     top-2 eigenpairs of B, FP64 subspace iteration with
-//               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (one block)
+//   k_square    M = (B / max|B|)^4 by two FP64 squarings (grid)
+//   k_eigen     top-2 eigenpairs of B: FP64 subspace iteration on M with
+//               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (one
+//               block), then a Rayleigh-Ritz step with B
 //   k_project   x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa),
 //               the sum in compensated (two-float) FP32 arithmetic
 //   k_edge_sum / k_rescale: scale so that sum_E ||x_i - x_j|| = m.
@@ -179,6 +181,40 @@ __global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__re
 }
 
 // ------------------------------------------------------------- eigen-solve
+// *scale = 1 / max |B_ij| (one block)
+__global__ void k_absmax_inv(int64_t count, const double *__restrict__ B, double *__restrict__ scale) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int64_t t = threadIdx.x; t < count; t += blockDim.x) m = fmax(m, fabs(B[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t = fmax(t, red[w]);
+    *scale = t > 0.0 ? 1.0 / t : 1.0;
+  }
+}
+
+// C = (sA)(sA) for a symmetric k x k matrix A, s = *scale (or 1): 16 x 16 output tiles
+__global__ void __launch_bounds__(256) k_square_f64(int32_t k, const double *__restrict__ A,
+                                                    const double *__restrict__ scale, double *__restrict__ C) {
+  __shared__ double ta[16][17], tb[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
+  const double sc = scale ? *scale : 1.0;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    ta[ty][tx] = (r < k && k0 + tx < k) ? A[(size_t)r * k + k0 + tx] * sc : 0.0;
+    tb[ty][tx] = (k0 + ty < k && c < k) ? A[(size_t)(k0 + ty) * k + c] * sc : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc = fma(ta[ty][t], tb[t][tx], acc);
+    __syncthreads();
+  }
+  if (r < k && c < k) C[(size_t)r * k + c] = acc;
+}
+
 // block-wide sum of N doubles per thread (result broadcast to all threads)
 template <int N>
 __device__ void block_sum(double (&v)[N], double *scratch /* [warps*N] */) {
@@ -305,16 +341,22 @@ struct EigOut {
   int32_t converged;
 };
 
-// top-2 eigenpairs of B (k x k, FP64) by subspace iteration of dimension P
+// top-2 eigenpairs of B (k x k, FP64).  Subspace iteration of dimension P
+// runs on M (the fourth power of B / max|B|, same eigenvectors, ratios of
+// eigenvalues raised to the fourth power, so the subspace converges four
+// times faster per iteration) with a Rayleigh-Ritz step every iteration;
+// a final Rayleigh-Ritz step with B itself gives the eigenvalues and the
+// reported residual.
 __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, const double *__restrict__ B,
+                                                       const double *__restrict__ M,
                                                        const unsigned long long *__restrict__ s,
                                                        double *__restrict__ vout /* [2][k] */,
                                                        EigOut *__restrict__ out, double *__restrict__ eig_user,
                                                        int32_t *__restrict__ status, int maxit, double tol) {
   extern __shared__ __align__(16) double sm[];
   const int P = min(kEigP, k);
-  double *V = sm;               // k x P
-  double *Y = V + (size_t)k * P;  // k x P
+  double *V = sm;                       // k x P
+  double *Y = V + (size_t)k * P;        // k x P
   double *scratch = Y + (size_t)k * P;  // kEigScratch doubles
   __shared__ double H[kEigP * kEigP], Q[kEigP * kEigP];
   __shared__ int s_done;
@@ -326,20 +368,21 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
   if (threadIdx.x == 0) s_done = 0;
   __syncthreads();
 
-  int it = 0;
-  for (; it < maxit; ++it) {
-    // Y = B V (one warp per row, lanes over columns)
+  // one Rayleigh-Ritz step with matrix A on span(V): V <- Ritz vectors,
+  // Y <- A V, H diagonal <- Ritz values (descending); returns the relative
+  // residual max_{j<2} ||A v_j - h_j v_j|| / |h_0|
+  auto rayleigh_ritz = [&](const double *__restrict__ A) -> double {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = warp; r < k; r += nwarp) {
+    for (int r = warp; r < k; r += nwarp) {  // Y = A V, one warp per row
       double acc[kEigP];
 #pragma unroll
       for (int q = 0; q < kEigP; ++q) acc[q] = 0.0;
-      const double *brow = B + (size_t)r * k;
+      const double *arow = A + (size_t)r * k;
       for (int c = lane; c < k; c += 32) {
-        const double bv = __ldg(brow + c);
+        const double av = __ldg(arow + c);
 #pragma unroll
         for (int q = 0; q < kEigP; ++q)
-          if (q < P) acc[q] += bv * V[c * P + q];
+          if (q < P) acc[q] += av * V[c * P + q];
       }
 #pragma unroll
       for (int q = 0; q < kEigP; ++q)
@@ -351,8 +394,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
           if (q < P) Y[r * P + q] = acc[q];
     }
     __syncthreads();
-    // H = V^T Y (symmetric P x P)
-    double h[kEigP * (kEigP + 1) / 2];
+    double h[kEigP * (kEigP + 1) / 2];  // H = V^T Y, upper triangle
 #pragma unroll
     for (int q = 0; q < kEigP * (kEigP + 1) / 2; ++q) h[q] = 0.0;
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
@@ -369,15 +411,13 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
       for (int i = 0; i < kEigP; ++i)
         for (int j = i; j < kEigP; ++j, ++q)
           if (j < P) {
-            // symmetrise V^T B V from both triangles' estimates
             H[i * P + j] = h[q];
             H[j * P + i] = h[q];
           }
       tiny_jacobi(P, H, Q);
     }
     __syncthreads();
-    // Ritz vectors W = V Q (into V) and B W = Y Q (into Y); residuals of the top two
-    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {  // W = V Q, A W = Y Q
       double wv[kEigP], yv[kEigP];
 #pragma unroll
       for (int j = 0; j < kEigP; ++j) {
@@ -404,15 +444,21 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
         res[j] += e * e;
       }
     block_sum<2>(res, scratch);
-    const double lam0 = fabs(H[0]);
-    if (threadIdx.x == 0) s_done = (sqrt(res[0]) <= tol * lam0 && sqrt(res[1]) <= tol * lam0) ? 1 : 0;
+    const double h0 = fabs(H[0]);
+    return h0 > 0.0 ? sqrt(fmax(res[0], res[1])) / h0 : 0.0;
+  };
+
+  int it = 0;
+  for (; it < maxit; ++it) {
+    const double r = rayleigh_ritz(M);
+    if (threadIdx.x == 0) s_done = r <= tol ? 1 : 0;
     __syncthreads();
     if (s_done) break;
-    // next basis: orthonormalised B W
-    for (int t = threadIdx.x; t < k * P; t += blockDim.x) V[t] = Y[t];
+    for (int t = threadIdx.x; t < k * P; t += blockDim.x) V[t] = Y[t];  // next basis: orthonormalised M W
     __syncthreads();
     orthonormalise(k, P, V, scratch, 0x9e37ull + (unsigned long long)it);
   }
+  const double last_res = rayleigh_ritz(B);
   // top-2 Ritz vectors are columns 0, 1 of V; sign: largest |entry| positive
   __shared__ int s_big[2];
   if (threadIdx.x < 2) {
@@ -452,6 +498,8 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
     if (eig_user) {
       eig_user[0] = out->lam[0];
       eig_user[1] = out->lam[1];
+      eig_user[2] = (double)it;
+      eig_user[3] = last_res;
     }
     if (!s_done || !(H[0] > 0.0)) dev_fail(status, SSM_E_NUMERIC);
   }
@@ -577,7 +625,7 @@ __global__ void k_rescale(int32_t n, T2 *__restrict__ pos, const double *__restr
 
 struct MdsWs {
   unsigned long long *Glo, *Ghi, *s;
-  double *B, *rowmean, *vv, *part, *scale;
+  double *B, *B2, *M, *bscale, *rowmean, *vv, *part, *scale;
   EigOut *eo;
   unsigned *done, *dmax;
 };
@@ -589,6 +637,9 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.Ghi = c.take<unsigned long long>(kk);
   w.s = c.take<unsigned long long>(k);
   w.B = c.take<double>(kk);
+  w.B2 = c.take<double>(kk);
+  w.M = c.take<double>(kk);
+  w.bscale = c.take<double>(1);
   w.rowmean = c.take<double>(k);
   w.vv = c.take<double>(2 * (size_t)k);
   w.part = c.take<double>(4096);
@@ -634,7 +685,11 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   const int P = std::min(kEigP, (int)k);
   const size_t esm = (2 * (size_t)k * P + kEigScratch) * sizeof(double);
   SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
+  k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
+  const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
+  k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B, w.bscale, w.B2);  // (B/max|B|)^2
+  k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B2, nullptr, w.M);   // (B/max|B|)^4
+  k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
   const int64_t cnt = (int64_t)k * n;
   k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);

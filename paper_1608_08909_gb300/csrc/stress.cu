@@ -143,11 +143,11 @@ struct StressWs {
   size_t bfs_bytes;
 };
 
-static size_t carve_stress(Carver &c, StressWs &w, int32_t n, int32_t S, int32_t nbatches) {
+static size_t carve_stress(Carver &c, StressWs &w, int32_t n, int64_t m2, int32_t S, int32_t nbatches) {
   w.src = c.take<int32_t>(S);
   w.dist = c.take<uint16_t>((size_t)S * n);
   w.part = c.take<double>(4 * (size_t)pair_blocks() * (size_t)nbatches);
-  w.bfs_bytes = msbfs_workspace(n, S);
+  w.bfs_bytes = msbfs_workspace(n, m2, S);
   w.bfs = c.take<char>(w.bfs_bytes);
   return c.size();
 }
@@ -164,22 +164,23 @@ static void stress_shape(int32_t n, int32_t nsources, int32_t *S, int32_t *nbatc
 
 }  // namespace ssm
 
-SSM_API size_t ssm_stress_workspace(int32_t n, int32_t nsources, int32_t ntargets) {
+SSM_API size_t ssm_stress_workspace(int32_t n, int64_t m, int32_t nsources, int32_t ntargets) {
   (void)ntargets;
-  if (n < 2 || nsources < 0) return 0;
+  if (n < 2 || m < 0 || nsources < 0) return 0;
   int32_t S, nb;
   ssm::stress_shape(n, nsources, &S, &nb);
   ssm::Carver c(nullptr, 0);
   ssm::StressWs w;
-  return ssm::carve_stress(c, w, n, S, nb);
+  return ssm::carve_stress(c, w, n, 2 * m, S, nb);
 }
 
-SSM_API int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const void *pos, int32_t precision,
+SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, const void *pos,
+                       int32_t precision,
                        int32_t nsources, int32_t ntargets, uint64_t seed, double *out, double *sums, int32_t *status,
                        void *ws, size_t ws_bytes, cudaStream_t s) {
   using namespace ssm;
-  if (n < 2 || !rowptr || !colidx || !pos || !out || !status || !ws)
-    return fail(SSM_E_ARG, "ssm_stress: null pointer or n < 2");
+  if (n < 2 || m < 0 || !rowptr || !colidx || !pos || !out || !status || !ws)
+    return fail(SSM_E_ARG, "ssm_stress: null pointer or bad size");
   if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_stress: precision must be 32 or 64");
   if (nsources < 0 || nsources > 65535 || (nsources > 0 && ntargets < 1))
     return fail(SSM_E_ARG, "ssm_stress: need 0 <= nsources <= 65535 and ntargets >= 1 when sampling");
@@ -188,12 +189,12 @@ SSM_API int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, 
   if ((int64_t)n * ((S + 31) / 32) >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_stress: n*ceil(S/32) too large");
   Carver c(ws, ws_bytes);
   StressWs w;
-  carve_stress(c, w, n, S, nb);
+  carve_stress(c, w, n, 2 * m, S, nb);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_stress: workspace %zu bytes, need %zu", ws_bytes, c.size());
   const int pb = pair_blocks();
   if (nsources > 0) {
     k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
-    int rc = launch_msbfs(n, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
+    int rc = launch_msbfs(n, 2 * m, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
     if (rc) return rc;
     if (precision == 64)
       k_pairs_sampled<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
@@ -205,7 +206,7 @@ SSM_API int ssm_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, 
     for (int b = 0; b < nb; ++b) {
       const int32_t base = b * S, B = std::min<int32_t>(S, n - base);
       k_batch_sources<<<std::max(1, (B + 255) / 256), 256, 0, s>>>(base, B, w.src);
-      int rc = launch_msbfs(n, rowptr, colidx, B, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
+      int rc = launch_msbfs(n, 2 * m, rowptr, colidx, B, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
       if (rc) return rc;
       double *part = w.part + 4 * (size_t)pb * b;
       if (precision == 64)

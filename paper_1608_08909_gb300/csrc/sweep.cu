@@ -44,7 +44,13 @@ constexpr int kChunk = 256;     // neighbours per chunk task
 constexpr size_t kSmemBudget = 200 * 1024;
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
-constexpr int kPrefetch = 16;  // pivots whose d words are loaded ahead
+#ifndef SSM_SWEEP_PREFETCH
+#define SSM_SWEEP_PREFETCH 8
+#endif
+#ifndef SSM_SWEEP_MIN_BLOCKS
+#define SSM_SWEEP_MIN_BLOCKS 4
+#endif
+constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
 constexpr unsigned long long kChunkWaitNs = 20000000ull;  // 20 ms
 
 struct SweepArgs {
@@ -175,10 +181,10 @@ __device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const i
 
 // ----------------------------------------------------------------- FP32
 template <bool VEC, bool SMEM>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
+__global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
                                                               float2 *__restrict__ pout) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float4 *pxy = reinterpret_cast<float4 *>(smem);       // (x, x, y, y) per pivot
+  float4 *pxy = reinterpret_cast<float4 *>(smem);       // (-x, -x, -y, -y) per pivot
   uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
   float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
   if (__ldcg(A.stop)) return;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f32(SweepArgs A, const 
     const float2 xy = pin[p];
     const int o = __ldg(A.cnt_off + a), e = __ldg(A.cnt_off + a + 1);
     const unsigned soff = 2u * (unsigned)o, dcap = 2u * (unsigned)(e - o) - 1u;  // D_a = 2 ecc_a + 1
-    pxy[a] = make_float4(xy.x, xy.x, xy.y, xy.y);
+    pxy[a] = make_float4(-xy.x, -xy.x, -xy.y, -xy.y);
     pidx[a] = make_uint2(tab0 + 4u * soff - 4u * 0x4B000000u, 0x4B000000u | dcap);
   }
   if (SMEM)
@@ -235,57 +241,74 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f32(SweepArgs A, const 
     const int b1 = live1 ? __ldg(A.rowptr + i0 + 1) : 0, e1 = live1 ? __ldg(A.rowptr + i0 + 2) : 0;
     const float2 xi2 = make_float2(x0.x, x1.x), yi2 = make_float2(x0.y, x1.y);
 
-    // pivot terms, a = 0..k-1; the d words of the next kPrefetch pivots are
-    // always in flight (one 32-bit load per lane per pivot)
-    float2 nx2 = make_float2(0.f, 0.f), ny2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
-    const uint16_t *row = A.dip + i0;
+    // pivot terms, a = 0..k-1.  The d words of the next kPrefetch pivots are
+    // always in flight; lanes past the last node read a valid row segment
+    // (clamped index) and discard it.  Per pivot with B = s u, W = B u r^2 the
+    // numerator gains W x_p + B (x_i - x_p); the two parts are summed apart
+    // (wx += W (-x_p), bx += B (x_i - x_p)) so that no sum cancels.
+    float2 wx2 = make_float2(0.f, 0.f), wy2 = make_float2(0.f, 0.f);
+    float2 bx2 = make_float2(0.f, 0.f), by2 = make_float2(0.f, 0.f);
+    float2 den2 = make_float2(0.f, 0.f);
+    const int ic = VEC ? min(i0, n - 2) : min(i0, n - 1);
+    const int ic1 = VEC ? ic + 1 : min(i0 + 1, n - 1);
+    const uint16_t *col0 = A.dip + ic, *col1 = A.dip + ic1;
+    const size_t stride = (size_t)n;
     auto load_pair = [&](int a) -> unsigned {
-      if (a >= k || !live0) return 0u;
-      const uint16_t *r = row + (size_t)a * n;
-      if (VEC) return __ldg(reinterpret_cast<const unsigned *>(r));
-      const unsigned lo = (unsigned)__ldg(r), hi = live1 ? (unsigned)__ldg(r + 1) : 0u;
-      return lo | (hi << 16);
+      if (VEC) return __ldg(reinterpret_cast<const unsigned *>(col0 + (size_t)a * stride));
+      return (unsigned)__ldg(col0 + (size_t)a * stride) | ((unsigned)__ldg(col1 + (size_t)a * stride) << 16);
+    };
+    auto pivot_term = [&](int a, unsigned pk) {
+      const float4 P = pxy[a];  // (-x, -x, -y, -y)
+      const uint2 I = pidx[a];
+      // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
+      const float f0 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
+      const float f1 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
+      const float c0 = fminf(f0, __uint_as_float(I.y)), c1 = fminf(f1, __uint_as_float(I.y));
+      float2 s2;
+      if (SMEM) {
+        s2.x = lds_f32(4u * __float_as_uint(c0) + I.x);
+        s2.y = lds_f32(4u * __float_as_uint(c1) + I.x);
+      } else {
+        const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
+        s2.x = __ldg(A.stab + soff + (__float_as_uint(c0) - 0x4B000000u));
+        s2.y = __ldg(A.stab + soff + (__float_as_uint(c1) - 0x4B000000u));
+      }
+      const float2 d2 = __fadd2_rn(make_float2(f0, f1), kMagic2);
+      const float2 dx2 = __fadd2_rn(xi2, make_float2(P.x, P.y));
+      const float2 dy2 = __fadd2_rn(yi2, make_float2(P.z, P.w));
+      float2 r2 = __ffma2_rn(dy2, dy2, __fmul2_rn(dx2, dx2));
+      r2 = make_float2(fmaxf(r2.x, kR2Floor), fmaxf(r2.y, kR2Floor));
+      // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
+      const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, make_float2(1e-36f, 1e-36f));
+      const float2 u2 = make_float2(rsqrt_approx(q2.x), rsqrt_approx(q2.y));
+      const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
+      const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
+      wx2 = __ffma2_rn(W2, make_float2(P.x, P.y), wx2);
+      wy2 = __ffma2_rn(W2, make_float2(P.z, P.w), wy2);
+      bx2 = __ffma2_rn(B2, dx2, bx2);
+      by2 = __ffma2_rn(B2, dy2, by2);
+      den2 = __fadd2_rn(den2, W2);
     };
     unsigned buf[kPrefetch];
+    int a0 = 0;
+    if (k >= 2 * kPrefetch) {
 #pragma unroll
-    for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(t);
-    for (int a0 = 0; a0 < k; a0 += kPrefetch) {
+      for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(t);
+      for (; a0 + 2 * kPrefetch <= k; a0 += kPrefetch) {
 #pragma unroll
-      for (int t = 0; t < kPrefetch; ++t) {
-        const int a = a0 + t;
-        const unsigned pk = buf[t];
-        buf[t] = load_pair(a + kPrefetch);
-        if (a >= k) break;
-        const float4 P = pxy[a];
-        const uint2 I = pidx[a];
-        // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
-        const float f0 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
-        const float f1 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
-        const float c0 = fminf(f0, __uint_as_float(I.y)), c1 = fminf(f1, __uint_as_float(I.y));
-        float2 s2;
-        if (SMEM) {
-          s2.x = lds_f32(4u * __float_as_uint(c0) + I.x);
-          s2.y = lds_f32(4u * __float_as_uint(c1) + I.x);
-        } else {
-          const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
-          s2.x = __ldg(A.stab + soff + (__float_as_uint(c0) - 0x4B000000u));
-          s2.y = __ldg(A.stab + soff + (__float_as_uint(c1) - 0x4B000000u));
+        for (int t = 0; t < kPrefetch; ++t) {
+          const unsigned pk = buf[t];
+          buf[t] = load_pair(a0 + kPrefetch + t);
+          pivot_term(a0 + t, pk);
         }
-        const float2 d2 = __fadd2_rn(make_float2(f0, f1), kMagic2);
-        const float2 dx2 = __fadd2_rn(xi2, make_float2(-P.x, -P.y));
-        const float2 dy2 = __fadd2_rn(yi2, make_float2(-P.z, -P.w));
-        float2 r2 = __ffma2_rn(dy2, dy2, __fmul2_rn(dx2, dx2));
-        r2 = make_float2(fmaxf(r2.x, kR2Floor), fmaxf(r2.y, kR2Floor));
-        // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
-        const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, make_float2(1e-36f, 1e-36f));
-        const float2 u2 = make_float2(rsqrt_approx(q2.x), rsqrt_approx(q2.y));
-        const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
-        const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
-        nx2 = __ffma2_rn(B2, dx2, __ffma2_rn(W2, make_float2(P.x, P.y), nx2));
-        ny2 = __ffma2_rn(B2, dy2, __ffma2_rn(W2, make_float2(P.z, P.w), ny2));
-        den2 = __fadd2_rn(den2, W2);
       }
+#pragma unroll
+      for (int t = 0; t < kPrefetch; ++t) pivot_term(a0 + t, buf[t]);
+      a0 += kPrefetch;
     }
+    for (; a0 < k; ++a0) pivot_term(a0, load_pair(a0));
+    const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
+    const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
 
     // neighbour terms (w = 1, d = 1)
     float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;

@@ -36,16 +36,16 @@ def test_status_strings_and_workspace_queries():
     assert L.ssm_status_string(-3) == b"graph is disconnected"
     assert L.ssm_iterate_workspace(1000, 2000, 50, 600, 32) > 8000
     assert L.ssm_iterate_workspace(1000, 2000, 50, 600, 64) > 8000
-    assert L.ssm_pivot_bfs_workspace(1000, 64) >= L.ssm_pivot_bfs_workspace(1000, 32) > 0
+    assert L.ssm_pivot_bfs_workspace(1000, 2000, 64) >= L.ssm_pivot_bfs_workspace(1000, 2000, 32) > 0
     assert L.ssm_build_graph_workspace(0, 5) == 0
 
 
 @pytest.mark.parametrize("call", [
-    lambda L: L.ssm_select_pivots(10, None, None, 3, 0, None, None, None, 0, None),
-    lambda L: L.ssm_pivot_bfs(10, None, None, 3, None, None, None, None, 0, None),
+    lambda L: L.ssm_select_pivots(10, 9, None, None, 3, 0, None, None, None, 0, None),
+    lambda L: L.ssm_pivot_bfs(10, 9, None, None, 3, None, None, None, None, 0, None),
     lambda L: L.ssm_iterate(10, 9, None, None, 3, None, None, None, None, 3, None, 32, 1, 0.0, None, None, None,
                             None, 0, None),
-    lambda L: L.ssm_stress(1, None, None, None, 32, 0, 0, 0, None, None, None, None, 0, None),
+    lambda L: L.ssm_stress(1, 0, None, None, None, 32, 0, 0, 0, None, None, None, None, 0, None),
     lambda L: L.ssm_pivotmds(10, None, None, 1, None, None, 32, 0, None, None, None, 0, None),
 ])
 def test_bad_arguments_rejected_on_host(call):
