@@ -122,6 +122,28 @@ int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, in
                   uint32_t *cnt, int64_t cnt_len, int32_t *status,
                   void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* ssm_aggregate without any workspace, for callers that cannot allocate
+ * device memory: for example a serving process that reserved its whole device
+ * memory budget up front and admits work against it byte by byte, or code
+ * that runs where the CUDA allocator must not be entered (a host callback, a
+ * library whose memory comes from another allocator).  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ * Same results as ssm_aggregate.  Its scratch (one word per pivot) is a fixed
+ * array in device memory that every GPU loading the library keeps until the
+ * process exits, so it handles at most 4096 pivots (SSM_E_ARG beyond).  The
+ * first call on each device looks up that array's address, with the device
+ * current; make that first call before capturing the stream into a CUDA graph.
+ * All calls share the array: calls that overlap on the GPU (other streams or
+ * other threads) race and must be serialised by the caller.
+ * Synchronous: computes region[n] and the table length, stores the length in
+ * *cnt_len (host), and returns SSM_E_NOMEM if it exceeds cnt_cap (cnt untouched;
+ * call again with cnt of that size, cnt may be NULL when cnt_cap is 0);
+ * otherwise fills cnt_off[k+1] and cnt[*cnt_len] as ssm_aggregate does.
+ * Calls no allocating function of CUDA or of any other library. */
+int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *cnt_off,
+                          uint32_t *cnt, int64_t cnt_cap, int64_t *cnt_len, int32_t *status,
+                          cudaStream_t stream);
+
 /* ---------------------------------------------------------------------
  * Initial layout (Algorithm 1 lines 3-4): PivotMDS over the k pivots
  * (Brandes and Pich 2007), then, if rescale != 0, a uniform scale so that the

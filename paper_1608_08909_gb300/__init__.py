@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
-    "ssm_aggregate", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -65,6 +65,7 @@ def lib():
                 "ssm_aggregate_workspace": (sz, [i32]),
                 "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
+                "ssm_aggregate_noalloc": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
@@ -201,6 +202,20 @@ def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, ch
     if check:
         ssm_check(st, "ssm_aggregate", stream)
     return region, off, cnt
+
+
+def ssm_aggregate_noalloc(dip: torch.Tensor, region: torch.Tensor, cnt_off: torch.Tensor, cnt: torch.Tensor | None,
+                          status: torch.Tensor, stream=None) -> int:
+    """ssm_aggregate into caller buffers with no workspace (the library allocates
+    nothing).  Returns the table length; raises SSMError (code -5) if cnt is
+    missing or too small for it."""
+    L = lib()
+    k, n = dip.shape
+    cap = 0 if cnt is None else cnt.numel()
+    out = ctypes.c_int64(0)
+    _rc(L.ssm_aggregate_noalloc(n, k, _ptr(dip), _ptr(region), _ptr(cnt_off), _ptr(cnt), cap, ctypes.byref(out),
+                                _ptr(status), _stream(stream)), "ssm_aggregate_noalloc")
+    return int(out.value)
 
 
 def ssm_pivotmds(g: Graph, dip: torch.Tensor, precision: int = 32, rescale: bool = True, stream=None,

@@ -5,6 +5,8 @@
 //   cnt[cnt_off[a] + t] = |{ i in R(a) : d_ia <= t }|.
 // The sweep then reads s = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)]
 // instead of a stored k x n weight table.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ssm {
@@ -139,6 +141,68 @@ SSM_API int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *re
   k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
   k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
   k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+// ---------------------------------------------------------------- without allocation
+// Scratch of ssm_aggregate_noalloc: one eccentricity per pivot and the table
+// length, in a fixed device array (every GPU that loads the library holds one
+// copy until the process exits).  Host code must not use the array's name as
+// a device address; it asks the runtime for the address once per device.
+namespace ssm {
+constexpr int kNoAllocMaxPivots = 4096;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned g_agg_scratch[kNoAllocMaxPivots + 4];
+static std::mutex g_agg_mutex;
+static void *g_agg_addr[kNoAllocMaxDevices];
+
+// device address of g_agg_scratch on the current device (looked up on the
+// first call for that device, with that device current)
+static int agg_scratch(unsigned **out) {
+  int dev = 0;
+  SSM_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SSM_E_ARG, "ssm_aggregate_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_agg_mutex);
+  if (!g_agg_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_agg_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "ssm_aggregate_noalloc: cudaGetSymbolAddress");
+    g_agg_addr[dev] = p;
+  }
+  *out = static_cast<unsigned *>(g_agg_addr[dev]);
+  return SSM_OK;
+}
+}  // namespace ssm
+
+SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *cnt_off,
+                                  uint32_t *cnt, int64_t cnt_cap, int64_t *cnt_len, int32_t *status,
+                                  cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || !dip || !region || !cnt_off || !cnt_len || !status || cnt_cap < 0 || (cnt_cap > 0 && !cnt))
+    return fail(SSM_E_ARG, "ssm_aggregate_noalloc: null pointer or bad size");
+  if (k < 1 || k > kNoAllocMaxPivots)
+    return fail(SSM_E_ARG, "ssm_aggregate_noalloc: k = %d, this entry point handles 1 <= k <= %d pivots", k,
+                kNoAllocMaxPivots);
+  unsigned *ecc = nullptr;
+  int rc = agg_scratch(&ecc);
+  if (rc) return rc;
+  long long *len = reinterpret_cast<long long *>(ecc + kNoAllocMaxPivots);
+  SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
+  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
+  long long h = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  *cnt_len = h;
+  if (h > cnt_cap)
+    return fail(SSM_E_NOMEM, "ssm_aggregate_noalloc: the count table needs %lld entries, cnt holds %lld", h,
+                (long long)cnt_cap);
+  if (h >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_aggregate_noalloc: table length must be below 2^31");
+  SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)h * sizeof(uint32_t), s));
+  k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, h, status);
+  k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, h, cnt);
+  k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, h, cnt);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
