@@ -49,6 +49,20 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _captured_traffic(workload: str):
+    """DRAM bytes per sweep launch from the committed ncu capture, or None if
+    there is none for this workload or the kernel source changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"sweep_{workload}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = os.path.join(ROOT, "paper_1608_08909_gb300", "csrc", "sweep.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec.get("dram_bytes_per_launch") if rec.get("sweep_cu_sha256") == digest else None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -227,10 +241,7 @@ def run_gpu(args):
     bytes_per_launch = 2 * k * n + 4 * (n + 1) + 8 * m + 8 * n + 8 * n
     launch_s = (sum(sweep_ms) / 1e3) / (args.steps * iters)
     achieved = bytes_per_launch / launch_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"sweep_{args.workload}_traffic.json")
-    if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get("dram_bytes_per_launch")
+    traffic = _captured_traffic(args.workload)
 
     result = {
         "metric": "sparse-stress node-updates/s",

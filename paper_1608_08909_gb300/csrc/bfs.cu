@@ -19,6 +19,106 @@ constexpr int kBfsThreads = 512;
 constexpr unsigned kInf = 0xFFFFFFFFu;
 
 // --------------------------------------------------------------------------
+// one BFS level expanded by one block
+// --------------------------------------------------------------------------
+constexpr int kFlatChunk = 2048;  // frontier nodes whose degree prefix sits in shared memory
+constexpr int kFlatU = 8;         // adjacency loads in flight per thread
+
+struct FlatSmem {
+  unsigned pref[kFlatChunk + 1];  // exclusive prefix of the chunk's degrees
+  int rb[kFlatChunk];             // row begin of each chunk node
+  unsigned warp_tot[32];
+  unsigned total;
+};
+
+// exclusive prefix of v over the block (blockDim.x <= 1024); the block total lands in S.total
+__device__ __forceinline__ unsigned block_scan_excl(unsigned v, FlatSmem &S) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = (blockDim.x + 31u) >> 5;
+  unsigned incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += t;
+  }
+  if (lane == 31) S.warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned w = lane < nw ? S.warp_tot[lane] : 0u;
+    unsigned wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= (unsigned)o) wi += t;
+    }
+    if (lane < nw) S.warp_tot[lane] = wi - w;
+    if (lane == 31) S.total = wi;
+  }
+  __syncthreads();
+  return incl - v + S.warp_tot[warp];
+}
+
+// One BFS level by one block.  fr(i) gives the row range of frontier node i
+// (i < cc).  The frontier is taken in chunks of kFlatChunk nodes: a prefix of
+// their degrees goes to shared memory, then all edge slots of the chunk are
+// spread evenly over the block's threads, kFlatU independent 16-byte
+// adjacency loads in flight per thread (one latency per kFlatU slots, not one
+// per 32-slot round of a warp).  gather(e) claims neighbour e.x and returns
+// whether it is new; emit(e, claimed) runs for every slot with the whole
+// warp converged (appends use warp ballots).  Every thread of the block must
+// call this with the same cc.
+template <class Fr, class Gather, class Emit>
+__device__ void block_expand_level(Fr &&fr, unsigned cc, const int4 *__restrict__ adj, FlatSmem &S, Gather &&gather,
+                                   Emit &&emit) {
+  const unsigned tid = threadIdx.x, nth = blockDim.x;
+  for (unsigned c0 = 0; c0 < cc; c0 += kFlatChunk) {
+    const unsigned cn = min((unsigned)kFlatChunk, cc - c0);
+    const unsigned per = (cn + nth - 1) / nth;  // <= kFlatChunk / 32
+    unsigned mine = 0;
+    for (unsigned j = 0; j < per; ++j) {
+      const unsigned i = tid * per + j;
+      if (i < cn) {
+        const int2 r = fr(c0 + i);
+        S.rb[i] = r.x;
+        mine += (unsigned)(r.y - r.x);
+      }
+    }
+    unsigned off = block_scan_excl(mine, S);
+    for (unsigned j = 0; j < per; ++j) {
+      const unsigned i = tid * per + j;
+      if (i < cn) {
+        S.pref[i] = off;
+        off += (unsigned)(fr(c0 + i).y - S.rb[i]);
+      }
+    }
+    if (tid == 0) S.pref[cn] = S.total;
+    __syncthreads();
+    const unsigned E = S.pref[cn];
+    for (unsigned base = 0; base < E; base += nth * kFlatU) {
+      int4 e[kFlatU];
+      bool act[kFlatU];
+#pragma unroll
+      for (int u = 0; u < kFlatU; ++u) {
+        const unsigned t = base + (unsigned)u * nth + tid;
+        act[u] = t < E;
+        e[u] = make_int4(0, 0, 0, 0);
+        if (act[u]) {
+          unsigned lo = 0;  // largest i with pref[i] <= t
+#pragma unroll
+          for (unsigned step = kFlatChunk / 2; step > 0; step >>= 1)
+            if (lo + step <= cn && S.pref[lo + step] <= t) lo += step;
+          e[u] = __ldg(adj + S.rb[lo] + (int)(t - S.pref[lo]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kFlatU; ++u) act[u] = act[u] && gather(e[u]);
+#pragma unroll
+      for (int u = 0; u < kFlatU; ++u) emit(e[u], act[u]);
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
 // max/min sp
 // --------------------------------------------------------------------------
 constexpr int kSoloMax = 2048;       // frontiers up to this size are expanded by block 0 alone
@@ -47,8 +147,8 @@ struct MaxMinArgs {
 // Every new frontier is also written to the global queue, so the grid can
 // take over when it grows.  Returns with qcnt and *level describing the
 // frontier it stopped at.
-__device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*sq)[kSoloMax], unsigned *s_cnt) {
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+__device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*sq)[kSoloMax], unsigned *s_cnt,
+                            FlatSmem &S) {
   const unsigned *qin0 = (L & 1) ? A.q1 : A.q0;
   for (unsigned e = threadIdx.x; e < c; e += blockDim.x) {
     const unsigned u = __ldcg(qin0 + e);
@@ -66,20 +166,17 @@ __device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*
     const int nxt = cur ^ 1;
     unsigned *qout = ((L + 1) & 1) ? A.q1 : A.q0;
     const unsigned nd = L + 1;
-    for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
-      const unsigned e = base + lane;
-      const int2 r = e < cc ? sq[cur][e] : make_int2(0, 0);
-      warp_for_each_edge4_batched<8>(
-          r.x, r.y, A.adj, [&](int, int4 ed) { return atomicMin(A.mind + ed.x, nd) > nd; },
-          [&](int, int4 ed, bool push) {
-            const unsigned pos = warp_slot(push, s_cnt + nxt);
-            if (push) {
-              qout[pos] = (unsigned)ed.x;
-              if (pos < (unsigned)kSoloMax) sq[nxt][pos] = make_int2(ed.y, ed.z);
-            }
-          });
-    }
-    __syncthreads();
+    const int2 *fr = sq[cur];
+    block_expand_level(
+        [&](unsigned i) { return fr[i]; }, cc, A.adj, S,
+        [&](int4 ed) { return atomicMin(A.mind + ed.x, nd) > nd; },
+        [&](int4 ed, bool push) {
+          const unsigned pos = warp_slot(push, s_cnt + nxt);
+          if (push) {
+            qout[pos] = (unsigned)ed.x;
+            if (pos < (unsigned)kSoloMax) sq[nxt][pos] = make_int2(ed.y, ed.z);
+          }
+        });
     if (threadIdx.x == 0) s_cnt[cur] = 0;
     __syncthreads();
     cur = nxt;
@@ -99,7 +196,9 @@ __device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*
 // mind is reached along a shortest path of such nodes, so the result is
 // exactly mind = min(mind, d(p, .)).
 __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
-  __shared__ int2 sq[2][kSoloMax];
+  extern __shared__ __align__(16) unsigned char mm_smem[];
+  int2 (*sq)[kSoloMax] = reinterpret_cast<int2 (*)[kSoloMax]>(mm_smem);
+  FlatSmem &S = *reinterpret_cast<FlatSmem *>(mm_smem + sizeof(int2) * 2 * kSoloMax);
   __shared__ unsigned s_cnt[2];
   const unsigned nthreads = gridDim.x * blockDim.x;
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -128,7 +227,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
       const unsigned c = __ldcg(A.qcnt + L % 3);
       if (c == 0) break;
       if (c <= (unsigned)kSoloMax) {
-        if (blockIdx.x == 0) maxmin_solo(A, L, c, sq, s_cnt);
+        if (blockIdx.x == 0) maxmin_solo(A, L, c, sq, s_cnt, S);
         if (!grid_barrier(A.bar, A.status)) return;
         L = __ldcg(A.level);
         continue;
@@ -221,10 +320,12 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
-  const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, 0, 1);
+  const size_t smem = sizeof(int2) * 2 * kSoloMax + sizeof(FlatSmem);
+  SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_maxmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, smem, 1);
   if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: kernel cannot be resident");
   void *args[] = {&A};
-  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_maxmin, dim3(blocks), dim3(kBfsThreads), args, 0, s));
+  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_maxmin, dim3(blocks), dim3(kBfsThreads), args, smem, s));
   return SSM_OK;
 }
 
@@ -247,6 +348,7 @@ size_t maxmin_workspace(int32_t n, int64_t m2) {
 constexpr int kCtaThreads = 512;
 constexpr int kCtaSlotsPerSm = 2;
 constexpr size_t kCtaBitmapMax = 200 * 1024;  // bytes of shared memory for the visited bitmap
+constexpr size_t kAdj4MaxBytes = 48u << 20;     // expanded adjacency kept only while it fits well inside L2
 
 struct CtaBfsArgs {
   int32_t n;
@@ -265,6 +367,7 @@ struct CtaBfsArgs {
 // (claimed with shared atomicOr), whose frontier holds the row ranges of the
 // nodes (fetched when a node is appended) and whose levels are separated by
 // __syncthreads.  Appends are compacted with warp ballots.
+template <bool ADJ4>
 __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
   extern __shared__ unsigned vis[];
   __shared__ unsigned s_cnt[2];
@@ -301,20 +404,37 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
       for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
         const unsigned e = base + lane;
         const int2 r = e < cc ? __ldcg(qin + e) : make_int2(0, 0);
-        warp_for_each_edge4_batched<4>(
-            r.x, r.y, A.adj,
-            [&](int, int4 ed) {
-              const unsigned bit = 1u << ((unsigned)ed.x & 31u);
-              unsigned *wp = vis + ((unsigned)ed.x >> 5);
-              return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
-            },
-            [&](int, int4 ed, bool push) {
-              const unsigned pos = warp_slot(push, s_cnt + nxt);
-              if (push) {
-                row[ed.x] = nd;
-                qout[pos] = make_int2(ed.y, ed.z);
-              }
-            });
+        if (ADJ4) {
+          warp_for_each_edge4_batched<4>(
+              r.x, r.y, A.adj,
+              [&](int, int4 ed) {
+                const unsigned bit = 1u << ((unsigned)ed.x & 31u);
+                unsigned *wp = vis + ((unsigned)ed.x >> 5);
+                return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
+              },
+              [&](int, int4 ed, bool push) {
+                const unsigned pos = warp_slot(push, s_cnt + nxt);
+                if (push) {
+                  row[ed.x] = nd;
+                  qout[pos] = make_int2(ed.y, ed.z);
+                }
+              });
+        } else {
+          warp_for_each_neighbor_batched<4>(
+              r.x, r.y, A.colidx,
+              [&](int, int, int v) {
+                const unsigned bit = 1u << ((unsigned)v & 31u);
+                unsigned *wp = vis + ((unsigned)v >> 5);
+                return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
+              },
+              [&](int, int, int v, bool push) {
+                const unsigned pos = warp_slot(push, s_cnt + nxt);
+                if (push) {
+                  row[v] = nd;
+                  qout[pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
+                }
+              });
+        }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -491,13 +611,19 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     B.adj = adj;
     B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
     if (!c.ok) return fail(SSM_E_NOMEM, "BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
-    int rc = expand_adj(m2, rowptr, colidx, adj, s);
-    if (rc) return rc;
+    // the 16-byte expanded adjacency saves a dependent load per level but
+    // quadruples adjacency traffic: use it only while it stays L2-resident
+    const bool adj4 = (size_t)m2 * sizeof(int4) <= kAdj4MaxBytes;
+    if (adj4) {
+      int rc = expand_adj(m2, rowptr, colidx, adj, s);
+      if (rc) return rc;
+    }
+    const void *kern = adj4 ? (const void *)k_bfs_cta<true> : (const void *)k_bfs_cta<false>;
     const size_t smem = (size_t)((n + 31) / 32) * 4;
-    SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_bfs_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
-    k_bfs_cta<<<slots, kCtaThreads, smem, s>>>(B);
-    SSM_TRY_CUDA(cudaGetLastError());
+    void *args[] = {&B};
+    SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(slots), dim3(kCtaThreads), args, smem, s));
     return SSM_OK;
   }
   MsBfsArgs A;

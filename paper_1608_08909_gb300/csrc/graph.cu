@@ -1,6 +1,6 @@
 // Graph construction (Section 1: a simple undirected graph G = (V, E)):
 // edge list -> CSR with both directions, rows sorted ascending, self-loops and
-// repeated edges dropped, followed by a connectivity check (one BFS).
+// repeated edges dropped, followed by a connectivity check (union-find).
 //
 //   count degrees (atomics) -> exclusive scan -> scatter both directions
 //   -> sort every row (warp bitonic in registers for rows <= 32, block bitonic
@@ -142,13 +142,56 @@ __global__ void k_compact(int32_t n, int64_t total, const int *__restrict__ off,
     rowptr[row] = pos[off[row]];
 }
 
+// ---- connectivity by union-find (no per-level latency): every input edge
+// links the root with the larger id under the one with the smaller id by
+// compare-and-swap; afterwards the graph is connected iff exactly one node is
+// its own root.
+__device__ __forceinline__ int uf_find(int *parent, int x) {
+  int p = __ldcg(parent + x);
+  while (p != x) {
+    const int gp = __ldcg(parent + p);
+    if (gp != p) atomicCAS(parent + x, p, gp);  // path halving (only ever shortens)
+    x = p;
+    p = __ldcg(parent + x);
+  }
+  return x;
+}
+
+__global__ void k_uf_init(int32_t n, int *__restrict__ parent) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    parent[i] = (int)i;
+}
+
+// one thread per input edge (balanced whatever the degrees); self-loops and
+// repeated edges are harmless
+__global__ void k_uf_link(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int *parent) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    int a = uf_find(parent, __ldg(src + e)), b = uf_find(parent, __ldg(dst + e));
+    while (a != b) {
+      if (a > b) { const int t2 = a; a = b; b = t2; }
+      const int old = atomicCAS(parent + b, b, a);  // b is a root: hang it under a
+      if (old == b) break;
+      a = uf_find(parent, a);
+      b = uf_find(parent, old);
+    }
+  }
+}
+
+__global__ void k_uf_roots(int32_t n, const int *__restrict__ parent, unsigned *__restrict__ roots) {
+  unsigned c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += (__ldcg(parent + i) == (int)i);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(roots, c);
+}
+
 struct BuildWs {
   int *deg, *off, *cursor, *flag, *pos, *tiles;
   int32_t *tmp;
   unsigned *big_rows, *big_count;
   int32_t *status;
-  void *bfs_ws;
-  size_t bfs_bytes;
+  int *parent;
+  unsigned *roots;
 };
 
 static size_t carve_build(Carver &c, BuildWs &w, int32_t n, int64_t m_in) {
@@ -164,8 +207,8 @@ static size_t carve_build(Carver &c, BuildWs &w, int32_t n, int64_t m_in) {
   w.big_rows = c.take<unsigned>(n);
   w.big_count = c.take<unsigned>(1);
   w.status = c.take<int32_t>(2);
-  w.bfs_bytes = maxmin_workspace(n, 2 * m_in);
-  w.bfs_ws = c.take<char>(w.bfs_bytes);
+  w.parent = c.take<int>(n);
+  w.roots = c.take<unsigned>(1);
   return c.size();
 }
 
@@ -217,11 +260,14 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   SSM_TRY_CUDA(cudaMemcpyAsync(&uniq, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
   *m_out = uniq / 2;
-  // connectivity: one BFS from node 0 over the final CSR (status[1] receives its pivot slot)
-  rc = launch_maxmin(n, (int64_t)uniq, rowptr, colidx, 1, 0, w.status + 1, w.status, w.bfs_ws, w.bfs_bytes, s);
-  if (rc) return rc;
-  SSM_TRY_CUDA(cudaMemcpyAsync(&hstatus, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  // connectivity: union-find over the final CSR
+  SSM_TRY_CUDA(cudaMemsetAsync(w.roots, 0, sizeof(unsigned), s));
+  k_uf_init<<<nblocks, 256, 0, s>>>(n, w.parent);
+  k_uf_link<<<eblocks, 256, 0, s>>>(m_in, src, dst, w.parent);
+  k_uf_roots<<<nblocks, 256, 0, s>>>(n, w.parent, w.roots);
+  unsigned roots = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&roots, w.roots, sizeof roots, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
-  if (hstatus) return fail(hstatus, "ssm_build_graph: %s", ssm_status_string(hstatus));
+  if (roots != 1) return fail(SSM_E_DISCONNECTED, "ssm_build_graph: %u connected components", roots);
   return SSM_OK;
 }

@@ -12,15 +12,16 @@
 //
 // FP32 kernel, GB300 layout:
 //  * a lane owns two consecutive nodes; their d_ia for one pivot arrive in one
-//    32-bit load, so a warp streams a contiguous 128-byte segment of the
-//    pivot-major d_ip row per pivot;
+//    32-bit load.  ssm_iterate first re-lays d_ip into 64-node tiles
+//    ([tile][pivot][64 nodes]), so a warp streams one contiguous block per tile,
+//    a 128-byte row per pivot at a fixed stride (no per-load address arithmetic);
 //  * the pivot term is evaluated for the node pair with packed FP32x2
 //    arithmetic and one rsqrt per node: with q = d^2 r^2, u = q^{-1/2},
 //    B = s u = w d / r and W = B u r^2 = s / d^2 = w, the term adds
 //    W x_p + B (x_i - x_p) to the numerator and W to the denominator;
-//    r^2 is floored at 1e-24 so coincident points (r == 0) add w x_p, as
-//    the r == 0 rule says, and q gets + 1e-36 so it stays positive at d = 0
-//    (relative change of a valid term below 1e-12);
+//    r^2 gets + 1e-24 so coincident points (r == 0) add w x_p, as the r == 0
+//    rule says, and q gets + 1e-36 so it stays positive at d = 0 (relative
+//    change of a term with r >= 1e-6 below 1e-12);
 //  * s comes from a per-pivot table indexed directly by d (0 for d < 2,
 //    cnt[min(d/2, ecc)] up to d = 2 ecc + 1, then |R(a)|), held in shared
 //    memory with the pivot positions and loaded once per persistent block;
@@ -48,7 +49,7 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_PREFETCH 8
 #endif
 #ifndef SSM_SWEEP_MIN_BLOCKS
-#define SSM_SWEEP_MIN_BLOCKS 4
+#define SSM_SWEEP_MIN_BLOCKS 3
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
 constexpr unsigned long long kChunkWaitNs = 20000000ull;  // 20 ms
@@ -57,6 +58,7 @@ struct SweepArgs {
   int32_t n, k;
   const int32_t *rowptr, *colidx, *pivots, *cnt_off;
   const uint16_t *dip;
+  const unsigned *dtile;  // d_ip re-laid as [tile][pivot][32 words of two nodes] (64-node tiles)
   const uint32_t *cnt;
   int32_t cnt_len;
   int32_t stab_len;       // 2 * cnt_len
@@ -180,7 +182,7 @@ __device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const i
 }
 
 // ----------------------------------------------------------------- FP32
-template <bool VEC, bool SMEM>
+template <bool SMEM>
 __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
                                                               float2 *__restrict__ pout) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -208,7 +210,10 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
   const unsigned lane = threadIdx.x & 31u;
   const unsigned ntiles = (unsigned)((n + 63) / 64);
   const unsigned nchunks = (unsigned)__ldg(A.cfirst + n);
-  const float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
+  // loop-invariant constant pairs, kept in registers (opaque to the compiler so
+  // it does not rebuild them from immediates inside the pivot loop)
+  float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
+  asm volatile("" : "+f"(kMagic2.x), "+f"(kMagic2.y));
   for (;;) {
     unsigned task = 0;
     if (lane == 0) task = atomicAdd(A.tile_ctr, 1u);
@@ -249,42 +254,43 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
     float2 wx2 = make_float2(0.f, 0.f), wy2 = make_float2(0.f, 0.f);
     float2 bx2 = make_float2(0.f, 0.f), by2 = make_float2(0.f, 0.f);
     float2 den2 = make_float2(0.f, 0.f);
-    const int ic = VEC ? min(i0, n - 2) : min(i0, n - 1);
-    const int ic1 = VEC ? ic + 1 : min(i0 + 1, n - 1);
-    const uint16_t *col0 = A.dip + ic, *col1 = A.dip + ic1;
-    const size_t stride = (size_t)n;
-    auto load_pair = [&](int a) -> unsigned {
-      if (VEC) return __ldg(reinterpret_cast<const unsigned *>(col0 + (size_t)a * stride));
-      return (unsigned)__ldg(col0 + (size_t)a * stride) | ((unsigned)__ldg(col1 + (size_t)a * stride) << 16);
-    };
+    // this tile's d words: pivot a of lane l at tp[a * 32] (one contiguous 128-byte row per pivot)
+    const unsigned *tp = A.dtile + (size_t)tile * (size_t)k * 32u + lane;
+    auto load_pair = [&](int a) -> unsigned { return __ldg(tp + (unsigned)a * 32u); };
+    float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
+    asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
     auto pivot_term = [&](int a, unsigned pk) {
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
       const uint2 I = pidx[a];
       // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
-      const float f0 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
-      const float f1 = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
-      const float c0 = fminf(f0, __uint_as_float(I.y)), c1 = fminf(f1, __uint_as_float(I.y));
+      float2 f2;
+      f2.x = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
+      f2.y = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
+      const float cap = __uint_as_float(I.y);
       float2 s2;
       if (SMEM) {
-        s2.x = lds_f32(4u * __float_as_uint(c0) + I.x);
-        s2.y = lds_f32(4u * __float_as_uint(c1) + I.x);
+        s2.x = lds_f32(4u * __float_as_uint(fminf(f2.x, cap)) + I.x);
+        s2.y = lds_f32(4u * __float_as_uint(fminf(f2.y, cap)) + I.x);
       } else {
         const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
-        s2.x = __ldg(A.stab + soff + (__float_as_uint(c0) - 0x4B000000u));
-        s2.y = __ldg(A.stab + soff + (__float_as_uint(c1) - 0x4B000000u));
+        s2.x = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.x, cap)) - 0x4B000000u));
+        s2.y = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.y, cap)) - 0x4B000000u));
       }
-      const float2 d2 = __fadd2_rn(make_float2(f0, f1), kMagic2);
-      const float2 dx2 = __fadd2_rn(xi2, make_float2(P.x, P.y));
-      const float2 dy2 = __fadd2_rn(yi2, make_float2(P.z, P.w));
-      float2 r2 = __ffma2_rn(dy2, dy2, __fmul2_rn(dx2, dx2));
-      r2 = make_float2(fmaxf(r2.x, kR2Floor), fmaxf(r2.y, kR2Floor));
+      const float2 d2 = __fadd2_rn(f2, kMagic2);
+      const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
+      const float2 dx2 = __fadd2_rn(xi2, px2);
+      const float2 dy2 = __fadd2_rn(yi2, py2);
+      // r^2 + 1e-24: coincident points (r == 0) add w x_p only, as the r == 0 rule says
+      const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
       // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
-      const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, make_float2(1e-36f, 1e-36f));
-      const float2 u2 = make_float2(rsqrt_approx(q2.x), rsqrt_approx(q2.y));
+      const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, kTinyQ2);
+      float2 u2;
+      u2.x = rsqrt_approx(q2.x);
+      u2.y = rsqrt_approx(q2.y);
       const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
       const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
-      wx2 = __ffma2_rn(W2, make_float2(P.x, P.y), wx2);
-      wy2 = __ffma2_rn(W2, make_float2(P.z, P.w), wy2);
+      wx2 = __ffma2_rn(W2, px2, wx2);
+      wy2 = __ffma2_rn(W2, py2, wy2);
       bx2 = __ffma2_rn(B2, dx2, bx2);
       by2 = __ffma2_rn(B2, dy2, by2);
       den2 = __fadd2_rn(den2, W2);
@@ -377,6 +383,24 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
 }
 
 // ----------------------------------------------------------------- setup (once per ssm_iterate)
+// dtile[(t * k + a) * 32 + l] = d_ip[a][64t + 2l] | d_ip[a][64t + 2l + 1] << 16 (0 past the last node)
+__global__ void k_tile_dip(int32_t n, int32_t k, const uint16_t *__restrict__ dip, unsigned *__restrict__ dtile) {
+  const int64_t ntiles = (n + 63) / 64;
+  const int64_t total = ntiles * (int64_t)k * 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(w & 31);
+    const int64_t ta = w >> 5;
+    const int a = (int)(ta % k);
+    const int64_t t = ta / k;
+    const int64_t i = t * 64 + 2 * l;
+    const uint16_t *row = dip + (size_t)a * n;
+    const unsigned lo = i < n ? (unsigned)__ldg(row + i) : 0u;
+    const unsigned hi = i + 1 < n ? (unsigned)__ldg(row + i + 1) : 0u;
+    dtile[w] = lo | (hi << 16);
+  }
+}
+
+
 // s-by-d table: stab[2 off_a + d] = (d >= 2) ? cnt[off_a + min(d/2, ecc_a)] : 0, d = 0..2 ecc_a + 1
 __global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, const uint32_t *__restrict__ cnt,
                              float *__restrict__ stab) {
@@ -517,12 +541,14 @@ struct IterWs {
   float2 *cpart;
   unsigned *cflag;
   int *tiles;     // scan workspace
+  unsigned *dtile;
 };
 
 // a row of deg > kChunkDeg yields ceil(deg / kChunk) <= 0.0116 deg chunks, below deg / 64
 static size_t max_chunks(int64_t m2) { return (size_t)(m2 / 64 + 1); }
 
-static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int64_t cnt_len, int32_t precision) {
+static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t k, int64_t cnt_len,
+                            int32_t precision) {
   const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
   w.tmp = c.take<char>((size_t)n * elem);
   w.ctr = c.take<unsigned>(2);
@@ -536,17 +562,17 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int64_t
   w.cpart = c.take<float2>(mc);
   w.cflag = c.take<unsigned>(mc);
   w.tiles = c.take<int>((size_t)scan_tiles(n) + 1);
+  w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + 63) / 64) * (size_t)k * 32);
   return c.size();
 }
 
 }  // namespace ssm
 
 SSM_API size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision) {
-  (void)k;
-  if (n < 1 || m < 0 || cnt_len < 0) return 0;
+  if (n < 1 || m < 0 || k < 1 || cnt_len < 0) return 0;
   ssm::Carver c(nullptr, 0);
   ssm::IterWs w;
-  return ssm::carve_iterate(c, w, n, 2 * m, cnt_len, precision);
+  return ssm::carve_iterate(c, w, n, 2 * m, k, cnt_len, precision);
 }
 
 SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
@@ -564,12 +590,12 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   if (cnt_len < k || cnt_len >= ((int64_t)1 << 30)) return fail(SSM_E_ARG, "ssm_iterate: bad count-table length");
   Carver c(ws, ws_bytes);
   IterWs w;
-  carve_iterate(c, w, n, 2 * m, cnt_len, precision);
+  carve_iterate(c, w, n, 2 * m, k, cnt_len, precision);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_iterate: workspace %zu bytes, need %zu", ws_bytes, c.size());
 
   SweepArgs A;
   A.n = n; A.k = k; A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.cnt_off = cnt_off;
-  A.dip = dip; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
+  A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
   A.stab = w.stab; A.cfirst = w.cfirst; A.cnode = w.cnode; A.cpart = w.cpart; A.cflag = w.cflag; A.stamp = 0;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
   A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol; A.status = status;
@@ -584,7 +610,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   const void *kern;
   size_t smem;
   int64_t tiles;
-  bool vec = (n % 2) == 0, tsm = true;
+  bool tsm = true;
   if (precision == 64) {
     const size_t piv = (size_t)k * sizeof(PivD), tab = (size_t)cnt_len * sizeof(double);
     tsm = piv + tab <= kSmemBudget;
@@ -593,6 +619,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     tiles = (n + 31) / 32;
   } else {
     k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
+    k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, dip, w.dtile);
     k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
     int rc = exclusive_scan(w.nch, w.cfirst, n, w.tiles, s);
     if (rc) return rc;
@@ -601,8 +628,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2)), tab = (size_t)(2 * cnt_len) * sizeof(float);
     tsm = piv + tab <= kSmemBudget;
     smem = piv + (tsm ? tab : 0);
-    kern = vec ? (tsm ? (const void *)k_sweep_f32<true, true> : (const void *)k_sweep_f32<true, false>)
-               : (tsm ? (const void *)k_sweep_f32<false, true> : (const void *)k_sweep_f32<false, false>);
+    kern = tsm ? (const void *)k_sweep_f32<true> : (const void *)k_sweep_f32<false>;
     tiles = (n + 63) / 64;
   }
   SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
