@@ -49,18 +49,25 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _captured_traffic(workload: str):
-    """DRAM bytes per sweep launch from the committed ncu capture, or None if
-    there is none for this workload or the kernel source changed since."""
+def _kernel_sources_digest() -> str:
+    """sha256 over the sources the sweep kernel is compiled from."""
     import hashlib
 
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1608_08909_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _captured_traffic(workload: str):
+    """DRAM bytes per sweep launch from the committed ncu capture, or None if
+    there is none for this workload or the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", f"sweep_{workload}_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    src = os.path.join(ROOT, "paper_1608_08909_gb300", "csrc", "sweep.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return rec.get("dram_bytes_per_launch") if rec.get("sweep_cu_sha256") == digest else None
+    ok = rec.get("kernel_sources_sha256") == _kernel_sources_digest()
+    return rec.get("dram_bytes_per_launch") if ok else None
 
 
 class ClockSampler:
@@ -118,14 +125,6 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def launches_per_step(iters: int, exhaustive_batches: int) -> int:
-    """Kernels of this library launched by one step (memsets not counted):
-    build graph 13 (degree count, 2 scans of 3, scatter, 2 row sorts, flags,
-    compaction, connectivity BFS), pivots 1, d_ip BFS 1, aggregate size 2,
-    aggregate 4, PivotMDS 8, sweeps iters + 1 copy-back, stress 2 + 3 per batch."""
-    return 13 + 1 + 1 + 2 + 4 + 8 + (iters + 1) + 1 + 3 * exhaustive_batches
-
-
 def run_gpu(args):
     import numpy as np
     import torch
@@ -181,7 +180,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     m = g.m
     terms_per_step = iters * (k * n + 2 * m)
-    batches = 0 if S > 0 else (n + 1023) // 1024
 
     for _ in range(args.warmup):
         step(src_d, dst_d)
@@ -192,6 +190,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = ssm.kernel_launches()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -202,6 +201,7 @@ def run_gpu(args):
             for i, st in enumerate(STAGES):
                 stage_ms[st] += ev[i].elapsed_time(ev[i + 1]) / args.steps
             sweep_ms.append(ev[5].elapsed_time(ev[6]))
+    timed_launches = ssm.kernel_launches() - launches0
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -282,7 +282,7 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "node-term updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
-        "gpu_launches": launches_per_step(iters, batches) * args.steps,
+        "gpu_launches": timed_launches,
         "stress_normalized": float(out.cpu()[3]),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -60,6 +60,12 @@ const char *ssm_status_string(int code);
  * storage valid until the next failing call on the same thread). */
 const char *ssm_last_error(void);
 
+/* Number of kernels this library has enqueued since it was loaded, over all
+ * host threads and devices (memsets and copies are not counted).  A
+ * diagnostic with no counterpart in the paper: a caller reads it before and
+ * after a sequence of calls to learn how many kernels the sequence issued. */
+unsigned long long ssm_kernel_launches(void);
+
 /* Synchronous: waits for `stream`, then returns the device status word
  * (SSM_OK if it is 0), or SSM_E_CUDA if the stream reported a CUDA error. */
 int ssm_check(const int32_t *status, cudaStream_t stream);

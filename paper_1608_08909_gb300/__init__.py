@@ -55,6 +55,7 @@ def lib():
             sig = {
                 "ssm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
                 "ssm_last_error": (ctypes.c_char_p, []),
+                "ssm_kernel_launches": (ctypes.c_ulonglong, []),
                 "ssm_check": (ctypes.c_int, [v, v]),
                 "ssm_build_graph_workspace": (sz, [i32, i64]),
                 "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, sz, v]),
@@ -79,6 +80,11 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels the library has enqueued since it was loaded (ssm_kernel_launches)."""
+    return int(lib().ssm_kernel_launches())
 
 
 def _require_cuda():

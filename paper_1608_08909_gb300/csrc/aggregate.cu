@@ -116,8 +116,8 @@ SSM_API int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_
   long long *len = c.take<long long>(1);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate_size: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
-  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc);
-  k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc);
+  note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
   long long h = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
@@ -137,10 +137,10 @@ SSM_API int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *re
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)cnt_len * sizeof(uint32_t), s));
-  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
-  k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
-  k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
-  k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
+  note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
+  note_launch(), k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
@@ -189,8 +189,8 @@ SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int
   if (rc) return rc;
   long long *len = reinterpret_cast<long long *>(ecc + kNoAllocMaxPivots);
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
-  k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
-  k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
   long long h = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
@@ -200,9 +200,9 @@ SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int
                 (long long)cnt_cap);
   if (h >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_aggregate_noalloc: table length must be below 2^31");
   SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)h * sizeof(uint32_t), s));
-  k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, h, status);
-  k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, h, cnt);
-  k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, h, cnt);
+  note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, h, status);
+  note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, h, cnt);
+  note_launch(), k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, h, cnt);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }

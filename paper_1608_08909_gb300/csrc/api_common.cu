@@ -2,11 +2,16 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace ssm {
 
 static thread_local char g_last_error[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int fail(int code, const char *fmt, ...) {
   va_list ap;
@@ -53,6 +58,8 @@ SSM_API const char *ssm_status_string(int code) {
 }
 
 SSM_API const char *ssm_last_error(void) { return ssm::g_last_error; }
+
+SSM_API unsigned long long ssm_kernel_launches(void) { return ssm::g_launches.load(std::memory_order_relaxed); }
 
 SSM_API int ssm_check(const int32_t *status, cudaStream_t stream) {
   int32_t h = 0;

@@ -294,7 +294,7 @@ __global__ void k_expand_adj(int64_t m2, const int32_t *__restrict__ rowptr, con
 static int expand_adj(int64_t m2, const int32_t *rowptr, const int32_t *colidx, int4 *adj, cudaStream_t s) {
   if (m2 <= 0) return SSM_OK;
   const int blocks = (int)std::min<int64_t>((m2 + 255) / 256, (int64_t)num_sms() * 8);
-  k_expand_adj<<<blocks, 256, 0, s>>>(m2, rowptr, colidx, adj);
+  note_launch(), k_expand_adj<<<blocks, 256, 0, s>>>(m2, rowptr, colidx, adj);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
@@ -325,6 +325,7 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, smem, 1);
   if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: kernel cannot be resident");
   void *args[] = {&A};
+  note_launch();
   SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_maxmin, dim3(blocks), dim3(kBfsThreads), args, smem, s));
   return SSM_OK;
 }
@@ -623,6 +624,7 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
     void *args[] = {&B};
+    note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(slots), dim3(kCtaThreads), args, smem, s));
     return SSM_OK;
   }
@@ -642,6 +644,7 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
   const int blocks = cooperative_blocks((const void *)k_msbfs, kBfsThreads, 0, 2);
   if (blocks < 1) return fail(SSM_E_CUDA, "multi-source BFS: kernel cannot be resident");
   void *args[] = {&A};
+  note_launch();
   SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs, dim3(blocks), dim3(kBfsThreads), args, 0, s));
   return SSM_OK;
 }

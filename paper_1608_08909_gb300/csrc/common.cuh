@@ -15,6 +15,10 @@ namespace ssm {
 int fail(int code, const char *fmt, ...);          // records ssm_last_error, returns code
 int cuda_status(cudaError_t e, const char *what);  // SSM_OK or SSM_E_CUDA (recorded)
 int num_sms();                                     // SM count of the current device
+// Counts one kernel enqueued by this library; every launch site calls it just
+// before its launch ("note_launch(), k<<<...>>>(...)" keeps if/else one-liners
+// single expressions).  ssm_kernel_launches() reports the running total.
+void note_launch();
 #define SSM_TRY_CUDA(call)                                  \
   do {                                                      \
     cudaError_t e_ = (call);                                \

@@ -238,13 +238,13 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   SSM_TRY_CUDA(cudaMemsetAsync(w.cursor, 0, (size_t)n * sizeof(int), s));
   SSM_TRY_CUDA(cudaMemsetAsync(w.big_count, 0, sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(w.status, 0, 2 * sizeof(int32_t), s));
-  k_count_degrees<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.deg, w.status);
+  note_launch(), k_count_degrees<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.deg, w.status);
   int rc = exclusive_scan(w.deg, w.off, n, w.tiles, s);
   if (rc) return rc;
-  k_scatter<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.off, w.cursor, w.tmp);
-  k_sort_small_rows<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.big_rows, w.big_count);
-  k_sort_big_rows<<<sms * 2, kSortBlock, 0, s>>>(w.off, w.tmp, w.big_rows, w.big_count);
-  k_flag_unique<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.flag);
+  note_launch(), k_scatter<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.off, w.cursor, w.tmp);
+  note_launch(), k_sort_small_rows<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.big_rows, w.big_count);
+  note_launch(), k_sort_big_rows<<<sms * 2, kSortBlock, 0, s>>>(w.off, w.tmp, w.big_rows, w.big_count);
+  note_launch(), k_flag_unique<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.flag);
   // total directed entries before dedupe = off[n]; read it to size the scan
   int total = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&total, w.off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -254,7 +254,7 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   if (hstatus) return fail(hstatus, "ssm_build_graph: %s", ssm_status_string(hstatus));
   rc = exclusive_scan(w.flag, w.pos, total, w.tiles, s);
   if (rc) return rc;
-  k_compact<<<std::max(eblocks, nblocks), 256, 0, s>>>(n, total, w.off, w.tmp, w.flag, w.pos, rowptr, colidx);
+  note_launch(), k_compact<<<std::max(eblocks, nblocks), 256, 0, s>>>(n, total, w.off, w.tmp, w.flag, w.pos, rowptr, colidx);
   SSM_TRY_CUDA(cudaGetLastError());
   int32_t uniq = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&uniq, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -262,9 +262,9 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   *m_out = uniq / 2;
   // connectivity: union-find over the final CSR
   SSM_TRY_CUDA(cudaMemsetAsync(w.roots, 0, sizeof(unsigned), s));
-  k_uf_init<<<nblocks, 256, 0, s>>>(n, w.parent);
-  k_uf_link<<<eblocks, 256, 0, s>>>(m_in, src, dst, w.parent);
-  k_uf_roots<<<nblocks, 256, 0, s>>>(n, w.parent, w.roots);
+  note_launch(), k_uf_init<<<nblocks, 256, 0, s>>>(n, w.parent);
+  note_launch(), k_uf_link<<<eblocks, 256, 0, s>>>(m_in, src, dst, w.parent);
+  note_launch(), k_uf_roots<<<nblocks, 256, 0, s>>>(n, w.parent, w.roots);
   unsigned roots = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&roots, w.roots, sizeof roots, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));

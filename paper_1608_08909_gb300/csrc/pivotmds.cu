@@ -679,30 +679,30 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   SSM_TRY_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), s));
   const int T = (k + kGT - 1) / kGT;
   dim3 ggrid((unsigned)(T * (T + 1) / 2), (unsigned)((n + kGChunk - 1) / kGChunk));
-  k_gram<<<ggrid, 256, 0, s>>>(n, k, dip, w.Glo, w.Ghi);
-  k_colsum<<<std::min(k, sms * 4), 256, 0, s>>>(n, k, dip, w.s);
-  k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
+  note_launch(), k_gram<<<ggrid, 256, 0, s>>>(n, k, dip, w.Glo, w.Ghi);
+  note_launch(), k_colsum<<<std::min(k, sms * 4), 256, 0, s>>>(n, k, dip, w.s);
+  note_launch(), k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
   const int P = std::min(kEigP, (int)k);
   const size_t esm = (2 * (size_t)k * P + kEigScratch) * sizeof(double);
   SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
+  note_launch(), k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
   const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
-  k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B, w.bscale, w.B2);  // (B/max|B|)^2
-  k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B2, nullptr, w.M);   // (B/max|B|)^4
-  k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
+  note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B, w.bscale, w.B2);  // (B/max|B|)^2
+  note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B2, nullptr, w.M);   // (B/max|B|)^4
+  note_launch(), k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
   const int64_t cnt = (int64_t)k * n;
-  k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
+  note_launch(), k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   const size_t psm = (size_t)k * sizeof(float4);
-  k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);
+  note_launch(), k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);
   if (rescale) {
     const int eb = std::min(pb, 4096);
     if (precision == 64) {
-      k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, w.part, w.done, w.scale, status);
-      k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
+      note_launch(), k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, w.part, w.done, w.scale, status);
+      note_launch(), k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
     } else {
-      k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, w.part, w.done, w.scale, status);
-      k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
+      note_launch(), k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, w.part, w.done, w.scale, status);
+      note_launch(), k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
     }
   }
   SSM_TRY_CUDA(cudaGetLastError());

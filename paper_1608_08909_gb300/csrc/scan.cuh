@@ -93,9 +93,9 @@ static inline int exclusive_scan(const int *in, int *out, int64_t count, int *ti
     SSM_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
     return SSM_OK;
   }
-  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, tile_ws, count);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(tile_ws, tiles, out + count);
-  k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, tile_ws, count);
+  note_launch(), k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, tile_ws, count);
+  note_launch(), k_scan_sums<<<1, kScanThreads, 0, s>>>(tile_ws, tiles, out + count);
+  note_launch(), k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, tile_ws, count);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }

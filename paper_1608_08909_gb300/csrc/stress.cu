@@ -193,31 +193,31 @@ SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_stress: workspace %zu bytes, need %zu", ws_bytes, c.size());
   const int pb = pair_blocks();
   if (nsources > 0) {
-    k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
+    note_launch(), k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
     int rc = launch_msbfs(n, 2 * m, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
     if (rc) return rc;
     if (precision == 64)
-      k_pairs_sampled<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+      note_launch(), k_pairs_sampled<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
                                                            (const double2 *)pos, w.part, status);
     else
-      k_pairs_sampled<float2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+      note_launch(), k_pairs_sampled<float2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
                                                           (const float2 *)pos, w.part, status);
   } else {
     for (int b = 0; b < nb; ++b) {
       const int32_t base = b * S, B = std::min<int32_t>(S, n - base);
-      k_batch_sources<<<std::max(1, (B + 255) / 256), 256, 0, s>>>(base, B, w.src);
+      note_launch(), k_batch_sources<<<std::max(1, (B + 255) / 256), 256, 0, s>>>(base, B, w.src);
       int rc = launch_msbfs(n, 2 * m, rowptr, colidx, B, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
       if (rc) return rc;
       double *part = w.part + 4 * (size_t)pb * b;
       if (precision == 64)
-        k_pairs_exhaustive<double2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const double2 *)pos, part,
+        note_launch(), k_pairs_exhaustive<double2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const double2 *)pos, part,
                                                                 status);
       else
-        k_pairs_exhaustive<float2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const float2 *)pos, part,
+        note_launch(), k_pairs_exhaustive<float2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const float2 *)pos, part,
                                                                status);
     }
   }
-  k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);
+  note_launch(), k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }

@@ -618,12 +618,12 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     kern = tsm ? (const void *)k_sweep_f64<true> : (const void *)k_sweep_f64<false>;
     tiles = (n + 31) / 32;
   } else {
-    k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
-    k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, dip, w.dtile);
-    k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
+    note_launch(), k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
+    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, dip, w.dtile);
+    note_launch(), k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
     int rc = exclusive_scan(w.nch, w.cfirst, n, w.tiles, s);
     if (rc) return rc;
-    k_chunk_nodes<<<nb, 256, 0, s>>>(n, w.cfirst, w.cnode);
+    note_launch(), k_chunk_nodes<<<nb, 256, 0, s>>>(n, w.cfirst, w.cnode);
     SSM_TRY_CUDA(cudaMemsetAsync(w.cflag, 0, max_chunks(2 * m) * sizeof(unsigned), s));
     const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2)), tab = (size_t)(2 * cnt_len) * sizeof(float);
     tsm = piv + tab <= kSmemBudget;
@@ -643,13 +643,14 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     A.stamp = (unsigned)t + 1u;
     void *pin = even ? pos : w.tmp, *pout = even ? w.tmp : pos;
     void *args[] = {&A, &pin, &pout};
+    note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(blocks), dim3(kSweepThreads), args, smem, s));
   }
   const int cb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   if (precision == 64)
-    k_copy_back_if_odd<double2><<<cb, 256, 0, s>>>(n, iters_done, (const double2 *)w.tmp, (double2 *)pos);
+    note_launch(), k_copy_back_if_odd<double2><<<cb, 256, 0, s>>>(n, iters_done, (const double2 *)w.tmp, (double2 *)pos);
   else
-    k_copy_back_if_odd<float2><<<cb, 256, 0, s>>>(n, iters_done, (const float2 *)w.tmp, (float2 *)pos);
+    note_launch(), k_copy_back_if_odd<float2><<<cb, 256, 0, s>>>(n, iters_done, (const float2 *)w.tmp, (float2 *)pos);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
