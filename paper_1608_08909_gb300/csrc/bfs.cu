@@ -299,14 +299,8 @@ static int expand_adj(int64_t m2, const int32_t *rowptr, const int32_t *colidx, 
   return SSM_OK;
 }
 
-int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
-                  int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
-  Carver c(ws, ws_bytes);
-  MaxMinArgs A;
-  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
-  A.pivots = pivots; A.status = status;
-  int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
-  A.adj = adj;
+static void carve_maxmin(Carver &c, MaxMinArgs &A, unsigned **spill, int32_t n, int64_t m2) {
+  A.adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
   A.mind = c.take<unsigned>(n);
   A.q0 = c.take<unsigned>(n);
   A.q1 = c.take<unsigned>(n);
@@ -314,9 +308,23 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   A.level = c.take<unsigned>(1);
   A.best = c.take<unsigned long long>(2);
   A.bar = c.take<BarrierState>(1);
+  *spill = c.take<unsigned>(std::max<size_t>(1, maxmin_cluster_spill_entries(n)));
+}
+
+int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+                  int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Carver c(ws, ws_bytes);
+  MaxMinArgs A;
+  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
+  A.pivots = pivots; A.status = status;
+  unsigned *spill = nullptr;
+  carve_maxmin(c, A, &spill, n, m2);
   if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
-  int rc = expand_adj(m2, rowptr, colidx, adj, s);
+  int rc = expand_adj(m2, rowptr, colidx, const_cast<int4 *>(A.adj), s);
   if (rc) return rc;
+  bool launched = false;
+  rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, s, &launched);
+  if (rc || launched) return rc;
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
@@ -332,14 +340,9 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
 
 size_t maxmin_workspace(int32_t n, int64_t m2) {
   Carver c(nullptr, 0);
-  c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
-  c.take<unsigned>(n);
-  c.take<unsigned>(n);
-  c.take<unsigned>(n);
-  c.take<unsigned>(4);
-  c.take<unsigned>(1);
-  c.take<unsigned long long>(2);
-  c.take<BarrierState>(1);
+  MaxMinArgs A;
+  unsigned *spill;
+  carve_maxmin(c, A, &spill, n, m2);
   return c.size();
 }
 

@@ -109,6 +109,51 @@ def test_select_pivots_k_equals_n():
     assert sorted(got.tolist()) == list(range(n))
 
 
+def test_select_pivots_tiny_graphs():
+    for n in (2, 3, 5):
+        n_, s, d = I.path(n)
+        og = O.build_csr(n_, s, d)
+        g = _gpu_graph(n_, s, d)
+        got = ssm.ssm_select_pivots(g, n_, n_ - 1).cpu().numpy()
+        assert np.array_equal(got, O.maxmin(og, n_, n_ - 1))
+
+
+def test_select_pivots_long_path():
+    # 20000 BFS levels per pivot
+    n, s, d = I.path(20000)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 6, 777).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, 6, 777))
+
+
+@pytest.mark.parametrize("start", [0, 5])
+def test_select_pivots_star_frontier_overflow(start):
+    # one BFS level of 300000 nodes: more than the shared-memory queues of the
+    # cluster kernel hold, so most of the level goes through the global spill
+    n = 300001
+    s = np.zeros(n - 1, np.int32)
+    d = np.arange(1, n, dtype=np.int32)
+    # a short tail so the pivots are not all leaves of the star
+    s = np.concatenate([s, np.array([7, 300001, 300002], np.int32)])
+    d = np.concatenate([d, np.array([300001, 300002, 300003], np.int32)])
+    n += 3
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 5, start).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, 5, start))
+
+
+def test_select_pivots_large_grid_kernel():
+    # 720000 nodes: mind does not fit the cluster's shared memory, so the
+    # cooperative grid kernel runs
+    n, s, d = I.grid(900, 800)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 6, 12345).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, 6, 12345))
+
+
 # ------------------------------------------------------------------ a2 d_ip
 
 @pytest.mark.parametrize("name,k", [("grid32", 50), ("path", 7), ("btree", 33), ("rgg", 100), ("ba", 64),
