@@ -15,16 +15,23 @@
 //    32-bit load.  ssm_iterate first re-lays d_ip into 64-node tiles
 //    ([tile][pivot][64 nodes]), so a warp streams one contiguous block per tile,
 //    a 128-byte row per pivot at a fixed stride (no per-load address arithmetic);
-//  * the pivot term is evaluated for the node pair with packed FP32x2
-//    arithmetic and one rsqrt per node: with q = d^2 r^2, u = q^{-1/2},
-//    B = s u = w d / r and W = B u r^2 = s / d^2 = w, the term adds
+//  * full-table mode (graphs whose largest d_ip fits a k x (dmax+1) table in
+//    shared memory, e.g. small-world graphs): the table holds (w, w d) for
+//    every pivot and distance, w = s / d^2, so a term is one table gather, one
+//    rsqrt (u = 1/r) and B = (w d) u = w d / r; it adds w x_p + B (x_i - x_p)
+//    to the numerator.  The denominator deg(i) + sum_a w'_ia does not change
+//    between iterations and is summed once per ssm_iterate call;
+//  * clamped mode (large distances): s comes from a per-pivot table indexed
+//    directly by d (0 for d < 2, cnt[min(d/2, ecc)] up to d = 2 ecc + 1, then
+//    |R(a)|), and the term uses one rsqrt per node: with q = d^2 r^2,
+//    u = q^{-1/2}, B = s u = w d / r and W = B u r^2 = s / d^2 = w, it adds
 //    W x_p + B (x_i - x_p) to the numerator and W to the denominator;
-//    r^2 gets + 1e-24 so coincident points (r == 0) add w x_p, as the r == 0
-//    rule says, and q gets + 1e-36 so it stays positive at d = 0 (relative
-//    change of a term with r >= 1e-6 below 1e-12);
-//  * s comes from a per-pivot table indexed directly by d (0 for d < 2,
-//    cnt[min(d/2, ecc)] up to d = 2 ecc + 1, then |R(a)|), held in shared
-//    memory with the pivot positions and loaded once per persistent block;
+//  * in both modes the node pair is evaluated with packed FP32x2 arithmetic
+//    where the operands pair up naturally; r^2 gets + 1e-24 so coincident
+//    points (r == 0) add w x_p, as the r == 0 rule says (the clamped mode
+//    also adds 1e-36 to q so it stays positive at d = 0; relative change of a
+//    term with r >= 1e-6 below 1e-12); tables and pivot positions sit in
+//    shared memory, loaded once per persistent block;
 //  * warps take 64-node tiles from an atomic counter; rows longer than
 //    kChunkDeg are cut into kChunk-neighbour tasks handed out first, whose
 //    partial sums the owning tile adds in chunk order (results do not depend
@@ -43,6 +50,7 @@ constexpr int kLightDeg = 32;   // rows up to this length: one lane walks the ro
 constexpr int kChunkDeg = 128;  // rows longer than this: cut into chunk tasks
 constexpr int kChunk = 256;     // neighbours per chunk task
 constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kFullTabMax = 48 * 1024;  // bytes of the (w, w d) table of the full-table mode
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
 #ifndef SSM_SWEEP_PREFETCH
@@ -50,6 +58,9 @@ constexpr float kR2Floor = 1e-24f;
 #endif
 #ifndef SSM_SWEEP_MIN_BLOCKS
 #define SSM_SWEEP_MIN_BLOCKS 3
+#endif
+#ifndef SSM_SWEEP_FULL_MIN_BLOCKS
+#define SSM_SWEEP_FULL_MIN_BLOCKS 3
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
 constexpr unsigned long long kChunkWaitNs = 20000000ull;  // 20 ms
@@ -63,6 +74,9 @@ struct SweepArgs {
   int32_t cnt_len;
   int32_t stab_len;       // 2 * cnt_len
   const float *stab;      // [stab_len] s by d, per pivot (global copy)
+  const float2 *wtab;     // [k][dmax+1] (w, w d) by pivot and distance (full-table mode)
+  int32_t dmax;           // largest d_ip entry (full-table mode)
+  const float *den;       // [n] deg(i) + sum_a w'_ia (full-table mode)
   const int32_t *cfirst;  // [n+1] first chunk task of each node; cfirst[n] = chunks
   const int32_t *cnode;   // [chunks] node of each chunk task
   float2 *cpart;          // [chunks] neighbour partial sums
@@ -182,13 +196,25 @@ __device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const i
 }
 
 // ----------------------------------------------------------------- FP32
-template <bool SMEM>
-__global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
+__device__ __forceinline__ float2 lds_f32x2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+
+// MODE: kClampSmem / kClampGlobal (s table in shared / global memory), kFull
+constexpr int kClampSmem = 0, kClampGlobal = 1, kFull = 2;
+
+template <int MODE>
+__global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_BLOCKS : SSM_SWEEP_MIN_BLOCKS) k_sweep_f32(SweepArgs A, const float2 *__restrict__ pin,
                                                               float2 *__restrict__ pout) {
+  constexpr bool SMEM = MODE == kClampSmem;
+  constexpr bool FULL = MODE == kFull;
   extern __shared__ __align__(16) unsigned char smem[];
   float4 *pxy = reinterpret_cast<float4 *>(smem);       // (-x, -x, -y, -y) per pivot
   uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
   float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
+  float2 *wtab = reinterpret_cast<float2 *>(pidx + A.k);  // full-table mode: (w, w d) by pivot and d
   if (__ldcg(A.stop)) return;
   const int n = A.n, k = A.k;
   // Table address of node distance d for pivot a: with c = bits(2^23 + min(d, D_a))
@@ -205,6 +231,10 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
   }
   if (SMEM)
     for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
+  const unsigned wrow = 8u * (unsigned)(A.dmax + 1);  // bytes of one pivot's (w, w d) row
+  if (FULL)
+    for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) wtab[t] = __ldg(A.wtab + t);
+  const unsigned wtab0 = FULL ? (unsigned)__cvta_generic_to_shared(wtab) : 0u;
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
@@ -259,7 +289,32 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
     auto load_pair = [&](int a) -> unsigned { return __ldg(tp + (unsigned)a * 32u); };
     float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
     asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
+    // full-table mode accumulators, per node (lo, hi)
+    float wxl = 0.f, wxh = 0.f, wyl = 0.f, wyh = 0.f, bxl = 0.f, bxh = 0.f, byl = 0.f, byh = 0.f;
+    auto pivot_term_full = [&](int a, unsigned pk) {
+      const float4 P = pxy[a];  // (-x, -x, -y, -y)
+      const unsigned tb = wtab0 + (unsigned)a * wrow;
+      const float2 tl = lds_f32x2(tb + 8u * (pk & 0xFFFFu));  // (w, w d) of the even node
+      const float2 th = lds_f32x2(tb + 8u * (pk >> 16));      // and of the odd node
+      const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
+      const float2 dx2 = __fadd2_rn(xi2, px2);
+      const float2 dy2 = __fadd2_rn(yi2, py2);
+      const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
+      const float bl = tl.y * rsqrt_approx(r2.x), bh = th.y * rsqrt_approx(r2.y);  // w d / r
+      wxl = fmaf(tl.x, P.x, wxl);
+      wxh = fmaf(th.x, P.x, wxh);
+      wyl = fmaf(tl.x, P.z, wyl);
+      wyh = fmaf(th.x, P.z, wyh);
+      bxl = fmaf(bl, dx2.x, bxl);
+      bxh = fmaf(bh, dx2.y, bxh);
+      byl = fmaf(bl, dy2.x, byl);
+      byh = fmaf(bh, dy2.y, byh);
+    };
     auto pivot_term = [&](int a, unsigned pk) {
+      if constexpr (FULL) {
+        pivot_term_full(a, pk);
+        return;
+      }
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
       const uint2 I = pidx[a];
       // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
@@ -313,6 +368,13 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
       a0 += kPrefetch;
     }
     for (; a0 < k; ++a0) pivot_term(a0, load_pair(a0));
+    if constexpr (FULL) {
+      bx2 = make_float2(bxl, bxh);
+      by2 = make_float2(byl, byh);
+      wx2 = make_float2(wxl, wxh);
+      wy2 = make_float2(wyl, wyh);
+      den2 = make_float2(live0 ? __ldg(A.den + i0) : 0.f, live1 ? __ldg(A.den + i0 + 1) : 0.f);
+    }
     const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
     const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
 
@@ -356,9 +418,11 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
 
     // X^{t+1} and this tile's share of the relative change
     float cn = 0.f, cd = 0.f;
-    if ((live0 && !(den2.x == den2.x)) || (live1 && !(den2.y == den2.y))) dev_fail(A.status, SSM_E_NUMERIC);
+    // a NaN (clamped mode: in the weights; full-table mode: in the numerator) is an error
+    const float2 chk = FULL ? __fadd2_rn(nx2, ny2) : den2;
+    if ((live0 && !(chk.x == chk.x)) || (live1 && !(chk.y == chk.y))) dev_fail(A.status, SSM_E_NUMERIC);
     if (live0) {
-      const float dn = den2.x + (float)deg0;
+      const float dn = FULL ? den2.x : den2.x + (float)deg0;
       const float xn = dn > 0.f ? (nx2.x + sx0) / dn : x0.x, yn = dn > 0.f ? (ny2.x + sy0) / dn : x0.y;
       pout[i0] = make_float2(xn, yn);
       const float ex = xn - x0.x, ey = yn - x0.y;
@@ -366,7 +430,7 @@ __global__ void __launch_bounds__(kSweepThreads, SSM_SWEEP_MIN_BLOCKS) k_sweep_f
       cd = fmaf(x0.x, x0.x, x0.y * x0.y);
     }
     if (live1) {
-      const float dn = den2.y + (float)deg1;
+      const float dn = FULL ? den2.y : den2.y + (float)deg1;
       const float xn = dn > 0.f ? (nx2.y + sx1) / dn : x1.x, yn = dn > 0.f ? (ny2.y + sy1) / dn : x1.y;
       pout[i0 + 1] = make_float2(xn, yn);
       const float ex = xn - x1.x, ey = yn - x1.y;
@@ -409,6 +473,54 @@ __global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, con
     for (int d = threadIdx.x; d <= 2 * ecc + 1; d += blockDim.x)
       stab[2 * o + d] = d >= 2 ? (float)cnt[o + min(d >> 1, ecc)] : 0.f;
   }
+}
+
+// full-table mode: wtab[a (dmax+1) + d] = (w, w d), w = s / d^2 with s as in
+// k_build_stab (0 for d < 2), rounded from double
+__global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict__ cnt_off,
+                             const uint32_t *__restrict__ cnt, float2 *__restrict__ wtab) {
+  const int64_t total = (int64_t)k * (dmax + 1);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / (dmax + 1)), d = (int)(t - (int64_t)a * (dmax + 1));
+    const int o = cnt_off[a], ecc = cnt_off[a + 1] - o - 1;
+    float2 e = make_float2(0.f, 0.f);
+    if (d >= 2) {
+      const double sd = (double)cnt[o + min(d >> 1, ecc)], dd = (double)d;
+      e = make_float2((float)(sd / (dd * dd)), (float)(sd / dd));
+    }
+    wtab[t] = e;
+  }
+}
+
+// full-table mode: den[i] = deg(i) + sum_{a = 0..k-1} w'_ia in FP32, pivots in
+// order (the sum the clamped mode forms inside every sweep)
+__global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *__restrict__ dtile,
+                            const float2 *__restrict__ wtab, const int32_t *__restrict__ rowptr,
+                            float *__restrict__ den) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t ntiles = (n + 63) / 64;
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles;
+       tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const unsigned *tp = dtile + tile * (int64_t)k * 32 + lane;
+    float dl = 0.f, dh = 0.f;
+    for (int a = 0; a < k; ++a) {
+      const unsigned pk = __ldg(tp + (int64_t)a * 32);
+      const float2 *row = wtab + (int64_t)a * (dmax + 1);
+      dl += __ldg(&row[pk & 0xFFFFu].x);
+      dh += __ldg(&row[pk >> 16].x);
+    }
+    const int64_t i0 = tile * 64 + 2 * lane;
+    if (i0 < n) den[i0] = dl + (float)(rowptr[i0 + 1] - rowptr[i0]);
+    if (i0 + 1 < n) den[i0 + 1] = dh + (float)(rowptr[i0 + 2] - rowptr[i0 + 1]);
+  }
+}
+
+__global__ void k_dip_max(int64_t count, const uint16_t *__restrict__ dip, unsigned *__restrict__ out) {
+  unsigned m = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned)__ldg(dip + t));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 __global__ void k_chunk_count(int32_t n, const int32_t *__restrict__ rowptr, int *__restrict__ nch) {
@@ -542,6 +654,9 @@ struct IterWs {
   unsigned *cflag;
   int *tiles;     // scan workspace
   unsigned *dtile;
+  float2 *wtab;   // full-table mode (w, w d) table
+  float *den;     // [n] full-table mode denominators
+  unsigned *dmax; // largest d_ip entry
 };
 
 // a row of deg > kChunkDeg yields ceil(deg / kChunk) <= 0.0116 deg chunks, below deg / 64
@@ -563,6 +678,9 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.cflag = c.take<unsigned>(mc);
   w.tiles = c.take<int>((size_t)scan_tiles(n) + 1);
   w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + 63) / 64) * (size_t)k * 32);
+  w.wtab = precision == 64 ? nullptr : c.take<float2>(kFullTabMax / sizeof(float2));
+  w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
+  w.dmax = c.take<unsigned>(1);
   return c.size();
 }
 
@@ -596,7 +714,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   SweepArgs A;
   A.n = n; A.k = k; A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.cnt_off = cnt_off;
   A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
-  A.stab = w.stab; A.cfirst = w.cfirst; A.cnode = w.cnode; A.cpart = w.cpart; A.cflag = w.cflag; A.stamp = 0;
+  A.stab = w.stab; A.wtab = nullptr; A.dmax = 0; A.den = nullptr; A.cfirst = w.cfirst; A.cnode = w.cnode; A.cpart = w.cpart; A.cflag = w.cflag; A.stamp = 0;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
   A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol; A.status = status;
 
@@ -618,17 +736,42 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     kern = tsm ? (const void *)k_sweep_f64<true> : (const void *)k_sweep_f64<false>;
     tiles = (n + 31) / 32;
   } else {
-    note_launch(), k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
+    // the largest distance decides between the full (w, w d) table and the clamped s table
+    SSM_TRY_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), s));
+    const int64_t kn = (int64_t)k * n;
+    note_launch(), k_dip_max<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kn + 255) / 256, sms * 8)), 256, 0, s>>>(
+        kn, dip, w.dmax);
+    unsigned dmax = 0;
+    SSM_TRY_CUDA(cudaMemcpyAsync(&dmax, w.dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SSM_TRY_CUDA(cudaStreamSynchronize(s));
+    const bool full = (size_t)k * ((size_t)dmax + 1) * sizeof(float2) <= kFullTabMax;
+    A.dmax = (int32_t)dmax;
+    A.wtab = w.wtab;
+    A.den = w.den;
     note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, dip, w.dtile);
+    if (full) {
+      note_launch(), k_build_wtab<<<std::max(1, std::min(sms * 4, (int)(((int64_t)k * (dmax + 1) + 255) / 256))), 256, 0,
+                                    s>>>(k, (int32_t)dmax, cnt_off, cnt, w.wtab);
+      note_launch(), k_sweep_den<<<std::max(1, (int)std::min<int64_t>(((int64_t)n + 511) / 512, sms * 8)), 256, 0, s>>>(
+          n, k, (int32_t)dmax, w.dtile, w.wtab, rowptr, w.den);
+    } else {
+      note_launch(), k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
+    }
     note_launch(), k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
     int rc = exclusive_scan(w.nch, w.cfirst, n, w.tiles, s);
     if (rc) return rc;
     note_launch(), k_chunk_nodes<<<nb, 256, 0, s>>>(n, w.cfirst, w.cnode);
     SSM_TRY_CUDA(cudaMemsetAsync(w.cflag, 0, max_chunks(2 * m) * sizeof(unsigned), s));
-    const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2)), tab = (size_t)(2 * cnt_len) * sizeof(float);
-    tsm = piv + tab <= kSmemBudget;
-    smem = piv + (tsm ? tab : 0);
-    kern = tsm ? (const void *)k_sweep_f32<true> : (const void *)k_sweep_f32<false>;
+    const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2));
+    if (full) {
+      smem = piv + (size_t)k * ((size_t)dmax + 1) * sizeof(float2);
+      kern = (const void *)k_sweep_f32<kFull>;
+    } else {
+      const size_t tab = (size_t)(2 * cnt_len) * sizeof(float);
+      tsm = piv + tab <= kSmemBudget;
+      smem = piv + (tsm ? tab : 0);
+      kern = tsm ? (const void *)k_sweep_f32<kClampSmem> : (const void *)k_sweep_f32<kClampGlobal>;
+    }
     tiles = (n + 63) / 64;
   }
   SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

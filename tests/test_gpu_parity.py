@@ -288,6 +288,27 @@ def test_sweep_fp32_single_step(name, k):
     assert rel.item() == pytest.approx(orel, rel=1e-4)
 
 
+@pytest.mark.parametrize("k", [12, 100])
+def test_sweep_fp32_both_weight_table_modes(k):
+    """The FP32 sweep keeps a (w, w d) table over all pivots and distances when
+    k * (max d + 1) entries fit (k = 12 on this graph) and a clamped s table
+    otherwise (k = 100); both must meet the tolerance from the same state."""
+    n, s, d = GRAPHS["rgg"]()
+    prep = O.prepare(n, s, d, k)
+    dmax = int(prep.dip.max())
+    assert (k * (dmax + 1) * 8 <= 48 * 1024) == (k == 12)
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(k, prep)
+    x = prep.pos0
+    for _ in range(3):
+        x, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x)
+    x0 = x.astype(np.float32)
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_iterate(g, P, pos, 1)
+    opos, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x0.astype(np.float64))
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+
+
 @pytest.mark.parametrize("name,k", [("rgg", 100), ("ba", 64), ("btree", 33)])
 def test_sweep_fp32_along_oracle_trajectory(name, k):
     """FP32 step error along the oracle's FP64 trajectory: at every iteration t
