@@ -184,12 +184,12 @@ int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
  * *rel_change (device double, the last computed change).  cnt_off and cnt are
  * the tables of ssm_aggregate, cnt_len = cnt_off[k] (from ssm_aggregate_size);
  * m is the edge count (colidx has 2m entries).  1 <= iters, 1 <= k <= 4096.
- * Device error SSM_E_TIMEOUT if a node's neighbour-chunk partial sums were
- * not published within 20 ms (rows longer than 128 are split into chunks that
- * other warps of the same launch sum).  Precision 32 waits once for `stream`
- * (after its first kernel) to read the largest d_ip entry on the host: when
- * k * (max d + 1) weight pairs fit in shared memory the sweep uses a full
- * (w', w' d) table, otherwise a table of s clamped at 2 ecc_a + 1.
+ * Precision 32 waits once for `stream`
+ * (after its first kernels) to read the largest d_ip entry and the number of
+ * rows longer than 32 and 1024 entries on the host: when k * (max d + 1)
+ * weight pairs fit in shared memory the sweep uses a full (w', w' d) table,
+ * otherwise a table of s clamped at 2 ecc_a + 1; the neighbour sums of each
+ * iteration are taken by one thread, warp or block per row by length.
  * ------------------------------------------------------------------- */
 size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision);
 int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,

@@ -32,23 +32,22 @@
 //    also adds 1e-36 to q so it stays positive at d = 0; relative change of a
 //    term with r >= 1e-6 below 1e-12); tables and pivot positions sit in
 //    shared memory, loaded once per persistent block;
-//  * warps take 64-node tiles from an atomic counter; rows longer than
-//    kChunkDeg are cut into kChunk-neighbour tasks handed out first, whose
-//    partial sums the owning tile adds in chunk order (results do not depend
-//    on scheduling).
+//  * the neighbour terms of every node are summed first by k_sweep_nbr, one
+//    thread per row of up to kShortDeg entries, one warp per row up to
+//    kMidDeg, one block per longer row (each sum in a fixed order); the
+//    tile kernel reads them with the node's other per-node data;
+//  * warps take 64-node tiles from an atomic counter.
 // The relative change ||X^{t+1}-X^t||/||X^t|| is reduced in FP64 in a fixed
 // order by the last block to finish.
 #include <algorithm>
 
 #include "common.cuh"
-#include "scan.cuh"
 
 namespace ssm {
 
 constexpr int kSweepThreads = 256;
-constexpr int kLightDeg = 32;   // rows up to this length: one lane walks the row
-constexpr int kChunkDeg = 128;  // rows longer than this: cut into chunk tasks
-constexpr int kChunk = 256;     // neighbours per chunk task
+constexpr int kShortDeg = 32;   // neighbour rows up to this length: one thread
+constexpr int kMidDeg = 1024;   // up to this length: one warp; longer rows: one block
 constexpr size_t kSmemBudget = 200 * 1024;
 constexpr size_t kFullTabMax = 48 * 1024;  // bytes of the (w, w d) table of the full-table mode
 constexpr int kMaxPivotsSweep = 4096;
@@ -63,7 +62,6 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_FULL_MIN_BLOCKS 3
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
-constexpr unsigned long long kChunkWaitNs = 20000000ull;  // 20 ms
 
 struct SweepArgs {
   int32_t n, k;
@@ -77,11 +75,7 @@ struct SweepArgs {
   const float2 *wtab;     // [k][dmax+1] (w, w d) by pivot and distance (full-table mode)
   int32_t dmax;           // largest d_ip entry (full-table mode)
   const float *den;       // [n] deg(i) + sum_a w'_ia (full-table mode)
-  const int32_t *cfirst;  // [n+1] first chunk task of each node; cfirst[n] = chunks
-  const int32_t *cnode;   // [chunks] node of each chunk task
-  float2 *cpart;          // [chunks] neighbour partial sums
-  unsigned *cflag;        // [chunks] stamp of the launch that wrote cpart
-  unsigned stamp;         // this launch's stamp
+  const float2 *nb;       // [n] neighbour sums of this iteration (k_sweep_nbr)
   unsigned *tile_ctr;     // next task to hand out
   unsigned *done_ctr;     // blocks finished
   double *tile_part;      // [ntiles][2] (sum dx^2, sum x^2) per tile
@@ -195,6 +189,80 @@ __device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const i
   sy = warp_sumf(sy);
 }
 
+// Neighbour sums nb[i] = sum_{j in N(i)} (x_j + (x_i - x_j)/r_ij) (r == 0:
+// x_j) for one iteration.  Blocks [0, nlong) take one long row each (a
+// block-stride walk, then a fixed-order block sum), the next ceil(nmid / 8)
+// blocks one medium row per warp, the rest one node per thread (rows of at
+// most kShortDeg entries; longer rows were listed).  Every sum has a fixed
+// order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_sweep_nbr(int32_t n, const int32_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colidx, const float2 *__restrict__ pin,
+                                                   int32_t nlong, const int32_t *__restrict__ long_rows, int32_t nmid,
+                                                   const int32_t *__restrict__ mid_rows, float2 *__restrict__ nb,
+                                                   const int32_t *__restrict__ stop) {
+  if (__ldcg(stop)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int b = blockIdx.x;
+  if (b < nlong) {
+    __shared__ float red[2][8];
+    const int i = __ldg(long_rows + b);
+    const int rb = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
+    const float2 xi = pin[i];
+    float sx = 0.f, sy = 0.f;
+    for (int t = rb + (int)threadIdx.x; t < re; t += (int)blockDim.x) edge_term(xi.x, xi.y, pin[__ldg(colidx + t)], sx, sy);
+    sx = warp_sumf(sx);
+    sy = warp_sumf(sy);
+    if (lane == 0) {
+      red[0][warp] = sx;
+      red[1][warp] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float ax = 0.f, ay = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        ax += red[0][w];
+        ay += red[1][w];
+      }
+      nb[i] = make_float2(ax, ay);
+    }
+    return;
+  }
+  b -= nlong;
+  const int midb = (nmid + 7) / 8;
+  if (b < midb) {
+    const int r = b * 8 + warp;
+    if (r >= nmid) return;
+    const int i = __ldg(mid_rows + r);
+    const float2 xi = pin[i];
+    float sx, sy;
+    warp_row(pin, colidx, __ldg(rowptr + i), __ldg(rowptr + i + 1), xi.x, xi.y, sx, sy);
+    if (lane == 0) nb[i] = make_float2(sx, sy);
+    return;
+  }
+  b -= midb;
+  const int i = b * (int)blockDim.x + (int)threadIdx.x;
+  if (i >= n) return;
+  const int rb = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
+  if (re - rb > kShortDeg) return;
+  const float2 xi = pin[i];
+  float sx = 0.f, sy = 0.f;
+  light_row(pin, colidx, rb, re, xi.x, xi.y, sx, sy);
+  nb[i] = make_float2(sx, sy);
+}
+
+// lists the rows longer than kShortDeg (medium: up to kMidDeg) for k_sweep_nbr;
+// counts[0] = medium rows, counts[1] = long rows
+__global__ void k_nbr_classify(int32_t n, const int32_t *__restrict__ rowptr, unsigned *__restrict__ counts,
+                               int32_t *__restrict__ mid_rows, int32_t *__restrict__ long_rows) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int deg = rowptr[i + 1] - rowptr[i];
+    if (deg > kMidDeg)
+      long_rows[atomicAdd(counts + 1, 1u)] = (int32_t)i;
+    else if (deg > kShortDeg)
+      mid_rows[atomicAdd(counts, 1u)] = (int32_t)i;
+  }
+}
+
 // ----------------------------------------------------------------- FP32
 __device__ __forceinline__ float2 lds_f32x2(unsigned addr) {
   float2 v;
@@ -239,32 +307,14 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 
   const unsigned lane = threadIdx.x & 31u;
   const unsigned ntiles = (unsigned)((n + 63) / 64);
-  const unsigned nchunks = (unsigned)__ldg(A.cfirst + n);
   // loop-invariant constant pairs, kept in registers (opaque to the compiler so
   // it does not rebuild them from immediates inside the pivot loop)
   float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
   asm volatile("" : "+f"(kMagic2.x), "+f"(kMagic2.y));
   for (;;) {
-    unsigned task = 0;
-    if (lane == 0) task = atomicAdd(A.tile_ctr, 1u);
-    task = __shfl_sync(0xffffffffu, task, 0);
-
-    if (task < nchunks) {  // ---- a chunk of a long row
-      const int node = __ldg(A.cnode + task);
-      const int rb = __ldg(A.rowptr + node), re = __ldg(A.rowptr + node + 1);
-      const int b = rb + ((int)task - __ldg(A.cfirst + node)) * kChunk;
-      const int e = min(b + kChunk, re);
-      const float2 xi = pin[node];
-      float sx, sy;
-      warp_row(pin, A.colidx, b, e, xi.x, xi.y, sx, sy);
-      if (lane == 0) {
-        A.cpart[task] = make_float2(sx, sy);
-        __threadfence();
-        st_release_u32(A.cflag + task, A.stamp);
-      }
-      continue;
-    }
-    const unsigned tile = task - nchunks;
+    unsigned tile = 0;
+    if (lane == 0) tile = atomicAdd(A.tile_ctr, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= ntiles) break;
 
     // ---- a tile of 64 nodes: this lane owns i0 and i0 + 1
@@ -272,8 +322,6 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     const bool live0 = i0 < n, live1 = i0 + 1 < n;
     const float2 x0 = live0 ? pin[i0] : make_float2(0.f, 0.f);
     const float2 x1 = live1 ? pin[i0 + 1] : make_float2(0.f, 0.f);
-    const int b0 = live0 ? __ldg(A.rowptr + i0) : 0, e0 = live0 ? __ldg(A.rowptr + i0 + 1) : 0;
-    const int b1 = live1 ? __ldg(A.rowptr + i0 + 1) : 0, e1 = live1 ? __ldg(A.rowptr + i0 + 2) : 0;
     const float2 xi2 = make_float2(x0.x, x1.x), yi2 = make_float2(x0.y, x1.y);
 
     // pivot terms, a = 0..k-1.  The d words of the next kPrefetch pivots are
@@ -378,42 +426,16 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
     const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
 
-    // neighbour terms (w = 1, d = 1)
-    float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
-    const int deg0 = e0 - b0, deg1 = e1 - b1;
-    if (deg0 <= kLightDeg) light_row(pin, A.colidx, b0, e0, x0.x, x0.y, sx0, sy0);
-    if (deg1 <= kLightDeg) light_row(pin, A.colidx, b1, e1, x1.x, x1.y, sx1, sy1);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int bj = j ? b1 : b0, ej = j ? e1 : e0, dj = ej - bj;
-      unsigned mid = __ballot_sync(0xffffffffu, dj > kLightDeg && dj <= kChunkDeg);
-      while (mid) {  // medium rows: the whole warp, one row at a time
-        const int src = __ffs(mid) - 1;
-        mid &= mid - 1u;
-        const int hb = __shfl_sync(0xffffffffu, bj, src), he = __shfl_sync(0xffffffffu, ej, src);
-        const float hx = __shfl_sync(0xffffffffu, j ? x1.x : x0.x, src);
-        const float hy = __shfl_sync(0xffffffffu, j ? x1.y : x0.y, src);
-        float sx, sy;
-        warp_row(pin, A.colidx, hb, he, hx, hy, sx, sy);
-        if ((int)lane == src) {
-          if (j) { sx1 += sx; sy1 += sy; } else { sx0 += sx; sy0 += sy; }
-        }
-      }
-      if (dj > kChunkDeg) {  // long row: its chunk partials, in chunk order
-        const int c0 = __ldg(A.cfirst + i0 + j), c1 = __ldg(A.cfirst + i0 + j + 1);
-        float ax = 0.f, ay = 0.f;
-        for (int c = c0; c < c1; ++c) {
-          // the chunk was handed out before this tile and its warp is running
-          const unsigned long long t0 = globaltimer_ns();
-          bool ready = ld_acquire_u32(A.cflag + c) == A.stamp;
-          while (!ready && globaltimer_ns() - t0 < kChunkWaitNs) ready = ld_acquire_u32(A.cflag + c) == A.stamp;
-          if (!ready) dev_fail(A.status, SSM_E_TIMEOUT);
-          const float2 part = ready ? __ldcg(A.cpart + c) : make_float2(0.f, 0.f);
-          ax += part.x;
-          ay += part.y;
-        }
-        if (j) { sx1 += ax; sy1 += ay; } else { sx0 += ax; sy0 += ay; }
-      }
+    // neighbour terms (w = 1, d = 1), summed by k_sweep_nbr
+    const float2 nb0 = live0 ? __ldg(A.nb + i0) : make_float2(0.f, 0.f);
+    const float2 nb1 = live1 ? __ldg(A.nb + i0 + 1) : make_float2(0.f, 0.f);
+    const float sx0 = nb0.x, sy0 = nb0.y, sx1 = nb1.x, sy1 = nb1.y;
+    float deg0 = 0.f, deg1 = 0.f;
+    if (!FULL) {
+      const int r0 = live0 ? __ldg(A.rowptr + i0) : 0, r1 = live0 ? __ldg(A.rowptr + i0 + 1) : 0;
+      const int r2 = live1 ? __ldg(A.rowptr + i0 + 2) : 0;
+      deg0 = (float)(r1 - r0);
+      deg1 = (float)(r2 - r1);
     }
 
     // X^{t+1} and this tile's share of the relative change
@@ -422,7 +444,7 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     const float2 chk = FULL ? __fadd2_rn(nx2, ny2) : den2;
     if ((live0 && !(chk.x == chk.x)) || (live1 && !(chk.y == chk.y))) dev_fail(A.status, SSM_E_NUMERIC);
     if (live0) {
-      const float dn = FULL ? den2.x : den2.x + (float)deg0;
+      const float dn = FULL ? den2.x : den2.x + deg0;
       const float xn = dn > 0.f ? (nx2.x + sx0) / dn : x0.x, yn = dn > 0.f ? (ny2.x + sy0) / dn : x0.y;
       pout[i0] = make_float2(xn, yn);
       const float ex = xn - x0.x, ey = yn - x0.y;
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       cd = fmaf(x0.x, x0.x, x0.y * x0.y);
     }
     if (live1) {
-      const float dn = FULL ? den2.y : den2.y + (float)deg1;
+      const float dn = FULL ? den2.y : den2.y + deg1;
       const float xn = dn > 0.f ? (nx2.y + sx1) / dn : x1.x, yn = dn > 0.f ? (ny2.y + sy1) / dn : x1.y;
       pout[i0 + 1] = make_float2(xn, yn);
       const float ex = xn - x1.x, ey = yn - x1.y;
@@ -521,18 +543,6 @@ __global__ void k_dip_max(int64_t count, const uint16_t *__restrict__ dip, unsig
     m = max(m, (unsigned)__ldg(dip + t));
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
-
-__global__ void k_chunk_count(int32_t n, const int32_t *__restrict__ rowptr, int *__restrict__ nch) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int deg = rowptr[i + 1] - rowptr[i];
-    nch[i] = deg > kChunkDeg ? (deg + kChunk - 1) / kChunk : 0;
-  }
-}
-
-__global__ void k_chunk_nodes(int32_t n, const int32_t *__restrict__ cfirst, int32_t *__restrict__ cnode) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) cnode[c] = (int32_t)i;
 }
 
 // ----------------------------------------------------------------- FP64
@@ -647,20 +657,13 @@ struct IterWs {
   int32_t *stop;
   double *tile_part;
   float *stab;
-  int *nch;       // [n] chunk counts
-  int32_t *cfirst;  // [n+1]
-  int32_t *cnode;
-  float2 *cpart;
-  unsigned *cflag;
-  int *tiles;     // scan workspace
+  float2 *nb;       // [n] neighbour sums
+  int32_t *mid_rows, *long_rows;  // [n] rows longer than kShortDeg / kMidDeg
   unsigned *dtile;
   float2 *wtab;   // full-table mode (w, w d) table
   float *den;     // [n] full-table mode denominators
-  unsigned *dmax; // largest d_ip entry
+  unsigned *meta;  // [4] largest d_ip entry, medium rows, long rows
 };
-
-// a row of deg > kChunkDeg yields ceil(deg / kChunk) <= 0.0116 deg chunks, below deg / 64
-static size_t max_chunks(int64_t m2) { return (size_t)(m2 / 64 + 1); }
 
 static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t k, int64_t cnt_len,
                             int32_t precision) {
@@ -670,17 +673,13 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.stop = c.take<int32_t>(1);
   w.tile_part = c.take<double>(2 * ((size_t)n / 32 + 2));
   w.stab = c.take<float>((size_t)(2 * cnt_len));
-  w.nch = c.take<int>((size_t)n);
-  w.cfirst = c.take<int32_t>((size_t)n + 1);
-  const size_t mc = max_chunks(m2);
-  w.cnode = c.take<int32_t>(mc);
-  w.cpart = c.take<float2>(mc);
-  w.cflag = c.take<unsigned>(mc);
-  w.tiles = c.take<int>((size_t)scan_tiles(n) + 1);
+  w.nb = precision == 64 ? nullptr : c.take<float2>((size_t)n);
+  w.mid_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
+  w.long_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
   w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + 63) / 64) * (size_t)k * 32);
   w.wtab = precision == 64 ? nullptr : c.take<float2>(kFullTabMax / sizeof(float2));
   w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
-  w.dmax = c.take<unsigned>(1);
+  w.meta = c.take<unsigned>(4);
   return c.size();
 }
 
@@ -714,7 +713,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   SweepArgs A;
   A.n = n; A.k = k; A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.cnt_off = cnt_off;
   A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
-  A.stab = w.stab; A.wtab = nullptr; A.dmax = 0; A.den = nullptr; A.cfirst = w.cfirst; A.cnode = w.cnode; A.cpart = w.cpart; A.cflag = w.cflag; A.stamp = 0;
+  A.stab = w.stab; A.wtab = nullptr; A.dmax = 0; A.den = nullptr; A.nb = w.nb;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
   A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol; A.status = status;
 
@@ -728,6 +727,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   const void *kern;
   size_t smem;
   int64_t tiles;
+  unsigned meta[3] = {0, 0, 0};
   bool tsm = true;
   if (precision == 64) {
     const size_t piv = (size_t)k * sizeof(PivD), tab = (size_t)cnt_len * sizeof(double);
@@ -736,14 +736,16 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     kern = tsm ? (const void *)k_sweep_f64<true> : (const void *)k_sweep_f64<false>;
     tiles = (n + 31) / 32;
   } else {
-    // the largest distance decides between the full (w, w d) table and the clamped s table
-    SSM_TRY_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), s));
+    // the largest distance decides between the full (w, w d) table and the
+    // clamped s table; the row lengths decide the neighbour-kernel grid
+    SSM_TRY_CUDA(cudaMemsetAsync(w.meta, 0, 4 * sizeof(unsigned), s));
     const int64_t kn = (int64_t)k * n;
     note_launch(), k_dip_max<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kn + 255) / 256, sms * 8)), 256, 0, s>>>(
-        kn, dip, w.dmax);
-    unsigned dmax = 0;
-    SSM_TRY_CUDA(cudaMemcpyAsync(&dmax, w.dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        kn, dip, w.meta);
+    note_launch(), k_nbr_classify<<<nb, 256, 0, s>>>(n, rowptr, w.meta + 1, w.mid_rows, w.long_rows);
+    SSM_TRY_CUDA(cudaMemcpyAsync(meta, w.meta, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SSM_TRY_CUDA(cudaStreamSynchronize(s));
+    const unsigned dmax = meta[0];
     const bool full = (size_t)k * ((size_t)dmax + 1) * sizeof(float2) <= kFullTabMax;
     A.dmax = (int32_t)dmax;
     A.wtab = w.wtab;
@@ -757,11 +759,6 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     } else {
       note_launch(), k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
     }
-    note_launch(), k_chunk_count<<<nb, 256, 0, s>>>(n, rowptr, w.nch);
-    int rc = exclusive_scan(w.nch, w.cfirst, n, w.tiles, s);
-    if (rc) return rc;
-    note_launch(), k_chunk_nodes<<<nb, 256, 0, s>>>(n, w.cfirst, w.cnode);
-    SSM_TRY_CUDA(cudaMemsetAsync(w.cflag, 0, max_chunks(2 * m) * sizeof(unsigned), s));
     const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2));
     if (full) {
       smem = piv + (size_t)k * ((size_t)dmax + 1) * sizeof(float2);
@@ -781,10 +778,14 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   const int64_t want = (tiles + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
 
+  const int32_t nmid = (int32_t)meta[1], nlong = (int32_t)meta[2];
+  const unsigned nbr_blocks = (unsigned)(nlong + (nmid + 7) / 8 + (n + 255) / 256);
   for (int t = 0; t < iters; ++t) {
     const bool even = (t & 1) == 0;
-    A.stamp = (unsigned)t + 1u;
     void *pin = even ? pos : w.tmp, *pout = even ? w.tmp : pos;
+    if (precision == 32)
+      note_launch(), k_sweep_nbr<<<nbr_blocks, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pin, nlong, w.long_rows,
+                                                             nmid, w.mid_rows, w.nb, w.stop);
     void *args[] = {&A, &pin, &pout};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(blocks), dim3(kSweepThreads), args, smem, s));

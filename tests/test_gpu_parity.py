@@ -288,6 +288,32 @@ def test_sweep_fp32_single_step(name, k):
     assert rel.item() == pytest.approx(orel, rel=1e-4)
 
 
+def _hubs_graph():
+    """A long row (node 0, degree 3999), a medium row (node 1, degree ~500) and
+    short rows (a random tree plus random extra edges)."""
+    n, s, d = _rand_graph(11, 4000, 3000)
+    s = np.concatenate([s, np.zeros(3999, np.int32), np.ones(500, np.int32)])
+    d = np.concatenate([d, np.arange(1, 4000, dtype=np.int32), np.arange(3000, 3500, dtype=np.int32)])
+    return n, s, d
+
+
+@pytest.mark.parametrize("k", [8, 60])
+def test_sweep_fp32_long_medium_short_rows(k):
+    """Neighbour sums are taken per thread (short rows), per warp (medium rows)
+    and per block (rows above 1024 entries); one step from the same state."""
+    n, s, d = _hubs_graph()
+    prep = O.prepare(n, s, d, k)
+    deg = np.diff(prep.g.rowptr)
+    assert deg.max() > 1024 and ((deg > 32) & (deg <= 1024)).any()
+    g = _gpu_graph(n, s, d)
+    P = _gpu_pivots(k, prep)
+    x0 = prep.pos0.astype(np.float32)
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_iterate(g, P, pos, 1)
+    opos, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x0.astype(np.float64))
+    assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+
+
 @pytest.mark.parametrize("k", [12, 100])
 def test_sweep_fp32_both_weight_table_modes(k):
     """The FP32 sweep keeps a (w, w d) table over all pivots and distances when
