@@ -364,6 +364,7 @@ struct CtaBfsArgs {
   int32_t *status;
   const int4 *adj; // [2m] edge-expanded adjacency
   int2 *queues;    // [slots][2][n] row ranges of the frontier
+  const unsigned *run_if;  // run only if this device word is nonzero (the pulled BFS gave up)
 };
 
 // Each block owns sources blockIdx.x, blockIdx.x + gridDim.x, ...; per source
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
   __shared__ unsigned s_total;
   const unsigned n = (unsigned)A.n, nwords = (n + 31u) / 32u;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (__ldcg(A.run_if) == 0u) return;
   int2 *qa = A.queues + (size_t)blockIdx.x * 2 * n, *qb = qa + n;
   for (int si = blockIdx.x; si < A.nsrc; si += gridDim.x) {
     for (unsigned w = threadIdx.x; w < nwords; w += blockDim.x) vis[w] = 0u;
@@ -596,6 +598,8 @@ size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   if (cta_bfs_fits(n)) {
     c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
     c.take<int2>((size_t)cta_bfs_slots(k) * 2 * (size_t)n);
+    c.take<unsigned>(1);
+    c.take<char>(msbfs_pull_workspace(n));
     return c.size();
   }
   MsBfsArgs A;
@@ -603,6 +607,9 @@ size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   return c.size();
 }
 
+// Graphs whose visited bitmap fits shared memory: first the pulled bitset BFS
+// (few levels, every level touches most edges); if it gives up on a large
+// diameter, one block per source (k_bfs_cta).  Larger graphs: k_msbfs.
 int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                  const int32_t *sources, uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   Carver c(ws, ws_bytes);
@@ -614,18 +621,25 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
     B.adj = adj;
     B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
+    unsigned *gaveup = c.take<unsigned>(1);
+    const size_t pw = msbfs_pull_workspace(n);
+    void *pws = c.take<char>(pw);
+    B.run_if = gaveup;
     if (!c.ok) return fail(SSM_E_NOMEM, "BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
+    SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(gaveup, 0, sizeof(unsigned), s));
+    int rc = launch_msbfs_pull(n, rowptr, colidx, k, sources, dist, status, gaveup, pws, pw, s);
+    if (rc) return rc;
     // the 16-byte expanded adjacency saves a dependent load per level but
     // quadruples adjacency traffic: use it only while it stays L2-resident
     const bool adj4 = (size_t)m2 * sizeof(int4) <= kAdj4MaxBytes;
     if (adj4) {
-      int rc = expand_adj(m2, rowptr, colidx, adj, s);
+      rc = expand_adj(m2, rowptr, colidx, adj, s);
       if (rc) return rc;
     }
     const void *kern = adj4 ? (const void *)k_bfs_cta<true> : (const void *)k_bfs_cta<false>;
     const size_t smem = (size_t)((n + 31) / 32) * 4;
     SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
     void *args[] = {&B};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(slots), dim3(kCtaThreads), args, smem, s));

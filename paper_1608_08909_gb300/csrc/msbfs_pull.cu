@@ -1,0 +1,283 @@
+// Multi-source BFS with one bit per source, pulled level by level (the
+// "bottom-up" direction): at level L every node v that some sources have not
+// reached yet ORs the frontier words of its neighbours,
+//   new_v = (OR_{u in N(v)} F_L[u]) & ~seen_v,
+// stopping its walk as soon as every missing source has turned up.  Each
+// node's words are written by its own lane only, so no atomics are needed
+// after the sources are seeded, and d_ip[s][v] = L + 1 is stored for the new
+// bits with a warp-wide loop over the union of the lanes' new bits, so the
+// stores of one source land on consecutive nodes.
+//
+// This wins on graphs of small diameter (hubs, expanders), where a few levels
+// each touch most edges and the per-source BFS would walk every edge once per
+// source.  On large-diameter graphs every level re-reads the frontier words
+// of all unfinished nodes, so a pass gives up when its first kPullProbeLevel
+// levels reached less than 1/64 of all (source, node) pairs, or after
+// kPullMaxLevels levels, and reports it; the caller then runs the per-source
+// BFS.  Sources are taken in
+// passes of 256 (eight 32-bit words per node).
+#include <algorithm>
+
+#include "bfs.cuh"
+
+namespace ssm {
+
+constexpr int kPullThreads = 512;
+constexpr int kPullSources = 256;  // sources per pass: 8 words per node
+constexpr int kPullW4 = kPullSources / 128;  // uint4 chunks per node
+constexpr unsigned kPullMaxLevels = 24;
+constexpr unsigned kPullProbeLevel = 6;  // after this level at least 1/64 of all pairs must be reached
+constexpr int kPullLong = 64;  // longer rows are walked by the whole warp
+
+struct PullArgs {
+  int32_t n;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  int32_t nsrc;     // sources in this pass (<= kPullSources)
+  int32_t base;     // index of the pass's first source
+  const int32_t *sources;
+  uint16_t *dist;   // [all sources][n]
+  int32_t *status;
+  uint4 *seen;      // [n][kPullW4] sources that reached the node
+  uint4 *F[2];      // [n][kPullW4] frontier bits of the current / next level
+  unsigned *flag;   // [6]: new bits seen at level L, nodes left unfinished (both by L mod 3)
+  unsigned long long *found;  // (source, node) pairs reached up to the probe level
+  unsigned *gaveup; // set when a pass needed more than kPullMaxLevels levels
+  BarrierState *bar;
+};
+
+__device__ __forceinline__ unsigned src_mask(int nsrc, int w) {  // valid source bits of word w
+  const int lo = w * 32;
+  if (lo >= nsrc) return 0u;
+  return nsrc - lo >= 32 ? 0xFFFFFFFFu : (1u << (nsrc - lo)) - 1u;
+}
+
+__device__ __forceinline__ unsigned word(const uint4 q, int j) {
+  return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
+}
+
+__global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
+  const unsigned n = (unsigned)A.n;
+
+  if (__ldcg(A.gaveup)) return;  // an earlier pass already gave up
+  // level 0: the sources (seen and F[0] were cleared by the caller)
+  for (int a = (int)gtid; a < A.nsrc; a += (int)nthreads) {
+    const unsigned v = (unsigned)__ldg(A.sources + A.base + a);
+    const unsigned bit = 1u << (a & 31);
+    unsigned *s = reinterpret_cast<unsigned *>(A.seen + (size_t)v * kPullW4) + (a >> 5);
+    unsigned *f = reinterpret_cast<unsigned *>(A.F[0] + (size_t)v * kPullW4) + (a >> 5);
+    atomicOr(s, bit);
+    atomicOr(f, bit);
+    A.dist[(size_t)(A.base + a) * n + v] = 0;
+  }
+  if (gtid == 0) {
+    for (int i = 0; i < 6; ++i) A.flag[i] = 0u;
+    *A.found = 0ull;
+  }
+  if (!grid_barrier(A.bar, A.status)) return;
+
+  uint4 valid[kPullW4];
+#pragma unroll
+  for (int c = 0; c < kPullW4; ++c)
+    valid[c] = make_uint4(src_mask(A.nsrc, 4 * c), src_mask(A.nsrc, 4 * c + 1), src_mask(A.nsrc, 4 * c + 2),
+                          src_mask(A.nsrc, 4 * c + 3));
+
+  for (unsigned L = 0;; ++L) {
+    if (L >= kPullMaxLevels) {
+      if (gtid == 0) atomicExch(A.gaveup, 1u);
+      return;
+    }
+    const uint4 *fcur = (L & 1u) ? A.F[1] : A.F[0];
+    uint4 *fnext = (L & 1u) ? A.F[0] : A.F[1];
+    // the flags of level L+1 were last read right after the barrier of level
+    // L-2, which every thread has passed since
+    if (gtid == 0) {
+      A.flag[(L + 1u) % 3u] = 0u;
+      A.flag[3 + (L + 1u) % 3u] = 0u;
+    }
+    const uint16_t nd = (uint16_t)(L + 1u);
+    bool any_new = false, unfinished = false;
+    unsigned pairs = 0;  // new (source, node) pairs of this lane (counted up to the probe level)
+    for (unsigned base = gwarp * 32u; base < n; base += nwarps * 32u) {
+      const unsigned v = base + lane;
+      const bool live = v < n;
+      uint4 miss[kPullW4], acc[kPullW4];
+      bool open = false;
+#pragma unroll
+      for (int c = 0; c < kPullW4; ++c) {
+        const uint4 s = live ? A.seen[(size_t)v * kPullW4 + c] : valid[c];
+        miss[c] = make_uint4(~s.x & valid[c].x, ~s.y & valid[c].y, ~s.z & valid[c].z, ~s.w & valid[c].w);
+        acc[c] = make_uint4(0u, 0u, 0u, 0u);
+        open |= (miss[c].x | miss[c].y | miss[c].z | miss[c].w) != 0u;
+      }
+      int rb = 0, re = 0;
+      if (open) {
+        rb = __ldg(A.rowptr + v);
+        re = __ldg(A.rowptr + v + 1);
+      }
+      // rows longer than kPullLong: the whole warp walks each of them
+      unsigned longs = __ballot_sync(0xffffffffu, open && re - rb > kPullLong);
+      while (longs) {
+        const int src = __ffs(longs) - 1;
+        longs &= longs - 1u;
+        const int hb = __shfl_sync(0xffffffffu, rb, src), he = __shfl_sync(0xffffffffu, re, src);
+        uint4 part[kPullW4];
+#pragma unroll
+        for (int c = 0; c < kPullW4; ++c) part[c] = make_uint4(0u, 0u, 0u, 0u);
+        for (int t = hb + (int)lane; t < he; t += 32) {
+          const unsigned u = (unsigned)__ldg(A.colidx + t);
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c) {
+            const uint4 f = __ldcg(fcur + (size_t)u * kPullW4 + c);
+            part[c].x |= f.x;
+            part[c].y |= f.y;
+            part[c].z |= f.z;
+            part[c].w |= f.w;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kPullW4; ++c) {
+          part[c].x = __reduce_or_sync(0xffffffffu, part[c].x);
+          part[c].y = __reduce_or_sync(0xffffffffu, part[c].y);
+          part[c].z = __reduce_or_sync(0xffffffffu, part[c].z);
+          part[c].w = __reduce_or_sync(0xffffffffu, part[c].w);
+        }
+        if ((int)lane == src) {
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c) acc[c] = part[c];
+        }
+      }
+      if (open && re - rb <= kPullLong) {
+        // four neighbours in flight, stop once every missing source turned up
+        for (int t = rb; t < re; t += 4) {
+          unsigned u[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) u[e] = t + e < re ? (unsigned)__ldg(A.colidx + t + e) : 0xFFFFFFFFu;
+          bool done = true;
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (u[e] == 0xFFFFFFFFu) continue;
+              const uint4 f = __ldcg(fcur + (size_t)u[e] * kPullW4 + c);
+              acc[c].x |= f.x;
+              acc[c].y |= f.y;
+              acc[c].z |= f.z;
+              acc[c].w |= f.w;
+            }
+            done &= ((acc[c].x & miss[c].x) == miss[c].x) && ((acc[c].y & miss[c].y) == miss[c].y) &&
+                    ((acc[c].z & miss[c].z) == miss[c].z) && ((acc[c].w & miss[c].w) == miss[c].w);
+          }
+          if (done) break;
+        }
+      }
+      uint4 nw[kPullW4];
+      bool got = false, left = false;
+#pragma unroll
+      for (int c = 0; c < kPullW4; ++c) {
+        nw[c] = make_uint4(acc[c].x & miss[c].x, acc[c].y & miss[c].y, acc[c].z & miss[c].z, acc[c].w & miss[c].w);
+        got |= (nw[c].x | nw[c].y | nw[c].z | nw[c].w) != 0u;
+        left |= (nw[c].x ^ miss[c].x) | (nw[c].y ^ miss[c].y) | (nw[c].z ^ miss[c].z) | (nw[c].w ^ miss[c].w);
+      }
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < kPullW4; ++c) {
+          fnext[(size_t)v * kPullW4 + c] = nw[c];
+          if (got) {
+            uint4 s = A.seen[(size_t)v * kPullW4 + c];
+            s.x |= nw[c].x;
+            s.y |= nw[c].y;
+            s.z |= nw[c].z;
+            s.w |= nw[c].w;
+            A.seen[(size_t)v * kPullW4 + c] = s;
+          }
+        }
+      }
+      any_new |= got;
+      unfinished |= left;
+      if (L < kPullProbeLevel)
+#pragma unroll
+        for (int c = 0; c < kPullW4; ++c)
+          pairs += __popc(nw[c].x) + __popc(nw[c].y) + __popc(nw[c].z) + __popc(nw[c].w);
+      // d_ip[s][v] = L + 1 for the new bits, one source at a time across the warp
+#pragma unroll
+      for (int c = 0; c < kPullW4; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const unsigned mine = word(nw[c], j);
+          unsigned all = __reduce_or_sync(0xffffffffu, mine);
+          const int w = 4 * c + j;
+          while (all) {
+            const int b = __ffs(all) - 1;
+            all &= all - 1u;
+            if ((mine >> b) & 1u) A.dist[(size_t)(A.base + 32 * w + b) * n + v] = nd;
+          }
+        }
+    }
+    if (__any_sync(0xffffffffu, any_new) && lane == 0) atomicOr(A.flag + L % 3u, 1u);
+    if (__any_sync(0xffffffffu, unfinished) && lane == 0) atomicOr(A.flag + 3 + L % 3u, 1u);
+    if (L < kPullProbeLevel) {
+      pairs = __reduce_add_sync(0xffffffffu, pairs);
+      if (lane == 0 && pairs) atomicAdd(A.found, (unsigned long long)pairs);
+    }
+    if (!grid_barrier(A.bar, A.status)) return;
+    // a graph whose BFS balls grow slowly (large diameter) is left to the
+    // per-source BFS early
+    if (L + 1u == kPullProbeLevel && __ldcg(A.flag + L % 3u) != 0u &&
+        __ldcg(A.found) * 64ull < (unsigned long long)A.n * (unsigned long long)A.nsrc) {
+      if (gtid == 0) atomicExch(A.gaveup, 1u);
+      return;
+    }
+    if (__ldcg(A.flag + L % 3u) == 0u) {
+      // nothing new at this level: the pass is complete; unreached pairs mean
+      // the graph is disconnected
+      if (gtid == 0 && __ldcg(A.flag + 3 + L % 3u) != 0u) dev_fail(A.status, SSM_E_DISCONNECTED);
+      return;
+    }
+  }
+}
+
+size_t msbfs_pull_workspace(int32_t n) {
+  Carver c(nullptr, 0);
+  c.take<uint4>((size_t)n * kPullW4);
+  c.take<uint4>((size_t)n * kPullW4);
+  c.take<uint4>((size_t)n * kPullW4);
+  c.take<unsigned>(6);
+  c.take<unsigned long long>(1);
+  c.take<BarrierState>(1);
+  return c.size();
+}
+
+int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
+                      uint16_t *dist, int32_t *status, unsigned *gaveup, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Carver c(ws, ws_bytes);
+  PullArgs A;
+  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.sources = sources; A.dist = dist; A.status = status;
+  A.seen = c.take<uint4>((size_t)n * kPullW4);
+  A.F[0] = c.take<uint4>((size_t)n * kPullW4);
+  A.F[1] = c.take<uint4>((size_t)n * kPullW4);
+  A.flag = c.take<unsigned>(6);
+  A.found = c.take<unsigned long long>(1);
+  A.bar = c.take<BarrierState>(1);
+  A.gaveup = gaveup;
+  if (!c.ok) return fail(SSM_E_NOMEM, "multi-source BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const int blocks = cooperative_blocks((const void *)k_msbfs_pull, kPullThreads, 0, 2);
+  if (blocks < 1) return fail(SSM_E_CUDA, "multi-source BFS: kernel cannot be resident");
+  for (int base = 0; base < k; base += kPullSources) {
+    A.base = base;
+    A.nsrc = std::min(kPullSources, k - base);
+    SSM_TRY_CUDA(cudaMemsetAsync(A.seen, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(A.F[0], 0, (size_t)n * kPullW4 * sizeof(uint4), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+    void *args[] = {&A};
+    note_launch();
+    SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs_pull, dim3(blocks), dim3(kPullThreads), args, 0, s));
+  }
+  return SSM_OK;
+}
+
+}  // namespace ssm

@@ -157,8 +157,11 @@ def test_select_pivots_large_grid_kernel():
 # ------------------------------------------------------------------ a2 d_ip
 
 @pytest.mark.parametrize("name,k", [("grid32", 50), ("path", 7), ("btree", 33), ("rgg", 100), ("ba", 64),
-                                    ("messy", 1), ("messy", 95)])
+                                    ("messy", 1), ("messy", 95), ("ba", 300), ("messy", 600)])
 def test_pivot_bfs_bit_exact(name, k):
+    """Small-diameter graphs (ba, messy, btree) take the pulled bitset BFS,
+    k > 256 in several passes; the others give up on it after 24 levels and
+    take the per-source BFS."""
     n, s, d = GRAPHS[name]()
     og = O.build_csr(n, s, d)
     g = _gpu_graph(n, s, d)
@@ -176,14 +179,18 @@ def test_pivot_bfs_repeated_pivots():
     assert np.array_equal(dip, O.pivot_dist(og, piv))
 
 
-def test_pivot_bfs_disconnected():
-    n = 40
-    s = np.array(list(range(0, 19)) + list(range(20, 39)), np.int32)
+@pytest.mark.parametrize("long_arm", [False, True])
+def test_pivot_bfs_disconnected(long_arm):
+    # two paths: short (the pulled BFS notices) or longer than 24 levels (the
+    # per-source BFS does)
+    n = 80 if long_arm else 40
+    half = n // 2
+    s = np.array(list(range(0, half - 1)) + list(range(half, n - 1)), np.int32)
     d = s + 1
     og = O.build_csr(n, s, d)
     g = ssm.Graph(n, og.m, torch.from_numpy(og.rowptr).to(DEV), torch.from_numpy(og.colidx).to(DEV))
     with pytest.raises(ssm.SSMError) as e:
-        ssm.ssm_pivot_bfs(g, torch.tensor([0, 25], dtype=torch.int32, device=DEV))
+        ssm.ssm_pivot_bfs(g, torch.tensor([0, half + 5], dtype=torch.int32, device=DEV))
     assert e.value.code == -3
 
 
