@@ -349,10 +349,19 @@ size_t maxmin_workspace(int32_t n, int64_t m2) {
 // --------------------------------------------------------------------------
 // one source per block: visited bitmap in shared memory
 // --------------------------------------------------------------------------
-constexpr int kCtaThreads = 512;
-constexpr int kCtaSlotsPerSm = 2;
+#ifndef SSM_CTA_THREADS
+#define SSM_CTA_THREADS 512
+#endif
+#ifndef SSM_CTA_SLOTS
+#define SSM_CTA_SLOTS 4
+#endif
+#ifndef SSM_ADJ4_MAX_MB
+#define SSM_ADJ4_MAX_MB 48
+#endif
+constexpr int kCtaThreads = SSM_CTA_THREADS;
+constexpr int kCtaSlotsPerSm = SSM_CTA_SLOTS;
 constexpr size_t kCtaBitmapMax = 200 * 1024;  // bytes of shared memory for the visited bitmap
-constexpr size_t kAdj4MaxBytes = 48u << 20;     // expanded adjacency kept only while it fits well inside L2
+constexpr size_t kAdj4MaxBytes = (size_t)SSM_ADJ4_MAX_MB << 20;  // expanded adjacency kept only while it fits well inside L2
 
 struct CtaBfsArgs {
   int32_t n;
@@ -456,7 +465,19 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
 }
 
 static bool cta_bfs_fits(int32_t n) { return (size_t)((n + 31) / 32) * 4 <= kCtaBitmapMax; }
-static int cta_bfs_slots(int32_t nsrc) { return std::max(1, std::min(nsrc, num_sms() * kCtaSlotsPerSm)); }
+// concurrent sources: as many blocks as fit on the device (at most
+// kCtaSlotsPerSm per SM), each with the visited bitmap of n nodes
+static int cta_bfs_slots(int32_t n, int32_t nsrc) {
+  int per_sm = 0;
+  const size_t smem = (size_t)((n + 31) / 32) * 4;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_bfs_cta<true>, kCtaThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::max(1, std::min(nsrc, num_sms() * std::min(per_sm, kCtaSlotsPerSm)));
+}
 
 // --------------------------------------------------------------------------
 // multi-source bitset BFS
@@ -597,7 +618,7 @@ size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   Carver c(nullptr, 0);
   if (cta_bfs_fits(n)) {
     c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
-    c.take<int2>((size_t)cta_bfs_slots(k) * 2 * (size_t)n);
+    c.take<int2>((size_t)cta_bfs_slots(n, k) * 2 * (size_t)n);
     c.take<unsigned>(1);
     c.take<char>(msbfs_pull_workspace(n));
     return c.size();
@@ -617,7 +638,7 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     CtaBfsArgs B;
     B.n = n; B.rowptr = rowptr; B.colidx = colidx; B.nsrc = k; B.sources = sources; B.dist = dist;
     B.status = status;
-    const int slots = cta_bfs_slots(k);
+    const int slots = cta_bfs_slots(n, k);
     int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
     B.adj = adj;
     B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
