@@ -9,7 +9,7 @@
 //   k_gram      G = Delta^T Delta (upper tiles, 64x64 per block, node chunks)
 //   k_colsum    s_a
 //   k_prepare_b B = 1/4 J (G - s s^T/n) J
-//   k_square    M = (B / max|B|)^4 by two FP64 squarings (grid)
+//   k_square    M = (B / max|B|)^(2^kEigPowerLog2) by FP64 squarings (grid)
 //   k_eigen     top-2 eigenpairs of B: FP64 subspace iteration on M with
 //               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (one
 //               block), then a Rayleigh-Ritz step with B
@@ -26,7 +26,17 @@ constexpr int kGT = 64;          // Gram tile edge
 constexpr int kGStage = 32;      // nodes per shared-memory stage
 constexpr int kGChunk = 8192;    // nodes per block
 constexpr int kGPad = kGT + 4;   // padded row (keeps 16-byte alignment)
-constexpr int kEigP = 8;         // subspace dimension
+#ifndef SSM_EIG_P
+#define SSM_EIG_P 4
+#endif
+#ifndef SSM_EIG_POWER_LOG2
+#define SSM_EIG_POWER_LOG2 2
+#endif
+constexpr int kEigP = SSM_EIG_P;  // subspace dimension
+// the iteration runs on (B / max|B|)^(2^this): higher powers speed up close
+// eigenvalue pairs but drown the second pair below FP64 precision when
+// lambda_2 / lambda_1 is small, so the fourth power is kept
+constexpr int kEigPowerLog2 = SSM_EIG_POWER_LOG2;
 constexpr int kEigThreads = 256;
 constexpr int kMaxPivotsMds = 1024;
 constexpr int kEigScratch = (kEigThreads / 32) * (kEigP * (kEigP + 1) / 2);  // doubles for block_sum
@@ -119,13 +129,38 @@ __global__ void __launch_bounds__(256) k_gram(int32_t n, int32_t k, const uint16
 }
 
 // s_a = sum_i d_ia^2 (exact: below 2^63 for n < 2^31)
+// s[a] = sum_i d_ia^2 (exact; s zeroed by the caller).  Blocks take chunks of
+// kColChunk nodes of one pivot row, eight distances per 16-byte load.
+constexpr int kColChunk = 65536;
 __global__ void k_colsum(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
                          unsigned long long *__restrict__ s) {
   __shared__ unsigned long long part[32];
-  for (int a = blockIdx.x; a < k; a += gridDim.x) {
-    unsigned long long acc = 0;
+  const int64_t nchunks = (n + kColChunk - 1) / kColChunk;
+  for (int64_t task = blockIdx.x; task < (int64_t)k * nchunks; task += gridDim.x) {
+    const int a = (int)(task / nchunks);
+    const int64_t c0 = (task - (int64_t)a * nchunks) * kColChunk;
+    const int64_t c1 = min((int64_t)n, c0 + kColChunk);
     const uint16_t *row = dip + (size_t)a * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    unsigned long long acc = 0;
+    // rows start at multiples of n entries: 16-byte loads from the first aligned entry on
+    int64_t v0 = c0;
+    while (v0 < c1 && (((size_t)(row + v0)) & 15) != 0) ++v0;
+    for (int64_t i = c0 + threadIdx.x; i < v0; i += blockDim.x) {
+      const unsigned long long d = __ldg(row + i);
+      acc += d * d;
+    }
+    const int64_t nv = (c1 - v0) / 8;
+    const uint4 *vrow = reinterpret_cast<const uint4 *>(row + v0);
+    for (int64_t q = threadIdx.x; q < nv; q += blockDim.x) {
+      const uint4 w = __ldg(vrow + q);
+      const unsigned x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const unsigned long long lo = x[h] & 0xFFFFu, hi = x[h] >> 16;
+        acc += lo * lo + hi * hi;
+      }
+    }
+    for (int64_t i = v0 + nv * 8 + threadIdx.x; i < c1; i += blockDim.x) {
       const unsigned long long d = __ldg(row + i);
       acc += d * d;
     }
@@ -135,13 +170,12 @@ __global__ void k_colsum(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
     if (threadIdx.x == 0) {
       unsigned long long t = 0;
       for (int w = 0; w < (int)blockDim.x / 32; ++w) t += part[w];
-      s[a] = t;
+      atomicAdd(s + a, t);
     }
     __syncthreads();
   }
 }
 
-// B = 1/4 J_k (G - s s^T / n) J_k  (one block, FP64)
 __global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__restrict__ Glo,
                             const unsigned long long *__restrict__ Ghi, const unsigned long long *__restrict__ s,
                             double *__restrict__ B, double *__restrict__ rowmean) {
@@ -342,8 +376,8 @@ struct EigOut {
 };
 
 // top-2 eigenpairs of B (k x k, FP64).  Subspace iteration of dimension P
-// runs on M (the fourth power of B / max|B|, same eigenvectors, ratios of
-// eigenvalues raised to the fourth power, so the subspace converges four
+// runs on M (the 2^kEigPowerLog2-th power of B / max|B|, same eigenvectors,
+// ratios of eigenvalues raised to that power, so the subspace converges that
 // times faster per iteration) with a Rayleigh-Ritz step every iteration;
 // a final Rayleigh-Ritz step with B itself gives the eigenvalues and the
 // reported residual.
@@ -448,9 +482,54 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
     return h0 > 0.0 ? sqrt(fmax(res[0], res[1])) / h0 : 0.0;
   };
 
+  // convergence test on B itself: max_{j<2} ||B v_j - q_j v_j|| / |q_0| with
+  // the Rayleigh quotients q_j = v_j^T B v_j (the powers of B in M shrink the
+  // second pair's share, so a test on M alone would stop early for it)
+  auto residual_b = [&]() -> double {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = warp; r < k; r += nwarp) {  // Y[:, 0..1] = B V[:, 0..1], one warp per row
+      double a0 = 0.0, a1 = 0.0;
+      const double *brow = B + (size_t)r * k;
+      for (int c = lane; c < k; c += 32) {
+        const double bv = __ldg(brow + c);
+        a0 += bv * V[c * P + 0];
+        if (P > 1) a1 += bv * V[c * P + 1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      }
+      if (lane == 0) {
+        Y[r * P + 0] = a0;
+        if (P > 1) Y[r * P + 1] = a1;
+      }
+    }
+    __syncthreads();
+    double q[2] = {0.0, 0.0};
+    for (int r = threadIdx.x; r < k; r += blockDim.x)
+      for (int j = 0; j < 2 && j < P; ++j) q[j] += V[r * P + j] * Y[r * P + j];
+    block_sum<2>(q, scratch);
+    double e[2] = {0.0, 0.0};
+    for (int r = threadIdx.x; r < k; r += blockDim.x)
+      for (int j = 0; j < 2 && j < P; ++j) {
+        const double d = Y[r * P + j] - q[j] * V[r * P + j];
+        e[j] += d * d;
+      }
+    block_sum<2>(e, scratch);
+    const double q0 = fabs(q[0]);
+    return q0 > 0.0 ? sqrt(fmax(e[0], e[1])) / q0 : 0.0;
+  };
+
   int it = 0;
   for (; it < maxit; ++it) {
-    const double r = rayleigh_ritz(M);
+    rayleigh_ritz(M);
+    // Y = M W is kept for the next basis; the test on B uses the V columns only
+    for (int t = threadIdx.x; t < k * P; t += blockDim.x) sm[2 * (size_t)k * P + kEigScratch + t] = Y[t];
+    __syncthreads();
+    const double r = residual_b();
+    for (int t = threadIdx.x; t < k * P; t += blockDim.x) Y[t] = sm[2 * (size_t)k * P + kEigScratch + t];
+    __syncthreads();
     if (threadIdx.x == 0) s_done = r <= tol ? 1 : 0;
     __syncthreads();
     if (s_done) break;
@@ -575,17 +654,45 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
                                                   const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
                                                   double *__restrict__ part, unsigned *__restrict__ done,
                                                   double *__restrict__ scale, int32_t *__restrict__ status) {
+  using R = decltype(pos[0].x);  // edge lengths in the precision of the positions, summed in FP64
   __shared__ double red[8];
   __shared__ unsigned s_ticket;
+  const int lane = threadIdx.x & 31;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T2 xi = pos[i];
-    for (int t = __ldg(rowptr + i); t < __ldg(rowptr + i + 1); ++t) {
-      const int j = __ldg(colidx + t);
-      if (j <= i) continue;
-      const T2 xj = pos[j];
-      const double dx = (double)xi.x - (double)xj.x, dy = (double)xi.y - (double)xj.y;
-      acc += sqrt(dx * dx + dy * dy);
+  // a warp takes 32 consecutive nodes; rows longer than 32 are walked by the whole warp
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    int b = 0, e = 0;
+    T2 xi{};
+    if (i < n) {
+      b = __ldg(rowptr + i);
+      e = __ldg(rowptr + i + 1);
+      xi = pos[i];
+    }
+    if (e - b <= 32) {
+      for (int t = b; t < e; ++t) {
+        const int j = __ldg(colidx + t);
+        if (j <= i) continue;
+        const T2 xj = pos[j];
+        const R dx = xi.x - xj.x, dy = xi.y - xj.y;
+        acc += (double)sqrt(dx * dx + dy * dy);
+      }
+    }
+    unsigned longs = __ballot_sync(0xffffffffu, e - b > 32);
+    while (longs) {
+      const int src = __ffs(longs) - 1;
+      longs &= longs - 1u;
+      const int hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+      const int64_t hi = base + src;
+      const R hx = __shfl_sync(0xffffffffu, xi.x, src), hy = __shfl_sync(0xffffffffu, xi.y, src);
+      for (int t = hb + lane; t < he; t += 32) {
+        const int j = __ldg(colidx + t);
+        if (j <= hi) continue;
+        const T2 xj = pos[j];
+        const R dx = hx - xj.x, dy = hy - xj.y;
+        acc += (double)sqrt(dx * dx + dy * dy);
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -625,7 +732,7 @@ __global__ void k_rescale(int32_t n, T2 *__restrict__ pos, const double *__restr
 
 struct MdsWs {
   unsigned long long *Glo, *Ghi, *s;
-  double *B, *B2, *M, *bscale, *rowmean, *vv, *part, *scale;
+  double *B, *B2, *Btmp, *M, *bscale, *rowmean, *vv, *part, *scale;
   EigOut *eo;
   unsigned *done, *dmax;
 };
@@ -638,6 +745,7 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.s = c.take<unsigned long long>(k);
   w.B = c.take<double>(kk);
   w.B2 = c.take<double>(kk);
+  w.Btmp = c.take<double>(kk);
   w.M = c.take<double>(kk);
   w.bscale = c.take<double>(1);
   w.rowmean = c.take<double>(k);
@@ -680,15 +788,26 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   const int T = (k + kGT - 1) / kGT;
   dim3 ggrid((unsigned)(T * (T + 1) / 2), (unsigned)((n + kGChunk - 1) / kGChunk));
   note_launch(), k_gram<<<ggrid, 256, 0, s>>>(n, k, dip, w.Glo, w.Ghi);
-  note_launch(), k_colsum<<<std::min(k, sms * 4), 256, 0, s>>>(n, k, dip, w.s);
+  SSM_TRY_CUDA(cudaMemsetAsync(w.s, 0, (size_t)k * sizeof(unsigned long long), s));
+  {
+    const int64_t tasks = (int64_t)k * ((n + kColChunk - 1) / kColChunk);
+    note_launch(), k_colsum<<<(unsigned)std::min<int64_t>(tasks, (int64_t)sms * 8), 256, 0, s>>>(n, k, dip, w.s);
+  }
   note_launch(), k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
   const int P = std::min(kEigP, (int)k);
-  const size_t esm = (2 * (size_t)k * P + kEigScratch) * sizeof(double);
+  const size_t esm = (3 * (size_t)k * P + kEigScratch) * sizeof(double);  // V, Y, saved Y, scratch
   SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
   note_launch(), k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
   const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
-  note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B, w.bscale, w.B2);  // (B/max|B|)^2
-  note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, w.B2, nullptr, w.M);   // (B/max|B|)^4
+  // M = (B/max|B|)^(2^kEigPowerLog2) by repeated squaring
+  {
+    const double *src = w.B;
+    for (int q = 0; q < kEigPowerLog2; ++q) {
+      double *dst = (q == kEigPowerLog2 - 1) ? w.M : ((q & 1) ? w.Btmp : w.B2);
+      note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, src, q == 0 ? w.bscale : nullptr, dst);
+      src = dst;
+    }
+  }
   note_launch(), k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
   const int64_t cnt = (int64_t)k * n;
   note_launch(), k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
