@@ -60,13 +60,15 @@ def _kernel_sources_digest() -> str:
 
 
 def _captured_traffic(workload: str):
-    """DRAM bytes per sweep launch from the committed ncu capture, or None if
-    there is none for this workload or the kernel sources changed since."""
+    """DRAM bytes of one Jacobi iteration (both sweep kernels) from the committed
+    ncu capture, or None if there is none for this workload or the kernel
+    sources changed since."""
     path = os.path.join(ROOT, "profiles", f"sweep_{workload}_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     ok = rec.get("kernel_sources_sha256") == _kernel_sources_digest()
+    ok = ok and rec.get("kernel") == "one Jacobi iteration: k_sweep_nbr + k_sweep_f32"
     return rec.get("dram_bytes_per_launch") if ok else None
 
 
@@ -236,6 +238,36 @@ def run_gpu(args):
     h2d = int(src.nbytes + dst.nbytes)
     d2h = int(pos_h.numel() * pos_h.element_size() + out_h.numel() * out_h.element_size())
 
+    # the plain FP64 sweep on the same device beside the FP32 one: both start
+    # from the PivotMDS layout of the same pivots, run the same iterations, and
+    # report their time per iteration and the stress they reach
+    fp64 = None
+    if not args.no_fp64:
+        g, P, _, _ = step(src_d, dst_d)
+        pos32, _ = ssm.ssm_pivotmds(g, P.dip, 32, True)
+        pos64, _ = ssm.ssm_pivotmds(g, P.dip, 64, True)
+        res = {}
+        for name, pos_p in (("f32", pos32), ("f64", pos64)):
+            ssm.ssm_iterate(g, P, pos_p.clone(), 2)  # warm-up (table setup, caches)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ssm.ssm_iterate(g, P, pos_p, iters, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st, _ = ssm.ssm_stress(g, pos_p, S, T, W["seed"])
+            res[name] = (e0.elapsed_time(e1) / iters, float(st.cpu()[3]))
+        fp64 = {
+            "iterations": iters,
+            "f32_ms_per_iteration": res["f32"][0],
+            "f64_ms_per_iteration": res["f64"][0],
+            "f32_speedup": res["f64"][0] / res["f32"][0],
+            "f32_stress_normalized": res["f32"][1],
+            "f64_stress_normalized": res["f64"][1],
+            "stress_rel_diff": abs(res["f32"][1] - res["f64"][1]) / res["f64"][1],
+            "note": "same pivots and PivotMDS start in each precision; stress on the bench's sampled pairs",
+        }
+
     # roofline of the sweep kernel (one launch = one Jacobi iteration)
     peak, peak_kind = _peaks()
     bytes_per_launch = 2 * k * n + 4 * (n + 1) + 8 * m + 8 * n + 8 * n
@@ -268,7 +300,7 @@ def run_gpu(args):
             "stage_ms": {st: round(v, 3) for st, v in stage_ms.items()},
         },
         "roofline": {
-            "kernel": "k_sweep_f32 (one Jacobi iteration)",
+            "kernel": "one Jacobi iteration: k_sweep_nbr + k_sweep_f32",
             "bound": "hbm",
             "achieved": achieved,
             "peak": peak,
@@ -280,6 +312,7 @@ def run_gpu(args):
             "launch_us": launch_s * 1e6,
         },
         "clocks": clocks,
+        "fp64_sweep": fp64,
         "e2e": {"value": e2e_value, "unit": "node-term updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
         "gpu_launches": timed_launches,
@@ -394,6 +427,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rgg256k")
     ap.add_argument("--iters", type=int, default=0, help="override the sweep count (0: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
