@@ -49,7 +49,8 @@ constexpr int kSweepThreads = 256;
 constexpr int kShortDeg = 32;   // neighbour rows up to this length: one thread
 constexpr int kMidDeg = 1024;   // up to this length: one warp; longer rows: one block
 constexpr size_t kSmemBudget = 200 * 1024;
-constexpr size_t kFullTabMax = 48 * 1024;  // bytes of the (w, w d) table of the full-table mode
+constexpr int kFullPlane = 6144;  // full-table mode: k (max d + 1) <= this; w and w d in two planes of this many floats
+constexpr unsigned kFullPlaneBytes = kFullPlane * 4u;
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
 #ifndef SSM_SWEEP_PREFETCH
@@ -72,7 +73,7 @@ struct SweepArgs {
   int32_t cnt_len;
   int32_t stab_len;       // 2 * cnt_len
   const float *stab;      // [stab_len] s by d, per pivot (global copy)
-  const float2 *wtab;     // [k][dmax+1] (w, w d) by pivot and distance (full-table mode)
+  const float *wtab;      // [2][kFullPlane]: w by pivot and distance ([k][dmax+1]), then w d (full-table mode)
   int32_t dmax;           // largest d_ip entry (full-table mode)
   const float *den;       // [n] deg(i) + sum_a w'_ia (full-table mode)
   const float2 *nb;       // [n] neighbour sums of this iteration (k_sweep_nbr)
@@ -103,6 +104,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
+// Programmatic dependent launch: the sweep's kernels are launched so that the
+// next one may start while the previous one drains; it waits here before it
+// touches anything the previous kernel writes (a no-op without that launch mode).
+__device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float lds_f32(unsigned addr) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
@@ -119,11 +125,22 @@ __device__ void finish_iteration(const SweepArgs &A, unsigned ntiles) {
   __syncthreads();
   if (s_ticket != gridDim.x - 1) return;
   __threadfence();
-  double num = 0.0, den = 0.0;
-  for (unsigned t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    num += __ldcg(A.tile_part + 2 * (size_t)t);
-    den += __ldcg(A.tile_part + 2 * (size_t)t + 1);
+  // four independent partial sums per thread keep loads in flight; they are
+  // added in a fixed order, so the result does not depend on timing
+  double nq[4] = {0.0, 0.0, 0.0, 0.0}, dq[4] = {0.0, 0.0, 0.0, 0.0};
+  const unsigned step = 4u * blockDim.x;
+  for (unsigned t0 = threadIdx.x; t0 < ntiles; t0 += step) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned t = t0 + (unsigned)q * blockDim.x;
+      if (t < ntiles) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(A.tile_part) + t);
+        nq[q] += v.x;
+        dq[q] += v.y;
+      }
+    }
   }
+  double num = (nq[0] + nq[1]) + (nq[2] + nq[3]), den = (dq[0] + dq[1]) + (dq[2] + dq[3]);
   num = warp_sum(num);
   den = warp_sum(den);
   if ((threadIdx.x & 31) == 0) {
@@ -156,20 +173,22 @@ __device__ __forceinline__ void edge_term(float xi, float yi, float2 q, float &s
   sy += fmaf(dy, inv, q.y);
 }
 
-// one lane walks a short row, four independent gathers in flight
+// one lane walks a short row in batches of eight: the batch's column indices
+// load together, then its eight positions, so a row of up to eight entries
+// costs two dependent memory latencies (terms still added in row order)
 __device__ __forceinline__ void light_row(const float2 *__restrict__ pin, const int32_t *__restrict__ colidx, int beg,
                                           int end, float xi, float yi, float &sx, float &sy) {
-  int t = beg;
-  for (; t + 4 <= end; t += 4) {
-    const int j0 = __ldg(colidx + t), j1 = __ldg(colidx + t + 1), j2 = __ldg(colidx + t + 2),
-              j3 = __ldg(colidx + t + 3);
-    const float2 q0 = pin[j0], q1 = pin[j1], q2 = pin[j2], q3 = pin[j3];
-    edge_term(xi, yi, q0, sx, sy);
-    edge_term(xi, yi, q1, sx, sy);
-    edge_term(xi, yi, q2, sx, sy);
-    edge_term(xi, yi, q3, sx, sy);
+  for (int t = beg; t < end; t += 8) {
+    int j[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) j[q] = t + q < end ? __ldg(colidx + t + q) : -1;
+    float2 x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = j[q] >= 0 ? pin[j[q]] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j[q] >= 0) edge_term(xi, yi, x[q], sx, sy);
   }
-  for (; t < end; ++t) edge_term(xi, yi, pin[__ldg(colidx + t)], sx, sy);
 }
 
 // the whole warp walks one row segment [b, e) around (hx, hy); the sums land in every lane
@@ -200,6 +219,7 @@ __global__ void __launch_bounds__(256) k_sweep_nbr(int32_t n, const int32_t *__r
                                                    int32_t nlong, const int32_t *__restrict__ long_rows, int32_t nmid,
                                                    const int32_t *__restrict__ mid_rows, float2 *__restrict__ nb,
                                                    const int32_t *__restrict__ stop) {
+  wait_previous_kernel();
   if (__ldcg(stop)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int b = blockIdx.x;
@@ -282,9 +302,19 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
   float4 *pxy = reinterpret_cast<float4 *>(smem);       // (-x, -x, -y, -y) per pivot
   uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
   float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
-  float2 *wtab = reinterpret_cast<float2 *>(pidx + A.k);  // full-table mode: (w, w d) by pivot and d
-  if (__ldcg(A.stop)) return;
+  float *wtab = reinterpret_cast<float *>(pidx + A.k);  // full-table mode: the two planes of A.wtab
   const int n = A.n, k = A.k;
+  // the weight tables do not depend on the previous kernels: load them first
+  if (SMEM)
+    for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
+  const unsigned wrow = 4u * (unsigned)(A.dmax + 1);  // bytes of one pivot's row of a plane
+  if (FULL)
+    for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) {
+      wtab[t] = __ldg(A.wtab + t);
+      wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
+    }
+  wait_previous_kernel();
+  if (__ldcg(A.stop)) return;
   // Table address of node distance d for pivot a: with c = bits(2^23 + min(d, D_a))
   // (a float whose low bits are the integer), addr = 4 c + base_a where
   // base_a = table start + 4 offset_a - 4 * 0x4B000000 (mod 2^32).
@@ -297,11 +327,6 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     pxy[a] = make_float4(-xy.x, -xy.x, -xy.y, -xy.y);
     pidx[a] = make_uint2(tab0 + 4u * soff - 4u * 0x4B000000u, 0x4B000000u | dcap);
   }
-  if (SMEM)
-    for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
-  const unsigned wrow = 8u * (unsigned)(A.dmax + 1);  // bytes of one pivot's (w, w d) row
-  if (FULL)
-    for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) wtab[t] = __ldg(A.wtab + t);
   const unsigned wtab0 = FULL ? (unsigned)__cvta_generic_to_shared(wtab) : 0u;
   __syncthreads();
 
@@ -337,26 +362,26 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     auto load_pair = [&](int a) -> unsigned { return __ldg(tp + (unsigned)a * 32u); };
     float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
     asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
-    // full-table mode accumulators, per node (lo, hi)
-    float wxl = 0.f, wxh = 0.f, wyl = 0.f, wyh = 0.f, bxl = 0.f, bxh = 0.f, byl = 0.f, byh = 0.f;
+    // full-table mode: w and w d of both nodes land in register pairs (the two
+    // planes sit a fixed kFullPlaneBytes apart), so every product is packed
     auto pivot_term_full = [&](int a, unsigned pk) {
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
       const unsigned tb = wtab0 + (unsigned)a * wrow;
-      const float2 tl = lds_f32x2(tb + 8u * (pk & 0xFFFFu));  // (w, w d) of the even node
-      const float2 th = lds_f32x2(tb + 8u * (pk >> 16));      // and of the odd node
+      const unsigned al = tb + 4u * (pk & 0xFFFFu), ah = tb + 4u * (pk >> 16);
+      const float2 w2 = make_float2(lds_f32(al), lds_f32(ah));
+      const float2 wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
       const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
       const float2 dx2 = __fadd2_rn(xi2, px2);
       const float2 dy2 = __fadd2_rn(yi2, py2);
       const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
-      const float bl = tl.y * rsqrt_approx(r2.x), bh = th.y * rsqrt_approx(r2.y);  // w d / r
-      wxl = fmaf(tl.x, P.x, wxl);
-      wxh = fmaf(th.x, P.x, wxh);
-      wyl = fmaf(tl.x, P.z, wyl);
-      wyh = fmaf(th.x, P.z, wyh);
-      bxl = fmaf(bl, dx2.x, bxl);
-      bxh = fmaf(bh, dx2.y, bxh);
-      byl = fmaf(bl, dy2.x, byl);
-      byh = fmaf(bh, dy2.y, byh);
+      float2 u2;
+      u2.x = rsqrt_approx(r2.x);
+      u2.y = rsqrt_approx(r2.y);
+      const float2 B2 = __fmul2_rn(wd2, u2);  // w d / r
+      wx2 = __ffma2_rn(w2, px2, wx2);
+      wy2 = __ffma2_rn(w2, py2, wy2);
+      bx2 = __ffma2_rn(B2, dx2, bx2);
+      by2 = __ffma2_rn(B2, dy2, by2);
     };
     auto pivot_term = [&](int a, unsigned pk) {
       if constexpr (FULL) {
@@ -416,13 +441,7 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       a0 += kPrefetch;
     }
     for (; a0 < k; ++a0) pivot_term(a0, load_pair(a0));
-    if constexpr (FULL) {
-      bx2 = make_float2(bxl, bxh);
-      by2 = make_float2(byl, byh);
-      wx2 = make_float2(wxl, wxh);
-      wy2 = make_float2(wyl, wyh);
-      den2 = make_float2(live0 ? __ldg(A.den + i0) : 0.f, live1 ? __ldg(A.den + i0 + 1) : 0.f);
-    }
+    if constexpr (FULL) den2 = make_float2(live0 ? __ldg(A.den + i0) : 0.f, live1 ? __ldg(A.den + i0 + 1) : 0.f);
     const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
     const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
 
@@ -497,27 +516,29 @@ __global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, con
   }
 }
 
-// full-table mode: wtab[a (dmax+1) + d] = (w, w d), w = s / d^2 with s as in
-// k_build_stab (0 for d < 2), rounded from double
+// full-table mode: wtab[a (dmax+1) + d] = w and wtab[kFullPlane + a (dmax+1) + d]
+// = w d, w = s / d^2 with s as in k_build_stab (0 for d < 2), rounded from double
 __global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict__ cnt_off,
-                             const uint32_t *__restrict__ cnt, float2 *__restrict__ wtab) {
+                             const uint32_t *__restrict__ cnt, float *__restrict__ wtab) {
   const int64_t total = (int64_t)k * (dmax + 1);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(t / (dmax + 1)), d = (int)(t - (int64_t)a * (dmax + 1));
     const int o = cnt_off[a], ecc = cnt_off[a + 1] - o - 1;
-    float2 e = make_float2(0.f, 0.f);
+    float w = 0.f, wd = 0.f;
     if (d >= 2) {
       const double sd = (double)cnt[o + min(d >> 1, ecc)], dd = (double)d;
-      e = make_float2((float)(sd / (dd * dd)), (float)(sd / dd));
+      w = (float)(sd / (dd * dd));
+      wd = (float)(sd / dd);
     }
-    wtab[t] = e;
+    wtab[t] = w;
+    wtab[kFullPlane + t] = wd;
   }
 }
 
 // full-table mode: den[i] = deg(i) + sum_{a = 0..k-1} w'_ia in FP32, pivots in
 // order (the sum the clamped mode forms inside every sweep)
 __global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *__restrict__ dtile,
-                            const float2 *__restrict__ wtab, const int32_t *__restrict__ rowptr,
+                            const float *__restrict__ wtab, const int32_t *__restrict__ rowptr,
                             float *__restrict__ den) {
   const unsigned lane = threadIdx.x & 31u;
   const int64_t ntiles = (n + 63) / 64;
@@ -527,9 +548,9 @@ __global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *
     float dl = 0.f, dh = 0.f;
     for (int a = 0; a < k; ++a) {
       const unsigned pk = __ldg(tp + (int64_t)a * 32);
-      const float2 *row = wtab + (int64_t)a * (dmax + 1);
-      dl += __ldg(&row[pk & 0xFFFFu].x);
-      dh += __ldg(&row[pk >> 16].x);
+      const float *row = wtab + (int64_t)a * (dmax + 1);
+      dl += __ldg(row + (pk & 0xFFFFu));
+      dh += __ldg(row + (pk >> 16));
     }
     const int64_t i0 = tile * 64 + 2 * lane;
     if (i0 < n) den[i0] = dl + (float)(rowptr[i0 + 1] - rowptr[i0]);
@@ -660,7 +681,7 @@ struct IterWs {
   float2 *nb;       // [n] neighbour sums
   int32_t *mid_rows, *long_rows;  // [n] rows longer than kShortDeg / kMidDeg
   unsigned *dtile;
-  float2 *wtab;   // full-table mode (w, w d) table
+  float *wtab;    // full-table mode: w and w d planes
   float *den;     // [n] full-table mode denominators
   unsigned *meta;  // [4] largest d_ip entry, medium rows, long rows
 };
@@ -677,7 +698,7 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.mid_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
   w.long_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
   w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + 63) / 64) * (size_t)k * 32);
-  w.wtab = precision == 64 ? nullptr : c.take<float2>(kFullTabMax / sizeof(float2));
+  w.wtab = precision == 64 ? nullptr : c.take<float>(2 * (size_t)kFullPlane);
   w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
   w.meta = c.take<unsigned>(4);
   return c.size();
@@ -746,7 +767,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     SSM_TRY_CUDA(cudaMemcpyAsync(meta, w.meta, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SSM_TRY_CUDA(cudaStreamSynchronize(s));
     const unsigned dmax = meta[0];
-    const bool full = (size_t)k * ((size_t)dmax + 1) * sizeof(float2) <= kFullTabMax;
+    const bool full = (size_t)k * ((size_t)dmax + 1) <= (size_t)kFullPlane;
     A.dmax = (int32_t)dmax;
     A.wtab = w.wtab;
     A.den = w.den;
@@ -761,7 +782,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     }
     const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2));
     if (full) {
-      smem = piv + (size_t)k * ((size_t)dmax + 1) * sizeof(float2);
+      smem = piv + 2 * (size_t)kFullPlaneBytes;
       kern = (const void *)k_sweep_f32<kFull>;
     } else {
       const size_t tab = (size_t)(2 * cnt_len) * sizeof(float);
@@ -783,9 +804,30 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   for (int t = 0; t < iters; ++t) {
     const bool even = (t & 1) == 0;
     void *pin = even ? pos : w.tmp, *pout = even ? w.tmp : pos;
-    if (precision == 32)
-      note_launch(), k_sweep_nbr<<<nbr_blocks, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pin, nlong, w.long_rows,
-                                                             nmid, w.mid_rows, w.nb, w.stop);
+    if (precision == 32) {
+      // both kernels of an iteration are launched as programmatic dependents of
+      // the kernel before them (each waits in wait_previous_kernel)
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nbr_blocks);
+      cfg.blockDim = dim3(256);
+      cfg.stream = s;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      note_launch();
+      SSM_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_sweep_nbr, n, rowptr, colidx, (const float2 *)pin, nlong,
+                                      (const int32_t *)w.long_rows, nmid, (const int32_t *)w.mid_rows, w.nb,
+                                      (const int32_t *)w.stop));
+      cfg.gridDim = dim3(blocks);
+      cfg.blockDim = dim3(kSweepThreads);
+      cfg.dynamicSmemBytes = smem;
+      void *args[] = {&A, &pin, &pout};
+      note_launch();
+      SSM_TRY_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
+      continue;
+    }
     void *args[] = {&A, &pin, &pout};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(blocks), dim3(kSweepThreads), args, smem, s));
