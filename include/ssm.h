@@ -170,6 +170,21 @@ int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
                  double *eig, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
+ * The dense contraction of PivotMDS (Algorithm 1 line 3): the integer Gram
+ * matrix of the squared pivot distances,
+ *   G[a][b] = sum_i d_ia^2 d_ib^2   (exact, 128-bit unsigned),
+ * on which ssm_pivotmds applies the double centring at the k x k level.
+ * Writes g_lo[k*k], g_hi[k*k] (device, uint64): entry a*k + b holds the low
+ * and high 64 bits of G[a][b] for a <= b; entries with a > b are zero.  The
+ * call zeroes both arrays itself.  Runs on the tensor cores (4-bit digit
+ * planes in FP16, FP32 accumulation of exact integers).  1 <= k <= 1024.
+ * Device errors: SSM_E_TIMEOUT (a tensor-core wait ran out).
+ * ------------------------------------------------------------------- */
+size_t ssm_gram_workspace(int32_t n, int32_t k);
+int ssm_gram(int32_t n, int32_t k, const uint16_t *dip, uint64_t *g_lo, uint64_t *g_hi, int32_t *status,
+             void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
  * Stress majorization (Eq. 4; Algorithm 1 lines 5-10), Jacobi schedule:
  * each iteration computes every x_i^{t+1} from X^t,
  *   x_i^{t+1} = [ sum_{j in N(i)} (x_j + (x_i - x_j)/r_ij)

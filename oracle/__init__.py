@@ -157,6 +157,28 @@ def adapted_weights(dip: np.ndarray, region: np.ndarray) -> np.ndarray:
     return w
 
 
+def gram(dip: np.ndarray) -> np.ndarray:
+    """The dense contraction inside PivotMDS (Algorithm 1, line 3) before any
+    centring: G[a][b] = sum_i d_ia^2 d_ib^2 over the pivot-major table, as
+    exact Python integers (object array [k, k]).  Each squared distance is
+    split into 16-bit halves, s = 2^16 h + l, so that every partial product
+    sum h_a h_b, h_a l_b, l_a l_b is an integer below 2^53 and the float64
+    matrix products are exact; the halves are recombined in integers."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    k, n = dip.shape
+    if n >= (1 << 21):
+        raise OracleError(-1, "gram: n too large for exact float64 partial sums")
+    sq = dip.astype(np.uint64) ** 2
+    h = (sq >> np.uint64(16)).astype(np.float64)
+    l = (sq & np.uint64(0xFFFF)).astype(np.float64)
+    hh, hl, lh, ll = h @ h.T, h @ l.T, l @ h.T, l @ l.T
+    G = np.empty((k, k), dtype=object)
+    for a in range(k):
+        for b in range(k):
+            G[a, b] = ((int(hh[a, b]) << 32) + ((int(hl[a, b]) + int(lh[a, b])) << 16) + int(ll[a, b]))
+    return G
+
+
 def pivotmds(dip: np.ndarray, return_b: bool = False):
     """PivotMDS layout [n][2] and the two eigenvalues (and B = C^T C if asked)."""
     dip = np.ascontiguousarray(dip, dtype=np.uint16)

@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
-    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -67,6 +67,8 @@ def lib():
                 "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
                 "ssm_aggregate_noalloc": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, v]),
+                "ssm_gram_workspace": (sz, [i32, i32]),
+                "ssm_gram": (ctypes.c_int, [i32, i32, v, v, v, v, v, sz, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
@@ -222,6 +224,23 @@ def ssm_aggregate_noalloc(dip: torch.Tensor, region: torch.Tensor, cnt_off: torc
     _rc(L.ssm_aggregate_noalloc(n, k, _ptr(dip), _ptr(region), _ptr(cnt_off), _ptr(cnt), cap, ctypes.byref(out),
                                 _ptr(status), _stream(stream)), "ssm_aggregate_noalloc")
     return int(out.value)
+
+
+def ssm_gram(dip: torch.Tensor, stream=None, check: bool = True):
+    """Exact Gram matrix of the squared pivot distances, G[a][b] = sum_i d_ia^2 d_ib^2
+    for a <= b, as two int64 tensors [k, k] holding the low and high 64 bits
+    (reinterpret as unsigned); entries below the diagonal are zero."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    lo = torch.empty((k, k), dtype=torch.int64, device=dev)
+    hi = torch.empty((k, k), dtype=torch.int64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_gram_workspace(n, k), dev)
+    _rc(L.ssm_gram(n, k, _ptr(dip), _ptr(lo), _ptr(hi), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_gram")
+    if check:
+        ssm_check(st, "ssm_gram", stream)
+    return lo, hi
 
 
 def ssm_pivotmds(g: Graph, dip: torch.Tensor, precision: int = 32, rescale: bool = True, stream=None,

@@ -6,7 +6,8 @@
 // so the only O(n k^2) work is the integer Gram matrix G = Delta^T Delta.
 // G is accumulated exactly (128-bit integers), which makes it independent of
 // summation order; everything after it is k x k FP64:
-//   k_gram      G = Delta^T Delta (upper tiles, 64x64 per block, node chunks)
+//   k_dmax      largest d_ia (how many digits the Gram needs)
+//   k_gram_tc   G = Delta^T Delta on the tensor cores (gram_tc.cu)
 //   k_colsum    s_a
 //   k_prepare_b B = 1/4 J (G - s s^T/n) J
 //   k_square    M = (B / max|B|)^(2^kEigPowerLog2) by FP64 squarings (grid)
@@ -19,13 +20,10 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gram_tc.cuh"
 
 namespace ssm {
 
-constexpr int kGT = 64;          // Gram tile edge
-constexpr int kGStage = 32;      // nodes per shared-memory stage
-constexpr int kGChunk = 8192;    // nodes per block
-constexpr int kGPad = kGT + 4;   // padded row (keeps 16-byte alignment)
 #ifndef SSM_EIG_P
 #define SSM_EIG_P 4
 #endif
@@ -40,93 +38,6 @@ constexpr int kEigPowerLog2 = SSM_EIG_POWER_LOG2;
 constexpr int kEigThreads = 256;
 constexpr int kMaxPivotsMds = 1024;
 constexpr int kEigScratch = (kEigThreads / 32) * (kEigP * (kEigP + 1) / 2);  // doubles for block_sum
-
-// ------------------------------------------------------------- Gram matrix
-__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long v) {
-  lo += v;
-  hi += (lo < v) ? 1ull : 0ull;
-}
-
-__global__ void __launch_bounds__(256) k_gram(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
-                                              unsigned long long *__restrict__ Glo,
-                                              unsigned long long *__restrict__ Ghi) {
-  __shared__ __align__(16) unsigned sA[kGStage][kGPad];
-  __shared__ __align__(16) unsigned sB[kGStage][kGPad];
-  __shared__ unsigned s_dmax;
-  const int T = (k + kGT - 1) / kGT;
-  int p = blockIdx.x, ta = 0;
-  while (p >= T - ta) { p -= T - ta; ++ta; }
-  const int tb = ta + p;
-  const int i_begin = blockIdx.y * kGChunk;
-  const int i_end = min(n, i_begin + kGChunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-
-  unsigned long long lo[4][4], hi[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) lo[r][c] = hi[r][c] = 0ull;
-
-  for (int i0 = i_begin; i0 < i_end; i0 += kGStage) {
-    if (threadIdx.x == 0) s_dmax = 0;
-    __syncthreads();
-    unsigned dm = 0;
-    for (int q = threadIdx.x; q < kGStage * kGT; q += blockDim.x) {
-      const int c = q % kGStage, r = q / kGStage;  // consecutive threads: consecutive nodes
-      const int i = i0 + c;
-      const int a = ta * kGT + r, b = tb * kGT + r;
-      const unsigned da = (a < k && i < i_end) ? __ldg(dip + (size_t)a * n + i) : 0u;
-      const unsigned db = (b < k && i < i_end) ? __ldg(dip + (size_t)b * n + i) : 0u;
-      sA[c][r] = da * da;
-      sB[c][r] = db * db;
-      dm = max(dm, max(da, db));
-    }
-    atomicMax(&s_dmax, dm);
-    __syncthreads();
-    if (s_dmax <= 23170u) {
-      // 32 products of values below 2^29 stay below 2^64: accumulate the
-      // stage with plain 64-bit multiply-adds, then fold into 128 bits
-      unsigned long long st[4][4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) st[r][c] = 0ull;
-#pragma unroll 4
-      for (int c = 0; c < kGStage; ++c) {
-        const uint4 av = *reinterpret_cast<const uint4 *>(&sA[c][ty * 4]);
-        const uint4 bv = *reinterpret_cast<const uint4 *>(&sB[c][tx * 4]);
-        const unsigned a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) st[r][q] += (unsigned long long)a4[r] * b4[q];
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) add128(lo[r][q], hi[r][q], st[r][q]);
-    } else {
-      for (int c = 0; c < kGStage; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            add128(lo[r][q], hi[r][q], (unsigned long long)sA[c][ty * 4 + r] * sB[c][tx * 4 + q]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int a = ta * kGT + ty * 4 + r, b = tb * kGT + tx * 4 + q;
-      if (a >= k || b >= k || a > b) continue;
-      const size_t o = (size_t)a * k + b;
-      const unsigned long long old = atomicAdd(Glo + o, lo[r][q]);
-      const unsigned long long carry = (old + lo[r][q] < old) ? 1ull : 0ull;
-      if (hi[r][q] + carry) atomicAdd(Ghi + o, hi[r][q] + carry);
-    }
-}
 
 // s_a = sum_i d_ia^2 (exact: below 2^63 for n < 2^31)
 // s[a] = sum_i d_ia^2 (exact; s zeroed by the caller).  Blocks take chunks of
@@ -758,7 +669,36 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   return c.size();
 }
 
+// G = Delta^T Delta into Glo/Ghi (zeroed here) and the largest d_ip entry into *dmax
+static int launch_gram(int32_t n, int32_t k, const uint16_t *dip, unsigned *dmax, unsigned long long *Glo,
+                       unsigned long long *Ghi, int32_t *status, cudaStream_t s) {
+  const size_t kk = (size_t)k * k;
+  SSM_TRY_CUDA(cudaMemsetAsync(Glo, 0, kk * sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(Ghi, 0, kk * sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned), s));
+  // the largest distance decides how many 4-bit digits the tensor-core Gram needs
+  const int64_t cnt = (int64_t)k * n;
+  note_launch(), k_dmax<<<std::min<int64_t>((cnt + 255) / 256, (int64_t)num_sms() * 8), 256, 0, s>>>(cnt, dip, dmax);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return launch_gram_tc(n, k, dip, dmax, Glo, Ghi, status, s);
+}
+
 }  // namespace ssm
+
+SSM_API size_t ssm_gram_workspace(int32_t n, int32_t k) {
+  if (n < 1 || k < 1) return 0;
+  return 256;
+}
+
+SSM_API int ssm_gram(int32_t n, int32_t k, const uint16_t *dip, uint64_t *g_lo, uint64_t *g_hi, int32_t *status,
+                     void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || !dip || !g_lo || !g_hi || !status || !ws) return fail(SSM_E_ARG, "ssm_gram: null pointer or n < 1");
+  if (k < 1 || k > kMaxPivotsMds) return fail(SSM_E_ARG, "ssm_gram: need 1 <= k <= %d", kMaxPivotsMds);
+  if (ws_bytes < ssm_gram_workspace(n, k)) return fail(SSM_E_NOMEM, "ssm_gram: workspace %zu bytes, need 256", ws_bytes);
+  return launch_gram(n, k, dip, static_cast<unsigned *>(ws), reinterpret_cast<unsigned long long *>(g_lo),
+                     reinterpret_cast<unsigned long long *>(g_hi), status, s);
+}
 
 SSM_API size_t ssm_pivotmds_workspace(int32_t n, int32_t k) {
   if (n < 1 || k < 1) return 0;
@@ -781,13 +721,11 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_pivotmds: workspace %zu bytes, need %zu", ws_bytes, c.size());
   const size_t kk = (size_t)k * k;
   const int sms = num_sms();
-  SSM_TRY_CUDA(cudaMemsetAsync(w.Glo, 0, kk * sizeof(unsigned long long), s));
-  SSM_TRY_CUDA(cudaMemsetAsync(w.Ghi, 0, kk * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(w.done, 0, sizeof(unsigned), s));
-  SSM_TRY_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(unsigned), s));
-  const int T = (k + kGT - 1) / kGT;
-  dim3 ggrid((unsigned)(T * (T + 1) / 2), (unsigned)((n + kGChunk - 1) / kGChunk));
-  note_launch(), k_gram<<<ggrid, 256, 0, s>>>(n, k, dip, w.Glo, w.Ghi);
+  {
+    const int rc = launch_gram(n, k, dip, w.dmax, w.Glo, w.Ghi, status, s);
+    if (rc) return rc;
+  }
   SSM_TRY_CUDA(cudaMemsetAsync(w.s, 0, (size_t)k * sizeof(unsigned long long), s));
   {
     const int64_t tasks = (int64_t)k * ((n + kColChunk - 1) / kColChunk);
@@ -809,8 +747,6 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
     }
   }
   note_launch(), k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
-  const int64_t cnt = (int64_t)k * n;
-  note_launch(), k_dmax<<<std::min<int64_t>((cnt + 255) / 256, sms * 8), 256, 0, s>>>(cnt, dip, w.dmax);
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   const size_t psm = (size_t)k * sizeof(float4);
   note_launch(), k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);

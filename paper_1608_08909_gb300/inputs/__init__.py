@@ -11,6 +11,8 @@ generators stand in for them:
 * ``rgg(n, mean_deg, seed)``  -- random geometric graph, largest component kept
 * ``ba(n, attach, seed)``     -- Barabasi-Albert preferential attachment
 * ``induced_prefix(...)``     -- the subgraph induced by nodes 0..n_keep-1
+* ``distance_table(k, n, dmax, seed)`` -- a uniform random k x n uint16 table
+  (values 0..dmax, dmax present) for exactness tests of the dense contraction
 
 Each returns ``(n, src, dst)`` with int32 numpy edge arrays.  This module holds
 none of the layout method's arithmetic; it is the one piece both the CUDA path
@@ -125,6 +127,16 @@ def induced_prefix(n_keep: int, src: np.ndarray, dst: np.ndarray):
         lib.gen_free(ctypes.cast(s, ctypes.c_void_p))
         lib.gen_free(ctypes.cast(d, ctypes.c_void_p))
     return n_keep, a, b
+
+
+def distance_table(k: int, n: int, dmax: int, seed: int) -> np.ndarray:
+    """Uniform random pivot-major uint16 table [k, n] with entries in 0..dmax
+    and dmax itself at one seeded position (not a metric; it exercises every
+    bit of every squared entry)."""
+    rng = np.random.default_rng(seed)
+    t = rng.integers(0, dmax + 1, size=(k, n), dtype=np.int64)
+    t[rng.integers(0, k), rng.integers(0, n)] = dmax
+    return t.astype(np.uint16)
 
 
 # Named workloads (the sizes of the configurations this library is measured on)

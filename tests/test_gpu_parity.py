@@ -214,6 +214,38 @@ def test_aggregate_bit_exact(name, k):
 
 # ------------------------------------------------------------------ a4/a5 PivotMDS
 
+def _gram_u128(lo, hi):
+    lo = lo.cpu().numpy().view(np.uint64)
+    hi = hi.cpu().numpy().view(np.uint64)
+    return lo, hi
+
+
+@pytest.mark.parametrize("k,n,dmax,offset", [
+    (200, 20001, 3, 0),        # one 4-bit digit, odd n (two-byte loads), ragged second tile
+    (200, 20001, 15, 0),       # two digits
+    (130, 33000, 200, 0),      # four digits, even n (four-byte loads), three node ranges
+    (130, 33000, 200, 1),      # the same table two bytes off a 4-byte boundary
+    (129, 16389, 3000, 0),     # six digits, a node range of 5 nodes
+    (256, 5000, 65534, 0),     # eight digits (16 digit blocks), full tiles
+    (1, 70, 65534, 0),         # one pivot: G is one number, above 2^64
+    (3, 1, 9, 0),              # one node
+])
+def test_gram_exact(k, n, dmax, offset):
+    """The tensor-core Gram matrix, every entry a <= b bit-exact in 128 bits,
+    zero below the diagonal."""
+    dip = I.distance_table(k, n, dmax, 11 + k + n)
+    buf = torch.zeros(k * n + offset, dtype=torch.int16, device=DEV)
+    buf[offset:] = torch.from_numpy(dip.view(np.int16).reshape(-1)).to(DEV)
+    gd = buf[offset:].view(k, n)
+    lo, hi = _gram_u128(*ssm.ssm_gram(gd))
+    G = O.gram(dip)
+    iu = np.triu_indices(k)
+    got = [(int(h) << 64) | int(l) for h, l in zip(hi[iu], lo[iu])]
+    assert got == list(G[iu])
+    il = np.tril_indices(k, -1)
+    assert not lo[il].any() and not hi[il].any()
+
+
 @pytest.mark.parametrize("name,k", [("grid32", 50), ("rgg", 100), ("ba", 64), ("btree", 33), ("path", 7)])
 def test_pivotmds_matches_oracle(name, k):
     """Eigenvalues to 1e-10; positions to FP32 rounding where the eigenvector is

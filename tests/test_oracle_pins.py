@@ -330,6 +330,32 @@ def test_pivotmds_eigs_match_library():
         np.testing.assert_allclose(pos[:, r], C @ v, rtol=1e-8, atol=1e-8 * np.abs(pos).max())
 
 
+def test_gram_brute_force_integers():
+    """The exact Gram matrix against Python-integer loops, on values that fill
+    all 32 bits of d^2 (where float64 sums of the full products would round)."""
+    dip = I.distance_table(4, 11, 65534, 7)
+    G = O.gram(dip)
+    for a in range(4):
+        for b in range(4):
+            assert G[a, b] == sum(int(dip[a, i]) ** 2 * int(dip[b, i]) ** 2 for i in range(11))
+    assert G[0, 0] > 2 ** 64  # the 128-bit range is reached
+
+
+def test_gram_centres_to_pivotmds_b():
+    """Double centring commutes with the contraction: C^T C = 1/4 J (G - s s^T / n) J
+    with s_a = sum_i d_ia^2 and J the k x k centring matrix, against the B
+    that the oracle's PivotMDS forms from the centred C."""
+    n, s, d = I.rgg(400, 8.0, 3)
+    g = O.build_csr(n, s, d)
+    dip = O.pivot_dist(g, O.maxmin(g, 20))
+    _, _, B = O.pivotmds(dip, return_b=True)
+    G = O.gram(dip).astype(np.float64)
+    sa = (dip.astype(np.float64) ** 2).sum(1)
+    k = dip.shape[0]
+    J = np.eye(k) - 1.0 / k
+    np.testing.assert_allclose(0.25 * J @ (G - np.outer(sa, sa) / n) @ J, B, rtol=1e-9, atol=1e-9 * np.abs(B).max())
+
+
 def test_pivotmds_path_is_exact_1d():
     """On a path d_ij = |i-j| is Euclidean in 1-D, so classical MDS is exact:
     x_i is proportional to i - mean(i) and the second eigenvalue vanishes."""
