@@ -36,7 +36,11 @@
 //    thread per row of up to kShortDeg entries, one warp per row up to
 //    kMidDeg, one block per longer row (each sum in a fixed order); the
 //    tile kernel reads them with the node's other per-node data;
-//  * warps take 64-node tiles from an atomic counter.
+//  * warps take 64-node tiles from an atomic counter; when there are too few
+//    tiles to keep every warp busy to the end, each tile's pivots are split
+//    into nsplit ranges taken as separate tasks, and the last range of a tile
+//    to finish adds the ranges' partial sums in range order (independent of
+//    timing) and updates the tile's nodes.
 // The relative change ||X^{t+1}-X^t||/||X^t|| is reduced in FP64 in a fixed
 // order by the last block to finish.
 #include <algorithm>
@@ -60,7 +64,7 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_MIN_BLOCKS 3
 #endif
 #ifndef SSM_SWEEP_FULL_MIN_BLOCKS
-#define SSM_SWEEP_FULL_MIN_BLOCKS 3
+#define SSM_SWEEP_FULL_MIN_BLOCKS 4
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
 
@@ -80,6 +84,10 @@ struct SweepArgs {
   unsigned *tile_ctr;     // next task to hand out
   unsigned *done_ctr;     // blocks finished
   double *tile_part;      // [ntiles][2] (sum dx^2, sum x^2) per tile
+  int32_t nsplit;         // pivot ranges per tile (1: a warp takes whole tiles)
+  int32_t psplit;         // pivots per range
+  float2 *part;           // [5][ntiles * nsplit][32] partial sums of the ranges (nsplit > 1)
+  unsigned *arrive;       // [ntiles] ranges of the tile finished so far (nsplit > 1)
   int32_t *stop;          // set when the relative change fell below tol
   int32_t *iters_done;
   double *rel_change;
@@ -332,15 +340,18 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 
   const unsigned lane = threadIdx.x & 31u;
   const unsigned ntiles = (unsigned)((n + 63) / 64);
+  const unsigned nsplit = (unsigned)A.nsplit, ntasks = ntiles * nsplit;
   // loop-invariant constant pairs, kept in registers (opaque to the compiler so
   // it does not rebuild them from immediates inside the pivot loop)
   float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
   asm volatile("" : "+f"(kMagic2.x), "+f"(kMagic2.y));
   for (;;) {
-    unsigned tile = 0;
-    if (lane == 0) tile = atomicAdd(A.tile_ctr, 1u);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= ntiles) break;
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(A.tile_ctr, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= ntasks) break;
+    const unsigned tile = task / nsplit, split = task - tile * nsplit;
+    const int a_lo = (int)split * A.psplit, a_hi = min(k, a_lo + A.psplit);
 
     // ---- a tile of 64 nodes: this lane owns i0 and i0 + 1
     const int i0 = (int)(tile * 64u + 2u * lane);
@@ -424,11 +435,11 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       den2 = __fadd2_rn(den2, W2);
     };
     unsigned buf[kPrefetch];
-    int a0 = 0;
-    if (k >= 2 * kPrefetch) {
+    int a0 = a_lo;
+    if (a_hi - a_lo >= 2 * kPrefetch) {
 #pragma unroll
-      for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(t);
-      for (; a0 + 2 * kPrefetch <= k; a0 += kPrefetch) {
+      for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(a0 + t);
+      for (; a0 + 2 * kPrefetch <= a_hi; a0 += kPrefetch) {
 #pragma unroll
         for (int t = 0; t < kPrefetch; ++t) {
           const unsigned pk = buf[t];
@@ -440,7 +451,42 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       for (int t = 0; t < kPrefetch; ++t) pivot_term(a0 + t, buf[t]);
       a0 += kPrefetch;
     }
-    for (; a0 < k; ++a0) pivot_term(a0, load_pair(a0));
+    for (; a0 < a_hi; ++a0) pivot_term(a0, load_pair(a0));
+    if (nsplit > 1) {
+      // publish this range's sums; the last range of the tile adds all of them
+      // in range order and goes on to update the nodes
+      const size_t stride = (size_t)ntasks * 32u;
+      float2 *pp = A.part + (size_t)task * 32u + lane;
+      pp[0] = wx2;
+      pp[stride] = wy2;
+      pp[2 * stride] = bx2;
+      pp[3 * stride] = by2;
+      if (!FULL) pp[4 * stride] = den2;
+      __threadfence();
+      __syncwarp();
+      unsigned prior = 0;
+      if (lane == 0) prior = atomicAdd(A.arrive + tile, 1u);
+      prior = __shfl_sync(0xffffffffu, prior, 0);
+      if (prior != nsplit - 1) continue;
+      __threadfence();
+      if (lane == 0) A.arrive[tile] = 0u;  // ready for the next iteration
+      const float2 *q = A.part + (size_t)tile * nsplit * 32u + lane;
+      float2 s0 = __ldcg(q), s1 = __ldcg(q + stride), s2 = __ldcg(q + 2 * stride), s3 = __ldcg(q + 3 * stride);
+      float2 s4 = FULL ? make_float2(0.f, 0.f) : __ldcg(q + 4 * stride);
+      for (unsigned r = 1; r < nsplit; ++r) {
+        const float2 *qr = q + (size_t)r * 32u;
+        s0 = __fadd2_rn(s0, __ldcg(qr));
+        s1 = __fadd2_rn(s1, __ldcg(qr + stride));
+        s2 = __fadd2_rn(s2, __ldcg(qr + 2 * stride));
+        s3 = __fadd2_rn(s3, __ldcg(qr + 3 * stride));
+        if (!FULL) s4 = __fadd2_rn(s4, __ldcg(qr + 4 * stride));
+      }
+      wx2 = s0;
+      wy2 = s1;
+      bx2 = s2;
+      by2 = s3;
+      den2 = s4;
+    }
     if constexpr (FULL) den2 = make_float2(live0 ? __ldg(A.den + i0) : 0.f, live1 ? __ldg(A.den + i0 + 1) : 0.f);
     const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
     const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
@@ -684,7 +730,24 @@ struct IterWs {
   float *wtab;    // full-table mode: w and w d planes
   float *den;     // [n] full-table mode denominators
   unsigned *meta;  // [4] largest d_ip entry, medium rows, long rows
+  float2 *part;    // pivot-range partial sums (few-tile graphs), split_cap tasks
+  unsigned *arrive;  // [tiles]
+  int64_t split_cap;  // tasks the partial sums have room for (0: no splitting)
 };
+
+// Splitting tiles into pivot ranges pays only when there are fewer tiles than
+// about two per resident warp; the sweep kernel keeps at most kSplitWarpsPerSm
+// warps per SM, so larger graphs get no scratch for it.
+#ifndef SSM_SWEEP_SPLIT_TASKS
+#define SSM_SWEEP_SPLIT_TASKS 4
+#endif
+constexpr int kSplitTasksPerWarp = SSM_SWEEP_SPLIT_TASKS;  // target tasks per resident warp (0: never split)
+constexpr int kMaxSplit = 4;
+constexpr int kSplitWarpsPerSm = 32;
+static int64_t split_capacity(int32_t n) {
+  const int64_t tiles = ((int64_t)n + 63) / 64;
+  return tiles < 2 * (int64_t)num_sms() * kSplitWarpsPerSm ? kMaxSplit * tiles : 0;
+}
 
 static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t k, int64_t cnt_len,
                             int32_t precision) {
@@ -701,6 +764,9 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.wtab = precision == 64 ? nullptr : c.take<float>(2 * (size_t)kFullPlane);
   w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
   w.meta = c.take<unsigned>(4);
+  w.split_cap = precision == 64 ? 0 : split_capacity(n);
+  w.part = w.split_cap ? c.take<float2>(5 * 32 * (size_t)w.split_cap) : nullptr;
+  w.arrive = w.split_cap ? c.take<unsigned>((size_t)((n + 63) / 64)) : nullptr;
   return c.size();
 }
 
@@ -736,6 +802,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
   A.stab = w.stab; A.wtab = nullptr; A.dmax = 0; A.den = nullptr; A.nb = w.nb;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
+  A.nsplit = 1; A.psplit = k; A.part = w.part; A.arrive = w.arrive;
   A.iters_done = iters_done; A.rel_change = rel_change; A.tol = tol; A.status = status;
 
   const int sms = num_sms();
@@ -798,6 +865,17 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   if (per_sm < 1) return fail(SSM_E_ARG, "ssm_iterate: %zu bytes of shared memory do not fit", smem);
   const int64_t want = (tiles + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+  if (precision == 32 && w.split_cap > 0 && kSplitTasksPerWarp > 0) {
+    // about kSplitTasksPerWarp tasks per resident warp, ranges of at least 2 kPrefetch pivots
+    const int64_t warps = (int64_t)blocks * (kSweepThreads / 32);
+    int64_t S = tiles >= 2 * warps ? 1 : (kSplitTasksPerWarp * warps + tiles - 1) / tiles;
+    S = std::min<int64_t>({S, (int64_t)kMaxSplit, std::max<int64_t>(1, k / (2 * kPrefetch)), w.split_cap / tiles});
+    if (S > 1) {
+      A.psplit = (int32_t)((k + S - 1) / S);
+      A.nsplit = (int32_t)((k + A.psplit - 1) / A.psplit);
+      SSM_TRY_CUDA(cudaMemsetAsync(w.arrive, 0, (size_t)tiles * sizeof(unsigned), s));
+    }
+  }
 
   const int32_t nmid = (int32_t)meta[1], nlong = (int32_t)meta[2];
   const unsigned nbr_blocks = (unsigned)(nlong + (nmid + 7) / 8 + (n + 255) / 256);
