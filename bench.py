@@ -418,6 +418,75 @@ def cpu_baseline_from(value, workload, k, iters):
                        f"{SAMPLE_SOURCES} stress sources; stages scaled by their cost model")}
 
 
+# ----------------------------------------------------------------------------- serving
+
+def run_serve(args):
+    """Continuous-batching serving: seeded Poisson stream of layout requests of
+    mixed families, n log-uniform in [1k, 200k], k = 100, 100 iterations,
+    admitted under an HBM budget; capacity measured closed-loop, then open-loop
+    replays at fractions of it, each reporting p50/p99 arrival-to-result latency."""
+    import numpy as np
+    import torch
+
+    import paper_1608_08909_gb300 as ssm
+    from paper_1608_08909_gb300 import inputs as I
+    from paper_1608_08909_gb300 import serve as SV
+
+    torch.cuda.set_device(0)
+    reqs = I.request_stream(args.serve_jobs, 20000, n_min=1000, n_max=200000)
+    jobs, terms = [], []
+    for i, r in enumerate(reqs):
+        n, s, d = I.mixed_graph(r["family"], r["n"], r["seed"])
+        jobs.append(SV.LayoutJob(n=n, src=s, dst=d, k=100, iters=100, tag=i))
+        terms.append(100 * (n * min(100, n) + 2 * len(s)))
+    gaps = [r["gap"] for r in reqs]
+    budget = int(args.serve_budget_gb * (1 << 30))
+    launches0 = ssm.kernel_launches()
+    with SV.LayoutServer(budget, slots=args.serve_slots) as srv:
+        for j in jobs[:3]:  # warm-up: library load, first-use costs
+            srv.submit(j).result()
+        torch.cuda.synchronize()
+        ncap = min(len(jobs), args.serve_capacity_jobs)
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            res = [f.result() for f in [srv.submit(j) for j in jobs[:ncap]]]
+            t1 = time.perf_counter()
+            capacity = ncap / (t1 - t0)
+            levels = []
+            for frac in args.serve_loads:
+                rate = frac * capacity
+                t2 = time.perf_counter()
+                futs = SV.replay(srv, jobs, gaps, rate)
+                out = [f.result() for f in futs]
+                t3 = time.perf_counter()
+                p = SV.latency_percentiles(out)
+                levels.append({"load": frac, "arrival_rate_per_s": round(rate, 3),
+                               "throughput_per_s": round(len(out) / (t3 - t2), 3),
+                               "p50_ms": round(p["p50"] * 1e3, 2), "p99_ms": round(p["p99"] * 1e3, 2),
+                               "node_term_updates_per_s": round(sum(terms) / (t3 - t2), 1),
+                               "peak_concurrent": srv.peak_active})
+        peak_reserved = srv.peak_reserved
+    ns = np.array([j.n for j in jobs])
+    top = levels[-1] if levels else None
+    line = {
+        "metric": "serving: layout requests/s (p50/p99 latency)",
+        "value": round(capacity, 3), "unit": "requests/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve", "requests": len(jobs), "families": list(I.FAMILIES),
+                   "n_range": [int(ns.min()), int(ns.max())], "n_mean": round(float(ns.mean()), 1),
+                   "k": 100, "iters": 100, "hbm_budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
+                   "capacity_requests": ncap},
+        "capacity_closed_loop_per_s": round(capacity, 3),
+        "levels": levels,
+        "p50_ms": top["p50_ms"] if top else None, "p99_ms": top["p99_ms"] if top else None,
+        "peak_reserved_gb": round(peak_reserved / (1 << 30), 3),
+        "gpu_launches": ssm.kernel_launches() - launches0,
+        "clocks": clk.summary(),
+        "vs_baseline": None,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,11 +497,19 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="override the sweep count (0: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead of a single graph")
+    ap.add_argument("--serve-jobs", type=int, default=300)
+    ap.add_argument("--serve-capacity-jobs", type=int, default=100)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -329,7 +329,7 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
   const size_t smem = sizeof(int2) * 2 * kSoloMax + sizeof(FlatSmem);
-  SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_maxmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_maxmin));
   const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, smem, 1);
   if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: kernel cannot be resident");
   void *args[] = {&A};
@@ -660,7 +660,7 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     }
     const void *kern = adj4 ? (const void *)k_bfs_cta<true> : (const void *)k_bfs_cta<false>;
     const size_t smem = (size_t)((n + 31) / 32) * 4;
-    SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SSM_TRY_CUDA(allow_dynamic_smem(kern));
     void *args[] = {&B};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(slots), dim3(kCtaThreads), args, smem, s));

@@ -280,5 +280,9 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64
 
 // Persistent cooperative launch sized to the device: blocks = SMs * resident.
 int cooperative_blocks(const void *kernel, int threads, size_t smem, int max_per_sm);
+// Lets `kernel` take as much dynamic shared memory as the device allows.  The
+// attribute is the same on every call, so calls on concurrent host threads
+// (each launching with its own size) cannot undo one another.
+cudaError_t allow_dynamic_smem(const void *kernel);
 
 }  // namespace ssm

@@ -369,7 +369,7 @@ int launch_gram_tc(int32_t n, int32_t k, const uint16_t *dip, const unsigned *dm
   const size_t smem = gram_tc_smem();
   // two distances per 4-byte load when every row starts on a 4-byte boundary
   const int wide = ((n & 1) == 0 && ((uintptr_t)dip & 3u) == 0) ? 1 : 0;
-  SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_gram_tc));
   note_launch(), k_gram_tc<<<num_sms(), kTcThreads, smem, s>>>(n, k, dip, wide, dmax, Glo, Ghi, status);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;

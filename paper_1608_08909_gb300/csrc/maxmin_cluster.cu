@@ -354,8 +354,7 @@ static McShape mc_shape(int32_t n) {
       (void)cudaGetLastError();
       continue;
     }
-    if (cudaFuncSetAttribute((const void *)k_maxmin_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    if (allow_dynamic_smem((const void *)k_maxmin_cluster) != cudaSuccess) {
       (void)cudaGetLastError();
       continue;
     }

@@ -734,7 +734,7 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   note_launch(), k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
   const int P = std::min(kEigP, (int)k);
   const size_t esm = (3 * (size_t)k * P + kEigScratch) * sizeof(double);  // V, Y, saved Y, scratch
-  SSM_TRY_CUDA(cudaFuncSetAttribute((const void *)k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_eigen));
   note_launch(), k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
   const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
   // M = (B/max|B|)^(2^kEigPowerLog2) by repeated squaring

@@ -859,7 +859,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     }
     tiles = (n + 63) / 64;
   }
-  SSM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SSM_TRY_CUDA(allow_dynamic_smem(kern));
   int per_sm = 0;
   SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
   if (per_sm < 1) return fail(SSM_E_ARG, "ssm_iterate: %zu bytes of shared memory do not fit", smem);

@@ -13,6 +13,10 @@ generators stand in for them:
 * ``induced_prefix(...)``     -- the subgraph induced by nodes 0..n_keep-1
 * ``distance_table(k, n, dmax, seed)`` -- a uniform random k x n uint16 table
   (values 0..dmax, dmax present) for exactness tests of the dense contraction
+* ``mixed_graph(family, n, seed)`` / ``request_stream(count, seed, ...)`` -- the
+  mixed families (near-square grid, random binary tree, RGG of mean degree 6)
+  and a seeded stream of layout requests (log-uniform sizes, unit-rate
+  exponential inter-arrival gaps) for the serving and batching workloads
 
 Each returns ``(n, src, dst)`` with int32 numpy edge arrays.  This module holds
 none of the layout method's arithmetic; it is the one piece both the CUDA path
@@ -137,6 +141,37 @@ def distance_table(k: int, n: int, dmax: int, seed: int) -> np.ndarray:
     t = rng.integers(0, dmax + 1, size=(k, n), dtype=np.int64)
     t[rng.integers(0, k), rng.integers(0, n)] = dmax
     return t.astype(np.uint16)
+
+
+FAMILIES = ("grid", "btree", "rgg")
+
+
+def mixed_graph(family: str, n: int, seed: int):
+    """One graph of the mixed serving / batching families, about n nodes:
+    a near-square grid (rows = floor(sqrt(n))), a random binary tree (node i
+    hangs below a uniformly chosen earlier node with fewer than two children),
+    or the largest component of an RGG of mean degree 6."""
+    if family == "grid":
+        r = max(1, int(np.floor(np.sqrt(n))))
+        return grid(r, max(1, n // r))
+    if family == "btree":
+        return random_btree(n, seed)
+    if family == "rgg":
+        return rgg(n, 6.0, seed)
+    raise KeyError(family)
+
+
+def request_stream(count: int, seed: int, n_min: int = 1000, n_max: int = 200000):
+    """Seeded layout requests: a list of dicts (family, n, seed, gap) with n
+    log-uniform in [n_min, n_max], the family drawn uniformly from FAMILIES and
+    gap an exponential inter-arrival time of unit rate (scale by 1/rate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        out.append(dict(family=FAMILIES[int(rng.integers(0, len(FAMILIES)))], n=n,
+                        seed=int(rng.integers(1, 2 ** 62)), gap=float(rng.exponential(1.0))))
+    return out
 
 
 # Named workloads (the sizes of the configurations this library is measured on)
