@@ -203,7 +203,7 @@ int ssm_gram(int32_t n, int32_t k, const uint16_t *dip, uint64_t *g_lo, uint64_t
  * (after its first kernels) to read the largest d_ip entry and the number of
  * rows longer than 32 and 1024 entries on the host: when k * (max d + 1)
  * weight pairs fit in shared memory the sweep uses a full (w', w' d) table,
- * otherwise a table of s clamped at 2 ecc_a + 1; the neighbour sums of each
+ * otherwise a table of s clamped at 2 ecc_a + 2; the neighbour sums of each
  * iteration are taken by one thread, warp or block per row by length.
  * ------------------------------------------------------------------- */
 size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision);
@@ -212,6 +212,41 @@ int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *coli
                 const uint32_t *cnt, int64_t cnt_len, void *pos, int32_t precision, int32_t iters,
                 double tol, int32_t *iters_done, double *rel_change, int32_t *status,
                 void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Batched sweeps: the Jacobi sweeps of Eq. 4 (Algorithm 1 lines 5-10) for G
+ * independent small graphs in one CUDA-graph launch of one persistent kernel.
+ * Each graph is prepared as for ssm_iterate (CSR, pivots, d_ip, cnt_off, cnt)
+ * and packed into shared arrays; ssm_batch_graph gives, per graph, its sizes
+ * and where its pieces start in the packed arrays (element offsets):
+ *   rowptr[row_off .. row_off + n]   local row offsets (0 .. 2m, into colidx at col_off)
+ *   colidx[col_off ..]               local node ids 0..n-1
+ *   pivots[piv_off .. + k]           local node ids
+ *   dip[dip_off .. + k n]            pivot-major uint16, as ssm_pivot_bfs writes it
+ *   cnt_off[cnt_off_off .. + k + 1]  local offsets into cnt at cnt_base, cnt_len = cnt_off[k]
+ *   pos[2 node_off .. + 2 n]         float (x, y) pairs, updated in place
+ * Graphs have 1 <= n <= 12288 nodes and 1 <= k <= min(n, 1024) pivots.  Each
+ * graph runs `iters` iterations (FP32, the clamped s-table form of the
+ * single-graph sweep, neighbour terms in ascending column order) in one block
+ * with its positions in shared memory; rel_change[g] (device double) gets the
+ * relative change of graph g's last iteration.  threads = 128, 256 or 512
+ * fixes the block size; 0 tunes it on this batch (a few iterations per
+ * candidate on a scratch copy of the positions, timed with CUDA events; the
+ * chosen size goes to *threads_used, host, if not NULL).  Synchronous when
+ * tuning, else asynchronous on `stream` (the descriptor array is copied
+ * before the call returns).  Workspace: ssm_batch_iterate_workspace(G, graphs).
+ * Device errors: SSM_E_NUMERIC (non-finite weights), SSM_E_GRAPH (a pivot or
+ * column id outside its graph).
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int32_t n, k, cnt_len, reserved;
+  int64_t node_off, row_off, col_off, piv_off, dip_off, cnt_off_off, cnt_base;
+} ssm_batch_graph;
+size_t ssm_batch_iterate_workspace(int32_t G, const ssm_batch_graph *graphs);
+int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const int32_t *rowptr, const int32_t *colidx,
+                      const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
+                      float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t *threads_used,
+                      int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
  * Full stress of a layout (Eq. 1, w_ij = d_ij^-2) with optimal scaling

@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
-    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -70,6 +70,8 @@ def lib():
                 "ssm_gram_workspace": (sz, [i32, i32]),
                 "ssm_gram": (ctypes.c_int, [i32, i32, v, v, v, v, v, sz, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
+                "ssm_batch_iterate_workspace": (sz, [i32, v]),
+                "ssm_batch_iterate": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, i32, v, i32, v, v, v, sz, v]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
                 "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
@@ -307,6 +309,76 @@ def ssm_stress(g: Graph, pos: torch.Tensor, nsources: int = 0, ntargets: int = 0
     if check:
         ssm_check(work.status, "ssm_stress", stream)
     return work.out, work.sums
+
+
+_BATCH_DTYPE = None
+
+
+def _batch_dtype():
+    """numpy layout of ssm_batch_graph (include/ssm.h)."""
+    import numpy as np
+    global _BATCH_DTYPE
+    if _BATCH_DTYPE is None:
+        _BATCH_DTYPE = np.dtype([("n", "<i4"), ("k", "<i4"), ("cnt_len", "<i4"), ("reserved", "<i4"),
+                                 ("node_off", "<i8"), ("row_off", "<i8"), ("col_off", "<i8"), ("piv_off", "<i8"),
+                                 ("dip_off", "<i8"), ("cnt_off_off", "<i8"), ("cnt_base", "<i8")])
+        assert _BATCH_DTYPE.itemsize == 72
+    return _BATCH_DTYPE
+
+
+def ssm_batch_iterate(items, iters: int, threads: int = 0, stream=None, check: bool = True):
+    """Jacobi sweeps for a batch of small graphs in one launch (ssm_batch_iterate).
+
+    items: list of (Graph, Pivots, pos float32 [n, 2]) on one device; every
+    pos is updated in place.  Returns (rel_change float64 [G] device tensor,
+    the block size used)."""
+    import numpy as np
+    L = lib()
+    G = len(items)
+    dev = items[0][2].device
+    desc = np.zeros(G, dtype=_batch_dtype())
+    node = row = col = piv = dipo = offo = cbase = 0
+    for i, (g, p, pos) in enumerate(items):
+        if pos.dtype != torch.float32 or pos.shape != (g.n, 2):
+            raise ValueError("batch positions must be float32 [n, 2]")
+        desc[i] = (g.n, p.k, p.cnt.numel(), 0, node, row, col, piv, dipo, offo, cbase)
+        node += g.n
+        row += g.n + 1
+        col += g.colidx.numel()
+        piv += p.k
+        dipo += p.k * g.n
+        offo += p.k + 1
+        cbase += p.cnt.numel()
+    import contextlib
+    ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+    with ctx:
+        return _batch_call(L, items, desc, col, iters, threads, stream, check, dev)
+
+
+def _batch_call(L, items, desc, col, iters, threads, stream, check, dev):
+    G = len(items)
+    rowptr = torch.cat([g.rowptr for g, _, _ in items])
+    colidx = torch.cat([g.colidx for g, _, _ in items]) if col else torch.zeros(1, dtype=torch.int32, device=dev)
+    pivots = torch.cat([p.pivots for _, p, _ in items])
+    dip = torch.cat([p.dip.view(torch.int16).reshape(-1) for _, p, _ in items])
+    cnt_off = torch.cat([p.cnt_off for _, p, _ in items])
+    cnt = torch.cat([p.cnt.view(torch.int32) for _, p, _ in items])
+    pos_all = torch.cat([pos for _, _, pos in items])
+    rel = torch.zeros(G, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    dp = desc.ctypes.data_as(ctypes.c_void_p)
+    ws = _ws(L.ssm_batch_iterate_workspace(G, dp), dev)
+    used = ctypes.c_int32(0)
+    _rc(L.ssm_batch_iterate(G, dp, _ptr(rowptr), _ptr(colidx), _ptr(pivots), _ptr(dip), _ptr(cnt_off), _ptr(cnt),
+                            _ptr(pos_all), iters, _ptr(rel), threads, ctypes.byref(used), _ptr(st), _ptr(ws), ws.numel(),
+                            _stream(stream)), "ssm_batch_iterate")
+    if check:
+        ssm_check(st, "ssm_batch_iterate", stream)
+    o = 0
+    for g, _, pos in items:
+        pos.copy_(pos_all[o:o + g.n])
+        o += g.n
+    return rel, int(used.value)
 
 
 def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, device="cuda", stream=None):

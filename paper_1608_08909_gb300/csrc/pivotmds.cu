@@ -432,6 +432,9 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
     return q0 > 0.0 ? sqrt(fmax(e[0], e[1])) / q0 : 0.0;
   };
 
+  __shared__ int s_stuck;
+  double best = 1e300;
+  int since_best = 0;
   int it = 0;
   for (; it < maxit; ++it) {
     rayleigh_ritz(M);
@@ -441,12 +444,36 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
     const double r = residual_b();
     for (int t = threadIdx.x; t < k * P; t += blockDim.x) Y[t] = sm[2 * (size_t)k * P + kEigScratch + t];
     __syncthreads();
-    if (threadIdx.x == 0) s_done = r <= tol ? 1 : 0;
+    if (threadIdx.x == 0) {
+      s_done = r <= tol ? 1 : 0;
+      // when lambda_2 / lambda_1 is small the second pair sinks below FP64
+      // precision in the powers of B and the residual stalls: go on with B
+      if (r < 0.9 * best) {
+        best = r;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      s_stuck = since_best >= 50 ? 1 : 0;
+    }
     __syncthreads();
-    if (s_done) break;
+    if (s_done || s_stuck) break;
     for (int t = threadIdx.x; t < k * P; t += blockDim.x) V[t] = Y[t];  // next basis: orthonormalised M W
     __syncthreads();
     orthonormalise(k, P, V, scratch, 0x9e37ull + (unsigned long long)it);
+  }
+  // subspace iteration on B itself (rate lambda_{P+1} / lambda_2 for the
+  // second vector, no powers to drown it) until the same test passes
+  if (!s_done) {
+    for (++it; it < maxit; ++it) {
+      const double r = rayleigh_ritz(B);  // V <- Ritz vectors of B, Y <- B V
+      if (threadIdx.x == 0) s_done = r <= tol ? 1 : 0;
+      __syncthreads();
+      if (s_done) break;
+      for (int t = threadIdx.x; t < k * P; t += blockDim.x) V[t] = Y[t];
+      __syncthreads();
+      orthonormalise(k, P, V, scratch, 0x7f4aull + (unsigned long long)it);
+    }
   }
   const double last_res = rayleigh_ritz(B);
   // top-2 Ritz vectors are columns 0, 1 of V; sign: largest |entry| positive

@@ -22,7 +22,7 @@
 //    to the numerator.  The denominator deg(i) + sum_a w'_ia does not change
 //    between iterations and is summed once per ssm_iterate call;
 //  * clamped mode (large distances): s comes from a per-pivot table indexed
-//    directly by d (0 for d < 2, cnt[min(d/2, ecc)] up to d = 2 ecc + 1, then
+//    directly by d (0 for d < 2, cnt[min(d/2, ecc)] up to d = 2 ecc + 2, then
 //    |R(a)|), and the term uses one rsqrt per node: with q = d^2 r^2,
 //    u = q^{-1/2}, B = s u = w d / r and W = B u r^2 = s / d^2 = w, it adds
 //    W x_p + B (x_i - x_p) to the numerator and W to the denominator;
@@ -75,7 +75,7 @@ struct SweepArgs {
   const unsigned *dtile;  // d_ip re-laid as [tile][pivot][32 words of two nodes] (64-node tiles)
   const uint32_t *cnt;
   int32_t cnt_len;
-  int32_t stab_len;       // 2 * cnt_len
+  int32_t stab_len;       // 2 cnt_len + k
   const float *stab;      // [stab_len] s by d, per pivot (global copy)
   const float *wtab;      // [2][kFullPlane]: w by pivot and distance ([k][dmax+1]), then w d (full-table mode)
   int32_t dmax;           // largest d_ip entry (full-table mode)
@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     const int p = __ldg(A.pivots + a);
     const float2 xy = pin[p];
     const int o = __ldg(A.cnt_off + a), e = __ldg(A.cnt_off + a + 1);
-    const unsigned soff = 2u * (unsigned)o, dcap = 2u * (unsigned)(e - o) - 1u;  // D_a = 2 ecc_a + 1
+    // pivot a's table: d = 0 .. D_a = 2 ecc_a + 2 at 2 off_a + a (D_a >= 2, so a region
+    // of the pivot alone, ecc_a = 0, still gets s = |R(a)| = 1 at d >= 2)
+    const unsigned soff = 2u * (unsigned)o + (unsigned)a, dcap = 2u * (unsigned)(e - o);
     pxy[a] = make_float4(-xy.x, -xy.x, -xy.y, -xy.y);
     pidx[a] = make_uint2(tab0 + 4u * soff - 4u * 0x4B000000u, 0x4B000000u | dcap);
   }
@@ -552,13 +554,14 @@ __global__ void k_tile_dip(int32_t n, int32_t k, const uint16_t *__restrict__ di
 }
 
 
-// s-by-d table: stab[2 off_a + d] = (d >= 2) ? cnt[off_a + min(d/2, ecc_a)] : 0, d = 0..2 ecc_a + 1
+// s-by-d table: stab[2 off_a + a + d] = (d >= 2) ? cnt[off_a + min(d/2, ecc_a)] : 0,
+// d = 0 .. 2 ecc_a + 2 (larger d clamp to the last entry, |R(a)|)
 __global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, const uint32_t *__restrict__ cnt,
                              float *__restrict__ stab) {
   for (int a = blockIdx.x; a < k; a += gridDim.x) {
     const int o = cnt_off[a], ecc = cnt_off[a + 1] - o - 1;
-    for (int d = threadIdx.x; d <= 2 * ecc + 1; d += blockDim.x)
-      stab[2 * o + d] = d >= 2 ? (float)cnt[o + min(d >> 1, ecc)] : 0.f;
+    for (int d = threadIdx.x; d <= 2 * ecc + 2; d += blockDim.x)
+      stab[2 * o + a + d] = d >= 2 ? (float)cnt[o + min(d >> 1, ecc)] : 0.f;
   }
 }
 
@@ -756,7 +759,7 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.ctr = c.take<unsigned>(2);
   w.stop = c.take<int32_t>(1);
   w.tile_part = c.take<double>(2 * ((size_t)n / 32 + 2));
-  w.stab = c.take<float>((size_t)(2 * cnt_len));
+  w.stab = c.take<float>((size_t)(2 * cnt_len + k));
   w.nb = precision == 64 ? nullptr : c.take<float2>((size_t)n);
   w.mid_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
   w.long_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
@@ -799,7 +802,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
 
   SweepArgs A;
   A.n = n; A.k = k; A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.cnt_off = cnt_off;
-  A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len);
+  A.dip = dip; A.dtile = w.dtile; A.cnt = cnt; A.cnt_len = (int32_t)cnt_len; A.stab_len = (int32_t)(2 * cnt_len + k);
   A.stab = w.stab; A.wtab = nullptr; A.dmax = 0; A.den = nullptr; A.nb = w.nb;
   A.tile_ctr = w.ctr; A.done_ctr = w.ctr + 1; A.tile_part = w.tile_part; A.stop = w.stop;
   A.nsplit = 1; A.psplit = k; A.part = w.part; A.arrive = w.arrive;
@@ -852,7 +855,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
       smem = piv + 2 * (size_t)kFullPlaneBytes;
       kern = (const void *)k_sweep_f32<kFull>;
     } else {
-      const size_t tab = (size_t)(2 * cnt_len) * sizeof(float);
+      const size_t tab = (size_t)(2 * cnt_len + k) * sizeof(float);
       tsm = piv + tab <= kSmemBudget;
       smem = piv + (tsm ? tab : 0);
       kern = tsm ? (const void *)k_sweep_f32<kClampSmem> : (const void *)k_sweep_f32<kClampGlobal>;

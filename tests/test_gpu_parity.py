@@ -284,6 +284,26 @@ def test_pivotmds_matches_oracle(name, k):
         assert _norm_err(pos.cpu().numpy(), O.rescale(og, opos)) < 1e-9
 
 
+@pytest.mark.parametrize("n0,seed", [(83, 2573530203214907681), (725, 3306426093002437330)])
+def test_pivotmds_small_second_eigenvalue(n0, seed):
+    """Small RGGs whose lambda_2 / lambda_1 is below 1e-2: the second pair sinks
+    below FP64 precision in the powers of B, and the solver finishes on B
+    itself; eigenvalues to 1e-10, positions to FP32 / FP64 rounding."""
+    n, s, d = I.mixed_graph("rgg", n0, seed)
+    k = max(2, min(100, n // 4))
+    og = O.build_csr(n, s, d)
+    dip = O.pivot_dist(og, O.maxmin(og, k, 0))
+    opos, oeig, B = O.pivotmds(dip, return_b=True)
+    lam = np.linalg.eigvalsh(B)[::-1]
+    assert lam[1] < 0.03 * lam[0]
+    g = _gpu_graph(n, s, d)
+    for prec, tol in ((32, 2e-6), (64, 1e-9)):
+        pos, eig = ssm.ssm_pivotmds(g, torch.from_numpy(dip).to(DEV), precision=prec, rescale=False)
+        eig = eig.cpu().numpy()
+        np.testing.assert_allclose(eig[:2], oeig, rtol=1e-10)
+        assert _norm_err(pos.cpu().numpy().astype(np.float64), opos) < tol
+
+
 # ------------------------------------------------------------------ a6/a7 sweep
 
 def _gpu_pivots(k, prep):
@@ -372,6 +392,34 @@ def test_sweep_fp32_both_weight_table_modes(k):
     ssm.ssm_iterate(g, P, pos, 1)
     opos, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x0.astype(np.float64))
     assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
+
+
+def test_sweep_fp32_single_node_regions():
+    """Pivots whose region is the pivot alone (ecc = 0) still weigh every node at
+    distance d >= 2 with s = |R(a)| = 1 (w' = 1/d^2), in the clamped-table mode
+    (a 2000-node path, so k (max d + 1) is far above the full table) of the
+    single-graph sweep and in the batched sweep."""
+    n, s, d = I.path(2000)
+    og = O.build_csr(n, s, d)
+    piv = np.array(list(range(9)) + [1000, 1999], np.int32)
+    k = len(piv)
+    dip = O.pivot_dist(og, piv)
+    reg = O.regions(dip)
+    ecc, off, cnt = O.histograms(dip, reg)
+    assert (np.asarray(ecc)[:8] == 0).all()
+    w = O.adapted_weights(dip, reg)
+    rng = np.random.default_rng(5)
+    x0 = rng.normal(size=(n, 2)).astype(np.float32)
+    want, _ = O.sweep_jacobi(og, piv, dip, w, x0.astype(np.float64))
+    g = _gpu_graph(n, s, d)
+    P = ssm.Pivots(k, torch.from_numpy(piv).to(DEV), torch.from_numpy(dip).to(DEV), torch.from_numpy(reg).to(DEV),
+                   torch.from_numpy(np.asarray(off).astype(np.int32)).to(DEV), torch.from_numpy(cnt).to(DEV))
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_iterate(g, P, pos, 1)
+    assert _norm_err(pos.cpu().numpy(), want) < 1e-5
+    pos = torch.from_numpy(x0.copy()).to(DEV)
+    ssm.ssm_batch_iterate([(g, P, pos)], 1)
+    assert _norm_err(pos.cpu().numpy(), want) < 1e-5
 
 
 @pytest.mark.parametrize("name,k", [("rgg", 100), ("ba", 64), ("btree", 33)])
