@@ -292,11 +292,20 @@ struct EigOut {
 // times faster per iteration) with a Rayleigh-Ritz step every iteration;
 // a final Rayleigh-Ritz step with B itself gives the eigenvalues and the
 // reported residual.
+// The k x k products (A V, one warp per row) are spread over the blocks of a
+// cooperative grid: each block writes its rows into Yg (two alternating
+// buffers), and after a grid barrier every block copies the whole product
+// into its shared memory.  Everything else -- Rayleigh-Ritz, residuals,
+// Gram-Schmidt, the convergence decisions -- every block computes on its own
+// identical copy, so the blocks stay in step without further exchange; block
+// 0 writes the results.
 __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, const double *__restrict__ B,
                                                        const double *__restrict__ M,
                                                        const unsigned long long *__restrict__ s,
                                                        double *__restrict__ vout /* [2][k] */,
                                                        EigOut *__restrict__ out, double *__restrict__ eig_user,
+                                                       double *__restrict__ Yg /* [2][k][P] */,
+                                                       BarrierState *__restrict__ bar,
                                                        int32_t *__restrict__ status, int maxit, double tol) {
   extern __shared__ __align__(16) double sm[];
   const int P = min(kEigP, k);
@@ -313,12 +322,14 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
   if (threadIdx.x == 0) s_done = 0;
   __syncthreads();
 
-  // one Rayleigh-Ritz step with matrix A on span(V): V <- Ritz vectors,
-  // Y <- A V, H diagonal <- Ritz values (descending); returns the relative
-  // residual max_{j<2} ||A v_j - h_j v_j|| / |h_0|
-  auto rayleigh_ritz = [&](const double *__restrict__ A) -> double {
+  // Y[:, 0..ncols) = A V[:, 0..ncols) over the grid (see above); false if a
+  // grid barrier gave up (status is set, every block stops)
+  int nprod = 0;
+  auto product = [&](const double *__restrict__ A, int ncols) -> bool {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = warp; r < k; r += nwarp) {  // Y = A V, one warp per row
+    double *yg = Yg + (size_t)(nprod & 1) * k * P;
+    ++nprod;
+    for (int r = blockIdx.x * nwarp + warp; r < k; r += gridDim.x * nwarp) {
       double acc[kEigP];
 #pragma unroll
       for (int q = 0; q < kEigP; ++q) acc[q] = 0.0;
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
         const double av = __ldg(arow + c);
 #pragma unroll
         for (int q = 0; q < kEigP; ++q)
-          if (q < P) acc[q] += av * V[c * P + q];
+          if (q < ncols) acc[q] += av * V[c * P + q];
       }
 #pragma unroll
       for (int q = 0; q < kEigP; ++q)
@@ -336,9 +347,24 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
       if (lane == 0)
 #pragma unroll
         for (int q = 0; q < kEigP; ++q)
-          if (q < P) Y[r * P + q] = acc[q];
+          if (q < ncols) yg[r * P + q] = acc[q];
     }
+    if (gridDim.x > 1) {
+      if (!grid_barrier(bar, status)) return false;
+    } else {
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < k * P; t += blockDim.x)
+      if ((t % P) < ncols) Y[t] = __ldcg(yg + t);
     __syncthreads();
+    return true;
+  };
+
+  // one Rayleigh-Ritz step with matrix A on span(V): V <- Ritz vectors,
+  // Y <- A V, H diagonal <- Ritz values (descending); returns the relative
+  // residual max_{j<2} ||A v_j - h_j v_j|| / |h_0|, or -1 if a grid barrier gave up
+  auto rayleigh_ritz = [&](const double *__restrict__ A) -> double {
+    if (!product(A, P)) return -1.0;
     double h[kEigP * (kEigP + 1) / 2];  // H = V^T Y, upper triangle
 #pragma unroll
     for (int q = 0; q < kEigP * (kEigP + 1) / 2; ++q) h[q] = 0.0;
@@ -397,26 +423,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
   // the Rayleigh quotients q_j = v_j^T B v_j (the powers of B in M shrink the
   // second pair's share, so a test on M alone would stop early for it)
   auto residual_b = [&]() -> double {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = warp; r < k; r += nwarp) {  // Y[:, 0..1] = B V[:, 0..1], one warp per row
-      double a0 = 0.0, a1 = 0.0;
-      const double *brow = B + (size_t)r * k;
-      for (int c = lane; c < k; c += 32) {
-        const double bv = __ldg(brow + c);
-        a0 += bv * V[c * P + 0];
-        if (P > 1) a1 += bv * V[c * P + 1];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      }
-      if (lane == 0) {
-        Y[r * P + 0] = a0;
-        if (P > 1) Y[r * P + 1] = a1;
-      }
-    }
-    __syncthreads();
+    if (!product(B, min(2, P))) return -1.0;  // Y[:, 0..1] = B V[:, 0..1]
     double q[2] = {0.0, 0.0};
     for (int r = threadIdx.x; r < k; r += blockDim.x)
       for (int j = 0; j < 2 && j < P; ++j) q[j] += V[r * P + j] * Y[r * P + j];
@@ -437,11 +444,12 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
   int since_best = 0;
   int it = 0;
   for (; it < maxit; ++it) {
-    rayleigh_ritz(M);
+    if (rayleigh_ritz(M) < 0.0) return;
     // Y = M W is kept for the next basis; the test on B uses the V columns only
     for (int t = threadIdx.x; t < k * P; t += blockDim.x) sm[2 * (size_t)k * P + kEigScratch + t] = Y[t];
     __syncthreads();
     const double r = residual_b();
+    if (r < 0.0) return;
     for (int t = threadIdx.x; t < k * P; t += blockDim.x) Y[t] = sm[2 * (size_t)k * P + kEigScratch + t];
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -467,6 +475,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
   if (!s_done) {
     for (++it; it < maxit; ++it) {
       const double r = rayleigh_ritz(B);  // V <- Ritz vectors of B, Y <- B V
+      if (r < 0.0) return;
       if (threadIdx.x == 0) s_done = r <= tol ? 1 : 0;
       __syncthreads();
       if (s_done) break;
@@ -476,6 +485,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
     }
   }
   const double last_res = rayleigh_ritz(B);
+  if (last_res < 0.0 || blockIdx.x != 0) return;  // block 0 writes the results
   // top-2 Ritz vectors are columns 0, 1 of V; sign: largest |entry| positive
   __shared__ int s_big[2];
   if (threadIdx.x < 2) {
@@ -609,12 +619,20 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
       xi = pos[i];
     }
     if (e - b <= 32) {
-      for (int t = b; t < e; ++t) {
-        const int j = __ldg(colidx + t);
-        if (j <= i) continue;
-        const T2 xj = pos[j];
-        const R dx = xi.x - xj.x, dy = xi.y - xj.y;
-        acc += (double)sqrt(dx * dx + dy * dy);
+      // eight column indices, then their eight positions, in flight together
+      for (int t = b; t < e; t += 8) {
+        int j[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) j[q] = t + q < e ? __ldg(colidx + t + q) : -1;
+        T2 xj[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xj[q] = j[q] > i ? pos[j[q]] : xi;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (j[q] > i) {
+            const R dx = xi.x - xj[q].x, dy = xi.y - xj[q].y;
+            acc += (double)sqrt(dx * dx + dy * dy);
+          }
       }
     }
     unsigned longs = __ballot_sync(0xffffffffu, e - b > 32);
@@ -644,10 +662,17 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
     s_ticket = atomicAdd(done, 1u);
   }
   __syncthreads();
-  if (s_ticket != gridDim.x - 1 || threadIdx.x != 0) return;
+  if (s_ticket != gridDim.x - 1) return;
+  // the last block adds the block sums: a fixed share per thread, then a fixed tree
   __threadfence();
+  double t = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double tot = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(part + b);
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) tot += red[w];
   const double m = (double)__ldg(rowptr + n) * 0.5;
   if (!(tot > 0.0) || !isfinite(tot)) {
     dev_fail(status, SSM_E_NUMERIC);
@@ -673,6 +698,8 @@ struct MdsWs {
   double *B, *B2, *Btmp, *M, *bscale, *rowmean, *vv, *part, *scale;
   EigOut *eo;
   unsigned *done, *dmax;
+  double *Yg;
+  BarrierState *bar;
 };
 
 static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
@@ -693,6 +720,8 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.eo = c.take<EigOut>(1);
   w.done = c.take<unsigned>(1);
   w.dmax = c.take<unsigned>(1);
+  w.Yg = c.take<double>(2 * (size_t)k * kEigP);
+  w.bar = c.take<BarrierState>(1);
   return c.size();
 }
 
@@ -773,7 +802,17 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
       src = dst;
     }
   }
-  note_launch(), k_eigen<<<1, kEigThreads, esm, s>>>(n, k, w.B, w.M, w.s, w.vv, w.eo, eig, status, 2000, 1e-12);
+  {
+    // one warp per row of the k x k products: as many blocks as the rows need, all resident
+    const int want = (k + kEigThreads / 32 - 1) / (kEigThreads / 32);
+    const int eblocks = std::max(1, std::min(want, cooperative_blocks((const void *)k_eigen, kEigThreads, esm, 1)));
+    SSM_TRY_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(BarrierState), s));
+    int maxit = 2000;
+    double tol = 1e-12;
+    void *args[] = {&n, &k, &w.B, &w.M, &w.s, &w.vv, &w.eo, &eig, &w.Yg, &w.bar, &status, &maxit, &tol};
+    note_launch();
+    SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_eigen, dim3(eblocks), dim3(kEigThreads), args, esm, s));
+  }
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   const size_t psm = (size_t)k * sizeof(float4);
   note_launch(), k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);
