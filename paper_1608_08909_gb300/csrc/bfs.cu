@@ -355,6 +355,9 @@ size_t maxmin_workspace(int32_t n, int64_t m2) {
 #ifndef SSM_CTA_SLOTS
 #define SSM_CTA_SLOTS 4
 #endif
+#ifndef SSM_CTA_BATCH
+#define SSM_CTA_BATCH 4
+#endif
 #ifndef SSM_ADJ4_MAX_MB
 #define SSM_ADJ4_MAX_MB 48
 #endif
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
         const unsigned e = base + lane;
         const int2 r = e < cc ? __ldcg(qin + e) : make_int2(0, 0);
         if (ADJ4) {
-          warp_for_each_edge4_batched<4>(
+          warp_for_each_edge4_batched<SSM_CTA_BATCH>(
               r.x, r.y, A.adj,
               [&](int, int4 ed) {
                 const unsigned bit = 1u << ((unsigned)ed.x & 31u);
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
                 }
               });
         } else {
-          warp_for_each_neighbor_batched<4>(
+          warp_for_each_neighbor_batched<SSM_CTA_BATCH>(
               r.x, r.y, A.colidx,
               [&](int, int, int v) {
                 const unsigned bit = 1u << ((unsigned)v & 31u);

@@ -563,21 +563,28 @@ __global__ void __launch_bounds__(256) k_project(int32_t n, int32_t k, const uin
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
     unsigned long long rs = 0;
     const uint16_t *col = dip + i;
-    for (int a = 0; a < k; ++a) {
-      const unsigned d = __ldg(col + (size_t)a * n);
-      const unsigned dd = d * d;
-      rs += dd;
-      const float4 v = sv[a];
-      if (!BIG) {
-        const float df = (float)dd;  // exact below 2^24
-        ff_madd(xh, xl, df, v.x, v.y);
-        ff_madd(yh, yl, df, v.z, v.w);
-      } else {
-        const float dh = (float)(dd & 0xFFFFF000u), dl = (float)(dd & 0xFFFu);  // both exact
-        ff_madd(xh, xl, dh, v.x, v.y);
-        ff_madd(xh, xl, dl, v.x, v.y);
-        ff_madd(yh, yl, dh, v.z, v.w);
-        ff_madd(yh, yl, dl, v.z, v.w);
+    // eight pivots' distances in flight per thread, then added in pivot order
+    for (int a0 = 0; a0 < k; a0 += 8) {
+      unsigned dq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dq[q] = a0 + q < k ? (unsigned)__ldg(col + (size_t)(a0 + q) * n) : 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (a0 + q >= k) break;
+        const unsigned dd = dq[q] * dq[q];
+        rs += dd;
+        const float4 v = sv[a0 + q];
+        if (!BIG) {
+          const float df = (float)dd;  // exact below 2^24
+          ff_madd(xh, xl, df, v.x, v.y);
+          ff_madd(yh, yl, df, v.z, v.w);
+        } else {
+          const float dh = (float)(dd & 0xFFFFF000u), dl = (float)(dd & 0xFFFu);  // both exact
+          ff_madd(xh, xl, dh, v.x, v.y);
+          ff_madd(xh, xl, dl, v.x, v.y);
+          ff_madd(yh, yl, dh, v.z, v.w);
+          ff_madd(yh, yl, dl, v.z, v.w);
+        }
       }
     }
     const double rbar = (double)rs / (double)k;
@@ -642,12 +649,20 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
       const int hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
       const int64_t hi = base + src;
       const R hx = __shfl_sync(0xffffffffu, xi.x, src), hy = __shfl_sync(0xffffffffu, xi.y, src);
-      for (int t = hb + lane; t < he; t += 32) {
-        const int j = __ldg(colidx + t);
-        if (j <= hi) continue;
-        const T2 xj = pos[j];
-        const R dx = hx - xj.x, dy = hy - xj.y;
-        acc += (double)sqrt(dx * dx + dy * dy);
+      // eight entries per lane in flight (hub rows of heavy-tailed graphs run to thousands)
+      for (int t0 = hb + lane; t0 < he; t0 += 32 * 8) {
+        int j[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) j[q] = t0 + 32 * q < he ? __ldg(colidx + t0 + 32 * q) : -1;
+        T2 xj[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xj[q] = j[q] > hi ? pos[j[q]] : T2{hx, hy};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (j[q] > hi) {
+            const R dx = hx - xj[q].x, dy = hy - xj[q].y;
+            acc += (double)sqrt(dx * dx + dy * dy);
+          }
       }
     }
   }
