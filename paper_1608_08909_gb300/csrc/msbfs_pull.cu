@@ -4,9 +4,12 @@
 //   new_v = (OR_{u in N(v)} F_L[u]) & ~seen_v,
 // stopping its walk as soon as every missing source has turned up.  Each
 // node's words are written by its own lane only, so no atomics are needed
-// after the sources are seeded, and d_ip[s][v] = L + 1 is stored for the new
-// bits with a warp-wide loop over the union of the lanes' new bits, so the
-// stores of one source land on consecutive nodes.
+// after the sources are seeded.  The new bits of every level are kept
+// (F_0 = the sources, F_{L+1} = the bits found at level L), and after the
+// pass k_pull_distances turns them into d_ip rows: a block takes 64 nodes,
+// folds each node's levels into five bit planes of the distance (bit j of
+// d(s, v) is bit s of plane j), and its warps write one source row segment
+// of 32 consecutive nodes per store.
 //
 // This wins on graphs of small diameter (hubs, expanders), where a few levels
 // each touch most edges and the per-source BFS would walk every edge once per
@@ -28,6 +31,10 @@ constexpr int kPullW4 = kPullSources / 128;  // uint4 chunks per node
 constexpr unsigned kPullMaxLevels = 24;
 constexpr unsigned kPullProbeLevel = 6;  // after this level at least 1/64 of all pairs must be reached
 constexpr int kPullLong = 64;  // longer rows are walked by the whole warp
+#ifndef SSM_PULL_LONG_BATCH
+#define SSM_PULL_LONG_BATCH 4
+#endif
+constexpr int kPullLongBatch = SSM_PULL_LONG_BATCH;  // neighbours per lane in flight while a warp walks a long row
 
 struct PullArgs {
   int32_t n;
@@ -39,7 +46,8 @@ struct PullArgs {
   uint16_t *dist;   // [all sources][n]
   int32_t *status;
   uint4 *seen;      // [n][kPullW4] sources that reached the node
-  uint4 *F[2];      // [n][kPullW4] frontier bits of the current / next level
+  uint4 *F;         // [kPullMaxLevels + 1][n][kPullW4] new bits of every level
+  unsigned *nlev;   // levels with new bits (written when the pass completes)
   unsigned *flag;   // [6]: new bits seen at level L, nodes left unfinished (both by L mod 3)
   unsigned long long *found;  // (source, node) pairs reached up to the probe level
   unsigned *gaveup; // set when a pass needed more than kPullMaxLevels levels
@@ -56,7 +64,7 @@ __device__ __forceinline__ unsigned word(const uint4 q, int j) {
   return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
 }
 
-__global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
+__global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
   const unsigned nthreads = gridDim.x * blockDim.x;
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -64,15 +72,14 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
   const unsigned n = (unsigned)A.n;
 
   if (__ldcg(A.gaveup)) return;  // an earlier pass already gave up
-  // level 0: the sources (seen and F[0] were cleared by the caller)
+  // level 0: the sources (seen and F_0 were cleared by the caller)
   for (int a = (int)gtid; a < A.nsrc; a += (int)nthreads) {
     const unsigned v = (unsigned)__ldg(A.sources + A.base + a);
     const unsigned bit = 1u << (a & 31);
     unsigned *s = reinterpret_cast<unsigned *>(A.seen + (size_t)v * kPullW4) + (a >> 5);
-    unsigned *f = reinterpret_cast<unsigned *>(A.F[0] + (size_t)v * kPullW4) + (a >> 5);
+    unsigned *f = reinterpret_cast<unsigned *>(A.F + (size_t)v * kPullW4) + (a >> 5);
     atomicOr(s, bit);
     atomicOr(f, bit);
-    A.dist[(size_t)(A.base + a) * n + v] = 0;
   }
   if (gtid == 0) {
     for (int i = 0; i < 6; ++i) A.flag[i] = 0u;
@@ -91,15 +98,14 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
       if (gtid == 0) atomicExch(A.gaveup, 1u);
       return;
     }
-    const uint4 *fcur = (L & 1u) ? A.F[1] : A.F[0];
-    uint4 *fnext = (L & 1u) ? A.F[0] : A.F[1];
+    const uint4 *fcur = A.F + (size_t)L * n * kPullW4;
+    uint4 *fnext = A.F + (size_t)(L + 1u) * n * kPullW4;
     // the flags of level L+1 were last read right after the barrier of level
     // L-2, which every thread has passed since
     if (gtid == 0) {
       A.flag[(L + 1u) % 3u] = 0u;
       A.flag[3 + (L + 1u) % 3u] = 0u;
     }
-    const uint16_t nd = (uint16_t)(L + 1u);
     bool any_new = false, unfinished = false;
     unsigned pairs = 0;  // new (source, node) pairs of this lane (counted up to the probe level)
     for (unsigned base = gwarp * 32u; base < n; base += nwarps * 32u) {
@@ -125,26 +131,42 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
         const int src = __ffs(longs) - 1;
         longs &= longs - 1u;
         const int hb = __shfl_sync(0xffffffffu, rb, src), he = __shfl_sync(0xffffffffu, re, src);
-        uint4 part[kPullW4];
-#pragma unroll
-        for (int c = 0; c < kPullW4; ++c) part[c] = make_uint4(0u, 0u, 0u, 0u);
-        for (int t = hb + (int)lane; t < he; t += 32) {
-          const unsigned u = (unsigned)__ldg(A.colidx + t);
-#pragma unroll
-          for (int c = 0; c < kPullW4; ++c) {
-            const uint4 f = __ldcg(fcur + (size_t)u * kPullW4 + c);
-            part[c].x |= f.x;
-            part[c].y |= f.y;
-            part[c].z |= f.z;
-            part[c].w |= f.w;
-          }
-        }
+        uint4 part[kPullW4], hmiss[kPullW4];
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c) {
-          part[c].x = __reduce_or_sync(0xffffffffu, part[c].x);
-          part[c].y = __reduce_or_sync(0xffffffffu, part[c].y);
-          part[c].z = __reduce_or_sync(0xffffffffu, part[c].z);
-          part[c].w = __reduce_or_sync(0xffffffffu, part[c].w);
+          part[c] = make_uint4(0u, 0u, 0u, 0u);
+          hmiss[c] = make_uint4(__shfl_sync(0xffffffffu, miss[c].x, src), __shfl_sync(0xffffffffu, miss[c].y, src),
+                                __shfl_sync(0xffffffffu, miss[c].z, src), __shfl_sync(0xffffffffu, miss[c].w, src));
+        }
+        // kPullLongBatch neighbours per lane in flight; the warp stops once the
+        // row's node has every missing source (hub rows run to thousands)
+        for (int t0 = hb + (int)lane; t0 - (int)lane < he; t0 += 32 * kPullLongBatch) {
+          unsigned u[kPullLongBatch];
+#pragma unroll
+          for (int e = 0; e < kPullLongBatch; ++e)
+            u[e] = t0 + 32 * e < he ? (unsigned)__ldg(A.colidx + t0 + 32 * e) : 0xFFFFFFFFu;
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c)
+#pragma unroll
+            for (int e = 0; e < kPullLongBatch; ++e) {
+              if (u[e] == 0xFFFFFFFFu) continue;
+              const uint4 f = __ldcg(fcur + (size_t)u[e] * kPullW4 + c);
+              part[c].x |= f.x;
+              part[c].y |= f.y;
+              part[c].z |= f.z;
+              part[c].w |= f.w;
+            }
+          bool done = true;
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c) {
+            part[c].x = __reduce_or_sync(0xffffffffu, part[c].x);
+            part[c].y = __reduce_or_sync(0xffffffffu, part[c].y);
+            part[c].z = __reduce_or_sync(0xffffffffu, part[c].z);
+            part[c].w = __reduce_or_sync(0xffffffffu, part[c].w);
+            done &= ((part[c].x & hmiss[c].x) == hmiss[c].x) && ((part[c].y & hmiss[c].y) == hmiss[c].y) &&
+                    ((part[c].z & hmiss[c].z) == hmiss[c].z) && ((part[c].w & hmiss[c].w) == hmiss[c].w);
+          }
+          if (done) break;  // warp-uniform: every lane holds the reduced words
         }
         if ((int)lane == src) {
 #pragma unroll
@@ -203,20 +225,6 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c)
           pairs += __popc(nw[c].x) + __popc(nw[c].y) + __popc(nw[c].z) + __popc(nw[c].w);
-      // d_ip[s][v] = L + 1 for the new bits, one source at a time across the warp
-#pragma unroll
-      for (int c = 0; c < kPullW4; ++c)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const unsigned mine = word(nw[c], j);
-          unsigned all = __reduce_or_sync(0xffffffffu, mine);
-          const int w = 4 * c + j;
-          while (all) {
-            const int b = __ffs(all) - 1;
-            all &= all - 1u;
-            if ((mine >> b) & 1u) A.dist[(size_t)(A.base + 32 * w + b) * n + v] = nd;
-          }
-        }
     }
     if (__any_sync(0xffffffffu, any_new) && lane == 0) atomicOr(A.flag + L % 3u, 1u);
     if (__any_sync(0xffffffffu, unfinished) && lane == 0) atomicOr(A.flag + 3 + L % 3u, 1u);
@@ -235,8 +243,58 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
     if (__ldcg(A.flag + L % 3u) == 0u) {
       // nothing new at this level: the pass is complete; unreached pairs mean
       // the graph is disconnected
-      if (gtid == 0 && __ldcg(A.flag + 3 + L % 3u) != 0u) dev_fail(A.status, SSM_E_DISCONNECTED);
+      if (gtid == 0) {
+        if (__ldcg(A.flag + 3 + L % 3u) != 0u) dev_fail(A.status, SSM_E_DISCONNECTED);
+        *A.nlev = L + 1u;  // F_0 .. F_L hold every distance
+      }
       return;
+    }
+  }
+}
+
+// d_ip rows from the level history (see the top of the file).  Block: 64
+// nodes; planes[w][j][v] = OR of F_L[v] word w over the levels L with bit j
+// set, so bit s & 31 of planes[s >> 5][j][v] is bit j of d(s, v).
+constexpr int kPullTile = 64;
+constexpr int kPullDistBits = 5;  // distances up to kPullMaxLevels < 32
+__global__ void __launch_bounds__(256) k_pull_distances(PullArgs A) {
+  __shared__ unsigned planes[kPullSources / 32][kPullDistBits][kPullTile];
+  __shared__ unsigned reached[kPullSources / 32][kPullTile];
+  if (__ldcg(A.gaveup)) return;
+  const unsigned nlev = __ldcg(A.nlev);
+  const int n = A.n;
+  const int v0 = blockIdx.x * kPullTile;
+  for (int t = threadIdx.x; t < (kPullSources / 32) * kPullTile; t += blockDim.x) {
+    const int w = t / kPullTile, v = t % kPullTile;
+    unsigned pl[kPullDistBits] = {0u, 0u, 0u, 0u, 0u}, any = 0u;
+    if (v0 + v < n)
+      for (unsigned L = 0; L < nlev; ++L) {
+        const unsigned f =
+            __ldcg(reinterpret_cast<const unsigned *>(A.F + ((size_t)L * n + (size_t)(v0 + v)) * kPullW4) + w);
+        any |= f;
+#pragma unroll
+        for (int j = 0; j < kPullDistBits; ++j)
+          if ((L >> j) & 1u) pl[j] |= f;
+      }
+#pragma unroll
+    for (int j = 0; j < kPullDistBits; ++j) planes[w][j][v] = pl[j];
+    reached[w][v] = any;
+  }
+  __syncthreads();
+  // warp: one source at a time, 32 consecutive nodes per store
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int sidx = warp; sidx < A.nsrc; sidx += nwarp) {
+    const int w = sidx >> 5;
+    const unsigned bit = 1u << (sidx & 31);
+    uint16_t *row = A.dist + (size_t)(A.base + sidx) * n;
+#pragma unroll
+    for (int h = 0; h < kPullTile / 32; ++h) {
+      const int v = 32 * h + lane;
+      if (v0 + v >= n) continue;
+      unsigned d = 0;
+#pragma unroll
+      for (int j = 0; j < kPullDistBits; ++j) d |= ((planes[w][j][v] & bit) ? 1u : 0u) << j;
+      row[v0 + v] = (reached[w][v] & bit) ? (uint16_t)d : (uint16_t)0xFFFFu;
     }
   }
 }
@@ -244,8 +302,8 @@ __global__ void __launch_bounds__(kPullThreads) k_msbfs_pull(PullArgs A) {
 size_t msbfs_pull_workspace(int32_t n) {
   Carver c(nullptr, 0);
   c.take<uint4>((size_t)n * kPullW4);
-  c.take<uint4>((size_t)n * kPullW4);
-  c.take<uint4>((size_t)n * kPullW4);
+  c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  c.take<unsigned>(1);
   c.take<unsigned>(6);
   c.take<unsigned long long>(1);
   c.take<BarrierState>(1);
@@ -258,8 +316,8 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
   PullArgs A;
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.sources = sources; A.dist = dist; A.status = status;
   A.seen = c.take<uint4>((size_t)n * kPullW4);
-  A.F[0] = c.take<uint4>((size_t)n * kPullW4);
-  A.F[1] = c.take<uint4>((size_t)n * kPullW4);
+  A.F = c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  A.nlev = c.take<unsigned>(1);
   A.flag = c.take<unsigned>(6);
   A.found = c.take<unsigned long long>(1);
   A.bar = c.take<BarrierState>(1);
@@ -271,11 +329,13 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
     A.base = base;
     A.nsrc = std::min(kPullSources, k - base);
     SSM_TRY_CUDA(cudaMemsetAsync(A.seen, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
-    SSM_TRY_CUDA(cudaMemsetAsync(A.F[0], 0, (size_t)n * kPullW4 * sizeof(uint4), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(A.F, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
     SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
     void *args[] = {&A};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs_pull, dim3(blocks), dim3(kPullThreads), args, 0, s));
+    note_launch(), k_pull_distances<<<(unsigned)((n + kPullTile - 1) / kPullTile), 256, 0, s>>>(A);
+    SSM_TRY_CUDA(cudaGetLastError());
   }
   return SSM_OK;
 }
