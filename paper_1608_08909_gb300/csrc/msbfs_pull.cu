@@ -47,6 +47,8 @@ struct PullArgs {
   int32_t *status;
   uint4 *seen;      // [n][kPullW4] sources that reached the node
   uint4 *F;         // [kPullMaxLevels + 1][n][kPullW4] new bits of every level
+  const int32_t *long_rows;  // nodes of degree above kPullLong
+  const unsigned *nlong;     // how many (device)
   unsigned *nlev;   // levels with new bits (written when the pass completes)
   unsigned *flag;   // [6]: new bits seen at level L, nodes left unfinished (both by L mod 3)
   unsigned long long *found;  // (source, node) pairs reached up to the probe level
@@ -72,6 +74,7 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
   const unsigned n = (unsigned)A.n;
 
   if (__ldcg(A.gaveup)) return;  // an earlier pass already gave up
+  const unsigned nlong = __ldcg(A.nlong);
   // level 0: the sources (seen and F_0 were cleared by the caller)
   for (int a = (int)gtid; a < A.nsrc; a += (int)nthreads) {
     const unsigned v = (unsigned)__ldg(A.sources + A.base + a);
@@ -125,54 +128,8 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
         rb = __ldg(A.rowptr + v);
         re = __ldg(A.rowptr + v + 1);
       }
-      // rows longer than kPullLong: the whole warp walks each of them
-      unsigned longs = __ballot_sync(0xffffffffu, open && re - rb > kPullLong);
-      while (longs) {
-        const int src = __ffs(longs) - 1;
-        longs &= longs - 1u;
-        const int hb = __shfl_sync(0xffffffffu, rb, src), he = __shfl_sync(0xffffffffu, re, src);
-        uint4 part[kPullW4], hmiss[kPullW4];
-#pragma unroll
-        for (int c = 0; c < kPullW4; ++c) {
-          part[c] = make_uint4(0u, 0u, 0u, 0u);
-          hmiss[c] = make_uint4(__shfl_sync(0xffffffffu, miss[c].x, src), __shfl_sync(0xffffffffu, miss[c].y, src),
-                                __shfl_sync(0xffffffffu, miss[c].z, src), __shfl_sync(0xffffffffu, miss[c].w, src));
-        }
-        // kPullLongBatch neighbours per lane in flight; the warp stops once the
-        // row's node has every missing source (hub rows run to thousands)
-        for (int t0 = hb + (int)lane; t0 - (int)lane < he; t0 += 32 * kPullLongBatch) {
-          unsigned u[kPullLongBatch];
-#pragma unroll
-          for (int e = 0; e < kPullLongBatch; ++e)
-            u[e] = t0 + 32 * e < he ? (unsigned)__ldg(A.colidx + t0 + 32 * e) : 0xFFFFFFFFu;
-#pragma unroll
-          for (int c = 0; c < kPullW4; ++c)
-#pragma unroll
-            for (int e = 0; e < kPullLongBatch; ++e) {
-              if (u[e] == 0xFFFFFFFFu) continue;
-              const uint4 f = __ldcg(fcur + (size_t)u[e] * kPullW4 + c);
-              part[c].x |= f.x;
-              part[c].y |= f.y;
-              part[c].z |= f.z;
-              part[c].w |= f.w;
-            }
-          bool done = true;
-#pragma unroll
-          for (int c = 0; c < kPullW4; ++c) {
-            part[c].x = __reduce_or_sync(0xffffffffu, part[c].x);
-            part[c].y = __reduce_or_sync(0xffffffffu, part[c].y);
-            part[c].z = __reduce_or_sync(0xffffffffu, part[c].z);
-            part[c].w = __reduce_or_sync(0xffffffffu, part[c].w);
-            done &= ((part[c].x & hmiss[c].x) == hmiss[c].x) && ((part[c].y & hmiss[c].y) == hmiss[c].y) &&
-                    ((part[c].z & hmiss[c].z) == hmiss[c].z) && ((part[c].w & hmiss[c].w) == hmiss[c].w);
-          }
-          if (done) break;  // warp-uniform: every lane holds the reduced words
-        }
-        if ((int)lane == src) {
-#pragma unroll
-          for (int c = 0; c < kPullW4; ++c) acc[c] = part[c];
-        }
-      }
+      // rows longer than kPullLong wait for the second phase of the level
+      const bool deferred = open && re - rb > kPullLong;
       if (open && re - rb <= kPullLong) {
         // four neighbours in flight, stop once every missing source turned up
         for (int t = rb; t < re; t += 4) {
@@ -205,7 +162,7 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
         got |= (nw[c].x | nw[c].y | nw[c].z | nw[c].w) != 0u;
         left |= (nw[c].x ^ miss[c].x) | (nw[c].y ^ miss[c].y) | (nw[c].z ^ miss[c].z) | (nw[c].w ^ miss[c].w);
       }
-      if (live) {
+      if (live && !deferred) {
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c) {
           fnext[(size_t)v * kPullW4 + c] = nw[c];
@@ -219,12 +176,85 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
           }
         }
       }
-      any_new |= got;
-      unfinished |= left;
-      if (L < kPullProbeLevel)
+      if (!deferred) {
+        any_new |= got;
+        unfinished |= left;
+        if (L < kPullProbeLevel)
+#pragma unroll
+          for (int c = 0; c < kPullW4; ++c)
+            pairs += __popc(nw[c].x) + __popc(nw[c].y) + __popc(nw[c].z) + __popc(nw[c].w);
+      }
+    }
+    // second phase: the open long rows (hubs), one per warp across the grid,
+    // kPullLongBatch entries per lane in flight, stopping once the node has
+    // every missing source
+    for (unsigned li = gwarp; li < nlong; li += nwarps) {
+      const unsigned v = (unsigned)__ldg(A.long_rows + li);
+      uint4 hmiss[kPullW4], part[kPullW4];
+      bool open = false;
+#pragma unroll
+      for (int c = 0; c < kPullW4; ++c) {
+        const uint4 sv = A.seen[(size_t)v * kPullW4 + c];
+        hmiss[c] = make_uint4(~sv.x & valid[c].x, ~sv.y & valid[c].y, ~sv.z & valid[c].z, ~sv.w & valid[c].w);
+        part[c] = make_uint4(0u, 0u, 0u, 0u);
+        open |= (hmiss[c].x | hmiss[c].y | hmiss[c].z | hmiss[c].w) != 0u;
+      }
+      if (!open) continue;  // warp-uniform; the first phase wrote its empty frontier word
+      const int hb = __ldg(A.rowptr + v), he = __ldg(A.rowptr + v + 1);
+      for (int t0 = hb + (int)lane; t0 - (int)lane < he; t0 += 32 * kPullLongBatch) {
+        unsigned u[kPullLongBatch];
+#pragma unroll
+        for (int e = 0; e < kPullLongBatch; ++e)
+          u[e] = t0 + 32 * e < he ? (unsigned)__ldg(A.colidx + t0 + 32 * e) : 0xFFFFFFFFu;
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c)
-          pairs += __popc(nw[c].x) + __popc(nw[c].y) + __popc(nw[c].z) + __popc(nw[c].w);
+#pragma unroll
+          for (int e = 0; e < kPullLongBatch; ++e) {
+            if (u[e] == 0xFFFFFFFFu) continue;
+            const uint4 f = __ldcg(fcur + (size_t)u[e] * kPullW4 + c);
+            part[c].x |= f.x;
+            part[c].y |= f.y;
+            part[c].z |= f.z;
+            part[c].w |= f.w;
+          }
+        bool done = true;
+#pragma unroll
+        for (int c = 0; c < kPullW4; ++c) {
+          part[c].x = __reduce_or_sync(0xffffffffu, part[c].x);
+          part[c].y = __reduce_or_sync(0xffffffffu, part[c].y);
+          part[c].z = __reduce_or_sync(0xffffffffu, part[c].z);
+          part[c].w = __reduce_or_sync(0xffffffffu, part[c].w);
+          done &= ((part[c].x & hmiss[c].x) == hmiss[c].x) && ((part[c].y & hmiss[c].y) == hmiss[c].y) &&
+                  ((part[c].z & hmiss[c].z) == hmiss[c].z) && ((part[c].w & hmiss[c].w) == hmiss[c].w);
+        }
+        if (done) break;  // warp-uniform: every lane holds the reduced words
+      }
+      bool got = false, left = false;
+      unsigned np = 0;
+#pragma unroll
+      for (int c = 0; c < kPullW4; ++c) {
+        const uint4 nw = make_uint4(part[c].x & hmiss[c].x, part[c].y & hmiss[c].y, part[c].z & hmiss[c].z,
+                                    part[c].w & hmiss[c].w);
+        got |= (nw.x | nw.y | nw.z | nw.w) != 0u;
+        left |= (nw.x ^ hmiss[c].x) | (nw.y ^ hmiss[c].y) | (nw.z ^ hmiss[c].z) | (nw.w ^ hmiss[c].w);
+        np += __popc(nw.x) + __popc(nw.y) + __popc(nw.z) + __popc(nw.w);
+        if (lane == 0) {
+          fnext[(size_t)v * kPullW4 + c] = nw;
+          if ((nw.x | nw.y | nw.z | nw.w) != 0u) {
+            uint4 sv = A.seen[(size_t)v * kPullW4 + c];
+            sv.x |= nw.x;
+            sv.y |= nw.y;
+            sv.z |= nw.z;
+            sv.w |= nw.w;
+            A.seen[(size_t)v * kPullW4 + c] = sv;
+          }
+        }
+      }
+      if (lane == 0) {
+        any_new |= got;
+        unfinished |= left;
+        if (L < kPullProbeLevel) pairs += np;
+      }
     }
     if (__any_sync(0xffffffffu, any_new) && lane == 0) atomicOr(A.flag + L % 3u, 1u);
     if (__any_sync(0xffffffffu, unfinished) && lane == 0) atomicOr(A.flag + 3 + L % 3u, 1u);
@@ -299,10 +329,19 @@ __global__ void __launch_bounds__(256) k_pull_distances(PullArgs A) {
   }
 }
 
+// the nodes of degree above kPullLong, in any order (the pass is order-free)
+__global__ void k_pull_long_rows(int32_t n, const int32_t *__restrict__ rowptr, int32_t *__restrict__ out,
+                                 unsigned *__restrict__ count) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (__ldg(rowptr + v + 1) - __ldg(rowptr + v) > kPullLong) out[atomicAdd(count, 1u)] = v;
+}
+
 size_t msbfs_pull_workspace(int32_t n) {
   Carver c(nullptr, 0);
   c.take<uint4>((size_t)n * kPullW4);
   c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  c.take<int32_t>((size_t)n);
+  c.take<unsigned>(1);
   c.take<unsigned>(1);
   c.take<unsigned>(6);
   c.take<unsigned long long>(1);
@@ -317,6 +356,8 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.sources = sources; A.dist = dist; A.status = status;
   A.seen = c.take<uint4>((size_t)n * kPullW4);
   A.F = c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  int32_t *long_rows = c.take<int32_t>((size_t)n);
+  unsigned *nlong = c.take<unsigned>(1);
   A.nlev = c.take<unsigned>(1);
   A.flag = c.take<unsigned>(6);
   A.found = c.take<unsigned long long>(1);
@@ -325,6 +366,13 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
   if (!c.ok) return fail(SSM_E_NOMEM, "multi-source BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
   const int blocks = cooperative_blocks((const void *)k_msbfs_pull, kPullThreads, 0, 2);
   if (blocks < 1) return fail(SSM_E_CUDA, "multi-source BFS: kernel cannot be resident");
+  // the long rows (listed on the device; the BFS reads their number there)
+  SSM_TRY_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned), s));
+  note_launch(), k_pull_long_rows<<<std::max(1, std::min((n + 255) / 256, num_sms() * 8)), 256, 0, s>>>(
+      n, rowptr, long_rows, nlong);
+  SSM_TRY_CUDA(cudaGetLastError());
+  A.long_rows = long_rows;
+  A.nlong = nlong;
   for (int base = 0; base < k; base += kPullSources) {
     A.base = base;
     A.nsrc = std::min(kPullSources, k - base);
