@@ -11,10 +11,12 @@
 // (the pivot itself, or a neighbour already counted as an edge term).
 //
 // FP32 kernel, GB300 layout:
-//  * a lane owns two consecutive nodes; their d_ia for one pivot arrive in one
-//    32-bit load.  ssm_iterate first re-lays d_ip into 64-node tiles
-//    ([tile][pivot][64 nodes]), so a warp streams one contiguous block per tile,
-//    a 128-byte row per pivot at a fixed stride (no per-load address arithmetic);
+//  * a lane owns kNpl = 4 consecutive nodes (two packed pairs); their d_ia for
+//    one pivot arrive in one 8-byte load, and the pivot's position and table
+//    row serve all four.  ssm_iterate first re-lays d_ip into 128-node tiles
+//    ([tile][pivot][128 nodes]), so a warp streams one contiguous block per
+//    tile, a 256-byte row per pivot at a fixed stride (no per-load address
+//    arithmetic);
 //  * full-table mode (graphs whose largest d_ip fits a k x (dmax+1) table in
 //    shared memory, e.g. small-world graphs): the table holds (w, w d) for
 //    every pivot and distance, w = s / d^2, so a term is one table gather, one
@@ -36,7 +38,7 @@
 //    thread per row of up to kShortDeg entries, one warp per row up to
 //    kMidDeg, one block per longer row (each sum in a fixed order); the
 //    tile kernel reads them with the node's other per-node data;
-//  * warps take 64-node tiles from an atomic counter; when there are too few
+//  * warps take 128-node tiles from an atomic counter; when there are too few
 //    tiles to keep every warp busy to the end, each tile's pivots are split
 //    into nsplit ranges taken as separate tasks, and the last range of a tile
 //    to finish adds the ranges' partial sums in range order (independent of
@@ -44,6 +46,7 @@
 // The relative change ||X^{t+1}-X^t||/||X^t|| is reduced in FP64 in a fixed
 // order by the last block to finish.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -61,12 +64,23 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_PREFETCH 8
 #endif
 #ifndef SSM_SWEEP_MIN_BLOCKS
-#define SSM_SWEEP_MIN_BLOCKS 3
+#define SSM_SWEEP_MIN_BLOCKS 2
 #endif
 #ifndef SSM_SWEEP_FULL_MIN_BLOCKS
-#define SSM_SWEEP_FULL_MIN_BLOCKS 4
+#define SSM_SWEEP_FULL_MIN_BLOCKS 2
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
+#ifndef SSM_SWEEP_NPL
+#define SSM_SWEEP_NPL 4
+#endif
+constexpr int kNpl = SSM_SWEEP_NPL;        // nodes per lane in the FP32 sweep (2 or 4)
+constexpr int kPpl = kNpl / 2;             // node pairs per lane (packed FP32x2)
+constexpr int kTileNodes = 32 * kNpl;      // nodes per warp task
+static_assert(kNpl == 2 || kNpl == 4, "two or four nodes per lane");
+// the kPpl 32-bit words (two 16-bit distances each) a lane loads per pivot
+typedef std::conditional<kPpl == 2, uint2, unsigned>::type DWords;
+__device__ __forceinline__ unsigned dword(uint2 w, int j) { return j == 0 ? w.x : w.y; }
+__device__ __forceinline__ unsigned dword(unsigned w, int) { return w; }
 
 struct SweepArgs {
   int32_t n, k;
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned ntiles = (unsigned)((n + 63) / 64);
+  const unsigned ntiles = (unsigned)((n + kTileNodes - 1) / kTileNodes);
   const unsigned nsplit = (unsigned)A.nsplit, ntasks = ntiles * nsplit;
   // loop-invariant constant pairs, kept in registers (opaque to the compiler so
   // it does not rebuild them from immediates inside the pivot loop)
@@ -355,115 +369,135 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     const unsigned tile = task / nsplit, split = task - tile * nsplit;
     const int a_lo = (int)split * A.psplit, a_hi = min(k, a_lo + A.psplit);
 
-    // ---- a tile of 64 nodes: this lane owns i0 and i0 + 1
-    const int i0 = (int)(tile * 64u + 2u * lane);
-    const bool live0 = i0 < n, live1 = i0 + 1 < n;
-    const float2 x0 = live0 ? pin[i0] : make_float2(0.f, 0.f);
-    const float2 x1 = live1 ? pin[i0 + 1] : make_float2(0.f, 0.f);
-    const float2 xi2 = make_float2(x0.x, x1.x), yi2 = make_float2(x0.y, x1.y);
+    // ---- a tile of kTileNodes nodes: this lane owns i0 .. i0 + kNpl - 1, as
+    // kPpl pairs (2j, 2j + 1) whose arithmetic is packed FP32x2
+    const int i0 = (int)(tile * (unsigned)kTileNodes + (unsigned)kNpl * lane);
+    float2 xi2[kPpl], yi2[kPpl], xs[kNpl];
+#pragma unroll
+    for (int q = 0; q < kNpl; ++q) xs[q] = i0 + q < n ? pin[i0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kPpl; ++j) {
+      xi2[j] = make_float2(xs[2 * j].x, xs[2 * j + 1].x);
+      yi2[j] = make_float2(xs[2 * j].y, xs[2 * j + 1].y);
+    }
 
-    // pivot terms, a = 0..k-1.  The d words of the next kPrefetch pivots are
-    // always in flight; lanes past the last node read a valid row segment
-    // (clamped index) and discard it.  Per pivot with B = s u, W = B u r^2 the
-    // numerator gains W x_p + B (x_i - x_p); the two parts are summed apart
+    // pivot terms, a in [a_lo, a_hi).  The d words of the next kPrefetch pivots
+    // are always in flight; lanes past the last node read zeros (d = 0: no
+    // term).  Per pivot with B = s u, W = B u r^2 the numerator gains
+    // W x_p + B (x_i - x_p); the two parts are summed apart
     // (wx += W (-x_p), bx += B (x_i - x_p)) so that no sum cancels.
-    float2 wx2 = make_float2(0.f, 0.f), wy2 = make_float2(0.f, 0.f);
-    float2 bx2 = make_float2(0.f, 0.f), by2 = make_float2(0.f, 0.f);
-    float2 den2 = make_float2(0.f, 0.f);
-    // this tile's d words: pivot a of lane l at tp[a * 32] (one contiguous 128-byte row per pivot)
-    const unsigned *tp = A.dtile + (size_t)tile * (size_t)k * 32u + lane;
-    auto load_pair = [&](int a) -> unsigned { return __ldg(tp + (unsigned)a * 32u); };
+    float2 wx2[kPpl], wy2[kPpl], bx2[kPpl], by2[kPpl], den2[kPpl];
+#pragma unroll
+    for (int j = 0; j < kPpl; ++j) {
+      wx2[j] = wy2[j] = bx2[j] = by2[j] = den2[j] = make_float2(0.f, 0.f);
+    }
+    // this tile's d words: pivot a of lane l at tp[a * 32] (one contiguous
+    // 32 kPpl-word row per pivot, kPpl words -- kNpl distances -- per lane)
+    const DWords *tp = reinterpret_cast<const DWords *>(A.dtile) + (size_t)tile * (size_t)k * 32u + lane;
+    auto load_words = [&](int a) -> DWords { return __ldg(tp + (unsigned)a * 32u); };
     float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
     asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
-    // full-table mode: w and w d of both nodes land in register pairs (the two
+    // full-table mode: w and w d of a node pair land in register pairs (the two
     // planes sit a fixed kFullPlaneBytes apart), so every product is packed
-    auto pivot_term_full = [&](int a, unsigned pk) {
+    auto pivot_term_full = [&](int a, DWords pw) {
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
-      const unsigned tb = wtab0 + (unsigned)a * wrow;
-      const unsigned al = tb + 4u * (pk & 0xFFFFu), ah = tb + 4u * (pk >> 16);
-      const float2 w2 = make_float2(lds_f32(al), lds_f32(ah));
-      const float2 wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
       const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
-      const float2 dx2 = __fadd2_rn(xi2, px2);
-      const float2 dy2 = __fadd2_rn(yi2, py2);
-      const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
-      float2 u2;
-      u2.x = rsqrt_approx(r2.x);
-      u2.y = rsqrt_approx(r2.y);
-      const float2 B2 = __fmul2_rn(wd2, u2);  // w d / r
-      wx2 = __ffma2_rn(w2, px2, wx2);
-      wy2 = __ffma2_rn(w2, py2, wy2);
-      bx2 = __ffma2_rn(B2, dx2, bx2);
-      by2 = __ffma2_rn(B2, dy2, by2);
+      const unsigned tb = wtab0 + (unsigned)a * wrow;
+#pragma unroll
+      for (int j = 0; j < kPpl; ++j) {
+        const unsigned pk = dword(pw, j);
+        const unsigned al = tb + 4u * (pk & 0xFFFFu), ah = tb + 4u * (pk >> 16);
+        const float2 w2 = make_float2(lds_f32(al), lds_f32(ah));
+        const float2 wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
+        const float2 dx2 = __fadd2_rn(xi2[j], px2);
+        const float2 dy2 = __fadd2_rn(yi2[j], py2);
+        const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
+        float2 u2;
+        u2.x = rsqrt_approx(r2.x);
+        u2.y = rsqrt_approx(r2.y);
+        const float2 B2 = __fmul2_rn(wd2, u2);  // w d / r
+        wx2[j] = __ffma2_rn(w2, px2, wx2[j]);
+        wy2[j] = __ffma2_rn(w2, py2, wy2[j]);
+        bx2[j] = __ffma2_rn(B2, dx2, bx2[j]);
+        by2[j] = __ffma2_rn(B2, dy2, by2[j]);
+      }
     };
-    auto pivot_term = [&](int a, unsigned pk) {
+    auto pivot_term = [&](int a, DWords pw) {
       if constexpr (FULL) {
-        pivot_term_full(a, pk);
+        pivot_term_full(a, pw);
         return;
       }
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
       const uint2 I = pidx[a];
-      // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
-      float2 f2;
-      f2.x = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
-      f2.y = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
-      const float cap = __uint_as_float(I.y);
-      float2 s2;
-      if (SMEM) {
-        s2.x = lds_f32(4u * __float_as_uint(fminf(f2.x, cap)) + I.x);
-        s2.y = lds_f32(4u * __float_as_uint(fminf(f2.y, cap)) + I.x);
-      } else {
-        const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
-        s2.x = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.x, cap)) - 0x4B000000u));
-        s2.y = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.y, cap)) - 0x4B000000u));
-      }
-      const float2 d2 = __fadd2_rn(f2, kMagic2);
       const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
-      const float2 dx2 = __fadd2_rn(xi2, px2);
-      const float2 dy2 = __fadd2_rn(yi2, py2);
-      // r^2 + 1e-24: coincident points (r == 0) add w x_p only, as the r == 0 rule says
-      const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
-      // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
-      const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, kTinyQ2);
-      float2 u2;
-      u2.x = rsqrt_approx(q2.x);
-      u2.y = rsqrt_approx(q2.y);
-      const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
-      const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
-      wx2 = __ffma2_rn(W2, px2, wx2);
-      wy2 = __ffma2_rn(W2, py2, wy2);
-      bx2 = __ffma2_rn(B2, dx2, bx2);
-      by2 = __ffma2_rn(B2, dy2, by2);
-      den2 = __fadd2_rn(den2, W2);
+      const float cap = __uint_as_float(I.y);
+#pragma unroll
+      for (int j = 0; j < kPpl; ++j) {
+        const unsigned pk = dword(pw, j);
+        // 2^23 + d as a float for each node (exact), and the same clamped at 2^23 + D_a
+        float2 f2;
+        f2.x = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
+        f2.y = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
+        float2 s2;
+        if (SMEM) {
+          s2.x = lds_f32(4u * __float_as_uint(fminf(f2.x, cap)) + I.x);
+          s2.y = lds_f32(4u * __float_as_uint(fminf(f2.y, cap)) + I.x);
+        } else {
+          const unsigned soff = (I.x + 4u * 0x4B000000u) >> 2;
+          s2.x = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.x, cap)) - 0x4B000000u));
+          s2.y = __ldg(A.stab + soff + (__float_as_uint(fminf(f2.y, cap)) - 0x4B000000u));
+        }
+        const float2 d2 = __fadd2_rn(f2, kMagic2);
+        const float2 dx2 = __fadd2_rn(xi2[j], px2);
+        const float2 dy2 = __fadd2_rn(yi2[j], py2);
+        // r^2 + 1e-24: coincident points (r == 0) add w x_p only, as the r == 0 rule says
+        const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
+        // + 1e-36 keeps q > 0 when d = 0 (the node is pivot a; s = 0 there)
+        const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, kTinyQ2);
+        float2 u2;
+        u2.x = rsqrt_approx(q2.x);
+        u2.y = rsqrt_approx(q2.y);
+        const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
+        const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
+        wx2[j] = __ffma2_rn(W2, px2, wx2[j]);
+        wy2[j] = __ffma2_rn(W2, py2, wy2[j]);
+        bx2[j] = __ffma2_rn(B2, dx2, bx2[j]);
+        by2[j] = __ffma2_rn(B2, dy2, by2[j]);
+        den2[j] = __fadd2_rn(den2[j], W2);
+      }
     };
-    unsigned buf[kPrefetch];
+    DWords buf[kPrefetch];
     int a0 = a_lo;
     if (a_hi - a_lo >= 2 * kPrefetch) {
 #pragma unroll
-      for (int t = 0; t < kPrefetch; ++t) buf[t] = load_pair(a0 + t);
+      for (int t = 0; t < kPrefetch; ++t) buf[t] = load_words(a0 + t);
       for (; a0 + 2 * kPrefetch <= a_hi; a0 += kPrefetch) {
 #pragma unroll
         for (int t = 0; t < kPrefetch; ++t) {
-          const unsigned pk = buf[t];
-          buf[t] = load_pair(a0 + kPrefetch + t);
-          pivot_term(a0 + t, pk);
+          const DWords pw = buf[t];
+          buf[t] = load_words(a0 + kPrefetch + t);
+          pivot_term(a0 + t, pw);
         }
       }
 #pragma unroll
       for (int t = 0; t < kPrefetch; ++t) pivot_term(a0 + t, buf[t]);
       a0 += kPrefetch;
     }
-    for (; a0 < a_hi; ++a0) pivot_term(a0, load_pair(a0));
+    for (; a0 < a_hi; ++a0) pivot_term(a0, load_words(a0));
     if (nsplit > 1) {
       // publish this range's sums; the last range of the tile adds all of them
-      // in range order and goes on to update the nodes
+      // in range order and goes on to update the nodes.  Layout:
+      // part[(q kPpl + j) stride + task 32 + lane], q = wx, wy, bx, by, den
       const size_t stride = (size_t)ntasks * 32u;
       float2 *pp = A.part + (size_t)task * 32u + lane;
-      pp[0] = wx2;
-      pp[stride] = wy2;
-      pp[2 * stride] = bx2;
-      pp[3 * stride] = by2;
-      if (!FULL) pp[4 * stride] = den2;
+#pragma unroll
+      for (int j = 0; j < kPpl; ++j) {
+        pp[(0 * kPpl + j) * stride] = wx2[j];
+        pp[(1 * kPpl + j) * stride] = wy2[j];
+        pp[(2 * kPpl + j) * stride] = bx2[j];
+        pp[(3 * kPpl + j) * stride] = by2[j];
+        if (!FULL) pp[(4 * kPpl + j) * stride] = den2[j];
+      }
       __threadfence();
       __syncwarp();
       unsigned prior = 0;
@@ -473,58 +507,60 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       __threadfence();
       if (lane == 0) A.arrive[tile] = 0u;  // ready for the next iteration
       const float2 *q = A.part + (size_t)tile * nsplit * 32u + lane;
-      float2 s0 = __ldcg(q), s1 = __ldcg(q + stride), s2 = __ldcg(q + 2 * stride), s3 = __ldcg(q + 3 * stride);
-      float2 s4 = FULL ? make_float2(0.f, 0.f) : __ldcg(q + 4 * stride);
-      for (unsigned r = 1; r < nsplit; ++r) {
-        const float2 *qr = q + (size_t)r * 32u;
-        s0 = __fadd2_rn(s0, __ldcg(qr));
-        s1 = __fadd2_rn(s1, __ldcg(qr + stride));
-        s2 = __fadd2_rn(s2, __ldcg(qr + 2 * stride));
-        s3 = __fadd2_rn(s3, __ldcg(qr + 3 * stride));
-        if (!FULL) s4 = __fadd2_rn(s4, __ldcg(qr + 4 * stride));
+#pragma unroll
+      for (int j = 0; j < kPpl; ++j) {
+        float2 s0 = __ldcg(q + (0 * kPpl + j) * stride), s1 = __ldcg(q + (1 * kPpl + j) * stride);
+        float2 s2 = __ldcg(q + (2 * kPpl + j) * stride), s3 = __ldcg(q + (3 * kPpl + j) * stride);
+        float2 s4 = FULL ? make_float2(0.f, 0.f) : __ldcg(q + (4 * kPpl + j) * stride);
+        for (unsigned r = 1; r < nsplit; ++r) {
+          const float2 *qr = q + (size_t)r * 32u;
+          s0 = __fadd2_rn(s0, __ldcg(qr + (0 * kPpl + j) * stride));
+          s1 = __fadd2_rn(s1, __ldcg(qr + (1 * kPpl + j) * stride));
+          s2 = __fadd2_rn(s2, __ldcg(qr + (2 * kPpl + j) * stride));
+          s3 = __fadd2_rn(s3, __ldcg(qr + (3 * kPpl + j) * stride));
+          if (!FULL) s4 = __fadd2_rn(s4, __ldcg(qr + (4 * kPpl + j) * stride));
+        }
+        wx2[j] = s0;
+        wy2[j] = s1;
+        bx2[j] = s2;
+        by2[j] = s3;
+        den2[j] = s4;
       }
-      wx2 = s0;
-      wy2 = s1;
-      bx2 = s2;
-      by2 = s3;
-      den2 = s4;
-    }
-    if constexpr (FULL) den2 = make_float2(live0 ? __ldg(A.den + i0) : 0.f, live1 ? __ldg(A.den + i0 + 1) : 0.f);
-    const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
-    const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
-
-    // neighbour terms (w = 1, d = 1), summed by k_sweep_nbr
-    const float2 nb0 = live0 ? __ldg(A.nb + i0) : make_float2(0.f, 0.f);
-    const float2 nb1 = live1 ? __ldg(A.nb + i0 + 1) : make_float2(0.f, 0.f);
-    const float sx0 = nb0.x, sy0 = nb0.y, sx1 = nb1.x, sy1 = nb1.y;
-    float deg0 = 0.f, deg1 = 0.f;
-    if (!FULL) {
-      const int r0 = live0 ? __ldg(A.rowptr + i0) : 0, r1 = live0 ? __ldg(A.rowptr + i0 + 1) : 0;
-      const int r2 = live1 ? __ldg(A.rowptr + i0 + 2) : 0;
-      deg0 = (float)(r1 - r0);
-      deg1 = (float)(r2 - r1);
     }
 
     // X^{t+1} and this tile's share of the relative change
     float cn = 0.f, cd = 0.f;
-    // a NaN (clamped mode: in the weights; full-table mode: in the numerator) is an error
-    const float2 chk = FULL ? __fadd2_rn(nx2, ny2) : den2;
-    if ((live0 && !(chk.x == chk.x)) || (live1 && !(chk.y == chk.y))) dev_fail(A.status, SSM_E_NUMERIC);
-    if (live0) {
-      const float dn = FULL ? den2.x : den2.x + deg0;
-      const float xn = dn > 0.f ? (nx2.x + sx0) / dn : x0.x, yn = dn > 0.f ? (ny2.x + sy0) / dn : x0.y;
-      pout[i0] = make_float2(xn, yn);
-      const float ex = xn - x0.x, ey = yn - x0.y;
-      cn = fmaf(ex, ex, ey * ey);
-      cd = fmaf(x0.x, x0.x, x0.y * x0.y);
-    }
-    if (live1) {
-      const float dn = FULL ? den2.y : den2.y + deg1;
-      const float xn = dn > 0.f ? (nx2.y + sx1) / dn : x1.x, yn = dn > 0.f ? (ny2.y + sy1) / dn : x1.y;
-      pout[i0 + 1] = make_float2(xn, yn);
-      const float ex = xn - x1.x, ey = yn - x1.y;
-      cn = fmaf(ex, ex, fmaf(ey, ey, cn));
-      cd = fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, cd));
+    int rprev = 0;
+    if (!FULL && i0 < n) rprev = __ldg(A.rowptr + i0);
+#pragma unroll
+    for (int q = 0; q < kNpl; ++q) {
+      const int i = i0 + q;
+      const int j = q >> 1;
+      const bool hi = (q & 1) != 0;
+      const bool live = i < n;
+      // neighbour terms (w = 1, d = 1), summed by k_sweep_nbr
+      const float2 nbq = live ? __ldg(A.nb + i) : make_float2(0.f, 0.f);
+      float dn;
+      if (FULL) {
+        dn = live ? __ldg(A.den + i) : 0.f;
+      } else {
+        const int rnext = live ? __ldg(A.rowptr + i + 1) : rprev;
+        dn = (hi ? den2[j].y : den2[j].x) + (float)(rnext - rprev);
+        rprev = rnext;
+      }
+      const float nx = hi ? bx2[j].y - wx2[j].y : bx2[j].x - wx2[j].x;
+      const float ny = hi ? by2[j].y - wy2[j].y : by2[j].x - wy2[j].x;
+      // a NaN (clamped mode: in the weights; full-table mode: in the numerator) is an error
+      const float chk = FULL ? nx + ny : (hi ? den2[j].y : den2[j].x);
+      if (live && !(chk == chk)) dev_fail(A.status, SSM_E_NUMERIC);
+      if (live) {
+        const float2 x = xs[q];
+        const float xn = dn > 0.f ? (nx + nbq.x) / dn : x.x, yn = dn > 0.f ? (ny + nbq.y) / dn : x.y;
+        pout[i] = make_float2(xn, yn);
+        const float ex = xn - x.x, ey = yn - x.y;
+        cn = fmaf(ex, ex, fmaf(ey, ey, cn));
+        cd = fmaf(x.x, x.x, fmaf(x.y, x.y, cd));
+      }
     }
     const double tn = warp_sum((double)cn), td = warp_sum((double)cd);
     if (lane == 0) {
@@ -536,16 +572,19 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 }
 
 // ----------------------------------------------------------------- setup (once per ssm_iterate)
-// dtile[(t * k + a) * 32 + l] = d_ip[a][64t + 2l] | d_ip[a][64t + 2l + 1] << 16 (0 past the last node)
+// dtile[((t k + a) 32 + l) kPpl + j] = d_ip[a][i] | d_ip[a][i + 1] << 16 with
+// i = t kTileNodes + kNpl l + 2 j (0 past the last node)
 __global__ void k_tile_dip(int32_t n, int32_t k, const uint16_t *__restrict__ dip, unsigned *__restrict__ dtile) {
-  const int64_t ntiles = (n + 63) / 64;
-  const int64_t total = ntiles * (int64_t)k * 32;
+  const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
+  const int64_t total = ntiles * (int64_t)k * 32 * kPpl;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(w & 31);
-    const int64_t ta = w >> 5;
+    const int j = (int)(w % kPpl);
+    const int64_t wl = w / kPpl;
+    const int l = (int)(wl & 31);
+    const int64_t ta = wl >> 5;
     const int a = (int)(ta % k);
     const int64_t t = ta / k;
-    const int64_t i = t * 64 + 2 * l;
+    const int64_t i = t * kTileNodes + (int64_t)kNpl * l + 2 * j;
     const uint16_t *row = dip + (size_t)a * n;
     const unsigned lo = i < n ? (unsigned)__ldg(row + i) : 0u;
     const unsigned hi = i + 1 < n ? (unsigned)__ldg(row + i + 1) : 0u;
@@ -585,25 +624,32 @@ __global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict_
 }
 
 // full-table mode: den[i] = deg(i) + sum_{a = 0..k-1} w'_ia in FP32, pivots in
-// order (the sum the clamped mode forms inside every sweep)
+// order (the sum the clamped mode forms inside every sweep); one warp per tile
 __global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *__restrict__ dtile,
                             const float *__restrict__ wtab, const int32_t *__restrict__ rowptr,
                             float *__restrict__ den) {
   const unsigned lane = threadIdx.x & 31u;
-  const int64_t ntiles = (n + 63) / 64;
+  const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
   for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles;
        tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const unsigned *tp = dtile + tile * (int64_t)k * 32 + lane;
-    float dl = 0.f, dh = 0.f;
+    const DWords *tp = reinterpret_cast<const DWords *>(dtile) + tile * (int64_t)k * 32 + lane;
+    float acc[kNpl];
+#pragma unroll
+    for (int q = 0; q < kNpl; ++q) acc[q] = 0.f;
     for (int a = 0; a < k; ++a) {
-      const unsigned pk = __ldg(tp + (int64_t)a * 32);
+      const DWords pw = __ldg(tp + (int64_t)a * 32);
       const float *row = wtab + (int64_t)a * (dmax + 1);
-      dl += __ldg(row + (pk & 0xFFFFu));
-      dh += __ldg(row + (pk >> 16));
+#pragma unroll
+      for (int j = 0; j < kPpl; ++j) {
+        const unsigned pk = dword(pw, j);
+        acc[2 * j] += __ldg(row + (pk & 0xFFFFu));
+        acc[2 * j + 1] += __ldg(row + (pk >> 16));
+      }
     }
-    const int64_t i0 = tile * 64 + 2 * lane;
-    if (i0 < n) den[i0] = dl + (float)(rowptr[i0 + 1] - rowptr[i0]);
-    if (i0 + 1 < n) den[i0 + 1] = dh + (float)(rowptr[i0 + 2] - rowptr[i0 + 1]);
+    const int64_t i0 = tile * kTileNodes + (int64_t)kNpl * lane;
+#pragma unroll
+    for (int q = 0; q < kNpl; ++q)
+      if (i0 + q < n) den[i0 + q] = acc[q] + (float)(rowptr[i0 + q + 1] - rowptr[i0 + q]);
   }
 }
 
@@ -745,10 +791,10 @@ struct IterWs {
 #define SSM_SWEEP_SPLIT_TASKS 4
 #endif
 constexpr int kSplitTasksPerWarp = SSM_SWEEP_SPLIT_TASKS;  // target tasks per resident warp (0: never split)
-constexpr int kMaxSplit = 4;
+constexpr int kMaxSplit = 8;
 constexpr int kSplitWarpsPerSm = 32;
 static int64_t split_capacity(int32_t n) {
-  const int64_t tiles = ((int64_t)n + 63) / 64;
+  const int64_t tiles = ((int64_t)n + kTileNodes - 1) / kTileNodes;
   return tiles < 2 * (int64_t)num_sms() * kSplitWarpsPerSm ? kMaxSplit * tiles : 0;
 }
 
@@ -763,13 +809,13 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.nb = precision == 64 ? nullptr : c.take<float2>((size_t)n);
   w.mid_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
   w.long_rows = precision == 64 ? nullptr : c.take<int32_t>((size_t)n);
-  w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + 63) / 64) * (size_t)k * 32);
+  w.dtile = precision == 64 ? nullptr : c.take<unsigned>((size_t)((n + kTileNodes - 1) / kTileNodes) * (size_t)k * 32 * kPpl);
   w.wtab = precision == 64 ? nullptr : c.take<float>(2 * (size_t)kFullPlane);
   w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
   w.meta = c.take<unsigned>(4);
   w.split_cap = precision == 64 ? 0 : split_capacity(n);
-  w.part = w.split_cap ? c.take<float2>(5 * 32 * (size_t)w.split_cap) : nullptr;
-  w.arrive = w.split_cap ? c.take<unsigned>((size_t)((n + 63) / 64)) : nullptr;
+  w.part = w.split_cap ? c.take<float2>(5 * kPpl * 32 * (size_t)w.split_cap) : nullptr;
+  w.arrive = w.split_cap ? c.take<unsigned>((size_t)((n + kTileNodes - 1) / kTileNodes)) : nullptr;
   return c.size();
 }
 
@@ -860,7 +906,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
       smem = piv + (tsm ? tab : 0);
       kern = tsm ? (const void *)k_sweep_f32<kClampSmem> : (const void *)k_sweep_f32<kClampGlobal>;
     }
-    tiles = (n + 63) / 64;
+    tiles = (n + kTileNodes - 1) / kTileNodes;
   }
   SSM_TRY_CUDA(allow_dynamic_smem(kern));
   int per_sm = 0;
