@@ -17,16 +17,39 @@ constexpr int kAggThreads = 256;
 // per-pivot maximum distance over its region
 __global__ void __launch_bounds__(kAggThreads) k_region_ecc(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
                                                             int32_t *__restrict__ region, unsigned *__restrict__ ecc) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  // the loop runs over whole warps so that lanes past n can join the warp-wide
+  // aggregation below
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+    const int64_t i = i0 + (threadIdx.x & 31);
+    const bool live = i < n;
     unsigned best = 0xFFFFFFFFu;
     int32_t arg = 0;
-    const uint16_t *col = dip + i;
-    for (int32_t a = 0; a < k; ++a) {
-      const unsigned d = __ldg(col + (size_t)a * n);
-      if (d < best) { best = d; arg = a; }
+    if (live) {
+      const uint16_t *col = dip + i;
+      // eight pivots' distances in flight, compared in pivot order (ties to the lowest a)
+      for (int32_t a0 = 0; a0 < k; a0 += 8) {
+        unsigned dq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dq[q] = a0 + q < k ? (unsigned)__ldg(col + (size_t)(a0 + q) * n) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (dq[q] < best) {
+            best = dq[q];
+            arg = a0 + q;
+          }
+      }
+      if (region) region[i] = arg;
     }
-    if (region) region[i] = arg;
-    atomicMax(ecc + arg, best);
+    // one atomic per distinct region among the warp's nodes
+    const unsigned peers = __match_any_sync(0xffffffffu, live ? arg : -1);
+    const unsigned bval = live ? best : 0u;
+    unsigned m = 0u;
+    for (int src = 0; src < 32; ++src) {  // the maximum over this lane's group
+      const unsigned t = __shfl_sync(0xffffffffu, bval, src);
+      if ((peers >> src) & 1u) m = max(m, t);
+    }
+    if (live && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicMax(ecc + arg, m);
   }
 }
 
@@ -61,10 +84,18 @@ __global__ void __launch_bounds__(kAggThreads) k_histogram(int32_t n, const uint
                                                            const int32_t *__restrict__ region,
                                                            const int32_t *__restrict__ cnt_off, int64_t cnt_len,
                                                            unsigned *__restrict__ cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = region[i];
-    const int64_t slot = (int64_t)cnt_off[a] + __ldg(dip + (size_t)a * n + i);
-    if (slot < cnt_len) atomicAdd(cnt + slot, 1u);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+    const int64_t i = i0 + (threadIdx.x & 31);
+    int64_t slot = -1;
+    if (i < n) {
+      const int32_t a = region[i];
+      slot = (int64_t)cnt_off[a] + __ldg(dip + (size_t)a * n + i);
+      if (slot >= cnt_len) slot = -1;
+    }
+    // one atomic per distinct slot among the warp's nodes
+    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)slot);
+    if (slot >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(cnt + slot, (unsigned)__popc(peers));
   }
 }
 
