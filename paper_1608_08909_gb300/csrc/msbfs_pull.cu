@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(256) k_pull_distances(PullArgs A) {
   const int n = A.n;
   const int v0 = blockIdx.x * kPullTile;
   for (int t = threadIdx.x; t < (kPullSources / 32) * kPullTile; t += blockDim.x) {
-    const int w = t / kPullTile, v = t % kPullTile;
+    // consecutive threads take consecutive words of one node (coalesced reads)
+    const int w = t % (kPullSources / 32), v = t / (kPullSources / 32);
     unsigned pl[kPullDistBits] = {0u, 0u, 0u, 0u, 0u}, any = 0u;
     if (v0 + v < n)
       for (unsigned L = 0; L < nlev; ++L) {
