@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_1608_08909_gb300 as ssm
@@ -52,3 +53,48 @@ def test_bad_arguments_rejected_on_host(call):
     L = ssm.lib()
     assert call(L) == -1
     assert len(L.ssm_last_error()) > 0
+
+
+def _batch_desc(specs):
+    desc = np.zeros(len(specs), dtype=ssm._batch_dtype())
+    for i, (n, k, cnt_len) in enumerate(specs):
+        desc[i] = (n, k, cnt_len, 0, 0, 0, 0, 0, 0, 0, 0)
+    return desc
+
+
+@pytest.mark.parametrize("specs,threads,what", [
+    ([(12289, 10, 20)], 0, "n = 12289"),     # above the shared-memory positions limit
+    ([(100, 0, 20)], 0, "k = 0"),
+    ([(100, 101, 200)], 0, "k = 101"),       # more pivots than nodes
+    ([(100, 10, 5)], 0, "cnt_len < k"),
+    ([(100, 10, 20)], 192, "threads"),       # not a tuned block size
+])
+def test_batch_arguments_rejected_on_host(specs, threads, what):
+    """ssm_batch_iterate checks every descriptor before touching the device
+    (the dummy device pointers below are never dereferenced)."""
+    L = ssm.lib()
+    desc = _batch_desc(specs)
+    dp = desc.ctypes.data_as(ctypes.c_void_p)
+    fake = ctypes.c_void_p(256)
+    rc = L.ssm_batch_iterate(len(specs), dp, fake, fake, fake, fake, fake, fake, fake, 1, fake, threads, None, fake,
+                             fake, 1 << 20, None)
+    assert rc == -1
+    assert len(L.ssm_last_error()) > 0
+
+
+def test_batch_workspace_grows_with_the_batch():
+    L = ssm.lib()
+    one = _batch_desc([(1000, 50, 1100)])
+    two = _batch_desc([(1000, 50, 1100), (4000, 100, 4200)])
+    w1 = L.ssm_batch_iterate_workspace(1, one.ctypes.data_as(ctypes.c_void_p))
+    w2 = L.ssm_batch_iterate_workspace(2, two.ctypes.data_as(ctypes.c_void_p))
+    # the tiled d_ip copy alone: 2 k n (rounded up to 64-node tiles) per graph
+    assert w1 >= 2 * 50 * 1024 and w2 >= w1 + 2 * 100 * 4032
+
+
+def test_gram_arguments_rejected_on_host():
+    L = ssm.lib()
+    fake = ctypes.c_void_p(256)
+    assert L.ssm_gram(10, 0, fake, fake, fake, fake, fake, 256, None) == -1
+    assert L.ssm_gram(10, 1025, fake, fake, fake, fake, fake, 256, None) == -1
+    assert L.ssm_gram(10, 5, fake, fake, fake, fake, fake, 16, None) == -5  # workspace too small
