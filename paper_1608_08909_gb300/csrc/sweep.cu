@@ -912,7 +912,10 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   int per_sm = 0;
   SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
   if (per_sm < 1) return fail(SSM_E_ARG, "ssm_iterate: %zu bytes of shared memory do not fit", smem);
-  const int64_t want = (tiles + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
+  // one warp per tile, or up to kSplitTasksPerWarp warps per tile on graphs
+  // small enough to split (their pivot ranges keep the extra warps busy)
+  const int64_t per_tile = (precision == 32 && w.split_cap > 0 && kSplitTasksPerWarp > 0) ? kSplitTasksPerWarp : 1;
+  const int64_t want = (tiles * per_tile + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
   if (precision == 32 && w.split_cap > 0 && kSplitTasksPerWarp > 0) {
     // about kSplitTasksPerWarp tasks per resident warp, ranges of at least 2 kPrefetch pivots
