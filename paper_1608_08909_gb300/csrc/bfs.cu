@@ -221,9 +221,16 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
     }
     const bool last = (j == A.k - 1);
     if (last && j > 0) break;  // the final pivot needs no search
+    // level 0 is the pivot alone: block 0 seeded it and expands it (and the
+    // levels after it while they stay small) on its own, so the other blocks
+    // need not see the seed and go straight to the barrier after that phase
+    if (blockIdx.x == 0) {
+      __syncthreads();
+      maxmin_solo(A, 0, 1, sq, s_cnt, S);
+    }
     if (!grid_barrier(A.bar, A.status)) return;
 
-    for (unsigned L = 0;;) {
+    for (unsigned L = __ldcg(A.level);;) {
       const unsigned c = __ldcg(A.qcnt + L % 3);
       if (c == 0) break;
       if (c <= (unsigned)kSoloMax) {

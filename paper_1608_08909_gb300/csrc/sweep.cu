@@ -800,6 +800,7 @@ static int64_t split_capacity(int32_t n) {
 
 static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t k, int64_t cnt_len,
                             int32_t precision) {
+  (void)m2;  // the sweep's scratch does not grow with the edge count
   const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
   w.tmp = c.take<char>((size_t)n * elem);
   w.ctr = c.take<unsigned>(2);

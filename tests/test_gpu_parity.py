@@ -154,6 +154,16 @@ def test_select_pivots_large_grid_kernel():
     assert np.array_equal(got, O.maxmin(og, 6, 12345))
 
 
+def test_select_pivots_large_ba_kernel():
+    # 700000 nodes of a Barabasi-Albert graph (hubs, small diameter) also run
+    # the cooperative grid kernel, over many short pruned searches
+    n, s, d = I.ba(700000, 4, 3)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 24, 0).cpu().numpy()
+    assert np.array_equal(got, O.maxmin(og, 24, 0))
+
+
 # ------------------------------------------------------------------ a2 d_ip
 
 @pytest.mark.parametrize("name,k", [("grid32", 50), ("path", 7), ("btree", 33), ("rgg", 100), ("ba", 64),
