@@ -356,22 +356,26 @@ size_t maxmin_workspace(int32_t n, int64_t m2) {
 // --------------------------------------------------------------------------
 // one source per block: visited bitmap in shared memory
 // --------------------------------------------------------------------------
-#ifndef SSM_CTA_THREADS
-#define SSM_CTA_THREADS 512
+#ifndef SSM_CTA_STEP
+#define SSM_CTA_STEP 4
 #endif
-#ifndef SSM_CTA_SLOTS
-#define SSM_CTA_SLOTS 4
+#ifndef SSM_CTA_LANE_ROW
+#define SSM_CTA_LANE_ROW 32
 #endif
-#ifndef SSM_CTA_BATCH
-#define SSM_CTA_BATCH 4
+#ifndef SSM_CTA_QMAX
+#define SSM_CTA_QMAX 4096
 #endif
-#ifndef SSM_ADJ4_MAX_MB
-#define SSM_ADJ4_MAX_MB 48
+#ifndef SSM_ADJ2_MAX_MB
+#define SSM_ADJ2_MAX_MB 48
 #endif
-constexpr int kCtaThreads = SSM_CTA_THREADS;
-constexpr int kCtaSlotsPerSm = SSM_CTA_SLOTS;
-constexpr size_t kCtaBitmapMax = 200 * 1024;  // bytes of shared memory for the visited bitmap
-constexpr size_t kAdj4MaxBytes = (size_t)SSM_ADJ4_MAX_MB << 20;  // expanded adjacency kept only while it fits well inside L2
+constexpr int kCtaThreads = 512;
+constexpr int kCtaStep = SSM_CTA_STEP;         // edges whose loads a lane has in flight at once
+constexpr int kCtaLaneRow = SSM_CTA_LANE_ROW;  // rows up to this length: one lane; longer: the warp
+constexpr int kCtaQMax = SSM_CTA_QMAX;         // frontier entries per level kept in shared memory (at most)
+constexpr size_t kCtaBitmapMax = 200 * 1024;   // bytes of shared memory for the visited bitmap
+constexpr size_t kAdj2MaxBytes = (size_t)SSM_ADJ2_MAX_MB << 20;  // packed adjacency kept only while it fits well inside L2
+constexpr int kAdj2NodeBits = 21;              // packed adjacency: node id below 2^21 ...
+constexpr unsigned kAdj2DegEsc = 2047u;        // ... and min(deg, 2047) above it (2047: read rowptr)
 
 struct CtaBfsArgs {
   int32_t n;
@@ -381,25 +385,38 @@ struct CtaBfsArgs {
   const int32_t *sources;
   uint16_t *dist;  // [nsrc][n]
   int32_t *status;
-  const int4 *adj; // [2m] edge-expanded adjacency
-  int2 *queues;    // [slots][2][n] row ranges of the frontier
+  const int2 *adj; // [2m] packed adjacency (v | min(deg v, 2047) << 21, rowptr[v])
+  int2 *queues;    // [slots][2][n] frontier entries (row start, degree) past the shared part
+  int32_t qsm;     // entries per level kept in shared memory (a multiple of 32)
   const unsigned *run_if;  // run only if this device word is nonzero (the pulled BFS gave up)
 };
 
 // Each block owns sources blockIdx.x, blockIdx.x + gridDim.x, ...; per source
 // a level-synchronous BFS whose visited set is a bitmap in shared memory
-// (claimed with shared atomicOr), whose frontier holds the row ranges of the
-// nodes (fetched when a node is appended) and whose levels are separated by
-// __syncthreads.  Appends are compacted with warp ballots.
-template <bool ADJ4>
-__global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
-  extern __shared__ unsigned vis[];
-  __shared__ unsigned s_cnt[2];
-  __shared__ unsigned s_total;
+// (claimed with shared atomicOr).  The frontier holds (row start, degree) of
+// its nodes -- read from the packed adjacency when a node is claimed, so the
+// next level needs no rowptr lookup -- in shared memory for its first qsm
+// entries, in global memory past them.  Levels are separated by one
+// __syncthreads (three rotating frontier counters: level L reads counter
+// L mod 3, appends to L + 1 mod 3, and thread 0 clears L + 2 mod 3, which
+// nobody reads again before the barrier).  A lane walks the row of its own
+// frontier node with the loads of kCtaStep edges in flight (the warp takes
+// as many steps as its longest row needs); rows longer than kCtaLaneRow are
+// walked by the whole warp, one row at a time.  Each step claims its nodes,
+// compacts the appends with warp ballots and reserves their slots with one
+// shared-memory atomic, so a round costs about one global-memory latency.
+template <bool ADJ, int MINB>
+__global__ void __launch_bounds__(kCtaThreads, MINB) k_bfs_cta(CtaBfsArgs A) {
+  extern __shared__ __align__(16) unsigned cta_smem[];
+  __shared__ unsigned s_cnt[3];
   const unsigned n = (unsigned)A.n, nwords = (n + 31u) / 32u;
+  unsigned *vis = cta_smem;
+  int2 *sq = reinterpret_cast<int2 *>(cta_smem + ((nwords + 3u) & ~3u));  // [2][qsm]
+  const unsigned qsm = (unsigned)A.qsm;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   if (__ldcg(A.run_if) == 0u) return;
-  int2 *qa = A.queues + (size_t)blockIdx.x * 2 * n, *qb = qa + n;
+  int2 *const qg = A.queues + (size_t)blockIdx.x * 2 * n;
   for (int si = blockIdx.x; si < A.nsrc; si += gridDim.x) {
     for (unsigned w = threadIdx.x; w < nwords; w += blockDim.x) vis[w] = 0u;
     __syncthreads();
@@ -407,86 +424,192 @@ __global__ void __launch_bounds__(kCtaThreads) k_bfs_cta(CtaBfsArgs A) {
     if (threadIdx.x == 0) {
       const unsigned s = (unsigned)__ldg(A.sources + si);
       vis[s >> 5] |= 1u << (s & 31u);
-      qa[0] = make_int2(__ldg(A.rowptr + s), __ldg(A.rowptr + s + 1));
+      const int rb = __ldg(A.rowptr + s);
+      const int2 e0 = make_int2(rb, __ldg(A.rowptr + s + 1) - rb);
+      if (qsm > 0) sq[0] = e0; else qg[0] = e0;
       row[s] = 0;
       s_cnt[0] = 1;
       s_cnt[1] = 0;
-      s_total = 1;
+      s_cnt[2] = 0;
     }
     __syncthreads();
-    int cur = 0;
+    unsigned total = 0;  // nodes reached (thread 0)
+    int c0 = 0;          // counter of this level
     for (unsigned L = 0;; ++L) {
-      const unsigned cc = s_cnt[cur];
+      const unsigned cc = s_cnt[c0];
       if (cc == 0) break;
       if (L + 1 > 65534u) {
         if (threadIdx.x == 0) dev_fail(A.status, SSM_E_DIST_OVERFLOW);
         break;
       }
-      const int nxt = cur ^ 1;
-      const int2 *qin = cur ? qb : qa;
-      int2 *qout = cur ? qa : qb;
+      const int c1 = c0 == 2 ? 0 : c0 + 1, c2 = c1 == 2 ? 0 : c1 + 1;
+      if (threadIdx.x == 0) {
+        total += cc;
+        s_cnt[c2] = 0;
+      }
+      const unsigned bin = L & 1u, bout = bin ^ 1u;
+      const int2 *sin = sq + bin * qsm, *gin = qg + (size_t)bin * n;
+      int2 *sout = sq + bout * qsm, *gout = qg + (size_t)bout * n;
+      unsigned *cnt_next = s_cnt + c1;
       const uint16_t nd = (uint16_t)(L + 1);
+      // claim the nodes of up to kCtaStep edges per lane (edge u valid where
+      // ok[u]) and append the new ones to the next frontier
+      auto step = [&](const int (&idx)[kCtaStep], const bool (&ok)[kCtaStep]) {
+        int2 ed[kCtaStep];
+        bool push[kCtaStep];
+#pragma unroll
+        for (int u = 0; u < kCtaStep; ++u) ed[u] = ok[u] ? __ldg(A.adj + idx[u]) : make_int2(0, 0);
+        unsigned tot = 0;
+#pragma unroll
+        for (int u = 0; u < kCtaStep; ++u) {
+          push[u] = false;
+          if (ok[u]) {
+            const unsigned v = (unsigned)ed[u].x & ((1u << kAdj2NodeBits) - 1u);
+            const unsigned bit = 1u << (v & 31u);
+            unsigned *wp = vis + (v >> 5);
+            push[u] = !(*wp & bit) && !(atomicOr(wp, bit) & bit);
+          }
+          tot += __popc(__ballot_sync(0xffffffffu, push[u]));
+        }
+        if (tot == 0) return;
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(cnt_next, tot);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+#pragma unroll
+        for (int u = 0; u < kCtaStep; ++u) {
+          const unsigned mk = __ballot_sync(0xffffffffu, push[u]);
+          if (push[u]) {
+            const unsigned v = (unsigned)ed[u].x & ((1u << kAdj2NodeBits) - 1u);
+            unsigned dg = (unsigned)ed[u].x >> kAdj2NodeBits;
+            if (dg == kAdj2DegEsc) dg = (unsigned)(__ldg(A.rowptr + v + 1) - ed[u].y);
+            row[v] = nd;
+            const unsigned q = pos + __popc(mk & lt);
+            const int2 ent = make_int2(ed[u].y, (int)dg);
+            if (q < qsm) sout[q] = ent; else gout[q] = ent;
+          }
+          pos += __popc(mk);
+        }
+      };
       for (unsigned base = warp * 32u; base < cc; base += nwarps * 32u) {
         const unsigned e = base + lane;
-        const int2 r = e < cc ? __ldcg(qin + e) : make_int2(0, 0);
-        if (ADJ4) {
-          warp_for_each_edge4_batched<SSM_CTA_BATCH>(
-              r.x, r.y, A.adj,
-              [&](int, int4 ed) {
-                const unsigned bit = 1u << ((unsigned)ed.x & 31u);
-                unsigned *wp = vis + ((unsigned)ed.x >> 5);
-                return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
-              },
-              [&](int, int4 ed, bool push) {
-                const unsigned pos = warp_slot(push, s_cnt + nxt);
-                if (push) {
-                  row[ed.x] = nd;
-                  qout[pos] = make_int2(ed.y, ed.z);
-                }
-              });
+        const int2 r = e < cc ? (e < qsm ? sin[e] : __ldcg(gin + e)) : make_int2(0, 0);
+        if (ADJ) {
+          const bool mine = r.y <= kCtaLaneRow;
+          const int steps = __reduce_max_sync(0xffffffffu, mine ? r.y : 0);
+          for (int j = 0; j < steps; j += kCtaStep) {
+            int idx[kCtaStep];
+            bool ok[kCtaStep];
+#pragma unroll
+            for (int u = 0; u < kCtaStep; ++u) {
+              ok[u] = mine && j + u < r.y;
+              idx[u] = r.x + j + u;
+            }
+            step(idx, ok);
+          }
+          // rows longer than kCtaLaneRow: the whole warp walks each in turn
+          unsigned longm = __ballot_sync(0xffffffffu, !mine);
+          while (longm) {
+            const int o = __ffs(longm) - 1;
+            longm &= longm - 1u;
+            const int rb = __shfl_sync(0xffffffffu, r.x, o), dg = __shfl_sync(0xffffffffu, r.y, o);
+            for (int t = 0; t < dg; t += 32 * kCtaStep) {
+              int idx[kCtaStep];
+              bool ok[kCtaStep];
+#pragma unroll
+              for (int u = 0; u < kCtaStep; ++u) {
+                const int t1 = t + 32 * u + (int)lane;
+                ok[u] = t1 < dg;
+                idx[u] = rb + t1;
+              }
+              step(idx, ok);
+            }
+          }
         } else {
-          warp_for_each_neighbor_batched<SSM_CTA_BATCH>(
-              r.x, r.y, A.colidx,
+          warp_for_each_neighbor_batched<4>(
+              r.x, r.x + r.y, A.colidx,
               [&](int, int, int v) {
                 const unsigned bit = 1u << ((unsigned)v & 31u);
                 unsigned *wp = vis + ((unsigned)v >> 5);
                 return !(*wp & bit) && !(atomicOr(wp, bit) & bit);
               },
               [&](int, int, int v, bool push) {
-                const unsigned pos = warp_slot(push, s_cnt + nxt);
+                const unsigned q = warp_slot(push, cnt_next);
                 if (push) {
                   row[v] = nd;
-                  qout[pos] = make_int2(__ldg(A.rowptr + v), __ldg(A.rowptr + v + 1));
+                  const int rb = __ldg(A.rowptr + v);
+                  const int2 ent = make_int2(rb, __ldg(A.rowptr + v + 1) - rb);
+                  if (q < qsm) sout[q] = ent; else gout[q] = ent;
                 }
               });
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        s_total += s_cnt[nxt];
-        s_cnt[cur] = 0;
-      }
-      __syncthreads();
-      cur = nxt;
+      c0 = c1;
     }
-    if (threadIdx.x == 0 && s_total != n) dev_fail(A.status, SSM_E_DISCONNECTED);
+    if (threadIdx.x == 0 && total != n) dev_fail(A.status, SSM_E_DISCONNECTED);
     __syncthreads();
   }
 }
 
+// packed adjacency: adj[t] = (v | min(deg v, 2047) << 21, rowptr[v]) for v = colidx[t]
+__global__ void k_pack_adj(int64_t m2, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                           int2 *__restrict__ adj) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = __ldg(colidx + t);
+    const int rb = __ldg(rowptr + v);
+    const unsigned dg = min((unsigned)(__ldg(rowptr + v + 1) - rb), kAdj2DegEsc);
+    adj[t] = make_int2((int)((unsigned)v | (dg << kAdj2NodeBits)), rb);
+  }
+}
+
 static bool cta_bfs_fits(int32_t n) { return (size_t)((n + 31) / 32) * 4 <= kCtaBitmapMax; }
-// concurrent sources: as many blocks as fit on the device (at most
-// kCtaSlotsPerSm per SM), each with the visited bitmap of n nodes
-static int cta_bfs_slots(int32_t n, int32_t nsrc) {
+
+struct CtaBfsShape {
+  bool many;  // four blocks per SM (32 registers a thread), else two (64)
+  int slots, qsm;
+  size_t smem;
+};
+
+static const void *cta_bfs_kernel(bool packed, bool many) {
+  if (packed) return many ? (const void *)k_bfs_cta<true, 4> : (const void *)k_bfs_cta<true, 2>;
+  return many ? (const void *)k_bfs_cta<false, 4> : (const void *)k_bfs_cta<false, 2>;
+}
+
+// Blocks of 512 threads: two per SM while the sources fit two per SM, with
+// the shared memory an SM can give each beyond the bitmap holding the first
+// qsm frontier entries of both levels; four per SM for more sources, with the
+// bitmap alone (measured on rgg256k: a shared-memory frontier at four blocks
+// per SM leaves less L1 for the adjacency reads and was slower).  Without a
+// device (workspace queries on a host) one slot per SM is assumed.
+static CtaBfsShape cta_bfs_shape(int32_t n, int32_t nsrc) {
+  CtaBfsShape S;
+  const int sms = num_sms();
+  S.many = nsrc > 2 * sms;
+  const int want = S.many ? 4 : 2;
+  const size_t bitmap = (size_t)(((n + 31) / 32 + 3) & ~3) * 4;
+  int dev = 0, per_sm_smem = 0, per_block_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_block_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    per_sm_smem = 0;
+    per_block_max = 0;
+  }
+  const int64_t budget = std::min<int64_t>(per_block_max, (int64_t)per_sm_smem / want - 1024) - 64;
+  int64_t q = (!S.many && budget > (int64_t)bitmap) ? (budget - (int64_t)bitmap) / (2 * (int64_t)sizeof(int2)) : 0;
+  q = std::min<int64_t>(q, kCtaQMax) & ~31ll;
+  S.qsm = (int)std::max<int64_t>(0, q);
+  S.smem = bitmap + 2 * (size_t)S.qsm * sizeof(int2);
   int per_sm = 0;
-  const size_t smem = (size_t)((n + 31) / 32) * 4;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_bfs_cta<true>, kCtaThreads, smem) !=
-          cudaSuccess ||
+  const void *kern = cta_bfs_kernel(true, S.many);
+  if (allow_dynamic_smem(kern) != cudaSuccess || allow_dynamic_smem(cta_bfs_kernel(false, S.many)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, S.smem) != cudaSuccess ||
       per_sm < 1) {
     (void)cudaGetLastError();
     per_sm = 1;
   }
-  return std::max(1, std::min(nsrc, num_sms() * std::min(per_sm, kCtaSlotsPerSm)));
+  S.slots = std::max(1, std::min(nsrc, sms * std::min(per_sm, want)));
+  return S;
 }
 
 // --------------------------------------------------------------------------
@@ -627,8 +750,8 @@ static void msbfs_carve(Carver &c, MsBfsArgs &A, int32_t n, int32_t k) {
 size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   Carver c(nullptr, 0);
   if (cta_bfs_fits(n)) {
-    c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
-    c.take<int2>((size_t)cta_bfs_slots(n, k) * 2 * (size_t)n);
+    c.take<int2>((size_t)(m2 > 0 ? m2 : 1));
+    c.take<int2>((size_t)cta_bfs_shape(n, k).slots * 2 * (size_t)n);
     c.take<unsigned>(1);
     c.take<char>(msbfs_pull_workspace(n));
     return c.size();
@@ -648,10 +771,11 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     CtaBfsArgs B;
     B.n = n; B.rowptr = rowptr; B.colidx = colidx; B.nsrc = k; B.sources = sources; B.dist = dist;
     B.status = status;
-    const int slots = cta_bfs_slots(n, k);
-    int4 *adj = c.take<int4>((size_t)(m2 > 0 ? m2 : 1));
+    const CtaBfsShape S = cta_bfs_shape(n, k);
+    int2 *adj = c.take<int2>((size_t)(m2 > 0 ? m2 : 1));
     B.adj = adj;
-    B.queues = c.take<int2>((size_t)slots * 2 * (size_t)n);
+    B.queues = c.take<int2>((size_t)S.slots * 2 * (size_t)n);
+    B.qsm = S.qsm;
     unsigned *gaveup = c.take<unsigned>(1);
     const size_t pw = msbfs_pull_workspace(n);
     void *pws = c.take<char>(pw);
@@ -661,19 +785,16 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     SSM_TRY_CUDA(cudaMemsetAsync(gaveup, 0, sizeof(unsigned), s));
     int rc = launch_msbfs_pull(n, rowptr, colidx, k, sources, dist, status, gaveup, pws, pw, s);
     if (rc) return rc;
-    // the 16-byte expanded adjacency saves a dependent load per level but
-    // quadruples adjacency traffic: use it only while it stays L2-resident
-    const bool adj4 = (size_t)m2 * sizeof(int4) <= kAdj4MaxBytes;
-    if (adj4) {
-      rc = expand_adj(m2, rowptr, colidx, adj, s);
-      if (rc) return rc;
+    // the packed adjacency saves a dependent rowptr load per level but doubles
+    // adjacency traffic: use it only while it stays L2-resident
+    const bool packed = (size_t)m2 * sizeof(int2) <= kAdj2MaxBytes && n < (1 << kAdj2NodeBits);
+    if (packed && m2 > 0) {
+      const int blocks = (int)std::min<int64_t>((m2 + 255) / 256, (int64_t)num_sms() * 8);
+      note_launch(), k_pack_adj<<<blocks, 256, 0, s>>>(m2, rowptr, colidx, adj);
     }
-    const void *kern = adj4 ? (const void *)k_bfs_cta<true> : (const void *)k_bfs_cta<false>;
-    const size_t smem = (size_t)((n + 31) / 32) * 4;
-    SSM_TRY_CUDA(allow_dynamic_smem(kern));
     void *args[] = {&B};
     note_launch();
-    SSM_TRY_CUDA(cudaLaunchKernel(kern, dim3(slots), dim3(kCtaThreads), args, smem, s));
+    SSM_TRY_CUDA(cudaLaunchKernel(cta_bfs_kernel(packed, S.many), dim3(S.slots), dim3(kCtaThreads), args, S.smem, s));
     return SSM_OK;
   }
   MsBfsArgs A;

@@ -217,47 +217,6 @@ __device__ __forceinline__ void warp_for_each_neighbor_batched(int beg, int end,
   }
 }
 
-// The same over an edge-expanded adjacency: adj[t] = (v, rowptr[v],
-// rowptr[v+1], 0) for colidx[t] = v, so a neighbour and its row range arrive
-// in one 16-byte load.  gather(u, e) and emit(u, e, act) receive the entry.
-template <int U, class Gather, class Emit>
-__device__ __forceinline__ void warp_for_each_edge4_batched(int beg, int end, const int4 *__restrict__ adj,
-                                                            Gather &&gather, Emit &&emit) {
-  const unsigned lane = threadIdx.x & 31u;
-  const int deg = end > beg ? end - beg : 0;
-  int incl = deg;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((int)lane >= o) incl += t;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  for (int base = 0; base < total; base += 32 * U) {
-    int4 e[U];
-    bool act[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + 32 * u + (int)lane;
-      act[u] = idx < total;
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        const int pv = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-        if (pv <= idx) lo += step;
-      }
-      const int own = lo > 31 ? 31 : lo;
-      const int o_incl = __shfl_sync(0xffffffffu, incl, own);
-      const int o_deg = __shfl_sync(0xffffffffu, deg, own);
-      const int o_beg = __shfl_sync(0xffffffffu, beg, own);
-      e[u] = act[u] ? __ldg(adj + o_beg + (idx - (o_incl - o_deg))) : make_int4(0, 0, 0, 0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) act[u] = act[u] && gather(u, e[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) emit(u, e[u], act[u]);
-  }
-}
-
 // Appends val for the lanes with pred to q (with a shared-memory counter) and
 // returns each appending lane's slot; all lanes must call it together.
 __device__ __forceinline__ unsigned warp_slot(bool pred, unsigned *s_counter) {

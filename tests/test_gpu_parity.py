@@ -189,6 +189,34 @@ def test_pivot_bfs_repeated_pivots():
     assert np.array_equal(dip, O.pivot_dist(og, piv))
 
 
+def test_pivot_bfs_long_graph_with_hub_rows():
+    """A path of 300 nodes (too deep for the pulled BFS) carrying a star of 1000
+    leaves and nodes of degree 20 to 40: the per-source BFS walks short rows
+    one lane per row and the long ones with the whole warp, in one level."""
+    rng = np.random.default_rng(11)
+    L = 300
+    s = list(range(L - 1))
+    d = list(range(1, L))
+    nxt = L
+    for hub, leaves in [(150, 1000), (40, 33), (41, 32), (260, 20), (261, 40)]:
+        s += [hub] * leaves
+        d += list(range(nxt, nxt + leaves))
+        nxt += leaves
+    # a few chords between leaves of different hubs
+    leaves_all = np.arange(L, nxt)
+    a, b = rng.choice(leaves_all, 50), rng.choice(leaves_all, 50)
+    keep = a != b
+    s += list(a[keep])
+    d += list(b[keep])
+    n = nxt
+    s, d = np.array(s, np.int32), np.array(d, np.int32)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    piv = O.maxmin(og, 12, 0)
+    dip = ssm.ssm_pivot_bfs(g, torch.from_numpy(piv).to(DEV)).cpu().numpy()
+    assert np.array_equal(dip, O.pivot_dist(og, piv))
+
+
 @pytest.mark.parametrize("long_arm", [False, True])
 def test_pivot_bfs_disconnected(long_arm):
     # two paths: short (the pulled BFS notices) or longer than 24 levels (the
