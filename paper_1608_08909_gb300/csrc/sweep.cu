@@ -56,8 +56,11 @@ constexpr int kSweepThreads = 256;
 constexpr int kShortDeg = 32;   // neighbour rows up to this length: one thread
 constexpr int kMidDeg = 1024;   // up to this length: one warp; longer rows: one block
 constexpr size_t kSmemBudget = 200 * 1024;
-constexpr int kFullPlane = 6144;  // full-table mode: k (max d + 1) <= this; w and w d in two planes of this many floats
+constexpr int kFullPlane = 6112;  // full-table mode: k (max d + 1) <= this; w and w d in two planes of this many floats
 constexpr unsigned kFullPlaneBytes = kFullPlane * 4u;
+// full-table mode: both planes in static shared memory (a fixed address, so a
+// table read is one shared load at the node's byte offset plus a constant)
+__shared__ __align__(16) float g_wtab[2 * kFullPlane];
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
 #ifndef SSM_SWEEP_PREFETCH
@@ -324,16 +327,14 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
   float4 *pxy = reinterpret_cast<float4 *>(smem);       // (-x, -x, -y, -y) per pivot
   uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
   float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
-  float *wtab = reinterpret_cast<float *>(pidx + A.k);  // full-table mode: the two planes of A.wtab
   const int n = A.n, k = A.k;
   // the weight tables do not depend on the previous kernels: load them first
   if (SMEM)
     for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
-  const unsigned wrow = 4u * (unsigned)(A.dmax + 1);  // bytes of one pivot's row of a plane
-  if (FULL)
+  if constexpr (FULL)
     for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) {
-      wtab[t] = __ldg(A.wtab + t);
-      wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
+      g_wtab[t] = __ldg(A.wtab + t);
+      g_wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
     }
   wait_previous_kernel();
   if (__ldcg(A.stop)) return;
@@ -351,7 +352,8 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     pxy[a] = make_float4(-xy.x, -xy.x, -xy.y, -xy.y);
     pidx[a] = make_uint2(tab0 + 4u * soff - 4u * 0x4B000000u, 0x4B000000u | dcap);
   }
-  const unsigned wtab0 = FULL ? (unsigned)__cvta_generic_to_shared(wtab) : 0u;
+  unsigned wtab0 = 0u;
+  if constexpr (FULL) wtab0 = (unsigned)__cvta_generic_to_shared(g_wtab);
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
@@ -397,16 +399,17 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     auto load_words = [&](int a) -> DWords { return __ldg(tp + (unsigned)a * 32u); };
     float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
     asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
-    // full-table mode: w and w d of a node pair land in register pairs (the two
-    // planes sit a fixed kFullPlaneBytes apart), so every product is packed
+    // full-table mode: a d word holds the byte offsets 4 (a (dmax + 1) + d) of
+    // two nodes' table entries; w and w d of a node pair land in register
+    // pairs (the two planes sit a fixed kFullPlaneBytes apart), so every
+    // product is packed
     auto pivot_term_full = [&](int a, DWords pw) {
       const float4 P = pxy[a];  // (-x, -x, -y, -y)
       const float2 px2 = make_float2(P.x, P.y), py2 = make_float2(P.z, P.w);
-      const unsigned tb = wtab0 + (unsigned)a * wrow;
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        const unsigned al = tb + 4u * (pk & 0xFFFFu), ah = tb + 4u * (pk >> 16);
+        const unsigned al = wtab0 + (pk & 0xFFFFu), ah = wtab0 + (pk >> 16);
         const float2 w2 = make_float2(lds_f32(al), lds_f32(ah));
         const float2 wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
         const float2 dx2 = __fadd2_rn(xi2[j], px2);
@@ -572,9 +575,12 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 }
 
 // ----------------------------------------------------------------- setup (once per ssm_iterate)
-// dtile[((t k + a) 32 + l) kPpl + j] = d_ip[a][i] | d_ip[a][i + 1] << 16 with
-// i = t kTileNodes + kNpl l + 2 j (0 past the last node)
-__global__ void k_tile_dip(int32_t n, int32_t k, const uint16_t *__restrict__ dip, unsigned *__restrict__ dtile) {
+// dtile[((t k + a) 32 + l) kPpl + j] = e(d_ip[a][i]) | e(d_ip[a][i + 1]) << 16 with
+// i = t kTileNodes + kNpl l + 2 j (d = 0 past the last node); e(d) = d, or in
+// full-table mode (row = dmax + 1 > 0) the byte offset 4 (a row + d) of the
+// node's entry in a table plane
+__global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__restrict__ dip,
+                           unsigned *__restrict__ dtile) {
   const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
   const int64_t total = ntiles * (int64_t)k * 32 * kPpl;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
@@ -585,9 +591,13 @@ __global__ void k_tile_dip(int32_t n, int32_t k, const uint16_t *__restrict__ di
     const int a = (int)(ta % k);
     const int64_t t = ta / k;
     const int64_t i = t * kTileNodes + (int64_t)kNpl * l + 2 * j;
-    const uint16_t *row = dip + (size_t)a * n;
-    const unsigned lo = i < n ? (unsigned)__ldg(row + i) : 0u;
-    const unsigned hi = i + 1 < n ? (unsigned)__ldg(row + i + 1) : 0u;
+    const uint16_t *drow = dip + (size_t)a * n;
+    unsigned lo = i < n ? (unsigned)__ldg(drow + i) : 0u;
+    unsigned hi = i + 1 < n ? (unsigned)__ldg(drow + i + 1) : 0u;
+    if (row > 0) {
+      lo = 4u * ((unsigned)a * (unsigned)row + lo);
+      hi = 4u * ((unsigned)a * (unsigned)row + hi);
+    }
     dtile[w] = lo | (hi << 16);
   }
 }
@@ -624,8 +634,9 @@ __global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict_
 }
 
 // full-table mode: den[i] = deg(i) + sum_{a = 0..k-1} w'_ia in FP32, pivots in
-// order (the sum the clamped mode forms inside every sweep); one warp per tile
-__global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *__restrict__ dtile,
+// order (the sum the clamped mode forms inside every sweep); one warp per tile;
+// dtile holds table byte offsets
+__global__ void k_sweep_den(int32_t n, int32_t k, const unsigned *__restrict__ dtile,
                             const float *__restrict__ wtab, const int32_t *__restrict__ rowptr,
                             float *__restrict__ den) {
   const unsigned lane = threadIdx.x & 31u;
@@ -638,12 +649,11 @@ __global__ void k_sweep_den(int32_t n, int32_t k, int32_t dmax, const unsigned *
     for (int q = 0; q < kNpl; ++q) acc[q] = 0.f;
     for (int a = 0; a < k; ++a) {
       const DWords pw = __ldg(tp + (int64_t)a * 32);
-      const float *row = wtab + (int64_t)a * (dmax + 1);
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        acc[2 * j] += __ldg(row + (pk & 0xFFFFu));
-        acc[2 * j + 1] += __ldg(row + (pk >> 16));
+        acc[2 * j] += __ldg(wtab + ((pk & 0xFFFFu) >> 2));
+        acc[2 * j + 1] += __ldg(wtab + (pk >> 18));
       }
     }
     const int64_t i0 = tile * kTileNodes + (int64_t)kNpl * lane;
@@ -888,18 +898,18 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     A.dmax = (int32_t)dmax;
     A.wtab = w.wtab;
     A.den = w.den;
-    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, dip, w.dtile);
+    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile);
     if (full) {
       note_launch(), k_build_wtab<<<std::max(1, std::min(sms * 4, (int)(((int64_t)k * (dmax + 1) + 255) / 256))), 256, 0,
                                     s>>>(k, (int32_t)dmax, cnt_off, cnt, w.wtab);
       note_launch(), k_sweep_den<<<std::max(1, (int)std::min<int64_t>(((int64_t)n + 511) / 512, sms * 8)), 256, 0, s>>>(
-          n, k, (int32_t)dmax, w.dtile, w.wtab, rowptr, w.den);
+          n, k, w.dtile, w.wtab, rowptr, w.den);
     } else {
       note_launch(), k_build_stab<<<std::min(k, sms * 4), 128, 0, s>>>(k, cnt_off, cnt, w.stab);
     }
     const size_t piv = (size_t)k * (sizeof(float4) + sizeof(uint2));
     if (full) {
-      smem = piv + 2 * (size_t)kFullPlaneBytes;
+      smem = piv;  // the table planes are static shared memory
       kern = (const void *)k_sweep_f32<kFull>;
     } else {
       const size_t tab = (size_t)(2 * cnt_len + k) * sizeof(float);
