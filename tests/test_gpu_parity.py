@@ -217,6 +217,41 @@ def test_pivot_bfs_long_graph_with_hub_rows():
     assert np.array_equal(dip, O.pivot_dist(og, piv))
 
 
+def _broom_graph():
+    """A path of 40 nodes ending in a hub with 5000 leaves, each leaf with a
+    pendant node: two BFS levels of 5000 nodes behind a hub row, deep enough
+    for the per-source BFS."""
+    L, B = 40, 5000
+    s = list(range(L - 1)) + [L - 1] * B + list(range(L, L + B))
+    d = list(range(1, L)) + list(range(L, L + B)) + list(range(L + B, L + 2 * B))
+    return L + 2 * B, np.array(s, np.int32), np.array(d, np.int32)
+
+
+@pytest.mark.parametrize("k", [6, 400])
+def test_pivot_bfs_wide_levels(k):
+    """Frontiers larger than the shared-memory part of the frontier queue
+    (few sources: 4096 entries per level there, the rest in global memory;
+    many sources: all in global memory), reached through a 5000-entry row."""
+    n, s, d = _broom_graph()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    rng = np.random.default_rng(k)
+    piv = np.concatenate([[0, 20], rng.integers(0, n, k - 2)]).astype(np.int32)
+    dip = ssm.ssm_pivot_bfs(g, torch.from_numpy(piv).to(DEV)).cpu().numpy()
+    assert np.array_equal(dip, O.pivot_dist(og, piv))
+
+
+def test_pivot_bfs_many_sources_deep_graph():
+    """More sources than two per SM on a large-diameter graph: four blocks
+    per SM, frontier in global memory."""
+    n, s, d = GRAPHS["rgg"]()
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    piv = np.random.default_rng(5).integers(0, n, 700).astype(np.int32)
+    dip = ssm.ssm_pivot_bfs(g, torch.from_numpy(piv).to(DEV)).cpu().numpy()
+    assert np.array_equal(dip, O.pivot_dist(og, piv))
+
+
 @pytest.mark.parametrize("long_arm", [False, True])
 def test_pivot_bfs_disconnected(long_arm):
     # two paths: short (the pulled BFS notices) or longer than 24 levels (the
