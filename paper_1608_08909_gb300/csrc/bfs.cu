@@ -372,6 +372,10 @@ constexpr int kCtaThreads = 512;
 constexpr int kCtaStep = SSM_CTA_STEP;         // edges whose loads a lane has in flight at once
 constexpr int kCtaLaneRow = SSM_CTA_LANE_ROW;  // rows up to this length: one lane; longer: the warp
 constexpr int kCtaQMax = SSM_CTA_QMAX;         // frontier entries per level kept in shared memory (at most)
+#ifndef SSM_CTA_FEW_MIN_NODES
+#define SSM_CTA_FEW_MIN_NODES 131072
+#endif
+constexpr int kCtaFewMinNodes = SSM_CTA_FEW_MIN_NODES;  // smaller graphs always take four blocks per SM
 constexpr size_t kCtaBitmapMax = 200 * 1024;   // bytes of shared memory for the visited bitmap
 constexpr size_t kAdj2MaxBytes = (size_t)SSM_ADJ2_MAX_MB << 20;  // packed adjacency kept only while it fits well inside L2
 constexpr int kAdj2NodeBits = 21;              // packed adjacency: node id below 2^21 ...
@@ -575,16 +579,18 @@ static const void *cta_bfs_kernel(bool packed, bool many) {
   return many ? (const void *)k_bfs_cta<false, 4> : (const void *)k_bfs_cta<false, 2>;
 }
 
-// Blocks of 512 threads: two per SM while the sources fit two per SM, with
-// the shared memory an SM can give each beyond the bitmap holding the first
-// qsm frontier entries of both levels; four per SM for more sources, with the
-// bitmap alone (measured on rgg256k: a shared-memory frontier at four blocks
-// per SM leaves less L1 for the adjacency reads and was slower).  Without a
-// device (workspace queries on a host) one slot per SM is assumed.
+// Blocks of 512 threads: on a large graph whose sources fit two per SM, two
+// per SM, with the shared memory an SM can give each beyond the bitmap holding
+// the first qsm frontier entries of both levels; otherwise four per SM, with
+// the bitmap alone (measured: a shared-memory frontier at four blocks per SM
+// leaves less L1 for the adjacency reads and was slower on rgg256k, and two
+// fat blocks per SM cost concurrent requests of mid-size graphs 7 % of the
+// serving capacity).  Without a device (workspace queries on a host) one slot
+// per SM is assumed.
 static CtaBfsShape cta_bfs_shape(int32_t n, int32_t nsrc) {
   CtaBfsShape S;
   const int sms = num_sms();
-  S.many = nsrc > 2 * sms;
+  S.many = nsrc > 2 * sms || n < kCtaFewMinNodes;
   const int want = S.many ? 4 : 2;
   const size_t bitmap = (size_t)(((n + 31) / 32 + 3) & ~3) * 4;
   int dev = 0, per_sm_smem = 0, per_block_max = 0;

@@ -217,22 +217,23 @@ def test_pivot_bfs_long_graph_with_hub_rows():
     assert np.array_equal(dip, O.pivot_dist(og, piv))
 
 
-def _broom_graph():
-    """A path of 40 nodes ending in a hub with 5000 leaves, each leaf with a
-    pendant node: two BFS levels of 5000 nodes behind a hub row, deep enough
-    for the per-source BFS."""
-    L, B = 40, 5000
+def _broom_graph(B):
+    """A path of 40 nodes ending in a hub with B leaves, each leaf with a
+    pendant node: two BFS levels of B nodes behind a hub row, deep enough for
+    the per-source BFS."""
+    L = 40
     s = list(range(L - 1)) + [L - 1] * B + list(range(L, L + B))
     d = list(range(1, L)) + list(range(L, L + B)) + list(range(L + B, L + 2 * B))
     return L + 2 * B, np.array(s, np.int32), np.array(d, np.int32)
 
 
-@pytest.mark.parametrize("k", [6, 400])
-def test_pivot_bfs_wide_levels(k):
+@pytest.mark.parametrize("k,B", [(6, 70000), (400, 5000), (6, 5000)])
+def test_pivot_bfs_wide_levels(k, B):
     """Frontiers larger than the shared-memory part of the frontier queue
-    (few sources: 4096 entries per level there, the rest in global memory;
-    many sources: all in global memory), reached through a 5000-entry row."""
-    n, s, d = _broom_graph()
+    (few sources on a graph above 131072 nodes: 4096 entries per level there,
+    the rest in global memory; otherwise all in global memory), reached
+    through a row of B entries."""
+    n, s, d = _broom_graph(B)
     og = O.build_csr(n, s, d)
     g = _gpu_graph(n, s, d)
     rng = np.random.default_rng(k)
