@@ -74,3 +74,28 @@ def test_fullsize_sampled_stress(rgg):
     want, wsums = O.full_stress(og, pos.cpu().numpy().astype(np.float64), 1024, 1024, 1, return_sums=True)
     np.testing.assert_allclose(sums.cpu().numpy(), wsums, rtol=1e-9)
     np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-9)
+
+
+@pytest.mark.parametrize("family", ["ba", "grid"])
+def test_one_sweep_many_tiles(family):
+    """Graphs with more than two 128-node tiles per resident warp, where every
+    warp takes whole tiles (full-table mode on the Barabasi-Albert graph,
+    clamped mode on the 800 x 800 grid)."""
+    if family == "ba":
+        n, s, d = I.ba(700000, 4, 3)
+    else:
+        n, s, d = I.grid(800, 800)
+    k = 32
+    og = O.build_csr(n, s, d)
+    g, P, pos, eig = ssm.prepare(n, s, d, k, precision=32)
+    x0 = pos.cpu().numpy().astype(np.float64)
+    dip = P.dip.cpu().numpy()
+    w = O.adapted_weights(dip, P.region.cpu().numpy())
+    want, orel = O.sweep_jacobi(og, P.pivots.cpu().numpy(), dip, w, x0)
+    p = pos.clone()
+    _, rel = ssm.ssm_iterate(g, P, p, 1)
+    got = p.cpu().numpy().astype(np.float64)
+    c = want - want.mean(0)
+    err = np.sqrt(((got - want) ** 2).sum(1)).max() / np.sqrt((c ** 2).sum(1).mean())
+    assert err < 1e-5
+    assert rel.item() == pytest.approx(orel, rel=1e-4)
