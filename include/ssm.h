@@ -66,6 +66,28 @@ const char *ssm_last_error(void);
  * after a sequence of calls to learn how many kernels the sequence issued. */
 unsigned long long ssm_kernel_launches(void);
 
+/* Sets the longest time one wait at a device-wide barrier may take before
+ * the kernel gives up with SSM_E_TIMEOUT (the persistent kernels of
+ * ssm_select_pivots, ssm_pivot_bfs, ssm_stress and ssm_pivotmds wait at such
+ * barriers between their steps); ns = 0 restores the default of 2 s, values
+ * above 2^32 - 1 are clamped.  Returns the previous setting.  A diagnostic
+ * with no counterpart in the paper, for tests of the timeout path: a limit of
+ * a few nanoseconds makes the first wait of such a kernel run out, and the
+ * kernel then records SSM_E_TIMEOUT, releases the other blocks and returns.
+ * It applies to calls made after it, on every host thread; while it is
+ * non-zero each such call also copies the limit from host memory. */
+unsigned long long ssm_set_wait_limit_ns(unsigned long long ns);
+
+/* What the last ssm_iterate call on this host thread chose, in out[4] (host):
+ *   out[0] the sweep kernel: 0 FP32 with the clamped s table in shared memory,
+ *          1 FP32 with the clamped s table in global memory, 2 FP32 with the
+ *          full (w', w' d) table, 3 FP64 with the counts in shared memory,
+ *          4 FP64 with the counts in global memory (-1: no call yet);
+ *   out[1] pivot ranges per 128-node tile (1: a warp takes whole tiles);
+ *   out[2] blocks of the sweep grid;  out[3] the largest d_ip entry (FP32) or -1.
+ * A diagnostic with no counterpart in the paper. */
+void ssm_last_sweep_config(int32_t *out);
+
 /* Synchronous: waits for `stream`, then returns the device status word
  * (SSM_OK if it is 0), or SSM_E_CUDA if the stream reported a CUDA error. */
 int ssm_check(const int32_t *status, cudaStream_t stream);
@@ -99,11 +121,38 @@ int ssm_select_pivots(int32_t n, int64_t m, const int32_t *rowptr, const int32_t
                       void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
+ * Pivot sampling, "k-means sp" (Section 4.1, the paper's recommended
+ * sampler): k max/min-sp pivots pivots_in[k] (from ssm_select_pivots) and
+ * their table dip[k*n] (from ssm_pivot_bfs) are refined by k-means over the
+ * nodes' shortest-path entries.  Node i is y_i = (d_0i, ..., d_{k-1,i}) in
+ * Z^k; cluster a starts with centre y of pivots_in[a].  Each pass assigns
+ * every node to the centre c_a minimising ||y_i - c_a||^2 (ties to the lowest
+ * a), compared as alpha_a - beta_a * t_ia with t_ia = y_i . S_a exact,
+ * alpha_a = sum_b (S_ab/n_a)^2 (FP64, b ascending) and beta_a = 2/n_a, where
+ * c_a = S_a/n_a; then the centres become the members' means (an empty cluster
+ * keeps its centre).  At most max_iter passes (the paper caps its k-means at
+ * 50); it stops after the first pass, beyond the first, that moves no node.
+ * pivots_out[a] (device int32) = the member of cluster a nearest its centre
+ * (compared exactly as n_a ||y_i||^2 - 2 t_ia, ties to the lowest node id),
+ * or pivots_in[a] if the cluster is empty.  assign[n] (device int32, may be
+ * NULL) receives each node's cluster, *iters (device int32) the passes run.
+ * The caller then recomputes d_ip for pivots_out with ssm_pivot_bfs.
+ * Asynchronous (every pass is enqueued; passes after the stop return at
+ * once).  1 <= k <= min(n, 1024), 1 <= max_iter.  Device error SSM_E_ARG
+ * when n * max(d) >= 2^32 or n * k * max(d)^2 >= 2^53 (the bounds of the
+ * exact integer arithmetic) or a pivot id is outside 0..n-1.
+ * ------------------------------------------------------------------- */
+size_t ssm_kmeans_pivots_workspace(int32_t n, int32_t k);
+int ssm_kmeans_pivots(int32_t n, int32_t k, const uint16_t *dip, const int32_t *pivots_in, int32_t max_iter,
+                      int32_t *pivots_out, int32_t *assign, int32_t *iters, int32_t *status,
+                      void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
  * Pivot distances d_ip (Algorithm 1 line 2, unit edge lengths): one
  * multi-source BFS from all k pivots at once.  Writes dip[k*n] (uint16,
  * pivot-major).  1 <= k <= 65535, n*ceil(k/32) < 2^31.  Pivots need not be
  * distinct.  Device errors: SSM_E_DISCONNECTED, SSM_E_DIST_OVERFLOW,
- * SSM_E_TIMEOUT.
+ * SSM_E_TIMEOUT, SSM_E_ARG (a pivot id outside 0..n-1).
  * ------------------------------------------------------------------- */
 size_t ssm_pivot_bfs_workspace(int32_t n, int64_t m, int32_t k);
 int ssm_pivot_bfs(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
@@ -176,7 +225,7 @@ int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
  * on which ssm_pivotmds applies the double centring at the k x k level.
  * Writes g_lo[k*k], g_hi[k*k] (device, uint64): entry a*k + b holds the low
  * and high 64 bits of G[a][b] for a <= b; entries with a > b are zero.  The
- * call zeroes both arrays itself.  Runs on the tensor cores (4-bit digit
+ * call zeroes both arrays itself.  Runs on the tensor cores (5-bit digit
  * planes in FP16, FP32 accumulation of exact integers).  1 <= k <= 1024.
  * Device errors: SSM_E_TIMEOUT (a tensor-core wait ran out).
  * ------------------------------------------------------------------- */

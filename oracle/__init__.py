@@ -54,6 +54,7 @@ def _load():
                 "orc_build_csr": [i32, i64, v, v, v, v, v],
                 "orc_bfs": [i32, v, v, i32, v],
                 "orc_maxmin": [i32, v, v, i32, i32, v],
+                "orc_kmeans_sp": [i32, i32, v, v, i32, v, v, v],
                 "orc_pivot_dist": [i32, v, v, i32, v, v],
                 "orc_regions": [i32, i32, v, v],
                 "orc_histograms": [i32, i32, v, v, v, v, v, i64],
@@ -61,6 +62,8 @@ def _load():
                 "orc_pivotmds": [i32, i32, v, v, v, v],
                 "orc_rescale": [i32, v, v, v],
                 "orc_sweep_jacobi": [i32, v, v, i32, v, v, v, v, v, v],
+                "orc_sweep_jacobi_rows": [i32, v, v, i32, v, v, v, v, v, i32, i32],
+                "orc_stress_sums_range": [i32, v, v, v, i32, i32, u64, i32, i32, v],
                 "orc_sweep_gs": [i32, v, v, i32, v, v, v, v],
                 "orc_splitmix64": [u64, i64, v],
                 "orc_sample_pairs": [i32, i32, i32, u64, v, v],
@@ -70,6 +73,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            lib.orc_relchange.argtypes = [i32, v, v]
+            lib.orc_relchange.restype = d
             _lib = lib
     return _lib
 
@@ -114,6 +119,20 @@ def maxmin(g: Graph, k: int, start: int = 0) -> np.ndarray:
     piv = np.zeros(k, np.int32)
     _chk(_load().orc_maxmin(g.n, _p(g.rowptr), _p(g.colidx), k, start, _p(piv)), "maxmin")
     return piv
+
+
+def kmeans_sp(dip: np.ndarray, pivots, max_iter: int = 50):
+    """k-means sp (Section 4.1) from the max/min-sp pivots and their d_ip table:
+    returns (new pivots [k] int32, final cluster of every node [n] int32,
+    assignment passes)."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    pivots = _i32(pivots)
+    k, n = dip.shape
+    out = np.zeros(k, np.int32)
+    asg = np.zeros(n, np.int32)
+    it = ctypes.c_int32(0)
+    _chk(_load().orc_kmeans_sp(n, k, _p(dip), _p(pivots), max_iter, _p(out), _p(asg), ctypes.byref(it)), "kmeans_sp")
+    return out, asg, it.value
 
 
 def pivot_dist(g: Graph, pivots) -> np.ndarray:
@@ -209,6 +228,77 @@ def sweep_jacobi(g: Graph, pivots, dip, w, pos):
     return out, rel.value
 
 
+def sweep_jacobi_threads(g: Graph, pivots, dip, w, pos, threads: int):
+    """sweep_jacobi with the node loop cut into `threads` contiguous ranges run
+    by host threads at once (ctypes releases the GIL during each C call).
+    Every node's update is computed exactly as in sweep_jacobi, and the
+    relative change is reduced afterwards in node order, so the result is
+    identical to sweep_jacobi's."""
+    import concurrent.futures as cf
+
+    pivots = _i32(pivots)
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros_like(pos)
+    n = g.n
+    cuts = [n * t // threads for t in range(threads + 1)]
+    lib = _load()
+
+    def run(t):
+        return lib.orc_sweep_jacobi_rows(n, _p(g.rowptr), _p(g.colidx), len(pivots), _p(pivots), _p(dip), _p(w),
+                                         _p(pos), _p(out), cuts[t], cuts[t + 1])
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for rc in ex.map(run, range(threads)):
+            _chk(rc, "sweep_jacobi_rows")
+    return out, lib.orc_relchange(n, _p(pos), _p(out))
+
+
+def pivot_dist_threads(g: Graph, pivots, threads: int) -> np.ndarray:
+    """pivot_dist with the pivots split over `threads` host threads; every row
+    is one independent BFS, so the table is identical to pivot_dist's."""
+    import concurrent.futures as cf
+
+    pivots = _i32(pivots)
+    parts = np.array_split(np.arange(len(pivots)), threads)
+    with cf.ThreadPoolExecutor(threads) as ex:
+        rows = list(ex.map(lambda idx: pivot_dist(g, pivots[idx]) if len(idx) else None, parts))
+    return np.concatenate([r for r in rows if r is not None], axis=0)
+
+
+def stress_sums_range(g: Graph, pos, S: int, T: int, seed: int, q0: int, q1: int) -> np.ndarray:
+    """The pair sums {sum (r-d)^2/d^2, S1, S2, N} of full_stress's pair list
+    restricted to its sources q0 <= q < q1."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    sums = np.zeros(4, np.float64)
+    _chk(_load().orc_stress_sums_range(g.n, _p(g.rowptr), _p(g.colidx), _p(pos), S, T, ctypes.c_uint64(seed), q0, q1,
+                                       _p(sums)), "stress_sums_range")
+    return sums
+
+
+def full_stress_threads(g: Graph, pos, S: int, T: int, seed: int, threads: int):
+    """full_stress's sums over its sources split into `threads` ranges run at
+    once and added in range order (the association of the sums differs from
+    full_stress's by rounding only).  Returns (out[4], sums[4]) with out as in
+    full_stress."""
+    import concurrent.futures as cf
+
+    nsrc = S if S > 0 else g.n
+    cuts = [nsrc * t // threads for t in range(threads + 1)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda t: stress_sums_range(g, pos, S, T, seed, cuts[t], cuts[t + 1]), range(threads)))
+    sums = np.zeros(4, np.float64)
+    for p_ in parts:
+        sums += p_
+    raw, s1, s2, npairs = sums
+    pairs = 0.5 * g.n * (g.n - 1)
+    f = pairs / npairs if S > 0 else 1.0
+    out = np.array([raw * f, s1 / s2 if s2 > 0 else 0.0, (npairs - s1 * s1 / s2 if s2 > 0 else npairs) * f, 0.0])
+    out[3] = out[2] / pairs
+    return out, sums
+
+
 def sweep_gs(g: Graph, pivots, dip, w, pos):
     """One in-place (node by node, ascending) update of Eq. 4; returns new positions."""
     pivots = _i32(pivots)
@@ -256,10 +346,13 @@ class Prepared:
         self.ecc, self.cnt_off, self.cnt, self.w, self.pos0, self.eig = ecc, cnt_off, cnt, w, pos0, eig
 
 
-def prepare(n: int, src, dst, k: int, start: int = 0) -> Prepared:
+def prepare(n: int, src, dst, k: int, start: int = 0, sampler: str = "maxmin", kmeans_iters: int = 50) -> Prepared:
     g = build_csr(n, src, dst)
     piv = maxmin(g, k, start)
     dip = pivot_dist(g, piv)
+    if sampler == "kmeans":
+        piv, _, _ = kmeans_sp(dip, piv, kmeans_iters)
+        dip = pivot_dist(g, piv)
     reg = regions(dip)
     ecc, off, cnt = histograms(dip, reg)
     w = adapted_weights(dip, reg)

@@ -12,6 +12,7 @@
  *   orc_build_csr        simple undirected graph G=(V,E)            (Section 1)
  *   orc_bfs              graph-theoretic distances d_ij, plain queue (Section 1, Eq. 1)
  *   orc_maxmin           "max/min sp" pivot sampling                 (Section 4.1)
+ *   orc_kmeans_sp        "k-means sp" pivot sampling                 (Section 4.1)
  *   orc_pivot_dist       d_ip for all pivots, one BFS per pivot      (Algorithm 1, line 2)
  *   orc_regions          regions R(p): closest pivot                 (Section 3)
  *   orc_histograms       per-pivot distance counts over R(p)         (Section 3, w'_ip)
@@ -19,8 +20,10 @@
  *   orc_pivotmds         PivotMDS initial layout                     (Algorithm 1, line 3)
  *   orc_rescale          edge-length rescale                          (Algorithm 1, line 4)
  *   orc_sweep_jacobi     one update of Eq. 4 for all nodes from X^t  (Eq. 4)
+ *                        (orc_sweep_jacobi_rows: the same for a node range)
  *   orc_sweep_gs         the same, in place node by node              (Algorithm 1, lines 6-10)
  *   orc_full_stress      Eq. 1 over all pairs, or over sampled pairs  (Eq. 1, Section 4)
+ *                        (orc_stress_sums_range: its pair sums for a source range)
  *
  * Readings taken where the paper is silent (each is listed with its reason
  * in the design notes of the repository):
@@ -147,6 +150,110 @@ int orc_maxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t 
   }
   free(mind); free(d);
   return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* pivot sampling: k-means sp (Section 4.1)                             */
+/* ------------------------------------------------------------------ */
+
+/* k-means over the shortest-path entries of k max/min-sp pivots.  Node i is
+ * the point y_i = (d_{0 i}, ..., d_{k-1 i}) of Z^k (column i of the pivot-
+ * major table dip); cluster a starts with centre y_{pivots_in[a]}.  Lloyd
+ * iterations, at most max_iter (the paper caps its k-means at 50):
+ *   assignment: node i joins the cluster a minimising ||y_i - c_a||^2, ties to
+ *     the lowest a; with c_a = S_a / n_a (S_a an integer vector, n_a > 0) the
+ *     quantity compared is g(i,a) = alpha_a - beta_a * t_ia, where
+ *     t_ia = y_i . S_a (an exact integer), beta_a = 2 / n_a and
+ *     alpha_a = sum_b (S_ab / n_a)^2 summed in b order, all in FP64 with one
+ *     rounding per operation -- ||y_i - c_a||^2 minus the common ||y_i||^2;
+ *   stop when an assignment (after the first) changes no node;
+ *   update: S_a = sum of the members' y, n_a = member count; a cluster left
+ *     empty keeps its previous centre.
+ * New pivot of cluster a: the member i minimising ||y_i - c_a||^2, compared
+ * exactly as the integer n_a ||y_i||^2 - 2 t_ia, ties to the lowest node id; a
+ * cluster empty at the end keeps pivots_in[a].  The exact-integer steps need
+ * n * k * max(d)^2 < 2^53 (else ORC_E_ARG).  assign (optional) receives the
+ * final cluster of every node, *iters the number of assignment passes. */
+int orc_kmeans_sp(int32_t n, int32_t k, const uint16_t *dip, const int32_t *pivots_in, int32_t max_iter,
+                  int32_t *pivots_out, int32_t *assign, int32_t *iters) {
+  if (n < 1 || k < 1 || max_iter < 1) return ORC_E_ARG;
+  int64_t dmax = 0;
+  for (int64_t t = 0; t < (int64_t)k * n; ++t)
+    if (dip[t] > dmax) dmax = dip[t];
+  if ((double)n * (double)k * (double)dmax * (double)dmax >= 9007199254740992.0) return ORC_E_ARG;
+  int64_t *S = (int64_t *)malloc((size_t)k * k * sizeof(int64_t));
+  int64_t *Snew = (int64_t *)malloc((size_t)k * k * sizeof(int64_t));
+  int64_t *cnt = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+  int64_t *cnew = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+  double *alpha = (double *)malloc((size_t)k * sizeof(double));
+  double *beta = (double *)malloc((size_t)k * sizeof(double));
+  int32_t *asg = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!S || !Snew || !cnt || !cnew || !alpha || !beta || !asg) {
+    free(S); free(Snew); free(cnt); free(cnew); free(alpha); free(beta); free(asg);
+    return ORC_E_NOMEM;
+  }
+  for (int32_t a = 0; a < k; ++a) {
+    for (int32_t b = 0; b < k; ++b) S[(int64_t)a * k + b] = dip[(int64_t)b * n + pivots_in[a]];
+    cnt[a] = 1;
+  }
+  for (int32_t i = 0; i < n; ++i) asg[i] = -1;
+  int32_t it = 0;
+  for (int32_t pass = 1; pass <= max_iter; ++pass) {
+    for (int32_t a = 0; a < k; ++a) {
+      double al = 0.0;
+      for (int32_t b = 0; b < k; ++b) {
+        double c = (double)S[(int64_t)a * k + b] / (double)cnt[a];
+        al += c * c;
+      }
+      alpha[a] = al;
+      beta[a] = 2.0 / (double)cnt[a];
+    }
+    int64_t changed = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t best = -1;
+      double gbest = 0.0;
+      for (int32_t a = 0; a < k; ++a) {
+        int64_t t = 0;
+        for (int32_t b = 0; b < k; ++b) t += (int64_t)dip[(int64_t)b * n + i] * S[(int64_t)a * k + b];
+        double g = alpha[a] - beta[a] * (double)t;
+        if (best < 0 || g < gbest) { best = a; gbest = g; }
+      }
+      if (asg[i] != best) { asg[i] = best; ++changed; }
+    }
+    it = pass;
+    if (pass > 1 && changed == 0) break;
+    memset(Snew, 0, (size_t)k * k * sizeof(int64_t));
+    memset(cnew, 0, (size_t)k * sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t a = asg[i];
+      cnew[a] += 1;
+      for (int32_t b = 0; b < k; ++b) Snew[(int64_t)a * k + b] += dip[(int64_t)b * n + i];
+    }
+    for (int32_t a = 0; a < k; ++a)
+      if (cnew[a] > 0) {
+        cnt[a] = cnew[a];
+        for (int32_t b = 0; b < k; ++b) S[(int64_t)a * k + b] = Snew[(int64_t)a * k + b];
+      }
+  }
+  for (int32_t a = 0; a < k; ++a) pivots_out[a] = -1;
+  int64_t *vbest = cnew; /* reuse: best n_a ||y_i||^2 - 2 t_ia per cluster */
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t a = asg[i];
+    int64_t yy = 0, t = 0;
+    for (int32_t b = 0; b < k; ++b) {
+      int64_t y = dip[(int64_t)b * n + i];
+      yy += y * y;
+      t += y * S[(int64_t)a * k + b];
+    }
+    int64_t v = cnt[a] * yy - 2 * t;
+    if (pivots_out[a] < 0 || v < vbest[a]) { pivots_out[a] = i; vbest[a] = v; }
+  }
+  for (int32_t a = 0; a < k; ++a)
+    if (pivots_out[a] < 0) pivots_out[a] = pivots_in[a];
+  if (assign) memcpy(assign, asg, (size_t)n * sizeof(int32_t));
+  if (iters) *iters = it;
+  free(S); free(Snew); free(cnt); free(cnew); free(alpha); free(beta); free(asg);
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------ */
@@ -420,22 +527,36 @@ static void eq4_update(int32_t n, const int32_t *rowptr, const int32_t *colidx, 
   else { out[0] = xi; out[1] = yi; }
 }
 
+/* The Jacobi update of Eq. 4 for the nodes i0 <= i < i1 only (every node's
+ * new position depends on X^t alone, so node ranges are independent). */
+int orc_sweep_jacobi_rows(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                          const int32_t *pivots, const uint16_t *dip, const double *w,
+                          const double *pos_in, double *pos_out, int32_t i0, int32_t i1) {
+  if (i0 < 0 || i1 < i0 || i1 > n) return ORC_E_ARG;
+  for (int32_t i = i0; i < i1; ++i)
+    eq4_update(n, rowptr, colidx, k, pivots, dip, w, pos_in, i, pos_out + 2 * (int64_t)i);
+  return ORC_OK;
+}
+
+/* relative positional change (Algorithm 1 line 5, read as a Frobenius ratio):
+ * ||X^{t+1} - X^t||_F / ||X^t||_F, summed in coordinate order */
+double orc_relchange(int32_t n, const double *pos_in, const double *pos_out) {
+  double num = 0.0, den = 0.0;
+  for (int64_t t = 0; t < 2 * (int64_t)n; ++t) {
+    double dd = pos_out[t] - pos_in[t];
+    num += dd * dd;
+    den += pos_in[t] * pos_in[t];
+  }
+  return den > 0.0 ? sqrt(num) / sqrt(den) : 0.0;
+}
+
 /* Jacobi: X^{t+1}_i from X^t for every i; relchange (optional) receives
  * ||X^{t+1} - X^t||_F / ||X^t||_F. */
 int orc_sweep_jacobi(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                      const int32_t *pivots, const uint16_t *dip, const double *w,
                      const double *pos_in, double *pos_out, double *relchange) {
-  for (int32_t i = 0; i < n; ++i)
-    eq4_update(n, rowptr, colidx, k, pivots, dip, w, pos_in, i, pos_out + 2 * (int64_t)i);
-  if (relchange) {
-    double num = 0.0, den = 0.0;
-    for (int64_t t = 0; t < 2 * (int64_t)n; ++t) {
-      double dd = pos_out[t] - pos_in[t];
-      num += dd * dd;
-      den += pos_in[t] * pos_in[t];
-    }
-    *relchange = den > 0.0 ? sqrt(num) / sqrt(den) : 0.0;
-  }
+  orc_sweep_jacobi_rows(n, rowptr, colidx, k, pivots, dip, w, pos_in, pos_out, 0, n);
+  if (relchange) *relchange = orc_relchange(n, pos_in, pos_out);
   return ORC_OK;
 }
 
@@ -486,6 +607,38 @@ int orc_sample_pairs(int32_t n, int32_t S, int32_t T, uint64_t seed, int32_t *sr
   return ORC_OK;
 }
 
+/* Pair sums of Eq. 1 over the sources q0 <= q < q1 of the pair list that
+ * orc_full_stress uses (S == 0: sources are the nodes, targets j > i; S > 0:
+ * the S*T sampled pairs of orc_sample_pairs).  acc[4] receives
+ * {sum (r-d)^2/d^2, S1 = sum r/d, S2 = sum r^2/d^2, N}, each summed pair by
+ * pair in list order.  srcs/tgts are the sampled list (NULL when S == 0). */
+static int stress_accumulate(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *pos,
+                             int32_t S, int32_t T, const int32_t *srcs, const int32_t *tgts, int32_t q0,
+                             int32_t q1, int32_t *dist, double *acc) {
+  double raw = 0.0, s1 = 0.0, s2 = 0.0, np = 0.0;
+  int rc = ORC_OK;
+  for (int32_t q = q0; rc == ORC_OK && q < q1; ++q) {
+    int32_t i = S > 0 ? srcs[q] : q;
+    rc = orc_bfs(n, rowptr, colidx, i, dist);
+    int32_t cnt = S > 0 ? T : n;
+    for (int32_t l = 0; rc == ORC_OK && l < cnt; ++l) {
+      int32_t j = S > 0 ? tgts[(int64_t)q * T + l] : l;
+      if (S == 0 && j <= i) continue;
+      if (dist[j] < 0) { rc = ORC_E_DISCONNECTED; break; }
+      double d = (double)dist[j];
+      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
+      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
+      double r = sqrt(dx * dx + dy * dy);
+      raw += (r - d) * (r - d) / (d * d);
+      s1 += r / d;
+      s2 += r * r / (d * d);
+      np += 1.0;
+    }
+  }
+  acc[0] = raw; acc[1] = s1; acc[2] = s2; acc[3] = np;
+  return rc;
+}
+
 /* Full stress of the layout pos.
  * S == 0: exhaustive, every pair i < j (a BFS from every node).
  * S > 0:  the S*T sampled pairs of orc_sample_pairs (a BFS from every source).
@@ -506,29 +659,11 @@ int orc_full_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, con
     if (!srcs || !tgts) { free(dist); free(srcs); free(tgts); return ORC_E_NOMEM; }
     orc_sample_pairs(n, S, T, seed, srcs, tgts);
   }
-  double raw = 0.0, s1 = 0.0, s2 = 0.0, np = 0.0;
-  int rc = ORC_OK;
-  int32_t nsrc = S > 0 ? S : n;
-  for (int32_t q = 0; rc == ORC_OK && q < nsrc; ++q) {
-    int32_t i = S > 0 ? srcs[q] : q;
-    rc = orc_bfs(n, rowptr, colidx, i, dist);
-    int32_t cnt = S > 0 ? T : n;
-    for (int32_t l = 0; rc == ORC_OK && l < cnt; ++l) {
-      int32_t j = S > 0 ? tgts[(int64_t)q * T + l] : l;
-      if (S == 0 && j <= i) continue;
-      if (dist[j] < 0) { rc = ORC_E_DISCONNECTED; break; }
-      double d = (double)dist[j];
-      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
-      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
-      double r = sqrt(dx * dx + dy * dy);
-      raw += (r - d) * (r - d) / (d * d);
-      s1 += r / d;
-      s2 += r * r / (d * d);
-      np += 1.0;
-    }
-  }
+  double acc[4];
+  int rc = stress_accumulate(n, rowptr, colidx, pos, S, T, srcs, tgts, 0, S > 0 ? S : n, dist, acc);
   free(dist); free(srcs); free(tgts);
   if (rc != ORC_OK) return rc;
+  double raw = acc[0], s1 = acc[1], s2 = acc[2], np = acc[3];
   double pairs = 0.5 * (double)n * (double)(n - 1);
   double f = S > 0 ? pairs / np : 1.0;
   if (sums) { sums[0] = raw; sums[1] = s1; sums[2] = s2; sums[3] = np; }
@@ -537,4 +672,25 @@ int orc_full_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, con
   out[2] = (s2 > 0.0 ? np - s1 * s1 / s2 : np) * f;
   out[3] = out[2] / pairs;
   return ORC_OK;
+}
+
+/* The pair sums of orc_full_stress restricted to the sources q0 <= q < q1 of
+ * its pair list (so that independent source ranges can be evaluated by
+ * separate callers and added); sums[4] as in orc_full_stress. */
+int orc_stress_sums_range(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *pos,
+                          int32_t S, int32_t T, uint64_t seed, int32_t q0, int32_t q1, double *sums) {
+  int32_t nsrc = S > 0 ? S : n;
+  if (n < 2 || S < 0 || (S > 0 && T < 1) || q0 < 0 || q1 < q0 || q1 > nsrc) return ORC_E_ARG;
+  int32_t *dist = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *srcs = NULL, *tgts = NULL;
+  if (!dist) return ORC_E_NOMEM;
+  if (S > 0) {
+    srcs = (int32_t *)malloc((size_t)S * sizeof(int32_t));
+    tgts = (int32_t *)malloc((size_t)S * T * sizeof(int32_t));
+    if (!srcs || !tgts) { free(dist); free(srcs); free(tgts); return ORC_E_NOMEM; }
+    orc_sample_pairs(n, S, T, seed, srcs, tgts);
+  }
+  int rc = stress_accumulate(n, rowptr, colidx, pos, S, T, srcs, tgts, q0, q1, dist, sums);
+  free(dist); free(srcs); free(tgts);
+  return rc;
 }

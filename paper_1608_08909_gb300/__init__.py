@@ -23,6 +23,7 @@ from . import _build
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
     "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+    "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -56,11 +57,15 @@ def lib():
                 "ssm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
                 "ssm_last_error": (ctypes.c_char_p, []),
                 "ssm_kernel_launches": (ctypes.c_ulonglong, []),
+                "ssm_set_wait_limit_ns": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
+                "ssm_last_sweep_config": (None, [v]),
                 "ssm_check": (ctypes.c_int, [v, v]),
                 "ssm_build_graph_workspace": (sz, [i32, i64]),
                 "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, sz, v]),
                 "ssm_select_pivots_workspace": (sz, [i32, i64]),
                 "ssm_select_pivots": (ctypes.c_int, [i32, i64, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_kmeans_pivots_workspace": (sz, [i32, i32]),
+                "ssm_kmeans_pivots": (ctypes.c_int, [i32, i32, v, v, i32, v, v, v, v, v, sz, v]),
                 "ssm_pivot_bfs_workspace": (sz, [i32, i64, i32]),
                 "ssm_pivot_bfs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, sz, v]),
                 "ssm_aggregate_workspace": (sz, [i32]),
@@ -89,6 +94,21 @@ def lib():
 def kernel_launches() -> int:
     """Kernels the library has enqueued since it was loaded (ssm_kernel_launches)."""
     return int(lib().ssm_kernel_launches())
+
+
+def ssm_set_wait_limit_ns(ns: int) -> int:
+    """Longest wait at a device-wide barrier before a kernel gives up with
+    SSM_E_TIMEOUT (0: the default 2 s); returns the previous setting."""
+    return int(lib().ssm_set_wait_limit_ns(int(ns)))
+
+
+def ssm_last_sweep_config() -> dict:
+    """What the last ssm_iterate on this thread chose (ssm_last_sweep_config)."""
+    out = (ctypes.c_int32 * 4)()
+    lib().ssm_last_sweep_config(ctypes.cast(out, ctypes.c_void_p))
+    kinds = {-1: None, 0: "f32_clamped_smem", 1: "f32_clamped_global", 2: "f32_full_table", 3: "f64_counts_smem",
+             4: "f64_counts_global"}
+    return {"kernel": kinds.get(out[0], out[0]), "nsplit": out[1], "blocks": out[2], "dmax": out[3]}
 
 
 def _require_cuda():
@@ -169,6 +189,25 @@ def ssm_select_pivots(g: Graph, k: int, start: int = 0, stream=None, check: bool
     if check:
         ssm_check(st, "ssm_select_pivots", stream)
     return piv
+
+
+def ssm_kmeans_pivots(dip: torch.Tensor, pivots: torch.Tensor, max_iter: int = 50, stream=None, check: bool = True):
+    """k-means sp (Section 4.1) from max/min-sp pivots and their d_ip table.
+    Returns (new pivots [k] int32, cluster of every node [n] int32, passes run
+    as a device int32 tensor)."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    out = torch.empty(k, dtype=torch.int32, device=dev)
+    asg = torch.empty(n, dtype=torch.int32, device=dev)
+    it = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_kmeans_pivots_workspace(n, k), dev)
+    _rc(L.ssm_kmeans_pivots(n, k, _ptr(dip), _ptr(pivots.contiguous()), max_iter, _ptr(out), _ptr(asg), _ptr(it),
+                            _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_kmeans_pivots")
+    if check:
+        ssm_check(st, "ssm_kmeans_pivots", stream)
+    return out, asg, it
 
 
 def ssm_pivot_bfs(g: Graph, pivots: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
@@ -381,14 +420,22 @@ def _batch_call(L, items, desc, col, iters, threads, stream, check, dev):
     return rel, int(used.value)
 
 
-def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, device="cuda", stream=None):
-    """Algorithm 1 lines 1-4 on the GPU: returns (Graph, Pivots, initial positions, eigenvalues)."""
+def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, device="cuda", stream=None,
+            sampler: str = "maxmin", kmeans_iters: int = 50):
+    """Algorithm 1 lines 1-4 on the GPU: returns (Graph, Pivots, initial positions, eigenvalues).
+    sampler: "maxmin" (max/min sp) or "kmeans" (k-means sp: max/min sp refined
+    by k-means over the pivots' distances, then d_ip of the new pivots)."""
     _require_cuda()
+    if sampler not in ("maxmin", "kmeans"):
+        raise ValueError("sampler must be 'maxmin' or 'kmeans'")
     src = torch.as_tensor(src, dtype=torch.int32).to(device, non_blocking=True)
     dst = torch.as_tensor(dst, dtype=torch.int32).to(device, non_blocking=True)
     g = ssm_build_graph(n, src, dst, stream)
     piv = ssm_select_pivots(g, k, start, stream)
     dip = ssm_pivot_bfs(g, piv, stream)
+    if sampler == "kmeans":
+        piv, _, _ = ssm_kmeans_pivots(dip, piv, kmeans_iters, stream)
+        dip = ssm_pivot_bfs(g, piv, stream)
     region, off, cnt = ssm_aggregate(dip, stream=stream)
     pos, eig = ssm_pivotmds(g, dip, precision, True, stream)
     return g, Pivots(k, piv, dip, region, off, cnt), pos, eig

@@ -10,6 +10,10 @@ namespace ssm {
 
 static thread_local char g_last_error[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
+// wait limit of the device-wide barriers set by ssm_set_wait_limit_ns (0: the default)
+static std::atomic<unsigned> g_wait_limit_ns{0};
+// the limit as a host word that a copy can read while another thread changes g_wait_limit_ns
+static thread_local unsigned g_wait_limit_copy = 0;
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -41,6 +45,14 @@ cudaError_t allow_dynamic_smem(const void *kernel) {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+int reset_barrier(BarrierState *b, cudaStream_t stream) {
+  SSM_TRY_CUDA(cudaMemsetAsync(b, 0, sizeof(BarrierState), stream));
+  g_wait_limit_copy = g_wait_limit_ns.load(std::memory_order_relaxed);
+  if (g_wait_limit_copy != 0)
+    SSM_TRY_CUDA(cudaMemcpyAsync(&b->limit_ns, &g_wait_limit_copy, sizeof(unsigned), cudaMemcpyHostToDevice, stream));
+  return SSM_OK;
 }
 
 int cooperative_blocks(const void *kernel, int threads, size_t smem, int max_per_sm) {
@@ -78,4 +90,9 @@ SSM_API int ssm_check(const int32_t *status, cudaStream_t stream) {
   if (e != cudaSuccess) return ssm::cuda_status(e, "ssm_check");
   if (h != 0) return ssm::fail(h, "device reported: %s", ssm_status_string(h));
   return SSM_OK;
+}
+
+SSM_API unsigned long long ssm_set_wait_limit_ns(unsigned long long ns) {
+  if (ns > 0xFFFFFFFFull) ns = 0xFFFFFFFFull;
+  return ssm::g_wait_limit_ns.exchange((unsigned)ns);
 }

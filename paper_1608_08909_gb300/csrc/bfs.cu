@@ -334,7 +334,7 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   if (rc || launched) return rc;
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
-  SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+  if (int rc_ = reset_barrier(A.bar, s)) return rc_;
   const size_t smem = sizeof(int2) * 2 * kSoloMax + sizeof(FlatSmem);
   SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_maxmin));
   const int blocks = cooperative_blocks((const void *)k_maxmin, kBfsThreads, smem, 1);
@@ -426,7 +426,11 @@ __global__ void __launch_bounds__(kCtaThreads, MINB) k_bfs_cta(CtaBfsArgs A) {
     __syncthreads();
     uint16_t *row = A.dist + (size_t)si * n;
     if (threadIdx.x == 0) {
-      const unsigned s = (unsigned)__ldg(A.sources + si);
+      unsigned s = (unsigned)__ldg(A.sources + si);
+      if (s >= n) {  // a source id outside the graph: recorded; node 0 keeps the search in bounds
+        dev_fail(A.status, SSM_E_ARG);
+        s = 0;
+      }
       vis[s >> 5] |= 1u << (s & 31u);
       const int rb = __ldg(A.rowptr + s);
       const int2 e0 = make_int2(rb, __ldg(A.rowptr + s + 1) - rb);
@@ -657,7 +661,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_msbfs(MsBfsArgs A) {
     const unsigned a = base + lane;
     bool push = false;
     unsigned idx = 0;
-    if (a < k) {
+    if (a < k && (unsigned)__ldg(A.sources + a) >= n) dev_fail(A.status, SSM_E_ARG);  // not seeded
+    if (a < k && (unsigned)__ldg(A.sources + a) < n) {
       const unsigned v = (unsigned)__ldg(A.sources + a);
       const unsigned w = a >> 5, bit = 1u << (a & 31u);
       idx = v * W + w;
@@ -814,7 +819,7 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
   for (int i = 0; i < 3; ++i) SSM_TRY_CUDA(cudaMemsetAsync(A.F[i], 0, nw * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.ndisc, 0, sizeof(unsigned long long), s));
-  SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+  if (int rc_ = reset_barrier(A.bar, s)) return rc_;
   SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
   const int blocks = cooperative_blocks((const void *)k_msbfs, kBfsThreads, 0, 2);
   if (blocks < 1) return fail(SSM_E_CUDA, "multi-source BFS: kernel cannot be resident");

@@ -45,15 +45,21 @@ struct Carver {
   size_t size() const { return (off + 255) & ~size_t(255); }
 };
 
-// Device-wide barrier state (zeroed before each persistent launch).
+// Device-wide barrier state, reset by reset_barrier() before each persistent
+// launch.  limit_ns is the longest one wait may take before the barrier gives
+// up (0: kBarrierTimeoutNs); it is non-zero only while a caller has set a
+// shorter limit with ssm_set_wait_limit_ns.
 struct BarrierState {
   unsigned count;
   unsigned gen;
   unsigned abort;
-  unsigned pad;
+  unsigned limit_ns;
 };
 
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
+
+// Zeroes *b on `stream` and, while a shorter wait limit is set, stores it.
+int reset_barrier(BarrierState *b, cudaStream_t stream);
 
 // ---------------------------------------------------------------- device side
 __device__ __forceinline__ void dev_fail(int32_t *status, int code) {
@@ -99,6 +105,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *b, int32_t *status) {
       __threadfence();
       st_release_u32(&b->gen, g + 1);
     } else {
+      const unsigned long long limit = b->limit_ns ? (unsigned long long)b->limit_ns : kBarrierTimeoutNs;
       unsigned long long t0 = globaltimer_ns();
       unsigned nap = 32;
       while (ld_acquire_u32(&b->gen) == g) {
@@ -107,7 +114,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *b, int32_t *status) {
         __nanosleep(nap);
         if (nap < 256) nap <<= 1;
         if (ld_acquire_u32(&b->abort)) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+        if (globaltimer_ns() - t0 > limit) {
           dev_fail(status, SSM_E_TIMEOUT);
           atomicExch(&b->abort, 1u);
           ok = 0;

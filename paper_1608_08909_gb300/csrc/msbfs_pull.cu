@@ -78,6 +78,10 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
   // level 0: the sources (seen and F_0 were cleared by the caller)
   for (int a = (int)gtid; a < A.nsrc; a += (int)nthreads) {
     const unsigned v = (unsigned)__ldg(A.sources + A.base + a);
+    if (v >= n) {  // a source id outside the graph: recorded, not seeded
+      dev_fail(A.status, SSM_E_ARG);
+      continue;
+    }
     const unsigned bit = 1u << (a & 31);
     unsigned *s = reinterpret_cast<unsigned *>(A.seen + (size_t)v * kPullW4) + (a >> 5);
     unsigned *f = reinterpret_cast<unsigned *>(A.F + (size_t)v * kPullW4) + (a >> 5);
@@ -291,7 +295,9 @@ __global__ void __launch_bounds__(256) k_pull_distances(PullArgs A) {
   __shared__ unsigned planes[kPullSources / 32][kPullDistBits][kPullTile];
   __shared__ unsigned reached[kPullSources / 32][kPullTile];
   if (__ldcg(A.gaveup)) return;
-  const unsigned nlev = __ldcg(A.nlev);
+  // nlev is zeroed before each pass; a pass that stopped early (a barrier
+  // wait ran out) leaves it 0 and the rows read as unreached
+  const unsigned nlev = min(__ldcg(A.nlev), kPullMaxLevels + 1u);
   const int n = A.n;
   const int v0 = blockIdx.x * kPullTile;
   for (int t = threadIdx.x; t < (kPullSources / 32) * kPullTile; t += blockDim.x) {
@@ -379,7 +385,8 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
     A.nsrc = std::min(kPullSources, k - base);
     SSM_TRY_CUDA(cudaMemsetAsync(A.seen, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
     SSM_TRY_CUDA(cudaMemsetAsync(A.F, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
-    SSM_TRY_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(BarrierState), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(A.nlev, 0, sizeof(unsigned), s));
+    if (int rc_ = reset_barrier(A.bar, s)) return rc_;
     void *args[] = {&A};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs_pull, dim3(blocks), dim3(kPullThreads), args, 0, s));

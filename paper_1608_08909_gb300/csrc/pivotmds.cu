@@ -821,7 +821,7 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
     // one warp per row of the k x k products: as many blocks as the rows need, all resident
     const int want = (k + kEigThreads / 32 - 1) / (kEigThreads / 32);
     const int eblocks = std::max(1, std::min(want, cooperative_blocks((const void *)k_eigen, kEigThreads, esm, 1)));
-    SSM_TRY_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(BarrierState), s));
+    if (int rc_ = reset_barrier(w.bar, s)) return rc_;
     int maxit = 2000;
     double tol = 1e-12;
     void *args[] = {&n, &k, &w.B, &w.M, &w.s, &w.vv, &w.eo, &eig, &w.Yg, &w.bar, &status, &maxit, &tol};

@@ -61,6 +61,16 @@ constexpr unsigned kFullPlaneBytes = kFullPlane * 4u;
 // full-table mode: both planes in static shared memory (a fixed address, so a
 // table read is one shared load at the node's byte offset plus a constant)
 __shared__ __align__(16) float g_wtab[2 * kFullPlane];
+// How the full-table kernel reads its table: 0 inline-asm shared loads from
+// the two planes, 1 plain shared loads from the two planes (the planes' fixed
+// offsets fold into the load instructions), 2 one 8-byte load of an
+// interleaved (w, w d) entry per node
+#ifndef SSM_SWEEP_FULL_LDS
+#define SSM_SWEEP_FULL_LDS 1
+#endif
+constexpr int kFullLds = SSM_SWEEP_FULL_LDS;
+// bytes per table entry in the offsets that the tiled copy carries
+constexpr unsigned kTabEntryBytes = kFullLds == 2 ? 8u : 4u;
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
 #ifndef SSM_SWEEP_PREFETCH
@@ -73,6 +83,10 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_FULL_MIN_BLOCKS 2
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
+// 1: the tile's positions are read again for the update instead of being kept in registers
+#ifndef SSM_SWEEP_RELOAD_X
+#define SSM_SWEEP_RELOAD_X 0
+#endif
 #ifndef SSM_SWEEP_NPL
 #define SSM_SWEEP_NPL 4
 #endif
@@ -89,7 +103,7 @@ struct SweepArgs {
   int32_t n, k;
   const int32_t *rowptr, *colidx, *pivots, *cnt_off;
   const uint16_t *dip;
-  const unsigned *dtile;  // d_ip re-laid as [tile][pivot][32 words of two nodes] (64-node tiles)
+  const unsigned *dtile;  // d_ip re-laid as [tile][pivot][32 lanes][kPpl words of two nodes] (kTileNodes-node tiles)
   const uint32_t *cnt;
   int32_t cnt_len;
   int32_t stab_len;       // 2 cnt_len + k
@@ -333,8 +347,12 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
   if constexpr (FULL)
     for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) {
-      g_wtab[t] = __ldg(A.wtab + t);
-      g_wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
+      if constexpr (kFullLds == 2) {
+        reinterpret_cast<float2 *>(g_wtab)[t] = make_float2(__ldg(A.wtab + t), __ldg(A.wtab + kFullPlane + t));
+      } else {
+        g_wtab[t] = __ldg(A.wtab + t);
+        g_wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
+      }
     }
   wait_previous_kernel();
   if (__ldcg(A.stop)) return;
@@ -343,7 +361,11 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
   // base_a = table start + 4 offset_a - 4 * 0x4B000000 (mod 2^32).
   const unsigned tab0 = SMEM ? (unsigned)__cvta_generic_to_shared(stab) : 0u;
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    const int p = __ldg(A.pivots + a);
+    int p = __ldg(A.pivots + a);
+    if ((unsigned)p >= (unsigned)n) {  // a pivot id outside the graph: recorded, read as node 0
+      dev_fail(A.status, SSM_E_ARG);
+      p = 0;
+    }
     const float2 xy = pin[p];
     const int o = __ldg(A.cnt_off + a), e = __ldg(A.cnt_off + a + 1);
     // pivot a's table: d = 0 .. D_a = 2 ecc_a + 2 at 2 off_a + a (D_a >= 2, so a region
@@ -409,9 +431,24 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        const unsigned al = wtab0 + (pk & 0xFFFFu), ah = wtab0 + (pk >> 16);
-        const float2 w2 = make_float2(lds_f32(al), lds_f32(ah));
-        const float2 wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
+        float2 w2, wd2;
+        if constexpr (kFullLds == 0) {
+          const unsigned al = wtab0 + (pk & 0xFFFFu), ah = wtab0 + (pk >> 16);
+          w2 = make_float2(lds_f32(al), lds_f32(ah));
+          wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
+        } else if constexpr (kFullLds == 1) {
+          const char *tb = reinterpret_cast<const char *>(g_wtab);
+          const unsigned ol = pk & 0xFFFFu, oh = pk >> 16;
+          w2 = make_float2(*reinterpret_cast<const float *>(tb + ol), *reinterpret_cast<const float *>(tb + oh));
+          wd2 = make_float2(*reinterpret_cast<const float *>(tb + kFullPlaneBytes + ol),
+                            *reinterpret_cast<const float *>(tb + kFullPlaneBytes + oh));
+        } else {
+          const char *tb = reinterpret_cast<const char *>(g_wtab);
+          const float2 el = *reinterpret_cast<const float2 *>(tb + (pk & 0xFFFFu));
+          const float2 eh = *reinterpret_cast<const float2 *>(tb + (pk >> 16));
+          w2 = make_float2(el.x, eh.x);
+          wd2 = make_float2(el.y, eh.y);
+        }
         const float2 dx2 = __fadd2_rn(xi2[j], px2);
         const float2 dy2 = __fadd2_rn(yi2[j], py2);
         const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
@@ -557,7 +594,11 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       const float chk = FULL ? nx + ny : (hi ? den2[j].y : den2[j].x);
       if (live && !(chk == chk)) dev_fail(A.status, SSM_E_NUMERIC);
       if (live) {
+#if SSM_SWEEP_RELOAD_X
+        const float2 x = pin[i];
+#else
         const float2 x = xs[q];
+#endif
         const float xn = dn > 0.f ? (nx + nbq.x) / dn : x.x, yn = dn > 0.f ? (ny + nbq.y) / dn : x.y;
         pout[i] = make_float2(xn, yn);
         const float ex = xn - x.x, ey = yn - x.y;
@@ -577,8 +618,8 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 // ----------------------------------------------------------------- setup (once per ssm_iterate)
 // dtile[((t k + a) 32 + l) kPpl + j] = e(d_ip[a][i]) | e(d_ip[a][i + 1]) << 16 with
 // i = t kTileNodes + kNpl l + 2 j (d = 0 past the last node); e(d) = d, or in
-// full-table mode (row = dmax + 1 > 0) the byte offset 4 (a row + d) of the
-// node's entry in a table plane
+// full-table mode (row = dmax + 1 > 0) the byte offset kTabEntryBytes (a row + d)
+// of the node's entry in the shared-memory table
 __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__restrict__ dip,
                            unsigned *__restrict__ dtile) {
   const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
@@ -595,8 +636,8 @@ __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__
     unsigned lo = i < n ? (unsigned)__ldg(drow + i) : 0u;
     unsigned hi = i + 1 < n ? (unsigned)__ldg(drow + i + 1) : 0u;
     if (row > 0) {
-      lo = 4u * ((unsigned)a * (unsigned)row + lo);
-      hi = 4u * ((unsigned)a * (unsigned)row + hi);
+      lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
+      hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
     }
     dtile[w] = lo | (hi << 16);
   }
@@ -652,8 +693,8 @@ __global__ void k_sweep_den(int32_t n, int32_t k, const unsigned *__restrict__ d
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        acc[2 * j] += __ldg(wtab + ((pk & 0xFFFFu) >> 2));
-        acc[2 * j + 1] += __ldg(wtab + (pk >> 18));
+        acc[2 * j] += __ldg(wtab + (pk & 0xFFFFu) / kTabEntryBytes);
+        acc[2 * j + 1] += __ldg(wtab + (pk >> 16) / kTabEntryBytes);
       }
     }
     const int64_t i0 = tile * kTileNodes + (int64_t)kNpl * lane;
@@ -695,7 +736,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(SweepArgs A, const 
   if (__ldcg(A.stop)) return;
   const int n = A.n, k = A.k;
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    const int p = __ldg(A.pivots + a);
+    int p = __ldg(A.pivots + a);
+    if ((unsigned)p >= (unsigned)n) {  // a pivot id outside the graph: recorded, read as node 0
+      dev_fail(A.status, SSM_E_ARG);
+      p = 0;
+    }
     const double2 xy = pin[p];
     const int o = __ldg(A.cnt_off + a);
     piv[a] = PivD{xy.x, xy.y, o, __ldg(A.cnt_off + a + 1) - o - 1};
@@ -807,6 +852,9 @@ static int64_t split_capacity(int32_t n) {
   const int64_t tiles = ((int64_t)n + kTileNodes - 1) / kTileNodes;
   return tiles < 2 * (int64_t)num_sms() * kSplitWarpsPerSm ? kMaxSplit * tiles : 0;
 }
+
+// what the last ssm_iterate call on this host thread chose (ssm_last_sweep_config)
+static thread_local int32_t g_last_config[4] = {-1, 0, 0, -1};
 
 static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t k, int64_t cnt_len,
                             int32_t precision) {
@@ -940,6 +988,10 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     }
   }
 
+  g_last_config[0] = precision == 64 ? (tsm ? 3 : 4) : (kern == (const void *)k_sweep_f32<kFull> ? 2 : (tsm ? 0 : 1));
+  g_last_config[1] = A.nsplit;
+  g_last_config[2] = blocks;
+  g_last_config[3] = precision == 64 ? -1 : (int32_t)meta[0];
   const int32_t nmid = (int32_t)meta[1], nlong = (int32_t)meta[2];
   const unsigned nbr_blocks = (unsigned)(nlong + (nmid + 7) / 8 + (n + 255) / 256);
   for (int t = 0; t < iters; ++t) {
@@ -980,4 +1032,8 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     note_launch(), k_copy_back_if_odd<float2><<<cb, 256, 0, s>>>(n, iters_done, (const float2 *)w.tmp, (float2 *)pos);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
+}
+
+SSM_API void ssm_last_sweep_config(int32_t *out) {
+  for (int i = 0; i < 4; ++i) out[i] = ssm::g_last_config[i];
 }

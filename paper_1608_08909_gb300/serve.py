@@ -11,9 +11,11 @@ keeps its CSR, d_ip and positions resident until it finishes.  Results do not
 depend on what else is running: each request has its own buffers, and every
 reduction of the library runs in a fixed order.
 
-``job_device_bytes`` gives the exact device memory a request holds at its
-peak (the library's own workspace queries plus its buffers), which is what
-admission charges against the budget.  The scheduler itself is host logic
+``job_device_bytes`` bounds the device memory a request allocates at its
+peak (the library's own workspace queries plus its buffers, with a margin for
+the allocator's rounding of small tensors), which is what admission charges
+against the budget.  The budget counts allocated bytes: blocks that torch's
+caching allocator keeps after a request frees them are outside it.  The scheduler itself is host logic
 that takes the job runner as a parameter, so it is tested without a GPU.
 """
 from __future__ import annotations
@@ -60,9 +62,11 @@ class LayoutResult:
 
 
 def job_device_bytes(n: int, m_in: int, k: int, stress_sources: int = 0, stress_targets: int = 0) -> int:
-    """Device bytes a request holds at its peak: the edge list, CSR, pivots,
-    d_ip, regions and counts, positions and the largest stage workspace (the
-    count table is bounded by n + k entries, since ecc_a + 1 <= |R(a)|)."""
+    """An upper bound of the device bytes a request allocates at its peak: the
+    edge list, CSR, pivots, d_ip, regions and counts, positions and the
+    largest stage workspace (the count table is bounded by n + k entries,
+    since ecc_a + 1 <= |R(a)|), plus 1 MB for the allocator's rounding of the
+    small status and result tensors."""
     from . import lib
 
     L = lib()

@@ -455,7 +455,7 @@ def test_sweep_fp32_both_weight_table_modes(k):
     n, s, d = GRAPHS["rgg"]()
     prep = O.prepare(n, s, d, k)
     dmax = int(prep.dip.max())
-    assert (k * (dmax + 1) * 8 <= 48 * 1024) == (k == 12)
+    assert (k * (dmax + 1) <= 6112) == (k == 12)
     g = _gpu_graph(n, s, d)
     P = _gpu_pivots(k, prep)
     x = prep.pos0
@@ -464,6 +464,9 @@ def test_sweep_fp32_both_weight_table_modes(k):
     x0 = x.astype(np.float32)
     pos = torch.from_numpy(x0.copy()).to(DEV)
     ssm.ssm_iterate(g, P, pos, 1)
+    cfg = ssm.ssm_last_sweep_config()
+    assert cfg["kernel"] == ("f32_full_table" if k == 12 else "f32_clamped_smem")
+    assert cfg["dmax"] == dmax
     opos, _ = O.sweep_jacobi(prep.g, prep.pivots, prep.dip, prep.w, x0.astype(np.float64))
     assert _norm_err(pos.cpu().numpy(), opos) < 1e-5
 

@@ -440,3 +440,137 @@ def test_sampled_stress_unbiased():
     ex = O.full_stress(p.g, p.pos0)
     est = np.mean([O.full_stress(p.g, p.pos0, 16, 64, seed)[0] for seed in range(60)])
     assert est == pytest.approx(ex[0], rel=0.03)
+
+
+def test_sample_pairs_first_pairs_hand_derived():
+    """The index mapping of the sampled pair list (source, then targets with the
+    skip over the source) against pairs derived by hand from the published
+    splitmix64 outputs (tests/golden/sample_pairs_seed0.txt); the second case
+    starts the stream so that the first source is node 0 and every target
+    takes the skip."""
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "sample_pairs_seed0.txt")) if ln.startswith("0x")]
+    assert len(rows) == 2
+    for r in rows:
+        seed, n, S, T = int(r[0], 16), int(r[1]), int(r[2]), int(r[3])
+        srcs, tgts = O.sample_pairs(n, S, T, seed)
+        assert srcs.tolist() == [int(r[4])]
+        assert tgts.reshape(-1).tolist() == [int(x) for x in r[5:]]
+
+
+def test_gauss_seidel_uses_updated_positions():
+    """One in-place sweep on the path 0-1-2 with the single pivot 0, from
+    x = (0,0), (3,0), (3,4), derived by hand from Eq. 4:
+      node 0: neighbour 1 at r = 3 -> (3,0) + (-3,0)/3 = (2,0);
+      node 1: neighbours 0 (already moved to (2,0), r = 1) and 2 (r = 4):
+              (2,0) + (1,0)/1 = (3,0) and (3,4) + (0,-4)/4 = (3,3) -> (3, 1.5)
+              (the Jacobi order, which reads the old (0,0), gives (2, 1.5));
+      node 2: neighbour 1 at (3,1.5), r = 2.5 -> (3,1.5) + (0,2.5)/2.5 = (3,2.5);
+              pivot 0 at (2,0), d = 2, R(0) = {0,1,2}, s = |{j: d_j0 <= 1}| = 2,
+              w' = 2/4 = 1/2, r = sqrt(17): w'((2,0) + 2 (1,4)/sqrt(17));
+              x_2 = [(3,2.5) + w'(...)] / (1 + 1/2)."""
+    n, s, d = 3, np.array([0, 1], np.int32), np.array([1, 2], np.int32)
+    g = O.build_csr(n, s, d)
+    piv = np.array([0], np.int32)
+    dip = O.pivot_dist(g, piv)
+    w = O.adapted_weights(dip, O.regions(dip))
+    x = np.array([[0.0, 0.0], [3.0, 0.0], [3.0, 4.0]])
+    r17 = math.sqrt(17.0)
+    want = np.array([[2.0, 0.0], [3.0, 1.5],
+                     [(3.0 + 0.5 * (2.0 + 2.0 / r17)) / 1.5, (2.5 + 0.5 * (8.0 / r17)) / 1.5]])
+    got = O.sweep_gs(g, piv, dip, w, x)
+    np.testing.assert_allclose(got, want, rtol=1e-15, atol=1e-15)
+    jac, _ = O.sweep_jacobi(g, piv, dip, w, x)
+    np.testing.assert_allclose(jac[1], [2.0, 1.5], rtol=1e-15)
+
+
+def test_node_range_and_source_range_pieces_add_up():
+    """The range forms used to spread the oracle over host threads: node ranges
+    of the Jacobi sweep reproduce the whole sweep exactly, source ranges of the
+    stress sums add up to the whole list's sums, and pivot subsets give the
+    same d_ip rows."""
+    n, s, d = I.rgg(2500, 8.0, 4)
+    p = O.prepare(n, s, d, 24)
+    a, ra = O.sweep_jacobi(p.g, p.pivots, p.dip, p.w, p.pos0)
+    b, rb = O.sweep_jacobi_threads(p.g, p.pivots, p.dip, p.w, p.pos0, 3)
+    assert np.array_equal(a, b) and ra == rb
+    out, sums = O.full_stress(p.g, p.pos0, 40, 33, 5, return_sums=True)
+    out2, sums2 = O.full_stress_threads(p.g, p.pos0, 40, 33, 5, 4)
+    np.testing.assert_allclose(sums2, sums, rtol=1e-13)
+    np.testing.assert_allclose(out2, out, rtol=1e-12)
+    ex, exs = O.full_stress(p.g, p.pos0, return_sums=True)
+    ex2, exs2 = O.full_stress_threads(p.g, p.pos0, 0, 0, 0, 3)
+    np.testing.assert_allclose(exs2, exs, rtol=1e-13)
+    assert np.array_equal(O.pivot_dist_threads(p.g, p.pivots, 5), p.dip)
+
+
+# ---------------------------------------------------------------- k-means sp (Section 4.1)
+
+def test_kmeans_sp_hand_derived_path():
+    """Path 0..6, max/min-sp pivots (0, 6): y_i = (i, 6 - i).  First pass: the
+    squared distances to y_0 and y_6 are 2 i^2 and 2 (6 - i)^2, node 3 ties and
+    joins cluster 0, so the clusters are {0,1,2,3} and {4,5,6} with means
+    (1.5, 4.5) and (5, 1).  Second pass: node 3 is at 4.5 from the first mean
+    and 8 from the second, node 4 at 6.5 and 2: nothing changes, stop after 2
+    passes.  New pivots: nodes 1 and 2 are both at 0.5 from (1.5, 4.5) -> the
+    lower id, 1; node 5 is the second mean itself -> 5."""
+    n, s, d = I.path(7)
+    g = O.build_csr(n, s, d)
+    piv = O.maxmin(g, 2)
+    assert piv.tolist() == [0, 6]
+    newp, asg, it = O.kmeans_sp(O.pivot_dist(g, piv), piv)
+    assert newp.tolist() == [1, 5]
+    assert asg.tolist() == [0, 0, 0, 0, 1, 1, 1]
+    assert it == 2
+
+
+@pytest.mark.parametrize("name", ["rgg", "grid", "rbtree"])
+def test_kmeans_sp_matches_library_lloyd(name):
+    """scikit-learn's Lloyd iterations from the same initial centres (the
+    max/min pivots' distance vectors) reach the same clusters in the same
+    number of passes on graphs without exact ties."""
+    KMeans = pytest.importorskip("sklearn.cluster").KMeans
+    n, s, d = {"rgg": lambda: I.rgg(400, 8.0, 3), "grid": lambda: I.grid(13, 17),
+               "rbtree": lambda: I.random_btree(300, 5)}[name]()
+    k = {"rgg": 12, "grid": 10, "rbtree": 9}[name]
+    g = O.build_csr(n, s, d)
+    piv = O.maxmin(g, k)
+    dip = O.pivot_dist(g, piv)
+    _, asg, it = O.kmeans_sp(dip, piv)
+    Y = dip.T.astype(np.float64)
+    km = KMeans(n_clusters=k, init=Y[piv], n_init=1, max_iter=50, tol=0.0, algorithm="lloyd").fit(Y)
+    assert np.array_equal(km.labels_, asg)
+    assert km.n_iter_ == it
+
+
+@pytest.mark.parametrize("seed", [2, 7])
+def test_kmeans_sp_is_an_exact_fixed_point(seed):
+    """In exact rational arithmetic: every node sits at a nearest centre of
+    the final clustering, every centre is its members' mean, and every new
+    pivot is the member nearest its centre with ties to the lowest id."""
+    from fractions import Fraction
+
+    n, s, d = I.ba(300, 3, seed)
+    k = 12
+    g = O.build_csr(n, s, d)
+    piv = O.maxmin(g, k)
+    dip = O.pivot_dist(g, piv)
+    newp, asg, it = O.kmeans_sp(dip, piv)
+    assert 1 <= it <= 50
+    Y = dip.T.astype(np.int64)
+    cent = []
+    for a in range(k):
+        mem = np.nonzero(asg == a)[0]
+        cent.append((Y[mem].sum(0), len(mem)) if len(mem) else None)
+    def dist(i, a):
+        S, c = cent[a]
+        return sum(Fraction(int(Y[i, b]) * c - int(S[b]), c) ** 2 for b in range(k))
+    for i in range(n):
+        dd = [dist(i, a) for a in range(k) if cent[a] is not None]
+        assert dist(i, asg[i]) == min(dd)
+    for a in range(k):
+        if cent[a] is None:
+            assert newp[a] == piv[a]
+            continue
+        mem = np.nonzero(asg == a)[0]
+        best = min(mem, key=lambda i: (dist(i, a), i))
+        assert newp[a] == best

@@ -171,3 +171,27 @@ def test_small_budget_serialises_admission():
         assert srv.peak_reserved <= budget
         assert srv.peak_active == 1
     assert all(np.isfinite(r.pos).all() for r in res)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("family,n0,stress", [("grid", 9000, 0), ("rgg", 30000, 32), ("btree", 20000, 0)])
+def test_job_device_bytes_bounds_the_allocation(family, n0, stress):
+    """What admission charges is at least what one request really allocates:
+    the rise of torch's peak allocated bytes over a whole request stays
+    within job_device_bytes."""
+    import torch
+
+    from paper_1608_08909_gb300 import inputs as I
+
+    n, s, d = I.mixed_graph(family, n0, 7)
+    job = S.LayoutJob(n=n, src=s, dst=d, k=100, iters=5, stress_sources=stress, stress_targets=64 if stress else 0)
+    stream = torch.cuda.Stream()
+    S.run_layout_job(job, stream)  # library load and first-use costs
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    S.run_layout_job(job, stream)
+    torch.cuda.synchronize()
+    rise = torch.cuda.max_memory_allocated() - base
+    bound = S.job_device_bytes(n, len(s), job.k, job.stress_sources, job.stress_targets)
+    assert 0 < rise <= bound
