@@ -268,6 +268,26 @@ def run_gpu(args):
             "note": "same pivots and PivotMDS start in each precision; stress on the bench's sampled pairs",
         }
 
+    # k-means sp (Section 4.1, the paper's recommended sampler) on the bench's
+    # max/min pivots and d_ip: passes, time, and the integer multiply-adds of
+    # its assignment passes (n k^2 each) per second
+    kmeans = None
+    if not args.no_kmeans:
+        g, P, _, _ = step(src_d, dst_d)
+        ssm.ssm_kmeans_pivots(P.dip, P.pivots, 50)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        newp, _, passes = ssm.ssm_kmeans_pivots(P.dip, P.pivots, 50, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        km_ms = e0.elapsed_time(e1)
+        npass = int(passes.item())
+        macs = npass * n * k * k
+        kmeans = {"passes": npass, "max_passes": 50, "ms": round(km_ms, 3),
+                  "int_mac_per_s": macs / (km_ms * 1e-3), "moved_pivots": int((newp != P.pivots).sum().item()),
+                  "note": "exact 64-bit integer dot products of the assignment (n k^2 per pass) on CUDA cores"}
+
     # roofline of the sweep kernel (one launch = one Jacobi iteration)
     peak, peak_kind = _peaks()
     bytes_per_launch = 2 * k * n + 4 * (n + 1) + 8 * m + 8 * n + 8 * n
@@ -313,6 +333,7 @@ def run_gpu(args):
         },
         "clocks": clocks,
         "fp64_sweep": fp64,
+        "kmeans_sp": kmeans,
         "e2e": {"value": e2e_value, "unit": "node-term updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
         "gpu_launches": timed_launches,
@@ -627,6 +648,7 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="override the sweep count (0: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
+    ap.add_argument("--no-kmeans", action="store_true", help="skip the k-means sp sampler timing")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead of a single graph")
     ap.add_argument("--batch", action="store_true", help="run the batching workload (many small graphs, one launch)")
     ap.add_argument("--batch-graphs", type=int, default=4096)

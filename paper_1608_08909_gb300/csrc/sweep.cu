@@ -212,20 +212,25 @@ __device__ __forceinline__ void edge_term(float xi, float yi, float2 q, float &s
   sy += fmaf(dy, inv, q.y);
 }
 
-// one lane walks a short row in batches of eight: the batch's column indices
-// load together, then its eight positions, so a row of up to eight entries
-// costs two dependent memory latencies (terms still added in row order)
+// one lane walks a short row in batches of kNbrBatch: the batch's column
+// indices load together, then its positions, so a row of up to kNbrBatch
+// entries costs two dependent memory latencies (terms still added in row order)
+#ifndef SSM_NBR_BATCH
+#define SSM_NBR_BATCH 8
+#endif
+constexpr int kNbrBatch = SSM_NBR_BATCH;  // column indices (then positions) a lane loads at once
+
 __device__ __forceinline__ void light_row(const float2 *__restrict__ pin, const int32_t *__restrict__ colidx, int beg,
                                           int end, float xi, float yi, float &sx, float &sy) {
-  for (int t = beg; t < end; t += 8) {
-    int j[8];
+  for (int t = beg; t < end; t += kNbrBatch) {
+    int j[kNbrBatch];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) j[q] = t + q < end ? __ldg(colidx + t + q) : -1;
-    float2 x[8];
+    for (int q = 0; q < kNbrBatch; ++q) j[q] = t + q < end ? __ldg(colidx + t + q) : -1;
+    float2 x[kNbrBatch];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = j[q] >= 0 ? pin[j[q]] : make_float2(0.f, 0.f);
+    for (int q = 0; q < kNbrBatch; ++q) x[q] = j[q] >= 0 ? pin[j[q]] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < kNbrBatch; ++q)
       if (j[q] >= 0) edge_term(xi, yi, x[q], sx, sy);
   }
 }
