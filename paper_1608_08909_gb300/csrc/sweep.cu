@@ -62,15 +62,15 @@ constexpr unsigned kFullPlaneBytes = kFullPlane * 4u;
 // table read is one shared load at the node's byte offset plus a constant)
 __shared__ __align__(16) float g_wtab[2 * kFullPlane];
 // How the full-table kernel reads its table: 0 inline-asm shared loads from
-// the two planes, 1 plain shared loads from the two planes (the planes' fixed
-// offsets fold into the load instructions), 2 one 8-byte load of an
-// interleaved (w, w d) entry per node
+// the two planes at 32-bit shared addresses, 1 plain shared loads from the two
+// planes (measured within 1 %; an interleaved (w, w d) entry per node was 5 %
+// slower)
 #ifndef SSM_SWEEP_FULL_LDS
-#define SSM_SWEEP_FULL_LDS 1
+#define SSM_SWEEP_FULL_LDS 0
 #endif
 constexpr int kFullLds = SSM_SWEEP_FULL_LDS;
 // bytes per table entry in the offsets that the tiled copy carries
-constexpr unsigned kTabEntryBytes = kFullLds == 2 ? 8u : 4u;
+constexpr unsigned kTabEntryBytes = 4u;
 constexpr int kMaxPivotsSweep = 4096;
 constexpr float kR2Floor = 1e-24f;
 #ifndef SSM_SWEEP_PREFETCH
@@ -352,12 +352,8 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
   if constexpr (FULL)
     for (int t = threadIdx.x; t < k * (A.dmax + 1); t += blockDim.x) {
-      if constexpr (kFullLds == 2) {
-        reinterpret_cast<float2 *>(g_wtab)[t] = make_float2(__ldg(A.wtab + t), __ldg(A.wtab + kFullPlane + t));
-      } else {
-        g_wtab[t] = __ldg(A.wtab + t);
-        g_wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
-      }
+      g_wtab[t] = __ldg(A.wtab + t);
+      g_wtab[kFullPlane + t] = __ldg(A.wtab + kFullPlane + t);
     }
   wait_previous_kernel();
   if (__ldcg(A.stop)) return;
@@ -441,18 +437,12 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
           const unsigned al = wtab0 + (pk & 0xFFFFu), ah = wtab0 + (pk >> 16);
           w2 = make_float2(lds_f32(al), lds_f32(ah));
           wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
-        } else if constexpr (kFullLds == 1) {
+        } else {
           const char *tb = reinterpret_cast<const char *>(g_wtab);
           const unsigned ol = pk & 0xFFFFu, oh = pk >> 16;
           w2 = make_float2(*reinterpret_cast<const float *>(tb + ol), *reinterpret_cast<const float *>(tb + oh));
           wd2 = make_float2(*reinterpret_cast<const float *>(tb + kFullPlaneBytes + ol),
                             *reinterpret_cast<const float *>(tb + kFullPlaneBytes + oh));
-        } else {
-          const char *tb = reinterpret_cast<const char *>(g_wtab);
-          const float2 el = *reinterpret_cast<const float2 *>(tb + (pk & 0xFFFFu));
-          const float2 eh = *reinterpret_cast<const float2 *>(tb + (pk >> 16));
-          w2 = make_float2(el.x, eh.x);
-          wd2 = make_float2(el.y, eh.y);
         }
         const float2 dx2 = __fadd2_rn(xi2[j], px2);
         const float2 dy2 = __fadd2_rn(yi2[j], py2);

@@ -407,7 +407,7 @@ def test_sweep_fp64_matches_oracle(name, k):
 
 
 @pytest.mark.parametrize("name,k", [("grid32", 50), ("grid_ragged", 33), ("rgg", 100), ("ba", 64), ("btree", 33),
-                                    ("messy", 95), ("rbtree", 64)])
+                                    ("messy", 95), ("rbtree", 64), ("ba", 377)])
 def test_sweep_fp32_single_step(name, k):
     n, s, d = GRAPHS[name]()
     prep = O.prepare(n, s, d, k)
