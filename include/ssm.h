@@ -177,6 +177,30 @@ int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, in
                   uint32_t *cnt, int64_t cnt_len, int32_t *status,
                   void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Regions with the paper's own tie rule (Section 3: R is built
+ * incrementally while the distances are computed, a tie going to the
+ * currently smallest partition), instead of ssm_aggregate's lowest pivot
+ * index.  Reading: nodes join in the order a multi-source search settles
+ * them -- increasing distance to their nearest pivots, equal distances by
+ * increasing node id; a node with one nearest pivot joins it, a node with
+ * several joins the one whose region has the fewest members at that moment
+ * (lowest index on equal sizes).  Writes region[n]; asynchronous.  The
+ * walk over tied nodes is sequential (one thread, region sizes in shared
+ * memory), so this is slower than ssm_aggregate on graphs with many ties.
+ * 1 <= k <= 8192.  Workspace ssm_regions_smallest_workspace(n).
+ * ssm_aggregate_regions then builds cnt_off[k+1] and cnt for GIVEN regions
+ * (ecc_a = max d_ia over the nodes of region a): synchronous; it stores the
+ * table length in *cnt_len (host) and returns SSM_E_NOMEM if it exceeds
+ * cnt_cap (cnt untouched; cnt may be NULL when cnt_cap is 0).  Workspace
+ * ssm_aggregate_workspace(k).  Device error SSM_E_ARG for a region id
+ * outside 0..k-1. */
+size_t ssm_regions_smallest_workspace(int32_t n);
+int ssm_regions_smallest(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *status,
+                         void *ws, size_t ws_bytes, cudaStream_t stream);
+int ssm_aggregate_regions(int32_t n, int32_t k, const uint16_t *dip, const int32_t *region, int32_t *cnt_off,
+                          uint32_t *cnt, int64_t cnt_cap, int64_t *cnt_len, int32_t *status,
+                          void *ws, size_t ws_bytes, cudaStream_t stream);
+
 /* ssm_aggregate without any workspace, for callers that cannot allocate
  * device memory: for example a serving process that reserved its whole device
  * memory budget up front and admits work against it byte by byte, or code
@@ -261,6 +285,44 @@ int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *coli
                 const uint32_t *cnt, int64_t cnt_len, void *pos, int32_t precision, int32_t iters,
                 double tol, int32_t *iters_done, double *rel_change, int32_t *status,
                 void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * The sparse model's update of Eq. 4 in the paper's own order (Algorithm 1
+ * lines 6-10): nodes 0..n-1 in turn, each moved in place from the positions
+ * already moved (Gauss-Seidel), in FP64 -- the order the paper uses, kept as
+ * a quality reference beside the Jacobi schedule of ssm_iterate.  Arguments
+ * as for ssm_iterate; pos is double[2n]; rel_change (device double) receives
+ * the relative change of the last sweep.  One block of 1024 threads sums each
+ * node's deg(i) + k terms (ascending per thread, then a fixed-order tree), so
+ * a sweep takes about n block steps.  Workspace ssm_iterate_gs_workspace(n).
+ * Device error SSM_E_ARG (a pivot id outside 0..n-1).  1 <= k <= 65535.
+ * ------------------------------------------------------------------- */
+size_t ssm_iterate_gs_workspace(int32_t n);
+int ssm_iterate_gs(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
+                   const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
+                   double *pos, int32_t iters, double *rel_change, int32_t *status,
+                   void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Full stress majorization (Section 3, the localized update before Eq. 4;
+ * the sparse model with k = n reduces to it): every node moves to
+ *   x_i = sum_{j != i} w_ij (x_j + d_ij (x_i - x_j)/r_ij) / sum_{j != i} w_ij,
+ * w_ij = d_ij^-2 (a term with r_ij == 0 adds w_ij x_j), over the all-pairs
+ * hop distances D[n*n] (uint16, D[i*n + j] = d_ij, symmetric; for example
+ * ssm_pivot_bfs with every node as a source, n <= 65535).
+ * order 0: Jacobi (every node from the previous iterate), precision 32 or 64
+ * (FP64 rounds each operation as the oracle does: bit-identical results);
+ * order 1: Gauss-Seidel (nodes 0..n-1 in turn, in place -- the order under
+ * which full stress decreases monotonically), precision 64 only.
+ * Runs `iters` sweeps on pos in place; rel_change (device double) receives
+ * the relative change of the last sweep.  O(n^2) per sweep; meant for the
+ * graph sizes of the paper's comparisons (about 1e3 to 2e4 nodes).
+ * Workspace ssm_full_iterate_workspace(n, precision).
+ * Device error SSM_E_DISCONNECTED (an entry 0xFFFF off the diagonal).
+ * ------------------------------------------------------------------- */
+size_t ssm_full_iterate_workspace(int32_t n, int32_t precision);
+int ssm_full_iterate(int32_t n, const uint16_t *D, void *pos, int32_t precision, int32_t order, int32_t iters,
+                     double *rel_change, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
  * Batched sweeps: the Jacobi sweeps of Eq. 4 (Algorithm 1 lines 5-10) for G

@@ -57,6 +57,7 @@ def _load():
                 "orc_kmeans_sp": [i32, i32, v, v, i32, v, v, v],
                 "orc_pivot_dist": [i32, v, v, i32, v, v],
                 "orc_regions": [i32, i32, v, v],
+                "orc_regions_smallest": [i32, i32, v, v],
                 "orc_histograms": [i32, i32, v, v, v, v, v, i64],
                 "orc_adapted_weights": [i32, i32, v, v, v],
                 "orc_pivotmds": [i32, i32, v, v, v, v],
@@ -65,6 +66,7 @@ def _load():
                 "orc_sweep_jacobi_rows": [i32, v, v, i32, v, v, v, v, v, i32, i32],
                 "orc_stress_sums_range": [i32, v, v, v, i32, i32, u64, i32, i32, v],
                 "orc_sweep_gs": [i32, v, v, i32, v, v, v, v],
+                "orc_full_sweep": [i32, v, v, v, i32, v],
                 "orc_splitmix64": [u64, i64, v],
                 "orc_sample_pairs": [i32, i32, i32, u64, v, v],
                 "orc_full_stress": [i32, v, v, v, i32, i32, u64, v, v],
@@ -148,6 +150,16 @@ def regions(dip: np.ndarray) -> np.ndarray:
     k, n = dip.shape
     reg = np.zeros(n, np.int32)
     _chk(_load().orc_regions(n, k, _p(dip), _p(reg)), "regions")
+    return reg
+
+
+def regions_smallest(dip: np.ndarray) -> np.ndarray:
+    """Regions with the paper's tie rule: ties to the currently smallest region,
+    nodes taken by increasing distance to their nearest pivot, then by id."""
+    dip = np.ascontiguousarray(dip, dtype=np.uint16)
+    k, n = dip.shape
+    reg = np.zeros(n, np.int32)
+    _chk(_load().orc_regions_smallest(n, k, _p(dip), _p(reg)), "regions_smallest")
     return reg
 
 
@@ -310,6 +322,23 @@ def sweep_gs(g: Graph, pivots, dip, w, pos):
     return pos
 
 
+def apsp(g: Graph) -> np.ndarray:
+    """All-pairs hop distances [n][n] uint16, one BFS per node (row i = BFS from i)."""
+    return pivot_dist(g, np.arange(g.n, dtype=np.int32))
+
+
+def full_sweep(D: np.ndarray, pos, order: int = 0):
+    """One sweep of full stress majorization over the all-pairs table D
+    (order 0 Jacobi, 1 Gauss-Seidel); returns (positions, relative change)."""
+    D = np.ascontiguousarray(D, dtype=np.uint16)
+    n = D.shape[0]
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros_like(pos)
+    rel = ctypes.c_double(0.0)
+    _chk(_load().orc_full_sweep(n, _p(D), _p(pos), _p(out), order, ctypes.byref(rel)), "full_sweep")
+    return out, rel.value
+
+
 def splitmix64(seed: int, count: int) -> np.ndarray:
     out = np.zeros(count, np.uint64)
     _chk(_load().orc_splitmix64(ctypes.c_uint64(seed), count, _p(out)), "splitmix64")
@@ -346,14 +375,15 @@ class Prepared:
         self.ecc, self.cnt_off, self.cnt, self.w, self.pos0, self.eig = ecc, cnt_off, cnt, w, pos0, eig
 
 
-def prepare(n: int, src, dst, k: int, start: int = 0, sampler: str = "maxmin", kmeans_iters: int = 50) -> Prepared:
+def prepare(n: int, src, dst, k: int, start: int = 0, sampler: str = "maxmin", kmeans_iters: int = 50,
+            ties: str = "lowest") -> Prepared:
     g = build_csr(n, src, dst)
     piv = maxmin(g, k, start)
     dip = pivot_dist(g, piv)
     if sampler == "kmeans":
         piv, _, _ = kmeans_sp(dip, piv, kmeans_iters)
         dip = pivot_dist(g, piv)
-    reg = regions(dip)
+    reg = regions(dip) if ties == "lowest" else regions_smallest(dip)
     ecc, off, cnt = histograms(dip, reg)
     w = adapted_weights(dip, reg)
     pos, eig = pivotmds(dip)

@@ -15,6 +15,7 @@
  *   orc_kmeans_sp        "k-means sp" pivot sampling                 (Section 4.1)
  *   orc_pivot_dist       d_ip for all pivots, one BFS per pivot      (Algorithm 1, line 2)
  *   orc_regions          regions R(p): closest pivot                 (Section 3)
+ *   orc_regions_smallest the same with the paper's smallest-partition ties (Section 3)
  *   orc_histograms       per-pivot distance counts over R(p)         (Section 3, w'_ip)
  *   orc_adapted_weights  w'_ip = s / d_ip^2 by direct count          (Section 3, after Eq. 4)
  *   orc_pivotmds         PivotMDS initial layout                     (Algorithm 1, line 3)
@@ -22,6 +23,7 @@
  *   orc_sweep_jacobi     one update of Eq. 4 for all nodes from X^t  (Eq. 4)
  *                        (orc_sweep_jacobi_rows: the same for a node range)
  *   orc_sweep_gs         the same, in place node by node              (Algorithm 1, lines 6-10)
+ *   orc_full_sweep       full stress majorization, Jacobi or in place (Section 3, before Eq. 4)
  *   orc_full_stress      Eq. 1 over all pairs, or over sampled pairs  (Eq. 1, Section 4)
  *                        (orc_stress_sums_range: its pair sums for a source range)
  *
@@ -290,6 +292,44 @@ int orc_regions(int32_t n, int32_t k, const uint16_t *dip, int32_t *region) {
       if (dip[(int64_t)a * n + i] < dip[(int64_t)best * n + i]) best = a;
     region[i] = best;
   }
+  return ORC_OK;
+}
+
+/* Regions with the paper's tie rule (Section 3: R is built incrementally
+ * while the distances are computed, a tie going to the currently smallest
+ * partition).  Reading: nodes join in the order a multi-source search
+ * settles them -- increasing distance L_i = min_a d_ia to their nearest
+ * pivots, equal distances by increasing node id; a node with one nearest
+ * pivot joins it, a node with several joins the one whose region has the
+ * fewest members at that moment, equal sizes to the lowest pivot index. */
+int orc_regions_smallest(int32_t n, int32_t k, const uint16_t *dip, int32_t *region) {
+  int32_t *L = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int64_t *size = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  int64_t *start = NULL;
+  int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!L || !size || !order) { free(L); free(size); free(order); return ORC_E_NOMEM; }
+  int32_t lmax = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t m = 65535;
+    for (int32_t a = 0; a < k; ++a)
+      if (dip[(int64_t)a * n + i] < m) m = dip[(int64_t)a * n + i];
+    L[i] = m;
+    if (m > lmax) lmax = m;
+  }
+  /* stable counting sort of the nodes by L */
+  start = (int64_t *)calloc((size_t)lmax + 2, sizeof(int64_t));
+  if (!start) { free(L); free(size); free(order); return ORC_E_NOMEM; }
+  for (int32_t i = 0; i < n; ++i) start[L[i] + 1] += 1;
+  for (int32_t l = 0; l <= lmax; ++l) start[l + 1] += start[l];
+  for (int32_t i = 0; i < n; ++i) order[start[L[i]]++] = i;
+  for (int32_t q = 0; q < n; ++q) {
+    int32_t v = order[q], best = -1;
+    for (int32_t a = 0; a < k; ++a)
+      if (dip[(int64_t)a * n + v] == L[v] && (best < 0 || size[a] < size[best])) best = a;
+    region[v] = best;
+    size[best] += 1;
+  }
+  free(L); free(size); free(start); free(order);
   return ORC_OK;
 }
 
@@ -569,6 +609,55 @@ int orc_sweep_gs(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
     pos[2 * (int64_t)i] = t[0];
     pos[2 * (int64_t)i + 1] = t[1];
   }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* full stress majorization (Section 3, the update before Eq. 4)        */
+/* ------------------------------------------------------------------ */
+
+/* new position of node i under full stress: every j != i with
+ * w_ij = 1/d_ij^2, d_ij = D[i*n + j] (all-pairs hop distances), j ascending */
+static void full_update(int32_t n, const uint16_t *D, const double *X, int32_t i, double *out) {
+  double xi = X[2 * (int64_t)i], yi = X[2 * (int64_t)i + 1];
+  double nx = 0.0, ny = 0.0, den = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (j == i) continue;
+    double d = (double)D[(int64_t)i * n + j];
+    double w = 1.0 / (d * d);
+    double xj = X[2 * (int64_t)j], yj = X[2 * (int64_t)j + 1];
+    double dx = xi - xj, dy = yi - yj;
+    double r = sqrt(dx * dx + dy * dy);
+    if (r > 0.0) { nx += w * (xj + d * dx / r); ny += w * (yj + d * dy / r); }
+    else { nx += w * xj; ny += w * yj; }
+    den += w;
+  }
+  if (den > 0.0) { out[0] = nx / den; out[1] = ny / den; }
+  else { out[0] = xi; out[1] = yi; }
+}
+
+/* One sweep of full stress majorization over the n x n distance table D.
+ * order 0: Jacobi (every node from pos_in); order 1: Gauss-Seidel, nodes
+ * 0..n-1 in turn, each from the positions already moved (the node-at-a-time
+ * order under which full stress decreases monotonically).  pos_out receives
+ * the new layout; relchange (optional) ||X' - X||_F / ||X||_F. */
+int orc_full_sweep(int32_t n, const uint16_t *D, const double *pos_in, double *pos_out, int32_t order,
+                   double *relchange) {
+  if (n < 1 || (order != 0 && order != 1)) return ORC_E_ARG;
+  for (int64_t t = 0; t < (int64_t)n * n; ++t)
+    if (D[t] == 0xFFFF) return ORC_E_DISCONNECTED;
+  if (order == 0) {
+    for (int32_t i = 0; i < n; ++i) full_update(n, D, pos_in, i, pos_out + 2 * (int64_t)i);
+  } else {
+    memcpy(pos_out, pos_in, 2 * (size_t)n * sizeof(double));
+    double t[2];
+    for (int32_t i = 0; i < n; ++i) {
+      full_update(n, D, pos_out, i, t);
+      pos_out[2 * (int64_t)i] = t[0];
+      pos_out[2 * (int64_t)i + 1] = t[1];
+    }
+  }
+  if (relchange) *relchange = orc_relchange(n, pos_in, pos_out);
   return ORC_OK;
 }
 

@@ -23,7 +23,8 @@ from . import _build
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
     "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
-    "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots",
+    "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
+    "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -72,6 +73,9 @@ def lib():
                 "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
                 "ssm_aggregate_noalloc": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, v]),
+                "ssm_regions_smallest_workspace": (sz, [i32]),
+                "ssm_regions_smallest": (ctypes.c_int, [i32, i32, v, v, v, v, sz, v]),
+                "ssm_aggregate_regions": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, v, sz, v]),
                 "ssm_gram_workspace": (sz, [i32, i32]),
                 "ssm_gram": (ctypes.c_int, [i32, i32, v, v, v, v, v, sz, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
@@ -80,6 +84,10 @@ def lib():
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
                 "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
+                "ssm_iterate_gs_workspace": (sz, [i32]),
+                "ssm_iterate_gs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, v, i32, v, v, v, sz, v]),
+                "ssm_full_iterate_workspace": (sz, [i32, i32]),
+                "ssm_full_iterate": (ctypes.c_int, [i32, v, v, i32, i32, i32, v, v, v, sz, v]),
                 "ssm_stress_workspace": (sz, [i32, i64, i32, i32]),
                 "ssm_stress": (ctypes.c_int, [i32, i64, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
             }
@@ -253,6 +261,42 @@ def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, ch
     return region, off, cnt
 
 
+def ssm_regions_smallest(dip: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
+    """Regions with the paper's tie rule (ties to the currently smallest region)."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    region = torch.empty(n, dtype=torch.int32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_regions_smallest_workspace(n), dev)
+    _rc(L.ssm_regions_smallest(n, k, _ptr(dip), _ptr(region), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_regions_smallest")
+    if check:
+        ssm_check(st, "ssm_regions_smallest", stream)
+    return region
+
+
+def ssm_aggregate_regions(dip: torch.Tensor, region: torch.Tensor, stream=None, check: bool = True):
+    """cnt_off and cnt (Section 3's counts) for given regions; returns (cnt_off, cnt)."""
+    L = lib()
+    k, n = dip.shape
+    dev = dip.device
+    off = torch.empty(k + 1, dtype=torch.int32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_aggregate_workspace(k), dev)
+    length = ctypes.c_int64(0)
+    rc = L.ssm_aggregate_regions(n, k, _ptr(dip), _ptr(region), _ptr(off), None, 0, ctypes.byref(length), _ptr(st),
+                                 _ptr(ws), ws.numel(), _stream(stream))
+    if rc not in (0, -5):
+        _rc(rc, "ssm_aggregate_regions")
+    cnt = torch.empty(max(int(length.value), 1), dtype=torch.uint32, device=dev)
+    _rc(L.ssm_aggregate_regions(n, k, _ptr(dip), _ptr(region), _ptr(off), _ptr(cnt), cnt.numel(), ctypes.byref(length),
+                                _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_aggregate_regions")
+    if check:
+        ssm_check(st, "ssm_aggregate_regions", stream)
+    return off, cnt[: int(length.value)]
+
+
 def ssm_aggregate_noalloc(dip: torch.Tensor, region: torch.Tensor, cnt_off: torch.Tensor, cnt: torch.Tensor | None,
                           status: torch.Tensor, stream=None) -> int:
     """ssm_aggregate into caller buffers with no workspace (the library allocates
@@ -325,6 +369,47 @@ def ssm_iterate(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, tol: float =
     if check:
         ssm_check(work.status, "ssm_iterate", stream)
     return work.iters_done, work.rel
+
+
+def ssm_iterate_gs(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, stream=None, check: bool = True):
+    """`iters` in-place (Gauss-Seidel) sweeps of Eq. 4 in FP64 on pos (float64 [n, 2]);
+    returns the relative change of the last sweep (device float64 tensor)."""
+    L = lib()
+    if pos.dtype != torch.float64:
+        raise ValueError("ssm_iterate_gs runs in FP64: pos must be float64")
+    dev = pos.device
+    rel = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_iterate_gs_workspace(g.n), dev)
+    _rc(L.ssm_iterate_gs(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), p.k, _ptr(p.pivots), _ptr(p.dip), _ptr(p.cnt_off),
+                         _ptr(p.cnt), _ptr(pos), iters, _ptr(rel), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_iterate_gs")
+    if check:
+        ssm_check(st, "ssm_iterate_gs", stream)
+    return rel
+
+
+def ssm_apsp(g: Graph, stream=None, check: bool = True) -> torch.Tensor:
+    """All-pairs hop distances [n, n] uint16: ssm_pivot_bfs with every node as a source."""
+    return ssm_pivot_bfs(g, torch.arange(g.n, dtype=torch.int32, device=g.rowptr.device), stream, check)
+
+
+def ssm_full_iterate(D: torch.Tensor, pos: torch.Tensor, iters: int, order: int = 0, stream=None, check: bool = True):
+    """`iters` sweeps of full stress majorization over the all-pairs table D
+    ([n, n] uint16) on pos in place (order 0 Jacobi FP32/FP64, order 1
+    Gauss-Seidel FP64); returns the relative change of the last sweep."""
+    L = lib()
+    n = D.shape[0]
+    precision = 64 if pos.dtype == torch.float64 else 32
+    dev = pos.device
+    rel = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_full_iterate_workspace(n, precision), dev)
+    _rc(L.ssm_full_iterate(n, _ptr(D), _ptr(pos), precision, order, iters, _ptr(rel), _ptr(st), _ptr(ws), ws.numel(),
+                           _stream(stream)), "ssm_full_iterate")
+    if check:
+        ssm_check(st, "ssm_full_iterate", stream)
+    return rel
 
 
 class StressWorkspace:

@@ -123,6 +123,146 @@ __global__ void k_row_prefix(int32_t k, const int32_t *__restrict__ cnt_off, int
   }
 }
 
+// ---------------------------------------------------------------- the paper's tie rule
+// Regions as Section 3 builds them: incrementally while the distances are
+// computed, a tie going to the currently smallest partition.  Nodes join in
+// the order a multi-source search settles them (increasing distance L to the
+// nearest pivot, then increasing id); a node with several nearest pivots
+// joins the one whose region is smallest at that moment (lowest index on
+// equal sizes).  The prepass finds each node's L and its nearest pivots
+// (up to kTieCand of them, ascending); one block then walks the levels in
+// order, 1024 node ids at a time: a chunk without ties adds its nodes in
+// parallel (the order of unique assignments does not matter), a chunk with
+// ties is walked in id order by one thread, which keeps the region sizes in
+// shared memory.
+constexpr int kTieCand = 4;
+constexpr int kTieMaxK = 8192;
+
+__global__ void __launch_bounds__(kAggThreads) k_tie_prepass(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                                             uint16_t *__restrict__ L, int4 *__restrict__ cand,
+                                                             int32_t *__restrict__ ncand, unsigned *__restrict__ lmax) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+    const int64_t i = i0 + (threadIdx.x & 31);
+    unsigned m = 0u;
+    if (i < n) {
+      const uint16_t *col = dip + i;
+      int c[kTieCand] = {0, 0, 0, 0};
+      int cnt = 0;
+      m = 0xFFFFFFFFu;
+      for (int32_t a0 = 0; a0 < k; a0 += 8) {
+        unsigned dq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dq[q] = a0 + q < k ? (unsigned)__ldg(col + (size_t)(a0 + q) * n) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (dq[q] < m) {
+            m = dq[q];
+            cnt = 0;
+          }
+          if (dq[q] == m && a0 + q < k) {
+            if (cnt < kTieCand) c[cnt] = a0 + q;
+            ++cnt;
+          }
+        }
+      }
+      L[i] = (uint16_t)m;
+      ncand[i] = cnt;
+      cand[i] = make_int4(c[0], c[1], c[2], c[3]);
+    }
+    m = __reduce_max_sync(0xffffffffu, i < n ? m : 0u);
+    if ((threadIdx.x & 31) == 0) atomicMax(lmax, m);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_regions_smallest(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                                           const uint16_t *__restrict__ L,
+                                                           const int4 *__restrict__ cand,
+                                                           const int32_t *__restrict__ ncand,
+                                                           const unsigned *__restrict__ lmax_p,
+                                                           int32_t *__restrict__ region) {
+  extern __shared__ unsigned tsize[];  // [k] current region sizes
+  __shared__ unsigned s_in[32], s_tied[32];
+  __shared__ int s_any;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) tsize[a] = 0u;
+  const unsigned lmax = *lmax_p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (unsigned l = 0; l <= lmax; ++l) {
+    for (int c = 0; c < n; c += blockDim.x) {
+      const int v = c + (int)threadIdx.x;
+      const bool in = v < n && (unsigned)L[v] == l;
+      const int nc = in ? ncand[v] : 0;
+      const unsigned bin = __ballot_sync(0xffffffffu, in), btied = __ballot_sync(0xffffffffu, in && nc > 1);
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      if (lane == 0) {
+        s_in[warp] = bin;
+        s_tied[warp] = btied;
+        if (btied) s_any = 1;
+      }
+      __syncthreads();
+      if (!s_any) {
+        if (in) {
+          const int a = cand[v].x;
+          atomicAdd(tsize + a, 1u);
+          region[v] = a;
+        }
+      } else if (threadIdx.x == 0) {
+        // nodes of this level in id order; ties to the smallest region
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+          for (unsigned mi = s_in[w]; mi; mi &= mi - 1u) {
+            const int b = __ffs(mi) - 1, node = c + 32 * w + b;
+            const int4 cv = cand[node];
+            int best = cv.x;
+            if ((s_tied[w] >> b) & 1u) {
+              const int cnt = ncand[node];
+              if (cnt <= kTieCand) {
+                const int cs[kTieCand] = {cv.x, cv.y, cv.z, cv.w};
+                for (int q = 1; q < cnt; ++q)
+                  if (tsize[cs[q]] < tsize[best]) best = cs[q];
+              } else {
+                best = -1;
+                for (int a = 0; a < k; ++a)
+                  if ((unsigned)__ldg(dip + (size_t)a * n + node) == l && (best < 0 || tsize[a] < tsize[best])) best = a;
+              }
+            }
+            tsize[best] += 1u;
+            region[node] = best;
+          }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ecc_a = max over the nodes of the given region a of d_ia
+__global__ void __launch_bounds__(kAggThreads) k_ecc_given(int32_t n, const uint16_t *__restrict__ dip,
+                                                           const int32_t *__restrict__ region, int32_t k,
+                                                           unsigned *__restrict__ ecc, int32_t *__restrict__ status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+    const int64_t i = i0 + (threadIdx.x & 31);
+    int a = -1;
+    unsigned d = 0u;
+    if (i < n) {
+      a = region[i];
+      if ((unsigned)a >= (unsigned)k) {
+        dev_fail(status, SSM_E_ARG);
+        a = -1;
+      } else {
+        d = __ldg(dip + (size_t)a * n + i);
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, a);
+    unsigned mx = 0u;
+    for (int src = 0; src < 32; ++src) {
+      const unsigned t = __shfl_sync(0xffffffffu, d, src);
+      if ((peers >> src) & 1u) mx = max(mx, t);
+    }
+    if (a >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicMax(ecc + a, mx);
+  }
+}
+
 static int grid_for(int64_t items, int threads) {
   int64_t b = (items + threads - 1) / threads;
   int64_t cap = (int64_t)num_sms() * 8;
@@ -230,6 +370,64 @@ SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int
     return fail(SSM_E_NOMEM, "ssm_aggregate_noalloc: the count table needs %lld entries, cnt holds %lld", h,
                 (long long)cnt_cap);
   if (h >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_aggregate_noalloc: table length must be below 2^31");
+  SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)h * sizeof(uint32_t), s));
+  note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, h, status);
+  note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, h, cnt);
+  note_launch(), k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, h, cnt);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+SSM_API size_t ssm_regions_smallest_workspace(int32_t n) {
+  if (n < 1) return 0;
+  ssm::Carver c(nullptr, 0);
+  c.take<uint16_t>((size_t)n);
+  c.take<int4>((size_t)n);
+  c.take<int32_t>((size_t)n);
+  c.take<unsigned>(1);
+  return c.size();
+}
+
+SSM_API int ssm_regions_smallest(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *status, void *ws,
+                                 size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || !dip || !region || !status || !ws) return fail(SSM_E_ARG, "ssm_regions_smallest: bad argument");
+  if (k < 1 || k > kTieMaxK) return fail(SSM_E_ARG, "ssm_regions_smallest: need 1 <= k <= %d", kTieMaxK);
+  Carver c(ws, ws_bytes);
+  uint16_t *L = c.take<uint16_t>((size_t)n);
+  int4 *cand = c.take<int4>((size_t)n);
+  int32_t *ncand = c.take<int32_t>((size_t)n);
+  unsigned *lmax = c.take<unsigned>(1);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_regions_smallest: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemsetAsync(lmax, 0, sizeof(unsigned), s));
+  note_launch(), k_tie_prepass<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, L, cand, ncand, lmax);
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_regions_smallest));
+  note_launch(), k_regions_smallest<<<1, 1024, (size_t)k * sizeof(unsigned), s>>>(n, k, dip, L, cand, ncand, lmax, region);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+SSM_API int ssm_aggregate_regions(int32_t n, int32_t k, const uint16_t *dip, const int32_t *region, int32_t *cnt_off,
+                                  uint32_t *cnt, int64_t cnt_cap, int64_t *cnt_len, int32_t *status, void *ws,
+                                  size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || k < 1 || !dip || !region || !cnt_off || !cnt_len || !status || !ws || cnt_cap < 0 || (cnt_cap > 0 && !cnt))
+    return fail(SSM_E_ARG, "ssm_aggregate_regions: bad argument");
+  Carver c(ws, ws_bytes);
+  unsigned *ecc = c.take<unsigned>(k);
+  long long *len = c.take<long long>(1);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate_regions: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
+  note_launch(), k_ecc_given<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, k, ecc, status);
+  note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
+  long long h = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  *cnt_len = h;
+  if (h > cnt_cap)
+    return fail(SSM_E_NOMEM, "ssm_aggregate_regions: the count table needs %lld entries, cnt holds %lld", h,
+                (long long)cnt_cap);
+  if (h >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_aggregate_regions: table length must be below 2^31");
   SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)h * sizeof(uint32_t), s));
   note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, h, status);
   note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, h, cnt);

@@ -574,3 +574,104 @@ def test_kmeans_sp_is_an_exact_fixed_point(seed):
         mem = np.nonzero(asg == a)[0]
         best = min(mem, key=lambda i: (dist(i, a), i))
         assert newp[a] == best
+
+
+# ---------------------------------------------------------------- full stress (Section 3, before Eq. 4)
+
+@pytest.mark.parametrize("name", ["grid", "rbtree", "rgg"])
+def test_full_sweep_is_the_sparse_model_with_every_node_a_pivot(name):
+    """Section 3: with k = n the sparse model reduces to full stress.  The
+    full-stress sweep (all j != i with w = 1/d^2, j ascending) against the
+    sparse sweep with every node a pivot (neighbours first, then pivots), in
+    both orders; the two differ only in the order of the sums."""
+    n, s, d = {"grid": lambda: I.grid(7, 9), "rbtree": lambda: I.random_btree(60, 2),
+               "rgg": lambda: I.rgg(90, 6.0, 3)}[name]()
+    g = O.build_csr(n, s, d)
+    D = O.apsp(g)
+    piv = np.arange(n, dtype=np.int32)
+    w = O.adapted_weights(D, O.regions(D))
+    x = np.random.default_rng(7).normal(size=(n, 2)) * 4
+    a, ra = O.full_sweep(D, x, 0)
+    b, rb = O.sweep_jacobi(g, piv, D, w, x)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    assert ra == pytest.approx(rb, rel=1e-12)
+    c, _ = O.full_sweep(D, x, 1)
+    np.testing.assert_allclose(c, O.sweep_gs(g, piv, D, w, x), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_full_gauss_seidel_decreases_full_stress(seed):
+    """The node-at-a-time update decreases full stress monotonically (the
+    property Section 3 cites); exhaustive stress after every sweep."""
+    rng = np.random.default_rng(seed)
+    n, s, d = _rand_graph(rng, 40, 0.06)
+    g = O.build_csr(n, s, d)
+    D = O.apsp(g)
+    x = rng.normal(size=(n, 2)) * 5
+    prev = O.full_stress(g, x)[0]
+    for _ in range(8):
+        x, _ = O.full_sweep(D, x, 1)
+        cur = O.full_stress(g, x)[0]
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
+def test_full_sweep_keeps_an_exact_layout():
+    """A path drawn at unit spacing realises every distance (r = d), so every
+    term is x_j + (x_i - x_j) = x_i and the layout is a fixed point."""
+    n, s, d = I.path(12)
+    D = O.apsp(O.build_csr(n, s, d))
+    x = np.stack([np.arange(n, dtype=np.float64), np.zeros(n)], 1)
+    for order in (0, 1):
+        y, rel = O.full_sweep(D, x, order)
+        np.testing.assert_allclose(y, x, atol=1e-12)
+        assert rel < 1e-14
+
+
+# ---------------------------------------------------------------- the paper's region tie rule
+
+def test_regions_smallest_hand_derived_path():
+    """Path 0..8 with pivots (0, 8, 4): distances to the nearest pivot are
+    0 (nodes 0, 4, 8), 1 (1, 3, 5, 7), 2 (2, 6).  Level 0: each pivot joins its
+    own region (sizes 1, 1, 1).  Level 1 in id order: 1 -> region 0, 3 ->
+    region 2, 5 -> region 2, 7 -> region 1 (each has one nearest pivot):
+    sizes 2, 2, 3.  Level 2: node 2 ties between regions 0 and 2 (sizes 2 and
+    3) -> 0; node 6 ties between regions 1 and 2 (sizes 2 and 3) -> 1."""
+    n, s, d = I.path(9)
+    g = O.build_csr(n, s, d)
+    dip = O.pivot_dist(g, [0, 8, 4])
+    assert O.regions_smallest(dip).tolist() == [0, 0, 0, 2, 2, 2, 1, 1, 1]
+
+
+def test_regions_smallest_differs_from_lowest_index():
+    """A star with centre 0 and leaves 1..6, a path 6-7-8, pivots (0, 7).
+    Level 0: node 0 -> region 0, node 7 -> region 1.  Level 1 in id order:
+    leaves 1..5 -> region 0 (size 6 after them); node 6 is at distance 1 from
+    both pivots and joins the smaller region 1 (size 1), where the
+    lowest-index rule puts it in region 0; node 8 -> region 1."""
+    s = [0, 0, 0, 0, 0, 0, 6, 7]
+    d = [1, 2, 3, 4, 5, 6, 7, 8]
+    g = O.build_csr(9, s, d)
+    dip = O.pivot_dist(g, [0, 7])
+    assert O.regions(dip)[6] == 0
+    assert O.regions_smallest(dip).tolist() == [0, 0, 0, 0, 0, 0, 1, 1, 1]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_regions_smallest_is_a_nearest_pivot_partition(seed):
+    """Invariants of any tie rule: every node joins a nearest pivot, every
+    pivot node its own region (distinct pivots), and nodes with a single
+    nearest pivot agree with the lowest-index rule."""
+    rng = np.random.default_rng(seed)
+    n, s, d = _rand_graph(rng, 60, 0.05)
+    g = O.build_csr(n, s, d)
+    piv = O.maxmin(g, 9)
+    dip = O.pivot_dist(g, piv)
+    reg = O.regions_smallest(dip)
+    low = O.regions(dip)
+    m = dip.min(0)
+    assert (dip[reg, np.arange(n)] == m).all()
+    for a, p in enumerate(piv):
+        assert reg[p] == a
+    single = (dip == m).sum(0) == 1
+    assert np.array_equal(reg[single], low[single])
