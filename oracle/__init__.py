@@ -67,9 +67,23 @@ def _load():
                 "orc_stress_sums_range": [i32, v, v, v, i32, i32, u64, i32, i32, v],
                 "orc_sweep_gs": [i32, v, v, i32, v, v, v, v],
                 "orc_full_sweep": [i32, v, v, v, i32, v],
+                "orc_procrustes": [i32, v, v, v],
+                "orc_hull_error": [i32, v, v, i32, v, v],
+                "orc_gabriel": [i32, v, v],
+                "orc_gabriel_jaccard": [i32, v, v, i32, v, v],
                 "orc_splitmix64": [u64, i64, v],
                 "orc_sample_pairs": [i32, i32, i32, u64, v, v],
                 "orc_full_stress": [i32, v, v, v, i32, i32, u64, v, v],
+                "orc_build_wcsr": [i32, i64, v, v, v, v, v, v, v],
+                "orc_sssp": [i32, v, v, v, i32, v],
+                "orc_wmaxmin": [i32, v, v, v, i32, i32, v],
+                "orc_wpivot_dist": [i32, v, v, v, i32, v, v],
+                "orc_wregions": [i32, i32, v, v],
+                "orc_wcounts_rows": [i32, v, v, i32, v, v, v, v, i32, i32],
+                "orc_wpivotmds": [i32, i32, v, v, v, v],
+                "orc_wrescale": [i32, v, v, v, v],
+                "orc_wsweep_jacobi_rows": [i32, v, v, v, i32, v, v, v, v, v, i32, i32],
+                "orc_wfull_stress": [i32, v, v, v, v, i32, i32, u64, v, v],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -339,6 +353,47 @@ def full_sweep(D: np.ndarray, pos, order: int = 0):
     return out, rel.value
 
 
+def procrustes(X, Y):
+    """Procrustes statistic of layouts X, Y [n][2] (rotation and uniform scale,
+    no reflection): returns (P, scale, angle)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    out = np.zeros(3, np.float64)
+    _chk(_load().orc_procrustes(len(X), _p(X), _p(Y), _p(out)), "procrustes")
+    return tuple(out.tolist())
+
+
+def hull_error(D: np.ndarray, pos, kh: int):
+    """Convex-hull error of Fig. 4 for hop radius kh: returns (mean, per-node errors)."""
+    D = np.ascontiguousarray(D, dtype=np.uint16)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = D.shape[0]
+    per = np.zeros(n, np.float64)
+    mean = ctypes.c_double(0.0)
+    _chk(_load().orc_hull_error(n, _p(D), _p(pos), kh, _p(per), ctypes.byref(mean)), "hull_error")
+    return mean.value, per
+
+
+def gabriel(pos) -> np.ndarray:
+    """Gabriel graph of a layout as an n x n 0/1 matrix (open-disc reading)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = len(pos)
+    adj = np.zeros((n, n), np.uint8)
+    _chk(_load().orc_gabriel(n, _p(pos), _p(adj)), "gabriel")
+    return adj
+
+
+def gabriel_jaccard(posA, posB, kh: int):
+    """Gabriel-graph kh-neighbourhood Jaccard similarity of Fig. 3: (mean, per node)."""
+    posA = np.ascontiguousarray(posA, dtype=np.float64)
+    posB = np.ascontiguousarray(posB, dtype=np.float64)
+    n = len(posA)
+    per = np.zeros(n, np.float64)
+    mean = ctypes.c_double(0.0)
+    _chk(_load().orc_gabriel_jaccard(n, _p(posA), _p(posB), kh, _p(per), ctypes.byref(mean)), "gabriel_jaccard")
+    return mean.value, per
+
+
 def splitmix64(seed: int, count: int) -> np.ndarray:
     out = np.zeros(count, np.uint64)
     _chk(_load().orc_splitmix64(ctypes.c_uint64(seed), count, _p(out)), "splitmix64")
@@ -397,3 +452,140 @@ def iterate(p: Prepared, pos, iters: int):
     for _ in range(iters):
         pos, rel = sweep_jacobi(p.g, p.pivots, p.dip, p.w, pos)
     return pos, rel
+
+
+# ---------------------------------------------------------------- weighted graphs
+class WGraph(Graph):
+    """CSR of a weighted simple undirected graph: as Graph plus elen[2m]
+    (float32, the length of the edge colidx[t])."""
+
+    def __init__(self, n, rowptr, colidx, m, elen):
+        super().__init__(n, rowptr, colidx, m)
+        self.elen = elen
+
+
+def build_wcsr(n: int, src, dst, lengths) -> WGraph:
+    src, dst = _i32(src), _i32(dst)
+    lengths = np.ascontiguousarray(lengths, dtype=np.float32)
+    rowptr = np.zeros(n + 1, np.int32)
+    colidx = np.zeros(max(2 * len(src), 1), np.int32)
+    elen = np.zeros(max(2 * len(src), 1), np.float32)
+    m = ctypes.c_int64(0)
+    _chk(_load().orc_build_wcsr(n, len(src), _p(src), _p(dst), _p(lengths), _p(rowptr), _p(colidx), _p(elen),
+                                ctypes.byref(m)), "build_wcsr")
+    return WGraph(n, rowptr, colidx[: 2 * m.value].copy(), m.value, elen[: 2 * m.value].copy())
+
+
+def sssp(g: WGraph, s: int) -> np.ndarray:
+    dist = np.zeros(g.n, np.float32)
+    _chk(_load().orc_sssp(g.n, _p(g.rowptr), _p(g.colidx), _p(g.elen), s, _p(dist)), "sssp")
+    return dist
+
+
+def wmaxmin(g: WGraph, k: int, start: int = 0) -> np.ndarray:
+    piv = np.zeros(k, np.int32)
+    _chk(_load().orc_wmaxmin(g.n, _p(g.rowptr), _p(g.colidx), _p(g.elen), k, start, _p(piv)), "wmaxmin")
+    return piv
+
+
+def wpivot_dist(g: WGraph, pivots) -> np.ndarray:
+    pivots = _i32(pivots)
+    dip = np.zeros((len(pivots), g.n), np.float32)
+    _chk(_load().orc_wpivot_dist(g.n, _p(g.rowptr), _p(g.colidx), _p(g.elen), len(pivots), _p(pivots), _p(dip)),
+         "wpivot_dist")
+    return dip
+
+
+def wregions(dip) -> np.ndarray:
+    dip = np.ascontiguousarray(dip, dtype=np.float32)
+    k, n = dip.shape
+    reg = np.zeros(n, np.int32)
+    _chk(_load().orc_wregions(n, k, _p(dip), _p(reg)), "wregions")
+    return reg
+
+
+def wcounts(g: WGraph, pivots, dip, region, i0: int = 0, i1: int | None = None, threads: int = 1) -> np.ndarray:
+    """s[a][i] for the nodes i0 <= i < i1 (other columns 0), by direct count;
+    the node range split over `threads` host threads."""
+    import concurrent.futures as cf
+
+    pivots, region = _i32(pivots), _i32(region)
+    dip = np.ascontiguousarray(dip, dtype=np.float32)
+    k, n = dip.shape
+    i1 = n if i1 is None else i1
+    s = np.zeros((k, n), np.uint32)
+    lib = _load()
+    cuts = [i0 + (i1 - i0) * t // threads for t in range(threads + 1)]
+
+    def run(t):
+        return lib.orc_wcounts_rows(n, _p(g.rowptr), _p(g.colidx), k, _p(pivots), _p(dip), _p(region), _p(s),
+                                    cuts[t], cuts[t + 1])
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for rc in ex.map(run, range(threads)):
+            _chk(rc, "wcounts_rows")
+    return s
+
+
+def wpivotmds(dip):
+    dip = np.ascontiguousarray(dip, dtype=np.float32)
+    k, n = dip.shape
+    pos = np.zeros((n, 2), np.float64)
+    eig = np.zeros(2, np.float64)
+    _chk(_load().orc_wpivotmds(n, k, _p(dip), _p(pos), _p(eig), None), "wpivotmds")
+    return pos, eig
+
+
+def wrescale(g: WGraph, pos) -> np.ndarray:
+    pos = np.array(pos, dtype=np.float64, order="C")
+    _chk(_load().orc_wrescale(g.n, _p(g.rowptr), _p(g.colidx), _p(g.elen), _p(pos)), "wrescale")
+    return pos
+
+
+def wsweep_jacobi(g: WGraph, pivots, dip, s, pos, threads: int = 1):
+    """One Jacobi update of Eq. 4 on a weighted graph: (positions, relative change)."""
+    import concurrent.futures as cf
+
+    pivots = _i32(pivots)
+    dip = np.ascontiguousarray(dip, dtype=np.float32)
+    s = np.ascontiguousarray(s, dtype=np.uint32)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros_like(pos)
+    n = g.n
+    lib = _load()
+    cuts = [n * t // threads for t in range(threads + 1)]
+
+    def run(t):
+        return lib.orc_wsweep_jacobi_rows(n, _p(g.rowptr), _p(g.colidx), _p(g.elen), len(pivots), _p(pivots),
+                                          _p(dip), _p(s), _p(pos), _p(out), cuts[t], cuts[t + 1])
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for rc in ex.map(run, range(threads)):
+            _chk(rc, "wsweep_jacobi_rows")
+    return out, lib.orc_relchange(n, _p(pos), _p(out))
+
+
+def wfull_stress(g: WGraph, pos, nsources: int = 0, ntargets: int = 0, seed: int = 0):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.zeros(4, np.float64)
+    sums = np.zeros(4, np.float64)
+    _chk(_load().orc_wfull_stress(g.n, _p(g.rowptr), _p(g.colidx), _p(g.elen), _p(pos), nsources, ntargets,
+                                  ctypes.c_uint64(seed), _p(out), _p(sums)), "wfull_stress")
+    return out, sums
+
+
+class WPrepared:
+    def __init__(self, g, pivots, dip, region, s, pos, eig):
+        self.g, self.pivots, self.dip, self.region, self.s, self.pos, self.eig = g, pivots, dip, region, s, pos, eig
+
+
+def wprepare(n: int, src, dst, lengths, k: int, start: int = 0, threads: int = 1) -> WPrepared:
+    """Algorithm 1 lines 1-4 on a weighted graph."""
+    g = build_wcsr(n, src, dst, lengths)
+    piv = wmaxmin(g, k, start)
+    dip = wpivot_dist(g, piv)
+    reg = wregions(dip)
+    s = wcounts(g, piv, dip, reg, threads=threads)
+    pos, eig = wpivotmds(dip)
+    pos = wrescale(g, pos)
+    return WPrepared(g, piv, dip, reg, s, pos, eig)

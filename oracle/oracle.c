@@ -24,7 +24,13 @@
  *                        (orc_sweep_jacobi_rows: the same for a node range)
  *   orc_sweep_gs         the same, in place node by node              (Algorithm 1, lines 6-10)
  *   orc_full_sweep       full stress majorization, Jacobi or in place (Section 3, before Eq. 4)
+ *   orc_procrustes       Procrustes statistic of two layouts          (Section 4, "Sampling Evaluation")
+ *   orc_hull_error       convex-hull error of k-neighbourhoods        (Section 4, Fig. 4)
+ *   orc_gabriel(_jaccard) Gabriel graph, neighbourhood similarity    (Section 4, Fig. 3)
  *   orc_full_stress      Eq. 1 over all pairs, or over sampled pairs  (Eq. 1, Section 4)
+ *   orc_build_wcsr, orc_sssp, orc_wmaxmin, orc_wpivot_dist, orc_wregions,
+ *   orc_wcounts_rows, orc_wpivotmds, orc_wrescale, orc_wsweep_jacobi_rows,
+ *   orc_wfull_stress     the same steps on weighted graphs            (Algorithm 1 line 2, Section 3)
  *                        (orc_stress_sums_range: its pair sums for a source range)
  *
  * Readings taken where the paper is silent (each is listed with its reason
@@ -452,9 +458,9 @@ static int jacobi_eigen(int32_t k, double *A, double *V) {
  *   tie) is positive;  x_i = ((C v1)_i, (C v2)_i).
  * pos is [n][2]; eig (optional) receives the two eigenvalues, B (optional,
  * k*k) receives C^T C before the eigen-solve. */
-int orc_pivotmds(int32_t n, int32_t k, const uint16_t *dip, double *pos, double *eig, double *Bout) {
-  if (k < 2) return ORC_E_ARG;
-  double *C = (double *)malloc((size_t)n * k * sizeof(double));
+/* the steps after delta: C ([n][k], holding delta_ia on entry) is centred
+ * in place; C is released here */
+static int pivotmds_from_delta(int32_t n, int32_t k, double *C, double *pos, double *eig, double *Bout) {
   double *rowm = (double *)calloc((size_t)n, sizeof(double));
   double *colm = (double *)calloc((size_t)k, sizeof(double));
   double *B = (double *)calloc((size_t)k * k, sizeof(double));
@@ -463,9 +469,7 @@ int orc_pivotmds(int32_t n, int32_t k, const uint16_t *dip, double *pos, double 
   double grand = 0.0;
   for (int32_t i = 0; i < n; ++i)
     for (int32_t a = 0; a < k; ++a) {
-      double d = (double)dip[(int64_t)a * n + i];
-      double delta = d * d;
-      C[(int64_t)i * k + a] = delta;
+      double delta = C[(int64_t)i * k + a];
       rowm[i] += delta;
       colm[a] += delta;
       grand += delta;
@@ -506,6 +510,32 @@ int orc_pivotmds(int32_t n, int32_t k, const uint16_t *dip, double *pos, double 
   }
   free(C); free(rowm); free(colm); free(B); free(V);
   return rc;
+}
+
+int orc_pivotmds(int32_t n, int32_t k, const uint16_t *dip, double *pos, double *eig, double *Bout) {
+  if (k < 2) return ORC_E_ARG;
+  double *C = (double *)malloc((size_t)n * k * sizeof(double));
+  if (!C) return ORC_E_NOMEM;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t a = 0; a < k; ++a) {
+      double d = (double)dip[(int64_t)a * n + i];
+      C[(int64_t)i * k + a] = d * d;
+    }
+  return pivotmds_from_delta(n, k, C, pos, eig, Bout);
+}
+
+/* PivotMDS on weighted distances: the same steps with delta_ia = d_ia^2
+ * from the float32 table (squared in FP64, exactly) */
+int orc_wpivotmds(int32_t n, int32_t k, const float *dip, double *pos, double *eig, double *Bout) {
+  if (k < 2) return ORC_E_ARG;
+  double *C = (double *)malloc((size_t)n * k * sizeof(double));
+  if (!C) return ORC_E_NOMEM;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t a = 0; a < k; ++a) {
+      double d = (double)dip[(int64_t)a * n + i];
+      C[(int64_t)i * k + a] = d * d;
+    }
+  return pivotmds_from_delta(n, k, C, pos, eig, Bout);
 }
 
 /* ------------------------------------------------------------------ */
@@ -662,6 +692,215 @@ int orc_full_sweep(int32_t n, const uint16_t *D, const double *pos_in, double *p
 }
 
 /* ------------------------------------------------------------------ */
+/* layout quality (Section 4)                                          */
+/* ------------------------------------------------------------------ */
+
+/* Procrustes statistic (Sibson 1978) of two layouts X and Y of the same n
+ * nodes ([n][2]): both centred, Y fitted by a uniform scale s and a proper
+ * rotation R (no reflection: Section 4 notes that the analysis cannot
+ * resolve reflections),
+ *   P = 1 - T^2 / (||Xc||^2 ||Yc||^2),  T = max_R tr(R Xc^T Yc)
+ *     = sqrt((m11 + m22)^2 + (m12 - m21)^2),  m_ab = sum_i xc_ia yc_ib.
+ * P is in [0, 1], 0 for a perfect match.  out = {P, s, theta} with
+ * Y ~ s R(theta) X + translation, R(theta) = [[c, -s], [s, c]]. */
+int orc_procrustes(int32_t n, const double *X, const double *Y, double *out) {
+  if (n < 1) return ORC_E_ARG;
+  double mx0 = 0.0, mx1 = 0.0, my0 = 0.0, my1 = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    mx0 += X[2 * (int64_t)i]; mx1 += X[2 * (int64_t)i + 1];
+    my0 += Y[2 * (int64_t)i]; my1 += Y[2 * (int64_t)i + 1];
+  }
+  mx0 /= n; mx1 /= n; my0 /= n; my1 /= n;
+  double m11 = 0.0, m12 = 0.0, m21 = 0.0, m22 = 0.0, xx = 0.0, yy = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    double x0 = X[2 * (int64_t)i] - mx0, x1 = X[2 * (int64_t)i + 1] - mx1;
+    double y0 = Y[2 * (int64_t)i] - my0, y1 = Y[2 * (int64_t)i + 1] - my1;
+    m11 += x0 * y0; m12 += x0 * y1; m21 += x1 * y0; m22 += x1 * y1;
+    xx += x0 * x0 + x1 * x1;
+    yy += y0 * y0 + y1 * y1;
+  }
+  double a = m11 + m22, b = m12 - m21;
+  double T = sqrt(a * a + b * b);
+  if (!(xx > 0.0) || !(yy > 0.0)) { out[0] = 1.0; out[1] = 0.0; out[2] = 0.0; return ORC_OK; }
+  out[0] = 1.0 - T * T / (xx * yy);
+  out[1] = T / xx;
+  out[2] = atan2(b, a);
+  return ORC_OK;
+}
+
+/* cross product (b - a) x (c - a), evaluated as written (the hull and the
+ * inside test of orc_hull_error share it) */
+static double cross3(const double *a, const double *b, const double *c) {
+  double ux = b[0] - a[0], uy = b[1] - a[1], vx = c[0] - a[0], vy = c[1] - a[1];
+  return ux * vy - uy * vx;
+}
+
+static const double *g_sort_pos; /* qsort context of the hull */
+static int cmp_xy(const void *pa, const void *pb) {
+  int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+  const double *A = g_sort_pos + 2 * (int64_t)a, *B = g_sort_pos + 2 * (int64_t)b;
+  if (A[0] != B[0]) return A[0] < B[0] ? -1 : 1;
+  if (A[1] != B[1]) return A[1] < B[1] ? -1 : 1;
+  return (a > b) - (a < b);
+}
+
+/* convex hull of the points idx[0..m) of pos (Andrew's monotone chain: sort by
+ * (x, y, index), lower then upper chain, a point is dropped while the turn
+ * it makes is not strictly counter-clockwise); hull receives the vertex
+ * indices counter-clockwise without repeating the first; returns their count */
+static int32_t monotone_hull(const double *pos, int32_t *idx, int32_t m, int32_t *hull) {
+  g_sort_pos = pos;
+  qsort(idx, (size_t)m, sizeof(int32_t), cmp_xy);
+  int32_t h = 0;
+  for (int32_t t = 0; t < m; ++t) { /* lower chain */
+    while (h >= 2 && cross3(pos + 2 * (int64_t)hull[h - 2], pos + 2 * (int64_t)hull[h - 1], pos + 2 * (int64_t)idx[t]) <= 0.0) --h;
+    hull[h++] = idx[t];
+  }
+  int32_t lo = h + 1;
+  for (int32_t t = m - 2; t >= 0; --t) { /* upper chain */
+    while (h >= lo && cross3(pos + 2 * (int64_t)hull[h - 2], pos + 2 * (int64_t)hull[h - 1], pos + 2 * (int64_t)idx[t]) <= 0.0) --h;
+    hull[h++] = idx[t];
+  }
+  if (h > 1) --h; /* the last point repeats the first */
+  return h;
+}
+
+/* is q inside or on the convex polygon hull[0..h) (counter-clockwise)?  A
+ * hull of one point: q equal to it; of two points: q on the segment */
+static int in_hull(const double *pos, const int32_t *hull, int32_t h, const double *q) {
+  if (h == 1) return q[0] == pos[2 * (int64_t)hull[0]] && q[1] == pos[2 * (int64_t)hull[0] + 1];
+  if (h == 2) {
+    const double *a = pos + 2 * (int64_t)hull[0], *b = pos + 2 * (int64_t)hull[1];
+    if (cross3(a, b, q) != 0.0) return 0;
+    return q[0] >= fmin(a[0], b[0]) && q[0] <= fmax(a[0], b[0]) && q[1] >= fmin(a[1], b[1]) && q[1] <= fmax(a[1], b[1]);
+  }
+  double x0 = pos[2 * (int64_t)hull[0]], x1 = x0, y0 = pos[2 * (int64_t)hull[0] + 1], y1 = y0;
+  for (int32_t e = 1; e < h; ++e) { /* outside the hull's bounding box: outside */
+    x0 = fmin(x0, pos[2 * (int64_t)hull[e]]); x1 = fmax(x1, pos[2 * (int64_t)hull[e]]);
+    y0 = fmin(y0, pos[2 * (int64_t)hull[e] + 1]); y1 = fmax(y1, pos[2 * (int64_t)hull[e] + 1]);
+  }
+  if (q[0] < x0 || q[0] > x1 || q[1] < y0 || q[1] > y1) return 0;
+  for (int32_t e = 0; e < h; ++e) {
+    const double *a = pos + 2 * (int64_t)hull[e], *b = pos + 2 * (int64_t)hull[(e + 1) % h];
+    if (cross3(a, b, q) < 0.0) return 0;
+  }
+  return 1;
+}
+
+/* Convex-hull error (Section 4, Fig. 4): for node v, B = {w : d_vw <= kh}
+ * (graph distances D, [n][n]), H = convex hull of the positions of B;
+ * err_v = |{u not in B : x_u inside or on H}| / (n - |B|) (0 when B = V).
+ * per_node (optional) receives err_v; *mean their mean in node order. */
+int orc_hull_error(int32_t n, const uint16_t *D, const double *pos, int32_t kh, double *per_node, double *mean) {
+  if (n < 1 || kh < 0) return ORC_E_ARG;
+  int32_t *ball = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *hull = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+  if (!ball || !hull) { free(ball); free(hull); return ORC_E_NOMEM; }
+  double sum = 0.0;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t m = 0;
+    for (int32_t w = 0; w < n; ++w)
+      if (D[(int64_t)v * n + w] <= kh) ball[m++] = w;
+    double err = 0.0;
+    if (m < n) {
+      int32_t h = monotone_hull(pos, ball, m, hull);
+      int64_t cnt = 0;
+      for (int32_t u = 0; u < n; ++u)
+        if (D[(int64_t)v * n + u] > kh && in_hull(pos, hull, h, pos + 2 * (int64_t)u)) ++cnt;
+      err = (double)cnt / (double)(n - m);
+    }
+    if (per_node) per_node[v] = err;
+    sum += err;
+  }
+  *mean = sum / (double)n;
+  free(ball); free(hull);
+  return ORC_OK;
+}
+
+/* Is w strictly inside the disc with diameter ab?  |2w - a - b|^2 < |a - b|^2,
+ * evaluated as written with a the lower and b the higher node id, so that
+ * the test for the pair (a, b) does not depend on the order it is asked in. */
+static int in_diameter_disc(const double *pos, int32_t a, int32_t b, int32_t w) {
+  if (a > b) { int32_t t = a; a = b; b = t; }
+  const double *A = pos + 2 * (int64_t)a, *B = pos + 2 * (int64_t)b, *W = pos + 2 * (int64_t)w;
+  double tx = 2.0 * W[0] - A[0] - B[0], ty = 2.0 * W[1] - A[1] - B[1];
+  double ex = A[0] - B[0], ey = A[1] - B[1];
+  return tx * tx + ty * ty < ex * ex + ey * ey;
+}
+
+/* Gabriel graph of a layout (Section 4, after Fig. 4): u and v adjacent iff
+ * no other point lies inside the disc with diameter uv (read as the open
+ * disc, so identical positions -- a disc of radius 0 -- are adjacent, as the
+ * paper adds them).  adj[u*n + v] = 1 for an edge (n x n bytes). */
+int orc_gabriel(int32_t n, const double *pos, uint8_t *adj) {
+  if (n < 1) return ORC_E_ARG;
+  memset(adj, 0, (size_t)n * n);
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t v = u + 1; v < n; ++v) {
+      int ok = 1;
+      for (int32_t w = 0; w < n && ok; ++w)
+        if (w != u && w != v && in_diameter_disc(pos, u, v, w)) ok = 0;
+      if (ok) adj[(int64_t)u * n + v] = adj[(int64_t)v * n + u] = 1;
+    }
+  return ORC_OK;
+}
+
+/* nodes within kh hops of s in the graph adj (n x n), s excluded; mark[]
+ * receives 1 for them; returns their number */
+static int32_t ball_adj(int32_t n, const uint8_t *adj, int32_t s, int32_t kh, int32_t *dist, int32_t *queue,
+                        uint8_t *mark) {
+  for (int32_t v = 0; v < n; ++v) { dist[v] = -1; mark[v] = 0; }
+  int32_t head = 0, tail = 0, cnt = 0;
+  dist[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    if (dist[u] == kh) continue;
+    for (int32_t v = 0; v < n; ++v)
+      if (adj[(int64_t)u * n + v] && dist[v] < 0) {
+        dist[v] = dist[u] + 1;
+        queue[tail++] = v;
+        mark[v] = 1;
+        ++cnt;
+      }
+  }
+  return cnt;
+}
+
+/* Gabriel-graph similarity (Section 4, Fig. 3): the Gabriel graphs of two
+ * layouts A and B of the same nodes, and for every node v the Jaccard
+ * coefficient of its kh-neighbourhoods (nodes within kh hops, v itself
+ * excluded) in the two graphs; 1 when both are empty.  per_node
+ * (optional) receives them, *mean their mean in node order. */
+int orc_gabriel_jaccard(int32_t n, const double *posA, const double *posB, int32_t kh, double *per_node,
+                        double *mean) {
+  if (n < 1 || kh < 1) return ORC_E_ARG;
+  uint8_t *ga = (uint8_t *)malloc((size_t)n * n), *gb = (uint8_t *)malloc((size_t)n * n);
+  uint8_t *ma = (uint8_t *)malloc((size_t)n), *mb = (uint8_t *)malloc((size_t)n);
+  int32_t *dist = (int32_t *)malloc((size_t)n * sizeof(int32_t)), *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!ga || !gb || !ma || !mb || !dist || !queue) {
+    free(ga); free(gb); free(ma); free(mb); free(dist); free(queue);
+    return ORC_E_NOMEM;
+  }
+  orc_gabriel(n, posA, ga);
+  orc_gabriel(n, posB, gb);
+  double sum = 0.0;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t ca = ball_adj(n, ga, v, kh, dist, queue, ma);
+    int32_t cb = ball_adj(n, gb, v, kh, dist, queue, mb);
+    int32_t both = 0;
+    for (int32_t w = 0; w < n; ++w) both += ma[w] & mb[w];
+    int32_t uni = ca + cb - both;
+    double j = uni > 0 ? (double)both / (double)uni : 1.0;
+    if (per_node) per_node[v] = j;
+    sum += j;
+  }
+  *mean = sum / (double)n;
+  free(ga); free(gb); free(ma); free(mb); free(dist); free(queue);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* stress (Eq. 1) with optimal scaling                                 */
 /* ------------------------------------------------------------------ */
 
@@ -782,4 +1021,313 @@ int orc_stress_sums_range(int32_t n, const int32_t *rowptr, const int32_t *colid
   int rc = stress_accumulate(n, rowptr, colidx, pos, S, T, srcs, tgts, q0, q1, dist, sums);
   free(dist); free(srcs); free(tgts);
   return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* weighted graphs (Algorithm 1 line 2: weighted MSSP; Section 3)        */
+/* ------------------------------------------------------------------ */
+/* Edge lengths l_ij are float32 (finite, at least FLT_MIN, n * max l below
+ * 1e37 so no path sum overflows).  A distance is the least path sum over the
+ * s-v paths with every partial sum rounded to float32 as the path is walked
+ * from s (d(v) = fl(d(u) + l_uv)); rounding is monotone, so this minimum is
+ * what any label-setting or label-correcting search reaches.  Stress weights
+ * are w_ij = l_ij^-2 on edges and w'_ip = s / d_ip^2 on pivots, with s the
+ * number of j in R(p) with 2 d_jp <= d_ip, decided in float32. */
+
+typedef struct { float d; int32_t v; } wheap_item;
+
+static void wheap_push(wheap_item *h, int64_t *len, float d, int32_t v) {
+  int64_t i = (*len)++;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d <= d) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i].d = d;
+  h[i].v = v;
+}
+
+static wheap_item wheap_pop(wheap_item *h, int64_t *len) {
+  wheap_item top = h[0], last = h[--(*len)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= *len) break;
+    if (c + 1 < *len && h[c + 1].d < h[c].d) ++c;
+    if (last.d <= h[c].d) break;
+    h[i] = h[c];
+    i = c;
+  }
+  if (*len > 0) h[i] = last;
+  return top;
+}
+
+typedef struct { int32_t v; float l; } nbr_len;
+
+static int cmp_nbr_len(const void *a, const void *b) {
+  const nbr_len *x = (const nbr_len *)a, *y = (const nbr_len *)b;
+  if (x->v != y->v) return (x->v > y->v) - (x->v < y->v);
+  return (x->l > y->l) - (x->l < y->l);
+}
+
+/* Weighted simple undirected graph: as orc_build_csr, and elen[t] is the
+ * length of the edge colidx[t]; a repeated edge keeps its shortest length.
+ * Lengths must be finite, at least FLT_MIN, with n * max length < 1e37. */
+int orc_build_wcsr(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst, const float *len,
+                   int32_t *rowptr, int32_t *colidx, float *elen, int64_t *m_out) {
+  if (n < 1 || m_in < 0) return ORC_E_ARG;
+  double lmax = 0.0;
+  for (int64_t e = 0; e < m_in; ++e) {
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return ORC_E_GRAPH;
+    if (!(len[e] >= 1.17549435e-38f) || !(len[e] <= 3.4e38f)) return ORC_E_ARG;
+    if (len[e] > lmax) lmax = len[e];
+  }
+  if ((double)n * lmax >= 1e37) return ORC_E_ARG;
+  int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  nbr_len *tmp = (nbr_len *)malloc((size_t)(2 * m_in + 1) * sizeof(nbr_len));
+  if (!deg || !fill || !tmp) { free(deg); free(fill); free(tmp); return ORC_E_NOMEM; }
+  for (int64_t e = 0; e < m_in; ++e)
+    if (src[e] != dst[e]) { deg[src[e] + 1]++; deg[dst[e] + 1]++; }
+  for (int32_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  memcpy(fill, deg, ((size_t)n + 1) * sizeof(int64_t));
+  for (int64_t e = 0; e < m_in; ++e)
+    if (src[e] != dst[e]) {
+      nbr_len a = {dst[e], len[e]}, b = {src[e], len[e]};
+      tmp[fill[src[e]]++] = a;
+      tmp[fill[dst[e]]++] = b;
+    }
+  int64_t out = 0;
+  rowptr[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t b = deg[i], e = deg[i + 1];
+    qsort(tmp + b, (size_t)(e - b), sizeof(nbr_len), cmp_nbr_len);
+    for (int64_t t = b; t < e; ++t)
+      if (t == b || tmp[t].v != tmp[t - 1].v) {  /* first of a group: the shortest */
+        colidx[out] = tmp[t].v;
+        elen[out] = tmp[t].l;
+        ++out;
+      }
+    rowptr[i + 1] = (int32_t)out;
+  }
+  free(deg); free(fill); free(tmp);
+  *m_out = out / 2;
+  return ORC_OK;
+}
+
+/* Dijkstra's algorithm with a binary heap (lazy deletion), float32 sums:
+ * dist[v] = least rounded path sum from s, +inf if unreachable. */
+int orc_sssp(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t s, float *dist) {
+  if (s < 0 || s >= n) return ORC_E_ARG;
+  int64_t cap = (int64_t)rowptr[n] + 1;
+  wheap_item *h = (wheap_item *)malloc((size_t)cap * sizeof(wheap_item));
+  uint8_t *done = (uint8_t *)calloc((size_t)n, 1);
+  if (!h || !done) { free(h); free(done); return ORC_E_NOMEM; }
+  for (int32_t v = 0; v < n; ++v) dist[v] = INFINITY;
+  int64_t len = 0;
+  dist[s] = 0.0f;
+  wheap_push(h, &len, 0.0f, s);
+  while (len > 0) {
+    wheap_item it = wheap_pop(h, &len);
+    int32_t u = it.v;
+    if (done[u]) continue;
+    done[u] = 1;
+    for (int32_t t = rowptr[u]; t < rowptr[u + 1]; ++t) {
+      int32_t v = colidx[t];
+      float nd = dist[u] + elen[t];
+      if (nd < dist[v]) {
+        dist[v] = nd;
+        wheap_push(h, &len, nd, v);
+      }
+    }
+  }
+  free(h); free(done);
+  return ORC_OK;
+}
+
+/* max/min sp on weighted distances (Section 4.1): as orc_maxmin with one
+ * Dijkstra per pivot; ties to the lowest node id. */
+int orc_wmaxmin(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                int32_t start, int32_t *pivots) {
+  if (k < 1 || k > n || start < 0 || start >= n) return ORC_E_ARG;
+  float *mind = (float *)malloc((size_t)n * sizeof(float));
+  float *d = (float *)malloc((size_t)n * sizeof(float));
+  if (!mind || !d) { free(mind); free(d); return ORC_E_NOMEM; }
+  int rc = orc_sssp(n, rowptr, colidx, elen, start, mind);
+  for (int32_t v = 0; rc == ORC_OK && v < n; ++v)
+    if (isinf(mind[v])) rc = ORC_E_DISCONNECTED;
+  if (rc == ORC_OK) pivots[0] = start;
+  for (int32_t j = 1; rc == ORC_OK && j < k; ++j) {
+    int32_t best = 0;
+    for (int32_t v = 1; v < n; ++v)
+      if (mind[v] > mind[best]) best = v;
+    pivots[j] = best;
+    rc = orc_sssp(n, rowptr, colidx, elen, best, d);
+    for (int32_t v = 0; v < n; ++v)
+      if (d[v] < mind[v]) mind[v] = d[v];
+  }
+  free(mind); free(d);
+  return rc;
+}
+
+/* weighted d_ip, pivot-major [k][n] float32, one Dijkstra per pivot */
+int orc_wpivot_dist(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                    const int32_t *pivots, float *dip) {
+  if (k < 1) return ORC_E_ARG;
+  int rc = ORC_OK;
+  for (int32_t a = 0; rc == ORC_OK && a < k; ++a) {
+    rc = orc_sssp(n, rowptr, colidx, elen, pivots[a], dip + (int64_t)a * n);
+    for (int32_t v = 0; rc == ORC_OK && v < n; ++v)
+      if (isinf(dip[(int64_t)a * n + v])) rc = ORC_E_DISCONNECTED;
+  }
+  return rc;
+}
+
+/* region[i] = the smallest pivot index a minimising d_ia (float32) */
+int orc_wregions(int32_t n, int32_t k, const float *dip, int32_t *region) {
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t best = 0;
+    for (int32_t a = 1; a < k; ++a)
+      if (dip[(int64_t)a * n + i] < dip[(int64_t)best * n + i]) best = a;
+    region[i] = best;
+  }
+  return ORC_OK;
+}
+
+static int row_has(const int32_t *rowptr, const int32_t *colidx, int32_t i, int32_t v) {
+  for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t)
+    if (colidx[t] == v) return 1;
+  return 0;
+}
+
+/* s[a][i] = |{j in R(a) : 2 d_ja <= d_ia}| by direct count (Section 3,
+ * after Eq. 4), for the nodes i0 <= i < i1; 0 where the pivot is i itself
+ * or one of its neighbours (the pivot sum of Eq. 4 runs over P \ N(i) and
+ * skips i). */
+int orc_wcounts_rows(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *pivots,
+                     const float *dip, const int32_t *region, uint32_t *s, int32_t i0, int32_t i1) {
+  if (i0 < 0 || i1 < i0 || i1 > n) return ORC_E_ARG;
+  for (int32_t a = 0; a < k; ++a) {
+    const float *row = dip + (int64_t)a * n;
+    for (int32_t i = i0; i < i1; ++i) {
+      uint32_t c = 0;
+      if (pivots[a] != i && !row_has(rowptr, colidx, i, pivots[a]))
+        for (int32_t j = 0; j < n; ++j)
+          if (region[j] == a && 2.0f * row[j] <= row[i]) ++c;
+      s[(int64_t)a * n + i] = c;
+    }
+  }
+  return ORC_OK;
+}
+
+/* rescale with the weighted target: sum_E ||x_i - x_j|| = sum_E l_ij
+ * (Algorithm 1 line 4; both sums over i < j in CSR order, FP64) */
+int orc_wrescale(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, double *pos) {
+  double len = 0.0, target = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+      int32_t j = colidx[t];
+      if (j <= i) continue;
+      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
+      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
+      len += sqrt(dx * dx + dy * dy);
+      target += (double)elen[t];
+    }
+  if (!(len > 0.0)) return ORC_E_NUMERIC;
+  double sc = target / len;
+  for (int64_t t = 0; t < 2 * (int64_t)n; ++t) pos[t] *= sc;
+  return ORC_OK;
+}
+
+/* Eq. 4 on a weighted graph, node i from X: neighbour terms with
+ * d_ij = l_ij, w_ij = 1 / l_ij^2 (CSR order), then pivot terms a = 0..k-1
+ * with d = d_ia, w' = s_ia / d^2, skipping the pivot when it is i or a
+ * neighbour of i. */
+static void eq4w_update(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                        const int32_t *pivots, const float *dip, const uint32_t *s, const double *X, int32_t i,
+                        double *out) {
+  double xi = X[2 * (int64_t)i], yi = X[2 * (int64_t)i + 1];
+  double nx = 0.0, ny = 0.0, den = 0.0;
+  for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+    int32_t j = colidx[t];
+    double l = (double)elen[t], w = 1.0 / (l * l);
+    double xj = X[2 * (int64_t)j], yj = X[2 * (int64_t)j + 1];
+    double dx = xi - xj, dy = yi - yj;
+    double r = sqrt(dx * dx + dy * dy);
+    if (r > 0.0) { nx += w * (xj + l * dx / r); ny += w * (yj + l * dy / r); }
+    else { nx += w * xj; ny += w * yj; }
+    den += w;
+  }
+  for (int32_t a = 0; a < k; ++a) {
+    int32_t p = pivots[a];
+    if (p == i || row_has(rowptr, colidx, i, p)) continue;
+    double d = (double)dip[(int64_t)a * n + i];
+    double wa = (double)s[(int64_t)a * n + i] / (d * d);
+    double xp = X[2 * (int64_t)p], yp = X[2 * (int64_t)p + 1];
+    double dx = xi - xp, dy = yi - yp;
+    double r = sqrt(dx * dx + dy * dy);
+    if (r > 0.0) { nx += wa * (xp + d * dx / r); ny += wa * (yp + d * dy / r); }
+    else { nx += wa * xp; ny += wa * yp; }
+    den += wa;
+  }
+  if (den > 0.0) { out[0] = nx / den; out[1] = ny / den; }
+  else { out[0] = xi; out[1] = yi; }
+}
+
+int orc_wsweep_jacobi_rows(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                           const int32_t *pivots, const float *dip, const uint32_t *s, const double *pos_in,
+                           double *pos_out, int32_t i0, int32_t i1) {
+  if (i0 < 0 || i1 < i0 || i1 > n) return ORC_E_ARG;
+  for (int32_t i = i0; i < i1; ++i)
+    eq4w_update(n, rowptr, colidx, elen, k, pivots, dip, s, pos_in, i, pos_out + 2 * (int64_t)i);
+  return ORC_OK;
+}
+
+/* full stress (Eq. 1) with weighted distances: exhaustive (S == 0, a
+ * Dijkstra from every node, pairs i < j) or over the S*T pairs of
+ * orc_sample_pairs; out and sums as in orc_full_stress. */
+int orc_wfull_stress(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen,
+                     const double *pos, int32_t S, int32_t T, uint64_t seed, double *out, double *sums) {
+  if (n < 2 || S < 0 || (S > 0 && T < 1)) return ORC_E_ARG;
+  float *dist = (float *)malloc((size_t)n * sizeof(float));
+  int32_t *srcs = NULL, *tgts = NULL;
+  if (!dist) return ORC_E_NOMEM;
+  if (S > 0) {
+    srcs = (int32_t *)malloc((size_t)S * sizeof(int32_t));
+    tgts = (int32_t *)malloc((size_t)S * T * sizeof(int32_t));
+    if (!srcs || !tgts) { free(dist); free(srcs); free(tgts); return ORC_E_NOMEM; }
+    orc_sample_pairs(n, S, T, seed, srcs, tgts);
+  }
+  double raw = 0.0, s1 = 0.0, s2 = 0.0, np = 0.0;
+  int rc = ORC_OK;
+  int32_t nsrc = S > 0 ? S : n;
+  for (int32_t q = 0; rc == ORC_OK && q < nsrc; ++q) {
+    int32_t i = S > 0 ? srcs[q] : q;
+    rc = orc_sssp(n, rowptr, colidx, elen, i, dist);
+    int32_t cnt = S > 0 ? T : n;
+    for (int32_t l = 0; rc == ORC_OK && l < cnt; ++l) {
+      int32_t j = S > 0 ? tgts[(int64_t)q * T + l] : l;
+      if (S == 0 && j <= i) continue;
+      if (isinf(dist[j])) { rc = ORC_E_DISCONNECTED; break; }
+      double d = (double)dist[j];
+      double dx = pos[2 * (int64_t)i] - pos[2 * (int64_t)j];
+      double dy = pos[2 * (int64_t)i + 1] - pos[2 * (int64_t)j + 1];
+      double r = sqrt(dx * dx + dy * dy);
+      raw += (r - d) * (r - d) / (d * d);
+      s1 += r / d;
+      s2 += r * r / (d * d);
+      np += 1.0;
+    }
+  }
+  free(dist); free(srcs); free(tgts);
+  if (rc != ORC_OK) return rc;
+  double pairs = 0.5 * (double)n * (double)(n - 1);
+  double f = S > 0 ? pairs / np : 1.0;
+  if (sums) { sums[0] = raw; sums[1] = s1; sums[2] = s2; sums[3] = np; }
+  out[0] = raw * f;
+  out[1] = s2 > 0.0 ? s1 / s2 : 0.0;
+  out[2] = (s2 > 0.0 ? np - s1 * s1 / s2 : np) * f;
+  out[3] = out[2] / pairs;
+  return ORC_OK;
 }

@@ -64,6 +64,9 @@ def _load():
             lib.gen_random_btree.argtypes = [ctypes.c_int32, ctypes.c_uint64, i32p, i64p, i32pp, i32pp]
             lib.gen_rgg.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                     i32p, i64p, i32pp, i32pp]
+            lib.gen_rgg_lengths.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                            i32p, i64p, i32pp, i32pp,
+                                            ctypes.POINTER(ctypes.POINTER(ctypes.c_float))]
             lib.gen_ba.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, i32p, i64p, i32pp, i32pp]
             lib.gen_induced_prefix.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p, i32pp, i32pp]
             _lib = lib
@@ -106,6 +109,41 @@ def random_btree(n: int, seed: int):
 
 def rgg(n: int, mean_deg: float, seed: int, radius: float = 0.0):
     return _call(_load().gen_rgg, n, mean_deg, radius, ctypes.c_uint64(seed))
+
+
+def rgg_lengths(n: int, mean_deg: float, seed: int, radius: float = 0.0):
+    """The graph of rgg(n, mean_deg, seed, radius) with float32 edge lengths
+    (Euclidean length / radius): returns (n, src, dst, len)."""
+    lib = _load()
+    nn = ctypes.c_int32(0)
+    m = ctypes.c_int64(0)
+    s = ctypes.POINTER(ctypes.c_int32)()
+    d = ctypes.POINTER(ctypes.c_int32)()
+    ln = ctypes.POINTER(ctypes.c_float)()
+    rc = lib.gen_rgg_lengths(n, mean_deg, radius, ctypes.c_uint64(seed), ctypes.byref(nn), ctypes.byref(m),
+                             ctypes.byref(s), ctypes.byref(d), ctypes.byref(ln))
+    if rc != 0:
+        raise ValueError(f"generator failed with status {rc}")
+    try:
+        mm = max(m.value, 1)
+        src = np.ctypeslib.as_array(s, shape=(mm,))[: m.value].copy()
+        dst = np.ctypeslib.as_array(d, shape=(mm,))[: m.value].copy()
+        lens = np.ctypeslib.as_array(ln, shape=(mm,))[: m.value].copy()
+    finally:
+        for ptr in (s, d, ln):
+            lib.gen_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return int(nn.value), src, dst, lens
+
+
+def random_lengths(m: int, seed: int, kind: str = "uniform", lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
+    """Seeded float32 edge lengths: "uniform" in [lo, hi), or "integer" in
+    {1, ..., int(hi)} (sums stay exact in float32 on small graphs)."""
+    rng = np.random.default_rng(seed)
+    if kind == "uniform":
+        return rng.uniform(lo, hi, size=m).astype(np.float32)
+    if kind == "integer":
+        return rng.integers(1, int(hi) + 1, size=m).astype(np.float32)
+    raise ValueError(f"unknown length kind {kind!r}")
 
 
 def ba(n: int, attach: int, seed: int):

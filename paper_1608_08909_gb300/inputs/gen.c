@@ -6,7 +6,8 @@
  * tree), which are not available here.  Every generator returns an
  * undirected edge list (src[e], dst[e]) over nodes 0..n-1 and holds none of
  * the layout method's arithmetic: no distances, weights or positions of the
- * method are computed here.  Both the CUDA path and the CPU oracle consume
+ * method are computed here (the edge lengths of gen_rgg_lengths are input
+ * data, the Euclidean lengths of the generated points' edges).  Both the CUDA path and the CPU oracle consume
  * these edge lists, so this file is the only code the two sides share.
  *
  * Random numbers come from splitmix64 (Steele, Lea and Flood, "Fast
@@ -119,7 +120,7 @@ static int32_t uf_find(int32_t *par, int32_t x) {
 
 /* keeps the largest component (ties: the one holding the smallest node id),
  * relabels its nodes in increasing original id, rewrites the edge list in place */
-static int keep_lcc(int32_t n, int64_t *m, int32_t *src, int32_t *dst, int32_t *n_out) {
+static int keep_lcc(int32_t n, int64_t *m, int32_t *src, int32_t *dst, float *len, int32_t *n_out) {
   int32_t *par = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int32_t *size = (int32_t *)calloc((size_t)n, sizeof(int32_t));
   if (!par || !size) { free(par); free(size); return -2; }
@@ -137,7 +138,12 @@ static int keep_lcc(int32_t n, int64_t *m, int32_t *src, int32_t *dst, int32_t *
   for (int32_t i = 0; i < n; ++i) lab[i] = (uf_find(par, i) == best) ? nn++ : -1;
   int64_t mm = 0;
   for (int64_t e = 0; e < *m; ++e) {
-    if (lab[src[e]] >= 0) { src[mm] = lab[src[e]]; dst[mm] = lab[dst[e]]; ++mm; }
+    if (lab[src[e]] >= 0) {
+      src[mm] = lab[src[e]];
+      dst[mm] = lab[dst[e]];
+      if (len) len[mm] = len[e];
+      ++mm;
+    }
   }
   free(par); free(size);
   *m = mm; *n_out = nn;
@@ -147,8 +153,8 @@ static int keep_lcc(int32_t n, int64_t *m, int32_t *src, int32_t *dst, int32_t *
 /* random geometric graph: n points uniform in the unit square, an edge for
  * every pair at Euclidean distance < radius (radius = sqrt(mean_deg/(pi n))
  * when radius <= 0), built with a bucket grid; the largest component is kept. */
-int gen_rgg(int32_t n, double mean_deg, double radius, uint64_t seed,
-            int32_t *n_out, int64_t *m_out, int32_t **src, int32_t **dst) {
+static int rgg_impl(int32_t n, double mean_deg, double radius, uint64_t seed,
+                    int32_t *n_out, int64_t *m_out, int32_t **src, int32_t **dst, float **len) {
   if (n < 2) return -1;
   if (radius <= 0) radius = sqrt(mean_deg / (3.14159265358979323846 * (double)n));
   double *px = (double *)malloc((size_t)n * sizeof(double));
@@ -196,25 +202,54 @@ int gen_rgg(int32_t n, double mean_deg, double radius, uint64_t seed,
             if (j <= i) continue;
             double ddx = px[i] - px[j], ddy = py[i] - py[j];
             if (ddx * ddx + ddy * ddy < r2) {
-              if (pass == 1) { (*src)[e] = i; (*dst)[e] = j; }
+              if (pass == 1) {
+                (*src)[e] = i;
+                (*dst)[e] = j;
+                if (len) (*len)[e] = (float)(sqrt(ddx * ddx + ddy * ddy) / radius);
+              }
               ++e;
             }
           }
         }
     }
-    if (pass == 0) { cap = e; if (alloc_edges(cap, src, dst)) goto fail; }
+    if (pass == 0) {
+      cap = e;
+      if (alloc_edges(cap, src, dst)) goto fail;
+      if (len) {
+        *len = (float *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(float));
+        if (!*len) { gen_free(*src); gen_free(*dst); goto fail; }
+      }
+    }
   }
   free(px); free(py); free(head); free(order); free(cellof);
   px = py = NULL;
   {
     int64_t m = cap;
-    if (keep_lcc(n, &m, *src, *dst, n_out)) { gen_free(*src); gen_free(*dst); return -2; }
+    if (keep_lcc(n, &m, *src, *dst, len ? *len : NULL, n_out)) {
+      gen_free(*src);
+      gen_free(*dst);
+      if (len) gen_free(*len);
+      return -2;
+    }
     *m_out = m;
   }
   return 0;
 fail:
   free(px); free(py); free(head); free(order); free(cellof);
   return -2;
+}
+
+int gen_rgg(int32_t n, double mean_deg, double radius, uint64_t seed,
+            int32_t *n_out, int64_t *m_out, int32_t **src, int32_t **dst) {
+  return rgg_impl(n, mean_deg, radius, seed, n_out, m_out, src, dst, NULL);
+}
+
+/* the same graph with edge lengths: the Euclidean length of each edge divided
+ * by the radius, as float (in (0, 1); a geometric stand-in for the paper's
+ * weighted inputs); the lengths are released with gen_free */
+int gen_rgg_lengths(int32_t n, double mean_deg, double radius, uint64_t seed,
+                    int32_t *n_out, int64_t *m_out, int32_t **src, int32_t **dst, float **len) {
+  return rgg_impl(n, mean_deg, radius, seed, n_out, m_out, src, dst, len);
 }
 
 /* Barabasi-Albert preferential attachment: a (m0)-clique seed with

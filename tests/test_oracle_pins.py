@@ -675,3 +675,146 @@ def test_regions_smallest_is_a_nearest_pivot_partition(seed):
         assert reg[p] == a
     single = (dip == m).sum(0) == 1
     assert np.array_equal(reg[single], low[single])
+
+
+# ---------------------------------------------------------------- Procrustes statistic (Section 4)
+
+def test_procrustes_similarity_transform_is_a_perfect_match():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(200, 2))
+    th, sc, t = 0.7, 2.5, np.array([3.0, -1.0])
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    Y = sc * X @ R.T + t
+    P, s, a = O.procrustes(X, Y)
+    assert abs(P) < 1e-14
+    assert s == pytest.approx(sc, rel=1e-13)
+    assert a == pytest.approx(th, rel=1e-13)
+
+
+def test_procrustes_matches_the_library_for_proper_rotations():
+    """scipy.spatial.procrustes fits an orthogonal map (reflections allowed):
+    where the best orthogonal fit is a rotation its disparity equals P; for a
+    mirror image scipy finds a perfect fit and P does not (the paper notes
+    that its Procrustes analysis cannot resolve reflections)."""
+    sp_proc = pytest.importorskip("scipy.spatial").procrustes
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(150, 2))
+    Y = X @ np.array([[0.6, -0.8], [0.8, 0.6]]).T + 0.3 * rng.normal(size=(150, 2))
+    _, _, disp = sp_proc(X, Y)
+    assert O.procrustes(X, Y)[0] == pytest.approx(disp, rel=1e-12)
+    M = X * np.array([1.0, -1.0])
+    _, _, disp = sp_proc(X, M)
+    assert disp < 1e-14
+    assert O.procrustes(X, M)[0] > 0.1
+
+
+def test_procrustes_range():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        X, Y = rng.normal(size=(80, 2)), rng.normal(size=(80, 2))
+        P = O.procrustes(X, Y)[0]
+        assert 0.0 <= P <= 1.0
+
+
+# ---------------------------------------------------------------- convex-hull error (Section 4, Fig. 4)
+
+def test_hull_error_against_library_hull():
+    """The per-node counts of the oracle against scipy's ConvexHull (Qhull) and
+    matplotlib-free point-in-polygon by Delaunay.find_simplex on random layouts
+    in general position (no three points collinear with probability 1)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(12)
+    n, s, d = I.rgg(120, 7.0, 5)
+    g = O.build_csr(n, s, d)
+    D = O.apsp(g)
+    x = rng.normal(size=(n, 2))
+    for kh in (1, 2, 4):
+        mean, per = O.hull_error(D, x, kh)
+        want = np.zeros(n)
+        for v in range(n):
+            ball = np.nonzero(D[v] <= kh)[0]
+            out = np.nonzero(D[v] > kh)[0]
+            if len(out) == 0:
+                continue
+            if len(ball) >= 3:
+                tri = spatial.Delaunay(x[ball])
+                inside = tri.find_simplex(x[out]) >= 0
+            else:
+                inside = np.zeros(len(out), bool)  # a point or a segment holds no other random point
+            want[v] = inside.sum() / len(out)
+        np.testing.assert_allclose(per, want, atol=0)
+        assert mean == pytest.approx(want.mean(), rel=1e-12)
+
+
+def test_hull_error_closed_forms():
+    """A 5 x 5 grid drawn at its integer coordinates, radius 1: the ball of an
+    interior node is a plus sign whose hull (a diamond) holds no other grid
+    point, so every error is 0; radius 2 for the centre node: the diamond
+    |dx| + |dy| <= 2 holds exactly the ball.  A layout that stacks every
+    node on one point puts every other node on the hull: error 1."""
+    n, s, d = I.grid(5, 5)
+    D = O.apsp(O.build_csr(n, s, d))
+    r, c = np.divmod(np.arange(n), 5)
+    x = np.stack([c, r], 1).astype(np.float64)
+    mean, per = O.hull_error(D, x, 1)
+    assert mean == 0.0
+    _, per2 = O.hull_error(D, x, 2)
+    assert per2[12] == 0.0
+    mean, per = O.hull_error(D, np.zeros((n, 2)), 1)
+    assert (per == 1.0).all()
+
+
+# ---------------------------------------------------------------- Gabriel graph similarity (Section 4, Fig. 3)
+
+def test_gabriel_graph_is_the_delaunay_subgraph_of_empty_diameter_discs():
+    """Library pin: the Gabriel graph is the set of Delaunay edges (scipy,
+    Qhull) whose diameter disc holds no other point; on random points in
+    general position the oracle's brute-force definition gives exactly that."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(3)
+    x = rng.random((150, 2))
+    adj = O.gabriel(x)
+    tri = spatial.Delaunay(x)
+    want = np.zeros_like(adj)
+    tree = spatial.cKDTree(x)
+    for simplex in tri.simplices:
+        for a, b in ((0, 1), (1, 2), (0, 2)):
+            u, v = simplex[a], simplex[b]
+            m = (x[u] + x[v]) / 2
+            r = np.linalg.norm(x[u] - x[v]) / 2
+            inside = [w for w in tree.query_ball_point(m, r * (1 - 1e-12)) if w not in (u, v)]
+            if not inside:
+                want[u, v] = want[v, u] = 1
+    assert np.array_equal(adj, want)
+
+
+def test_gabriel_special_cases():
+    """A square's corners: the other two corners lie on the diagonals'
+    diameter circles, not inside, so under the open-disc reading all six pairs
+    are Gabriel edges; identical positions are adjacent; a point at a
+    segment's midpoint blocks it."""
+    sq = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    adj = O.gabriel(sq)
+    assert adj.sum() == 12  # all 6 pairs: the diagonals' circles pass through the other corners
+    line = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]])
+    assert O.gabriel(line).tolist() == [[0, 1, 0], [1, 0, 1], [0, 1, 0]]
+    dup = np.array([[0.0, 0.0], [0.0, 0.0], [5.0, 5.0], [0.1, 4.9]])
+    assert O.gabriel(dup)[0, 1] == 1
+
+
+def test_gabriel_jaccard_identity_and_disjoint():
+    rng = np.random.default_rng(8)
+    x = rng.random((60, 2))
+    mean, per = O.gabriel_jaccard(x, x, 2)
+    assert mean == 1.0 and (per == 1.0).all()
+    # a layout and its copy rotated by 90 degrees have the same Gabriel graph
+    mean, _ = O.gabriel_jaccard(x, x[:, ::-1] * np.array([-1.0, 1.0]), 3)
+    assert mean == 1.0
+    # two layouts whose Gabriel graphs share no edge at radius 1
+    line = np.stack([np.arange(6.0), np.zeros(6)], 1)
+    perm = np.array([0, 2, 4, 1, 3, 5])
+    mean, per = O.gabriel_jaccard(line, line[np.argsort(perm)], 1)
+    adjA, adjB = O.gabriel(line), O.gabriel(line[np.argsort(perm)])
+    for v in range(6):
+        a, b = set(np.nonzero(adjA[v])[0]), set(np.nonzero(adjB[v])[0])
+        assert per[v] == pytest.approx(len(a & b) / len(a | b))
