@@ -288,6 +288,10 @@ def run_gpu(args):
                   "int_mac_per_s": macs / (km_ms * 1e-3), "moved_pivots": int((newp != P.pivots).sum().item()),
                   "note": "exact 64-bit integer dot products of the assignment (n k^2 per pass) on CUDA cores"}
 
+    weighted = None
+    if not args.no_weighted:
+        weighted = weighted_section(dev, stream, flush)
+
     # roofline of the sweep kernel (one launch = one Jacobi iteration)
     peak, peak_kind = _peaks()
     bytes_per_launch = 2 * k * n + 4 * (n + 1) + 8 * m + 8 * n + 8 * n
@@ -334,6 +338,7 @@ def run_gpu(args):
         "clocks": clocks,
         "fp64_sweep": fp64,
         "kmeans_sp": kmeans,
+        "weighted": weighted,
         "e2e": {"value": e2e_value, "unit": "node-term updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
         "gpu_launches": timed_launches,
@@ -351,6 +356,67 @@ def run_gpu(args):
 
 PMDS_SAMPLE_N = 16384     # PivotMDS of the oracle is timed on this many nodes of the full d_ip table
 SWEEP_SAMPLE = 2          # Jacobi sweeps of the oracle timed on all host threads (of the workload's iters)
+
+
+def weighted_section(dev, stream, flush, n0=262144, k=200, iters=100, reps=3):
+    """The whole path on a weighted graph (Algorithm 1 line 2's weighted
+    MSSP): a random geometric graph with Euclidean edge lengths (n0 points,
+    mean degree 8, largest component), k max/min pivots on weighted
+    distances, 100 FP32 sweeps, stress on 1024 x 1024 sampled pairs.  Stage
+    times are CUDA-event means over `reps` runs after one warm-up, L2 flushed
+    before each; the sweep's roofline uses its algorithmic bytes per
+    iteration: 4kn (distances) + 4kn (counts s) + 4(n+1) + 8m (colidx) + 8m
+    (lengths) + 8n (read X) + 8n (write X)."""
+    import torch
+
+    import paper_1608_08909_gb300 as ssm
+    from paper_1608_08909_gb300 import inputs as I
+
+    n, src, dst, ln = I.rgg_lengths(n0, 8.0, 21)
+    s_d = torch.from_numpy(src).to(dev)
+    d_d = torch.from_numpy(dst).to(dev)
+    l_d = torch.from_numpy(ln).to(dev)
+    names = ["graph", "pivots", "sssp", "counts", "pivotmds", "sweeps", "stress"]
+
+    def run(ev=None):
+        mark = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        mark(0)
+        g = ssm.ssm_build_wgraph(n, s_d, d_d, l_d, check=False)
+        mark(1)
+        piv = ssm.ssm_select_pivots_weighted(g, k, 0, check=False)
+        mark(2)
+        dist_t = ssm.ssm_pivot_sssp(g, piv, check=False)
+        mark(3)
+        _, s_tab = ssm.ssm_weighted_counts(g, piv, dist_t, check=False)
+        mark(4)
+        pos, _ = ssm.ssm_pivotmds_weighted(g, dist_t, 32, True, check=False)
+        mark(5)
+        ssm.ssm_iterate_weighted(g, piv, dist_t, s_tab, pos, iters, check=False)
+        mark(6)
+        out, _ = ssm.ssm_stress_weighted(g, pos, 1024, 1024, 7, check=False)
+        mark(7)
+        return g, out
+
+    g, out = run()
+    torch.cuda.synchronize()
+    ms = {st: 0.0 for st in names}
+    for _ in range(reps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        g, out = run(ev)
+        torch.cuda.synchronize()
+        for i, st in enumerate(names):
+            ms[st] += ev[i].elapsed_time(ev[i + 1]) / reps
+    m = g.m
+    it_s = ms["sweeps"] / 1e3 / iters
+    bytes_it = 8 * k * n + 4 * (n + 1) + 16 * m + 16 * n
+    peak, peak_kind = _peaks()
+    return {"graph": f"random geometric, Euclidean edge lengths, n={n}, m={m}", "k": k, "iters": iters,
+            "stage_ms": {st: round(v, 3) for st, v in ms.items()}, "step_ms": round(sum(ms.values()), 3),
+            "node_term_updates_per_s": iters * (k * n + 2 * m) / (ms["sweeps"] / 1e3),
+            "sweep_us_per_iteration": round(it_s * 1e6, 2), "sweep_algorithmic_bytes": bytes_it,
+            "sweep_hbm_frac": round(bytes_it / it_s / 1e9 / peak, 4), "peak_kind": peak_kind,
+            "stress_normalized": float(out.cpu()[3])}
 
 
 def _cpu_model() -> str:
@@ -530,6 +596,7 @@ def run_serve(args):
                                "node_term_updates_per_s": round(sum(terms) / (t3 - t2), 1),
                                "peak_concurrent": srv.peak_active})
         peak_reserved = srv.peak_reserved
+        waits = {"for_budget": srv.waited_for_budget, "for_slot": srv.waited_for_slot}
     ns = np.array([j.n for j in jobs])
     top = levels[-1] if levels else None
     line = {
@@ -544,6 +611,7 @@ def run_serve(args):
         "levels": levels,
         "p50_ms": top["p50_ms"] if top else None, "p99_ms": top["p99_ms"] if top else None,
         "peak_reserved_gb": round(peak_reserved / (1 << 30), 3),
+        "head_of_queue_waits": waits,
         "gpu_launches": ssm.kernel_launches() - launches0,
         "clocks": clk.summary(),
         "vs_baseline": None,
@@ -649,6 +717,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
     ap.add_argument("--no-kmeans", action="store_true", help="skip the k-means sp sampler timing")
+    ap.add_argument("--no-weighted", action="store_true", help="skip the weighted-graph pipeline timing")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead of a single graph")
     ap.add_argument("--batch", action="store_true", help="run the batching workload (many small graphs, one launch)")
     ap.add_argument("--batch-graphs", type=int, default=4096)

@@ -360,6 +360,114 @@ int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const int32_t *r
                       int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
+ * Layout quality measures (Section 4).
+ * ssm_procrustes: the Procrustes statistic (Sibson 1978) of layouts X and Y
+ * of the same n nodes (precision 32: float[2n], 64: double[2n]): both
+ * centred, Y fitted by a uniform scale and a proper rotation (the paper
+ * notes that its analysis cannot resolve reflections):
+ *   P = 1 - T^2 / (||Xc||^2 ||Yc||^2),  T = sqrt((m11 + m22)^2 + (m12 - m21)^2),
+ *   m_ab = sum_i xc_ia yc_ib;  P in [0, 1], 0 for a perfect match.
+ * out[3] (device double) = {P, scale, angle} with Y ~ scale R(angle) X +
+ * translation.  One block, FP64 sums in a fixed order; no workspace.
+ * ssm_hull_error: the convex-hull error of Fig. 4 for hop radius kh: for
+ * every node v, B = {w : d_vw <= kh} from the all-pairs table D[n*n], H the
+ * convex hull of B's positions, err_v = |{u not in B : x_u inside or on H}|
+ * / (n - |B|) (0 when B holds every node); per_node[n] (device double, may
+ * be NULL) and *mean (device double, the mean in node order).  Hull and
+ * inside tests use FP64 orientation tests.  A ball whose points outside the
+ * quadrilateral of its four extreme points number above 4096 is reported
+ * as SSM_E_ARG (err_v = -1).  Workspace ssm_hull_error_workspace(n).
+ * ssm_gabriel_jaccard: the Gabriel-graph comparison of Section 4: the
+ * Gabriel graphs of layouts A and B (u ~ v iff no third point lies strictly
+ * inside the disc with diameter uv, tested as |2w - a - b|^2 < |a - b|^2 in
+ * FP64 with a the lower id, so identical positions are adjacent), then for
+ * every node v the Jaccard coefficient |N_A ^ N_B| / |N_A u N_B| of the
+ * node sets within kh >= 1 hops of v in each graph (v excluded; 1 when both
+ * are empty); per_node[n] (may be NULL) and *mean (device doubles, the mean
+ * in node order).  Limits, reported as SSM_E_ARG in *status: 256 Gabriel
+ * neighbours per node (identical positions form cliques), 512 points met
+ * while bounding one node's neighbour region on the grid, 512 nodes in one
+ * kh-neighbourhood.  Workspace ssm_gabriel_jaccard_workspace(n) (about 6 KB
+ * per node).
+ * ------------------------------------------------------------------- */
+int ssm_procrustes(int32_t n, const void *X, const void *Y, int32_t precision, double *out, cudaStream_t stream);
+size_t ssm_hull_error_workspace(int32_t n);
+int ssm_hull_error(int32_t n, const uint16_t *D, const void *pos, int32_t precision, int32_t kh, double *per_node,
+                   double *mean, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t ssm_gabriel_jaccard_workspace(int32_t n);
+int ssm_gabriel_jaccard(int32_t n, const void *posA, const void *posB, int32_t precision, int32_t kh,
+                        double *per_node, double *mean, int32_t *status, void *ws, size_t ws_bytes,
+                        cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Weighted graphs (Algorithm 1 line 2: weighted MSSP; Section 3's weights
+ * with general edge lengths).  Edge lengths are float32, finite, at least
+ * FLT_MIN, with n * (largest length) < 1e37.  A distance d_ij is the least
+ * float32 path sum: along a path walked from the source, each edge's length
+ * is added to the running sum and rounded to float32; d_ij is the minimum
+ * over paths (any correct search reaches this value, so it is exact and
+ * reproducible).  Tables of distances are float32, pivot-major [k][n].
+ *
+ * ssm_edge_lengths: elen[2m] for the CSR (rowptr, colidx) that
+ *   ssm_build_graph made from the same edge list src/dst[m_in] with lengths
+ *   len[m_in]: elen[t] is the length of edge (i, colidx[t]); a repeated edge
+ *   keeps its shortest length.  Bad lengths: SSM_E_ARG; an edge missing
+ *   from the CSR: SSM_E_GRAPH (both in *status).  Workspace 256 bytes.
+ * ssm_pivot_sssp: dist[a*n + v] = d(sources[a], v) for a < k (one
+ *   label-correcting search per source, a block per source); an unreachable
+ *   node gives SSM_E_DISCONNECTED.  Workspace ssm_pivot_sssp_workspace(n, k).
+ * ssm_select_pivots_weighted: max/min sp (Section 4.1) on weighted
+ *   distances: pivots[0] = start, then the node farthest from the pivots so
+ *   far (ties to the lowest id), each search pruned to the nodes the new
+ *   pivot is strictly closer to.  Workspace ..._workspace(n, k).
+ * ssm_weighted_counts: region[i] = the lowest pivot index a minimising
+ *   d_ia; s_tab[a*n + i] = |{j in R(a) : 2 d_ja <= d_ia}| (float32 test),
+ *   0 where pivots[a] is i or a neighbour of i (the pivot sum of Eq. 4 runs
+ *   over P \ N(i)).  The adapted weight is w'_ia = s / d_ia^2.  Workspace
+ *   ssm_weighted_counts_workspace(n, k) (a sort of n 64-bit keys).
+ * ssm_pivotmds_weighted: as ssm_pivotmds from the float32 table
+ *   (delta = d^2 in FP64; C^T C from column-centred FP64 sums), rescaled so
+ *   that sum_E ||x_i - x_j|| = sum_E l_ij when rescale != 0.
+ * ssm_iterate_weighted: `iters` Jacobi updates of Eq. 4 with
+ *   w_ij = l_ij^-2, d_ij = l_ij on the edges and w'_ia = s_ia / d_ia^2 on
+ *   the pivots (skipped where s_ia = 0), in place on pos (float2 or
+ *   double2 by precision; FP64 rounds every operation as written, in the
+ *   order of the plain definition); *rel_change (device double) receives
+ *   ||X^{t+1} - X^t||_F / ||X^t||_F of the last update.
+ *   Workspace ssm_iterate_weighted_workspace(n, precision).
+ * ssm_stress_weighted: ssm_stress with weighted distances (exhaustive when
+ *   nsources == 0, else the same sampled pair list).
+ * ------------------------------------------------------------------- */
+int ssm_edge_lengths(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst, const float *len, int64_t m,
+                     const int32_t *rowptr, const int32_t *colidx, float *elen, int32_t *status, void *ws,
+                     size_t ws_bytes, cudaStream_t stream);
+size_t ssm_pivot_sssp_workspace(int32_t n, int32_t k);
+int ssm_pivot_sssp(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                   const int32_t *sources, float *dist, int32_t *status, void *ws, size_t ws_bytes,
+                   cudaStream_t stream);
+size_t ssm_select_pivots_weighted_workspace(int32_t n, int32_t k);
+int ssm_select_pivots_weighted(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, const float *elen,
+                               int32_t k, int32_t start, int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes,
+                               cudaStream_t stream);
+size_t ssm_weighted_counts_workspace(int32_t n, int32_t k);
+int ssm_weighted_counts(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *pivots,
+                        const float *dist, int32_t *region, uint32_t *s_tab, int32_t *status, void *ws,
+                        size_t ws_bytes, cudaStream_t stream);
+size_t ssm_pivotmds_weighted_workspace(int32_t n, int32_t k);
+int ssm_pivotmds_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                          const float *dist, void *pos, int32_t precision, int32_t rescale, double *eig,
+                          int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t ssm_iterate_weighted_workspace(int32_t n, int32_t precision);
+int ssm_iterate_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
+                         const int32_t *pivots, const float *dist, const uint32_t *s_tab, void *pos,
+                         int32_t precision, int32_t iters, double *rel_change, int32_t *status, void *ws,
+                         size_t ws_bytes, cudaStream_t stream);
+size_t ssm_stress_weighted_workspace(int32_t n, int32_t nsources);
+int ssm_stress_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, const void *pos,
+                        int32_t precision, int32_t nsources, int32_t ntargets, uint64_t seed, double *out,
+                        double *sums, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------
  * Full stress of a layout (Eq. 1, w_ij = d_ij^-2) with optimal scaling
  * (Section 4: drawings are rescaled to their lowest stress).
  * nsources == 0: exhaustive over all pairs i < j (a BFS from every node).

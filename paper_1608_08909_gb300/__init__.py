@@ -24,7 +24,9 @@ __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
     "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
     "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
-    "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions",
+    "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions", "ssm_procrustes", "ssm_hull_error", "ssm_gabriel_jaccard",
+    "WGraph", "ssm_build_wgraph", "ssm_pivot_sssp", "ssm_select_pivots_weighted", "ssm_weighted_counts",
+    "ssm_pivotmds_weighted", "ssm_iterate_weighted", "ssm_stress_weighted", "layout_weighted",
 ]
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "edge endpoint out of range", -3: "graph is disconnected",
@@ -88,6 +90,24 @@ def lib():
                 "ssm_iterate_gs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, v, i32, v, v, v, sz, v]),
                 "ssm_full_iterate_workspace": (sz, [i32, i32]),
                 "ssm_full_iterate": (ctypes.c_int, [i32, v, v, i32, i32, i32, v, v, v, sz, v]),
+                "ssm_procrustes": (ctypes.c_int, [i32, v, v, i32, v, v]),
+                "ssm_hull_error_workspace": (sz, [i32]),
+                "ssm_hull_error": (ctypes.c_int, [i32, v, v, i32, i32, v, v, v, v, sz, v]),
+                "ssm_gabriel_jaccard_workspace": (sz, [i32]),
+                "ssm_gabriel_jaccard": (ctypes.c_int, [i32, v, v, i32, i32, v, v, v, v, sz, v]),
+                "ssm_edge_lengths": (ctypes.c_int, [i32, i64, v, v, v, i64, v, v, v, v, v, sz, v]),
+                "ssm_pivot_sssp_workspace": (sz, [i32, i32]),
+                "ssm_pivot_sssp": (ctypes.c_int, [i32, i64, v, v, v, i32, v, v, v, v, sz, v]),
+                "ssm_select_pivots_weighted_workspace": (sz, [i32, i32]),
+                "ssm_select_pivots_weighted": (ctypes.c_int, [i32, i64, v, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_weighted_counts_workspace": (sz, [i32, i32]),
+                "ssm_weighted_counts": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, v, v, sz, v]),
+                "ssm_pivotmds_weighted_workspace": (sz, [i32, i32]),
+                "ssm_pivotmds_weighted": (ctypes.c_int, [i32, v, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_iterate_weighted_workspace": (sz, [i32, i32]),
+                "ssm_iterate_weighted": (ctypes.c_int, [i32, v, v, v, i32, v, v, v, v, i32, i32, v, v, v, sz, v]),
+                "ssm_stress_weighted_workspace": (sz, [i32, i32]),
+                "ssm_stress_weighted": (ctypes.c_int, [i32, v, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
                 "ssm_stress_workspace": (sz, [i32, i64, i32, i32]),
                 "ssm_stress": (ctypes.c_int, [i32, i64, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
             }
@@ -412,6 +432,54 @@ def ssm_full_iterate(D: torch.Tensor, pos: torch.Tensor, iters: int, order: int 
     return rel
 
 
+def ssm_procrustes(X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
+    """Procrustes statistic of two layouts [n, 2] (same dtype): device float64
+    tensor {P, scale, angle}."""
+    if X.dtype != Y.dtype or X.shape != Y.shape:
+        raise ValueError("layouts must have the same shape and dtype")
+    out = torch.zeros(3, dtype=torch.float64, device=X.device)
+    precision = 64 if X.dtype == torch.float64 else 32
+    _rc(lib().ssm_procrustes(X.shape[0], _ptr(X.contiguous()), _ptr(Y.contiguous()), precision, _ptr(out),
+                             _stream(stream)), "ssm_procrustes")
+    return out
+
+
+def ssm_hull_error(D: torch.Tensor, pos: torch.Tensor, kh: int, stream=None, check: bool = True):
+    """Convex-hull error of Fig. 4: returns (mean, per-node errors) as device float64 tensors."""
+    L = lib()
+    n = D.shape[0]
+    dev = pos.device
+    per = torch.empty(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_hull_error_workspace(n), dev)
+    precision = 64 if pos.dtype == torch.float64 else 32
+    _rc(L.ssm_hull_error(n, _ptr(D), _ptr(pos.contiguous()), precision, kh, _ptr(per), _ptr(mean), _ptr(st), _ptr(ws),
+                         ws.numel(), _stream(stream)), "ssm_hull_error")
+    if check:
+        ssm_check(st, "ssm_hull_error", stream)
+    return mean, per
+
+
+def ssm_gabriel_jaccard(posA: torch.Tensor, posB: torch.Tensor, kh: int, stream=None, check: bool = True):
+    """Gabriel-graph Jaccard comparison of two layouts (Section 4): returns (mean, per-node) float64 tensors."""
+    L = lib()
+    n = posA.shape[0]
+    if posB.shape != posA.shape or posB.dtype != posA.dtype:
+        raise ValueError("ssm_gabriel_jaccard: layouts differ in shape or dtype")
+    dev = posA.device
+    per = torch.empty(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_gabriel_jaccard_workspace(n), dev)
+    precision = 64 if posA.dtype == torch.float64 else 32
+    _rc(L.ssm_gabriel_jaccard(n, _ptr(posA.contiguous()), _ptr(posB.contiguous()), precision, kh, _ptr(per),
+                              _ptr(mean), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_gabriel_jaccard")
+    if check:
+        ssm_check(st, "ssm_gabriel_jaccard", stream)
+    return mean, per
+
+
 class StressWorkspace:
     def __init__(self, n: int, m: int, nsources: int, ntargets: int, device):
         self.ws = _ws(lib().ssm_stress_workspace(n, m, nsources, ntargets), device)
@@ -532,3 +600,145 @@ def layout(n: int, src, dst, k: int = 200, iters: int = 100, tol: float = 0.0, s
     g, p, pos, _ = prepare(n, src, dst, k, start, precision, device)
     ssm_iterate(g, p, pos, iters, tol)
     return pos
+
+
+# ---------------------------------------------------------------- weighted graphs
+@dataclass
+class WGraph(Graph):
+    elen: torch.Tensor = None  # float32 [2m], the length of edge colidx[t]
+
+
+def ssm_build_wgraph(n: int, src: torch.Tensor, dst: torch.Tensor, lengths: torch.Tensor, stream=None,
+                     check: bool = True) -> WGraph:
+    """CSR of the weighted simple undirected graph (a repeated edge keeps its
+    shortest length): ssm_build_graph, then ssm_edge_lengths."""
+    g = ssm_build_graph(n, src, dst, stream)
+    L = lib()
+    dev = src.device
+    src = src.contiguous().to(torch.int32)
+    dst = dst.contiguous().to(torch.int32)
+    lengths = lengths.contiguous().to(torch.float32)
+    elen = torch.empty(max(2 * g.m, 1), dtype=torch.float32, device=dev)
+    st = _status(dev)
+    ws = _ws(256, dev)
+    _rc(L.ssm_edge_lengths(n, src.numel(), _ptr(src), _ptr(dst), _ptr(lengths), g.m, _ptr(g.rowptr), _ptr(g.colidx),
+                           _ptr(elen), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_edge_lengths")
+    if check:
+        ssm_check(st, "ssm_edge_lengths", stream)
+    return WGraph(g.n, g.m, g.rowptr, g.colidx, elen[: 2 * g.m])
+
+
+def ssm_pivot_sssp(g: WGraph, sources: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
+    """Weighted distances [k, n] float32 from each source (least float32 path sums)."""
+    L = lib()
+    dev = g.rowptr.device
+    k = sources.numel()
+    dist = torch.empty((k, g.n), dtype=torch.float32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_pivot_sssp_workspace(g.n, k), dev)
+    _rc(L.ssm_pivot_sssp(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), k, _ptr(sources.contiguous()),
+                         _ptr(dist), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_pivot_sssp")
+    if check:
+        ssm_check(st, "ssm_pivot_sssp", stream)
+    return dist
+
+
+def ssm_select_pivots_weighted(g: WGraph, k: int, start: int = 0, stream=None, check: bool = True) -> torch.Tensor:
+    L = lib()
+    dev = g.rowptr.device
+    piv = torch.empty(k, dtype=torch.int32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_select_pivots_weighted_workspace(g.n, k), dev)
+    _rc(L.ssm_select_pivots_weighted(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), k, start, _ptr(piv),
+                                     _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_select_pivots_weighted")
+    if check:
+        ssm_check(st, "ssm_select_pivots_weighted", stream)
+    return piv
+
+
+def ssm_weighted_counts(g: WGraph, pivots: torch.Tensor, dist: torch.Tensor, stream=None, check: bool = True):
+    """Returns (region[n] int32, s[k, n] uint32) of Section 3 on weighted distances."""
+    L = lib()
+    k, n = dist.shape
+    dev = dist.device
+    region = torch.empty(n, dtype=torch.int32, device=dev)
+    s_tab = torch.empty((k, n), dtype=torch.uint32, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_weighted_counts_workspace(n, k), dev)
+    _rc(L.ssm_weighted_counts(n, _ptr(g.rowptr), _ptr(g.colidx), k, _ptr(pivots.contiguous()), _ptr(dist),
+                              _ptr(region), _ptr(s_tab), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_weighted_counts")
+    if check:
+        ssm_check(st, "ssm_weighted_counts", stream)
+    return region, s_tab
+
+
+def ssm_pivotmds_weighted(g: WGraph, dist: torch.Tensor, precision: int = 32, rescale: bool = True, stream=None,
+                          check: bool = True):
+    """PivotMDS from the weighted distance table: returns (pos [n, 2], eig [4] float64)."""
+    L = lib()
+    k, n = dist.shape
+    dev = dist.device
+    pos = torch.empty((n, 2), dtype=torch.float64 if precision == 64 else torch.float32, device=dev)
+    eig = torch.zeros(4, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_pivotmds_weighted_workspace(n, k), dev)
+    _rc(L.ssm_pivotmds_weighted(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), k, _ptr(dist), _ptr(pos), precision,
+                                int(rescale), _ptr(eig), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_pivotmds_weighted")
+    if check:
+        ssm_check(st, "ssm_pivotmds_weighted", stream)
+    return pos, eig
+
+
+def ssm_iterate_weighted(g: WGraph, pivots: torch.Tensor, dist: torch.Tensor, s_tab: torch.Tensor,
+                         pos: torch.Tensor, iters: int, stream=None, check: bool = True) -> torch.Tensor:
+    """`iters` Jacobi updates of Eq. 4 on a weighted graph, in place on pos;
+    returns the last relative change (device float64 [1])."""
+    L = lib()
+    k, n = dist.shape
+    dev = pos.device
+    precision = 64 if pos.dtype == torch.float64 else 32
+    rel = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_iterate_weighted_workspace(n, precision), dev)
+    _rc(L.ssm_iterate_weighted(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), k, _ptr(pivots.contiguous()),
+                               _ptr(dist), _ptr(s_tab), _ptr(pos), precision, iters, _ptr(rel), _ptr(st), _ptr(ws),
+                               ws.numel(), _stream(stream)), "ssm_iterate_weighted")
+    if check:
+        ssm_check(st, "ssm_iterate_weighted", stream)
+    return rel
+
+
+def ssm_stress_weighted(g: WGraph, pos: torch.Tensor, nsources: int = 0, ntargets: int = 0, seed: int = 0,
+                        stream=None, check: bool = True):
+    """{raw, alpha*, scaled, normalized} and the four pair sums (float64 device tensors)."""
+    L = lib()
+    dev = pos.device
+    precision = 64 if pos.dtype == torch.float64 else 32
+    out = torch.zeros(4, dtype=torch.float64, device=dev)
+    sums = torch.zeros(4, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    ws = _ws(L.ssm_stress_weighted_workspace(g.n, nsources), dev)
+    _rc(L.ssm_stress_weighted(g.n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), _ptr(pos.contiguous()), precision,
+                              nsources, ntargets, ctypes.c_uint64(seed), _ptr(out), _ptr(sums), _ptr(st), _ptr(ws),
+                              ws.numel(), _stream(stream)), "ssm_stress_weighted")
+    if check:
+        ssm_check(st, "ssm_stress_weighted", stream)
+    return out, sums
+
+
+def layout_weighted(n: int, src, dst, lengths, k: int, iters: int, start: int = 0, device="cuda"):
+    """Algorithm 1 on a weighted graph, every step on the GPU: returns
+    (graph, pivots, dist, region, s, positions float32 [n, 2], eigenvalues)."""
+    _require_cuda()
+    src = torch.as_tensor(src, dtype=torch.int32).to(device)
+    dst = torch.as_tensor(dst, dtype=torch.int32).to(device)
+    lengths = torch.as_tensor(lengths, dtype=torch.float32).to(device)
+    g = ssm_build_wgraph(n, src, dst, lengths)
+    piv = ssm_select_pivots_weighted(g, k, start)
+    dist = ssm_pivot_sssp(g, piv)
+    region, s_tab = ssm_weighted_counts(g, piv, dist)
+    pos, eig = ssm_pivotmds_weighted(g, dist, 32, True)
+    ssm_iterate_weighted(g, piv, dist, s_tab, pos, iters)
+    return g, piv, dist, region, s_tab, pos, eig

@@ -299,9 +299,12 @@ struct EigOut {
 // Gram-Schmidt, the convergence decisions -- every block computes on its own
 // identical copy, so the blocks stay in step without further exchange; block
 // 0 writes the results.
+// S: the type of the column sums s_a (exact integers for hop distances,
+// FP64 for weighted distances)
+template <class S>
 __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, const double *__restrict__ B,
                                                        const double *__restrict__ M,
-                                                       const unsigned long long *__restrict__ s,
+                                                       const S *__restrict__ s,
                                                        double *__restrict__ vout /* [2][k] */,
                                                        EigOut *__restrict__ out, double *__restrict__ eig_user,
                                                        double *__restrict__ Yg /* [2][k][P] */,
@@ -607,10 +610,14 @@ __global__ void k_dmax(int64_t count, const uint16_t *__restrict__ dip, unsigned
 template <class T2>
 __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__restrict__ rowptr,
                                                   const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
+                                                  const float *__restrict__ elen,
                                                   double *__restrict__ part, unsigned *__restrict__ done,
                                                   double *__restrict__ scale, int32_t *__restrict__ status) {
   using R = decltype(pos[0].x);  // edge lengths in the precision of the positions, summed in FP64
-  __shared__ double red[8];
+  // elen (weighted graphs, may be null): the target is the sum of the edge
+  // lengths instead of m, summed alongside in FP64
+  __shared__ double red[8], redl[8];
+  double accl = 0.0;
   __shared__ unsigned s_ticket;
   const int lane = threadIdx.x & 31;
   double acc = 0.0;
@@ -639,6 +646,7 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
           if (j[q] > i) {
             const R dx = xi.x - xj[q].x, dy = xi.y - xj[q].y;
             acc += (double)sqrt(dx * dx + dy * dy);
+            if (elen) accl += (double)__ldg(elen + t + q);
           }
       }
     }
@@ -662,17 +670,28 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
           if (j[q] > hi) {
             const R dx = hx - xj[q].x, dy = hy - xj[q].y;
             acc += (double)sqrt(dx * dx + dy * dy);
+            if (elen) accl += (double)__ldg(elen + t0 + 32 * q);
           }
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    accl += __shfl_xor_sync(0xffffffffu, accl, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = acc;
+    redl[threadIdx.x >> 5] = accl;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
-    part[blockIdx.x] = t;
+    double t = 0.0, tl = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      t += red[w];
+      tl += redl[w];
+    }
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = tl;
     __threadfence();
     s_ticket = atomicAdd(done, 1u);
   }
@@ -680,15 +699,27 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
   if (s_ticket != gridDim.x - 1) return;
   // the last block adds the block sums: a fixed share per thread, then a fixed tree
   __threadfence();
-  double t = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(part + b);
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  double t = 0.0, tl = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    t += __ldcg(part + 2 * b);
+    tl += __ldcg(part + 2 * b + 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    tl += __shfl_xor_sync(0xffffffffu, tl, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = t;
+    redl[threadIdx.x >> 5] = tl;
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double tot = 0.0;
-  for (int w = 0; w < (int)blockDim.x / 32; ++w) tot += red[w];
-  const double m = (double)__ldg(rowptr + n) * 0.5;
+  double tot = 0.0, totl = 0.0;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+    tot += red[w];
+    totl += redl[w];
+  }
+  const double m = elen ? totl : (double)__ldg(rowptr + n) * 0.5;
   if (!(tot > 0.0) || !isfinite(tot)) {
     dev_fail(status, SSM_E_NUMERIC);
     *scale = 1.0;
@@ -730,7 +761,7 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.bscale = c.take<double>(1);
   w.rowmean = c.take<double>(k);
   w.vv = c.take<double>(2 * (size_t)k);
-  w.part = c.take<double>(4096);
+  w.part = c.take<double>(8192);
   w.scale = c.take<double>(1);
   w.eo = c.take<EigOut>(1);
   w.done = c.take<unsigned>(1);
@@ -738,6 +769,57 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.Yg = c.take<double>(2 * (size_t)k * kEigP);
   w.bar = c.take<BarrierState>(1);
   return c.size();
+}
+
+// top-2 eigenpairs of w.B (already formed) and the projection constants
+// (from the column sums s_a of Delta) into w.vv / w.eo
+template <class S>
+static int launch_eigen(int32_t n, int32_t k, MdsWs &w, const S *colsum, double *eig, int32_t *status,
+                        cudaStream_t s) {
+  const size_t kk = (size_t)k * k;
+  const int P = std::min(kEigP, (int)k);
+  const size_t esm = (3 * (size_t)k * P + kEigScratch) * sizeof(double);  // V, Y, saved Y, scratch
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_eigen<S>));
+  note_launch(), k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
+  const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
+  // M = (B/max|B|)^(2^kEigPowerLog2) by repeated squaring
+  {
+    const double *src = w.B;
+    for (int q = 0; q < kEigPowerLog2; ++q) {
+      double *dst = (q == kEigPowerLog2 - 1) ? w.M : ((q & 1) ? w.Btmp : w.B2);
+      note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, src, q == 0 ? w.bscale : nullptr, dst);
+      src = dst;
+    }
+  }
+  // one warp per row of the k x k products: as many blocks as the rows need, all resident
+  const int want = (k + kEigThreads / 32 - 1) / (kEigThreads / 32);
+  const int eblocks = std::max(1, std::min(want, cooperative_blocks((const void *)k_eigen<S>, kEigThreads, esm, 1)));
+  if (int rc_ = reset_barrier(w.bar, s)) return rc_;
+  int maxit = 2000;
+  double tol = 1e-12;
+  void *args[] = {&n, &k, &w.B, &w.M, &colsum, &w.vv, &w.eo, &eig, &w.Yg, &w.bar, &status, &maxit, &tol};
+  note_launch();
+  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_eigen<S>, dim3(eblocks), dim3(kEigThreads), args, esm, s));
+  return SSM_OK;
+}
+
+// Algorithm 1 line 4: scale so that sum_E ||x_i - x_j|| = sum_E l_ij (m for
+// unit edges, elen == nullptr); w.done must be zero
+static int launch_rescale(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, void *pos,
+                          int32_t precision, MdsWs &w, int32_t *status, cudaStream_t s) {
+  const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)num_sms() * 8);
+  const int eb = std::min(pb, 4096);
+  if (precision == 64) {
+    note_launch(), k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, elen, w.part,
+                                                          w.done, w.scale, status);
+    note_launch(), k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
+  } else {
+    note_launch(), k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, elen, w.part,
+                                                         w.done, w.scale, status);
+    note_launch(), k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
+  }
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
 }
 
 // G = Delta^T Delta into Glo/Ghi (zeroed here) and the largest d_ip entry into *dmax
@@ -790,7 +872,6 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
   MdsWs w;
   carve_mds(c, w, n, k);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_pivotmds: workspace %zu bytes, need %zu", ws_bytes, c.size());
-  const size_t kk = (size_t)k * k;
   const int sms = num_sms();
   SSM_TRY_CUDA(cudaMemsetAsync(w.done, 0, sizeof(unsigned), s));
   {
@@ -803,44 +884,250 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
     note_launch(), k_colsum<<<(unsigned)std::min<int64_t>(tasks, (int64_t)sms * 8), 256, 0, s>>>(n, k, dip, w.s);
   }
   note_launch(), k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
-  const int P = std::min(kEigP, (int)k);
-  const size_t esm = (3 * (size_t)k * P + kEigScratch) * sizeof(double);  // V, Y, saved Y, scratch
-  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_eigen));
-  note_launch(), k_absmax_inv<<<1, 1024, 0, s>>>((int64_t)kk, w.B, w.bscale);
-  const dim3 sq_grid((unsigned)((k + 15) / 16), (unsigned)((k + 15) / 16));
-  // M = (B/max|B|)^(2^kEigPowerLog2) by repeated squaring
-  {
-    const double *src = w.B;
-    for (int q = 0; q < kEigPowerLog2; ++q) {
-      double *dst = (q == kEigPowerLog2 - 1) ? w.M : ((q & 1) ? w.Btmp : w.B2);
-      note_launch(), k_square_f64<<<sq_grid, 256, 0, s>>>(k, src, q == 0 ? w.bscale : nullptr, dst);
-      src = dst;
-    }
-  }
-  {
-    // one warp per row of the k x k products: as many blocks as the rows need, all resident
-    const int want = (k + kEigThreads / 32 - 1) / (kEigThreads / 32);
-    const int eblocks = std::max(1, std::min(want, cooperative_blocks((const void *)k_eigen, kEigThreads, esm, 1)));
-    if (int rc_ = reset_barrier(w.bar, s)) return rc_;
-    int maxit = 2000;
-    double tol = 1e-12;
-    void *args[] = {&n, &k, &w.B, &w.M, &w.s, &w.vv, &w.eo, &eig, &w.Yg, &w.bar, &status, &maxit, &tol};
-    note_launch();
-    SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_eigen, dim3(eblocks), dim3(kEigThreads), args, esm, s));
-  }
+  if (int rc = launch_eigen(n, k, w, w.s, eig, status, s)) return rc;
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   const size_t psm = (size_t)k * sizeof(float4);
   note_launch(), k_project<<<pb, 256, psm, s>>>(n, k, dip, w.vv, w.eo, w.dmax, pos, precision);
-  if (rescale) {
-    const int eb = std::min(pb, 4096);
-    if (precision == 64) {
-      note_launch(), k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, w.part, w.done, w.scale, status);
-      note_launch(), k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
-    } else {
-      note_launch(), k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, w.part, w.done, w.scale, status);
-      note_launch(), k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
+  if (rescale) return launch_rescale(n, rowptr, colidx, nullptr, pos, precision, w, status, s);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+
+// ------------------------------------------------------------- weighted
+// PivotMDS on a float32 distance table (weighted graphs).  delta_ia = d_ia^2
+// is formed in FP64 (exactly); with cbar_a the column means,
+//   C^T C = 1/4 J_k G' J_k,  G'_ab = sum_i (delta_ia - cbar_a)(delta_ib - cbar_b),
+// the column centring applied before the product so that nothing cancels;
+// G' is summed in FP64 per fixed node chunk and the chunk partials are added
+// in chunk order.
+namespace ssm {
+
+constexpr int kWTile = 32;
+
+static int64_t wgram_chunk(int32_t n) {
+  int64_t c = ((int64_t)n + 63) / 64;
+  c = std::max<int64_t>(1024, std::min<int64_t>(16384, c));
+  return (c + kWTile - 1) / kWTile * kWTile;
+}
+
+// partc[a * nchunks + c] = sum over the nodes of chunk c of d_ia^2 (fixed tree)
+__global__ void __launch_bounds__(256) k_wcolsum_part(int32_t n, int32_t k, const float *__restrict__ dist,
+                                                      int64_t chunk, int64_t nchunks, double *__restrict__ partc) {
+  __shared__ double red[8];
+  for (int64_t task = blockIdx.x; task < (int64_t)k * nchunks; task += gridDim.x) {
+    const int a = (int)(task / nchunks);
+    const int64_t c = task - (int64_t)a * nchunks;
+    const int64_t i0 = c * chunk, i1 = min((int64_t)n, i0 + chunk);
+    double acc = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double d = (double)__ldg(dist + (size_t)a * n + i);
+      acc += d * d;
     }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      partc[task] = t;
+    }
+    __syncthreads();
   }
+}
+
+__global__ void k_wcolsum_final(int32_t k, int64_t nchunks, const double *__restrict__ partc,
+                                double *__restrict__ colsum) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < k; a += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int64_t c = 0; c < nchunks; ++c) t += partc[(size_t)a * nchunks + c];
+    colsum[a] = t;
+  }
+}
+
+// one 32 x 32 tile (ta <= tb) of G' over one node chunk; 16 x 16 threads,
+// 2 x 2 outputs each; partials into partg[c][a][b]
+__global__ void __launch_bounds__(256) k_wgram(int32_t n, int32_t k, const float *__restrict__ dist,
+                                               const double *__restrict__ colsum, int64_t chunk, int64_t nchunks,
+                                               int32_t ntiles, double *__restrict__ partg) {
+  __shared__ double sa[kWTile][kWTile + 1], sb[kWTile][kWTile + 1];  // [node][pivot]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t npairs = (int64_t)ntiles * (ntiles + 1) / 2;
+  const double inv_n = 1.0 / (double)n;
+  for (int64_t task = blockIdx.x; task < npairs * nchunks; task += gridDim.x) {
+    const int64_t c = task / npairs;
+    int64_t pr = task - c * npairs;
+    int ta = 0;
+    while (pr >= ntiles - ta) {
+      pr -= ntiles - ta;
+      ++ta;
+    }
+    const int tb = ta + (int)pr;
+    const int a0 = ta * kWTile, b0 = tb * kWTile;
+    const int64_t i0 = c * chunk, i1 = min((int64_t)n, i0 + chunk);
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int64_t ib = i0; ib < i1; ib += kWTile) {
+      // stage 32 nodes x 32 pivots of each side, centred by the column means
+      for (int e = threadIdx.x; e < kWTile * kWTile; e += blockDim.x) {
+        const int pv = e / kWTile, nd = e % kWTile;
+        const int64_t i = ib + nd;
+        double va = 0.0, vb = 0.0;
+        if (i < i1) {
+          if (a0 + pv < k) {
+            const double d = (double)__ldg(dist + (size_t)(a0 + pv) * n + i);
+            va = d * d - colsum[a0 + pv] * inv_n;
+          }
+          if (b0 + pv < k) {
+            const double d = (double)__ldg(dist + (size_t)(b0 + pv) * n + i);
+            vb = d * d - colsum[b0 + pv] * inv_n;
+          }
+        }
+        sa[nd][pv] = va;
+        sb[nd][pv] = vb;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int nd = 0; nd < kWTile; ++nd) {
+        const double x0 = sa[nd][2 * ty], x1 = sa[nd][2 * ty + 1];
+        const double y0 = sb[nd][2 * tx], y1 = sb[nd][2 * tx + 1];
+        acc[0][0] += x0 * y0;
+        acc[0][1] += x0 * y1;
+        acc[1][0] += x1 * y0;
+        acc[1][1] += x1 * y1;
+      }
+      __syncthreads();
+    }
+    double *pg = partg + (size_t)c * k * k;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int a = a0 + 2 * ty + p, b = b0 + 2 * tx + q;
+        if (a < k && b < k) pg[(size_t)a * k + b] = acc[p][q];
+      }
+  }
+}
+
+// G'_ab (a <= b, mirrored) = sum of the chunk partials in chunk order
+__global__ void k_wgram_reduce(int32_t k, int64_t nchunks, const double *__restrict__ partg, double *__restrict__ G) {
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < kk; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / k), b = (int)(t - (int64_t)a * k);
+    if (a > b) continue;
+    double g = 0.0;
+    for (int64_t c = 0; c < nchunks; ++c) g += partg[(size_t)c * kk + t];
+    G[(size_t)a * k + b] = g;
+    G[(size_t)b * k + a] = g;
+  }
+}
+
+// B = 1/4 (G' - rowmean_a - rowmean_b + grand mean), in place (one block)
+__global__ void k_center_b(int32_t k, double *__restrict__ B, double *__restrict__ rowmean) {
+  __shared__ double red[32];
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < k; ++b) acc += B[(size_t)a * k + b];
+    rowmean[a] = acc / (double)k;
+  }
+  __syncthreads();
+  double g = 0.0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) g += rowmean[a];
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+    red[0] = t / (double)k;
+  }
+  __syncthreads();
+  const double gm = red[0];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int a = t / k, b = t % k;
+    B[t] = 0.25 * (B[t] - rowmean[a] - rowmean[b] + gm);
+  }
+}
+
+// x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa), FP64
+__global__ void __launch_bounds__(256) k_wproject(int32_t n, int32_t k, const float *__restrict__ dist,
+                                                  const double *__restrict__ vv, const EigOut *__restrict__ eo,
+                                                  void *__restrict__ pos, int precision) {
+  extern __shared__ __align__(16) double svv[];  // v0[k], v1[k]
+  for (int a = threadIdx.x; a < 2 * k; a += blockDim.x) svv[a] = vv[a];
+  __syncthreads();
+  const double sig0 = eo->sigma[0], sig1 = eo->sigma[1], kap0 = eo->kappa[0], kap1 = eo->kappa[1];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0.0, y = 0.0, rs = 0.0;
+    for (int a = 0; a < k; ++a) {
+      const double d = (double)__ldg(dist + (size_t)a * n + i);
+      const double dd = d * d;
+      rs += dd;
+      x += dd * svv[a];
+      y += dd * svv[k + a];
+    }
+    const double rbar = rs / (double)k;
+    x = -0.5 * (x - rbar * sig0 - kap0);
+    y = -0.5 * (y - rbar * sig1 - kap1);
+    if (precision == 64) reinterpret_cast<double2 *>(pos)[i] = make_double2(x, y);
+    else reinterpret_cast<float2 *>(pos)[i] = make_float2((float)x, (float)y);
+  }
+}
+
+struct WMdsWs {
+  double *colsum, *partc, *partg;
+};
+
+static size_t carve_wmds(Carver &c, MdsWs &w, WMdsWs &x, int32_t n, int32_t k) {
+  carve_mds(c, w, n, k);
+  const int64_t ch = wgram_chunk(n), nch = ((int64_t)n + ch - 1) / ch;
+  x.colsum = c.take<double>((size_t)k);
+  x.partc = c.take<double>((size_t)k * nch);
+  x.partg = c.take<double>((size_t)nch * k * k);
+  return c.size();
+}
+
+}  // namespace ssm
+
+SSM_API size_t ssm_pivotmds_weighted_workspace(int32_t n, int32_t k) {
+  if (n < 1 || k < 1) return 0;
+  ssm::Carver c(nullptr, 0);
+  ssm::MdsWs w;
+  ssm::WMdsWs x;
+  return ssm::carve_wmds(c, w, x, n, k);
+}
+
+SSM_API int ssm_pivotmds_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen,
+                                  int32_t k, const float *dist, void *pos, int32_t precision, int32_t rescale,
+                                  double *eig, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || !dist || !pos || !status || !ws || (rescale && (!rowptr || !colidx || !elen)))
+    return fail(SSM_E_ARG, "ssm_pivotmds_weighted: null pointer or n < 1");
+  if (k < 2 || k > kMaxPivotsMds || k > n)
+    return fail(SSM_E_ARG, "ssm_pivotmds_weighted: need 2 <= k <= min(n, %d)", kMaxPivotsMds);
+  if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_pivotmds_weighted: precision must be 32 or 64");
+  Carver c(ws, ws_bytes);
+  MdsWs w;
+  WMdsWs x;
+  carve_wmds(c, w, x, n, k);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_pivotmds_weighted: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const int sms = num_sms();
+  const int64_t ch = wgram_chunk(n), nch = ((int64_t)n + ch - 1) / ch;
+  const int ntiles = (k + kWTile - 1) / kWTile;
+  SSM_TRY_CUDA(cudaMemsetAsync(w.done, 0, sizeof(unsigned), s));
+  note_launch(), k_wcolsum_part<<<(unsigned)std::min<int64_t>((int64_t)k * nch, (int64_t)sms * 8), 256, 0, s>>>(
+      n, k, dist, ch, nch, x.partc);
+  note_launch(), k_wcolsum_final<<<std::max(1, (k + 255) / 256), 256, 0, s>>>(k, nch, x.partc, x.colsum);
+  const int64_t gtasks = (int64_t)ntiles * (ntiles + 1) / 2 * nch;
+  note_launch(), k_wgram<<<(unsigned)std::min<int64_t>(gtasks, (int64_t)sms * 8), 256, 0, s>>>(
+      n, k, dist, x.colsum, ch, nch, ntiles, x.partg);
+  const int64_t kk = (int64_t)k * k;
+  note_launch(), k_wgram_reduce<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kk + 255) / 256, sms * 4)), 256, 0,
+                                  s>>>(k, nch, x.partg, w.B);
+  note_launch(), k_center_b<<<1, 1024, 0, s>>>(k, w.B, w.rowmean);
+  if (int rc = launch_eigen(n, k, w, (const double *)x.colsum, eig, status, s)) return rc;
+  const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
+  note_launch(), k_wproject<<<pb, 256, 2 * (size_t)k * sizeof(double), s>>>(n, k, dist, w.vv, w.eo, pos, precision);
+  if (rescale) return launch_rescale(n, rowptr, colidx, elen, pos, precision, w, status, s);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }

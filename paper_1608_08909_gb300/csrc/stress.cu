@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "bfs.cuh"
+#include "weighted.cuh"
 
 namespace ssm {
 
@@ -25,8 +26,12 @@ __global__ void k_batch_sources(int32_t base, int32_t B, int32_t *__restrict__ s
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x) src[j] = base + j;
 }
 
-template <class T2>
-__device__ __forceinline__ void pair_terms(const T2 *__restrict__ pos, int i, int j, unsigned d, double (&acc)[4]) {
+// a pair distance that cannot be used: unreachable (or the same node)
+__device__ __forceinline__ bool bad_dist(uint16_t d) { return d == 0xFFFFu || d == 0u; }
+__device__ __forceinline__ bool bad_dist(float d) { return !(d > 0.0f) || isinf(d); }
+
+template <class T2, class D>
+__device__ __forceinline__ void pair_terms(const T2 *__restrict__ pos, int i, int j, D d, double (&acc)[4]) {
   const T2 a = pos[i], b = pos[j];
   const double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y;
   const double r = sqrt(dx * dx + dy * dy);
@@ -55,9 +60,9 @@ __device__ __forceinline__ void block_store_sums(double (&acc)[4], double *__res
 }
 
 // exhaustive batch: sources base..base+B-1, pairs (base+a, v) with v > base+a
-template <class T2>
+template <class T2, class D>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_exhaustive(int32_t n, int32_t base, int32_t B,
-                                                                    const uint16_t *__restrict__ dist,
+                                                                    const D *__restrict__ dist,
                                                                     const T2 *__restrict__ pos,
                                                                     double *__restrict__ part,
                                                                     int32_t *__restrict__ status) {
@@ -67,8 +72,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_exhaustive(int32_t n, in
     const int a = (int)(t / n), v = (int)(t - (int64_t)a * n);
     const int i = base + a;
     if (v <= i) continue;
-    const unsigned d = __ldg(dist + t);
-    if (d == 0xFFFFu || d == 0u) {
+    const D d = __ldg(dist + t);
+    if (bad_dist(d)) {
       dev_fail(status, SSM_E_DISCONNECTED);
       continue;
     }
@@ -78,10 +83,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_exhaustive(int32_t n, in
 }
 
 // sampled: source j (src[j]), targets l = 0..T-1 from the splitmix64 stream
-template <class T2>
+template <class T2, class D>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_sampled(int32_t n, int32_t S, int32_t T, uint64_t seed,
                                                                  const int32_t *__restrict__ src,
-                                                                 const uint16_t *__restrict__ dist,
+                                                                 const D *__restrict__ dist,
                                                                  const T2 *__restrict__ pos,
                                                                  double *__restrict__ part,
                                                                  int32_t *__restrict__ status) {
@@ -93,8 +98,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_sampled(int32_t n, int32
     const uint64_t u = splitmix64_at(seed, (uint64_t)S + (uint64_t)t);
     int v = (int)(((u >> 32) * (uint64_t)(n - 1)) >> 32);
     v += (v >= s) ? 1 : 0;
-    const unsigned d = __ldg(dist + (size_t)j * n + v);
-    if (d == 0xFFFFu || d == 0u) {
+    const D d = __ldg(dist + (size_t)j * n + v);
+    if (bad_dist(d)) {
       dev_fail(status, SSM_E_DISCONNECTED);
       continue;
     }
@@ -197,10 +202,10 @@ SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_
     int rc = launch_msbfs(n, 2 * m, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
     if (rc) return rc;
     if (precision == 64)
-      note_launch(), k_pairs_sampled<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+      note_launch(), k_pairs_sampled<double2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
                                                            (const double2 *)pos, w.part, status);
     else
-      note_launch(), k_pairs_sampled<float2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+      note_launch(), k_pairs_sampled<float2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
                                                           (const float2 *)pos, w.part, status);
   } else {
     for (int b = 0; b < nb; ++b) {
@@ -210,11 +215,87 @@ SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_
       if (rc) return rc;
       double *part = w.part + 4 * (size_t)pb * b;
       if (precision == 64)
-        note_launch(), k_pairs_exhaustive<double2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const double2 *)pos, part,
+        note_launch(), k_pairs_exhaustive<double2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const double2 *)pos, part,
                                                                 status);
       else
-        note_launch(), k_pairs_exhaustive<float2><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const float2 *)pos, part,
+        note_launch(), k_pairs_exhaustive<float2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist, (const float2 *)pos, part,
                                                                status);
+    }
+  }
+  note_launch(), k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+// ------------------------------------------------------------- weighted
+// The same sums with weighted distances: the float32 least path sums of the
+// weighted search (weighted.cu) from the sources, in batches.
+namespace ssm {
+struct WStressWs {
+  int32_t *src;
+  float *dist;
+  double *part;
+  void *sssp;
+  size_t sssp_bytes;
+};
+static size_t carve_wstress(Carver &c, WStressWs &w, int32_t n, int32_t S, int32_t nbatches) {
+  w.src = c.take<int32_t>(S);
+  w.dist = c.take<float>((size_t)S * n);
+  w.part = c.take<double>(4 * (size_t)pair_blocks() * (size_t)nbatches);
+  w.sssp_bytes = sssp_slot_bytes(n) * (size_t)sssp_blocks(S);
+  w.sssp = c.take<char>(w.sssp_bytes);
+  return c.size();
+}
+}  // namespace ssm
+
+SSM_API size_t ssm_stress_weighted_workspace(int32_t n, int32_t nsources) {
+  if (n < 2 || nsources < 0) return 0;
+  int32_t S, nb;
+  ssm::stress_shape(n, nsources, &S, &nb);
+  ssm::Carver c(nullptr, 0);
+  ssm::WStressWs w;
+  return ssm::carve_wstress(c, w, n, S, nb);
+}
+
+SSM_API int ssm_stress_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen,
+                                const void *pos, int32_t precision, int32_t nsources, int32_t ntargets, uint64_t seed,
+                                double *out, double *sums, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 2 || !rowptr || !colidx || !elen || !pos || !out || !status || !ws)
+    return fail(SSM_E_ARG, "ssm_stress_weighted: null pointer or bad size");
+  if (precision != 32 && precision != 64) return fail(SSM_E_ARG, "ssm_stress_weighted: precision must be 32 or 64");
+  if (nsources < 0 || nsources > 65535 || (nsources > 0 && ntargets < 1))
+    return fail(SSM_E_ARG, "ssm_stress_weighted: need 0 <= nsources <= 65535 and ntargets >= 1 when sampling");
+  int32_t S, nb;
+  stress_shape(n, nsources, &S, &nb);
+  Carver c(ws, ws_bytes);
+  WStressWs w;
+  carve_wstress(c, w, n, S, nb);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_stress_weighted: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  const int pb = pair_blocks();
+  if (nsources > 0) {
+    note_launch(), k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
+    int rc = launch_sssp(n, rowptr, colidx, elen, S, w.src, w.dist, status, w.sssp, w.sssp_bytes, s);
+    if (rc) return rc;
+    if (precision == 64)
+      note_launch(), k_pairs_sampled<double2, float><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+                                                                            (const double2 *)pos, w.part, status);
+    else
+      note_launch(), k_pairs_sampled<float2, float><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
+                                                                           (const float2 *)pos, w.part, status);
+  } else {
+    for (int b = 0; b < nb; ++b) {
+      const int32_t base = b * S, B = std::min<int32_t>(S, n - base);
+      note_launch(), k_batch_sources<<<std::max(1, (B + 255) / 256), 256, 0, s>>>(base, B, w.src);
+      int rc = launch_sssp(n, rowptr, colidx, elen, B, w.src, w.dist, status, w.sssp, w.sssp_bytes, s);
+      if (rc) return rc;
+      double *part = w.part + 4 * (size_t)pb * b;
+      if (precision == 64)
+        note_launch(), k_pairs_exhaustive<double2, float><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist,
+                                                                               (const double2 *)pos, part, status);
+      else
+        note_launch(), k_pairs_exhaustive<float2, float><<<pb, kPairThreads, 0, s>>>(n, base, B, w.dist,
+                                                                              (const float2 *)pos, part, status);
     }
   }
   note_launch(), k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);

@@ -139,6 +139,11 @@ class LayoutServer:
         self._closed = False
         self.peak_reserved = 0
         self.peak_active = 0
+        # requests that reached the head of the queue and had to wait: for
+        # bytes (a slot was free but the budget was not) or for a slot
+        self.waited_for_budget = 0
+        self.waited_for_slot = 0
+        self._head_seen = None
         self.admit_order: list = []
         self._pool = concurrent.futures.ThreadPoolExecutor(max_workers=slots, thread_name_prefix="ssm-slot")
         self._thread = threading.Thread(target=self._dispatch, name="ssm-dispatch", daemon=True)
@@ -186,6 +191,12 @@ class LayoutServer:
                         job, fut, need, t = self._queue[0]
                         if self._free and self._reserved + need <= self.budget:
                             break
+                        if self._head_seen is not fut:
+                            self._head_seen = fut
+                            if self._free:
+                                self.waited_for_budget += 1
+                            else:
+                                self.waited_for_slot += 1
                     elif self._closed:
                         return
                     self._cv.wait()

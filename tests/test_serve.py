@@ -61,6 +61,17 @@ def test_budget_slots_and_arrival_order(budget, slots):
     assert all(r.t_arrival <= r.t_admit <= r.t_done for r in res)
 
 
+def test_waits_are_attributed_to_the_budget_or_the_slots():
+    # budget-bound: 8 slots, but two 40-byte requests never fit a 60-byte budget together
+    with S.LayoutServer(60, slots=8, runner=_Probe(2), sizer=lambda j: j.n) as srv:
+        [f.result(timeout=30) for f in [srv.submit(j) for j in _jobs([40] * 20)]]
+        assert srv.waited_for_budget > 0 and srv.waited_for_slot == 0
+    # slot-bound: the budget holds everything, one slot
+    with S.LayoutServer(10_000, slots=1, runner=_Probe(3), sizer=lambda j: j.n) as srv:
+        [f.result(timeout=30) for f in [srv.submit(j) for j in _jobs([40] * 20)]]
+        assert srv.waited_for_slot > 0 and srv.waited_for_budget == 0
+
+
 def test_requests_run_concurrently_when_they_fit():
     probe = _Probe(1)
     with S.LayoutServer(10_000, slots=4, runner=probe, sizer=lambda j: j.n) as srv:
