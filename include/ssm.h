@@ -434,7 +434,8 @@ int ssm_gabriel_jaccard(int32_t n, const void *posA, const void *posB, int32_t p
  *   double2 by precision; FP64 rounds every operation as written, in the
  *   order of the plain definition); *rel_change (device double) receives
  *   ||X^{t+1} - X^t||_F / ||X^t||_F of the last update.
- *   Workspace ssm_iterate_weighted_workspace(n, precision).
+ *   FP32 forms w' = s / d^2 once per call in the workspace and takes 1/r
+ *   from rsqrt.  Workspace ssm_iterate_weighted_workspace(n, k, precision).
  * ssm_stress_weighted: ssm_stress with weighted distances (exhaustive when
  *   nsources == 0, else the same sampled pair list).
  * ------------------------------------------------------------------- */
@@ -457,7 +458,7 @@ size_t ssm_pivotmds_weighted_workspace(int32_t n, int32_t k);
 int ssm_pivotmds_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
                           const float *dist, void *pos, int32_t precision, int32_t rescale, double *eig,
                           int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
-size_t ssm_iterate_weighted_workspace(int32_t n, int32_t precision);
+size_t ssm_iterate_weighted_workspace(int32_t n, int32_t k, int32_t precision);
 int ssm_iterate_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
                          const int32_t *pivots, const float *dist, const uint32_t *s_tab, void *pos,
                          int32_t precision, int32_t iters, double *rel_change, int32_t *status, void *ws,

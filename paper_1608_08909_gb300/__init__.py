@@ -104,7 +104,7 @@ def lib():
                 "ssm_weighted_counts": (ctypes.c_int, [i32, v, v, i32, v, v, v, v, v, v, sz, v]),
                 "ssm_pivotmds_weighted_workspace": (sz, [i32, i32]),
                 "ssm_pivotmds_weighted": (ctypes.c_int, [i32, v, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
-                "ssm_iterate_weighted_workspace": (sz, [i32, i32]),
+                "ssm_iterate_weighted_workspace": (sz, [i32, i32, i32]),
                 "ssm_iterate_weighted": (ctypes.c_int, [i32, v, v, v, i32, v, v, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_stress_weighted_workspace": (sz, [i32, i32]),
                 "ssm_stress_weighted": (ctypes.c_int, [i32, v, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
@@ -701,7 +701,7 @@ def ssm_iterate_weighted(g: WGraph, pivots: torch.Tensor, dist: torch.Tensor, s_
     precision = 64 if pos.dtype == torch.float64 else 32
     rel = torch.zeros(1, dtype=torch.float64, device=dev)
     st = _status(dev)
-    ws = _ws(L.ssm_iterate_weighted_workspace(n, precision), dev)
+    ws = _ws(L.ssm_iterate_weighted_workspace(n, k, precision), dev)
     _rc(L.ssm_iterate_weighted(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(g.elen), k, _ptr(pivots.contiguous()),
                                _ptr(dist), _ptr(s_tab), _ptr(pos), precision, iters, _ptr(rel), _ptr(st), _ptr(ws),
                                ws.numel(), _stream(stream)), "ssm_iterate_weighted")

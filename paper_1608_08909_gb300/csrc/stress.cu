@@ -242,7 +242,7 @@ static size_t carve_wstress(Carver &c, WStressWs &w, int32_t n, int32_t S, int32
   w.src = c.take<int32_t>(S);
   w.dist = c.take<float>((size_t)S * n);
   w.part = c.take<double>(4 * (size_t)pair_blocks() * (size_t)nbatches);
-  w.sssp_bytes = sssp_slot_bytes(n) * (size_t)sssp_blocks(S);
+  w.sssp_bytes = sssp_ws_bytes(n, S);
   w.sssp = c.take<char>(w.sssp_bytes);
   return c.size();
 }

@@ -23,7 +23,9 @@
 //                           s_ia = |{j in R(a) : 2 d_ja <= d_ia}| by binary
 //                           search in each region's sorted distances; s = 0
 //                           where the pivot is i or a neighbour of i
-//   k_wsweep                Eq. 4 with w_ij = l_ij^-2 and w'_ia = s_ia/d_ia^2
+//   k_wsweep, k_wsweep_f32  Eq. 4 with w_ij = l_ij^-2 and w'_ia = s_ia/d_ia^2
+//                           (FP64 as written; FP32 with w' formed once per
+//                           call and one rsqrt per term)
 #include <algorithm>
 
 #include "common.cuh"
@@ -32,8 +34,8 @@
 namespace ssm {
 
 constexpr unsigned kInfBits = 0x7f800000u;
-constexpr int kSsspThreads = 512;
-constexpr int kSsspWarps = kSsspThreads / 32;
+constexpr int kSsspThreads = 512;       // the max/min search: one block, the whole graph
+constexpr int kSsspMultiThreads = 512;  // one source per block, up to three blocks per SM
 
 // ------------------------------------------------------------ edge lengths
 __global__ void k_fill_u32(int64_t count, unsigned *__restrict__ p, unsigned v) {
@@ -90,69 +92,131 @@ __global__ void k_elen_check(int32_t n, int64_t m2, const unsigned *__restrict__
 }
 
 // ------------------------------------------------------------ SSSP
-// Queue slots of one block: two queues of n entries and two membership
-// bitmaps of n bits (cleared again by the search before it returns).
+// Near-far label-correcting search (two-bucket Delta-stepping): only labels
+// below a threshold T are relaxed in a round ("near"); a node lowered to a
+// label at or above T waits in the far pile; when the near queue is empty
+// T grows by Delta (at least to the smallest far label plus Delta) and the
+// far pile is split again.  Plain rounds over every improved node (the
+// first form) re-relaxed each node about 20 times on a 262K-node geometric
+// graph; the threshold keeps the search close to label-setting order while
+// each round still relaxes a whole band of nodes.  Any order that relaxes
+// until nothing improves reaches the same least path sums.
+//
+// Per block: near queues (current, next), two far piles (ping-pong), and
+// membership bitmaps: one per near queue (the next queue's bits are set by
+// the relaxations of a round, the current queue's bits cleared as its nodes
+// are taken) and one for the far pile.
 struct SsspSlot {
-  int32_t *q[2];
-  unsigned *inq[2];
+  int32_t *nq[2];
+  int32_t *fq[2];
+  unsigned *in_near[2], *in_far;
 };
+
+__host__ __device__ inline size_t sssp_qbytes(int32_t n) { return (((size_t)n * 4) + 255) & ~size_t(255); }
+__host__ __device__ inline size_t sssp_bbytes(int32_t n) { return ((((size_t)n + 31) / 32) * 4 + 255) & ~size_t(255); }
 
 __device__ __forceinline__ SsspSlot sssp_slot(char *base, size_t slot_bytes, int b, int32_t n) {
   char *p = base + (size_t)b * slot_bytes;
-  const size_t qb = (((size_t)n * 4) + 255) & ~size_t(255);
-  const size_t bb = ((((size_t)n + 31) / 32) * 4 + 255) & ~size_t(255);
+  const size_t qb = sssp_qbytes(n), bb = sssp_bbytes(n);
   SsspSlot s;
-  s.q[0] = (int32_t *)p;
-  s.q[1] = (int32_t *)(p + qb);
-  s.inq[0] = (unsigned *)(p + 2 * qb);
-  s.inq[1] = (unsigned *)(p + 2 * qb + bb);
+  s.nq[0] = (int32_t *)p;
+  s.nq[1] = (int32_t *)(p + qb);
+  s.fq[0] = (int32_t *)(p + 2 * qb);
+  s.fq[1] = (int32_t *)(p + 3 * qb);
+  s.in_near[0] = (unsigned *)(p + 4 * qb);
+  s.in_near[1] = (unsigned *)(p + 4 * qb + bb);
+  s.in_far = (unsigned *)(p + 4 * qb + 2 * bb);
   return s;
 }
 
-size_t sssp_slot_bytes(int32_t n) {
-  const size_t qb = (((size_t)n * 4) + 255) & ~size_t(255);
-  const size_t bb = ((((size_t)n + 31) / 32) * 4 + 255) & ~size_t(255);
-  return 2 * qb + 2 * bb;
+size_t sssp_slot_bytes(int32_t n) { return 4 * sssp_qbytes(n) + 3 * sssp_bbytes(n); }
+
+__device__ __forceinline__ bool set_bit(unsigned *bm, int v) {
+  const unsigned bit = 1u << (v & 31);
+  return !(atomicOr(bm + (v >> 5), bit) & bit);
 }
 
 // One search from `source` into row (labels as float bits).  init: set every
 // label to +inf first; otherwise the row's labels stay (max/min's pruned
-// search: only nodes the new pivot is strictly closer to change).
+// search: only nodes the new pivot is strictly closer to change).  delta is
+// the band width.  The bitmaps are clear on entry and on return.
 __device__ void sssp_block(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                            const unsigned *__restrict__ elen, int32_t source, unsigned *__restrict__ row, bool init,
-                           SsspSlot sl, int32_t *__restrict__ status) {
-  __shared__ unsigned s_next;
+                           float delta, SsspSlot sl, int32_t *__restrict__ status) {
+  __shared__ unsigned s_nnext, s_nfar, s_nfar2, s_minfar;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (init)
     for (int v = threadIdx.x; v < n; v += blockDim.x) row[v] = kInfBits;
   __syncthreads();
   if (threadIdx.x == 0) {
     row[source] = 0u;
-    sl.q[0][0] = source;
-    sl.inq[0][source >> 5] |= 1u << (source & 31);
+    sl.nq[0][0] = source;
+    s_nfar = 0;
   }
   __syncthreads();
-  unsigned ncur = 1;
-  int cur = 0;
-  for (int64_t round = 0; ncur > 0; ++round) {
-    if (round > (int64_t)n + 1) {  // every label is final after n rounds
+  unsigned nnear = 1, nfar = 0;
+  int cur = 0, fcur = 0;
+  float T = delta;
+  // every pass relaxes at least one node whose label is then final for the
+  // band, so the passes are bounded; the cap only guards against a fault
+  const int64_t cap = 64ll * ((int64_t)n + 16);
+  for (int64_t pass = 0;; ++pass) {
+    if (pass > cap) {
       if (threadIdx.x == 0) dev_fail(status, SSM_E_NUMERIC);
       break;
     }
-    if (threadIdx.x == 0) s_next = 0;
+    if (nnear == 0) {
+      if (nfar == 0) break;
+      // next band: T >= smallest far label + delta; split the far pile
+      const int32_t *fq = fcur ? sl.fq[1] : sl.fq[0];
+      int32_t *fq2 = fcur ? sl.fq[0] : sl.fq[1];
+      int32_t *nq = cur ? sl.nq[1] : sl.nq[0];
+      if (threadIdx.x == 0) {
+        s_minfar = kInfBits;
+        s_nnext = 0;
+        s_nfar2 = 0;
+      }
+      __syncthreads();
+      for (unsigned t = threadIdx.x; t < nfar; t += blockDim.x) atomicMin(&s_minfar, __ldcg(row + fq[t]));
+      __syncthreads();
+      T = fmaxf(T + delta, __uint_as_float(s_minfar) + delta);
+      // where delta vanishes against the labels, take the next float above
+      // the smallest far label so that at least that node moves on
+      if (!(T > __uint_as_float(s_minfar))) T = __uint_as_float(s_minfar + 1u);
+      for (unsigned t = threadIdx.x; t < nfar; t += blockDim.x) {
+        const int v = fq[t];
+        atomicAnd(sl.in_far + (v >> 5), ~(1u << (v & 31)));
+        if (__uint_as_float(__ldcg(row + v)) < T) nq[atomicAdd(&s_nnext, 1u)] = v;
+        else {
+          set_bit(sl.in_far, v);
+          fq2[atomicAdd(&s_nfar2, 1u)] = v;
+        }
+      }
+      __syncthreads();
+      nnear = s_nnext;
+      nfar = s_nfar2;
+      fcur ^= 1;
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      s_nnext = 0;
+      s_nfar = nfar;
+    }
     __syncthreads();
-    const int32_t *qc = cur ? sl.q[1] : sl.q[0];
-    int32_t *qn = cur ? sl.q[0] : sl.q[1];
-    unsigned *inc = cur ? sl.inq[1] : sl.inq[0];
-    unsigned *inn = cur ? sl.inq[0] : sl.inq[1];
-    // a warp takes 32 queue entries at a time and walks their rows together,
+    const int32_t *qc = cur ? sl.nq[1] : sl.nq[0];
+    int32_t *qn = cur ? sl.nq[0] : sl.nq[1];
+    unsigned *inc = cur ? sl.in_near[1] : sl.in_near[0];
+    unsigned *inn = cur ? sl.in_near[0] : sl.in_near[1];
+    int32_t *fq = fcur ? sl.fq[1] : sl.fq[0];
+    // a warp takes 32 near entries at a time and walks their rows together,
     // 32 edge slots per step (hubs spread over the lanes)
-    for (unsigned base = (unsigned)warp * 32u; base < ncur; base += kSsspWarps * 32u) {
+    for (unsigned base = (unsigned)warp * 32u; base < nnear; base += blockDim.x) {
       const unsigned idx = base + (unsigned)lane;
-      int v = -1, b = 0, e = 0;
+      int b = 0, e = 0;
       unsigned dvb = kInfBits;
-      if (idx < ncur) {
-        v = qc[idx];
+      if (idx < nnear) {
+        const int v = qc[idx];
         atomicAnd(inc + (v >> 5), ~(1u << (v & 31)));
         b = __ldg(rowptr + v);
         e = __ldg(rowptr + v + 1);
@@ -186,34 +250,60 @@ __device__ void sssp_block(int32_t n, const int32_t *__restrict__ rowptr, const 
           const unsigned ndb = __float_as_uint(nd);
           const unsigned old = atomicMin(row + u, ndb);
           if (ndb < old) {
-            const unsigned bit = 1u << (u & 31);
-            if (!(atomicOr(inn + (u >> 5), bit) & bit)) qn[atomicAdd(&s_next, 1u)] = u;
+            if (nd < T) {
+              if (set_bit(inn, u)) qn[atomicAdd(&s_nnext, 1u)] = u;
+            } else if (set_bit(sl.in_far, u)) {
+              fq[atomicAdd(&s_nfar, 1u)] = u;
+            }
           }
         }
       }
     }
     __syncthreads();
-    ncur = s_next;
+    nnear = s_nnext;
+    nfar = s_nfar;
     cur ^= 1;
     __syncthreads();
   }
 }
 
+// band width of the near-far search: kDeltaScale times the mean edge length
+constexpr float kDeltaScale = 8.0f;
+
+__global__ void k_mean_length(int32_t n, const int32_t *__restrict__ rowptr, const float *__restrict__ elen,
+                              float *__restrict__ delta) {
+  __shared__ double red[32];
+  const int64_t m2 = rowptr[n];
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < m2; t += blockDim.x) acc += (double)elen[t];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const float mean = m2 > 0 ? (float)(t / (double)m2) : 1.0f;
+    *delta = mean > 0.0f ? kDeltaScale * mean : 1.0f;
+  }
+}
+
 // d_ip mode: block b takes sources b, b + grid, ...; dist rows [k][n]
-__global__ void __launch_bounds__(kSsspThreads) k_sssp_multi(int32_t n, const int32_t *__restrict__ rowptr,
+__global__ void __launch_bounds__(kSsspMultiThreads, 3) k_sssp_multi(int32_t n, const int32_t *__restrict__ rowptr,
                                                              const int32_t *__restrict__ colidx,
                                                              const unsigned *__restrict__ elen, int32_t k,
                                                              const int32_t *__restrict__ sources,
-                                                             unsigned *__restrict__ dist, char *slots,
-                                                             size_t slot_bytes, int32_t *__restrict__ status) {
+                                                             unsigned *__restrict__ dist, const float *__restrict__ delta,
+                                                             char *slots, size_t slot_bytes,
+                                                             int32_t *__restrict__ status) {
   const SsspSlot sl = sssp_slot(slots, slot_bytes, blockIdx.x, n);
+  const float dl = *delta;
   for (int a = blockIdx.x; a < k; a += gridDim.x) {
     const int s = sources[a];
     if (s < 0 || s >= n) {
       if (threadIdx.x == 0) dev_fail(status, SSM_E_ARG);
       continue;
     }
-    sssp_block(n, rowptr, colidx, elen, s, dist + (size_t)a * n, true, sl, status);
+    sssp_block(n, rowptr, colidx, elen, s, dist + (size_t)a * n, true, dl, sl, status);
   }
 }
 
@@ -224,7 +314,8 @@ __global__ void __launch_bounds__(kSsspThreads) k_sssp_maxmin(int32_t n, const i
                                                               const unsigned *__restrict__ elen, int32_t start,
                                                               const unsigned long long *__restrict__ key,
                                                               int32_t *__restrict__ pivot_out,
-                                                              unsigned *__restrict__ mind, char *slots,
+                                                              unsigned *__restrict__ mind,
+                                                              const float *__restrict__ delta, char *slots,
                                                               size_t slot_bytes, bool init,
                                                               int32_t *__restrict__ status) {
   const SsspSlot sl = sssp_slot(slots, slot_bytes, 0, n);
@@ -234,7 +325,7 @@ __global__ void __launch_bounds__(kSsspThreads) k_sssp_maxmin(int32_t n, const i
     return;
   }
   if (threadIdx.x == 0) *pivot_out = s;
-  sssp_block(n, rowptr, colidx, elen, s, mind, init, sl, status);
+  sssp_block(n, rowptr, colidx, elen, s, mind, init, *delta, sl, status);
 }
 
 // *key = max over v of (bits(mind_v) << 32 | (2^32 - 1 - v)): the largest
@@ -265,15 +356,20 @@ __global__ void k_check_finite_rows(int64_t count, const unsigned *__restrict__ 
     }
 }
 
+size_t sssp_ws_bytes(int32_t n, int32_t k) { return 256 + sssp_slot_bytes(n) * (size_t)sssp_blocks(k); }
+
 int launch_sssp(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, int32_t k,
                 const int32_t *sources, float *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int blocks = sssp_blocks(k);
   const size_t sb = sssp_slot_bytes(n);
-  if (ws_bytes < sb * (size_t)blocks) return fail(SSM_E_NOMEM, "sssp: workspace %zu bytes, need %zu", ws_bytes,
-                                                  sb * (size_t)blocks);
-  SSM_TRY_CUDA(cudaMemsetAsync(ws, 0, sb * (size_t)blocks, s));
-  note_launch(), k_sssp_multi<<<blocks, kSsspThreads, 0, s>>>(n, rowptr, colidx, (const unsigned *)elen, k, sources,
-                                                            (unsigned *)dist, (char *)ws, sb, status);
+  if (ws_bytes < sssp_ws_bytes(n, k))
+    return fail(SSM_E_NOMEM, "sssp: workspace %zu bytes, need %zu", ws_bytes, sssp_ws_bytes(n, k));
+  float *delta = (float *)ws;
+  char *slots = (char *)ws + 256;
+  SSM_TRY_CUDA(cudaMemsetAsync(slots, 0, sb * (size_t)blocks, s));
+  note_launch(), k_mean_length<<<1, 1024, 0, s>>>(n, rowptr, elen, delta);
+  note_launch(), k_sssp_multi<<<blocks, kSsspMultiThreads, 0, s>>>(n, rowptr, colidx, (const unsigned *)elen, k, sources,
+                                                            (unsigned *)dist, delta, slots, sb, status);
   const int64_t cnt = (int64_t)k * n;
   note_launch(), k_check_finite_rows<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, (int64_t)num_sms() * 8), 256, 0,
                                        s>>>(cnt, (const unsigned *)dist, status);
@@ -281,7 +377,7 @@ int launch_sssp(int32_t n, const int32_t *rowptr, const int32_t *colidx, const f
   return SSM_OK;
 }
 
-int sssp_blocks(int32_t k) { return std::max(1, std::min<int>(k, num_sms() * 2)); }
+int sssp_blocks(int32_t k) { return std::max(1, std::min<int>(k, num_sms() * 3)); }
 
 // ------------------------------------------------------------ regions and s
 __global__ void k_wregion_keys(int32_t n, int32_t k, const float *__restrict__ dist, int32_t *__restrict__ region,
@@ -420,21 +516,10 @@ __global__ void k_wcounts(int32_t n, int32_t k, const int32_t *__restrict__ rowp
 // ------------------------------------------------------------ the sweep
 constexpr int kWSweepThreads = 256;
 
-// Eq. 4 for one node in FP32 (the library's fast path: FMA contraction
-// allowed) or FP64 (every operation rounded on its own, in the order of the
-// plain FP64 definition: bit-identical to it)
+// Eq. 4 for one node in FP64, every operation rounded on its own in the
+// order of the plain FP64 definition (bit-identical to it)
 template <class T2>
 struct WArith;
-
-template <>
-struct WArith<float2> {
-  using R = float;
-  __device__ static R add(R a, R b) { return a + b; }
-  __device__ static R sub(R a, R b) { return a - b; }
-  __device__ static R mul(R a, R b) { return a * b; }
-  __device__ static R div(R a, R b) { return a / b; }
-  __device__ static R sqrt_(R a) { return sqrtf(a); }
-};
 
 template <>
 struct WArith<double2> {
@@ -544,6 +629,121 @@ __global__ void __launch_bounds__(kWSweepThreads) k_wsweep(int32_t n, const int3
   *done = 0;
 }
 
+// FP32 form: w'_ia = s_ia / d_ia^2 formed once per call into wtab (0 where
+// the pivot term is skipped), then per term one rsqrt and multiply-adds:
+// u = 1/r, B = w' d u, numerator = sum w' x_p + sum B (x_i - x_p) (kept as
+// two sums so that nothing cancels); r = 0 contributes w' x_p only.  A thread
+// owns one node; eight pivots' (d, w') pairs are loaded before they are used.
+__global__ void k_wprep(int64_t count, const float *__restrict__ dist, const uint32_t *__restrict__ s_tab,
+                        float *__restrict__ wtab) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t sc = s_tab[t];
+    const float d = dist[t];
+    wtab[t] = sc ? (float)sc / (d * d) : 0.0f;
+  }
+}
+
+constexpr int kWPrefetch = 8;
+
+__global__ void __launch_bounds__(kWSweepThreads) k_wsweep_f32(int32_t n, const int32_t *__restrict__ rowptr,
+                                                               const int32_t *__restrict__ colidx,
+                                                               const float *__restrict__ elen, int32_t k,
+                                                               const int32_t *__restrict__ pivots,
+                                                               const float *__restrict__ dist,
+                                                               const float *__restrict__ wtab,
+                                                               const float2 *__restrict__ X, float2 *__restrict__ Y,
+                                                               double *__restrict__ part, unsigned *__restrict__ done,
+                                                               double *__restrict__ rel) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  float2 *xp = reinterpret_cast<float2 *>(wsm);
+  for (int a = threadIdx.x; a < k; a += blockDim.x) xp[a] = X[__ldg(pivots + a)];
+  __syncthreads();
+  double dn = 0.0, dd = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 xi = X[i];
+    float wx = 0.f, wy = 0.f, bx = 0.f, by = 0.f, den = 0.f;
+    for (int t = __ldg(rowptr + i); t < __ldg(rowptr + i + 1); ++t) {
+      const float l = __ldg(elen + t);
+      const float w = 1.0f / (l * l);
+      const float2 xj = X[__ldg(colidx + t)];
+      const float dx = xi.x - xj.x, dy = xi.y - xj.y;
+      const float r2 = dx * dx + dy * dy;
+      const float B = r2 > 0.f ? w * l * rsqrtf(r2) : 0.f;
+      wx += w * xj.x;
+      wy += w * xj.y;
+      bx += B * dx;
+      by += B * dy;
+      den += w;
+    }
+    const float *dcol = dist + i;
+    const float *wcol = wtab + i;
+    for (int a0 = 0; a0 < k; a0 += kWPrefetch) {
+      float dq[kWPrefetch], wq[kWPrefetch];
+#pragma unroll
+      for (int q = 0; q < kWPrefetch; ++q) {
+        const bool ok = a0 + q < k;
+        dq[q] = ok ? __ldg(dcol + (size_t)(a0 + q) * n) : 0.f;
+        wq[q] = ok ? __ldg(wcol + (size_t)(a0 + q) * n) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < kWPrefetch; ++q) {
+        if (a0 + q >= k) break;
+        const float2 p = xp[a0 + q];
+        const float w = wq[q];
+        const float dx = xi.x - p.x, dy = xi.y - p.y;
+        const float r2 = dx * dx + dy * dy;
+        const float B = r2 > 0.f ? w * dq[q] * rsqrtf(r2) : 0.f;
+        wx += w * p.x;
+        wy += w * p.y;
+        bx += B * dx;
+        by += B * dy;
+        den += w;
+      }
+    }
+    float2 y = xi;
+    if (den > 0.f) {
+      y.x = (wx + bx) / den;
+      y.y = (wy + by) / den;
+    }
+    Y[i] = y;
+    const double ex = (double)y.x - (double)xi.x, ey = (double)y.y - (double)xi.y;
+    dn += ex * ex + ey * ey;
+    dd += (double)xi.x * (double)xi.x + (double)xi.y * (double)xi.y;
+  }
+  __shared__ double red[2][kWSweepThreads / 32];
+  __shared__ unsigned s_ticket;
+  for (int o = 16; o > 0; o >>= 1) {
+    dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = dn;
+    red[1][threadIdx.x >> 5] = dd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int w = 0; w < kWSweepThreads / 32; ++w) {
+      a0 += red[0][w];
+      a1 += red[1][w];
+    }
+    part[2 * blockIdx.x] = a0;
+    part[2 * blockIdx.x + 1] = a1;
+    __threadfence();
+    s_ticket = atomicAdd(done, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1 || threadIdx.x != 0) return;
+  __threadfence();
+  double a0 = 0.0, a1 = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) {
+    a0 += __ldcg(part + 2 * b);
+    a1 += __ldcg(part + 2 * b + 1);
+  }
+  *rel = a1 > 0.0 ? sqrt(a0) / sqrt(a1) : 0.0;
+  *done = 0;
+}
+
 }  // namespace ssm
 
 // =========================================================== C ABI
@@ -569,7 +769,7 @@ SSM_API int ssm_edge_lengths(int32_t n, int64_t m_in, const int32_t *src, const 
 
 SSM_API size_t ssm_pivot_sssp_workspace(int32_t n, int32_t k) {
   if (n < 1 || k < 1) return 0;
-  return ssm::sssp_slot_bytes(n) * (size_t)ssm::sssp_blocks(k);
+  return ssm::sssp_ws_bytes(n, k);
 }
 
 SSM_API int ssm_pivot_sssp(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, const float *elen,
@@ -586,11 +786,13 @@ namespace ssm {
 struct WmmWs {
   unsigned *mind;
   unsigned long long *keys;
+  float *delta;
   char *slot;
 };
 static size_t carve_wmm(Carver &c, WmmWs &w, int32_t n, int32_t k) {
   w.mind = c.take<unsigned>((size_t)n);
   w.keys = c.take<unsigned long long>((size_t)k);
+  w.delta = c.take<float>(1);
   w.slot = c.take<char>(sssp_slot_bytes(n));
   return c.size();
 }
@@ -619,13 +821,14 @@ SSM_API int ssm_select_pivots_weighted(int32_t n, int64_t m, const int32_t *rowp
   SSM_TRY_CUDA(cudaMemsetAsync(w.keys, 0, (size_t)k * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(w.slot, 0, sssp_slot_bytes(n), s));
   const size_t sb = sssp_slot_bytes(n);
+  note_launch(), k_mean_length<<<1, 1024, 0, s>>>(n, rowptr, elen, w.delta);
   note_launch(), k_sssp_maxmin<<<1, kSsspThreads, 0, s>>>(n, rowptr, colidx, (const unsigned *)elen, start, nullptr,
-                                                        pivots, w.mind, w.slot, sb, true, status);
+                                                        pivots, w.mind, w.delta, w.slot, sb, true, status);
   const unsigned ab = (unsigned)std::max(1, std::min((n + 255) / 256, num_sms() * 4));
   for (int a = 1; a < k; ++a) {
     note_launch(), k_wmm_argmax<<<ab, 256, 0, s>>>(n, w.mind, w.keys + a, status);
     note_launch(), k_sssp_maxmin<<<1, kSsspThreads, 0, s>>>(n, rowptr, colidx, (const unsigned *)elen, 0, w.keys + a,
-                                                          pivots + a, w.mind, w.slot, sb, false, status);
+                                                          pivots + a, w.mind, w.delta, w.slot, sb, false, status);
   }
   if (k == 1) note_launch(), k_wmm_argmax<<<ab, 256, 0, s>>>(n, w.mind, w.keys, status);  // reachability check
   SSM_TRY_CUDA(cudaGetLastError());
@@ -685,20 +888,22 @@ struct WSweepWs {
   void *buf;
   double *part;
   unsigned *done;
+  float *wtab;
 };
-static size_t carve_wsweep(Carver &c, WSweepWs &w, int32_t n, int32_t precision) {
+static size_t carve_wsweep(Carver &c, WSweepWs &w, int32_t n, int32_t k, int32_t precision) {
   w.buf = c.take<char>((size_t)n * (precision == 64 ? 16 : 8));
   w.part = c.take<double>(2 * (size_t)wsweep_blocks(n));
   w.done = c.take<unsigned>(1);
+  w.wtab = precision == 32 ? c.take<float>((size_t)k * n) : nullptr;
   return c.size();
 }
 }  // namespace ssm
 
-SSM_API size_t ssm_iterate_weighted_workspace(int32_t n, int32_t precision) {
-  if (n < 1 || (precision != 32 && precision != 64)) return 0;
+SSM_API size_t ssm_iterate_weighted_workspace(int32_t n, int32_t k, int32_t precision) {
+  if (n < 1 || k < 1 || (precision != 32 && precision != 64)) return 0;
   ssm::Carver c(nullptr, 0);
   ssm::WSweepWs w;
-  return ssm::carve_wsweep(c, w, n, precision);
+  return ssm::carve_wsweep(c, w, n, k, precision);
 }
 
 SSM_API int ssm_iterate_weighted(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen,
@@ -714,14 +919,22 @@ SSM_API int ssm_iterate_weighted(int32_t n, const int32_t *rowptr, const int32_t
   if ((size_t)k * esz > 200 * 1024) return fail(SSM_E_ARG, "ssm_iterate_weighted: k too large for the pivot stage");
   Carver c(ws, ws_bytes);
   WSweepWs w;
-  carve_wsweep(c, w, n, precision);
+  carve_wsweep(c, w, n, k, precision);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_iterate_weighted: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(w.done, 0, sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(rel_change, 0, sizeof(double), s));
   const int nb = wsweep_blocks(n);
   const size_t smem = (size_t)k * esz;
-  if (precision == 64) SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_wsweep<double2>));
-  else SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_wsweep<float2>));
+  if (precision == 64) {
+    SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_wsweep<double2>));
+  } else {
+    SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_wsweep_f32));
+    if (iters > 0) {
+      const int64_t cnt = (int64_t)k * n;
+      note_launch(), k_wprep<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
+          cnt, dist, s_tab, w.wtab);
+    }
+  }
   void *bufs[2] = {pos, w.buf};
   for (int it = 0; it < iters; ++it) {
     void *in = bufs[it & 1], *out = bufs[(it & 1) ^ 1];
@@ -730,9 +943,9 @@ SSM_API int ssm_iterate_weighted(int32_t n, const int32_t *rowptr, const int32_t
                                                                   (const double2 *)in, (double2 *)out, w.part, w.done,
                                                                   rel_change);
     else
-      note_launch(), k_wsweep<float2><<<nb, kWSweepThreads, smem, s>>>(n, rowptr, colidx, elen, k, pivots, dist, s_tab,
-                                                                 (const float2 *)in, (float2 *)out, w.part, w.done,
-                                                                 rel_change);
+      note_launch(), k_wsweep_f32<<<nb, kWSweepThreads, smem, s>>>(n, rowptr, colidx, elen, k, pivots, dist, w.wtab,
+                                                             (const float2 *)in, (float2 *)out, w.part, w.done,
+                                                             rel_change);
   }
   if (iters & 1) SSM_TRY_CUDA(cudaMemcpyAsync(pos, w.buf, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
   SSM_TRY_CUDA(cudaGetLastError());
