@@ -165,11 +165,11 @@ def run_gpu(args):
         mark(2)
         dip = ssm.ssm_pivot_bfs(g, piv, check=False)
         mark(3)
-        cnt_len = ssm.ssm_aggregate_size(dip)
+        cnt_len, dmax = ssm.ssm_aggregate_size(dip, with_dmax=True)
         region, off, cnt = ssm.ssm_aggregate(dip, cnt_len, check=False)
         mark(4)
         pos, _ = ssm.ssm_pivotmds(g, dip, 32, True, check=False)
-        P = ssm.Pivots(k, piv, dip, region, off, cnt)
+        P = ssm.Pivots(k, piv, dip, region, off, cnt, dmax)
         mark(5)
         ssm.ssm_iterate(g, P, pos, iters, check=False)
         mark(6)

@@ -98,14 +98,16 @@ int ssm_check(const int32_t *status, cudaStream_t stream);
  * both directions stored, self-loops and repeated edges dropped, rows
  * sorted ascending, then checks that G is connected (the paper keeps only
  * the largest component, Section 4 "Data"; callers pass that component).
- * rowptr has n+1 entries, colidx room for 2*m_in.  *m_out (host) receives m.
- * Synchronous.  Errors are returned directly: SSM_E_GRAPH for an endpoint
+ * rowptr has n+1 entries, colidx room for 2*m_in.  *m_out (host) receives m;
+ * row_classes (host int32[2], may be NULL) the number of rows with 33 to
+ * 1024 entries and with more than 1024 (the sweep's launch shape: pass them
+ * to ssm_iterate as hints[1], hints[2]).  Synchronous.  Errors are returned directly: SSM_E_GRAPH for an endpoint
  * outside 0..n-1, SSM_E_DISCONNECTED if some node is unreachable from node 0.
  * Requires 1 <= n, 0 <= m_in, 2*m_in < 2^31.
  * ------------------------------------------------------------------- */
 size_t ssm_build_graph_workspace(int32_t n, int64_t m_in);
 int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst,
-                    int32_t *rowptr, int32_t *colidx, int64_t *m_out,
+                    int32_t *rowptr, int32_t *colidx, int64_t *m_out, int32_t *row_classes,
                     void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
@@ -166,12 +168,13 @@ int ssm_pivot_bfs(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *co
  *   cnt[cnt_off[a] + t] = |{ i in R(a) : d_ia <= t }|, t = 0..ecc_a,
  * so that w'_ia = s / d_ia^2 with s = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)].
  * ssm_aggregate_size (synchronous) returns in *cnt_len (host) the table length
- * sum_a (ecc_a + 1); ssm_aggregate fills region[n] int32, cnt_off[k+1] int32,
+ * sum_a (ecc_a + 1) and in *dip_max (host, may be NULL) the largest d_ia
+ * (ssm_iterate's hints[0]); ssm_aggregate fills region[n] int32, cnt_off[k+1] int32,
  * cnt[cnt_len] uint32.  Workspace: ssm_aggregate_workspace(k) bytes for both.
  * Device error SSM_E_ARG if cnt_len does not match the table.
  * ------------------------------------------------------------------- */
 size_t ssm_aggregate_workspace(int32_t k);
-int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len,
+int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len, int32_t *dip_max,
                        void *ws, size_t ws_bytes, cudaStream_t stream);
 int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, int32_t *cnt_off,
                   uint32_t *cnt, int64_t cnt_len, int32_t *status,
@@ -272,19 +275,26 @@ int ssm_gram(int32_t n, int32_t k, const uint16_t *dip, uint64_t *g_lo, uint64_t
  * *rel_change (device double, the last computed change).  cnt_off and cnt are
  * the tables of ssm_aggregate, cnt_len = cnt_off[k] (from ssm_aggregate_size);
  * m is the edge count (colidx has 2m entries).  1 <= iters, 1 <= k <= 4096.
- * Precision 32 waits once for `stream`
- * (after its first kernels) to read the largest d_ip entry and the number of
- * rows longer than 32 and 1024 entries on the host: when k * (max d + 1)
- * weight pairs fit in shared memory the sweep uses a full (w', w' d) table,
- * otherwise a table of s clamped at 2 ecc_a + 2; the neighbour sums of each
- * iteration are taken by one thread, warp or block per row by length.
+ * Precision 32 chooses its form on the host from three numbers, hints[0] =
+ * the largest d_ip entry, hints[1] / hints[2] = the rows with 33..1024 /
+ * more than 1024 entries: when k * (max d + 1) weight pairs fit in shared
+ * memory the sweep uses a full (w', w' d) table, otherwise a table of s
+ * clamped at 2 ecc_a + 2; the neighbour sums of each iteration are taken by
+ * one thread, warp or block per row by length.  hints (host int32[3]) come
+ * from ssm_aggregate_size (dip_max) and ssm_build_graph (row_classes), both
+ * synchronous anyway, or from ssm_iterate_hints (synchronous); with hints
+ * the call is asynchronous, with hints == NULL it computes them and waits
+ * once for `stream`.  Wrong hints give SSM_E_ARG where they are out of
+ * range and wrong results otherwise. 
  * ------------------------------------------------------------------- */
 size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cnt_len, int32_t precision);
 int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                 const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off,
                 const uint32_t *cnt, int64_t cnt_len, void *pos, int32_t precision, int32_t iters,
                 double tol, int32_t *iters_done, double *rel_change, int32_t *status,
-                void *ws, size_t ws_bytes, cudaStream_t stream);
+                const int32_t *hints, void *ws, size_t ws_bytes, cudaStream_t stream);
+int ssm_iterate_hints(int32_t n, const int32_t *rowptr, int32_t k, const uint16_t *dip, int32_t *hints,
+                      void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
  * The sparse model's update of Eq. 4 in the paper's own order (Algorithm 1

@@ -24,7 +24,7 @@ __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
     "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
     "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
-    "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions", "ssm_procrustes", "ssm_hull_error", "ssm_gabriel_jaccard",
+    "ssm_iterate_hints", "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions", "ssm_procrustes", "ssm_hull_error", "ssm_gabriel_jaccard",
     "WGraph", "ssm_build_wgraph", "ssm_pivot_sssp", "ssm_select_pivots_weighted", "ssm_weighted_counts",
     "ssm_pivotmds_weighted", "ssm_iterate_weighted", "ssm_stress_weighted", "layout_weighted",
 ]
@@ -64,7 +64,7 @@ def lib():
                 "ssm_last_sweep_config": (None, [v]),
                 "ssm_check": (ctypes.c_int, [v, v]),
                 "ssm_build_graph_workspace": (sz, [i32, i64]),
-                "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, sz, v]),
+                "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, v, sz, v]),
                 "ssm_select_pivots_workspace": (sz, [i32, i64]),
                 "ssm_select_pivots": (ctypes.c_int, [i32, i64, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_kmeans_pivots_workspace": (sz, [i32, i32]),
@@ -72,7 +72,7 @@ def lib():
                 "ssm_pivot_bfs_workspace": (sz, [i32, i64, i32]),
                 "ssm_pivot_bfs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, sz, v]),
                 "ssm_aggregate_workspace": (sz, [i32]),
-                "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, sz, v]),
+                "ssm_aggregate_size": (ctypes.c_int, [i32, i32, v, v, v, v, sz, v]),
                 "ssm_aggregate": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, sz, v]),
                 "ssm_aggregate_noalloc": (ctypes.c_int, [i32, i32, v, v, v, v, i64, v, v, v]),
                 "ssm_regions_smallest_workspace": (sz, [i32]),
@@ -85,7 +85,8 @@ def lib():
                 "ssm_batch_iterate": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, i32, v, i32, v, v, v, sz, v]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
-                "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, sz, v]),
+                "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, v, sz, v]),
+                "ssm_iterate_hints": (ctypes.c_int, [i32, v, i32, v, v, v, sz, v]),
                 "ssm_iterate_gs_workspace": (sz, [i32]),
                 "ssm_iterate_gs": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, v, i32, v, v, v, sz, v]),
                 "ssm_full_iterate_workspace": (sz, [i32, i32]),
@@ -177,6 +178,7 @@ class Graph:
     m: int
     rowptr: torch.Tensor  # int32 [n+1]
     colidx: torch.Tensor  # int32 [2m]
+    row_classes: tuple | None = None  # rows with 33..1024 and > 1024 entries (from ssm_build_graph)
 
 
 @dataclass
@@ -187,6 +189,7 @@ class Pivots:
     region: torch.Tensor   # int32 [n]
     cnt_off: torch.Tensor  # int32 [k+1]
     cnt: torch.Tensor      # uint32 [cnt_off[k]]
+    dmax: int | None = None  # largest d_ip entry (from ssm_aggregate_size), a hint for ssm_iterate
 
 
 def ssm_build_graph(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> Graph:
@@ -201,9 +204,10 @@ def ssm_build_graph(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -
     colidx = torch.empty(max(2 * m_in, 1), dtype=torch.int32, device=dev)
     ws = _ws(L.ssm_build_graph_workspace(n, m_in), dev)
     m = ctypes.c_int64(0)
-    _rc(L.ssm_build_graph(n, m_in, _ptr(src), _ptr(dst), _ptr(rowptr), _ptr(colidx), ctypes.byref(m), _ptr(ws),
-                          ws.numel(), _stream(stream)), "ssm_build_graph")
-    return Graph(n, int(m.value), rowptr, colidx[: 2 * m.value])
+    rc_ = (ctypes.c_int32 * 2)()
+    _rc(L.ssm_build_graph(n, m_in, _ptr(src), _ptr(dst), _ptr(rowptr), _ptr(colidx), ctypes.byref(m),
+                          ctypes.cast(rc_, ctypes.c_void_p), _ptr(ws), ws.numel(), _stream(stream)), "ssm_build_graph")
+    return Graph(n, int(m.value), rowptr, colidx[: 2 * m.value], row_classes=(int(rc_[0]), int(rc_[1])))
 
 
 def ssm_select_pivots(g: Graph, k: int, start: int = 0, stream=None, check: bool = True) -> torch.Tensor:
@@ -252,14 +256,16 @@ def ssm_pivot_bfs(g: Graph, pivots: torch.Tensor, stream=None, check: bool = Tru
     return dip
 
 
-def ssm_aggregate_size(dip: torch.Tensor, stream=None) -> int:
+def ssm_aggregate_size(dip: torch.Tensor, stream=None, with_dmax: bool = False):
+    """Length of the count table (synchronous); with_dmax: (length, largest d_ip entry)."""
     L = lib()
     k, n = dip.shape
     ws = _ws(L.ssm_aggregate_workspace(k), dip.device)
     out = ctypes.c_int64(0)
-    _rc(L.ssm_aggregate_size(n, k, _ptr(dip), ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)),
-        "ssm_aggregate_size")
-    return int(out.value)
+    dm = ctypes.c_int32(0)
+    _rc(L.ssm_aggregate_size(n, k, _ptr(dip), ctypes.byref(out), ctypes.byref(dm), _ptr(ws), ws.numel(),
+                             _stream(stream)), "ssm_aggregate_size")
+    return (int(out.value), int(dm.value)) if with_dmax else int(out.value)
 
 
 def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, check: bool = True):
@@ -383,12 +389,27 @@ def ssm_iterate(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, tol: float =
     precision = 64 if pos.dtype == torch.float64 else 32
     if work is None:
         work = IterateWorkspace(g.n, g.m, p.k, p.cnt.numel(), precision, pos.device)
+    hints = None
+    if p.dmax is not None and g.row_classes is not None:  # no host wait inside the call
+        hints = (ctypes.c_int32 * 3)(int(p.dmax), int(g.row_classes[0]), int(g.row_classes[1]))
     _rc(L.ssm_iterate(g.n, g.m, _ptr(g.rowptr), _ptr(g.colidx), p.k, _ptr(p.pivots), _ptr(p.dip), _ptr(p.cnt_off),
                       _ptr(p.cnt), p.cnt.numel(), _ptr(pos), precision, iters, float(tol), _ptr(work.iters_done), _ptr(work.rel),
-                      _ptr(work.status), _ptr(work.ws), work.ws.numel(), _stream(stream)), "ssm_iterate")
+                      _ptr(work.status), ctypes.cast(hints, ctypes.c_void_p) if hints is not None else None,
+                      _ptr(work.ws), work.ws.numel(), _stream(stream)), "ssm_iterate")
     if check:
         ssm_check(work.status, "ssm_iterate", stream)
     return work.iters_done, work.rel
+
+
+def ssm_iterate_hints(g: Graph, dip: torch.Tensor, stream=None) -> tuple:
+    """(largest d_ip entry, rows with 33..1024 entries, rows with more): ssm_iterate's hints (synchronous)."""
+    L = lib()
+    k = dip.shape[0]
+    ws = _ws(256, dip.device)
+    h = (ctypes.c_int32 * 3)()
+    _rc(L.ssm_iterate_hints(g.n, _ptr(g.rowptr), k, _ptr(dip), ctypes.cast(h, ctypes.c_void_p), _ptr(ws), ws.numel(),
+                            _stream(stream)), "ssm_iterate_hints")
+    return int(h[0]), int(h[1]), int(h[2])
 
 
 def ssm_iterate_gs(g: Graph, p: Pivots, pos: torch.Tensor, iters: int, stream=None, check: bool = True):
@@ -589,9 +610,10 @@ def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, devic
     if sampler == "kmeans":
         piv, _, _ = ssm_kmeans_pivots(dip, piv, kmeans_iters, stream)
         dip = ssm_pivot_bfs(g, piv, stream)
-    region, off, cnt = ssm_aggregate(dip, stream=stream)
+    cnt_len, dmax = ssm_aggregate_size(dip, stream, with_dmax=True)
+    region, off, cnt = ssm_aggregate(dip, cnt_len, stream=stream)
     pos, eig = ssm_pivotmds(g, dip, precision, True, stream)
-    return g, Pivots(k, piv, dip, region, off, cnt), pos, eig
+    return g, Pivots(k, piv, dip, region, off, cnt, dmax), pos, eig
 
 
 def layout(n: int, src, dst, k: int = 200, iters: int = 100, tol: float = 0.0, start: int = 0,
@@ -625,7 +647,7 @@ def ssm_build_wgraph(n: int, src: torch.Tensor, dst: torch.Tensor, lengths: torc
                            _ptr(elen), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "ssm_edge_lengths")
     if check:
         ssm_check(st, "ssm_edge_lengths", stream)
-    return WGraph(g.n, g.m, g.rowptr, g.colidx, elen[: 2 * g.m])
+    return WGraph(g.n, g.m, g.rowptr, g.colidx, row_classes=g.row_classes, elen=elen[: 2 * g.m])
 
 
 def ssm_pivot_sssp(g: WGraph, sources: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:

@@ -14,9 +14,12 @@ namespace ssm {
 constexpr int kAggThreads = 256;
 
 // one thread per node: nearest pivot (ties to the lowest index) and the
-// per-pivot maximum distance over its region
+// per-pivot maximum distance over its region; dmax (may be null) receives
+// the largest entry of the whole table
 __global__ void __launch_bounds__(kAggThreads) k_region_ecc(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
-                                                            int32_t *__restrict__ region, unsigned *__restrict__ ecc) {
+                                                            int32_t *__restrict__ region, unsigned *__restrict__ ecc,
+                                                            unsigned *__restrict__ dmax) {
+  unsigned worst = 0u;
   // the loop runs over whole warps so that lanes past n can join the warp-wide
   // aggregation below
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -33,11 +36,13 @@ __global__ void __launch_bounds__(kAggThreads) k_region_ecc(int32_t n, int32_t k
 #pragma unroll
         for (int q = 0; q < 8; ++q) dq[q] = a0 + q < k ? (unsigned)__ldg(col + (size_t)(a0 + q) * n) : 0xFFFFFFFFu;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < 8; ++q) {
           if (dq[q] < best) {
             best = dq[q];
             arg = a0 + q;
           }
+          if (a0 + q < k) worst = max(worst, dq[q]);
+        }
       }
       if (region) region[i] = arg;
     }
@@ -50,6 +55,10 @@ __global__ void __launch_bounds__(kAggThreads) k_region_ecc(int32_t n, int32_t k
       if ((peers >> src) & 1u) m = max(m, t);
     }
     if (live && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicMax(ecc + arg, m);
+  }
+  if (dmax) {
+    for (int o = 16; o > 0; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0 && worst) atomicMax(dmax, worst);
   }
 }
 
@@ -274,25 +283,28 @@ static int grid_for(int64_t items, int threads) {
 SSM_API size_t ssm_aggregate_workspace(int32_t k) {
   ssm::Carver c(nullptr, 0);
   c.take<unsigned>(k > 0 ? k : 1);
-  c.take<long long>(1);
+  c.take<long long>(2);
   return c.size();
 }
 
-SSM_API int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len, void *ws,
-                               size_t ws_bytes, cudaStream_t s) {
+SSM_API int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_t *cnt_len, int32_t *dip_max,
+                               void *ws, size_t ws_bytes, cudaStream_t s) {
   using namespace ssm;
   if (n < 1 || k < 1 || !dip || !cnt_len || !ws) return fail(SSM_E_ARG, "ssm_aggregate_size: bad argument");
   Carver c(ws, ws_bytes);
   unsigned *ecc = c.take<unsigned>(k);
-  long long *len = c.take<long long>(1);
+  long long *len = c.take<long long>(2);  // the length, then the largest entry
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate_size: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc);
+  SSM_TRY_CUDA(cudaMemsetAsync(len, 0, 2 * sizeof(long long), s));
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc,
+                                                                              (unsigned *)(len + 1));
   note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
-  long long h = 0;
-  SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));
+  long long h[2] = {0, 0};
+  SSM_TRY_CUDA(cudaMemcpyAsync(h, len, sizeof h, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
-  *cnt_len = h;
+  *cnt_len = h[0];
+  if (dip_max) *dip_max = (int32_t)(unsigned)(h[1] & 0xFFFFFFFFll);
   return SSM_OK;
 }
 
@@ -308,7 +320,7 @@ SSM_API int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *re
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)cnt_len * sizeof(uint32_t), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, nullptr);
   note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
   note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
   note_launch(), k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
@@ -360,7 +372,7 @@ SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int
   if (rc) return rc;
   long long *len = reinterpret_cast<long long *>(ecc + kNoAllocMaxPivots);
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc);
+  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, nullptr);
   note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
   long long h = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));

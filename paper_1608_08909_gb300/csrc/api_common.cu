@@ -96,3 +96,22 @@ SSM_API unsigned long long ssm_set_wait_limit_ns(unsigned long long ns) {
   if (ns > 0xFFFFFFFFull) ns = 0xFFFFFFFFull;
   return ssm::g_wait_limit_ns.exchange((unsigned)ns);
 }
+
+namespace ssm {
+__global__ void k_row_classes(int32_t n, const int32_t *__restrict__ rowptr, unsigned *__restrict__ counts) {
+  unsigned mid = 0, lng = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int deg = rowptr[i + 1] - rowptr[i];
+    mid += (deg > kShortDeg && deg <= kMidDeg) ? 1u : 0u;
+    lng += deg > kMidDeg ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mid += __shfl_xor_sync(0xffffffffu, mid, o);
+    lng += __shfl_xor_sync(0xffffffffu, lng, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mid) atomicAdd(counts, mid);
+    if (lng) atomicAdd(counts + 1, lng);
+  }
+}
+}  // namespace ssm

@@ -58,6 +58,12 @@ struct BarrierState {
 
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 
+// Neighbour rows of the sweep by length: up to kShortDeg entries one thread,
+// up to kMidDeg one warp, longer rows one block (the graph builder counts
+// the two longer classes for the sweep's launch shape).
+constexpr int kShortDeg = 32;
+constexpr int kMidDeg = 1024;
+
 // Zeroes *b on `stream` and, while a shorter wait limit is set, stores it.
 int reset_barrier(BarrierState *b, cudaStream_t stream);
 
@@ -129,6 +135,9 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *b, int32_t *status) {
   __syncthreads();
   return s_ok != 0;
 }
+
+// counts[0] += rows with kShortDeg < length <= kMidDeg, counts[1] += longer rows
+__global__ void k_row_classes(int32_t n, const int32_t *__restrict__ rowptr, unsigned *__restrict__ counts);
 
 // All 32 lanes must call this together.  Lanes with pred append `val` to
 // q[*qcount ...]; one atomic per warp.

@@ -208,7 +208,7 @@ static size_t carve_build(Carver &c, BuildWs &w, int32_t n, int64_t m_in) {
   w.big_count = c.take<unsigned>(1);
   w.status = c.take<int32_t>(2);
   w.parent = c.take<int>(n);
-  w.roots = c.take<unsigned>(1);
+  w.roots = c.take<unsigned>(4);  // components, then the two row classes
   return c.size();
 }
 
@@ -222,7 +222,8 @@ SSM_API size_t ssm_build_graph_workspace(int32_t n, int64_t m_in) {
 }
 
 SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const int32_t *dst, int32_t *rowptr,
-                            int32_t *colidx, int64_t *m_out, void *ws, size_t ws_bytes, cudaStream_t s) {
+                            int32_t *colidx, int64_t *m_out, int32_t *row_classes, void *ws, size_t ws_bytes,
+                            cudaStream_t s) {
   using namespace ssm;
   if (n < 1 || m_in < 0 || !rowptr || !colidx || !m_out || !ws || (m_in > 0 && (!src || !dst)))
     return fail(SSM_E_ARG, "ssm_build_graph: null pointer or bad size (n=%d, m_in=%lld)", n, (long long)m_in);
@@ -261,13 +262,20 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
   *m_out = uniq / 2;
   // connectivity: union-find over the final CSR
-  SSM_TRY_CUDA(cudaMemsetAsync(w.roots, 0, sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.roots, 0, 4 * sizeof(unsigned), s));
   note_launch(), k_uf_init<<<nblocks, 256, 0, s>>>(n, w.parent);
   note_launch(), k_uf_link<<<eblocks, 256, 0, s>>>(m_in, src, dst, w.parent);
   note_launch(), k_uf_roots<<<nblocks, 256, 0, s>>>(n, w.parent, w.roots);
-  unsigned roots = 0;
-  SSM_TRY_CUDA(cudaMemcpyAsync(&roots, w.roots, sizeof roots, cudaMemcpyDeviceToHost, s));
+  // the sweep's row classes, read back with the component count
+  if (row_classes) note_launch(), k_row_classes<<<nblocks, 256, 0, s>>>(n, rowptr, w.roots + 1);
+  unsigned hr[3] = {0, 0, 0};
+  SSM_TRY_CUDA(cudaMemcpyAsync(hr, w.roots, sizeof hr, cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  const unsigned roots = hr[0];
+  if (row_classes) {
+    row_classes[0] = (int32_t)hr[1];
+    row_classes[1] = (int32_t)hr[2];
+  }
   if (roots != 1) return fail(SSM_E_DISCONNECTED, "ssm_build_graph: %u connected components", roots);
   return SSM_OK;
 }

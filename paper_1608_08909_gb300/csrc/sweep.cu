@@ -53,8 +53,6 @@
 namespace ssm {
 
 constexpr int kSweepThreads = 256;
-constexpr int kShortDeg = 32;   // neighbour rows up to this length: one thread
-constexpr int kMidDeg = 1024;   // up to this length: one warp; longer rows: one block
 constexpr size_t kSmemBudget = 200 * 1024;
 constexpr int kFullPlane = 6112;  // full-table mode: k (max d + 1) <= this; w and w d in two planes of this many floats
 constexpr unsigned kFullPlaneBytes = kFullPlane * 4u;
@@ -885,8 +883,8 @@ SSM_API size_t ssm_iterate_workspace(int32_t n, int64_t m, int32_t k, int64_t cn
 SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx, int32_t k,
                         const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
                         int64_t cnt_len, void *pos, int32_t precision, int32_t iters, double tol,
-                        int32_t *iters_done, double *rel_change, int32_t *status, void *ws, size_t ws_bytes,
-                        cudaStream_t s) {
+                        int32_t *iters_done, double *rel_change, int32_t *status, const int32_t *hints, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
   using namespace ssm;
   if (n < 1 || m < 0 || !rowptr || !colidx || !pivots || !dip || !cnt_off || !cnt || !pos || !iters_done ||
       !rel_change || !status || !ws)
@@ -929,13 +927,20 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   } else {
     // the largest distance decides between the full (w, w d) table and the
     // clamped s table; the row lengths decide the neighbour-kernel grid
+    // (from the caller's hints when given; otherwise read back once)
     SSM_TRY_CUDA(cudaMemsetAsync(w.meta, 0, 4 * sizeof(unsigned), s));
-    const int64_t kn = (int64_t)k * n;
-    note_launch(), k_dip_max<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kn + 255) / 256, sms * 8)), 256, 0, s>>>(
-        kn, dip, w.meta);
     note_launch(), k_nbr_classify<<<nb, 256, 0, s>>>(n, rowptr, w.meta + 1, w.mid_rows, w.long_rows);
-    SSM_TRY_CUDA(cudaMemcpyAsync(meta, w.meta, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SSM_TRY_CUDA(cudaStreamSynchronize(s));
+    if (hints) {
+      if (hints[0] < 0 || hints[0] > 65534 || hints[1] < 0 || hints[2] < 0 || hints[1] + hints[2] > n)
+        return fail(SSM_E_ARG, "ssm_iterate: bad hints");
+      for (int q = 0; q < 3; ++q) meta[q] = (unsigned)hints[q];
+    } else {
+      const int64_t kn = (int64_t)k * n;
+      note_launch(), k_dip_max<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kn + 255) / 256, sms * 8)), 256, 0,
+                                 s>>>(kn, dip, w.meta);
+      SSM_TRY_CUDA(cudaMemcpyAsync(meta, w.meta, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      SSM_TRY_CUDA(cudaStreamSynchronize(s));
+    }
     const unsigned dmax = meta[0];
     const bool full = (size_t)k * ((size_t)dmax + 1) <= (size_t)kFullPlane;
     A.dmax = (int32_t)dmax;
@@ -1026,6 +1031,26 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
   else
     note_launch(), k_copy_back_if_odd<float2><<<cb, 256, 0, s>>>(n, iters_done, (const float2 *)w.tmp, (float2 *)pos);
   SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}
+
+SSM_API int ssm_iterate_hints(int32_t n, const int32_t *rowptr, int32_t k, const uint16_t *dip, int32_t *hints,
+                              void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (n < 1 || k < 1 || !rowptr || !dip || !hints || !ws) return fail(SSM_E_ARG, "ssm_iterate_hints: bad argument");
+  if (ws_bytes < 256) return fail(SSM_E_NOMEM, "ssm_iterate_hints: workspace %zu bytes, need 256", ws_bytes);
+  unsigned *meta = (unsigned *)ws;
+  const int sms = num_sms();
+  SSM_TRY_CUDA(cudaMemsetAsync(meta, 0, 4 * sizeof(unsigned), s));
+  const int64_t kn = (int64_t)k * n;
+  note_launch(), k_dip_max<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kn + 255) / 256, sms * 8)), 256, 0, s>>>(
+      kn, dip, meta);
+  note_launch(), k_row_classes<<<(int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8), 256, 0, s>>>(
+      n, rowptr, meta + 1);
+  unsigned h[3] = {0, 0, 0};
+  SSM_TRY_CUDA(cudaMemcpyAsync(h, meta, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < 3; ++q) hints[q] = (int32_t)h[q];
   return SSM_OK;
 }
 

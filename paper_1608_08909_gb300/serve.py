@@ -88,7 +88,7 @@ def run_layout_job(job: LayoutJob, stream, device="cuda") -> LayoutResult:
     """The whole pipeline for one request on `stream` (blocks the calling thread)."""
     import torch
 
-    from . import (Pivots, ssm_aggregate, ssm_build_graph, ssm_iterate, ssm_pivot_bfs, ssm_pivotmds,
+    from . import (Pivots, ssm_aggregate, ssm_aggregate_size, ssm_build_graph, ssm_iterate, ssm_pivot_bfs, ssm_pivotmds,
                    ssm_select_pivots, ssm_stress)
 
     k = min(job.k, job.n)
@@ -99,9 +99,10 @@ def run_layout_job(job: LayoutJob, stream, device="cuda") -> LayoutResult:
         del src, dst
         piv = ssm_select_pivots(g, k, job.start, stream)
         dip = ssm_pivot_bfs(g, piv, stream)
-        region, off, cnt = ssm_aggregate(dip, stream=stream)
+        cnt_len, dmax = ssm_aggregate_size(dip, stream, with_dmax=True)
+        region, off, cnt = ssm_aggregate(dip, cnt_len, stream=stream)
         pos, eig = ssm_pivotmds(g, dip, 32, True, stream)
-        ssm_iterate(g, Pivots(k, piv, dip, region, off, cnt), pos, job.iters, stream=stream)
+        ssm_iterate(g, Pivots(k, piv, dip, region, off, cnt, dmax), pos, job.iters, stream=stream)
         stress = None
         if job.stress_sources > 0:
             out, _ = ssm_stress(g, pos, job.stress_sources, job.stress_targets, job.seed, stream)

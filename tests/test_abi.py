@@ -45,7 +45,9 @@ def test_status_strings_and_workspace_queries():
     lambda L: L.ssm_select_pivots(10, 9, None, None, 3, 0, None, None, None, 0, None),
     lambda L: L.ssm_pivot_bfs(10, 9, None, None, 3, None, None, None, None, 0, None),
     lambda L: L.ssm_iterate(10, 9, None, None, 3, None, None, None, None, 3, None, 32, 1, 0.0, None, None, None,
-                            None, 0, None),
+                            None, None, 0, None),
+    lambda L: L.ssm_iterate_hints(10, None, 3, None, None, None, 0, None),
+    lambda L: L.ssm_build_graph(0, 5, None, None, None, None, None, None, None, 0, None),
     lambda L: L.ssm_stress(1, 0, None, None, None, 32, 0, 0, 0, None, None, None, None, 0, None),
     lambda L: L.ssm_pivotmds(10, None, None, 1, None, None, 32, 0, None, None, None, 0, None),
 ])

@@ -604,3 +604,50 @@ def test_pipeline_grid32_end_to_end():
     assert _norm_err(pos.cpu().numpy(), opos) < 1e-8
     out, _ = ssm.ssm_stress(g, pos)
     np.testing.assert_allclose(out.cpu().numpy(), O.full_stress(prep.g, opos), rtol=1e-8)
+
+
+# ------------------------------------------------------------------ hints: no host wait in the sweep
+
+@pytest.mark.parametrize("name,k", [("rgg", 100), ("ba", 64), ("messy", 95), ("path", 7)])
+def test_iterate_hints_from_the_synchronous_calls(name, k):
+    """The largest distance from ssm_aggregate_size and the row classes from
+    ssm_build_graph equal what ssm_iterate_hints computes, and the sweep
+    gives the same bits with and without them."""
+    n, s, d = GRAPHS[name]()
+    g, P, pos, _ = ssm.prepare(n, s, d, k)
+    assert P.dmax is not None and g.row_classes is not None
+    assert ssm.ssm_iterate_hints(g, P.dip) == (P.dmax, g.row_classes[0], g.row_classes[1])
+    deg = np.diff(g.rowptr.cpu().numpy())
+    assert g.row_classes == (int(((deg > 32) & (deg <= 1024)).sum()), int((deg > 1024).sum()))
+    assert P.dmax == int(P.dip.max().item())
+    a, b = pos.clone(), pos.clone()
+    ssm.ssm_iterate(g, P, a, 3)
+    cfg_a = ssm.ssm_last_sweep_config()
+    P0 = ssm.Pivots(P.k, P.pivots, P.dip, P.region, P.cnt_off, P.cnt)  # no hints: computed inside
+    ssm.ssm_iterate(g, P0, b, 3)
+    assert ssm.ssm_last_sweep_config() == cfg_a
+    assert torch.equal(a, b)
+
+
+def test_iterate_with_hints_returns_before_the_stream_drains():
+    """With hints the FP32 call only enqueues: it returns while a half-second
+    kernel queued before it still runs; without hints it waits once."""
+    import time
+
+    n, s, d = GRAPHS["rgg"]()
+    g, P, pos, _ = ssm.prepare(n, s, d, 50)
+    ssm.ssm_iterate(g, P, pos.clone(), 1)  # first-use costs outside the timing
+    torch.cuda.synchronize()
+    cycles = 1_000_000_000  # about half a second at the GB300's 2 GHz SM clock
+    torch.cuda._sleep(cycles)
+    t0 = time.perf_counter()
+    ssm.ssm_iterate(g, P, pos.clone(), 1, check=False)
+    with_hints = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    P0 = ssm.Pivots(P.k, P.pivots, P.dip, P.region, P.cnt_off, P.cnt)
+    torch.cuda._sleep(cycles)
+    t0 = time.perf_counter()
+    ssm.ssm_iterate(g, P0, pos.clone(), 1, check=False)
+    without = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    assert with_hints < 0.2 < without
