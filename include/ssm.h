@@ -364,6 +364,39 @@ typedef struct {
   int64_t node_off, row_off, col_off, piv_off, dip_off, cnt_off_off, cnt_base;
 } ssm_batch_graph;
 size_t ssm_batch_iterate_workspace(int32_t G, const ssm_batch_graph *graphs);
+/* Batched preparation of the graphs above (Algorithm 1 lines 1-4 for G
+ * small graphs in two launches, one block per graph): from edge lists to
+ * the packed arrays ssm_batch_iterate reads.  Graph g has n nodes (1..12288),
+ * k max/min-sp pivots (2 <= k <= min(n, 100); start node 0), and m_in edges
+ * src/dst[edge_off .. edge_off + m_in) with local ids.
+ * ssm_batch_pivots (synchronous): builds each CSR (rowptr / colidx with room
+ * for 2 m_in entries per graph, packed as the out descriptors say), the k
+ * pivots (ties to the lowest id), d_ip, regions (ties to the lowest pivot
+ * index) and the eccentricities ecc[piv_off + a]; fills out[g] (offsets,
+ * cnt_len and cnt_base, with the count tables packed in graph order) and
+ * m_out[g] (host, edges after deduplication; may be NULL).  Device errors
+ * are read back and returned: SSM_E_GRAPH, SSM_E_DISCONNECTED.
+ * ssm_batch_layout_init (asynchronous): from those, cnt_off / cnt (as
+ * ssm_aggregate), PivotMDS (exact integer Gram matrix, FP64 eigenpairs by a
+ * parallel cyclic Jacobi method) and the rescale to unit mean edge length
+ * into pos (float x, y pairs at 2 node_off); eig (device double [2G], may be
+ * NULL) gets the two eigenvalues.  m[g] (host) = the edge counts.  Both use
+ * a workspace of ssm_batch_prepare_workspace(G, in) bytes (the same one).
+ */
+typedef struct {
+  int32_t n, k;
+  int64_t m_in, edge_off;
+} ssm_batch_input;
+size_t ssm_batch_prepare_workspace(int32_t G, const ssm_batch_input *in);
+int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t *src, const int32_t *dst,
+                     ssm_batch_graph *out, int32_t *rowptr, int32_t *colidx, int32_t *pivots, uint16_t *dip,
+                     int32_t *region, int32_t *ecc, int64_t *m_out, int32_t *status, void *ws, size_t ws_bytes,
+                     cudaStream_t stream);
+int ssm_batch_layout_init(int32_t G, const ssm_batch_graph *graphs, const int64_t *m, const int32_t *rowptr,
+                          const int32_t *colidx, const uint16_t *dip, const int32_t *region, const int32_t *ecc,
+                          int32_t *cnt_off, uint32_t *cnt, float *pos, double *eig, int32_t *status, void *ws,
+                          size_t ws_bytes, cudaStream_t stream);
+
 int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const int32_t *rowptr, const int32_t *colidx,
                       const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
                       float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t *threads_used,

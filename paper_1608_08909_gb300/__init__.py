@@ -22,7 +22,8 @@ from . import _build
 
 __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
-    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
+    "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate",
+    "ssm_batch_prepare", "ssm_batch_iterate_packed", "BatchPacked", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
     "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
     "ssm_iterate_hints", "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions", "ssm_procrustes", "ssm_hull_error", "ssm_gabriel_jaccard",
     "WGraph", "ssm_build_wgraph", "ssm_pivot_sssp", "ssm_select_pivots_weighted", "ssm_weighted_counts",
@@ -109,6 +110,9 @@ def lib():
                 "ssm_iterate_weighted": (ctypes.c_int, [i32, v, v, v, i32, v, v, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_stress_weighted_workspace": (sz, [i32, i32]),
                 "ssm_stress_weighted": (ctypes.c_int, [i32, v, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
+                "ssm_batch_prepare_workspace": (sz, [i32, v]),
+                "ssm_batch_pivots": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, v, v, v, v, v, sz, v]),
+                "ssm_batch_layout_init": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, v, v, v, v, v, sz, v]),
                 "ssm_stress_workspace": (sz, [i32, i64, i32, i32]),
                 "ssm_stress": (ctypes.c_int, [i32, i64, v, v, v, i32, i32, i32, u64, v, v, v, v, sz, v]),
             }
@@ -591,6 +595,106 @@ def _batch_call(L, items, desc, col, iters, threads, stream, check, dev):
     for g, _, pos in items:
         pos.copy_(pos_all[o:o + g.n])
         o += g.n
+    return rel, int(used.value)
+
+
+class BatchPacked:
+    """A batch prepared on the GPU (ssm_batch_pivots + ssm_batch_layout_init):
+    the packed arrays ssm_batch_iterate reads, with their descriptors."""
+
+    def __init__(self, desc, m, rowptr, colidx, pivots, dip, region, ecc, cnt_off, cnt, pos, eig):
+        self.desc, self.m = desc, m
+        self.rowptr, self.colidx, self.pivots, self.dip = rowptr, colidx, pivots, dip
+        self.region, self.ecc, self.cnt_off, self.cnt, self.pos, self.eig = region, ecc, cnt_off, cnt, pos, eig
+
+    def __len__(self):
+        return len(self.desc)
+
+    def graph(self, g: int) -> dict:
+        """Views of graph g's pieces (local ids), for inspection and tests."""
+        d = self.desc[g]
+        n, k = int(d["n"]), int(d["k"])
+        ro, co, po, do = int(d["row_off"]), int(d["col_off"]), int(d["piv_off"]), int(d["dip_off"])
+        rowptr = self.rowptr[ro:ro + n + 1]
+        m2 = 2 * int(self.m[g])
+        oo, cb = int(d["cnt_off_off"]), int(d["cnt_base"])
+        no = int(d["node_off"])
+        return {"n": n, "k": k, "m": int(self.m[g]), "rowptr": rowptr, "colidx": self.colidx[co:co + m2],
+                "pivots": self.pivots[po:po + k], "dip": self.dip[do:do + k * n].view(k, n),
+                "region": self.region[no:no + n], "cnt_off": self.cnt_off[oo:oo + k + 1],
+                "cnt": self.cnt[cb:cb + int(d["cnt_len"])], "pos": self.pos[no:no + n],
+                "eig": self.eig[2 * g:2 * g + 2] if self.eig is not None else None}
+
+
+def _batch_input_dtype():
+    import numpy as np
+    return np.dtype([("n", "<i4"), ("k", "<i4"), ("m_in", "<i8"), ("edge_off", "<i8")])
+
+
+def ssm_batch_prepare(graphs, device="cuda", stream=None, check: bool = True) -> BatchPacked:
+    """Algorithm 1 lines 1-4 for a batch of small graphs in two launches.
+    graphs: list of (n, src, dst, k) with host edge arrays (local ids)."""
+    import numpy as np
+    _require_cuda()
+    L = lib()
+    G = len(graphs)
+    inp = np.zeros(G, dtype=_batch_input_dtype())
+    eo = 0
+    for i, (n, s_, d_, k) in enumerate(graphs):
+        inp[i] = (n, k, len(s_), eo)
+        eo += len(s_)
+    src = torch.from_numpy(np.concatenate([np.asarray(g[1], np.int32) for g in graphs]) if eo else
+                           np.zeros(1, np.int32)).to(device)
+    dst = torch.from_numpy(np.concatenate([np.asarray(g[2], np.int32) for g in graphs]) if eo else
+                           np.zeros(1, np.int32)).to(device)
+    ns = inp["n"].astype(np.int64)
+    ks = inp["k"].astype(np.int64)
+    nodes, rows, cols = int(ns.sum()), int((ns + 1).sum()), max(1, int(2 * inp["m_in"].sum()))
+    pivs, dips, offs = int(ks.sum()), int((ks * ns).sum()), int((ks + 1).sum())
+    rowptr = torch.empty(rows, dtype=torch.int32, device=device)
+    colidx = torch.empty(cols, dtype=torch.int32, device=device)
+    pivots = torch.empty(pivs, dtype=torch.int32, device=device)
+    dip = torch.empty(dips, dtype=torch.uint16, device=device)
+    region = torch.empty(nodes, dtype=torch.int32, device=device)
+    ecc = torch.empty(pivs, dtype=torch.int32, device=device)
+    desc = np.zeros(G, dtype=_batch_dtype())
+    m = np.zeros(G, np.int64)
+    st = _status(device)
+    ip = inp.ctypes.data_as(ctypes.c_void_p)
+    ws = _ws(L.ssm_batch_prepare_workspace(G, ip), device)
+    _rc(L.ssm_batch_pivots(G, ip, _ptr(src), _ptr(dst), desc.ctypes.data_as(ctypes.c_void_p), _ptr(rowptr),
+                           _ptr(colidx), _ptr(pivots), _ptr(dip), _ptr(region), _ptr(ecc),
+                           m.ctypes.data_as(ctypes.c_void_p), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_batch_pivots")
+    cnt_off = torch.empty(offs, dtype=torch.int32, device=device)
+    cnt = torch.empty(max(1, int(desc["cnt_len"].astype(np.int64).sum())), dtype=torch.uint32, device=device)
+    pos = torch.empty((nodes, 2), dtype=torch.float32, device=device)
+    eig = torch.zeros(2 * G, dtype=torch.float64, device=device)
+    _rc(L.ssm_batch_layout_init(G, desc.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p),
+                                _ptr(rowptr), _ptr(colidx), _ptr(dip), _ptr(region), _ptr(ecc), _ptr(cnt_off),
+                                _ptr(cnt), _ptr(pos), _ptr(eig), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)),
+        "ssm_batch_layout_init")
+    if check:
+        ssm_check(st, "ssm_batch_layout_init", stream)
+    return BatchPacked(desc, m, rowptr, colidx, pivots, dip, region, ecc, cnt_off, cnt, pos, eig)
+
+
+def ssm_batch_iterate_packed(bp: BatchPacked, iters: int, threads: int = 0, stream=None, check: bool = True):
+    """ssm_batch_iterate on a prepared batch, positions updated in place in bp.pos;
+    returns (rel_change float64 [G], block size used)."""
+    L = lib()
+    G = len(bp)
+    dev = bp.pos.device
+    rel = torch.zeros(G, dtype=torch.float64, device=dev)
+    st = _status(dev)
+    dp = bp.desc.ctypes.data_as(ctypes.c_void_p)
+    ws = _ws(L.ssm_batch_iterate_workspace(G, dp), dev)
+    used = ctypes.c_int32(0)
+    _rc(L.ssm_batch_iterate(G, dp, _ptr(bp.rowptr), _ptr(bp.colidx), _ptr(bp.pivots), _ptr(bp.dip), _ptr(bp.cnt_off),
+                            _ptr(bp.cnt), _ptr(bp.pos), iters, _ptr(rel), threads, ctypes.byref(used), _ptr(st),
+                            _ptr(ws), ws.numel(), _stream(stream)), "ssm_batch_iterate")
+    if check:
+        ssm_check(st, "ssm_batch_iterate", stream)
     return rel, int(used.value)
 
 

@@ -1,0 +1,733 @@
+// Many small graphs prepared in two launches: Algorithm 1 lines 1-4 (graph,
+// max/min pivots, d_ip, regions and counts, PivotMDS and the rescale) for a
+// whole batch of independent layouts, feeding ssm_batch_iterate.
+//
+// One block owns one graph at a time (graphs handed out largest first from
+// an atomic counter).  k_prep_pivots builds the graph's CSR in shared memory
+// (degrees, scatter, rows sorted and deduplicated by one thread each), then
+// runs the k breadth-first searches of max/min sp level by level in shared
+// memory (distances and the running minimum as uint16, a visited bitmap,
+// two frontier queues); each search's distance row is the pivot's d_ip row.
+// Regions, the per-pivot eccentricities and the count-table length close
+// the first launch; the host reads the lengths once for the whole batch and
+// places the tables.  k_prep_layout then fills the cumulative counts, forms
+// the exact integer Gram matrix Delta^T Delta of the squared distances
+// (128-bit sums over 32-node chunks staged in shared memory), the FP64
+// matrix B = 1/4 J (G - s s^T / n) J, its eigenpairs by a parallel cyclic
+// Jacobi method (round-robin pairs, k/2 disjoint rotations per step, A and
+// the eigenvectors in shared memory), projects, signs and rescales the
+// layout.  Every reduction has a fixed order: results do not depend on
+// timing.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ssm {
+
+constexpr int kPrepMaxN = 12288;
+constexpr int kPrepMaxK = 100;
+constexpr int kPrepThreads = 512;
+constexpr int kPrepChunk = 32;     // nodes per staged chunk of the Gram
+constexpr int kJacobiSweeps = 60;  // upper bound; convergence ends it earlier
+
+struct PrepDev {
+  int32_t n, k;
+  int64_t m_in, edge_off;
+  int64_t node_off, row_off, col_off, piv_off, dip_off, cnt_off_off;
+};
+
+struct PrepArgs {
+  int32_t G, nmax;
+  const PrepDev *desc;
+  const int32_t *order;
+  const int32_t *src, *dst;
+  int32_t *tmp;  // scatter area, capacity 2 m_in per graph at col_off
+  int32_t *rowptr, *colidx, *pivots, *region;
+  uint16_t *dip;
+  int32_t *ecc;        // [sum k]
+  int64_t *lens;       // [G] count-table lengths
+  int64_t *medges;     // [G] edges after deduplication
+  unsigned *ctr;
+  int32_t *status;
+};
+
+// exclusive block scan of a[0..len) in place (len <= 3 * kPrepMaxN), total returned
+__device__ int block_exclusive_scan(int *a, int len, int *s_part) {
+  const int per = (len + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * per, e = min(len, b + per);
+  int t = 0;
+  for (int i = b; i < e; ++i) t += a[i];
+  s_part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < (int)blockDim.x; ++w) {
+      const int v = s_part[w];
+      s_part[w] = acc;
+      acc += v;
+    }
+    s_part[blockDim.x] = acc;
+  }
+  __syncthreads();
+  int acc = s_part[threadIdx.x];
+  for (int i = b; i < e; ++i) {
+    const int v = a[i];
+    a[i] = acc;
+    acc += v;
+  }
+  __syncthreads();
+  const int total = s_part[blockDim.x];
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  const int NM = A.nmax;
+  int *deg = reinterpret_cast<int *>(psm);               // [NM + 1]
+  int *off = deg + (NM + 1);                             // [NM + 1]
+  uint16_t *dist = reinterpret_cast<uint16_t *>(off + (NM + 1));  // [NM]
+  uint16_t *mind = dist + NM;                            // [NM]
+  uint16_t *q0 = mind + NM;                              // [NM]
+  uint16_t *q1 = q0 + NM;                                // [NM]
+  // 2 (NM + 1) ints and 4 NM uint16 before it: 8-byte aligned for any NM
+  unsigned *vis = reinterpret_cast<unsigned *>(q1 + NM);  // [(NM + 31) / 32]
+  int *s_part = reinterpret_cast<int *>(vis + (NM + 31) / 32);       // [kPrepThreads + 1]
+  int *s_ecc = s_part + kPrepThreads + 1;                             // [kPrepMaxK]
+  __shared__ int s_task, s_next;
+  __shared__ unsigned s_key;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctr, 1u);
+    __syncthreads();
+    const int task = s_task;
+    __syncthreads();
+    if (task >= A.G) break;
+    const int gi = A.order[task];
+    const PrepDev D = A.desc[gi];
+    const int n = D.n, k = D.k;
+    const int32_t *src = A.src + D.edge_off, *dst = A.dst + D.edge_off;
+    int32_t *tmp = A.tmp + D.col_off;
+    int32_t *rowptr = A.rowptr + D.row_off;
+    int32_t *colidx = A.colidx + D.col_off;
+    // ---- CSR: degrees, scatter, rows sorted and deduplicated
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) deg[i] = 0;
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < D.m_in; e += blockDim.x) {
+      const int u = src[e], v = dst[e];
+      if (u < 0 || u >= n || v < 0 || v >= n) {
+        dev_fail(A.status, SSM_E_GRAPH);
+        continue;
+      }
+      if (u == v) continue;
+      atomicAdd(deg + u, 1);
+      atomicAdd(deg + v, 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) off[i] = deg[i];
+    __syncthreads();
+    block_exclusive_scan(off, n + 1, s_part);
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) deg[i] = 0;  // cursors
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < D.m_in; e += blockDim.x) {
+      const int u = src[e], v = dst[e];
+      if (u < 0 || u >= n || v < 0 || v >= n || u == v) continue;
+      tmp[off[u] + atomicAdd(deg + u, 1)] = v;
+      tmp[off[v] + atomicAdd(deg + v, 1)] = u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int *row = tmp + off[i];
+      const int len = off[i + 1] - off[i];
+      for (int a = 1; a < len; ++a) {  // insertion sort (rows of these graphs are short)
+        const int x = row[a];
+        int b = a - 1;
+        while (b >= 0 && row[b] > x) {
+          row[b + 1] = row[b];
+          --b;
+        }
+        row[b + 1] = x;
+      }
+      int u = 0;
+      for (int a = 0; a < len; ++a) u += (a == 0 || row[a] != row[a - 1]) ? 1 : 0;
+      deg[i] = u;
+    }
+    __syncthreads();
+    const int m2 = block_exclusive_scan(deg, n + 1, s_part);
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) rowptr[i] = deg[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int *row = tmp + off[i];
+      const int len = off[i + 1] - off[i];
+      int o = deg[i];
+      for (int a = 0; a < len; ++a)
+        if (a == 0 || row[a] != row[a - 1]) colidx[o++] = row[a];
+    }
+    if (threadIdx.x == 0) A.medges[gi] = m2 / 2;
+    __syncthreads();
+    // ---- max/min sp (start node 0) with the d_ip rows
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mind[i] = 0xFFFFu;
+    __syncthreads();
+    for (int a = 0; a < k; ++a) {
+      int p = 0;
+      if (a > 0) {
+        if (threadIdx.x == 0) s_key = 0u;
+        __syncthreads();
+        unsigned best = 0u;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const unsigned key = ((unsigned)mind[i] << 16) | (0xFFFFu - (unsigned)i);
+          best = key > best ? key : best;
+        }
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_key, best);
+        __syncthreads();
+        p = (int)(0xFFFFu - (s_key & 0xFFFFu));
+      }
+      if (threadIdx.x == 0) A.pivots[D.piv_off + a] = p;
+      // breadth-first search from p, level by level
+      for (int i = threadIdx.x; i < n; i += blockDim.x) dist[i] = 0xFFFFu;
+      for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) vis[w] = 0u;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        dist[p] = 0;
+        vis[p >> 5] |= 1u << (p & 31);
+        q0[0] = (uint16_t)p;
+      }
+      __syncthreads();
+      int ncur = 1;
+      uint16_t *qc = q0, *qn = q1;
+      for (int level = 0; ncur > 0; ++level) {
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncur; t += blockDim.x) {
+          const int v = qc[t];
+          for (int j = rowptr[v]; j < rowptr[v + 1]; ++j) {
+            const int u = colidx[j];
+            const unsigned bit = 1u << (u & 31);
+            if (!(atomicOr(vis + (u >> 5), bit) & bit)) {
+              dist[u] = (uint16_t)(level + 1);
+              qn[atomicAdd(&s_next, 1)] = (uint16_t)u;
+            }
+          }
+        }
+        __syncthreads();
+        ncur = s_next;
+        uint16_t *t_ = qc;
+        qc = qn;
+        qn = t_;
+        __syncthreads();
+      }
+      uint16_t *row = A.dip + D.dip_off + (int64_t)a * n;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint16_t d = dist[i];
+        if (d == 0xFFFFu) dev_fail(A.status, SSM_E_DISCONNECTED);
+        row[i] = d;
+        mind[i] = min(mind[i], d);
+      }
+      __syncthreads();
+    }
+    // ---- regions (ties to the lowest pivot index) and eccentricities
+    for (int a = threadIdx.x; a < k; a += blockDim.x) s_ecc[a] = 0;
+    __syncthreads();
+    const uint16_t *dip = A.dip + D.dip_off;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int best = 0;
+      unsigned bd = dip[i];
+      for (int a = 1; a < k; ++a) {
+        const unsigned d = dip[(int64_t)a * n + i];
+        if (d < bd) {
+          bd = d;
+          best = a;
+        }
+      }
+      A.region[D.node_off + i] = best;
+      atomicMax(s_ecc + best, (int)bd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t len = 0;
+      for (int a = 0; a < k; ++a) {
+        A.ecc[D.piv_off + a] = s_ecc[a];
+        len += s_ecc[a] + 1;
+      }
+      A.lens[gi] = len;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ layout
+struct LayoutDev {
+  int32_t n, k;
+  int64_t m;
+  int64_t node_off, row_off, col_off, piv_off, dip_off, cnt_off_off, cnt_base;
+};
+
+struct LayoutArgs {
+  int32_t G;
+  const LayoutDev *desc;
+  const int32_t *order;
+  const int32_t *rowptr, *colidx, *region, *ecc;
+  const uint16_t *dip;
+  int32_t *cnt_off;
+  uint32_t *cnt;
+  float2 *pos;
+  double *eig;  // [2 G] or null
+  unsigned *ctr;
+  int32_t *status;
+};
+
+// fixed-order block sum of one double per thread
+__device__ double block_sum_d(double v, double *s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  double *Am = reinterpret_cast<double *>(lsm);              // [kPrepMaxK^2]
+  double *V = Am + kPrepMaxK * kPrepMaxK;                     // [kPrepMaxK^2]
+  uint32_t *chunk = reinterpret_cast<uint32_t *>(V + kPrepMaxK * kPrepMaxK);  // [kPrepChunk][kPrepMaxK]
+  __shared__ double s_red[kPrepThreads / 32];
+  __shared__ double s_c[kPrepMaxK / 2 + 1], s_s[kPrepMaxK / 2 + 1];
+  __shared__ unsigned long long s_col[kPrepMaxK];
+  __shared__ double s_rm[kPrepMaxK], s_v[2][kPrepMaxK];
+  __shared__ int s_off[kPrepMaxK + 1];
+  __shared__ int s_task, s_top[2], s_big[2];
+  __shared__ double s_sig[2], s_kap[2];
+  __shared__ int s_done;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(L.ctr, 1u);
+    __syncthreads();
+    const int task = s_task;
+    __syncthreads();
+    if (task >= L.G) break;
+    const int gi = L.order[task];
+    const LayoutDev D = L.desc[gi];
+    const int n = D.n, k = D.k;
+    const uint16_t *dip = L.dip + D.dip_off;
+    const int32_t *region = L.region + D.node_off;
+    const int32_t *ecc = L.ecc + D.piv_off;
+    // ---- Section 3's counts: cnt_off, histograms, prefix sums
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int a = 0; a < k; ++a) {
+        s_off[a] = acc;
+        acc += ecc[a] + 1;
+      }
+      s_off[k] = acc;
+    }
+    __syncthreads();
+    uint32_t *cnt = L.cnt + D.cnt_base;
+    for (int a = threadIdx.x; a <= k; a += blockDim.x) L.cnt_off[D.cnt_off_off + a] = s_off[a];
+    for (int t = threadIdx.x; t < s_off[k]; t += blockDim.x) cnt[t] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int a = region[i];
+      atomicAdd(cnt + s_off[a] + dip[(int64_t)a * n + i], 1u);
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+      uint32_t acc = 0;
+      for (int t = s_off[a]; t < s_off[a + 1]; ++t) {
+        acc += cnt[t];
+        cnt[t] = acc;
+      }
+    }
+    // ---- exact Gram G = Delta^T Delta (upper triangle, 128-bit) and s_a
+    const int npairs = k * (k + 1) / 2;
+    constexpr int kPairsPerThread = (kPrepMaxK * (kPrepMaxK + 1) / 2 + kPrepThreads - 1) / kPrepThreads;
+    unsigned __int128 acc[kPairsPerThread];
+    int pa[kPairsPerThread], pb[kPairsPerThread];
+#pragma unroll
+    for (int j = 0; j < kPairsPerThread; ++j) {
+      acc[j] = 0;
+      int p = threadIdx.x + j * blockDim.x;
+      int a = 0;
+      if (p < npairs) {
+        while (p >= k - a) {
+          p -= k - a;
+          ++a;
+        }
+        pa[j] = a;
+        pb[j] = a + p;
+      } else {
+        pa[j] = -1;
+        pb[j] = -1;
+      }
+    }
+    unsigned long long colsum = 0;
+    for (int i0 = 0; i0 < n; i0 += kPrepChunk) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kPrepChunk * k; e += blockDim.x) {
+        const int a = e / kPrepChunk, t = e % kPrepChunk;
+        const int i = i0 + t;
+        const uint32_t d = i < n ? dip[(int64_t)a * n + i] : 0u;
+        chunk[t * kPrepMaxK + a] = d * d;
+      }
+      __syncthreads();
+      if (threadIdx.x < k)
+        for (int t = 0; t < kPrepChunk; ++t) colsum += chunk[t * kPrepMaxK + threadIdx.x];
+#pragma unroll
+      for (int j = 0; j < kPairsPerThread; ++j) {
+        if (pa[j] < 0) continue;
+        const int a = pa[j], b = pb[j];
+        unsigned __int128 s = acc[j];
+        for (int t = 0; t < kPrepChunk; ++t)
+          s += (unsigned long long)chunk[t * kPrepMaxK + a] * (unsigned long long)chunk[t * kPrepMaxK + b];
+        acc[j] = s;
+      }
+    }
+    if (threadIdx.x < k) s_col[threadIdx.x] = colsum;
+    __syncthreads();
+    // B = G - s s^T / n, then 1/4 J B J
+    const double inv_n = 1.0 / (double)n;
+    const double two64 = 18446744073709551616.0;
+#pragma unroll
+    for (int j = 0; j < kPairsPerThread; ++j) {
+      if (pa[j] < 0) continue;
+      const int a = pa[j], b = pb[j];
+      const double g = (double)(unsigned long long)(acc[j] >> 64) * two64 + (double)(unsigned long long)acc[j];
+      const double v = g - ((double)s_col[a] * (double)s_col[b]) * inv_n;
+      Am[a * kPrepMaxK + b] = v;
+      Am[b * kPrepMaxK + a] = v;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+      double r = 0.0;
+      for (int b = 0; b < k; ++b) r += Am[a * kPrepMaxK + b];
+      s_rm[a] = r / (double)k;
+    }
+    __syncthreads();
+    double gm = 0.0;
+    for (int a = 0; a < k; ++a) gm += s_rm[a];
+    gm /= (double)k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int a = e / k, b = e % k;
+      Am[a * kPrepMaxK + b] = 0.25 * (Am[a * kPrepMaxK + b] - s_rm[a] - s_rm[b] + gm);
+      V[a * kPrepMaxK + b] = a == b ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // ---- parallel cyclic Jacobi: round-robin pairs, k/2 disjoint rotations
+    // per step, each zeroing A[p][q] with the textbook angle
+    const int m = k + (k & 1);
+    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int a = e / k, b = e % k;
+        const double v = Am[a * kPrepMaxK + b];
+        tot += v * v;
+        if (a != b) off += v * v;
+      }
+      off = block_sum_d(off, s_red);
+      tot = block_sum_d(tot, s_red);
+      if (off <= 1e-30 * tot || off == 0.0) break;
+      for (int r = 0; r < m - 1; ++r) {
+        for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
+          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
+          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
+          const int p = min(p0, q0), q = max(p0, q0);
+          double c = 1.0, s = 0.0;
+          if (q < k) {
+            const double apq = Am[p * kPrepMaxK + q];
+            if (apq != 0.0) {
+              const double app = Am[p * kPrepMaxK + p], aqq = Am[q * kPrepMaxK + q];
+              const double theta = (aqq - app) / (2.0 * apq);
+              const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              s = t * c;
+            }
+          }
+          s_c[i] = c;
+          s_s[i] = s;
+        }
+        __syncthreads();
+        // A <- A J and V <- V J (columns p, q of every pair)
+        for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
+          const int i = e / k, row = e % k;
+          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
+          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
+          const int p = min(p0, q0), q = max(p0, q0);
+          if (q >= k) continue;
+          const double c = s_c[i], s = s_s[i];
+          const double arp = Am[row * kPrepMaxK + p], arq = Am[row * kPrepMaxK + q];
+          Am[row * kPrepMaxK + p] = c * arp - s * arq;
+          Am[row * kPrepMaxK + q] = s * arp + c * arq;
+          const double vrp = V[row * kPrepMaxK + p], vrq = V[row * kPrepMaxK + q];
+          V[row * kPrepMaxK + p] = c * vrp - s * vrq;
+          V[row * kPrepMaxK + q] = s * vrp + c * vrq;
+        }
+        __syncthreads();
+        // A <- J^T A (rows p, q of every pair)
+        for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
+          const int i = e / k, col = e % k;
+          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
+          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
+          const int p = min(p0, q0), q = max(p0, q0);
+          if (q >= k) continue;
+          const double c = s_c[i], s = s_s[i];
+          const double apc = Am[p * kPrepMaxK + col], aqc = Am[q * kPrepMaxK + col];
+          Am[p * kPrepMaxK + col] = c * apc - s * aqc;
+          Am[q * kPrepMaxK + col] = s * apc + c * aqc;
+        }
+        __syncthreads();
+      }
+    }
+    // ---- the two largest eigenvalues (lowest index on a tie), signs
+    if (threadIdx.x == 0) {
+      int t0 = -1, t1 = -1;
+      for (int a = 0; a < k; ++a)
+        if (t0 < 0 || Am[a * kPrepMaxK + a] > Am[t0 * kPrepMaxK + t0]) t0 = a;
+      for (int a = 0; a < k; ++a) {
+        if (a == t0) continue;
+        if (t1 < 0 || Am[a * kPrepMaxK + a] > Am[t1 * kPrepMaxK + t1]) t1 = a;
+      }
+      s_top[0] = t0;
+      s_top[1] = t1 < 0 ? t0 : t1;
+      for (int r = 0; r < 2; ++r) {
+        int big = 0;
+        for (int a = 1; a < k; ++a)
+          if (fabs(V[a * kPrepMaxK + s_top[r]]) > fabs(V[big * kPrepMaxK + s_top[r]])) big = a;
+        s_big[r] = big;
+      }
+      s_done = Am[t0 * kPrepMaxK + t0] > 0.0;
+      if (L.eig) {
+        L.eig[2 * gi] = Am[s_top[0] * kPrepMaxK + s_top[0]];
+        L.eig[2 * gi + 1] = Am[s_top[1] * kPrepMaxK + s_top[1]];
+      }
+    }
+    __syncthreads();
+    if (!s_done) dev_fail(L.status, SSM_E_NUMERIC);
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      for (int r = 0; r < 2; ++r) {
+        const double sg = V[s_big[r] * kPrepMaxK + s_top[r]] < 0 ? -1.0 : 1.0;
+        s_v[r][a] = sg * V[a * kPrepMaxK + s_top[r]];
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sg0 = 0.0, sg1 = 0.0, cv0 = 0.0, cv1 = 0.0, cb = 0.0;
+      for (int a = 0; a < k; ++a) {
+        const double cbar = (double)s_col[a] * inv_n;
+        sg0 += s_v[0][a];
+        sg1 += s_v[1][a];
+        cv0 += cbar * s_v[0][a];
+        cv1 += cbar * s_v[1][a];
+        cb += cbar;
+      }
+      const double gbar = cb / (double)k;
+      s_sig[0] = sg0;
+      s_sig[1] = sg1;
+      s_kap[0] = cv0 - gbar * sg0;
+      s_kap[1] = cv1 - gbar * sg1;
+    }
+    __syncthreads();
+    // ---- x_i = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa), FP64
+    float2 *pos = L.pos + D.node_off;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double x = 0.0, y = 0.0, rs = 0.0;
+      for (int a = 0; a < k; ++a) {
+        const double d = (double)dip[(int64_t)a * n + i];
+        const double dd = d * d;
+        rs += dd;
+        x += dd * s_v[0][a];
+        y += dd * s_v[1][a];
+      }
+      const double rbar = rs / (double)k;
+      pos[i] = make_float2((float)(-0.5 * (x - rbar * s_sig[0] - s_kap[0])),
+                           (float)(-0.5 * (y - rbar * s_sig[1] - s_kap[1])));
+    }
+    __syncthreads();
+    // ---- rescale: sum_E ||x_i - x_j|| = m (lengths from the FP32 positions)
+    const int32_t *rowptr = L.rowptr + D.row_off;
+    const int32_t *colidx = L.colidx + D.col_off;
+    double len = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float2 xi = pos[i];
+      for (int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+        const int j = colidx[t];
+        if (j <= i) continue;
+        const float2 xj = pos[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y;
+        len += (double)sqrtf(dx * dx + dy * dy);
+      }
+    }
+    len = block_sum_d(len, s_red);
+    const bool okl = len > 0.0 && isfinite(len);
+    if (!okl && threadIdx.x == 0) dev_fail(L.status, SSM_E_NUMERIC);
+    const double sc = okl ? (double)D.m / len : 1.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float2 x = pos[i];
+      pos[i] = make_float2((float)((double)x.x * sc), (float)((double)x.y * sc));
+    }
+    __syncthreads();
+  }
+}
+
+// the workspace of both calls: descriptors, order, counter and lengths
+// first (the layout call uses only this prefix), then the scatter area
+struct PrepWs {
+  PrepDev *pd;
+  LayoutDev *ld;
+  int32_t *order;
+  unsigned *ctr;
+  int64_t *lens;  // [2 G]: table lengths, then edge counts
+  int32_t *tmp;
+};
+
+static void carve_prep(Carver &c, PrepWs &w, int32_t G, int64_t cap) {
+  w.pd = c.take<PrepDev>((size_t)G);
+  w.ld = c.take<LayoutDev>((size_t)G);
+  w.order = c.take<int32_t>((size_t)G);
+  w.ctr = c.take<unsigned>(2);
+  w.lens = c.take<int64_t>(2 * (size_t)G);
+  w.tmp = cap >= 0 ? c.take<int32_t>((size_t)std::max<int64_t>(cap, 1)) : nullptr;
+}
+
+static size_t prep_smem(int nmax) {
+  const size_t ints = 2 * (size_t)(nmax + 1) * sizeof(int);
+  const size_t u16 = 4 * (size_t)nmax * sizeof(uint16_t);
+  const size_t bits = (size_t)((nmax + 31) / 32) * sizeof(unsigned);
+  return ints + u16 + bits + (kPrepThreads + 1 + kPrepMaxK) * sizeof(int) + 16;
+}
+
+static size_t layout_smem() {
+  return 2 * (size_t)kPrepMaxK * kPrepMaxK * sizeof(double) + (size_t)kPrepChunk * kPrepMaxK * sizeof(uint32_t);
+}
+
+}  // namespace ssm
+
+// =========================================================== C ABI
+SSM_API size_t ssm_batch_prepare_workspace(int32_t G, const ssm_batch_input *in) {
+  if (G < 1 || !in) return 0;
+  int64_t cap = 0;
+  for (int32_t g = 0; g < G; ++g) cap += 2 * std::max<int64_t>(0, in[g].m_in);
+  ssm::Carver c(nullptr, 0);
+  ssm::PrepWs w;
+  ssm::carve_prep(c, w, G, cap);
+  return c.size();
+}
+
+SSM_API int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t *src, const int32_t *dst,
+                             ssm_batch_graph *out, int32_t *rowptr, int32_t *colidx, int32_t *pivots, uint16_t *dip,
+                             int32_t *region, int32_t *ecc, int64_t *m_out, int32_t *status, void *ws,
+                             size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (G < 1 || !in || !out || !rowptr || !colidx || !pivots || !dip || !region || !ecc || !status || !ws)
+    return fail(SSM_E_ARG, "ssm_batch_pivots: null pointer or G < 1");
+  std::vector<PrepDev> pd((size_t)G);
+  std::vector<int32_t> order((size_t)G);
+  int64_t node = 0, row = 0, col = 0, piv = 0, dipo = 0, offo = 0, edges = 0;
+  int nmax = 1;
+  for (int32_t g = 0; g < G; ++g) {
+    const ssm_batch_input &x = in[g];
+    if (x.n < 1 || x.n > kPrepMaxN) return fail(SSM_E_ARG, "ssm_batch_pivots: graph %d has n = %d (1..%d)", g, x.n, kPrepMaxN);
+    if (x.k < 2 || x.k > x.n || x.k > kPrepMaxK)
+      return fail(SSM_E_ARG, "ssm_batch_pivots: graph %d has k = %d (2..min(n, %d))", g, x.k, kPrepMaxK);
+    if (x.m_in < 0 || 2 * x.m_in >= ((int64_t)1 << 31)) return fail(SSM_E_ARG, "ssm_batch_pivots: graph %d edge count", g);
+    if (x.m_in > 0 && (!src || !dst)) return fail(SSM_E_ARG, "ssm_batch_pivots: null edge arrays");
+    PrepDev &d = pd[(size_t)g];
+    d.n = x.n; d.k = x.k; d.m_in = x.m_in; d.edge_off = x.edge_off;
+    d.node_off = node; d.row_off = row; d.col_off = col; d.piv_off = piv; d.dip_off = dipo; d.cnt_off_off = offo;
+    ssm_batch_graph &o = out[g];
+    o.n = x.n; o.k = x.k; o.cnt_len = 0; o.reserved = 0;
+    o.node_off = node; o.row_off = row; o.col_off = col; o.piv_off = piv; o.dip_off = dipo; o.cnt_off_off = offo;
+    o.cnt_base = 0;
+    node += x.n; row += x.n + 1; col += 2 * x.m_in; piv += x.k; dipo += (int64_t)x.k * x.n; offo += x.k + 1;
+    edges = std::max(edges, x.edge_off + x.m_in);
+    nmax = std::max(nmax, x.n);
+    order[(size_t)g] = g;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return (int64_t)pd[(size_t)a].n * pd[(size_t)a].k > (int64_t)pd[(size_t)b].n * pd[(size_t)b].k;
+  });
+  Carver c(ws, ws_bytes);
+  PrepWs w;
+  carve_prep(c, w, G, col);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_batch_pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  SSM_TRY_CUDA(cudaMemcpyAsync(w.pd, pd.data(), pd.size() * sizeof(PrepDev), cudaMemcpyHostToDevice, s));
+  SSM_TRY_CUDA(cudaMemcpyAsync(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  SSM_TRY_CUDA(cudaMemsetAsync(w.ctr, 0, 2 * sizeof(unsigned), s));
+  PrepArgs A;
+  A.G = G; A.nmax = nmax; A.desc = w.pd; A.order = w.order; A.src = src; A.dst = dst; A.tmp = w.tmp;
+  A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.region = region; A.dip = dip; A.ecc = ecc;
+  A.lens = w.lens; A.medges = w.lens + G; A.ctr = w.ctr; A.status = status;
+  const size_t smem = prep_smem(nmax);
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_prep_pivots));
+  int per_sm = 0;
+  SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prep_pivots, kPrepThreads, smem));
+  if (per_sm < 1) return fail(SSM_E_ARG, "ssm_batch_pivots: %zu bytes of shared memory do not fit", smem);
+  const int blocks = std::max(1, std::min(G, per_sm * num_sms()));
+  note_launch(), k_prep_pivots<<<blocks, kPrepThreads, smem, s>>>(A);
+  SSM_TRY_CUDA(cudaGetLastError());
+  std::vector<int64_t> h(2 * (size_t)G);
+  int32_t hst = 0;
+  SSM_TRY_CUDA(cudaMemcpyAsync(h.data(), w.lens, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaMemcpyAsync(&hst, status, sizeof hst, cudaMemcpyDeviceToHost, s));
+  SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hst) return fail(hst, "ssm_batch_pivots: %s", ssm_status_string(hst));
+  int64_t base = 0;
+  for (int32_t g = 0; g < G; ++g) {
+    if (h[(size_t)g] < in[g].k || h[(size_t)g] >= ((int64_t)1 << 30))
+      return fail(SSM_E_DISCONNECTED, "ssm_batch_pivots: graph %d has no valid count table (disconnected?)", g);
+    out[g].cnt_len = (int32_t)h[(size_t)g];
+    out[g].cnt_base = base;
+    base += h[(size_t)g];
+    if (m_out) m_out[g] = h[(size_t)G + g];
+  }
+  return SSM_OK;
+}
+
+SSM_API int ssm_batch_layout_init(int32_t G, const ssm_batch_graph *graphs, const int64_t *m, const int32_t *rowptr,
+                                  const int32_t *colidx, const uint16_t *dip, const int32_t *region,
+                                  const int32_t *ecc, int32_t *cnt_off, uint32_t *cnt, float *pos, double *eig,
+                                  int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  using namespace ssm;
+  if (G < 1 || !graphs || !m || !rowptr || !colidx || !dip || !region || !ecc || !cnt_off || !cnt || !pos ||
+      !status || !ws)
+    return fail(SSM_E_ARG, "ssm_batch_layout_init: null pointer or G < 1");
+  std::vector<LayoutDev> ld((size_t)G);
+  std::vector<int32_t> order((size_t)G);
+  for (int32_t g = 0; g < G; ++g) {
+    const ssm_batch_graph &x = graphs[g];
+    if (x.n < 1 || x.n > kPrepMaxN || x.k < 2 || x.k > kPrepMaxK || x.k > x.n || x.cnt_len < x.k)
+      return fail(SSM_E_ARG, "ssm_batch_layout_init: graph %d has n = %d, k = %d, cnt_len = %d", g, x.n, x.k, x.cnt_len);
+    if (m[g] < 1) return fail(SSM_E_ARG, "ssm_batch_layout_init: graph %d has no edges", g);
+    LayoutDev &d = ld[(size_t)g];
+    d.n = x.n; d.k = x.k; d.m = m[g];
+    d.node_off = x.node_off; d.row_off = x.row_off; d.col_off = x.col_off; d.piv_off = x.piv_off;
+    d.dip_off = x.dip_off; d.cnt_off_off = x.cnt_off_off; d.cnt_base = x.cnt_base;
+    order[(size_t)g] = g;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    const LayoutDev &x = ld[(size_t)a], &y = ld[(size_t)b];
+    return (int64_t)x.n * x.k * x.k > (int64_t)y.n * y.k * y.k;
+  });
+  Carver c(ws, ws_bytes);
+  PrepWs w;
+  carve_prep(c, w, G, -1);
+  if (!c.ok) return fail(SSM_E_NOMEM, "ssm_batch_layout_init: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  LayoutDev *dd = w.ld;
+  int32_t *dorder = w.order;
+  unsigned *ctr = w.ctr + 1;
+  SSM_TRY_CUDA(cudaMemcpyAsync(dd, ld.data(), ld.size() * sizeof(LayoutDev), cudaMemcpyHostToDevice, s));
+  SSM_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  SSM_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
+  LayoutArgs L;
+  L.G = G; L.desc = dd; L.order = dorder; L.rowptr = rowptr; L.colidx = colidx; L.region = region; L.ecc = ecc;
+  L.dip = dip; L.cnt_off = cnt_off; L.cnt = cnt; L.pos = reinterpret_cast<float2 *>(pos); L.eig = eig; L.ctr = ctr;
+  L.status = status;
+  const size_t smem = layout_smem();
+  SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_prep_layout));
+  int per_sm = 0;
+  SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prep_layout, kPrepThreads, smem));
+  if (per_sm < 1) return fail(SSM_E_ARG, "ssm_batch_layout_init: %zu bytes of shared memory do not fit", smem);
+  const int blocks = std::max(1, std::min(G, per_sm * num_sms()));
+  note_launch(), k_prep_layout<<<blocks, kPrepThreads, smem, s>>>(L);
+  SSM_TRY_CUDA(cudaGetLastError());
+  return SSM_OK;
+}

@@ -662,6 +662,17 @@ __global__ void __launch_bounds__(kWSweepThreads) k_wsweep_f32(int32_t n, const 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float2 xi = X[i];
     float wx = 0.f, wy = 0.f, bx = 0.f, by = 0.f, den = 0.f;
+    const float *dcol = dist + i;
+    const float *wcol = wtab + i;
+    // the first pivots' (d, w') are requested before the neighbour gathers,
+    // and every batch's loads are issued before the previous batch is used
+    float dq[kWPrefetch], wq[kWPrefetch];
+#pragma unroll
+    for (int q = 0; q < kWPrefetch; ++q) {
+      const bool ok = q < k;
+      dq[q] = ok ? __ldg(dcol + (size_t)q * n) : 0.f;
+      wq[q] = ok ? __ldg(wcol + (size_t)q * n) : 0.f;
+    }
     for (int t = __ldg(rowptr + i); t < __ldg(rowptr + i + 1); ++t) {
       const float l = __ldg(elen + t);
       const float w = 1.0f / (l * l);
@@ -675,15 +686,13 @@ __global__ void __launch_bounds__(kWSweepThreads) k_wsweep_f32(int32_t n, const 
       by += B * dy;
       den += w;
     }
-    const float *dcol = dist + i;
-    const float *wcol = wtab + i;
     for (int a0 = 0; a0 < k; a0 += kWPrefetch) {
-      float dq[kWPrefetch], wq[kWPrefetch];
+      float dn_[kWPrefetch], wn_[kWPrefetch];
 #pragma unroll
       for (int q = 0; q < kWPrefetch; ++q) {
-        const bool ok = a0 + q < k;
-        dq[q] = ok ? __ldg(dcol + (size_t)(a0 + q) * n) : 0.f;
-        wq[q] = ok ? __ldg(wcol + (size_t)(a0 + q) * n) : 0.f;
+        const bool ok = a0 + kWPrefetch + q < k;
+        dn_[q] = ok ? __ldg(dcol + (size_t)(a0 + kWPrefetch + q) * n) : 0.f;
+        wn_[q] = ok ? __ldg(wcol + (size_t)(a0 + kWPrefetch + q) * n) : 0.f;
       }
 #pragma unroll
       for (int q = 0; q < kWPrefetch; ++q) {
@@ -698,6 +707,11 @@ __global__ void __launch_bounds__(kWSweepThreads) k_wsweep_f32(int32_t n, const 
         bx += B * dx;
         by += B * dy;
         den += w;
+      }
+#pragma unroll
+      for (int q = 0; q < kWPrefetch; ++q) {
+        dq[q] = dn_[q];
+        wq[q] = wn_[q];
       }
     }
     float2 y = xi;

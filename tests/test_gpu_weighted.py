@@ -99,7 +99,7 @@ def test_bad_lengths_and_disconnected_graphs_are_errors():
     # the searches detect it too, on a CSR made by hand
     t = lambda a, dt: torch.tensor(a, dtype=dt, device=DEV)
     g = ssm.WGraph(4, 2, t([0, 1, 3, 4, 4], torch.int32), t([1, 0, 2, 1], torch.int32),
-                   t([1.0, 1.0, 2.0, 2.0], torch.float32))
+                   elen=t([1.0, 1.0, 2.0, 2.0], torch.float32))
     with pytest.raises(ssm.SSMError) as e:
         ssm.ssm_pivot_sssp(g, torch.tensor([0], dtype=torch.int32, device=DEV))
     assert e.value.code == -3
