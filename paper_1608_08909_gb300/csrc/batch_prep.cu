@@ -29,7 +29,6 @@ constexpr int kPrepMaxN = 12288;
 constexpr int kPrepMaxK = 100;
 constexpr int kPrepThreads = 512;
 constexpr int kPrepChunk = 32;     // nodes per staged chunk of the Gram
-constexpr int kJacobiSweeps = 60;  // upper bound; convergence ends it earlier
 
 struct PrepDev {
   int32_t n, k;
@@ -294,11 +293,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
   double *V = Am + kPrepMaxK * kPrepMaxK;                     // [kPrepMaxK^2]
   uint32_t *chunk = reinterpret_cast<uint32_t *>(V + kPrepMaxK * kPrepMaxK);  // [kPrepChunk][kPrepMaxK]
   __shared__ double s_red[kPrepThreads / 32];
-  __shared__ double s_c[kPrepMaxK / 2 + 1], s_s[kPrepMaxK / 2 + 1];
   __shared__ unsigned long long s_col[kPrepMaxK];
   __shared__ double s_rm[kPrepMaxK], s_v[2][kPrepMaxK];
   __shared__ int s_off[kPrepMaxK + 1];
-  __shared__ int s_task, s_top[2], s_big[2];
+  __shared__ double s_dg[kPrepMaxK], s_e[kPrepMaxK], s_p[kPrepMaxK], s_w[kPrepMaxK], s_lam[2];
+  __shared__ double s_y[2][kPrepMaxK], s_fd[kPrepMaxK], s_fu[kPrepMaxK], s_fu2[kPrepMaxK], s_fl[kPrepMaxK];
+  __shared__ int s_piv[kPrepMaxK];
+  __shared__ int s_task, s_big[2];
   __shared__ double s_sig[2], s_kap[2];
   __shared__ int s_done;
   for (;;) {
@@ -413,101 +414,191 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
       V[a * kPrepMaxK + b] = a == b ? 1.0 : 0.0;
     }
     __syncthreads();
-    // ---- parallel cyclic Jacobi: round-robin pairs, k/2 disjoint rotations
-    // per step, each zeroing A[p][q] with the textbook angle
-    const int m = k + (k & 1);
-    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        const int a = e / k, b = e % k;
-        const double v = Am[a * kPrepMaxK + b];
-        tot += v * v;
-        if (a != b) off += v * v;
+    // ---- top-2 eigenpairs: Householder reduction of B to a tridiagonal T
+    // (Q^T B Q = T, reflector vectors kept in V), the two largest
+    // eigenvalues of T by Sturm-count bisection, their eigenvectors by
+    // inverse iteration on T, and back through the reflectors
+    double *Hv = V;  // row j: the unit reflector of step j (entries j+1 .. k-1)
+    for (int j = 0; j + 2 < k; ++j) {
+      double sig = 0.0;
+      for (int r = j + 2 + threadIdx.x; r < k; r += blockDim.x) sig += Am[r * kPrepMaxK + j] * Am[r * kPrepMaxK + j];
+      sig = block_sum_d(sig, s_red);
+      const double x0 = Am[(j + 1) * kPrepMaxK + j];
+      if (sig == 0.0) {  // the column is already tridiagonal: H = I
+        for (int r = threadIdx.x; r < k; r += blockDim.x) Hv[j * kPrepMaxK + r] = 0.0;
+        if (threadIdx.x == 0) s_e[j] = x0;
+        __syncthreads();
+        continue;
       }
-      off = block_sum_d(off, s_red);
-      tot = block_sum_d(tot, s_red);
-      if (off <= 1e-30 * tot || off == 0.0) break;
-      for (int r = 0; r < m - 1; ++r) {
-        for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
-          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
-          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
-          const int p = min(p0, q0), q = max(p0, q0);
-          double c = 1.0, s = 0.0;
-          if (q < k) {
-            const double apq = Am[p * kPrepMaxK + q];
-            if (apq != 0.0) {
-              const double app = Am[p * kPrepMaxK + p], aqq = Am[q * kPrepMaxK + q];
-              const double theta = (aqq - app) / (2.0 * apq);
-              const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-              c = 1.0 / sqrt(t * t + 1.0);
-              s = t * c;
+      const double nrm = sqrt(x0 * x0 + sig);
+      const double alpha = x0 >= 0.0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vinv = 1.0 / sqrt(v0 * v0 + sig);
+      for (int r = threadIdx.x; r < k; r += blockDim.x)
+        Hv[j * kPrepMaxK + r] = r <= j ? 0.0 : (r == j + 1 ? v0 : Am[r * kPrepMaxK + j]) * vinv;
+      if (threadIdx.x == 0) s_e[j] = alpha;
+      __syncthreads();
+      // p = A v over the trailing block, K = v . p, w = 2 (p - K v)
+      const double *hv = Hv + j * kPrepMaxK;
+      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
+        double t = 0.0;
+        for (int c = j + 1; c < k; ++c) t += Am[r * kPrepMaxK + c] * hv[c];
+        s_p[r] = t;
+      }
+      __syncthreads();
+      double kk = 0.0;
+      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) kk += hv[r] * s_p[r];
+      kk = block_sum_d(kk, s_red);
+      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) s_w[r] = 2.0 * (s_p[r] - kk * hv[r]);
+      __syncthreads();
+      const int L = k - j - 1;
+      for (int e2 = threadIdx.x; e2 < L * L; e2 += blockDim.x) {
+        const int r = j + 1 + e2 / L, c = j + 1 + e2 % L;
+        Am[r * kPrepMaxK + c] -= hv[r] * s_w[c] + s_w[r] * hv[c];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      for (int a = 0; a < k; ++a) s_dg[a] = Am[a * kPrepMaxK + a];
+      if (k >= 2) s_e[k - 2] = Am[(k - 1) * kPrepMaxK + (k - 2)];
+    }
+    __syncthreads();
+    // eigenvalues number k-1 and k-2 (ascending) by bisection on Sturm counts,
+    // 32 points per step evaluated by the lanes of warp 0
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double lo = 0.0, hi = 0.0, emax = 0.0;
+      for (int a = 0; a < k; ++a) {
+        const double r = (a > 0 ? fabs(s_e[a - 1]) : 0.0) + (a + 1 < k ? fabs(s_e[a]) : 0.0);
+        lo = a == 0 ? s_dg[a] - r : fmin(lo, s_dg[a] - r);
+        hi = a == 0 ? s_dg[a] + r : fmax(hi, s_dg[a] + r);
+        if (a + 1 < k) emax = fmax(emax, fabs(s_e[a]));
+      }
+      const double tiny = 1e-300;
+      for (int want = 0; want < 2; ++want) {
+        const int idx = k - 1 - want;  // ascending index of the eigenvalue
+        double a0 = lo - 1e-12 * (fabs(lo) + fabs(hi)), b0 = hi + 1e-12 * (fabs(lo) + fabs(hi));
+        for (int it = 0; it < 40 && b0 - a0 > 4e-16 * fmax(fabs(a0), fabs(b0)); ++it) {
+          const double x = a0 + (b0 - a0) * (double)(lane + 1) / 33.0;
+          int cnt = 0;  // eigenvalues below x
+          double q = s_dg[0] - x;
+          cnt += q < 0.0;
+          for (int a = 1; a < k; ++a) {
+            if (q == 0.0) q = tiny;
+            q = (s_dg[a] - x) - s_e[a - 1] * s_e[a - 1] / q;
+            cnt += q < 0.0;
+          }
+          // the smallest lane point with more than idx eigenvalues below it
+          const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
+          const int first = above ? __ffs(above) - 1 : 32;
+          const double nb = first < 32 ? a0 + (b0 - a0) * (double)(first + 1) / 33.0 : b0;
+          const double na = first > 0 ? a0 + (b0 - a0) * (double)first / 33.0 : a0;
+          a0 = na;
+          b0 = nb;
+        }
+        if (lane == 0) s_lam[want] = 0.5 * (a0 + b0);
+      }
+      (void)emax;
+    }
+    __syncthreads();
+    // inverse iteration on T - lambda I (tridiagonal LU with partial
+    // pivoting), the second vector kept orthogonal to the first
+    if (threadIdx.x == 0) {
+      for (int want = 0; want < 2; ++want) {
+        double *y = s_y[want];
+        for (int a = 0; a < k; ++a) y[a] = 1.0 + 0.01 * (double)((a * 37) % 11);
+        const double lam = s_lam[want];
+        const double pert = 1e-14 * (fabs(lam) + 1e-300);
+        for (int it = 0; it < 4; ++it) {
+          // factor: dd (diagonal), du (first super), du2 (second super), dl (multipliers)
+          double *dd = s_fd, *du = s_fu, *du2 = s_fu2, *dl = s_fl;
+          for (int a = 0; a < k; ++a) {
+            dd[a] = s_dg[a] - lam;
+            du[a] = a + 1 < k ? s_e[a] : 0.0;
+            dl[a] = a + 1 < k ? s_e[a] : 0.0;
+            du2[a] = 0.0;
+          }
+          for (int a = 0; a + 1 < k; ++a) {
+            if (fabs(dd[a]) >= fabs(dl[a])) {
+              if (dd[a] == 0.0) dd[a] = pert;
+              const double f = dl[a] / dd[a];
+              dl[a] = f;
+              dd[a + 1] -= f * du[a];
+              s_piv[a] = 0;
+            } else {
+              const double f = dd[a] / dl[a];
+              dd[a] = dl[a];
+              dl[a] = f;
+              const double t = du[a];
+              du[a] = dd[a + 1];
+              dd[a + 1] = t - f * dd[a + 1];
+              if (a + 2 < k) {
+                du2[a] = du[a + 1];
+                du[a + 1] = -f * du[a + 1];
+              }
+              s_piv[a] = 1;
             }
           }
-          s_c[i] = c;
-          s_s[i] = s;
+          if (dd[k - 1] == 0.0) dd[k - 1] = pert;
+          // solve L U x = P y
+          for (int a = 0; a + 1 < k; ++a) {
+            if (s_piv[a] == 0) {
+              y[a + 1] -= dl[a] * y[a];
+            } else {
+              const double t = y[a];
+              y[a] = y[a + 1];
+              y[a + 1] = t - dl[a] * y[a];
+            }
+          }
+          y[k - 1] /= dd[k - 1];
+          if (k >= 2) y[k - 2] = (y[k - 2] - du[k - 2] * y[k - 1]) / dd[k - 2];
+          for (int a = k - 3; a >= 0; --a) y[a] = (y[a] - du[a] * y[a + 1] - du2[a] * y[a + 2]) / dd[a];
+          if (want == 1) {  // keep it orthogonal to the first eigenvector
+            double dt = 0.0;
+            for (int a = 0; a < k; ++a) dt += y[a] * s_y[0][a];
+            for (int a = 0; a < k; ++a) y[a] -= dt * s_y[0][a];
+          }
+          double nr = 0.0;
+          for (int a = 0; a < k; ++a) nr += y[a] * y[a];
+          nr = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+          for (int a = 0; a < k; ++a) y[a] *= nr;
         }
-        __syncthreads();
-        // A <- A J and V <- V J (columns p, q of every pair)
-        for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
-          const int i = e / k, row = e % k;
-          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
-          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
-          const int p = min(p0, q0), q = max(p0, q0);
-          if (q >= k) continue;
-          const double c = s_c[i], s = s_s[i];
-          const double arp = Am[row * kPrepMaxK + p], arq = Am[row * kPrepMaxK + q];
-          Am[row * kPrepMaxK + p] = c * arp - s * arq;
-          Am[row * kPrepMaxK + q] = s * arp + c * arq;
-          const double vrp = V[row * kPrepMaxK + p], vrq = V[row * kPrepMaxK + q];
-          V[row * kPrepMaxK + p] = c * vrp - s * vrq;
-          V[row * kPrepMaxK + q] = s * vrp + c * vrq;
-        }
-        __syncthreads();
-        // A <- J^T A (rows p, q of every pair)
-        for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
-          const int i = e / k, col = e % k;
-          const int p0 = i == 0 ? 0 : 1 + (i - 1 + r) % (m - 1);
-          const int q0 = 1 + (m - 2 - i + r) % (m - 1);
-          const int p = min(p0, q0), q = max(p0, q0);
-          if (q >= k) continue;
-          const double c = s_c[i], s = s_s[i];
-          const double apc = Am[p * kPrepMaxK + col], aqc = Am[q * kPrepMaxK + col];
-          Am[p * kPrepMaxK + col] = c * apc - s * aqc;
-          Am[q * kPrepMaxK + col] = s * apc + c * aqc;
-        }
-        __syncthreads();
       }
-    }
-    // ---- the two largest eigenvalues (lowest index on a tie), signs
-    if (threadIdx.x == 0) {
-      int t0 = -1, t1 = -1;
-      for (int a = 0; a < k; ++a)
-        if (t0 < 0 || Am[a * kPrepMaxK + a] > Am[t0 * kPrepMaxK + t0]) t0 = a;
-      for (int a = 0; a < k; ++a) {
-        if (a == t0) continue;
-        if (t1 < 0 || Am[a * kPrepMaxK + a] > Am[t1 * kPrepMaxK + t1]) t1 = a;
-      }
-      s_top[0] = t0;
-      s_top[1] = t1 < 0 ? t0 : t1;
-      for (int r = 0; r < 2; ++r) {
-        int big = 0;
-        for (int a = 1; a < k; ++a)
-          if (fabs(V[a * kPrepMaxK + s_top[r]]) > fabs(V[big * kPrepMaxK + s_top[r]])) big = a;
-        s_big[r] = big;
-      }
-      s_done = Am[t0 * kPrepMaxK + t0] > 0.0;
+      s_done = s_lam[0] > 0.0;
       if (L.eig) {
-        L.eig[2 * gi] = Am[s_top[0] * kPrepMaxK + s_top[0]];
-        L.eig[2 * gi + 1] = Am[s_top[1] * kPrepMaxK + s_top[1]];
+        L.eig[2 * gi] = s_lam[0];
+        L.eig[2 * gi + 1] = s_lam[1];
       }
     }
     __syncthreads();
-    if (!s_done) dev_fail(L.status, SSM_E_NUMERIC);
-    for (int a = threadIdx.x; a < k; a += blockDim.x)
-      for (int r = 0; r < 2; ++r) {
-        const double sg = V[s_big[r] * kPrepMaxK + s_top[r]] < 0 ? -1.0 : 1.0;
-        s_v[r][a] = sg * V[a * kPrepMaxK + s_top[r]];
+    // z = H_0 H_1 ... H_{k-3} y, the reflectors applied last to first
+    for (int j = k - 3; j >= 0; --j) {
+      const double *hv = Hv + j * kPrepMaxK;
+      double d0 = 0.0, d1 = 0.0;
+      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
+        d0 += hv[r] * s_y[0][r];
+        d1 += hv[r] * s_y[1][r];
       }
+      d0 = block_sum_d(d0, s_red);
+      d1 = block_sum_d(d1, s_red);
+      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
+        s_y[0][r] -= 2.0 * d0 * hv[r];
+        s_y[1][r] -= 2.0 * d1 * hv[r];
+      }
+      __syncthreads();
+    }
+    if (!s_done) dev_fail(L.status, SSM_E_NUMERIC);
+    // each vector signed so that its largest-magnitude entry (lowest index on a tie) is positive
+    if (threadIdx.x == 0)
+      for (int r = 0; r < 2; ++r) {
+        int big = 0;
+        for (int a = 1; a < k; ++a)
+          if (fabs(s_y[r][a]) > fabs(s_y[r][big])) big = a;
+        s_big[r] = big;
+      }
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      for (int r = 0; r < 2; ++r) s_v[r][a] = (s_y[r][s_big[r]] < 0 ? -1.0 : 1.0) * s_y[r][a];
     __syncthreads();
     if (threadIdx.x == 0) {
       double sg0 = 0.0, sg1 = 0.0, cv0 = 0.0, cv1 = 0.0, cb = 0.0;
