@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
   __shared__ double s_rm[kPrepMaxK], s_v[2][kPrepMaxK];
   __shared__ int s_off[kPrepMaxK + 1];
   __shared__ double s_dg[kPrepMaxK], s_e[kPrepMaxK], s_p[kPrepMaxK], s_w[kPrepMaxK], s_lam[2];
-  __shared__ double s_y[2][kPrepMaxK], s_fd[kPrepMaxK], s_fu[kPrepMaxK], s_fu2[kPrepMaxK], s_fl[kPrepMaxK];
-  __shared__ int s_piv[kPrepMaxK];
+  __shared__ double s_y[2][kPrepMaxK], s_fd[2][kPrepMaxK], s_fu[2][kPrepMaxK], s_fu2[2][kPrepMaxK], s_fl[2][kPrepMaxK];
+  __shared__ double s_e2[kPrepMaxK];
+  __shared__ int s_piv[2][kPrepMaxK];
   __shared__ int s_task, s_big[2];
   __shared__ double s_sig[2], s_kap[2];
   __shared__ int s_done;
@@ -378,10 +379,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
       for (int j = 0; j < kPairsPerThread; ++j) {
         if (pa[j] < 0) continue;
         const int a = pa[j], b = pb[j];
-        unsigned __int128 s = acc[j];
+        // a chunk's 32 products (each below 2^52) sum exactly in 64 bits;
+        // the chunk sums go into the 128-bit total
+        unsigned long long cs = 0;
         for (int t = 0; t < kPrepChunk; ++t)
-          s += (unsigned long long)chunk[t * kPrepMaxK + a] * (unsigned long long)chunk[t * kPrepMaxK + b];
-        acc[j] = s;
+          cs += (unsigned long long)chunk[t * kPrepMaxK + a] * (unsigned long long)chunk[t * kPrepMaxK + b];
+        acc[j] += cs;
       }
     }
     if (threadIdx.x < k) s_col[threadIdx.x] = colsum;
@@ -420,36 +423,45 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
     // inverse iteration on T, and back through the reflectors
     double *Hv = V;  // row j: the unit reflector of step j (entries j+1 .. k-1)
     for (int j = 0; j + 2 < k; ++j) {
-      double sig = 0.0;
-      for (int r = j + 2 + threadIdx.x; r < k; r += blockDim.x) sig += Am[r * kPrepMaxK + j] * Am[r * kPrepMaxK + j];
-      sig = block_sum_d(sig, s_red);
-      const double x0 = Am[(j + 1) * kPrepMaxK + j];
-      if (sig == 0.0) {  // the column is already tridiagonal: H = I
-        for (int r = threadIdx.x; r < k; r += blockDim.x) Hv[j * kPrepMaxK + r] = 0.0;
-        if (threadIdx.x == 0) s_e[j] = x0;
-        __syncthreads();
-        continue;
+      // warp 0: the reflector of column j (norm by shuffles)
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double sig = 0.0;
+        for (int r = j + 2 + lane; r < k; r += 32) sig += Am[r * kPrepMaxK + j] * Am[r * kPrepMaxK + j];
+        for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+        const double x0 = Am[(j + 1) * kPrepMaxK + j];
+        if (sig == 0.0) {  // the column is already tridiagonal: H = I
+          for (int r = lane; r < k; r += 32) Hv[j * kPrepMaxK + r] = 0.0;
+          if (lane == 0) s_e[j] = x0;
+        } else {
+          const double nrm = sqrt(x0 * x0 + sig);
+          const double alpha = x0 >= 0.0 ? -nrm : nrm;
+          const double v0 = x0 - alpha;
+          const double vinv = 1.0 / sqrt(v0 * v0 + sig);
+          for (int r = lane; r < k; r += 32)
+            Hv[j * kPrepMaxK + r] = r <= j ? 0.0 : (r == j + 1 ? v0 : Am[r * kPrepMaxK + j]) * vinv;
+          if (lane == 0) s_e[j] = alpha;
+        }
       }
-      const double nrm = sqrt(x0 * x0 + sig);
-      const double alpha = x0 >= 0.0 ? -nrm : nrm;
-      const double v0 = x0 - alpha;
-      const double vinv = 1.0 / sqrt(v0 * v0 + sig);
-      for (int r = threadIdx.x; r < k; r += blockDim.x)
-        Hv[j * kPrepMaxK + r] = r <= j ? 0.0 : (r == j + 1 ? v0 : Am[r * kPrepMaxK + j]) * vinv;
-      if (threadIdx.x == 0) s_e[j] = alpha;
       __syncthreads();
-      // p = A v over the trailing block, K = v . p, w = 2 (p - K v)
       const double *hv = Hv + j * kPrepMaxK;
+      if (hv[j + 1] == 0.0) continue;  // H = I (the same decision in every thread)
+      // p = A v over the trailing block (read down the columns: A is
+      // symmetric and consecutive threads then touch consecutive words)
       for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
         double t = 0.0;
-        for (int c = j + 1; c < k; ++c) t += Am[r * kPrepMaxK + c] * hv[c];
+        for (int c = j + 1; c < k; ++c) t += Am[c * kPrepMaxK + r] * hv[c];
         s_p[r] = t;
       }
       __syncthreads();
-      double kk = 0.0;
-      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) kk += hv[r] * s_p[r];
-      kk = block_sum_d(kk, s_red);
-      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) s_w[r] = 2.0 * (s_p[r] - kk * hv[r]);
+      // warp 0: K = v . p, w = 2 (p - K v)
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double kk = 0.0;
+        for (int r = j + 1 + lane; r < k; r += 32) kk += hv[r] * s_p[r];
+        for (int o = 16; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+        for (int r = j + 1 + lane; r < k; r += 32) s_w[r] = 2.0 * (s_p[r] - kk * hv[r]);
+      }
       __syncthreads();
       const int L = k - j - 1;
       for (int e2 = threadIdx.x; e2 < L * L; e2 += blockDim.x) {
@@ -464,106 +476,121 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
     }
     __syncthreads();
     // eigenvalues number k-1 and k-2 (ascending) by bisection on Sturm counts,
-    // 32 points per step evaluated by the lanes of warp 0
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      double lo = 0.0, hi = 0.0, emax = 0.0;
+    // 32 points per step evaluated by the lanes of warp 0 (the largest) and
+    // warp 1 (the second); each step of the count's recurrence takes 1/q from
+    // an FP32 reciprocal and one Newton step in FP64 (relative error near
+    // 2^-46: only the signs of the q are used, and GB300's FP64 division is
+    // the slow part of this loop)
+    for (int a = threadIdx.x; a + 1 < k; a += blockDim.x) s_e2[a] = s_e[a] * s_e[a];
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const int lane = threadIdx.x & 31, want = threadIdx.x >> 5;
+      double lo = 0.0, hi = 0.0;
       for (int a = 0; a < k; ++a) {
         const double r = (a > 0 ? fabs(s_e[a - 1]) : 0.0) + (a + 1 < k ? fabs(s_e[a]) : 0.0);
         lo = a == 0 ? s_dg[a] - r : fmin(lo, s_dg[a] - r);
         hi = a == 0 ? s_dg[a] + r : fmax(hi, s_dg[a] + r);
-        if (a + 1 < k) emax = fmax(emax, fabs(s_e[a]));
       }
-      const double tiny = 1e-300;
-      for (int want = 0; want < 2; ++want) {
-        const int idx = k - 1 - want;  // ascending index of the eigenvalue
-        double a0 = lo - 1e-12 * (fabs(lo) + fabs(hi)), b0 = hi + 1e-12 * (fabs(lo) + fabs(hi));
-        for (int it = 0; it < 40 && b0 - a0 > 4e-16 * fmax(fabs(a0), fabs(b0)); ++it) {
-          const double x = a0 + (b0 - a0) * (double)(lane + 1) / 33.0;
-          int cnt = 0;  // eigenvalues below x
-          double q = s_dg[0] - x;
-          cnt += q < 0.0;
-          for (int a = 1; a < k; ++a) {
-            if (q == 0.0) q = tiny;
-            q = (s_dg[a] - x) - s_e[a - 1] * s_e[a - 1] / q;
-            cnt += q < 0.0;
+      const int idx = k - 1 - want;  // ascending index of the eigenvalue
+      double a0 = lo - 1e-12 * (fabs(lo) + fabs(hi)), b0 = hi + 1e-12 * (fabs(lo) + fabs(hi));
+      for (int it = 0; it < 40 && b0 - a0 > 4e-16 * fmax(fabs(a0), fabs(b0)); ++it) {
+        const double x = a0 + (b0 - a0) * (double)(lane + 1) / 33.0;
+        int cnt = 0;  // eigenvalues below x
+        double q = s_dg[0] - x;
+        cnt += q < 0.0;
+        for (int a = 1; a < k; ++a) {
+          double r;
+          const double aq = fabs(q);
+          if (aq > 1e-30 && aq < 1e30) {
+            const double r0 = (double)__frcp_rn((float)q);
+            r = r0 * fma(-q, r0, 2.0);
+          } else {
+            r = 1.0 / (q == 0.0 ? 1e-300 : q);
           }
-          // the smallest lane point with more than idx eigenvalues below it
-          const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
-          const int first = above ? __ffs(above) - 1 : 32;
-          const double nb = first < 32 ? a0 + (b0 - a0) * (double)(first + 1) / 33.0 : b0;
-          const double na = first > 0 ? a0 + (b0 - a0) * (double)first / 33.0 : a0;
-          a0 = na;
-          b0 = nb;
+          q = fma(-s_e2[a - 1], r, s_dg[a] - x);
+          cnt += q < 0.0;
         }
-        if (lane == 0) s_lam[want] = 0.5 * (a0 + b0);
+        // the smallest lane point with more than idx eigenvalues below it
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
+        const int first = above ? __ffs(above) - 1 : 32;
+        const double nb = first < 32 ? a0 + (b0 - a0) * (double)(first + 1) / 33.0 : b0;
+        const double na = first > 0 ? a0 + (b0 - a0) * (double)first / 33.0 : a0;
+        a0 = na;
+        b0 = nb;
       }
-      (void)emax;
+      if (lane == 0) s_lam[want] = 0.5 * (a0 + b0);
     }
     __syncthreads();
     // inverse iteration on T - lambda I (tridiagonal LU with partial
-    // pivoting), the second vector kept orthogonal to the first
-    if (threadIdx.x == 0) {
-      for (int want = 0; want < 2; ++want) {
-        double *y = s_y[want];
-        for (int a = 0; a < k; ++a) y[a] = 1.0 + 0.01 * (double)((a * 37) % 11);
-        const double lam = s_lam[want];
-        const double pert = 1e-14 * (fabs(lam) + 1e-300);
-        for (int it = 0; it < 4; ++it) {
-          // factor: dd (diagonal), du (first super), du2 (second super), dl (multipliers)
-          double *dd = s_fd, *du = s_fu, *du2 = s_fu2, *dl = s_fl;
-          for (int a = 0; a < k; ++a) {
-            dd[a] = s_dg[a] - lam;
-            du[a] = a + 1 < k ? s_e[a] : 0.0;
-            dl[a] = a + 1 < k ? s_e[a] : 0.0;
-            du2[a] = 0.0;
+    // pivoting, factored once, two solves), one thread per eigenvalue; the
+    // second vector is then made orthogonal to the first
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+      const int want = threadIdx.x >> 5;
+      double *y = s_y[want];
+      double *dd = s_fd[want], *du = s_fu[want], *du2 = s_fu2[want], *dl = s_fl[want];
+      int *piv = s_piv[want];
+      const double lam = s_lam[want];
+      const double pert = 1e-14 * (fabs(lam) + 1e-300);
+      for (int a = 0; a < k; ++a) {
+        y[a] = 1.0 + 0.01 * (double)((a * 37) % 11);
+        dd[a] = s_dg[a] - lam;
+        du[a] = a + 1 < k ? s_e[a] : 0.0;
+        dl[a] = a + 1 < k ? s_e[a] : 0.0;
+        du2[a] = 0.0;
+      }
+      for (int a = 0; a + 1 < k; ++a) {
+        if (fabs(dd[a]) >= fabs(dl[a])) {
+          if (dd[a] == 0.0) dd[a] = pert;
+          const double f = dl[a] / dd[a];
+          dl[a] = f;
+          dd[a + 1] -= f * du[a];
+          piv[a] = 0;
+        } else {
+          const double f = dd[a] / dl[a];
+          dd[a] = dl[a];
+          dl[a] = f;
+          const double t = du[a];
+          du[a] = dd[a + 1];
+          dd[a + 1] = t - f * dd[a + 1];
+          if (a + 2 < k) {
+            du2[a] = du[a + 1];
+            du[a + 1] = -f * du[a + 1];
           }
-          for (int a = 0; a + 1 < k; ++a) {
-            if (fabs(dd[a]) >= fabs(dl[a])) {
-              if (dd[a] == 0.0) dd[a] = pert;
-              const double f = dl[a] / dd[a];
-              dl[a] = f;
-              dd[a + 1] -= f * du[a];
-              s_piv[a] = 0;
-            } else {
-              const double f = dd[a] / dl[a];
-              dd[a] = dl[a];
-              dl[a] = f;
-              const double t = du[a];
-              du[a] = dd[a + 1];
-              dd[a + 1] = t - f * dd[a + 1];
-              if (a + 2 < k) {
-                du2[a] = du[a + 1];
-                du[a + 1] = -f * du[a + 1];
-              }
-              s_piv[a] = 1;
-            }
-          }
-          if (dd[k - 1] == 0.0) dd[k - 1] = pert;
-          // solve L U x = P y
-          for (int a = 0; a + 1 < k; ++a) {
-            if (s_piv[a] == 0) {
-              y[a + 1] -= dl[a] * y[a];
-            } else {
-              const double t = y[a];
-              y[a] = y[a + 1];
-              y[a + 1] = t - dl[a] * y[a];
-            }
-          }
-          y[k - 1] /= dd[k - 1];
-          if (k >= 2) y[k - 2] = (y[k - 2] - du[k - 2] * y[k - 1]) / dd[k - 2];
-          for (int a = k - 3; a >= 0; --a) y[a] = (y[a] - du[a] * y[a + 1] - du2[a] * y[a + 2]) / dd[a];
-          if (want == 1) {  // keep it orthogonal to the first eigenvector
-            double dt = 0.0;
-            for (int a = 0; a < k; ++a) dt += y[a] * s_y[0][a];
-            for (int a = 0; a < k; ++a) y[a] -= dt * s_y[0][a];
-          }
-          double nr = 0.0;
-          for (int a = 0; a < k; ++a) nr += y[a] * y[a];
-          nr = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
-          for (int a = 0; a < k; ++a) y[a] *= nr;
+          piv[a] = 1;
         }
       }
+      if (dd[k - 1] == 0.0) dd[k - 1] = pert;
+      for (int a = 0; a < k; ++a) dd[a] = 1.0 / dd[a];  // reciprocals for the solves
+      for (int it = 0; it < 2; ++it) {
+        for (int a = 0; a + 1 < k; ++a) {
+          if (piv[a] == 0) {
+            y[a + 1] -= dl[a] * y[a];
+          } else {
+            const double t = y[a];
+            y[a] = y[a + 1];
+            y[a + 1] = t - dl[a] * y[a];
+          }
+        }
+        y[k - 1] *= dd[k - 1];
+        if (k >= 2) y[k - 2] = (y[k - 2] - du[k - 2] * y[k - 1]) * dd[k - 2];
+        for (int a = k - 3; a >= 0; --a) y[a] = (y[a] - du[a] * y[a + 1] - du2[a] * y[a + 2]) * dd[a];
+        double nr = 0.0;
+        for (int a = 0; a < k; ++a) nr += y[a] * y[a];
+        nr = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+        for (int a = 0; a < k; ++a) y[a] *= nr;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double dt = 0.0;
+      for (int a = 0; a < k; ++a) dt += s_y[1][a] * s_y[0][a];
+      double nr = 0.0;
+      for (int a = 0; a < k; ++a) {
+        s_y[1][a] -= dt * s_y[0][a];
+        nr += s_y[1][a] * s_y[1][a];
+      }
+      nr = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+      for (int a = 0; a < k; ++a) s_y[1][a] *= nr;
       s_done = s_lam[0] > 0.0;
       if (L.eig) {
         L.eig[2 * gi] = s_lam[0];
@@ -571,22 +598,29 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_layout(LayoutArgs L) {
       }
     }
     __syncthreads();
-    // z = H_0 H_1 ... H_{k-3} y, the reflectors applied last to first
-    for (int j = k - 3; j >= 0; --j) {
-      const double *hv = Hv + j * kPrepMaxK;
-      double d0 = 0.0, d1 = 0.0;
-      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
-        d0 += hv[r] * s_y[0][r];
-        d1 += hv[r] * s_y[1][r];
+    // z = H_0 H_1 ... H_{k-3} y, the reflectors applied last to first (one
+    // warp: k <= 100 entries, dot products by shuffles, no block barrier)
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int j = k - 3; j >= 0; --j) {
+        const double *hv = Hv + j * kPrepMaxK;
+        double d0 = 0.0, d1 = 0.0;
+        for (int r = j + 1 + lane; r < k; r += 32) {
+          d0 += hv[r] * s_y[0][r];
+          d1 += hv[r] * s_y[1][r];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        for (int r = j + 1 + lane; r < k; r += 32) {
+          s_y[0][r] -= 2.0 * d0 * hv[r];
+          s_y[1][r] -= 2.0 * d1 * hv[r];
+        }
+        __syncwarp();
       }
-      d0 = block_sum_d(d0, s_red);
-      d1 = block_sum_d(d1, s_red);
-      for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) {
-        s_y[0][r] -= 2.0 * d0 * hv[r];
-        s_y[1][r] -= 2.0 * d1 * hv[r];
-      }
-      __syncthreads();
     }
+    __syncthreads();
     if (!s_done) dev_fail(L.status, SSM_E_NUMERIC);
     // each vector signed so that its largest-magnitude entry (lowest index on a tie) is positive
     if (threadIdx.x == 0)
