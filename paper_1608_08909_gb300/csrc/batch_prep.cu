@@ -47,6 +47,9 @@ struct PrepArgs {
   int32_t *ecc;        // [sum k]
   int64_t *lens;       // [G] count-table lengths
   int64_t *medges;     // [G] edges after deduplication
+  int32_t *pairq;      // per block: two queues of pair_cap (pivot, node) pairs
+  int64_t pair_cap;
+  int64_t ubytes;      // the shared region of the three phases
   unsigned *ctr;
   int32_t *status;
 };
@@ -84,17 +87,14 @@ __device__ int block_exclusive_scan(int *a, int len, int *s_part) {
 __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
   extern __shared__ __align__(16) unsigned char psm[];
   const int NM = A.nmax;
-  int *deg = reinterpret_cast<int *>(psm);               // [NM + 1]
-  int *off = deg + (NM + 1);                             // [NM + 1]
-  uint16_t *dist = reinterpret_cast<uint16_t *>(off + (NM + 1));  // [NM]
-  uint16_t *mind = dist + NM;                            // [NM]
-  uint16_t *q0 = mind + NM;                              // [NM]
-  uint16_t *q1 = q0 + NM;                                // [NM]
-  // 2 (NM + 1) ints and 4 NM uint16 before it: 8-byte aligned for any NM
-  unsigned *vis = reinterpret_cast<unsigned *>(q1 + NM);  // [(NM + 31) / 32]
-  int *s_part = reinterpret_cast<int *>(vis + (NM + 31) / 32);       // [kPrepThreads + 1]
-  int *s_ecc = s_part + kPrepThreads + 1;                             // [kPrepMaxK]
-  __shared__ int s_task, s_next;
+  // one region serves the three phases in turn: the CSR build (degrees and
+  // offsets), max/min (running minimum and two queues) and the lockstep
+  // searches (a visited bit per (pivot, node) pair)
+  int *deg = reinterpret_cast<int *>(psm);  // [NM + 1]
+  int *off = deg + (NM + 1);                // [NM + 1]
+  int *s_part = reinterpret_cast<int *>(psm + A.ubytes);  // [kPrepThreads + 1]
+  int *s_ecc = s_part + kPrepThreads + 1;                  // [kPrepMaxK]
+  __shared__ int s_task, s_next, s_piv[kPrepMaxK];
   __shared__ unsigned s_key;
   for (;;) {
     if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctr, 1u);
@@ -163,8 +163,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
     }
     if (threadIdx.x == 0) A.medges[gi] = m2 / 2;
     __syncthreads();
-    // ---- max/min sp (start node 0) with the d_ip rows
-    for (int i = threadIdx.x; i < n; i += blockDim.x) mind[i] = 0xFFFFu;
+    // ---- max/min sp (start node 0): each search lowers the running minimum
+    // mind in place and only continues from nodes the new pivot is strictly
+    // closer to (mind is 1-Lipschitz along edges, so nothing beyond them
+    // can change); the first search reaches everything
+    int *mindi = deg;                                       // [NM] (the CSR arrays are free now)
+    uint16_t *qa = reinterpret_cast<uint16_t *>(off);       // [NM]
+    uint16_t *qb = qa + NM;                                 // [NM]
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mindi[i] = 0x7FFFFFFF;
     __syncthreads();
     for (int a = 0; a < k; ++a) {
       int p = 0;
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
         __syncthreads();
         unsigned best = 0u;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          const unsigned key = ((unsigned)mind[i] << 16) | (0xFFFFu - (unsigned)i);
+          const unsigned key = ((unsigned)mindi[i] << 16) | (0xFFFFu - (unsigned)i);
           best = key > best ? key : best;
         }
         for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -181,19 +187,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
         __syncthreads();
         p = (int)(0xFFFFu - (s_key & 0xFFFFu));
       }
-      if (threadIdx.x == 0) A.pivots[D.piv_off + a] = p;
-      // breadth-first search from p, level by level
-      for (int i = threadIdx.x; i < n; i += blockDim.x) dist[i] = 0xFFFFu;
-      for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) vis[w] = 0u;
-      __syncthreads();
       if (threadIdx.x == 0) {
-        dist[p] = 0;
-        vis[p >> 5] |= 1u << (p & 31);
-        q0[0] = (uint16_t)p;
+        A.pivots[D.piv_off + a] = p;
+        s_piv[a] = p;
+        mindi[p] = 0;
+        qa[0] = (uint16_t)p;
       }
       __syncthreads();
       int ncur = 1;
-      uint16_t *qc = q0, *qn = q1;
+      uint16_t *qc = qa, *qn = qb;
       for (int level = 0; ncur > 0; ++level) {
         if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
@@ -201,11 +203,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
           const int v = qc[t];
           for (int j = rowptr[v]; j < rowptr[v + 1]; ++j) {
             const int u = colidx[j];
-            const unsigned bit = 1u << (u & 31);
-            if (!(atomicOr(vis + (u >> 5), bit) & bit)) {
-              dist[u] = (uint16_t)(level + 1);
-              qn[atomicAdd(&s_next, 1)] = (uint16_t)u;
-            }
+            if (atomicMin(mindi + u, level + 1) > level + 1) qn[atomicAdd(&s_next, 1)] = (uint16_t)u;
           }
         }
         __syncthreads();
@@ -215,14 +213,55 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_pivots(PrepArgs A) {
         qn = t_;
         __syncthreads();
       }
-      uint16_t *row = A.dip + D.dip_off + (int64_t)a * n;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint16_t d = dist[i];
-        if (d == 0xFFFFu) dev_fail(A.status, SSM_E_DISCONNECTED);
-        row[i] = d;
-        mind[i] = min(mind[i], d);
+      if (a == 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+          if (mindi[i] == 0x7FFFFFFF) dev_fail(A.status, SSM_E_DISCONNECTED);
+      __syncthreads();
+    }
+    // ---- d_ip: the k searches in lockstep, one level for all pivots at a
+    // time; (pivot, node) pairs in global queues, one visited bit per pair
+    // in shared memory
+    {
+      unsigned *visk = reinterpret_cast<unsigned *>(psm);  // [(k n + 31) / 32], over the free CSR arrays
+      int32_t *pq0 = A.pairq + (int64_t)blockIdx.x * 2 * A.pair_cap, *pq1 = pq0 + A.pair_cap;
+      uint16_t *dipg = A.dip + D.dip_off;
+      const int words = (k * n + 31) / 32;
+      __syncthreads();
+      for (int w = threadIdx.x; w < words; w += blockDim.x) visk[w] = 0u;
+      __syncthreads();
+      for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        const int p = s_piv[a];
+        const int bit = a * n + p;
+        atomicOr(visk + (bit >> 5), 1u << (bit & 31));
+        dipg[(int64_t)a * n + p] = 0;
+        pq0[a] = (a << 14) | p;
       }
       __syncthreads();
+      int ncur = k;
+      int32_t *qc = pq0, *qn = pq1;
+      for (int level = 0; ncur > 0; ++level) {
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncur; t += blockDim.x) {
+          const int pr = qc[t];
+          const int a = pr >> 14, v = pr & 0x3FFF;
+          for (int j = rowptr[v]; j < rowptr[v + 1]; ++j) {
+            const int u = colidx[j];
+            const int bit = a * n + u;
+            const unsigned m = 1u << (bit & 31);
+            if (!(atomicOr(visk + (bit >> 5), m) & m)) {
+              dipg[(int64_t)a * n + u] = (uint16_t)(level + 1);
+              qn[atomicAdd(&s_next, 1)] = (a << 14) | u;
+            }
+          }
+        }
+        __syncthreads();
+        ncur = s_next;
+        int32_t *t_ = qc;
+        qc = qn;
+        qn = t_;
+        __syncthreads();
+      }
     }
     // ---- regions (ties to the lowest pivot index) and eccentricities
     for (int a = threadIdx.x; a < k; a += blockDim.x) s_ecc[a] = 0;
@@ -702,22 +741,33 @@ struct PrepWs {
   unsigned *ctr;
   int64_t *lens;  // [2 G]: table lengths, then edge counts
   int32_t *tmp;
+  int32_t *pairq;
 };
 
-static void carve_prep(Carver &c, PrepWs &w, int32_t G, int64_t cap) {
+static int prep_blocks(int32_t G) { return std::max(1, std::min(G, num_sms() * 4)); }
+
+// cap < 0: the prefix only (what the layout call uses)
+static void carve_prep(Carver &c, PrepWs &w, int32_t G, int64_t cap, int64_t kn_max) {
   w.pd = c.take<PrepDev>((size_t)G);
   w.ld = c.take<LayoutDev>((size_t)G);
   w.order = c.take<int32_t>((size_t)G);
   w.ctr = c.take<unsigned>(2);
   w.lens = c.take<int64_t>(2 * (size_t)G);
   w.tmp = cap >= 0 ? c.take<int32_t>((size_t)std::max<int64_t>(cap, 1)) : nullptr;
+  w.pairq = cap >= 0 ? c.take<int32_t>((size_t)prep_blocks(G) * 2 * (size_t)std::max<int64_t>(kn_max, 1)) : nullptr;
 }
 
-static size_t prep_smem(int nmax) {
-  const size_t ints = 2 * (size_t)(nmax + 1) * sizeof(int);
-  const size_t u16 = 4 * (size_t)nmax * sizeof(uint16_t);
-  const size_t bits = (size_t)((nmax + 31) / 32) * sizeof(unsigned);
-  return ints + u16 + bits + (kPrepThreads + 1 + kPrepMaxK) * sizeof(int) + 16;
+// the shared region: CSR arrays 2 (nmax + 1) ints, or the visited bits of
+// the lockstep searches, whichever is larger; then the scan and eccentricity
+// scratch
+static int64_t prep_region(int nmax, int64_t kn_max) {
+  const int64_t csr = 2 * ((int64_t)nmax + 1) * (int64_t)sizeof(int);
+  const int64_t bits = (kn_max + 31) / 32 * (int64_t)sizeof(unsigned);
+  return (std::max(csr, bits) + 15) / 16 * 16;
+}
+
+static size_t prep_smem(int nmax, int64_t kn_max) {
+  return (size_t)prep_region(nmax, kn_max) + (kPrepThreads + 1 + kPrepMaxK) * sizeof(int) + 16;
 }
 
 static size_t layout_smem() {
@@ -729,11 +779,14 @@ static size_t layout_smem() {
 // =========================================================== C ABI
 SSM_API size_t ssm_batch_prepare_workspace(int32_t G, const ssm_batch_input *in) {
   if (G < 1 || !in) return 0;
-  int64_t cap = 0;
-  for (int32_t g = 0; g < G; ++g) cap += 2 * std::max<int64_t>(0, in[g].m_in);
+  int64_t cap = 0, kn = 1;
+  for (int32_t g = 0; g < G; ++g) {
+    cap += 2 * std::max<int64_t>(0, in[g].m_in);
+    kn = std::max<int64_t>(kn, (int64_t)std::max(in[g].k, 0) * std::max(in[g].n, 0));
+  }
   ssm::Carver c(nullptr, 0);
   ssm::PrepWs w;
-  ssm::carve_prep(c, w, G, cap);
+  ssm::carve_prep(c, w, G, cap, kn);
   return c.size();
 }
 
@@ -746,7 +799,7 @@ SSM_API int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t
     return fail(SSM_E_ARG, "ssm_batch_pivots: null pointer or G < 1");
   std::vector<PrepDev> pd((size_t)G);
   std::vector<int32_t> order((size_t)G);
-  int64_t node = 0, row = 0, col = 0, piv = 0, dipo = 0, offo = 0, edges = 0;
+  int64_t node = 0, row = 0, col = 0, piv = 0, dipo = 0, offo = 0, edges = 0, kn_max = 1;
   int nmax = 1;
   for (int32_t g = 0; g < G; ++g) {
     const ssm_batch_input &x = in[g];
@@ -765,6 +818,7 @@ SSM_API int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t
     node += x.n; row += x.n + 1; col += 2 * x.m_in; piv += x.k; dipo += (int64_t)x.k * x.n; offo += x.k + 1;
     edges = std::max(edges, x.edge_off + x.m_in);
     nmax = std::max(nmax, x.n);
+    kn_max = std::max<int64_t>(kn_max, (int64_t)x.k * x.n);
     order[(size_t)g] = g;
   }
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -772,7 +826,7 @@ SSM_API int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t
   });
   Carver c(ws, ws_bytes);
   PrepWs w;
-  carve_prep(c, w, G, col);
+  carve_prep(c, w, G, col, kn_max);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_batch_pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemcpyAsync(w.pd, pd.data(), pd.size() * sizeof(PrepDev), cudaMemcpyHostToDevice, s));
   SSM_TRY_CUDA(cudaMemcpyAsync(w.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -781,12 +835,13 @@ SSM_API int ssm_batch_pivots(int32_t G, const ssm_batch_input *in, const int32_t
   A.G = G; A.nmax = nmax; A.desc = w.pd; A.order = w.order; A.src = src; A.dst = dst; A.tmp = w.tmp;
   A.rowptr = rowptr; A.colidx = colidx; A.pivots = pivots; A.region = region; A.dip = dip; A.ecc = ecc;
   A.lens = w.lens; A.medges = w.lens + G; A.ctr = w.ctr; A.status = status;
-  const size_t smem = prep_smem(nmax);
+  A.pairq = w.pairq; A.pair_cap = kn_max; A.ubytes = prep_region(nmax, kn_max);
+  const size_t smem = prep_smem(nmax, kn_max);
   SSM_TRY_CUDA(allow_dynamic_smem((const void *)k_prep_pivots));
   int per_sm = 0;
   SSM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prep_pivots, kPrepThreads, smem));
   if (per_sm < 1) return fail(SSM_E_ARG, "ssm_batch_pivots: %zu bytes of shared memory do not fit", smem);
-  const int blocks = std::max(1, std::min(G, per_sm * num_sms()));
+  const int blocks = std::max(1, std::min(prep_blocks(G), per_sm * num_sms()));
   note_launch(), k_prep_pivots<<<blocks, kPrepThreads, smem, s>>>(A);
   SSM_TRY_CUDA(cudaGetLastError());
   std::vector<int64_t> h(2 * (size_t)G);
@@ -834,7 +889,7 @@ SSM_API int ssm_batch_layout_init(int32_t G, const ssm_batch_graph *graphs, cons
   });
   Carver c(ws, ws_bytes);
   PrepWs w;
-  carve_prep(c, w, G, -1);
+  carve_prep(c, w, G, -1, 0);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_batch_layout_init: workspace %zu bytes, need %zu", ws_bytes, c.size());
   LayoutDev *dd = w.ld;
   int32_t *dorder = w.order;
