@@ -395,13 +395,40 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     kmax = std::max(kmax, g.k);
     tmax_len = std::max<int64_t>(tmax_len, 2 * (int64_t)g.cnt_len + g.k);
   }
-  const int smax = batch_table_floats(nmax, kmax, (int)std::min<int64_t>(tmax_len, 1 << 24));
-  // largest work first
-  std::vector<int32_t> order((size_t)G);
-  for (int32_t i = 0; i < G; ++i) order[(size_t)i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return (int64_t)dv[(size_t)a].n * dv[(size_t)a].k > (int64_t)dv[(size_t)b].n * dv[(size_t)b].k;
-  });
+  (void)nmax; (void)kmax; (void)tmax_len;
+  // size classes: a kernel's shared memory is sized for its largest graph,
+  // so small graphs run in their own launch with many blocks per SM; each
+  // class has its own order (largest work first), counter and block size
+  constexpr int kClasses = 3;
+  const int kClassMax[kClasses] = {1024, 4096, kBatchMaxN};
+  std::vector<int32_t> order;
+  order.reserve((size_t)G);
+  struct Cls {
+    int first, count, nmax, kmax, smax, threads, blocks;
+    int64_t work;
+  } cls[kClasses];
+  for (int ci = 0; ci < kClasses; ++ci) {
+    Cls &C = cls[ci];
+    C.first = (int)order.size();
+    C.nmax = 1; C.kmax = 1; C.work = 0;
+    int64_t tl = 0;
+    for (int32_t i = 0; i < G; ++i) {
+      const int lo = ci == 0 ? 0 : kClassMax[ci - 1];
+      if (graphs[i].n <= lo || graphs[i].n > kClassMax[ci]) continue;
+      order.push_back(i);
+      C.nmax = std::max(C.nmax, graphs[i].n);
+      C.kmax = std::max(C.kmax, graphs[i].k);
+      tl = std::max<int64_t>(tl, 2 * (int64_t)graphs[i].cnt_len + graphs[i].k);
+      C.work += (int64_t)graphs[i].n * graphs[i].k;
+    }
+    C.count = (int)order.size() - C.first;
+    std::stable_sort(order.begin() + C.first, order.end(), [&](int32_t a, int32_t b) {
+      return (int64_t)dv[(size_t)a].n * dv[(size_t)a].k > (int64_t)dv[(size_t)b].n * dv[(size_t)b].k;
+    });
+    C.smax = C.count ? batch_table_floats(C.nmax, C.kmax, (int)std::min<int64_t>(tl, 1 << 24)) : 0;
+    C.threads = threads;
+    C.blocks = 0;
+  }
   int64_t nodes = 0;
   for (int32_t i = 0; i < G; ++i) nodes = std::max<int64_t>(nodes, graphs[i].node_off + graphs[i].n);
   Carver c(ws, ws_bytes);
@@ -415,12 +442,20 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
   A.G = G; A.iters = iters; A.desc = w.desc; A.order = w.order; A.rowptr = rowptr; A.colidx = colidx;
   A.pivots = pivots; A.cnt_off = cnt_off; A.cnt = cnt; A.dip = dip; A.dtile = w.dtile; A.stab = w.stab;
   A.pos = reinterpret_cast<float2 *>(pos); A.rel_change = rel_change; A.ctr = w.ctr; A.status = status;
+  auto class_args = [&](const BatchArgs &base, int ci) {
+    BatchArgs X = base;
+    X.G = cls[ci].count;
+    X.order = w.order + cls[ci].first;
+    X.ctr = w.ctr + ci;
+    return X;
+  };
 
   note_launch(), k_batch_setup<<<G, 256, 0, s>>>(A);
   SSM_TRY_CUDA(cudaGetLastError());
 
   if (threads == 0) {
-    // tune the block size on this batch: a few iterations per candidate on a scratch copy
+    // tune the block size of every class on this batch: a few iterations
+    // per candidate on a scratch copy of the positions
     SSM_TRY_CUDA(cudaStreamSynchronize(s));
     BatchArgs T = A;
     T.pos = w.scratch;
@@ -428,56 +463,87 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     cudaEvent_t e0, e1;
     SSM_TRY_CUDA(cudaEventCreate(&e0));
     SSM_TRY_CUDA(cudaEventCreate(&e1));
-    float best = 0.f;
-    for (int cand : {128, 256, 512}) {
-      for (int rep = 0; rep < 2; ++rep) {  // the first run of a candidate warms it up
-        SSM_TRY_CUDA(cudaMemcpyAsync(w.scratch, pos, (size_t)nodes * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-        int blocks = 0;
-        int rc = batch_grid(cand, nmax, kmax, smax, G, &blocks);
-        if (rc) return rc;
-        SSM_TRY_CUDA(cudaEventRecord(e0, s));
-        rc = launch_batch_sweep(T, cand, blocks, nmax, kmax, smax, s);
-        if (rc) return rc;
-        SSM_TRY_CUDA(cudaEventRecord(e1, s));
-        SSM_TRY_CUDA(cudaEventSynchronize(e1));
-      }
-      float ms = 0.f;
-      SSM_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (threads == 0 || ms < best) {
-        best = ms;
-        threads = cand;
+    for (int ci = 0; ci < kClasses; ++ci) {
+      Cls &C = cls[ci];
+      if (!C.count) continue;
+      const BatchArgs TC = class_args(T, ci);
+      float best = 0.f;
+      C.threads = 0;
+      for (int cand : {128, 256, 512}) {
+        for (int rep = 0; rep < 2; ++rep) {  // the first run of a candidate warms it up
+          SSM_TRY_CUDA(cudaMemcpyAsync(w.scratch, pos, (size_t)nodes * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+          int blocks = 0;
+          int rc = batch_grid(cand, C.nmax, C.kmax, C.smax, C.count, &blocks);
+          if (rc) return rc;
+          SSM_TRY_CUDA(cudaEventRecord(e0, s));
+          rc = launch_batch_sweep(TC, cand, blocks, C.nmax, C.kmax, C.smax, s);
+          if (rc) return rc;
+          SSM_TRY_CUDA(cudaEventRecord(e1, s));
+          SSM_TRY_CUDA(cudaEventSynchronize(e1));
+        }
+        float ms = 0.f;
+        SSM_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (C.threads == 0 || ms < best) {
+          best = ms;
+          C.threads = cand;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  if (threads_used) *threads_used = threads;
-
-  // the sweeps of the whole batch: one CUDA graph (counter reset + persistent kernel), launched once
-  int blocks = 0;
-  {
-    const int rc = batch_grid(threads, nmax, kmax, smax, G, &blocks);
+  int heavy = 0;
+  for (int ci = 0; ci < kClasses; ++ci)
+    if (cls[ci].work > cls[heavy].work) heavy = ci;
+  if (threads_used) *threads_used = cls[heavy].threads;
+  for (int ci = 0; ci < kClasses; ++ci) {
+    if (!cls[ci].count) continue;
+    const int rc = batch_grid(cls[ci].threads, cls[ci].nmax, cls[ci].kmax, cls[ci].smax, cls[ci].count, &cls[ci].blocks);
     if (rc) return rc;
   }
-  // recorded on a private stream (the caller's may be the legacy default
-  // stream, which cannot be captured), launched on the caller's
-  cudaStream_t cs = nullptr;
-  SSM_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+
+  // the sweeps of the whole batch: one CUDA graph (per class a counter reset
+  // and a persistent kernel, the classes on forked branches so that their
+  // kernels can share the GPU), launched once; recorded on private streams
+  // (the caller's may be the legacy default stream, which cannot be
+  // captured), launched on the caller's
+  cudaStream_t cs[kClasses + 1] = {};
+  cudaEvent_t ev[kClasses + 1] = {};
+  for (int q = 0; q <= kClasses; ++q) {
+    SSM_TRY_CUDA(cudaStreamCreateWithFlags(&cs[q], cudaStreamNonBlocking));
+    SSM_TRY_CUDA(cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming));
+  }
+  auto cleanup = [&]() {
+    for (int q = 0; q <= kClasses; ++q) {
+      cudaStreamDestroy(cs[q]);
+      cudaEventDestroy(ev[q]);
+    }
+  };
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
-    cudaStreamDestroy(cs);
+    cleanup();
     SSM_TRY_CUDA(e);
   }
-  const int rc = launch_batch_sweep(A, threads, blocks, nmax, kmax, smax, cs);
-  e = cudaStreamEndCapture(cs, &graph);
-  cudaStreamDestroy(cs);
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
+  int rc = SSM_OK;
+  if ((e = cudaEventRecord(ev[kClasses], cs[0])) == cudaSuccess) {
+    for (int ci = 0; ci < kClasses && rc == SSM_OK && e == cudaSuccess; ++ci) {
+      if (!cls[ci].count) continue;
+      if ((e = cudaStreamWaitEvent(cs[ci + 1], ev[kClasses], 0)) != cudaSuccess) break;
+      rc = launch_batch_sweep(class_args(A, ci), cls[ci].threads, cls[ci].blocks, cls[ci].nmax, cls[ci].kmax,
+                              cls[ci].smax, cs[ci + 1]);
+      if (rc == SSM_OK) e = cudaEventRecord(ev[ci], cs[ci + 1]);
+      if (rc == SSM_OK && e == cudaSuccess) e = cudaStreamWaitEvent(cs[0], ev[ci], 0);
+    }
   }
-  SSM_TRY_CUDA(e);
+  cudaError_t e2 = cudaStreamEndCapture(cs[0], &graph);
+  cleanup();
+  if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    SSM_TRY_CUDA(e != cudaSuccess ? e : e2);
+  }
   e = cudaGraphInstantiate(&exec, graph, 0);
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
   if (exec) cudaGraphExecDestroy(exec);
