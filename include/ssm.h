@@ -101,8 +101,9 @@ int ssm_check(const int32_t *status, cudaStream_t stream);
  * rowptr has n+1 entries, colidx room for 2*m_in.  *m_out (host) receives m;
  * row_classes (host int32[2], may be NULL) the number of rows with 33 to
  * 1024 entries and with more than 1024 (the sweep's launch shape: pass them
- * to ssm_iterate as hints[1], hints[2]).  Synchronous.  Errors are returned directly: SSM_E_GRAPH for an endpoint
- * outside 0..n-1, SSM_E_DISCONNECTED if some node is unreachable from node 0.
+ * to ssm_iterate as hints[1], hints[2]).  Synchronous.  Errors are returned
+ * directly: SSM_E_GRAPH for an endpoint outside 0..n-1, SSM_E_DISCONNECTED
+ * if some node is unreachable from node 0.
  * Requires 1 <= n, 0 <= m_in, 2*m_in < 2^31.
  * ------------------------------------------------------------------- */
 size_t ssm_build_graph_workspace(int32_t n, int64_t m_in);
@@ -182,7 +183,7 @@ int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, in
 
 /* Regions with the paper's own tie rule (Section 3: R is built
  * incrementally while the distances are computed, a tie going to the
- * currently smallest partition), instead of ssm_aggregate's lowest pivot
+ * partition that is smallest at that moment), instead of ssm_aggregate's lowest pivot
  * index.  Reading: nodes join in the order a multi-source search settles
  * them -- increasing distance to their nearest pivots, equal distances by
  * increasing node id; a node with one nearest pivot joins it, a node with

@@ -168,7 +168,7 @@ def regions(dip: np.ndarray) -> np.ndarray:
 
 
 def regions_smallest(dip: np.ndarray) -> np.ndarray:
-    """Regions with the paper's tie rule: ties to the currently smallest region,
+    """Regions with the paper's tie rule: ties to the region that is smallest at that moment,
     nodes taken by increasing distance to their nearest pivot, then by id."""
     dip = np.ascontiguousarray(dip, dtype=np.uint16)
     k, n = dip.shape

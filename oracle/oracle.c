@@ -302,7 +302,7 @@ int orc_regions(int32_t n, int32_t k, const uint16_t *dip, int32_t *region) {
 }
 
 /* Regions with the paper's tie rule (Section 3: R is built incrementally
- * while the distances are computed, a tie going to the currently smallest
+ * while the distances are computed, a tie going to the smallest
  * partition).  Reading: nodes join in the order a multi-source search
  * settles them -- increasing distance L_i = min_a d_ia to their nearest
  * pivots, equal distances by increasing node id; a node with one nearest

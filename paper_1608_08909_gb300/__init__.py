@@ -292,7 +292,7 @@ def ssm_aggregate(dip: torch.Tensor, cnt_len: int | None = None, stream=None, ch
 
 
 def ssm_regions_smallest(dip: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
-    """Regions with the paper's tie rule (ties to the currently smallest region)."""
+    """Regions with the paper's tie rule (ties to the region that is smallest at that moment)."""
     L = lib()
     k, n = dip.shape
     dev = dip.device

@@ -134,8 +134,8 @@ __global__ void k_row_prefix(int32_t k, const int32_t *__restrict__ cnt_off, int
 
 // ---------------------------------------------------------------- the paper's tie rule
 // Regions as Section 3 builds them: incrementally while the distances are
-// computed, a tie going to the currently smallest partition.  Nodes join in
-// the order a multi-source search settles them (increasing distance L to the
+// computed, a tie going to the partition that is smallest at that moment.
+// Nodes join in the order a multi-source search settles them (increasing distance L to the
 // nearest pivot, then increasing id); a node with several nearest pivots
 // joins the one whose region is smallest at that moment (lowest index on
 // equal sizes).  The prepass finds each node's L and its nearest pivots
