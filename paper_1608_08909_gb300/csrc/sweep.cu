@@ -9,6 +9,12 @@
 //   w'_ia = s / d_ia^2,  s = cnt[cnt_off[a] + min(floor(d_ia/2), ecc_a)]
 // A term with r == 0 contributes w * x_j only.  d_ia <= 1 skips the pivot
 // (the pivot itself, or a neighbour already counted as an edge term).
+// The FP32 kernel evaluates the same update about x_i (W = sum_a w'_ia):
+//   x_i^{t+1} = x_i + (sum_a (B_a - w'_ia)(x_i - x_pa)
+//                      + sum_j (x_j - x_i)(1 - 1/r_ij)) / den,  B_a = w'_ia d_ia / r_ia,
+// since num = x_i den + those two sums; every sum is over differences, so the
+// result does not depend on where the layout sits, and a pivot costs two
+// accumulations per node instead of four.
 //
 // FP32 kernel, GB300 layout:
 //  * a lane owns kNpl = 4 consecutive nodes (two packed pairs); their d_ia for
@@ -19,18 +25,19 @@
 //    arithmetic);
 //  * full-table mode (graphs whose largest d_ip fits a k x (dmax+1) table in
 //    shared memory, e.g. small-world graphs): the table holds (w, w d) for
-//    every pivot and distance, w = s / d^2, so a term is one table gather, one
-//    rsqrt (u = 1/r) and B = (w d) u = w d / r; it adds w x_p + B (x_i - x_p)
-//    to the numerator.  The denominator deg(i) + sum_a w'_ia does not change
-//    between iterations and is summed once per ssm_iterate call;
+//    every pivot and distance, w = s / d^2 (stored as -w), so a term is one
+//    table gather, one rsqrt (u = 1/r) and B - w = (w d) u - w; it adds
+//    (B - w)(x_i - x_p).  The denominator deg(i) + sum_a w'_ia does not
+//    change between iterations and is summed once per ssm_iterate call;
 //  * clamped mode (large distances): s comes from a per-pivot table indexed
 //    directly by d (0 for d < 2, cnt[min(d/2, ecc)] up to d = 2 ecc + 2, then
 //    |R(a)|), and the term uses one rsqrt per node: with q = d^2 r^2,
 //    u = q^{-1/2}, B = s u = w d / r and W = B u r^2 = s / d^2 = w, it adds
-//    W x_p + B (x_i - x_p) to the numerator and W to the denominator;
+//    (B - W)(x_i - x_p) to the numerator and W to the denominator;
 //  * in both modes the node pair is evaluated with packed FP32x2 arithmetic
 //    where the operands pair up naturally; r^2 gets + 1e-24 so coincident
-//    points (r == 0) add w x_p, as the r == 0 rule says (the clamped mode
+//    points (r == 0, x_i - x_p = 0) add nothing about x_i, i.e. w x_p, as the
+//    r == 0 rule says (the clamped mode
 //    also adds 1e-36 to q so it stays positive at d = 0; relative change of a
 //    term with r >= 1e-6 below 1e-12); tables and pivot positions sit in
 //    shared memory, loaded once per persistent block;
@@ -78,7 +85,7 @@ constexpr float kR2Floor = 1e-24f;
 #define SSM_SWEEP_MIN_BLOCKS 2
 #endif
 #ifndef SSM_SWEEP_FULL_MIN_BLOCKS
-#define SSM_SWEEP_FULL_MIN_BLOCKS 2
+#define SSM_SWEEP_FULL_MIN_BLOCKS 3
 #endif
 constexpr int kPrefetch = SSM_SWEEP_PREFETCH;  // pivots whose d words are loaded ahead
 // 1: the tile's positions are read again for the update instead of being kept in registers
@@ -115,7 +122,7 @@ struct SweepArgs {
   double *tile_part;      // [ntiles][2] (sum dx^2, sum x^2) per tile
   int32_t nsplit;         // pivot ranges per tile (1: a warp takes whole tiles)
   int32_t psplit;         // pivots per range
-  float2 *part;           // [5][ntiles * nsplit][32] partial sums of the ranges (nsplit > 1)
+  float2 *part;           // [3 kPpl][ntiles * nsplit][32] partial sums of the ranges (nsplit > 1)
   unsigned *arrive;       // [ntiles] ranges of the tile finished so far (nsplit > 1)
   int32_t *stop;          // set when the relative change fell below tol
   int32_t *iters_done;
@@ -201,13 +208,14 @@ __device__ void finish_iteration(const SweepArgs &A, unsigned ntiles) {
   }
 }
 
-// neighbour term x_j + (x_i - x_j)/r (r == 0: x_j)
+// neighbour term less x_i: x_j + (x_i - x_j)/r - x_i = (x_j - x_i)(1 - 1/r)
+// (r == 0: x_j - x_i = 0)
 __device__ __forceinline__ void edge_term(float xi, float yi, float2 q, float &sx, float &sy) {
-  const float dx = xi - q.x, dy = yi - q.y;
-  const float r2 = fmaf(dx, dx, dy * dy);
-  const float inv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
-  sx += fmaf(dx, inv, q.x);
-  sy += fmaf(dy, inv, q.y);
+  const float ex = q.x - xi, ey = q.y - yi;
+  const float r2 = fmaf(ex, ex, ey * ey);
+  const float f = r2 > 0.f ? 1.f - rsqrt_approx(r2) : 0.f;
+  sx = fmaf(ex, f, sx);
+  sy = fmaf(ey, f, sy);
 }
 
 // one lane walks a short row in batches of kNbrBatch: the batch's column
@@ -250,8 +258,8 @@ __device__ __forceinline__ void warp_row(const float2 *__restrict__ pin, const i
   sy = warp_sumf(sy);
 }
 
-// Neighbour sums nb[i] = sum_{j in N(i)} (x_j + (x_i - x_j)/r_ij) (r == 0:
-// x_j) for one iteration.  Blocks [0, nlong) take one long row each (a
+// Neighbour sums nb[i] = sum_{j in N(i)} (x_j + (x_i - x_j)/r_ij - x_i) =
+// sum_j (x_j - x_i)(1 - 1/r_ij) (r == 0: 0) for one iteration.  Blocks [0, nlong) take one long row each (a
 // block-stride walk, then a fixed-order block sum), the next ceil(nmid / 8)
 // blocks one medium row per warp, the rest one node per thread (rows of at
 // most kShortDeg entries; longer rows were listed).  Every sum has a fixed
@@ -406,22 +414,24 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 
     // pivot terms, a in [a_lo, a_hi).  The d words of the next kPrefetch pivots
     // are always in flight; lanes past the last node read zeros (d = 0: no
-    // term).  Per pivot with B = s u, W = B u r^2 the numerator gains
-    // W x_p + B (x_i - x_p); the two parts are summed apart
-    // (wx += W (-x_p), bx += B (x_i - x_p)) so that no sum cancels.
-    float2 wx2[kPpl], wy2[kPpl], bx2[kPpl], by2[kPpl], den2[kPpl];
+    // term).  A pivot adds w x_p + B (x_i - x_p) to the numerator and w to the
+    // denominator (B = w d / r); about x_i that is (B - w)(x_i - x_p) added to
+    // ax, ay (and w to den in the clamped mode)
+    float2 ax2[kPpl], ay2[kPpl], den2[kPpl];
 #pragma unroll
     for (int j = 0; j < kPpl; ++j) {
-      wx2[j] = wy2[j] = bx2[j] = by2[j] = den2[j] = make_float2(0.f, 0.f);
+      ax2[j] = ay2[j] = den2[j] = make_float2(0.f, 0.f);
     }
     // this tile's d words: pivot a of lane l at tp[a * 32] (one contiguous
     // 32 kPpl-word row per pivot, kPpl words -- kNpl distances -- per lane)
     const DWords *tp = reinterpret_cast<const DWords *>(A.dtile) + (size_t)tile * (size_t)k * 32u + lane;
     auto load_words = [&](int a) -> DWords { return __ldg(tp + (unsigned)a * 32u); };
     float2 kTiny2 = make_float2(kR2Floor, kR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
+    float2 kMinus2 = make_float2(-1.f, -1.f);
     asm volatile("" : "+f"(kTiny2.x), "+f"(kTiny2.y), "+f"(kTinyQ2.x), "+f"(kTinyQ2.y));
+    if (!FULL) asm volatile("" : "+f"(kMinus2.x), "+f"(kMinus2.y));
     // full-table mode: a d word holds the byte offsets 4 (a (dmax + 1) + d) of
-    // two nodes' table entries; w and w d of a node pair land in register
+    // two nodes' table entries; -w and w d of a node pair land in register
     // pairs (the two planes sit a fixed kFullPlaneBytes apart), so every
     // product is packed
     auto pivot_term_full = [&](int a, DWords pw) {
@@ -430,15 +440,15 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        float2 w2, wd2;
+        float2 nw2, wd2;
         if constexpr (kFullLds == 0) {
           const unsigned al = wtab0 + (pk & 0xFFFFu), ah = wtab0 + (pk >> 16);
-          w2 = make_float2(lds_f32(al), lds_f32(ah));
+          nw2 = make_float2(lds_f32(al), lds_f32(ah));
           wd2 = make_float2(lds_f32(al + kFullPlaneBytes), lds_f32(ah + kFullPlaneBytes));
         } else {
           const char *tb = reinterpret_cast<const char *>(g_wtab);
           const unsigned ol = pk & 0xFFFFu, oh = pk >> 16;
-          w2 = make_float2(*reinterpret_cast<const float *>(tb + ol), *reinterpret_cast<const float *>(tb + oh));
+          nw2 = make_float2(*reinterpret_cast<const float *>(tb + ol), *reinterpret_cast<const float *>(tb + oh));
           wd2 = make_float2(*reinterpret_cast<const float *>(tb + kFullPlaneBytes + ol),
                             *reinterpret_cast<const float *>(tb + kFullPlaneBytes + oh));
         }
@@ -448,11 +458,9 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
         float2 u2;
         u2.x = rsqrt_approx(r2.x);
         u2.y = rsqrt_approx(r2.y);
-        const float2 B2 = __fmul2_rn(wd2, u2);  // w d / r
-        wx2[j] = __ffma2_rn(w2, px2, wx2[j]);
-        wy2[j] = __ffma2_rn(w2, py2, wy2[j]);
-        bx2[j] = __ffma2_rn(B2, dx2, bx2[j]);
-        by2[j] = __ffma2_rn(B2, dy2, by2[j]);
+        const float2 c2 = __ffma2_rn(wd2, u2, nw2);  // B - w = w d / r - w
+        ax2[j] = __ffma2_rn(c2, dx2, ax2[j]);
+        ay2[j] = __ffma2_rn(c2, dy2, ay2[j]);
       }
     };
     auto pivot_term = [&](int a, DWords pw) {
@@ -492,10 +500,9 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
         u2.y = rsqrt_approx(q2.y);
         const float2 B2 = __fmul2_rn(s2, u2);                  // s/(d r) = w d / r
         const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);  // s/d^2 = w
-        wx2[j] = __ffma2_rn(W2, px2, wx2[j]);
-        wy2[j] = __ffma2_rn(W2, py2, wy2[j]);
-        bx2[j] = __ffma2_rn(B2, dx2, bx2[j]);
-        by2[j] = __ffma2_rn(B2, dy2, by2[j]);
+        const float2 c2 = __ffma2_rn(W2, kMinus2, B2);         // B - w
+        ax2[j] = __ffma2_rn(c2, dx2, ax2[j]);
+        ay2[j] = __ffma2_rn(c2, dy2, ay2[j]);
         den2[j] = __fadd2_rn(den2[j], W2);
       }
     };
@@ -520,16 +527,14 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
     if (nsplit > 1) {
       // publish this range's sums; the last range of the tile adds all of them
       // in range order and goes on to update the nodes.  Layout:
-      // part[(q kPpl + j) stride + task 32 + lane], q = wx, wy, bx, by, den
+      // part[(q kPpl + j) stride + task 32 + lane], q = ax, ay, den
       const size_t stride = (size_t)ntasks * 32u;
       float2 *pp = A.part + (size_t)task * 32u + lane;
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
-        pp[(0 * kPpl + j) * stride] = wx2[j];
-        pp[(1 * kPpl + j) * stride] = wy2[j];
-        pp[(2 * kPpl + j) * stride] = bx2[j];
-        pp[(3 * kPpl + j) * stride] = by2[j];
-        if (!FULL) pp[(4 * kPpl + j) * stride] = den2[j];
+        pp[(0 * kPpl + j) * stride] = ax2[j];
+        pp[(1 * kPpl + j) * stride] = ay2[j];
+        if (!FULL) pp[(2 * kPpl + j) * stride] = den2[j];
       }
       __threadfence();
       __syncwarp();
@@ -543,21 +548,16 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         float2 s0 = __ldcg(q + (0 * kPpl + j) * stride), s1 = __ldcg(q + (1 * kPpl + j) * stride);
-        float2 s2 = __ldcg(q + (2 * kPpl + j) * stride), s3 = __ldcg(q + (3 * kPpl + j) * stride);
-        float2 s4 = FULL ? make_float2(0.f, 0.f) : __ldcg(q + (4 * kPpl + j) * stride);
+        float2 s2 = FULL ? make_float2(0.f, 0.f) : __ldcg(q + (2 * kPpl + j) * stride);
         for (unsigned r = 1; r < nsplit; ++r) {
           const float2 *qr = q + (size_t)r * 32u;
           s0 = __fadd2_rn(s0, __ldcg(qr + (0 * kPpl + j) * stride));
           s1 = __fadd2_rn(s1, __ldcg(qr + (1 * kPpl + j) * stride));
-          s2 = __fadd2_rn(s2, __ldcg(qr + (2 * kPpl + j) * stride));
-          s3 = __fadd2_rn(s3, __ldcg(qr + (3 * kPpl + j) * stride));
-          if (!FULL) s4 = __fadd2_rn(s4, __ldcg(qr + (4 * kPpl + j) * stride));
+          if (!FULL) s2 = __fadd2_rn(s2, __ldcg(qr + (2 * kPpl + j) * stride));
         }
-        wx2[j] = s0;
-        wy2[j] = s1;
-        bx2[j] = s2;
-        by2[j] = s3;
-        den2[j] = s4;
+        ax2[j] = s0;
+        ay2[j] = s1;
+        den2[j] = s2;
       }
     }
 
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
       const int j = q >> 1;
       const bool hi = (q & 1) != 0;
       const bool live = i < n;
-      // neighbour terms (w = 1, d = 1), summed by k_sweep_nbr
+      // neighbour terms (w = 1, d = 1) less deg(i) x_i, summed by k_sweep_nbr
       const float2 nbq = live ? __ldg(A.nb + i) : make_float2(0.f, 0.f);
       float dn;
       if (FULL) {
@@ -581,8 +581,8 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
         dn = (hi ? den2[j].y : den2[j].x) + (float)(rnext - rprev);
         rprev = rnext;
       }
-      const float nx = hi ? bx2[j].y - wx2[j].y : bx2[j].x - wx2[j].x;
-      const float ny = hi ? by2[j].y - wy2[j].y : by2[j].x - wy2[j].x;
+      const float nx = hi ? ax2[j].y : ax2[j].x;
+      const float ny = hi ? ay2[j].y : ay2[j].x;
       // a NaN (clamped mode: in the weights; full-table mode: in the numerator) is an error
       const float chk = FULL ? nx + ny : (hi ? den2[j].y : den2[j].x);
       if (live && !(chk == chk)) dev_fail(A.status, SSM_E_NUMERIC);
@@ -592,9 +592,8 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 #else
         const float2 x = xs[q];
 #endif
-        const float xn = dn > 0.f ? (nx + nbq.x) / dn : x.x, yn = dn > 0.f ? (ny + nbq.y) / dn : x.y;
-        pout[i] = make_float2(xn, yn);
-        const float ex = xn - x.x, ey = yn - x.y;
+        const float ex = dn > 0.f ? (nx + nbq.x) / dn : 0.f, ey = dn > 0.f ? (ny + nbq.y) / dn : 0.f;
+        pout[i] = make_float2(x.x + ex, x.y + ey);
         cn = fmaf(ex, ex, fmaf(ey, ey, cn));
         cd = fmaf(x.x, x.x, fmaf(x.y, x.y, cd));
       }
@@ -612,9 +611,11 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 // dtile[((t k + a) 32 + l) kPpl + j] = e(d_ip[a][i]) | e(d_ip[a][i + 1]) << 16 with
 // i = t kTileNodes + kNpl l + 2 j (d = 0 past the last node); e(d) = d, or in
 // full-table mode (row = dmax + 1 > 0) the byte offset kTabEntryBytes (a row + d)
-// of the node's entry in the shared-memory table
+// of the node's entry in the shared-memory table.  A distance above the table
+// (a wrong dmax hint) is recorded as SSM_E_ARG and clamped, so no table read
+// leaves the table
 __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__restrict__ dip,
-                           unsigned *__restrict__ dtile) {
+                           unsigned *__restrict__ dtile, int32_t *__restrict__ status) {
   const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
   const int64_t total = ntiles * (int64_t)k * 32 * kPpl;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
@@ -629,6 +630,12 @@ __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__
     unsigned lo = i < n ? (unsigned)__ldg(drow + i) : 0u;
     unsigned hi = i + 1 < n ? (unsigned)__ldg(drow + i + 1) : 0u;
     if (row > 0) {
+      const unsigned top = (unsigned)row - 1u;
+      if (lo > top || hi > top) {
+        dev_fail(status, SSM_E_ARG);
+        lo = min(lo, top);
+        hi = min(hi, top);
+      }
       lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
       hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
     }
@@ -648,7 +655,7 @@ __global__ void k_build_stab(int32_t k, const int32_t *__restrict__ cnt_off, con
   }
 }
 
-// full-table mode: wtab[a (dmax+1) + d] = w and wtab[kFullPlane + a (dmax+1) + d]
+// full-table mode: wtab[a (dmax+1) + d] = -w and wtab[kFullPlane + a (dmax+1) + d]
 // = w d, w = s / d^2 with s as in k_build_stab (0 for d < 2), rounded from double
 __global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict__ cnt_off,
                              const uint32_t *__restrict__ cnt, float *__restrict__ wtab) {
@@ -662,7 +669,7 @@ __global__ void k_build_wtab(int32_t k, int32_t dmax, const int32_t *__restrict_
       w = (float)(sd / (dd * dd));
       wd = (float)(sd / dd);
     }
-    wtab[t] = w;
+    wtab[t] = -w;
     wtab[kFullPlane + t] = wd;
   }
 }
@@ -686,8 +693,8 @@ __global__ void k_sweep_den(int32_t n, int32_t k, const unsigned *__restrict__ d
 #pragma unroll
       for (int j = 0; j < kPpl; ++j) {
         const unsigned pk = dword(pw, j);
-        acc[2 * j] += __ldg(wtab + (pk & 0xFFFFu) / kTabEntryBytes);
-        acc[2 * j + 1] += __ldg(wtab + (pk >> 16) / kTabEntryBytes);
+        acc[2 * j] -= __ldg(wtab + (pk & 0xFFFFu) / kTabEntryBytes);  // the table holds -w
+        acc[2 * j + 1] -= __ldg(wtab + (pk >> 16) / kTabEntryBytes);
       }
     }
     const int64_t i0 = tile * kTileNodes + (int64_t)kNpl * lane;
@@ -866,7 +873,7 @@ static size_t carve_iterate(Carver &c, IterWs &w, int32_t n, int64_t m2, int32_t
   w.den = precision == 64 ? nullptr : c.take<float>((size_t)n);
   w.meta = c.take<unsigned>(4);
   w.split_cap = precision == 64 ? 0 : split_capacity(n);
-  w.part = w.split_cap ? c.take<float2>(5 * kPpl * 32 * (size_t)w.split_cap) : nullptr;
+  w.part = w.split_cap ? c.take<float2>(3 * kPpl * 32 * (size_t)w.split_cap) : nullptr;
   w.arrive = w.split_cap ? c.take<unsigned>((size_t)((n + kTileNodes - 1) / kTileNodes)) : nullptr;
   return c.size();
 }
@@ -946,7 +953,7 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     A.dmax = (int32_t)dmax;
     A.wtab = w.wtab;
     A.den = w.den;
-    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile);
+    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile, status);
     if (full) {
       note_launch(), k_build_wtab<<<std::max(1, std::min(sms * 4, (int)(((int64_t)k * (dmax + 1) + 255) / 256))), 256, 0,
                                     s>>>(k, (int32_t)dmax, cnt_off, cnt, w.wtab);

@@ -126,9 +126,11 @@ def _coincident_state(prep, rng, count):
     return x
 
 
-@pytest.mark.parametrize("name,k,kernel", [("grid32", 50, "f32_full_table"), ("rgg", 100, "f32_clamped_smem")])
+@pytest.mark.parametrize("name,k,kernel", [("grid32", 50, "f32_full_table"), ("rgg", 100, "f32_clamped_smem"),
+                                           ("ba", 40, "f32_full_table")])
 def test_sweep_coincident_positions(name, k, kernel):
-    n, s, d = {"grid32": lambda: I.grid(32, 32), "rgg": lambda: I.rgg(6000, 8.0, 7)}[name]()
+    n, s, d = {"grid32": lambda: I.grid(32, 32), "rgg": lambda: I.rgg(6000, 8.0, 7),
+               "ba": lambda: I.ba(12000, 4, 3)}[name]()
     prep = O.prepare(n, s, d, k)
     x0 = _coincident_state(prep, np.random.default_rng(3), 40)
     # the state really has coincident pivot and edge terms

@@ -651,3 +651,18 @@ def test_iterate_with_hints_returns_before_the_stream_drains():
     without = time.perf_counter() - t0
     torch.cuda.synchronize()
     assert with_hints < 0.2 < without
+
+
+def test_iterate_rejects_a_dmax_hint_below_the_largest_distance():
+    """A largest-distance hint below the true one would send table reads past
+    the table: the tiled copy clamps them and the call fails with
+    SSM_E_ARG instead."""
+    n, s, d = GRAPHS["ba"]()
+    g, P, pos, _ = ssm.prepare(n, s, d, 64)
+    assert P.dmax >= 4
+    bad = ssm.Pivots(P.k, P.pivots, P.dip, P.region, P.cnt_off, P.cnt, P.dmax - 2)
+    with pytest.raises(ssm.SSMError) as e:
+        ssm.ssm_iterate(g, bad, pos.clone(), 1)
+    assert e.value.code == -1
+    # the context stays usable
+    ssm.ssm_iterate(g, P, pos, 1)
