@@ -88,6 +88,15 @@ unsigned long long ssm_set_wait_limit_ns(unsigned long long ns);
  * A diagnostic with no counterpart in the paper. */
 void ssm_last_sweep_config(int32_t *out);
 
+/* What the last max/min pivot selection on this host thread chose, in out[2]
+ * (host): out[0] the thread-block cluster size of the cluster kernel (0: the
+ * cooperative grid kernel; -1: no call yet), out[1] bytes of the distance to
+ * the closest pivot per node (4, or 2 for graphs whose 4-byte array does not
+ * fit the cluster; a search deeper than 65534 levels then hands the whole
+ * selection to the grid kernel on the device).  A diagnostic with no
+ * counterpart in the paper. */
+void ssm_last_pivot_config(int32_t *out);
+
 /* Synchronous: waits for `stream`, then returns the device status word
  * (SSM_OK if it is 0), or SSM_E_CUDA if the stream reported a CUDA error. */
 int ssm_check(const int32_t *status, cudaStream_t stream);

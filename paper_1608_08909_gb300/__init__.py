@@ -24,7 +24,7 @@ __all__ = [
     "SSMError", "lib", "ssm_build_graph", "ssm_select_pivots", "ssm_pivot_bfs", "ssm_aggregate_size",
     "ssm_aggregate", "ssm_aggregate_noalloc", "ssm_gram", "ssm_pivotmds", "ssm_batch_iterate",
     "ssm_batch_prepare", "ssm_batch_iterate_packed", "BatchPacked", "ssm_iterate", "ssm_stress", "ssm_check", "Graph", "Pivots", "layout",
-    "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
+    "ssm_set_wait_limit_ns", "ssm_last_sweep_config", "ssm_last_pivot_config", "ssm_kmeans_pivots", "ssm_iterate_gs", "ssm_apsp",
     "ssm_iterate_hints", "ssm_full_iterate", "ssm_regions_smallest", "ssm_aggregate_regions", "ssm_procrustes", "ssm_hull_error", "ssm_gabriel_jaccard",
     "WGraph", "ssm_build_wgraph", "ssm_pivot_sssp", "ssm_select_pivots_weighted", "ssm_weighted_counts",
     "ssm_pivotmds_weighted", "ssm_iterate_weighted", "ssm_stress_weighted", "layout_weighted",
@@ -63,6 +63,7 @@ def lib():
                 "ssm_kernel_launches": (ctypes.c_ulonglong, []),
                 "ssm_set_wait_limit_ns": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
                 "ssm_last_sweep_config": (None, [v]),
+                "ssm_last_pivot_config": (None, [v]),
                 "ssm_check": (ctypes.c_int, [v, v]),
                 "ssm_build_graph_workspace": (sz, [i32, i64]),
                 "ssm_build_graph": (ctypes.c_int, [i32, i64, v, v, v, v, v, v, v, sz, v]),
@@ -142,6 +143,13 @@ def ssm_last_sweep_config() -> dict:
     kinds = {-1: None, 0: "f32_clamped_smem", 1: "f32_clamped_global", 2: "f32_full_table", 3: "f64_counts_smem",
              4: "f64_counts_global"}
     return {"kernel": kinds.get(out[0], out[0]), "nsplit": out[1], "blocks": out[2], "dmax": out[3]}
+
+
+def ssm_last_pivot_config() -> dict:
+    """What the last max/min selection on this thread chose (ssm_last_pivot_config)."""
+    out = (ctypes.c_int32 * 2)()
+    lib().ssm_last_pivot_config(ctypes.cast(out, ctypes.c_void_p))
+    return {"cluster": out[0], "mind_bytes": out[1]}
 
 
 def _require_cuda():

@@ -139,6 +139,7 @@ struct MaxMinArgs {
   unsigned *level;    // level reached by a solo phase of block 0
   unsigned long long *best;  // [2] packed (mind << 32 | ~node) maxima, by pivot parity
   BarrierState *bar;
+  const unsigned *run_if;  // non-null: run only if *run_if != 0 (the cluster kernel gave the search up)
 };
 
 // Block 0 alone expands levels L, L+1, ... while the frontier has at most
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
   const unsigned n = (unsigned)A.n;
+  if (A.run_if && __ldcg(A.run_if) == 0u) return;  // every block, before any barrier
 
   for (unsigned v = gtid; v < n; v += nthreads) A.mind[v] = kInf;
   if (!grid_barrier(A.bar, A.status)) return;
@@ -316,22 +318,11 @@ static void carve_maxmin(Carver &c, MaxMinArgs &A, unsigned **spill, int32_t n, 
   A.best = c.take<unsigned long long>(2);
   A.bar = c.take<BarrierState>(1);
   *spill = c.take<unsigned>(std::max<size_t>(1, maxmin_cluster_spill_entries(n)));
+  A.run_if = c.take<unsigned>(1);
 }
 
-int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
-                  int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
-  Carver c(ws, ws_bytes);
-  MaxMinArgs A;
-  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
-  A.pivots = pivots; A.status = status;
-  unsigned *spill = nullptr;
-  carve_maxmin(c, A, &spill, n, m2);
-  if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
-  int rc = expand_adj(m2, rowptr, colidx, const_cast<int4 *>(A.adj), s);
-  if (rc) return rc;
-  bool launched = false;
-  rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, s, &launched);
-  if (rc || launched) return rc;
+// the cooperative grid kernel, after resetting its counters and barrier
+static int launch_maxmin_grid(MaxMinArgs A, cudaStream_t s) {
   SSM_TRY_CUDA(cudaMemsetAsync(A.qcnt, 0, 4 * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, 2 * sizeof(unsigned long long), s));
   if (int rc_ = reset_barrier(A.bar, s)) return rc_;
@@ -345,6 +336,37 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   return SSM_OK;
 }
 
+// Graphs whose mind fits a cluster: the first search (from start, over every
+// node) on the grid kernel, the other k - 1 searches (pruned, mostly small)
+// in the cluster; with a 2-byte mind the full grid selection is queued behind
+// them and runs only if the cluster handed over (a search deeper than 65534
+// levels).  Other graphs: the grid kernel alone.
+int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k, int32_t start,
+                  int32_t *pivots, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Carver c(ws, ws_bytes);
+  MaxMinArgs A;
+  A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.k = k; A.start = start;
+  A.pivots = pivots; A.status = status;
+  unsigned *spill = nullptr;
+  carve_maxmin(c, A, &spill, n, m2);
+  if (!c.ok) return fail(SSM_E_NOMEM, "max/min pivots: workspace %zu bytes, need %zu", ws_bytes, c.size());
+  int rc = expand_adj(m2, rowptr, colidx, const_cast<int4 *>(A.adj), s);
+  if (rc) return rc;
+  unsigned *fallback = const_cast<unsigned *>(A.run_if);
+  A.run_if = nullptr;
+  if (k >= 2 && maxmin_cluster_mind_bytes(n) > 0) {
+    MaxMinArgs first = A;
+    first.k = 1;
+    if ((rc = launch_maxmin_grid(first, s))) return rc;
+    int mind_bytes = 0;
+    rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, fallback, A.mind, A.best, s,
+                               &mind_bytes);
+    if (rc || mind_bytes == 4) return rc;
+    if (mind_bytes == 2) A.run_if = fallback;
+  }
+  if (!A.run_if) note_pivot_config(0, 4);
+  return launch_maxmin_grid(A, s);
+}
 size_t maxmin_workspace(int32_t n, int64_t m2) {
   Carver c(nullptr, 0);
   MaxMinArgs A;

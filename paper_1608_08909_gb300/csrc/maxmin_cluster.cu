@@ -6,7 +6,11 @@
 // whole chain runs in one cluster of C CTAs (C = 8 or 16):
 //   * node v belongs to CTA v mod C; its mind sits in that CTA's shared
 //     memory at slot v div C, so claiming a node is one DSMEM atomicMin
-//     (about 0.1 us) instead of an L2 atomic;
+//     (about 0.1 us) instead of an L2 atomic.  Graphs too large for 4 bytes
+//     per node keep mind in 2 bytes (distances stay below 65535 like d_ip):
+//     two nodes share a 32-bit word and a claim is a DSMEM compare-and-swap
+//     on it (within one level every claim writes the same value, so a word
+//     changes at most twice per level and the retry loop is short);
 //   * a claimed node is pushed, with its row range, into the frontier queue
 //     of its owner (a DSMEM atomicAdd for the slot and a DSMEM store), so the
 //     next level reads every entry from local shared memory and the levels
@@ -19,9 +23,12 @@
 //     balanced over the lanes;
 //   * the argmax of mind (ties to the lowest node id) is a scan of each
 //     CTA's own slice plus an exchange of C packed keys.
+// A search deeper than a 2-byte mind holds stops the kernel and leaves the
+// whole selection to the grid kernel, queued behind it on the same stream.
 // Queue entries beyond the shared-memory capacity go to a global spill area
 // (node ids only), so any frontier size is handled.
 #include <algorithm>
+#include <type_traits>
 
 #include "bfs.cuh"
 
@@ -39,6 +46,8 @@ constexpr int kMcQcapMin = 1024;
 #endif
 constexpr int kMcU = SSM_MC_U;  // edge slots per lane in flight
 constexpr unsigned kMcInf = 0xFFFFFFFFu;
+constexpr unsigned kMcInf16 = 0xFFFFu;
+constexpr int kMcCasTries = 64;  // a claim gives up (SSM_E_TIMEOUT) after this many failed swaps
 
 struct McArgs {
   int32_t n;
@@ -49,8 +58,13 @@ struct McArgs {
   int32_t *pivots;
   int32_t *status;
   unsigned *spill;  // [C][2][n] node ids of queue entries at index >= qcap
+  unsigned *fallback;  // 2-byte mind: set to 1 when a search went deeper than 65534 levels
+  // non-null: the first search (from start) was run on the whole GPU: mind
+  // after it, 4 bytes per node, and its packed (mind << 32 | ~node) maximum
+  const unsigned *init_mind;
+  const unsigned long long *init_best;
   int32_t cshift;   // C = 1 << cshift
-  int32_t slots;    // shared-memory mind slots per CTA (>= ceil(n / C), multiple of 4)
+  int32_t slots;    // shared-memory mind slots per CTA (>= ceil(n / C), multiple of 8)
   int32_t qcap;     // queue entries per parity in shared memory
 };
 
@@ -109,9 +123,39 @@ __device__ __forceinline__ void dsmem_st_u64(uint32_t a, unsigned long long v) {
   asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned dsmem_ld_u32(uint32_t a) {
+  unsigned v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned dsmem_cas_u32(uint32_t a, unsigned cmp, unsigned v) {
+  unsigned old;
+  asm volatile("atom.shared::cluster.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(a), "r"(cmp), "r"(v) : "memory");
+  return old;
+}
+
+// 2-byte mind: lowers the half h of the DSMEM word at a to nd if it is above
+// nd; returns the value it held (0 when pred is false, or when the swap kept
+// failing, which records SSM_E_TIMEOUT)
+__device__ __forceinline__ unsigned dsmem_claim16_if(bool pred, uint32_t a, unsigned h, unsigned nd, int32_t *status) {
+  if (!pred) return 0u;
+  const unsigned sh = 16u * h, mask = 0xFFFFu << sh;
+  unsigned w = dsmem_ld_u32(a);
+  for (int t = 0; t < kMcCasTries; ++t) {
+    const unsigned cur = (w & mask) >> sh;
+    if (cur <= nd) return cur;
+    const unsigned prev = dsmem_cas_u32(a, w, (w & ~mask) | (nd << sh));
+    if (prev == w) return cur;
+    w = prev;
+  }
+  dev_fail(status, SSM_E_TIMEOUT);
+  return 0u;
+}
+
 // ----------------------------------------------------------------- kernel
 struct McSmem {
-  unsigned *mind;  // [slots] hop distance to the closest chosen pivot, nodes r, r + C, ...
+  void *mind;      // [slots] hop distance to the closest chosen pivot, nodes r, r + C, ... (MB bytes each)
   int4 *q;         // [2][qcap] own frontier entries (v, rowptr[v], rowptr[v+1], 0) by level parity
   unsigned *cnts;  // [2][16] nodes pushed by every CTA, by level parity (published)
   unsigned *t3;    // [3] own queue lengths, rotating with the level (raised by the pushing CTAs)
@@ -121,6 +165,7 @@ struct McSmem {
 // One round of kMcU edge slots per lane at level L: claim each slot's node
 // (a DSMEM atomicMin on its owner's mind) and push the new ones to their
 // owners' queues of level L+1.
+template <int MB>
 __device__ __forceinline__ void mc_round(const McArgs &A, const McSmem &S, unsigned cs, unsigned L,
                                          const int4 (&e)[kMcU], bool (&act)[kMcU]) {
   const unsigned lane = threadIdx.x & 31u, cmask = (1u << cs) - 1u, nd = L + 1u, nxt = nd & 1u;
@@ -128,8 +173,12 @@ __device__ __forceinline__ void mc_round(const McArgs &A, const McSmem &S, unsig
   unsigned old[kMcU];
 #pragma unroll
   for (int u = 0; u < kMcU; ++u) {
-    const unsigned v = (unsigned)e[u].x;
-    old[u] = dsmem_atomic_min_if(act[u], dsmem_addr(S.mind + (v >> cs), v & cmask), nd);
+    const unsigned v = (unsigned)e[u].x, slot = v >> cs;
+    if constexpr (MB == 4)
+      old[u] = dsmem_atomic_min_if(act[u], dsmem_addr(static_cast<unsigned *>(S.mind) + slot, v & cmask), nd);
+    else
+      old[u] = dsmem_claim16_if(act[u], dsmem_addr(static_cast<unsigned *>(S.mind) + (slot >> 1), v & cmask), slot & 1u,
+                                nd, A.status);
   }
 #pragma unroll
   for (int u = 0; u < kMcU; ++u) act[u] = act[u] && old[u] > nd;
@@ -156,6 +205,7 @@ __device__ __forceinline__ void mc_round(const McArgs &A, const McSmem &S, unsig
 // lane 0 holds a row and the warp walks it directly; otherwise the edges of
 // all rows are spread evenly over the lanes (prefix of the degrees, each slot
 // finds its row by a binary search over the lanes).
+template <int MB>
 __device__ __forceinline__ void mc_rows(const McArgs &A, const McSmem &S, unsigned cs, unsigned L, int beg, int end,
                                         bool single) {
   const unsigned lane = threadIdx.x & 31u;
@@ -170,7 +220,7 @@ __device__ __forceinline__ void mc_rows(const McArgs &A, const McSmem &S, unsign
         act[u] = idx < en;
         e[u] = act[u] ? __ldg(A.adj + idx) : make_int4(0, 0, 0, 0);
       }
-      mc_round(A, S, cs, L, e, act);
+      mc_round<MB>(A, S, cs, L, e, act);
     }
     return;
   }
@@ -199,13 +249,14 @@ __device__ __forceinline__ void mc_rows(const McArgs &A, const McSmem &S, unsign
       const int o_incl = __shfl_sync(0xffffffffu, incl, own);
       e[u] = act[u] ? __ldg(A.adj + o_end - (o_incl - idx)) : make_int4(0, 0, 0, 0);
     }
-    mc_round(A, S, cs, L, e, act);
+    mc_round<MB>(A, S, cs, L, e, act);
   }
 }
 
 // Expands this CTA's queue of level L (cnt entries).  A warp takes ipw
 // consecutive entries, ipw a power of two chosen so that small levels are
 // spread over all warps.
+template <int MB>
 __device__ __forceinline__ void mc_expand(const McArgs &A, const McSmem &S, unsigned r, unsigned cs, unsigned L,
                                           unsigned cnt) {
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -226,17 +277,22 @@ __device__ __forceinline__ void mc_expand(const McArgs &A, const McSmem &S, unsi
         end = __ldg(A.rowptr + v + 1);
       }
     }
-    mc_rows(A, S, cs, L, beg, end, ipw == 1u);
+    mc_rows<MB>(A, S, cs, L, beg, end, ipw == 1u);
   }
 }
 
+// MB: bytes of mind per node (4, or 2 for graphs whose 4-byte mind does not fit)
+template <int MB>
 __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
   extern __shared__ __align__(16) unsigned char mc_smem[];
   __shared__ unsigned s_t3[3], s_p3[3];
   __shared__ unsigned long long s_wbest[kMcThreads / 32];
+  using MindT = typename std::conditional<MB == 4, unsigned, unsigned short>::type;
+  constexpr unsigned kInfM = MB == 4 ? kMcInf : kMcInf16;
   McSmem S;
-  S.mind = reinterpret_cast<unsigned *>(mc_smem);
-  S.q = reinterpret_cast<int4 *>(S.mind + A.slots);
+  MindT *mind = reinterpret_cast<MindT *>(mc_smem);
+  S.mind = mind;
+  S.q = reinterpret_cast<int4 *>(mc_smem + (size_t)MB * A.slots);
   S.cnts = reinterpret_cast<unsigned *>(S.q + 2 * (size_t)A.qcap);
   S.t3 = s_t3;
   S.p3 = s_p3;
@@ -248,11 +304,28 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
   const unsigned n = (unsigned)A.n;
   const unsigned own = n > r ? ((n - 1u - r) >> cs) + 1u : 0u;  // nodes r, r + C, ... below n
 
-  for (unsigned s = tid; s < own; s += blockDim.x) S.mind[s] = kMcInf;
+  unsigned p = (unsigned)A.start;
+  int j0 = 0;
+  if (A.init_mind) {
+    // the search from start ran on the whole GPU (it reaches every node, and
+    // a grid of all SMs does that faster than one cluster): take its mind
+    // and its maximum, which is pivot 1 (uniform: every CTA reads the same key)
+    const unsigned long long key0 = __ldcg(A.init_best);
+    const unsigned top = (unsigned)(key0 >> 32);
+    if (top == kMcInf) goto done;  // unreachable nodes: already recorded by that search
+    if (MB == 2 && top >= kMcInf16) {  // deeper than a 2-byte mind holds: the grid kernel takes over
+      if (r == 0 && tid == 0) *A.fallback = 1u;
+      goto done;
+    }
+    for (unsigned s = tid; s < own; s += blockDim.x) mind[s] = (MindT)__ldcg(A.init_mind + r + (s << cs));
+    p = ~(unsigned)key0;
+    j0 = 1;
+  } else {
+    for (unsigned s = tid; s < own; s += blockDim.x) mind[s] = (MindT)kInfM;
+  }
   cluster_sync();  // every CTA of the cluster runs before any DSMEM access
 
-  unsigned p = (unsigned)A.start;
-  for (int j = 0; j < A.k; ++j) {
+  for (int j = j0; j < A.k; ++j) {
     if (r == 0 && tid == 0) A.pivots[j] = (int32_t)p;
     const bool last = (j == A.k - 1);
     if (last && j > 0) break;  // the final pivot needs no search
@@ -263,7 +336,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
       s_t3[0] = s_t3[1] = s_t3[2] = 0;
       s_p3[0] = s_p3[1] = s_p3[2] = 0;
       if (r == (p & cmask)) {
-        S.mind[p >> cs] = 0;
+        mind[p >> cs] = 0;
         S.q[0] = make_int4((int)p, __ldg(A.rowptr + p), __ldg(A.rowptr + p + 1), 0);
         s_t3[0] = 1;
       }
@@ -275,23 +348,44 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
       if (tot == 0) break;  // same published counts in every CTA: uniform
+      if (MB == 2 && L + 1u >= kMcInf16) {  // a 2-byte mind cannot hold the next level (uniform):
+        if (r == 0 && tid == 0) *A.fallback = 1u;  // the grid kernel queued after this one takes over
+        goto done;
+      }
       const unsigned cnt = s_t3[L % 3u];
       if (tid == 0) {
         s_t3[(L + 2u) % 3u] = 0;  // read during level L-1; raised again from level L+1 on
         s_p3[(L + 2u) % 3u] = 0;
       }
-      mc_expand(A, S, r, cs, L, cnt);
+      mc_expand<MB>(A, S, r, cs, L, cnt);
       __syncthreads();  // own push count is final
       if (tid < C) dsmem_st_u32(dsmem_addr(S.cnts + ((L + 1u) & 1u) * 16u + r, tid), s_p3[(L + 1u) % 3u]);
       cluster_sync();
     }
 
-    // argmax of mind over the cluster, ties to the lowest node id
+    // argmax of mind over the cluster, ties to the lowest node id: a thread
+    // reads 16 bytes of slots at a time and keeps the first slot of the largest
+    // value it saw (slots ascending, so that is its lowest node id)
     unsigned long long key = 0;
-    for (unsigned s = tid; s < own; s += blockDim.x) {
-      const unsigned v = r + (s << cs);
-      const unsigned long long kk = ((unsigned long long)S.mind[s] << 32) | (unsigned long long)(~v);
-      key = kk > key ? kk : key;
+    {
+      constexpr unsigned kPer = 16u / MB;  // slots per 16-byte load (slots is a multiple of 8)
+      unsigned bv = 0, bs = 0;
+      bool any = false;
+      for (unsigned c = tid; c * kPer < own; c += blockDim.x) {
+        const uint4 w = reinterpret_cast<const uint4 *>(mind)[c];
+        const unsigned wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (unsigned e = 0; e < kPer; ++e) {
+          const unsigned sl = c * kPer + e;
+          const unsigned val = MB == 4 ? wd[e] : (wd[e >> 1] >> (16u * (e & 1u))) & 0xFFFFu;
+          if (sl < own && (!any || val > bv)) {
+            bv = val;
+            bs = sl;
+            any = true;
+          }
+        }
+      }
+      if (any) key = ((unsigned long long)bv << 32) | (unsigned long long)(~(r + (bs << cs)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -312,30 +406,37 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
     cluster_sync();
     key = 0;
     for (unsigned x = 0; x < C; ++x) key = bests[x] > key ? bests[x] : key;
-    if ((unsigned)(key >> 32) == kMcInf) {  // some node was never reached
+    if ((unsigned)(key >> 32) == kInfM) {  // some node was never reached
       if (r == 0 && tid == 0) dev_fail(A.status, SSM_E_DISCONNECTED);
       break;
     }
     if (last) break;
     p = ~(unsigned)key;
   }
+done:
   cluster_sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // ------------------------------------------------------------------- host
 struct McShape {
   int C = 0;
+  int mb = 4;  // bytes of mind per node
   int slots = 0;
   int qcap = 0;
   size_t smem = 0;
 };
 
-static size_t mc_smem_bytes(int slots, int qcap) {
-  return (size_t)slots * 4 + (size_t)2 * qcap * sizeof(int4) + 32 * 4 + kMcMaxCluster * 8;
+static size_t mc_smem_bytes(int slots, int qcap, int mb) {
+  return (size_t)slots * mb + (size_t)2 * qcap * sizeof(int4) + 32 * 4 + kMcMaxCluster * 8;
 }
 
-// Cluster shape for n nodes on the current device, or C == 0 if no cluster
-// of up to 16 CTAs holds mind in shared memory.
+static const void *mc_kernel(int mb) {
+  return mb == 4 ? (const void *)k_maxmin_cluster<4> : (const void *)k_maxmin_cluster<2>;
+}
+
+// Cluster shape for n nodes on the current device (16 CTAs before 8, 4-byte
+// mind before 2-byte), or C == 0 if no cluster of up to 16 CTAs holds mind in
+// shared memory.
 static McShape mc_shape(int32_t n) {
   McShape sh;
   int dev = 0, smem_max = 0;
@@ -343,65 +444,88 @@ static McShape mc_shape(int32_t n) {
   if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return sh;
   const size_t budget = (size_t)smem_max - 2 * 1024;  // static shared memory of the kernel
   for (int C : {16, 8}) {
-    const int slots = (int)((((int64_t)n + C - 1) / C + 3) / 4 * 4);
-    const size_t fixed = mc_smem_bytes(slots, 0);
-    if (fixed >= budget) continue;
-    const int qcap = (int)std::min<size_t>(kMcQcapMax, (budget - fixed) / (2 * sizeof(int4)));
-    if (qcap < kMcQcapMin) continue;
-    const size_t smem = mc_smem_bytes(slots, qcap);
-    if (C > 8 && cudaFuncSetAttribute((const void *)k_maxmin_cluster,
-                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      (void)cudaGetLastError();
-      continue;
+    for (int mb : {4, 2}) {
+      const void *kern = mc_kernel(mb);
+      // a multiple of 8 slots keeps the queue after mind 16-byte aligned
+      const int slots = (int)((((int64_t)n + C - 1) / C + 7) / 8 * 8);
+      const size_t fixed = mc_smem_bytes(slots, 0, mb);
+      if (fixed >= budget) continue;
+      const int qcap = (int)std::min<size_t>(kMcQcapMax, (budget - fixed) / (2 * sizeof(int4)));
+      if (qcap < kMcQcapMin) continue;
+      const size_t smem = mc_smem_bytes(slots, qcap, mb);
+      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (allow_dynamic_smem(kern) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)C);
+      cfg.blockDim = dim3(kMcThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (clusters < 1) continue;
+      sh.C = C;
+      sh.mb = mb;
+      sh.slots = slots;
+      sh.qcap = qcap;
+      sh.smem = smem;
+      return sh;
     }
-    if (allow_dynamic_smem((const void *)k_maxmin_cluster) != cudaSuccess) {
-      (void)cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)C);
-    cfg.blockDim = dim3(kMcThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)k_maxmin_cluster, &cfg) != cudaSuccess) {
-      (void)cudaGetLastError();
-      continue;
-    }
-    if (clusters < 1) continue;
-    sh.C = C;
-    sh.slots = slots;
-    sh.qcap = qcap;
-    sh.smem = smem;
-    return sh;
   }
   return sh;
 }
 
 bool maxmin_cluster_candidate(int32_t n) {
-  // mind of 4 bytes per node over at most 16 CTAs, with room for the queues
-  return (int64_t)n * 4 <= (int64_t)kMcMaxCluster * 160 * 1024;
+  // mind of 2 bytes per node over at most 16 CTAs, with room for the queues
+  return (int64_t)n * 2 <= (int64_t)kMcMaxCluster * 190 * 1024;
 }
 
 size_t maxmin_cluster_spill_entries(int32_t n) {
   return maxmin_cluster_candidate(n) ? (size_t)kMcMaxCluster * 2 * (size_t)n : 0;
 }
 
+// what the last pivot selection on this host thread chose (ssm_last_pivot_config)
+static thread_local int32_t g_last_pivot_config[2] = {-1, 0};
+
+void note_pivot_config(int32_t cluster, int32_t mind_bytes) {
+  g_last_pivot_config[0] = cluster;
+  g_last_pivot_config[1] = mind_bytes;
+}
+
+int maxmin_cluster_mind_bytes(int32_t n) {
+  if (!maxmin_cluster_candidate(n)) return 0;
+  const McShape sh = mc_shape(n);
+  return sh.C ? sh.mb : 0;
+}
+
 int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int32_t k, int32_t start,
-                          int32_t *pivots, int32_t *status, unsigned *spill, cudaStream_t s, bool *launched) {
-  *launched = false;
+                          int32_t *pivots, int32_t *status, unsigned *spill, unsigned *fallback,
+                          const unsigned *init_mind, const unsigned long long *init_best, cudaStream_t s,
+                          int *mind_bytes) {
+  *mind_bytes = 0;
   if (!maxmin_cluster_candidate(n)) return SSM_OK;
   const McShape sh = mc_shape(n);
   if (sh.C == 0) return SSM_OK;
   McArgs A;
   A.n = n; A.rowptr = rowptr; A.adj = adj; A.k = k; A.start = start; A.pivots = pivots; A.status = status;
   A.spill = spill;
+  A.fallback = fallback;
+  A.init_mind = init_mind;
+  A.init_best = init_best;
   A.cshift = sh.C == 16 ? 4 : 3;
   A.slots = sh.slots;
   A.qcap = sh.qcap;
@@ -417,10 +541,20 @@ int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if (sh.mb == 2) SSM_TRY_CUDA(cudaMemsetAsync(fallback, 0, sizeof(unsigned), s));
   note_launch();
-  SSM_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_maxmin_cluster, A));
-  *launched = true;
+  if (sh.mb == 4)
+    SSM_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_maxmin_cluster<4>, A));
+  else
+    SSM_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_maxmin_cluster<2>, A));
+  *mind_bytes = sh.mb;
+  note_pivot_config(sh.C, sh.mb);
   return SSM_OK;
 }
 
 }  // namespace ssm
+
+SSM_API void ssm_last_pivot_config(int32_t *out) {
+  out[0] = ssm::g_last_pivot_config[0];
+  out[1] = ssm::g_last_pivot_config[1];
+}

@@ -59,6 +59,7 @@ def test_pivot_bfs_above_bitmap_limit(family, k):
     og = O.build_csr(n, s, d)
     g = _gpu_graph(n, s, d)
     piv = ssm.ssm_select_pivots(g, k, 0)
+    assert ssm.ssm_last_pivot_config() == {"cluster": 0, "mind_bytes": 4}
     opiv = O.maxmin(og, k, 0)
     assert np.array_equal(piv.cpu().numpy(), opiv)
     dip = ssm.ssm_pivot_bfs(g, piv).cpu().numpy()

@@ -144,24 +144,48 @@ def test_select_pivots_star_frontier_overflow(start):
     assert np.array_equal(got, O.maxmin(og, 5, start))
 
 
-def test_select_pivots_large_grid_kernel():
-    # 720000 nodes: mind does not fit the cluster's shared memory, so the
-    # cooperative grid kernel runs
+def test_select_pivots_4_byte_cluster_kernel():
+    # 720000 nodes still fit a 4-byte mind in the cluster
     n, s, d = I.grid(900, 800)
     og = O.build_csr(n, s, d)
     g = _gpu_graph(n, s, d)
     got = ssm.ssm_select_pivots(g, 6, 12345).cpu().numpy()
+    assert ssm.ssm_last_pivot_config() == {"cluster": 16, "mind_bytes": 4}
+    assert np.array_equal(got, O.maxmin(og, 6, 12345))
+
+
+def test_select_pivots_large_grid_kernel():
+    # 960000 nodes: a 4-byte mind does not fit the cluster's shared memory, a
+    # 2-byte one does (node pairs claimed by compare-and-swap); 1,900 levels
+    n, s, d = I.grid(1000, 960)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 6, 12345).cpu().numpy()
+    assert ssm.ssm_last_pivot_config() == {"cluster": 16, "mind_bytes": 2}
     assert np.array_equal(got, O.maxmin(og, 6, 12345))
 
 
 def test_select_pivots_large_ba_kernel():
-    # 700000 nodes of a Barabasi-Albert graph (hubs, small diameter) also run
-    # the cooperative grid kernel, over many short pruned searches
-    n, s, d = I.ba(700000, 4, 3)
+    # 1,000,000 nodes of a Barabasi-Albert graph (hubs, small diameter): one
+    # search over every node, then many short pruned searches, with the
+    # 2-byte mind of the cluster kernel
+    n, s, d = I.ba(1000000, 4, 3)
     og = O.build_csr(n, s, d)
     g = _gpu_graph(n, s, d)
     got = ssm.ssm_select_pivots(g, 24, 0).cpu().numpy()
+    assert ssm.ssm_last_pivot_config() == {"cluster": 16, "mind_bytes": 2}
     assert np.array_equal(got, O.maxmin(og, 24, 0))
+
+
+def test_select_pivots_deep_search_hands_over_to_the_grid_kernel():
+    # a 900,000-node path: the 2-byte mind of the cluster kernel cannot hold
+    # level 65535, so the grid kernel queued behind it redoes the selection
+    n, s, d = I.path(900000)
+    og = O.build_csr(n, s, d)
+    g = _gpu_graph(n, s, d)
+    got = ssm.ssm_select_pivots(g, 3, 450000).cpu().numpy()
+    assert ssm.ssm_last_pivot_config() == {"cluster": 16, "mind_bytes": 2}
+    assert np.array_equal(got, O.maxmin(og, 3, 450000))
 
 
 # ------------------------------------------------------------------ a2 d_ip
