@@ -794,12 +794,27 @@ size_t msbfs_workspace(int32_t n, int64_t m2, int32_t k) {
   return c.size();
 }
 
+// dist[0 .. count) = 0xFFFF (unreached) when *run_if != 0
+__global__ void k_fill_unreached_if(int64_t count, const unsigned *__restrict__ run_if, uint16_t *__restrict__ dist) {
+  if (__ldcg(run_if) == 0u) return;
+  uint4 *d4 = reinterpret_cast<uint4 *>(dist);
+  const int64_t n16 = (reinterpret_cast<uintptr_t>(dist) & 15u) == 0 ? count / 8 : 0;  // 16-byte stores when aligned
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n16; t += (int64_t)gridDim.x * blockDim.x)
+    d4[t] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+  for (int64_t t = n16 * 8 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dist[t] = 0xFFFFu;
+}
+
 // Graphs whose visited bitmap fits shared memory: first the pulled bitset BFS
 // (few levels, every level touches most edges); if it gives up on a large
-// diameter, one block per source (k_bfs_cta).  Larger graphs: k_msbfs.
+// diameter, one block per source (k_bfs_cta), on a table first filled with
+// "unreached".  Larger graphs: k_msbfs.
 int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *colidx, int32_t k,
-                 const int32_t *sources, uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+                 const int32_t *sources, uint16_t *dist, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s,
+                 const PullPassFn *after_pass, const unsigned **pull_gaveup) {
   Carver c(ws, ws_bytes);
+  if (pull_gaveup) *pull_gaveup = nullptr;
   if (cta_bfs_fits(n)) {
     CtaBfsArgs B;
     B.n = n; B.rowptr = rowptr; B.colidx = colidx; B.nsrc = k; B.sources = sources; B.dist = dist;
@@ -814,10 +829,15 @@ int launch_msbfs(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *co
     void *pws = c.take<char>(pw);
     B.run_if = gaveup;
     if (!c.ok) return fail(SSM_E_NOMEM, "BFS: workspace %zu bytes, need %zu", ws_bytes, c.size());
-    SSM_TRY_CUDA(cudaMemsetAsync(dist, 0xFF, (size_t)k * n * sizeof(uint16_t), s));
     SSM_TRY_CUDA(cudaMemsetAsync(gaveup, 0, sizeof(unsigned), s));
-    int rc = launch_msbfs_pull(n, rowptr, colidx, k, sources, dist, status, gaveup, pws, pw, s);
+    int rc = launch_msbfs_pull(n, rowptr, colidx, k, sources, dist, status, gaveup, pws, pw, s, after_pass);
     if (rc) return rc;
+    if (pull_gaveup) *pull_gaveup = gaveup;
+    // a complete pulled BFS wrote every entry (or handed every pass over)
+    const int64_t cells = (int64_t)k * n;
+    note_launch(), k_fill_unreached_if<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((cells / 8 + 255) / 256,
+                                                                                          (int64_t)num_sms() * 8)),
+                                         256, 0, s>>>(cells, gaveup, dist);
     // the packed adjacency saves a dependent rowptr load per level but doubles
     // adjacency traffic: use it only while it stays L2-resident
     const bool packed = (size_t)m2 * sizeof(int2) <= kAdj2MaxBytes && n < (1 << kAdj2NodeBits);

@@ -29,6 +29,7 @@ constexpr int kPullThreads = 512;
 constexpr int kPullSources = 256;  // sources per pass: 8 words per node
 constexpr int kPullW4 = kPullSources / 128;  // uint4 chunks per node
 constexpr unsigned kPullMaxLevels = 24;
+static_assert(kPullSources == kPullPassSources && kPullMaxLevels + 1 == kPullPassLevels, "pass layout");
 constexpr unsigned kPullProbeLevel = 6;  // after this level at least 1/64 of all pairs must be reached
 constexpr int kPullLong = 64;  // longer rows are walked by the whole warp
 #ifndef SSM_PULL_LONG_BATCH
@@ -357,7 +358,8 @@ size_t msbfs_pull_workspace(int32_t n) {
 }
 
 int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t k, const int32_t *sources,
-                      uint16_t *dist, int32_t *status, unsigned *gaveup, void *ws, size_t ws_bytes, cudaStream_t s) {
+                      uint16_t *dist, int32_t *status, unsigned *gaveup, void *ws, size_t ws_bytes, cudaStream_t s,
+                      const PullPassFn *after_pass) {
   Carver c(ws, ws_bytes);
   PullArgs A;
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.sources = sources; A.dist = dist; A.status = status;
@@ -390,6 +392,12 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
     void *args[] = {&A};
     note_launch();
     SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_msbfs_pull, dim3(blocks), dim3(kPullThreads), args, 0, s));
+    if (after_pass) {
+      static_assert(kPullPassWords * 4 == kPullW4 * 16, "pass words per node");
+      const PullPass P = {reinterpret_cast<const unsigned *>(A.F), A.nlev, gaveup, A.base, A.nsrc, base / kPullSources};
+      if (int rc_ = (*after_pass)(P)) return rc_;
+      continue;
+    }
     note_launch(), k_pull_distances<<<(unsigned)((n + kPullTile - 1) / kPullTile), 256, 0, s>>>(A);
     SSM_TRY_CUDA(cudaGetLastError());
   }

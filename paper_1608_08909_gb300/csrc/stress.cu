@@ -3,8 +3,11 @@
 // reported), exhaustive over all pairs or over sampled pairs.
 //
 // Pair distances come from the multi-source bitset BFS (bfs.cu) run from a
-// batch of sources into a [sources][n] uint16 table; a pair kernel then
-// accumulates, in FP64 and in a fixed order,
+// batch of sources into a [sources][n] uint16 table, or, for sampled pairs on
+// graphs the pulled BFS handles, straight from the level bits of each pass
+// (the distance of (s, v) is the level at which bit s of v first appears, so
+// the full table is never written); a pair kernel then accumulates, in FP64
+// and in a fixed order,
 //   sum (r/d - 1)^2 = sum (r-d)^2/d^2,  S1 = sum r/d,  S2 = sum r^2/d^2,  N,
 // and the final kernel forms {raw, alpha* = S1/S2, N - S1^2/S2, normalized}.
 #include <algorithm>
@@ -82,22 +85,32 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_exhaustive(int32_t n, in
   block_store_sums(acc, part);
 }
 
-// sampled: source j (src[j]), targets l = 0..T-1 from the splitmix64 stream
+// sampled pair t = j T + l: source src[j], target from splitmix64 draw S + t
+// (uniform over the other n - 1 nodes)
+__device__ __forceinline__ int sampled_target(int32_t n, int32_t S, uint64_t seed, int64_t t, int s) {
+  const uint64_t u = splitmix64_at(seed, (uint64_t)S + (uint64_t)t);
+  const int v = (int)(((u >> 32) * (uint64_t)(n - 1)) >> 32);
+  return v + ((v >= s) ? 1 : 0);
+}
+
+// sampled: source j (src[j]), targets l = 0..T-1 from the splitmix64 stream;
+// with run_if, only if *run_if != 0 (the pulled BFS gave up and the table was
+// written instead)
 template <class T2, class D>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_sampled(int32_t n, int32_t S, int32_t T, uint64_t seed,
                                                                  const int32_t *__restrict__ src,
                                                                  const D *__restrict__ dist,
                                                                  const T2 *__restrict__ pos,
                                                                  double *__restrict__ part,
-                                                                 int32_t *__restrict__ status) {
+                                                                 int32_t *__restrict__ status,
+                                                                 const unsigned *__restrict__ run_if) {
+  if (run_if && __ldcg(run_if) == 0u) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int64_t total = (int64_t)S * T;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(t / T);
     const int s = __ldg(src + j);
-    const uint64_t u = splitmix64_at(seed, (uint64_t)S + (uint64_t)t);
-    int v = (int)(((u >> 32) * (uint64_t)(n - 1)) >> 32);
-    v += (v >= s) ? 1 : 0;
+    const int v = sampled_target(n, S, seed, t, s);
     const D d = __ldg(dist + (size_t)j * n + v);
     if (bad_dist(d)) {
       dev_fail(status, SSM_E_DISCONNECTED);
@@ -108,10 +121,53 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_sampled(int32_t n, int32
   block_store_sums(acc, part);
 }
 
-// fixed-order sum of all block partials, then the stress values
+// sampled pairs of the sources of one pulled-BFS pass (j = base .. base +
+// nsrc - 1), their distances read from the pass's level bits: d(s, v) = the
+// level L whose word holds bit j - base for node v; partial sums per block
+template <class T2>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_from_levels(int32_t n, int32_t S, int32_t T, uint64_t seed,
+                                                                     const int32_t *__restrict__ src, PullPass P,
+                                                                     const T2 *__restrict__ pos,
+                                                                     double *__restrict__ part,
+                                                                     int32_t *__restrict__ status) {
+  if (__ldcg(P.gaveup)) return;  // the table path takes over
+  const unsigned nlev = min(__ldcg(P.nlev), kPullPassLevels);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t total = (int64_t)P.nsrc * T;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / T);
+    const int j = P.base + a;
+    const int s = __ldg(src + j);
+    const int v = sampled_target(n, S, seed, (int64_t)j * T + (t - (int64_t)a * T), s);
+    const unsigned bit = 1u << (a & 31);
+    const unsigned *f = P.F + (size_t)v * kPullPassWords + (a >> 5);
+    unsigned d = 0xFFFFu;
+    for (unsigned L = 0; L < nlev; ++L)
+      if (__ldcg(f + (size_t)L * n * kPullPassWords) & bit) {
+        d = L;
+        break;
+      }
+    if (bad_dist((uint16_t)d)) {
+      dev_fail(status, SSM_E_DISCONNECTED);
+      continue;
+    }
+    pair_terms(pos, s, v, (uint16_t)d, acc);
+  }
+  block_store_sums(acc, part);
+}
+
+// fixed-order sum of all block partials, then the stress values; with
+// use_alt, the partials part_alt[0 .. nparts_alt) instead when *use_alt == 0
+// (the pulled BFS completed and its passes summed the pairs)
 __global__ void k_stress_final(int32_t n, int64_t nparts, const double *__restrict__ part, int sampled,
-                               double *__restrict__ out, double *__restrict__ sums) {
+                               double *__restrict__ out, double *__restrict__ sums,
+                               const double *__restrict__ part_alt = nullptr, int64_t nparts_alt = 0,
+                               const unsigned *__restrict__ use_alt = nullptr) {
   __shared__ double red[32][4];
+  if (use_alt && __ldcg(use_alt) == 0u) {
+    part = part_alt;
+    nparts = nparts_alt;
+  }
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t b = threadIdx.x; b < nparts; b += blockDim.x)
 #pragma unroll
@@ -144,6 +200,7 @@ struct StressWs {
   int32_t *src;
   uint16_t *dist;
   double *part;
+  double *part_pull;  // [passes][pair blocks][4] sampled sums from the pulled BFS's level bits
   void *bfs;
   size_t bfs_bytes;
 };
@@ -152,6 +209,7 @@ static size_t carve_stress(Carver &c, StressWs &w, int32_t n, int64_t m2, int32_
   w.src = c.take<int32_t>(S);
   w.dist = c.take<uint16_t>((size_t)S * n);
   w.part = c.take<double>(4 * (size_t)pair_blocks() * (size_t)nbatches);
+  w.part_pull = c.take<double>(4 * (size_t)pair_blocks() * (size_t)((S + kPullPassSources - 1) / kPullPassSources));
   w.bfs_bytes = msbfs_workspace(n, m2, S);
   w.bfs = c.take<char>(w.bfs_bytes);
   return c.size();
@@ -197,16 +255,32 @@ SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_
   carve_stress(c, w, n, 2 * m, S, nb);
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_stress: workspace %zu bytes, need %zu", ws_bytes, c.size());
   const int pb = pair_blocks();
+  const unsigned *gaveup = nullptr;
+  int64_t npull = 0;
   if (nsources > 0) {
     note_launch(), k_sample_sources<<<std::max(1, (S + 255) / 256), 256, 0, s>>>(n, S, seed, w.src);
-    int rc = launch_msbfs(n, 2 * m, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s);
+    // each pass of the pulled BFS sums its sources' pairs from its level bits
+    const PullPassFn from_levels = [&](const PullPass &P) -> int {
+      double *part = w.part_pull + 4 * (size_t)pb * (size_t)P.pass;
+      npull = std::max<int64_t>(npull, (int64_t)pb * (P.pass + 1));
+      if (precision == 64)
+        note_launch(), k_pairs_from_levels<double2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, P,
+                                                                                (const double2 *)pos, part, status);
+      else
+        note_launch(), k_pairs_from_levels<float2><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, P,
+                                                                               (const float2 *)pos, part, status);
+      SSM_TRY_CUDA(cudaGetLastError());
+      return SSM_OK;
+    };
+    int rc = launch_msbfs(n, 2 * m, rowptr, colidx, S, w.src, w.dist, status, w.bfs, w.bfs_bytes, s, &from_levels,
+                          &gaveup);
     if (rc) return rc;
     if (precision == 64)
       note_launch(), k_pairs_sampled<double2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
-                                                           (const double2 *)pos, w.part, status);
+                                                           (const double2 *)pos, w.part, status, gaveup);
     else
       note_launch(), k_pairs_sampled<float2, uint16_t><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
-                                                          (const float2 *)pos, w.part, status);
+                                                          (const float2 *)pos, w.part, status, gaveup);
   } else {
     for (int b = 0; b < nb; ++b) {
       const int32_t base = b * S, B = std::min<int32_t>(S, n - base);
@@ -222,7 +296,8 @@ SSM_API int ssm_stress(int32_t n, int64_t m, const int32_t *rowptr, const int32_
                                                                status);
     }
   }
-  note_launch(), k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums);
+  note_launch(), k_stress_final<<<1, 1024, 0, s>>>(n, (int64_t)pb * nb, w.part, nsources > 0, out, sums, w.part_pull,
+                                                   npull, gaveup);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
@@ -279,10 +354,10 @@ SSM_API int ssm_stress_weighted(int32_t n, const int32_t *rowptr, const int32_t 
     if (rc) return rc;
     if (precision == 64)
       note_launch(), k_pairs_sampled<double2, float><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
-                                                                            (const double2 *)pos, w.part, status);
+                                                                            (const double2 *)pos, w.part, status, nullptr);
     else
       note_launch(), k_pairs_sampled<float2, float><<<pb, kPairThreads, 0, s>>>(n, S, ntargets, seed, w.src, w.dist,
-                                                                           (const float2 *)pos, w.part, status);
+                                                                           (const float2 *)pos, w.part, status, nullptr);
   } else {
     for (int b = 0; b < nb; ++b) {
       const int32_t base = b * S, B = std::min<int32_t>(S, n - base);

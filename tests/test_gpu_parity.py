@@ -601,9 +601,14 @@ def test_stress_exhaustive(name):
         assert sums[3].item() == wsums[3] == n * (n - 1) / 2
 
 
-@pytest.mark.parametrize("S,T,seed", [(64, 256, 1), (100, 37, 9)])
-def test_stress_sampled(S, T, seed):
-    n, s, d = GRAPHS["rgg"]()
+@pytest.mark.parametrize("name,S,T,seed", [("rgg", 64, 256, 1), ("rgg", 100, 37, 9), ("ba", 600, 100, 3),
+                                           ("ba", 256, 64, 5)])
+def test_stress_sampled(name, S, T, seed):
+    """Sampled pairs: on the geometric graph (large diameter) the pulled BFS
+    gives up and the distance table is written; on the Barabasi-Albert graph
+    each pass of it sums its sources' pairs from its level bits (three passes
+    for 600 sources, the last one partial)."""
+    n, s, d = GRAPHS[name]()
     prep = O.prepare(n, s, d, 30)
     g = _gpu_graph(n, s, d)
     x = prep.pos0.astype(np.float32)
