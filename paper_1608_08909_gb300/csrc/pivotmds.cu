@@ -37,7 +37,7 @@ constexpr int kEigP = SSM_EIG_P;  // subspace dimension
 constexpr int kEigPowerLog2 = SSM_EIG_POWER_LOG2;
 constexpr int kEigThreads = 256;
 constexpr int kMaxPivotsMds = 1024;
-constexpr int kEigScratch = (kEigThreads / 32) * (kEigP * (kEigP + 1) / 2);  // doubles for block_sum
+constexpr int kEigScratch = (kEigThreads / 32 + 1) * (kEigP * (kEigP + 1) / 2);  // doubles for block_sum
 
 // s_a = sum_i d_ia^2 (exact: below 2^63 for n < 2^31)
 // s[a] = sum_i d_ia^2 (exact; s zeroed by the caller).  Blocks take chunks of
@@ -160,9 +160,12 @@ __global__ void __launch_bounds__(256) k_square_f64(int32_t k, const double *__r
   if (r < k && c < k) C[(size_t)r * k + c] = acc;
 }
 
-// block-wide sum of N doubles per thread (result broadcast to all threads)
+// block-wide sum of N doubles per thread (result broadcast to all threads).
+// GB300 runs FP64 at 1/64 of the FP32 rate and a warp instruction costs the
+// same with one lane as with 32, so the sum of the warp partials is formed
+// once, by thread 0, and broadcast through shared memory
 template <int N>
-__device__ void block_sum(double (&v)[N], double *scratch /* [warps*N] */) {
+__device__ void block_sum(double (&v)[N], double *scratch /* [(warps + 1) N] */) {
 #pragma unroll
   for (int j = 0; j < N; ++j)
 #pragma unroll
@@ -173,73 +176,110 @@ __device__ void block_sum(double (&v)[N], double *scratch /* [warps*N] */) {
 #pragma unroll
     for (int j = 0; j < N; ++j) scratch[w * N + j] = v[j];
   __syncthreads();
+  if (threadIdx.x == 0)
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    double t = 0.0;
-    for (int q = 0; q < nw; ++q) t += scratch[q * N + j];
-    v[j] = t;
-  }
+    for (int j = 0; j < N; ++j) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += scratch[q * N + j];
+      scratch[nw * N + j] = t;
+    }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < N; ++j) v[j] = scratch[nw * N + j];
   __syncthreads();
 }
 
-// cyclic Jacobi on a tiny symmetric P x P matrix (one thread); eigenvalues
-// on the diagonal of H, eigenvectors in the columns of Q, sorted descending
-__device__ void tiny_jacobi(int P, double *H, double *Q) {
-  for (int i = 0; i < P; ++i)
-    for (int j = 0; j < P; ++j) Q[i * P + j] = (i == j) ? 1.0 : 0.0;
+// cyclic Jacobi on a tiny symmetric P x P matrix (P <= 4) by one warp: a
+// sweep's six rotations in three rounds of two disjoint pairs ((0,1)(2,3),
+// (0,2)(1,3), (0,3)(1,2)); lanes 0 and 1 form a round's two rotations at
+// once and eight lanes apply them to columns, rows and Q.  Eigenvalues on the
+// diagonal of H, eigenvectors in the columns of Q, sorted descending.  (FP64
+// runs at 1/64 of the FP32 rate on GB300 and a warp instruction costs the
+// same with one lane as with 32, so the serial form paid for every element.)
+// round r's pair h: (0, r + 1) and the two indices left
+__device__ __forceinline__ int pair_lo(int r, int h) { return h == 0 ? 0 : (r == 0 ? 2 : 1); }
+__device__ __forceinline__ int pair_hi(int r, int h) { return h == 0 ? r + 1 : (r == 2 ? 2 : 3); }
+__device__ __forceinline__ void tiny_jacobi_warp(int P, double *H, double *Q) {
+  const int lane = threadIdx.x & 31;
+  if (lane < P * P) Q[lane] = (lane / P == lane % P) ? 1.0 : 0.0;
+  __syncwarp();
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int i = 0; i < P; ++i)
-      for (int j = 0; j < P; ++j) {
-        tot += H[i * P + j] * H[i * P + j];
-        if (i != j) off += H[i * P + j] * H[i * P + j];
-      }
-    if (off <= 1e-32 * tot || off == 0.0) break;
-    for (int p = 0; p < P; ++p)
-      for (int q = p + 1; q < P; ++q) {
-        const double apq = H[p * P + q];
-        if (apq == 0.0) continue;
-        const double theta = (H[q * P + q] - H[p * P + p]) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int r = 0; r < P; ++r) {
-          const double hp = H[r * P + p], hq = H[r * P + q];
-          H[r * P + p] = c * hp - s * hq;
-          H[r * P + q] = s * hp + c * hq;
-        }
-        for (int r = 0; r < P; ++r) {
-          const double hp = H[p * P + r], hq = H[q * P + r];
-          H[p * P + r] = c * hp - s * hq;
-          H[q * P + r] = s * hp + c * hq;
-        }
-        for (int r = 0; r < P; ++r) {
-          const double qp = Q[r * P + p], qq = Q[r * P + q];
-          Q[r * P + p] = c * qp - s * qq;
-          Q[r * P + q] = s * qp + c * qq;
+    if (lane < P * P) {
+      const double h = H[lane];
+      tot = h * h;
+      if (lane / P != lane % P) off = h * h;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (off <= 1e-32 * tot || off == 0.0) break;  // the same sums in every lane
+    for (int r = 0; r < 3; ++r) {
+      double c = 1.0, sn = 0.0;
+      if (lane < 2) {
+        const int p = pair_lo(r, lane), q = pair_hi(r, lane);
+        if (q < P) {
+          const double apq = H[p * P + q];
+          if (apq != 0.0) {
+            const double theta = (H[q * P + q] - H[p * P + p]) / (2.0 * apq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
         }
       }
-  }
-  // selection sort, descending eigenvalues
-  for (int i = 0; i < P; ++i) {
-    int m = i;
-    for (int j = i + 1; j < P; ++j)
-      if (H[j * P + j] > H[m * P + m]) m = j;
-    if (m != i) {
-      const double t = H[i * P + i];
-      H[i * P + i] = H[m * P + m];
-      H[m * P + m] = t;
-      for (int r = 0; r < P; ++r) {
-        const double u = Q[r * P + i];
-        Q[r * P + i] = Q[r * P + m];
-        Q[r * P + m] = u;
+      const double c0 = __shfl_sync(0xffffffffu, c, 0), s0 = __shfl_sync(0xffffffffu, sn, 0);
+      const double c1 = __shfl_sync(0xffffffffu, c, 1), s1 = __shfl_sync(0xffffffffu, sn, 1);
+      const int pr = lane >> 2, x = lane & 3;
+      const int p = pair_lo(r, pr & 1), q = pair_hi(r, pr & 1);
+      const bool act = lane < 8 && q < P && x < P;
+      const double cc = pr ? c1 : c0, ss = pr ? s1 : s0;
+      if (act) {  // columns p, q
+        const double hp = H[x * P + p], hq = H[x * P + q];
+        H[x * P + p] = cc * hp - ss * hq;
+        H[x * P + q] = ss * hp + cc * hq;
       }
+      __syncwarp();
+      if (act) {  // rows p, q
+        const double hp = H[p * P + x], hq = H[q * P + x];
+        H[p * P + x] = cc * hp - ss * hq;
+        H[q * P + x] = ss * hp + cc * hq;
+      }
+      if (act) {  // eigenvector columns p, q
+        const double qp = Q[x * P + p], qq = Q[x * P + q];
+        Q[x * P + p] = cc * qp - ss * qq;
+        Q[x * P + q] = ss * qp + cc * qq;
+      }
+      __syncwarp();
     }
   }
+  // selection sort, descending eigenvalues
+  if (lane == 0)
+    for (int i = 0; i < P; ++i) {
+      int m = i;
+      for (int j = i + 1; j < P; ++j)
+        if (H[j * P + j] > H[m * P + m]) m = j;
+      if (m != i) {
+        const double t = H[i * P + i];
+        H[i * P + i] = H[m * P + m];
+        H[m * P + m] = t;
+        for (int r = 0; r < P; ++r) {
+          const double u = Q[r * P + i];
+          Q[r * P + i] = Q[r * P + m];
+          Q[r * P + m] = u;
+        }
+      }
+    }
+  __syncwarp();
 }
 
 // orthonormalise the P columns of V (k x P, row-major in shared memory) by
 // Gram-Schmidt applied twice per column; a column that vanishes is replaced
-// by a fixed pseudo-random vector
+// by a fixed pseudo-random vector.  (Cholesky-QR in two passes costs fewer
+// block sums but leaves the basis less aligned with the previous Ritz
+// vectors, and the Rayleigh-Ritz step after it then needs more Jacobi sweeps.)
 __device__ void orthonormalise(int k, int P, double *V, double *scratch, unsigned long long salt) {
   for (int j = 0; j < P; ++j) {
     for (int attempt = 0; attempt < 3; ++attempt) {
@@ -388,7 +428,10 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
             H[i * P + j] = h[q];
             H[j * P + i] = h[q];
           }
-      tiny_jacobi(P, H, Q);
+    }
+    if (threadIdx.x < 32) {
+      __syncwarp();
+      tiny_jacobi_warp(P, H, Q);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < k; r += blockDim.x) {  // W = V Q, A W = Y Q
