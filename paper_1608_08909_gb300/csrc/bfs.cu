@@ -122,6 +122,7 @@ __device__ void block_expand_level(Fr &&fr, unsigned cc, const int4 *__restrict_
 // max/min sp
 // --------------------------------------------------------------------------
 constexpr int kSoloMax = 2048;       // frontiers up to this size are expanded by block 0 alone
+constexpr int kFirstSearchLevels = 16;  // depth up to which a cluster run's first search stays on the grid
 constexpr int kSoloLevels = 4096;    // block 0 hands back to the grid at least this often
 
 struct MaxMinArgs {
@@ -140,6 +141,8 @@ struct MaxMinArgs {
   unsigned long long *best;  // [2] packed (mind << 32 | ~node) maxima, by pivot parity
   BarrierState *bar;
   const unsigned *run_if;  // non-null: run only if *run_if != 0 (the cluster kernel gave the search up)
+  int32_t max_levels;      // > 0: stop the search at this depth and set *gave_up (the first search of a
+  unsigned *gave_up;       // cluster run: a deep graph is searched faster by the cluster itself)
 };
 
 // Block 0 alone expands levels L, L+1, ... while the frontier has at most
@@ -164,6 +167,7 @@ __device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*
   for (int steps = 0; steps < kSoloLevels; ++steps) {
     const unsigned cc = s_cnt[cur];
     if (cc == 0 || cc > (unsigned)kSoloMax) break;
+    if (A.max_levels > 0 && L >= (unsigned)A.max_levels) break;
     const int nxt = cur ^ 1;
     unsigned *qout = ((L + 1) & 1) ? A.q1 : A.q0;
     const unsigned nd = L + 1;
@@ -235,6 +239,10 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
     for (unsigned L = __ldcg(A.level);;) {
       const unsigned c = __ldcg(A.qcnt + L % 3);
       if (c == 0) break;
+      if (A.max_levels > 0 && L >= (unsigned)A.max_levels) {  // every block reads the same L: uniform
+        if (gtid == 0) *A.gave_up = 1u;
+        return;
+      }
       if (c <= (unsigned)kSoloMax) {
         if (blockIdx.x == 0) maxmin_solo(A, L, c, sq, s_cnt, S);
         if (!grid_barrier(A.bar, A.status)) return;
@@ -319,6 +327,7 @@ static void carve_maxmin(Carver &c, MaxMinArgs &A, unsigned **spill, int32_t n, 
   A.bar = c.take<BarrierState>(1);
   *spill = c.take<unsigned>(std::max<size_t>(1, maxmin_cluster_spill_entries(n)));
   A.run_if = c.take<unsigned>(1);
+  A.gave_up = c.take<unsigned>(1);
 }
 
 // the cooperative grid kernel, after resetting its counters and barrier
@@ -354,13 +363,19 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
   if (rc) return rc;
   unsigned *fallback = const_cast<unsigned *>(A.run_if);
   A.run_if = nullptr;
+  A.max_levels = 0;
   if (k >= 2 && maxmin_cluster_mind_bytes(n) > 0) {
+    // the first search on the grid while it stays within kFirstSearchLevels
+    // levels (small-world graphs: few levels of up to all nodes); deeper
+    // graphs leave it to the cluster, whose levels cost less
     MaxMinArgs first = A;
     first.k = 1;
+    first.max_levels = kFirstSearchLevels;
+    SSM_TRY_CUDA(cudaMemsetAsync(A.gave_up, 0, sizeof(unsigned), s));
     if ((rc = launch_maxmin_grid(first, s))) return rc;
     int mind_bytes = 0;
-    rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, fallback, A.mind, A.best, s,
-                               &mind_bytes);
+    rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, fallback, A.mind, A.best,
+                               A.gave_up, s, &mind_bytes);
     if (rc || mind_bytes == 4) return rc;
     if (mind_bytes == 2) A.run_if = fallback;
   }

@@ -22,13 +22,14 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
 // to run only if *fallback (device) was set: a search deeper than 65534
 // levels.  spill holds maxmin_cluster_spill_entries(n) entries.  With
 // init_mind / init_best (device; the grid kernel's mind and packed maximum
-// after a k = 1 run from start) the cluster starts at pivot 1.
+// after a k = 1 run from start) the cluster starts at pivot 1, unless
+// *init_gaveup (device) says that run stopped early.
 size_t maxmin_cluster_spill_entries(int32_t n);
 int maxmin_cluster_mind_bytes(int32_t n);  // 4 or 2 if the cluster kernel would run, else 0
 int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int32_t k, int32_t start,
                           int32_t *pivots, int32_t *status, unsigned *spill, unsigned *fallback,
-                          const unsigned *init_mind, const unsigned long long *init_best, cudaStream_t s,
-                          int *mind_bytes);
+                          const unsigned *init_mind, const unsigned long long *init_best,
+                          const unsigned *init_gaveup, cudaStream_t s, int *mind_bytes);
 // records the kernel the last selection took (cluster size, 0 for the grid kernel; mind bytes)
 void note_pivot_config(int32_t cluster, int32_t mind_bytes);
 

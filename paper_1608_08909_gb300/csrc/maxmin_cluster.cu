@@ -63,6 +63,7 @@ struct McArgs {
   // after it, 4 bytes per node, and its packed (mind << 32 | ~node) maximum
   const unsigned *init_mind;
   const unsigned long long *init_best;
+  const unsigned *init_gaveup;  // the first search stopped early: ignore init_mind and search from start
   int32_t cshift;   // C = 1 << cshift
   int32_t slots;    // shared-memory mind slots per CTA (>= ceil(n / C), multiple of 8)
   int32_t qcap;     // queue entries per parity in shared memory
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
 
   unsigned p = (unsigned)A.start;
   int j0 = 0;
-  if (A.init_mind) {
+  if (A.init_mind && __ldcg(A.init_gaveup) == 0u) {
     // the search from start ran on the whole GPU (it reaches every node, and
     // a grid of all SMs does that faster than one cluster): take its mind
     // and its maximum, which is pivot 1 (uniform: every CTA reads the same key)
@@ -514,8 +515,8 @@ int maxmin_cluster_mind_bytes(int32_t n) {
 
 int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int32_t k, int32_t start,
                           int32_t *pivots, int32_t *status, unsigned *spill, unsigned *fallback,
-                          const unsigned *init_mind, const unsigned long long *init_best, cudaStream_t s,
-                          int *mind_bytes) {
+                          const unsigned *init_mind, const unsigned long long *init_best,
+                          const unsigned *init_gaveup, cudaStream_t s, int *mind_bytes) {
   *mind_bytes = 0;
   if (!maxmin_cluster_candidate(n)) return SSM_OK;
   const McShape sh = mc_shape(n);
@@ -526,6 +527,7 @@ int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int
   A.fallback = fallback;
   A.init_mind = init_mind;
   A.init_best = init_best;
+  A.init_gaveup = init_gaveup;
   A.cshift = sh.C == 16 ? 4 : 3;
   A.slots = sh.slots;
   A.qcap = sh.qcap;
