@@ -278,6 +278,67 @@ static int grid_for(int64_t items, int threads) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// The same as k_region_ecc with four consecutive nodes per thread (one 8-byte
+// load per pivot, so a warp reads 256 contiguous bytes of a row), for n a
+// multiple of 4 and k <= kAggSmemPivots: the per-region maxima go through a
+// shared-memory copy of ecc (one shared atomicMax per node, then one global
+// atomicMax per pivot and block)
+constexpr int kAggSmemPivots = 4096;
+__global__ void __launch_bounds__(kAggThreads) k_region_ecc4(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
+                                                             int32_t *__restrict__ region, unsigned *__restrict__ ecc,
+                                                             unsigned *__restrict__ dmax) {
+  __shared__ unsigned s_ecc[kAggSmemPivots];
+  for (int a = threadIdx.x; a < k; a += blockDim.x) s_ecc[a] = 0u;
+  __syncthreads();
+  unsigned worst = 0u;
+  const int64_t n4 = n / 4;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 *col = reinterpret_cast<const uint2 *>(dip) + g;  // nodes 4g .. 4g + 3 of every row
+    unsigned best[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    int32_t arg[4] = {0, 0, 0, 0};
+    // eight pivots' words in flight, compared in pivot order (ties to the lowest a)
+    for (int32_t a0 = 0; a0 < k; a0 += 8) {
+      uint2 w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = a0 + q < k ? __ldg(col + (size_t)(a0 + q) * n4) : make_uint2(0u, 0u);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (a0 + q >= k) break;
+        const unsigned d[4] = {w[q].x & 0xFFFFu, w[q].x >> 16, w[q].y & 0xFFFFu, w[q].y >> 16};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          if (d[h] < best[h]) {
+            best[h] = d[h];
+            arg[h] = a0 + q;
+          }
+          worst = max(worst, d[h]);
+        }
+      }
+    }
+    if (region) reinterpret_cast<int4 *>(region)[g] = make_int4(arg[0], arg[1], arg[2], arg[3]);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) atomicMax(s_ecc + arg[h], best[h]);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x)
+    if (s_ecc[a]) atomicMax(ecc + a, s_ecc[a]);
+  if (dmax) {
+    for (int o = 16; o > 0; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0 && worst) atomicMax(dmax, worst);
+  }
+}
+
+// regions and eccentricities (and the largest entry into dmax when given)
+static void launch_region_ecc(int32_t n, int32_t k, const uint16_t *dip, int32_t *region, unsigned *ecc,
+                              unsigned *dmax, cudaStream_t s) {
+  const bool vec = n % 4 == 0 && k <= kAggSmemPivots && (reinterpret_cast<uintptr_t>(dip) & 7u) == 0 &&
+                   (!region || (reinterpret_cast<uintptr_t>(region) & 15u) == 0);
+  if (vec)
+    note_launch(), k_region_ecc4<<<grid_for(n / 4, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, dmax);
+  else
+    note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, dmax);
+}
+
 }  // namespace ssm
 
 SSM_API size_t ssm_aggregate_workspace(int32_t k) {
@@ -297,8 +358,7 @@ SSM_API int ssm_aggregate_size(int32_t n, int32_t k, const uint16_t *dip, int64_
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate_size: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(len, 0, 2 * sizeof(long long), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, nullptr, ecc,
-                                                                              (unsigned *)(len + 1));
+  launch_region_ecc(n, k, dip, nullptr, ecc, (unsigned *)(len + 1), s);
   note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
   long long h[2] = {0, 0};
   SSM_TRY_CUDA(cudaMemcpyAsync(h, len, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -320,7 +380,7 @@ SSM_API int ssm_aggregate(int32_t n, int32_t k, const uint16_t *dip, int32_t *re
   if (!c.ok) return fail(SSM_E_NOMEM, "ssm_aggregate: workspace %zu bytes, need %zu", ws_bytes, c.size());
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
   SSM_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)cnt_len * sizeof(uint32_t), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, nullptr);
+  launch_region_ecc(n, k, dip, region, ecc, nullptr, s);
   note_launch(), k_cnt_off<<<1, 32, 0, s>>>(k, ecc, cnt_off, (long long)cnt_len, status);
   note_launch(), k_histogram<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, dip, region, cnt_off, cnt_len, cnt);
   note_launch(), k_row_prefix<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(k, cnt_off, cnt_len, cnt);
@@ -372,7 +432,7 @@ SSM_API int ssm_aggregate_noalloc(int32_t n, int32_t k, const uint16_t *dip, int
   if (rc) return rc;
   long long *len = reinterpret_cast<long long *>(ecc + kNoAllocMaxPivots);
   SSM_TRY_CUDA(cudaMemsetAsync(ecc, 0, (size_t)k * sizeof(unsigned), s));
-  note_launch(), k_region_ecc<<<grid_for(n, kAggThreads), kAggThreads, 0, s>>>(n, k, dip, region, ecc, nullptr);
+  launch_region_ecc(n, k, dip, region, ecc, nullptr, s);
   note_launch(), k_table_len<<<1, 256, 0, s>>>(k, ecc, len);
   long long h = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&h, len, sizeof h, cudaMemcpyDeviceToHost, s));

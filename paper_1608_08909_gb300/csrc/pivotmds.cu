@@ -16,7 +16,7 @@
 //               block), then a Rayleigh-Ritz step with B
 //   k_project   x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa),
 //               the sum in compensated (two-float) FP32 arithmetic
-//   k_edge_sum / k_rescale: scale so that sum_E ||x_i - x_j|| = m.
+//   k_edge_sum_* / k_rescale: scale so that sum_E ||x_i - x_j|| = m.
 #include <algorithm>
 
 #include "common.cuh"
@@ -650,73 +650,111 @@ __global__ void k_dmax(int64_t count, const uint16_t *__restrict__ dip, unsigned
 }
 
 // ------------------------------------------------------------- rescale
+// Sum over the edges of ||x_i - x_j|| (each undirected edge once, from its
+// lower end i < j), in three steps with a fixed order of summation:
+//   k_edge_sum_rows  the sum of every row of at most kEdgeShort entries into
+//                    rowsum[i] (a lane per node, eight entries in flight);
+//                    longer rows are listed and get rowsum[i] from
+//   k_edge_sum_long  a warp per listed row (eight entries per lane in flight,
+//                    lanes then a fixed tree) -- hub rows of heavy-tailed
+//                    graphs are spread over the grid instead of queuing in
+//                    the warp that owns their node;
+//   k_edge_sum_total the rows in node order: a fixed share per thread, fixed
+//                    trees, the last block forms the scale.
+// Weighted graphs (elen) also sum the target lengths l_ij the same way.
+constexpr int kEdgeShort = 32;
+
 template <class T2>
-__global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__restrict__ rowptr,
-                                                  const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
-                                                  const float *__restrict__ elen,
-                                                  double *__restrict__ part, unsigned *__restrict__ done,
-                                                  double *__restrict__ scale, int32_t *__restrict__ status) {
-  using R = decltype(pos[0].x);  // edge lengths in the precision of the positions, summed in FP64
-  // elen (weighted graphs, may be null): the target is the sum of the edge
-  // lengths instead of m, summed alongside in FP64
-  __shared__ double red[8], redl[8];
-  double accl = 0.0;
-  __shared__ unsigned s_ticket;
+__device__ __forceinline__ double edge_len(T2 a, T2 b) {
+  using R = decltype(a.x);  // lengths in the precision of the positions, summed in FP64
+  const R dx = a.x - b.x, dy = a.y - b.y;
+  return (double)sqrt(dx * dx + dy * dy);
+}
+
+template <class T2>
+__global__ void __launch_bounds__(256) k_edge_sum_rows(int32_t n, const int32_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
+                                                       const float *__restrict__ elen, double *__restrict__ rowsum,
+                                                       double *__restrict__ rowlen, int32_t *__restrict__ longrows,
+                                                       unsigned *__restrict__ nlong) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+    if (e - b > kEdgeShort) {
+      longrows[atomicAdd(nlong, 1u)] = (int32_t)i;  // the list's order does not matter: rowsum is by node
+      continue;
+    }
+    const T2 xi = pos[i];
+    double acc = 0.0, accl = 0.0;
+    for (int t = b; t < e; t += 8) {
+      int j[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) j[q] = t + q < e ? __ldg(colidx + t + q) : -1;
+      T2 xj[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xj[q] = j[q] > i ? pos[j[q]] : xi;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (j[q] > i) {
+          acc += edge_len(xi, xj[q]);
+          if (elen) accl += (double)__ldg(elen + t + q);
+        }
+    }
+    rowsum[i] = acc;
+    if (elen) rowlen[i] = accl;
+  }
+}
+
+template <class T2>
+__global__ void __launch_bounds__(256) k_edge_sum_long(const int32_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ colidx, const T2 *__restrict__ pos,
+                                                       const float *__restrict__ elen,
+                                                       const int32_t *__restrict__ longrows,
+                                                       const unsigned *__restrict__ nlong, double *__restrict__ rowsum,
+                                                       double *__restrict__ rowlen) {
   const int lane = threadIdx.x & 31;
-  double acc = 0.0;
-  // a warp takes 32 consecutive nodes; rows longer than 32 are walked by the whole warp
-  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + lane;
-    int b = 0, e = 0;
-    T2 xi{};
-    if (i < n) {
-      b = __ldg(rowptr + i);
-      e = __ldg(rowptr + i + 1);
-      xi = pos[i];
+  const unsigned cnt = __ldcg(nlong);
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < cnt; r += nwarps) {
+    const int i = __ldg(longrows + r);
+    const int hb = __ldg(rowptr + i), he = __ldg(rowptr + i + 1);
+    const T2 xi = pos[i];
+    double acc = 0.0, accl = 0.0;
+    for (int t0 = hb + lane; t0 < he; t0 += 32 * 8) {
+      int j[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) j[q] = t0 + 32 * q < he ? __ldg(colidx + t0 + 32 * q) : -1;
+      T2 xj[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xj[q] = j[q] > i ? pos[j[q]] : xi;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (j[q] > i) {
+          acc += edge_len(xi, xj[q]);
+          if (elen) accl += (double)__ldg(elen + t0 + 32 * q);
+        }
     }
-    if (e - b <= 32) {
-      // eight column indices, then their eight positions, in flight together
-      for (int t = b; t < e; t += 8) {
-        int j[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) j[q] = t + q < e ? __ldg(colidx + t + q) : -1;
-        T2 xj[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) xj[q] = j[q] > i ? pos[j[q]] : xi;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (j[q] > i) {
-            const R dx = xi.x - xj[q].x, dy = xi.y - xj[q].y;
-            acc += (double)sqrt(dx * dx + dy * dy);
-            if (elen) accl += (double)__ldg(elen + t + q);
-          }
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      accl += __shfl_xor_sync(0xffffffffu, accl, o);
     }
-    unsigned longs = __ballot_sync(0xffffffffu, e - b > 32);
-    while (longs) {
-      const int src = __ffs(longs) - 1;
-      longs &= longs - 1u;
-      const int hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-      const int64_t hi = base + src;
-      const R hx = __shfl_sync(0xffffffffu, xi.x, src), hy = __shfl_sync(0xffffffffu, xi.y, src);
-      // eight entries per lane in flight (hub rows of heavy-tailed graphs run to thousands)
-      for (int t0 = hb + lane; t0 < he; t0 += 32 * 8) {
-        int j[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) j[q] = t0 + 32 * q < he ? __ldg(colidx + t0 + 32 * q) : -1;
-        T2 xj[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) xj[q] = j[q] > hi ? pos[j[q]] : T2{hx, hy};
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (j[q] > hi) {
-            const R dx = hx - xj[q].x, dy = hy - xj[q].y;
-            acc += (double)sqrt(dx * dx + dy * dy);
-            if (elen) accl += (double)__ldg(elen + t0 + 32 * q);
-          }
-      }
+    if (lane == 0) {
+      rowsum[i] = acc;
+      if (elen) rowlen[i] = accl;
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_edge_sum_total(int32_t n, const int32_t *__restrict__ rowptr,
+                                                        const double *__restrict__ rowsum,
+                                                        const double *__restrict__ rowlen, double *__restrict__ part,
+                                                        unsigned *__restrict__ done, double *__restrict__ scale,
+                                                        int32_t *__restrict__ status) {
+  __shared__ double red[8], redl[8];
+  __shared__ unsigned s_ticket;
+  double acc = 0.0, accl = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    acc += __ldcg(rowsum + i);
+    if (rowlen) accl += __ldcg(rowlen + i);
   }
   for (int o = 16; o > 0; o >>= 1) {
     acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -762,7 +800,7 @@ __global__ void __launch_bounds__(256) k_edge_sum(int32_t n, const int32_t *__re
     tot += red[w];
     totl += redl[w];
   }
-  const double m = elen ? totl : (double)__ldg(rowptr + n) * 0.5;
+  const double m = rowlen ? totl : (double)__ldg(rowptr + n) * 0.5;
   if (!(tot > 0.0) || !isfinite(tot)) {
     dev_fail(status, SSM_E_NUMERIC);
     *scale = 1.0;
@@ -789,10 +827,12 @@ struct MdsWs {
   unsigned *done, *dmax;
   double *Yg;
   BarrierState *bar;
+  double *rowsum, *rowlen;  // [n] per-row edge-length sums (rescale)
+  int32_t *longrows;        // [n] rows above kEdgeShort entries
+  unsigned *nlong;
 };
 
 static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
-  (void)n;
   const size_t kk = (size_t)k * k;
   w.Glo = c.take<unsigned long long>(kk);
   w.Ghi = c.take<unsigned long long>(kk);
@@ -811,6 +851,10 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.dmax = c.take<unsigned>(1);
   w.Yg = c.take<double>(2 * (size_t)k * kEigP);
   w.bar = c.take<BarrierState>(1);
+  w.rowsum = c.take<double>((size_t)n);
+  w.rowlen = c.take<double>((size_t)n);
+  w.longrows = c.take<int32_t>((size_t)n);
+  w.nlong = c.take<unsigned>(1);
   return c.size();
 }
 
@@ -851,16 +895,25 @@ static int launch_eigen(int32_t n, int32_t k, MdsWs &w, const S *colsum, double 
 static int launch_rescale(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *elen, void *pos,
                           int32_t precision, MdsWs &w, int32_t *status, cudaStream_t s) {
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)num_sms() * 8);
-  const int eb = std::min(pb, 4096);
+  const int eb = std::min(pb, 4096);  // part holds 2 per block
+  double *rowlen = elen ? w.rowlen : nullptr;
+  SSM_TRY_CUDA(cudaMemsetAsync(w.nlong, 0, sizeof(unsigned), s));
   if (precision == 64) {
-    note_launch(), k_edge_sum<double2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, elen, w.part,
-                                                          w.done, w.scale, status);
-    note_launch(), k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
+    note_launch(), k_edge_sum_rows<double2><<<pb, 256, 0, s>>>(n, rowptr, colidx, (const double2 *)pos, elen,
+                                                               w.rowsum, rowlen, w.longrows, w.nlong);
+    note_launch(), k_edge_sum_long<double2><<<pb, 256, 0, s>>>(rowptr, colidx, (const double2 *)pos, elen, w.longrows,
+                                                               w.nlong, w.rowsum, rowlen);
   } else {
-    note_launch(), k_edge_sum<float2><<<eb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, elen, w.part,
-                                                         w.done, w.scale, status);
-    note_launch(), k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
+    note_launch(), k_edge_sum_rows<float2><<<pb, 256, 0, s>>>(n, rowptr, colidx, (const float2 *)pos, elen,
+                                                              w.rowsum, rowlen, w.longrows, w.nlong);
+    note_launch(), k_edge_sum_long<float2><<<pb, 256, 0, s>>>(rowptr, colidx, (const float2 *)pos, elen, w.longrows,
+                                                              w.nlong, w.rowsum, rowlen);
   }
+  note_launch(), k_edge_sum_total<<<eb, 256, 0, s>>>(n, rowptr, w.rowsum, rowlen, w.part, w.done, w.scale, status);
+  if (precision == 64)
+    note_launch(), k_rescale<double2><<<pb, 256, 0, s>>>(n, (double2 *)pos, w.scale);
+  else
+    note_launch(), k_rescale<float2><<<pb, 256, 0, s>>>(n, (float2 *)pos, w.scale);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
