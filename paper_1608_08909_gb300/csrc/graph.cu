@@ -3,9 +3,10 @@
 // repeated edges dropped, followed by a connectivity check (union-find).
 //
 //   count degrees (atomics) -> exclusive scan -> scatter both directions
-//   -> sort every row (warp bitonic in registers for rows <= 32, block bitonic
-//      in shared memory up to kSmemSortCap, block bitonic in global memory
-//      beyond) -> flag first occurrences -> scan flags -> compact.
+//   -> sort every row (warp bitonic in registers for rows <= 128, block
+//      bitonic in shared memory up to kSmemSortCap, block bitonic in global
+//      memory beyond) -> flag first occurrences (entry-parallel) -> scan flags
+//      -> compact.
 #include <algorithm>
 
 #include "bfs.cuh"
@@ -47,6 +48,42 @@ __global__ void k_scatter(int64_t m, const int32_t *__restrict__ src, const int3
 // >= len never has to move, so comparisons touching it can be skipped.
 
 // rows of length <= 32: one warp per row, values in registers
+// Bitonic sort of 32 E keys held by a warp, key e 32 + lane in x[e] of that
+// lane: partners 32 or more apart sit in the same lane, closer ones in
+// another lane of the same slot (a shuffle)
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int32_t (&x)[E]) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int bs = 2; bs <= 32 * E; bs <<= 1) {
+#pragma unroll
+    for (int j = bs >> 1; j >= 1; j >>= 1) {
+      if (j >= 32) {
+        const int je = j >> 5;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if ((e & je) == 0) {
+            const bool asc = (((e * 32) & bs) == 0);
+            const int32_t a = x[e], c = x[e | je];
+            x[e] = asc ? min(a, c) : max(a, c);
+            x[e | je] = asc ? max(a, c) : min(a, c);
+          }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const unsigned idx = (unsigned)e * 32u + lane;
+          const bool asc = (idx & (unsigned)bs) == 0u;
+          const int32_t y = __shfl_xor_sync(0xffffffffu, x[e], j);
+          x[e] = (((idx & (unsigned)j) == 0u) == asc) ? min(x[e], y) : max(x[e], y);
+        }
+      }
+    }
+  }
+}
+
+// rows of up to kWarpSortMax entries: one warp each, keys in registers (1 or
+// 4 per lane); longer rows are listed for k_sort_big_rows
+constexpr int kWarpSortMax = 128;
 __global__ void k_sort_small_rows(int32_t n, const int *__restrict__ off, int32_t *__restrict__ tmp,
                                   unsigned *__restrict__ big_rows, unsigned *__restrict__ big_count) {
   const unsigned lane = threadIdx.x & 31u;
@@ -54,22 +91,28 @@ __global__ void k_sort_small_rows(int32_t n, const int *__restrict__ off, int32_
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = warp; row < n; row += nwarps) {
     const int b = off[row], len = off[row + 1] - b;
-    if (len > 32) {
+    if (len > kWarpSortMax) {
       if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = (unsigned)row;
       continue;
     }
-    int32_t x = (int)lane < len ? tmp[b + lane] : kPad;
+    if (len > 32) {
+      int32_t x[4];
 #pragma unroll
-    for (int bs = 2; bs <= 32; bs <<= 1) {
-      int32_t y = __shfl_xor_sync(0xffffffffu, x, bs - 1);
-      x = (lane & (bs >> 1)) ? max(x, y) : min(x, y);
-#pragma unroll
-      for (int j = bs >> 2; j >= 1; j >>= 1) {
-        y = __shfl_xor_sync(0xffffffffu, x, j);
-        x = (lane & j) ? max(x, y) : min(x, y);
+      for (int e = 0; e < 4; ++e) {
+        const int i = e * 32 + (int)lane;
+        x[e] = i < len ? tmp[b + i] : kPad;
       }
+      warp_bitonic<4>(x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = e * 32 + (int)lane;
+        if (i < len) tmp[b + i] = x[e];
+      }
+      continue;
     }
-    if ((int)lane < len) tmp[b + lane] = x;
+    int32_t x[1] = {(int)lane < len ? tmp[b + lane] : kPad};
+    warp_bitonic<1>(x);
+    if ((int)lane < len) tmp[b + lane] = x[0];
   }
 }
 
@@ -101,7 +144,7 @@ __device__ void block_bitonic(int len, Get get, Put put) {
   }
 }
 
-// rows longer than 32: one block per row
+// rows longer than kWarpSortMax: one block per row
 __global__ void __launch_bounds__(kSortBlock) k_sort_big_rows(const int *__restrict__ off, int32_t *__restrict__ tmp,
                                                                const unsigned *__restrict__ big_rows,
                                                                const unsigned *__restrict__ big_count) {
@@ -124,11 +167,19 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_big_rows(const int *__restr
 }
 
 // flag[t] = 1 for the first occurrence of a value within its (sorted) row
-__global__ void k_flag_unique(int32_t n, const int *__restrict__ off, const int32_t *__restrict__ tmp,
-                              int *__restrict__ flag) {
+// flag[t] = 1 for the first occurrence of a value in its (sorted) row: every
+// entry against the one before it, then (k_flag_row_starts) every row's first
+// entry, so hub rows do not queue in one thread
+__global__ void k_flag_unique(const int *__restrict__ total, const int32_t *__restrict__ tmp, int *__restrict__ flag) {
+  const int64_t tot = *total;  // off[n]: the directed entries before dedupe
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    flag[t] = (t == 0 || tmp[t] != tmp[t - 1]) ? 1 : 0;
+}
+
+__global__ void k_flag_row_starts(int32_t n, const int *__restrict__ off, int *__restrict__ flag) {
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
-    const int b = off[row], e = off[row + 1];
-    for (int t = b; t < e; ++t) flag[t] = (t == b || tmp[t] != tmp[t - 1]) ? 1 : 0;
+    const int b = off[row];
+    if (off[row + 1] > b) flag[b] = 1;
   }
 }
 
@@ -245,7 +296,8 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   note_launch(), k_scatter<<<eblocks, 256, 0, s>>>(m_in, src, dst, n, w.off, w.cursor, w.tmp);
   note_launch(), k_sort_small_rows<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.big_rows, w.big_count);
   note_launch(), k_sort_big_rows<<<sms * 2, kSortBlock, 0, s>>>(w.off, w.tmp, w.big_rows, w.big_count);
-  note_launch(), k_flag_unique<<<nblocks, 256, 0, s>>>(n, w.off, w.tmp, w.flag);
+  note_launch(), k_flag_unique<<<2 * eblocks, 256, 0, s>>>(w.off + n, w.tmp, w.flag);
+  note_launch(), k_flag_row_starts<<<nblocks, 256, 0, s>>>(n, w.off, w.flag);
   // total directed entries before dedupe = off[n]; read it to size the scan
   int total = 0;
   SSM_TRY_CUDA(cudaMemcpyAsync(&total, w.off + n, sizeof(int), cudaMemcpyDeviceToHost, s));

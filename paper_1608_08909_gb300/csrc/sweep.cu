@@ -615,31 +615,36 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
 // (a wrong dmax hint) is recorded as SSM_E_ARG and clamped, so no table read
 // leaves the table
 __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__restrict__ dip,
-                           unsigned *__restrict__ dtile, int32_t *__restrict__ status) {
-  const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
-  const int64_t total = ntiles * (int64_t)k * 32 * kPpl;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(w % kPpl);
-    const int64_t wl = w / kPpl;
-    const int l = (int)(wl & 31);
-    const int64_t ta = wl >> 5;
-    const int a = (int)(ta % k);
-    const int64_t t = ta / k;
-    const int64_t i = t * kTileNodes + (int64_t)kNpl * l + 2 * j;
+                           unsigned *__restrict__ dtile, int32_t *__restrict__ status, int32_t pair_loads) {
+  // node pair p = (2p, 2p + 1) of pivot a lands in word (t k + a) P + (p mod P), t = p div P,
+  // P = kTileNodes / 2 pairs per tile; blocks step over pivots in y, pairs in x
+  constexpr int64_t P = kTileNodes / 2;
+  const int64_t npairs = ((int64_t)(n + kTileNodes - 1) / kTileNodes) * P;
+  const unsigned top = row > 0 ? (unsigned)row - 1u : 0u;
+  for (int a = blockIdx.y; a < k; a += gridDim.y) {
     const uint16_t *drow = dip + (size_t)a * n;
-    unsigned lo = i < n ? (unsigned)__ldg(drow + i) : 0u;
-    unsigned hi = i + 1 < n ? (unsigned)__ldg(drow + i + 1) : 0u;
-    if (row > 0) {
-      const unsigned top = (unsigned)row - 1u;
-      if (lo > top || hi > top) {
-        dev_fail(status, SSM_E_ARG);
-        lo = min(lo, top);
-        hi = min(hi, top);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = 2 * p;
+      unsigned lo = 0u, hi = 0u;
+      if (pair_loads && i + 1 < n) {  // n even and dip 4-byte aligned: the pair is one aligned word
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(drow + i));
+        lo = v & 0xFFFFu;
+        hi = v >> 16;
+      } else {
+        if (i < n) lo = (unsigned)__ldg(drow + i);
+        if (i + 1 < n) hi = (unsigned)__ldg(drow + i + 1);
       }
-      lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
-      hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
+      if (row > 0) {
+        if (lo > top || hi > top) {
+          dev_fail(status, SSM_E_ARG);
+          lo = min(lo, top);
+          hi = min(hi, top);
+        }
+        lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
+        hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
+      }
+      dtile[((p / P) * k + a) * P + (p % P)] = lo | (hi << 16);
     }
-    dtile[w] = lo | (hi << 16);
   }
 }
 
@@ -953,7 +958,14 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
     A.dmax = (int32_t)dmax;
     A.wtab = w.wtab;
     A.den = w.den;
-    note_launch(), k_tile_dip<<<sms * 8, 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile, status);
+    {
+      const int64_t npairs = ((int64_t)n + kTileNodes - 1) / kTileNodes * (kTileNodes / 2);
+      const int gy = std::min(k, 16);
+      const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((npairs + 255) / 256, (int64_t)sms * 8 / gy + 1));
+      const int32_t pair_loads = (n % 2 == 0 && (reinterpret_cast<uintptr_t>(dip) & 3u) == 0) ? 1 : 0;
+      note_launch(), k_tile_dip<<<dim3(gx, gy), 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile, status,
+                                                           pair_loads);
+    }
     if (full) {
       note_launch(), k_build_wtab<<<std::max(1, std::min(sms * 4, (int)(((int64_t)k * (dmax + 1) + 255) / 256))), 256, 0,
                                     s>>>(k, (int32_t)dmax, cnt_off, cnt, w.wtab);
