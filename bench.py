@@ -677,10 +677,12 @@ def run_batch(args):
         for (_, _, pos), x in zip(items, start):
             pos.copy_(x)
 
-    _, threads = ssm.ssm_batch_iterate(items, 4, threads=0)  # tuning run (a copy is timed per candidate)
+    # tuning run (a copy is timed per candidate); the choice is kept per size
+    # class, so the calls below take it without tuning again
+    _, shape = ssm.ssm_batch_iterate(items, 4)
     for _ in range(max(1, args.warmup - 1)):
         reset()
-        ssm.ssm_batch_iterate(items, iters, threads=threads)
+        ssm.ssm_batch_iterate(items, iters)
     reset()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -688,7 +690,7 @@ def run_batch(args):
     with ClockSampler(0) as clk:
         w0 = time.perf_counter()
         e0.record()
-        rel, _ = ssm.ssm_batch_iterate(items, iters, threads=threads, check=False)
+        rel, _ = ssm.ssm_batch_iterate(items, iters, check=False)
         e1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
@@ -706,7 +708,7 @@ def run_batch(args):
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch", "graphs": len(items), "families": list(I.FAMILIES),
                    "n_range": [int(ns.min()), int(ns.max())], "n_sum": int(ns.sum()), "k": "min(100, n/4)",
-                   "iters": iters, "block_threads": threads, "launch": "one CUDA graph"},
+                   "iters": iters, "block_threads": shape[0], "nodes_per_lane": shape[1], "launch": "one CUDA graph"},
         "graphs_per_s": round(len(items) / (ms * 1e-3), 1),
         "ms_sweeps": round(ms, 3), "wall_ms_call": round(wall * 1e3, 3), "prepare_s": round(t_prep, 3),
         "batched_prepare": {"ms": round(t_bprep, 3), "wall_ms": round(t_bprep_wall * 1e3, 3),

@@ -358,14 +358,21 @@ int ssm_full_iterate(int32_t n, const uint16_t *D, void *pos, int32_t precision,
  *   pos[2 node_off .. + 2 n]         float (x, y) pairs, updated in place
  * Graphs have 1 <= n <= 12288 nodes and 1 <= k <= min(n, 1024) pivots.  Each
  * graph runs `iters` iterations (FP32, the clamped s-table form of the
- * single-graph sweep, neighbour terms in ascending column order) in one block
- * with its positions in shared memory; rel_change[g] (device double) gets the
- * relative change of graph g's last iteration.  threads = 128, 256 or 512
- * fixes the block size; 0 tunes it on this batch (a few iterations per
- * candidate on a scratch copy of the positions, timed with CUDA events; the
- * chosen size goes to *threads_used, host, if not NULL).  Synchronous when
- * tuning, else asynchronous on `stream` (the descriptor array is copied
- * before the call returns).  Workspace: ssm_batch_iterate_workspace(G, graphs).
+ * single-graph sweep evaluated about x_i, neighbour terms in ascending column
+ * order) in one block with its positions in shared memory; rel_change[g]
+ * (device double) gets the relative change of graph g's last iteration.
+ * Graphs fall into three size classes (n <= 1024, <= 4096, <= 12288), each
+ * launched with its own shape: threads = 128, 256 or 512 fixes the block
+ * size, nodes_per_lane = 2 or 4 the tile shape (64- or 128-node tiles); 0
+ * tunes that parameter per class on this batch (a few iterations per
+ * candidate on a scratch copy of the positions, timed with CUDA events) and
+ * keeps the choice for the process, per class fingerprint (largest n,
+ * largest k, table size, graph count, sum of n k), so a batch of the same
+ * shape is not tuned again.  threads fixed and nodes_per_lane 0 means 2.
+ * shape_used (host int32[2], may be NULL) gets the block size and nodes per
+ * lane of the class with the most work.  Synchronous while it tunes, else
+ * asynchronous on `stream` (the descriptors are copied before the call
+ * returns).  Workspace: ssm_batch_iterate_workspace(G, graphs).
  * Device errors: SSM_E_NUMERIC (non-finite weights), SSM_E_GRAPH (a pivot or
  * column id outside its graph).
  * ------------------------------------------------------------------- */
@@ -409,8 +416,8 @@ int ssm_batch_layout_init(int32_t G, const ssm_batch_graph *graphs, const int64_
 
 int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const int32_t *rowptr, const int32_t *colidx,
                       const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
-                      float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t *threads_used,
-                      int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+                      float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t nodes_per_lane,
+                      int32_t *shape_used, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------
  * Layout quality measures (Section 4).

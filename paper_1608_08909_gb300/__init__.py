@@ -84,7 +84,7 @@ def lib():
                 "ssm_gram": (ctypes.c_int, [i32, i32, v, v, v, v, v, sz, v]),
                 "ssm_pivotmds_workspace": (sz, [i32, i32]),
                 "ssm_batch_iterate_workspace": (sz, [i32, v]),
-                "ssm_batch_iterate": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, i32, v, i32, v, v, v, sz, v]),
+                "ssm_batch_iterate": (ctypes.c_int, [i32, v, v, v, v, v, v, v, v, i32, v, i32, i32, v, v, v, sz, v]),
                 "ssm_pivotmds": (ctypes.c_int, [i32, v, v, i32, v, v, i32, i32, v, v, v, sz, v]),
                 "ssm_iterate_workspace": (sz, [i32, i64, i32, i64, i32]),
                 "ssm_iterate": (ctypes.c_int, [i32, i64, v, v, i32, v, v, v, v, i64, v, i32, i32, d, v, v, v, v, v, sz, v]),
@@ -551,12 +551,13 @@ def _batch_dtype():
     return _BATCH_DTYPE
 
 
-def ssm_batch_iterate(items, iters: int, threads: int = 0, stream=None, check: bool = True):
+def ssm_batch_iterate(items, iters: int, threads: int = 0, nodes_per_lane: int = 0, stream=None, check: bool = True):
     """Jacobi sweeps for a batch of small graphs in one launch (ssm_batch_iterate).
 
     items: list of (Graph, Pivots, pos float32 [n, 2]) on one device; every
-    pos is updated in place.  Returns (rel_change float64 [G] device tensor,
-    the block size used)."""
+    pos is updated in place.  threads / nodes_per_lane: 0 tunes (and caches)
+    the block size / tile shape per size class.  Returns (rel_change float64
+    [G] device tensor, (block size, nodes per lane) of the heaviest class)."""
     import numpy as np
     L = lib()
     G = len(items)
@@ -577,10 +578,10 @@ def ssm_batch_iterate(items, iters: int, threads: int = 0, stream=None, check: b
     import contextlib
     ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
     with ctx:
-        return _batch_call(L, items, desc, col, iters, threads, stream, check, dev)
+        return _batch_call(L, items, desc, col, iters, threads, nodes_per_lane, stream, check, dev)
 
 
-def _batch_call(L, items, desc, col, iters, threads, stream, check, dev):
+def _batch_call(L, items, desc, col, iters, threads, nodes_per_lane, stream, check, dev):
     G = len(items)
     rowptr = torch.cat([g.rowptr for g, _, _ in items])
     colidx = torch.cat([g.colidx for g, _, _ in items]) if col else torch.zeros(1, dtype=torch.int32, device=dev)
@@ -593,17 +594,17 @@ def _batch_call(L, items, desc, col, iters, threads, stream, check, dev):
     st = _status(dev)
     dp = desc.ctypes.data_as(ctypes.c_void_p)
     ws = _ws(L.ssm_batch_iterate_workspace(G, dp), dev)
-    used = ctypes.c_int32(0)
+    used = (ctypes.c_int32 * 2)()
     _rc(L.ssm_batch_iterate(G, dp, _ptr(rowptr), _ptr(colidx), _ptr(pivots), _ptr(dip), _ptr(cnt_off), _ptr(cnt),
-                            _ptr(pos_all), iters, _ptr(rel), threads, ctypes.byref(used), _ptr(st), _ptr(ws), ws.numel(),
-                            _stream(stream)), "ssm_batch_iterate")
+                            _ptr(pos_all), iters, _ptr(rel), threads, nodes_per_lane, used, _ptr(st), _ptr(ws),
+                            ws.numel(), _stream(stream)), "ssm_batch_iterate")
     if check:
         ssm_check(st, "ssm_batch_iterate", stream)
     o = 0
     for g, _, pos in items:
         pos.copy_(pos_all[o:o + g.n])
         o += g.n
-    return rel, int(used.value)
+    return rel, (int(used[0]), int(used[1]))
 
 
 class BatchPacked:
@@ -687,9 +688,10 @@ def ssm_batch_prepare(graphs, device="cuda", stream=None, check: bool = True) ->
     return BatchPacked(desc, m, rowptr, colidx, pivots, dip, region, ecc, cnt_off, cnt, pos, eig)
 
 
-def ssm_batch_iterate_packed(bp: BatchPacked, iters: int, threads: int = 0, stream=None, check: bool = True):
+def ssm_batch_iterate_packed(bp: BatchPacked, iters: int, threads: int = 0, nodes_per_lane: int = 0, stream=None,
+                             check: bool = True):
     """ssm_batch_iterate on a prepared batch, positions updated in place in bp.pos;
-    returns (rel_change float64 [G], block size used)."""
+    returns (rel_change float64 [G], (block size, nodes per lane) of the heaviest class)."""
     L = lib()
     G = len(bp)
     dev = bp.pos.device
@@ -697,13 +699,13 @@ def ssm_batch_iterate_packed(bp: BatchPacked, iters: int, threads: int = 0, stre
     st = _status(dev)
     dp = bp.desc.ctypes.data_as(ctypes.c_void_p)
     ws = _ws(L.ssm_batch_iterate_workspace(G, dp), dev)
-    used = ctypes.c_int32(0)
+    used = (ctypes.c_int32 * 2)()
     _rc(L.ssm_batch_iterate(G, dp, _ptr(bp.rowptr), _ptr(bp.colidx), _ptr(bp.pivots), _ptr(bp.dip), _ptr(bp.cnt_off),
-                            _ptr(bp.cnt), _ptr(bp.pos), iters, _ptr(rel), threads, ctypes.byref(used), _ptr(st),
+                            _ptr(bp.cnt), _ptr(bp.pos), iters, _ptr(rel), threads, nodes_per_lane, used, _ptr(st),
                             _ptr(ws), ws.numel(), _stream(stream)), "ssm_batch_iterate")
     if check:
         ssm_check(st, "ssm_batch_iterate", stream)
-    return rel, int(used.value)
+    return rel, (int(used[0]), int(used[1]))
 
 
 def prepare(n: int, src, dst, k: int, start: int = 0, precision: int = 32, device="cuda", stream=None,

@@ -23,6 +23,10 @@
 // unless the caller fixes it: each candidate runs a few iterations on a
 // scratch copy of the positions, timed with CUDA events.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -35,7 +39,7 @@ constexpr int kBatchPrefetch = 8;
 constexpr float kBatchR2Floor = 1e-24f;
 
 struct BatchDev {
-  int32_t n, k, cnt_len, pad;
+  int32_t n, k, cnt_len, ppt;  // ppt: node pairs per tile of the tiled d_ip copy (32 or 64)
   int64_t node_off, row_off, col_off, piv_off, dip_off, cnt_off_off, cnt_base;
   int64_t dtile_off, stab_off;
 };
@@ -55,30 +59,38 @@ struct BatchArgs {
   int32_t *status;
 };
 
+__device__ __forceinline__ unsigned bword(uint2 w, int j) { return j == 0 ? w.x : w.y; }
+__device__ __forceinline__ unsigned bword(unsigned w, int) { return w; }
+
 __device__ __forceinline__ float b_rsqrt(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
-// per graph: the clamped s table (s by d at 2 off_a + a: 0 below 2,
-// cnt[min(d/2, ecc)] up to d = 2 ecc + 2, larger d clamped there) and d_ip re-laid in 64-node tiles, dtile[(t k + a) 32 + l] =
-// d(a, 64t + 2l) | d(a, 64t + 2l + 1) << 16 (0 past the last node)
-__global__ void k_batch_setup(BatchArgs A) {
-  const BatchDev D = A.desc[blockIdx.x];
+// per graph (block b: graph b, or order[b] with use_order): the clamped s
+// table (s by d at 2 off_a + a: 0 below 2, cnt[min(d/2, ecc)] up to d =
+// 2 ecc + 2, larger d clamped there; with do_stab) and d_ip re-laid in tiles
+// of P = ppt node pairs: word (t k + a) P + q holds d(a, 2(t P + q)) |
+// d(a, 2(t P + q) + 1) << 16 (0 past the last node) -- a lane owning
+// 2 P / 32 consecutive nodes reads its P / 32 words of a pivot together
+__global__ void k_batch_setup(BatchArgs A, int use_order, int do_stab) {
+  const int gi = use_order ? __ldg(A.order + blockIdx.x) : (int)blockIdx.x;
+  const BatchDev D = A.desc[gi];
   const int32_t *off = A.cnt_off + D.cnt_off_off;
-  for (int a = 0; a < D.k; ++a) {
-    const int o = __ldg(off + a), ecc = __ldg(off + a + 1) - o - 1;
-    for (int d = threadIdx.x; d <= 2 * ecc + 2; d += blockDim.x)
-      A.stab[D.stab_off + 2 * o + a + d] = d >= 2 ? (float)__ldg(A.cnt + D.cnt_base + o + min(d >> 1, ecc)) : 0.f;
-  }
-  const int64_t tiles = (D.n + 63) / 64, total = tiles * D.k * 32;
+  if (do_stab)
+    for (int a = 0; a < D.k; ++a) {
+      const int o = __ldg(off + a), ecc = __ldg(off + a + 1) - o - 1;
+      for (int d = threadIdx.x; d <= 2 * ecc + 2; d += blockDim.x)
+        A.stab[D.stab_off + 2 * o + a + d] = d >= 2 ? (float)__ldg(A.cnt + D.cnt_base + o + min(d >> 1, ecc)) : 0.f;
+    }
+  const int P = D.ppt;
+  const int tiles = (D.n + 2 * P - 1) / (2 * P), total = tiles * D.k * P;  // below 2^31: n <= 12288, k <= 1024
   const uint16_t *dip = A.dip + D.dip_off;
-  for (int64_t w = threadIdx.x; w < total; w += blockDim.x) {
-    const int l = (int)(w & 31);
-    const int64_t ta = w >> 5;
-    const int a = (int)(ta % D.k);
-    const int64_t i = (ta / D.k) * 64 + 2 * l;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    const int q = w % P, ta = w / P;
+    const int a = ta % D.k;
+    const int i = 2 * ((ta / D.k) * P + q);
     const uint16_t *row = dip + (size_t)a * D.n;
     const unsigned lo = i < D.n ? (unsigned)__ldg(row + i) : 0u;
     const unsigned hi = i + 1 < D.n ? (unsigned)__ldg(row + i + 1) : 0u;
@@ -86,10 +98,20 @@ __global__ void k_batch_setup(BatchArgs A) {
   }
 }
 
+// words of a graph's tiled copy, room for either tile shape (128-node tiles)
+static int64_t batch_words(int32_t n, int32_t k) { return (int64_t)((n + 127) / 128) * k * 64; }
+
 // shared memory: X[2][nmax] float2, pivot node[kmax], pivot table (base, clamp)[kmax],
-// tile partials [2][tmax], then (TAB_SMEM) the graph's s table [smax]
-template <int THREADS, bool TAB_SMEM>
+// tile partials [2][tmax], then (TAB_SMEM) the graph's s table [smax].
+// NPL: nodes per lane (2: 64-node tiles, one 32-bit word of two distances per
+// lane and pivot; 4: 128-node tiles, two words); the update is the
+// single-graph sweep's form about x_i: x_i + (sum_a (B - W)(x_i - x_p) +
+// sum_j (x_j - x_i)(1 - 1/r)) / (deg(i) + sum_a W)
+template <int THREADS, bool TAB_SMEM, int NPL>
 __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t nmax, int32_t kmax) {
+  constexpr int PPL = NPL / 2;    // node pairs per lane
+  constexpr int TN = 32 * NPL;    // nodes per tile
+  using DW = typename std::conditional<PPL == 2, uint2, unsigned>::type;
   extern __shared__ __align__(16) unsigned char bsm[];
   float2 *X0 = reinterpret_cast<float2 *>(bsm);
   float2 *X1 = X0 + nmax;
@@ -110,7 +132,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
     const int gi = __ldg(A.order + gslot);
     const BatchDev D = A.desc[gi];
     const int n = D.n, k = D.k;
-    const int tiles = (n + 63) / 64;
+    const int tiles = (n + TN - 1) / TN;
     float2 *pos = A.pos + D.node_off;
     for (int i = threadIdx.x; i < n; i += THREADS) X0[i] = pos[i];
     const int tab_len = 2 * D.cnt_len + k;
@@ -132,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
     __syncthreads();
     const int32_t *rowptr = A.rowptr + D.row_off;
     const int32_t *colidx = A.colidx + D.col_off;
-    const unsigned *dt = A.dtile + D.dtile_off;
+    const DW *dt = reinterpret_cast<const DW *>(A.dtile + D.dtile_off);
     const float *stab = TAB_SMEM ? stab_s : A.stab;
 
     for (int it = 0; it < A.iters; ++it) {
@@ -140,47 +162,53 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
       float2 *Xn = (it & 1) ? X0 : X1;
       const bool last = it + 1 == A.iters;
       for (int tile = warp; tile < tiles; tile += kWarps) {
-        const int i0 = tile * 64 + 2 * lane;
-        const bool live0 = i0 < n, live1 = i0 + 1 < n;
-        const float2 x0 = live0 ? Xc[i0] : make_float2(0.f, 0.f);
-        const float2 x1 = live1 ? Xc[i0 + 1] : make_float2(0.f, 0.f);
-        const float2 xi2 = make_float2(x0.x, x1.x), yi2 = make_float2(x0.y, x1.y);
-        float2 wx2 = make_float2(0.f, 0.f), wy2 = make_float2(0.f, 0.f);
-        float2 bx2 = make_float2(0.f, 0.f), by2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
-        const unsigned *tp = dt + (size_t)tile * (size_t)k * 32u + lane;
+        const int i0 = tile * TN + NPL * lane;
+        float2 xs[NPL], xi2[PPL], yi2[PPL], ax2[PPL], ay2[PPL], den2[PPL];
+#pragma unroll
+        for (int q = 0; q < NPL; ++q) xs[q] = i0 + q < n ? Xc[i0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < PPL; ++j) {
+          xi2[j] = make_float2(xs[2 * j].x, xs[2 * j + 1].x);
+          yi2[j] = make_float2(xs[2 * j].y, xs[2 * j + 1].y);
+          ax2[j] = ay2[j] = den2[j] = make_float2(0.f, 0.f);
+        }
+        const DW *tp = dt + (size_t)tile * (size_t)k * 32u + lane;
         const float2 kTiny2 = make_float2(kBatchR2Floor, kBatchR2Floor), kTinyQ2 = make_float2(1e-36f, 1e-36f);
-        const float2 kMagic2 = make_float2(-8388608.f, -8388608.f);
-        auto term = [&](int a, unsigned pk) {
+        const float2 kMagic2 = make_float2(-8388608.f, -8388608.f), kMinus2 = make_float2(-1.f, -1.f);
+        auto term = [&](int a, DW pw) {
           const float2 P = Xc[pnode[a]];
           const uint2 I = pidx[a];
-          float2 f2;
-          f2.x = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
-          f2.y = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
           const float cap = __uint_as_float(I.y);
-          float2 s2;
-          const unsigned ix = I.x + (__float_as_uint(fminf(f2.x, cap)) - 0x4B000000u);
-          const unsigned iy = I.x + (__float_as_uint(fminf(f2.y, cap)) - 0x4B000000u);
-          s2.x = TAB_SMEM ? stab[ix] : __ldg(stab + ix);
-          s2.y = TAB_SMEM ? stab[iy] : __ldg(stab + iy);
-          const float2 d2 = __fadd2_rn(f2, kMagic2);
           const float2 px2 = make_float2(-P.x, -P.x), py2 = make_float2(-P.y, -P.y);
-          const float2 dx2 = __fadd2_rn(xi2, px2);
-          const float2 dy2 = __fadd2_rn(yi2, py2);
-          // r^2 + 1e-24 (r == 0 adds w x_p only); + 1e-36 keeps q > 0 at d = 0
-          const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
-          const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, kTinyQ2);
-          float2 u2;
-          u2.x = b_rsqrt(q2.x);
-          u2.y = b_rsqrt(q2.y);
-          const float2 B2 = __fmul2_rn(s2, u2);
-          const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);
-          wx2 = __ffma2_rn(W2, px2, wx2);
-          wy2 = __ffma2_rn(W2, py2, wy2);
-          bx2 = __ffma2_rn(B2, dx2, bx2);
-          by2 = __ffma2_rn(B2, dy2, by2);
-          den2 = __fadd2_rn(den2, W2);
+#pragma unroll
+          for (int j = 0; j < PPL; ++j) {
+            const unsigned pk = bword(pw, j);
+            float2 f2;
+            f2.x = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5410u));
+            f2.y = __uint_as_float(__byte_perm(pk, 0x4B00u, 0x5432u));
+            float2 s2;
+            const unsigned ix = I.x + (__float_as_uint(fminf(f2.x, cap)) - 0x4B000000u);
+            const unsigned iy = I.x + (__float_as_uint(fminf(f2.y, cap)) - 0x4B000000u);
+            s2.x = TAB_SMEM ? stab[ix] : __ldg(stab + ix);
+            s2.y = TAB_SMEM ? stab[iy] : __ldg(stab + iy);
+            const float2 d2 = __fadd2_rn(f2, kMagic2);
+            const float2 dx2 = __fadd2_rn(xi2[j], px2);
+            const float2 dy2 = __fadd2_rn(yi2[j], py2);
+            // r^2 + 1e-24 (r == 0 adds w x_p only); + 1e-36 keeps q > 0 at d = 0
+            const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, kTiny2));
+            const float2 q2 = __ffma2_rn(__fmul2_rn(d2, d2), r2, kTinyQ2);
+            float2 u2;
+            u2.x = b_rsqrt(q2.x);
+            u2.y = b_rsqrt(q2.y);
+            const float2 B2 = __fmul2_rn(s2, u2);
+            const float2 W2 = __fmul2_rn(__fmul2_rn(B2, u2), r2);
+            const float2 c2 = __ffma2_rn(W2, kMinus2, B2);  // B - W
+            ax2[j] = __ffma2_rn(c2, dx2, ax2[j]);
+            ay2[j] = __ffma2_rn(c2, dy2, ay2[j]);
+            den2[j] = __fadd2_rn(den2[j], W2);
+          }
         };
-        unsigned buf[kBatchPrefetch];
+        DW buf[kBatchPrefetch];
         int a0 = 0;
         if (k >= 2 * kBatchPrefetch) {
 #pragma unroll
@@ -188,9 +216,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
           for (; a0 + 2 * kBatchPrefetch <= k; a0 += kBatchPrefetch) {
 #pragma unroll
             for (int t = 0; t < kBatchPrefetch; ++t) {
-              const unsigned pk = buf[t];
+              const DW pw = buf[t];
               buf[t] = __ldg(tp + (unsigned)(a0 + kBatchPrefetch + t) * 32u);
-              term(a0 + t, pk);
+              term(a0 + t, pw);
             }
           }
 #pragma unroll
@@ -198,14 +226,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
           a0 += kBatchPrefetch;
         }
         for (; a0 < k; ++a0) term(a0, __ldg(tp + (unsigned)a0 * 32u));
-        const float2 nx2 = __fadd2_rn(bx2, make_float2(-wx2.x, -wx2.y));
-        const float2 ny2 = __fadd2_rn(by2, make_float2(-wy2.x, -wy2.y));
-        if ((live0 && !(den2.x == den2.x)) || (live1 && !(den2.y == den2.y))) dev_fail(A.status, SSM_E_NUMERIC);
 
-        // neighbour terms (w = 1, d = 1) in ascending column order, X^t from shared memory
+        // neighbour terms (w = 1, d = 1) less deg(i) x_i, in ascending column
+        // order, X^t from shared memory; then the update about x_i
         float cn = 0.f, cd = 0.f;
-        if (live0) {
-          const int rb = __ldg(rowptr + i0), re = __ldg(rowptr + i0 + 1);
+#pragma unroll
+        for (int q = 0; q < NPL; ++q) {
+          const int i = i0 + q;
+          const int j = q >> 1;
+          const bool hi = (q & 1) != 0;
+          if (i >= n) continue;
+          const float dq = hi ? den2[j].y : den2[j].x;
+          if (!(dq == dq)) dev_fail(A.status, SSM_E_NUMERIC);
+          const float2 x = xs[q];
+          const int rb = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
           float sx = 0.f, sy = 0.f;
           for (int t = rb; t < re; ++t) {
             const unsigned c = (unsigned)__ldg(colidx + t);
@@ -213,42 +247,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_batch(BatchArgs A, int32_t
               dev_fail(A.status, SSM_E_GRAPH);
               continue;
             }
-            const float2 q = Xc[c];
-            const float dx = x0.x - q.x, dy = x0.y - q.y;
-            const float rr = fmaf(dx, dx, dy * dy);
-            const float inv = rr > 0.f ? b_rsqrt(rr) : 0.f;
-            sx += fmaf(dx, inv, q.x);
-            sy += fmaf(dy, inv, q.y);
+            const float2 qv = Xc[c];
+            const float ex = qv.x - x.x, ey = qv.y - x.y;
+            const float rr = fmaf(ex, ex, ey * ey);
+            const float f = rr > 0.f ? 1.f - b_rsqrt(rr) : 0.f;
+            sx = fmaf(ex, f, sx);
+            sy = fmaf(ey, f, sy);
           }
-          const float dn = den2.x + (float)(re - rb);
-          const float xn = dn > 0.f ? (nx2.x + sx) / dn : x0.x, yn = dn > 0.f ? (ny2.x + sy) / dn : x0.y;
-          Xn[i0] = make_float2(xn, yn);
-          const float ex = xn - x0.x, ey = yn - x0.y;
-          cn = fmaf(ex, ex, ey * ey);
-          cd = fmaf(x0.x, x0.x, x0.y * x0.y);
-        }
-        if (live1) {
-          const int rb = __ldg(rowptr + i0 + 1), re = __ldg(rowptr + i0 + 2);
-          float sx = 0.f, sy = 0.f;
-          for (int t = rb; t < re; ++t) {
-            const unsigned c = (unsigned)__ldg(colidx + t);
-            if (c >= (unsigned)n) {
-              dev_fail(A.status, SSM_E_GRAPH);
-              continue;
-            }
-            const float2 q = Xc[c];
-            const float dx = x1.x - q.x, dy = x1.y - q.y;
-            const float rr = fmaf(dx, dx, dy * dy);
-            const float inv = rr > 0.f ? b_rsqrt(rr) : 0.f;
-            sx += fmaf(dx, inv, q.x);
-            sy += fmaf(dy, inv, q.y);
-          }
-          const float dn = den2.y + (float)(re - rb);
-          const float xn = dn > 0.f ? (nx2.y + sx) / dn : x1.x, yn = dn > 0.f ? (ny2.y + sy) / dn : x1.y;
-          Xn[i0 + 1] = make_float2(xn, yn);
-          const float ex = xn - x1.x, ey = yn - x1.y;
+          const float dn = dq + (float)(re - rb);
+          const float nx = hi ? ax2[j].y : ax2[j].x, ny = hi ? ay2[j].y : ay2[j].x;
+          const float ex = dn > 0.f ? (nx + sx) / dn : 0.f, ey = dn > 0.f ? (ny + sy) / dn : 0.f;
+          Xn[i] = make_float2(x.x + ex, x.y + ey);
           cn = fmaf(ex, ex, fmaf(ey, ey, cn));
-          cd = fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, cd));
+          cd = fmaf(x.x, x.x, fmaf(x.y, x.y, cd));
         }
         if (last) {
           double tn = (double)cn, td = (double)cd;
@@ -307,20 +318,24 @@ static size_t carve_batch(Carver &c, BatchWs &w, int32_t G, int64_t words, int64
 static void batch_sizes(int32_t G, const ssm_batch_graph *g, int64_t &words, int64_t &stab_len, int64_t &nodes) {
   words = stab_len = nodes = 0;
   for (int32_t i = 0; i < G; ++i) {
-    words += (int64_t)((g[i].n + 63) / 64) * g[i].k * 32;
+    words += batch_words(g[i].n, g[i].k);
     stab_len += 2 * (int64_t)g[i].cnt_len + g[i].k;
     nodes += g[i].n;
   }
 }
 
 typedef void (*BatchKernel)(BatchArgs, int32_t, int32_t);
-static BatchKernel batch_kernel(int threads, bool tab_smem = false) {
+template <int NPL>
+static BatchKernel batch_kernel_npl(int threads, bool tab_smem) {
   switch (threads) {
-    case 128: return tab_smem ? k_sweep_batch<128, true> : k_sweep_batch<128, false>;
-    case 256: return tab_smem ? k_sweep_batch<256, true> : k_sweep_batch<256, false>;
-    case 512: return tab_smem ? k_sweep_batch<512, true> : k_sweep_batch<512, false>;
+    case 128: return tab_smem ? k_sweep_batch<128, true, NPL> : k_sweep_batch<128, false, NPL>;
+    case 256: return tab_smem ? k_sweep_batch<256, true, NPL> : k_sweep_batch<256, false, NPL>;
+    case 512: return tab_smem ? k_sweep_batch<512, true, NPL> : k_sweep_batch<512, false, NPL>;
     default: return nullptr;
   }
+}
+static BatchKernel batch_kernel(int threads, bool tab_smem = false, int npl = 2) {
+  return npl == 4 ? batch_kernel_npl<4>(threads, tab_smem) : npl == 2 ? batch_kernel_npl<2>(threads, tab_smem) : nullptr;
 }
 
 // the s tables go to shared memory when the largest one fits beside the positions
@@ -334,8 +349,8 @@ static int batch_table_floats(int nmax, int kmax, int smax) {
 
 // grid of the persistent kernel for a block size (attribute and occupancy
 // queries stay outside stream capture)
-static int batch_grid(int threads, int nmax, int kmax, int smax, int G, int *blocks) {
-  BatchKernel kern = batch_kernel(threads, smax > 0);
+static int batch_grid(int threads, int npl, int nmax, int kmax, int smax, int G, int *blocks) {
+  BatchKernel kern = batch_kernel(threads, smax > 0, npl);
   const size_t smem = batch_smem(nmax, kmax, smax);
   SSM_TRY_CUDA(allow_dynamic_smem((const void *)kern));
   int per_sm = 0;
@@ -345,10 +360,10 @@ static int batch_grid(int threads, int nmax, int kmax, int smax, int G, int *blo
   return SSM_OK;
 }
 
-static int launch_batch_sweep(const BatchArgs &A, int threads, int blocks, int nmax, int kmax, int smax,
+static int launch_batch_sweep(const BatchArgs &A, int threads, int npl, int blocks, int nmax, int kmax, int smax,
                               cudaStream_t s) {
   SSM_TRY_CUDA(cudaMemsetAsync(A.ctr, 0, sizeof(unsigned), s));
-  note_launch(), batch_kernel(threads, smax > 0)<<<blocks, threads, batch_smem(nmax, kmax, smax), s>>>(A, nmax, kmax);
+  note_launch(), batch_kernel(threads, smax > 0, npl)<<<blocks, threads, batch_smem(nmax, kmax, smax), s>>>(A, nmax, kmax);
   SSM_TRY_CUDA(cudaGetLastError());
   return SSM_OK;
 }
@@ -366,14 +381,16 @@ SSM_API size_t ssm_batch_iterate_workspace(int32_t G, const ssm_batch_graph *gra
 
 SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const int32_t *rowptr, const int32_t *colidx,
                               const int32_t *pivots, const uint16_t *dip, const int32_t *cnt_off, const uint32_t *cnt,
-                              float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t *threads_used,
-                              int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
+                              float *pos, int32_t iters, double *rel_change, int32_t threads, int32_t nodes_per_lane,
+                              int32_t *shape_used, int32_t *status, void *ws, size_t ws_bytes, cudaStream_t s) {
   using namespace ssm;
   if (G < 1 || !graphs || !rowptr || !colidx || !pivots || !dip || !cnt_off || !cnt || !pos || !rel_change ||
       !status || !ws)
     return fail(SSM_E_ARG, "ssm_batch_iterate: null pointer or G < 1");
   if (iters < 1) return fail(SSM_E_ARG, "ssm_batch_iterate: iters must be >= 1");
   if (threads != 0 && !batch_kernel(threads)) return fail(SSM_E_ARG, "ssm_batch_iterate: threads must be 0, 128, 256 or 512");
+  if (nodes_per_lane != 0 && nodes_per_lane != 2 && nodes_per_lane != 4)
+    return fail(SSM_E_ARG, "ssm_batch_iterate: nodes_per_lane must be 0, 2 or 4");
   int nmax = 1, kmax = 1;
   std::vector<BatchDev> dv((size_t)G);
   int64_t words = 0, stab_len = 0, tmax_len = 0;
@@ -385,11 +402,11 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     if (stab_len + 2 * (int64_t)g.cnt_len + g.k >= ((int64_t)1 << 31))
       return fail(SSM_E_ARG, "ssm_batch_iterate: count tables of the batch too long");
     BatchDev &d = dv[(size_t)i];
-    d.n = g.n; d.k = g.k; d.cnt_len = g.cnt_len; d.pad = 0;
+    d.n = g.n; d.k = g.k; d.cnt_len = g.cnt_len; d.ppt = 32;
     d.node_off = g.node_off; d.row_off = g.row_off; d.col_off = g.col_off; d.piv_off = g.piv_off;
     d.dip_off = g.dip_off; d.cnt_off_off = g.cnt_off_off; d.cnt_base = g.cnt_base;
     d.dtile_off = words; d.stab_off = stab_len;
-    words += (int64_t)((g.n + 63) / 64) * g.k * 32;
+    words += batch_words(g.n, g.k);
     stab_len += 2 * (int64_t)g.cnt_len + g.k;
     nmax = std::max(nmax, g.n);
     kmax = std::max(kmax, g.k);
@@ -404,7 +421,7 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
   std::vector<int32_t> order;
   order.reserve((size_t)G);
   struct Cls {
-    int first, count, nmax, kmax, smax, threads, blocks;
+    int first, count, nmax, kmax, smax, threads, npl, blocks;
     int64_t work;
   } cls[kClasses];
   for (int ci = 0; ci < kClasses; ++ci) {
@@ -427,7 +444,30 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     });
     C.smax = C.count ? batch_table_floats(C.nmax, C.kmax, (int)std::min<int64_t>(tl, 1 << 24)) : 0;
     C.threads = threads;
+    C.npl = nodes_per_lane != 0 ? nodes_per_lane : (threads != 0 ? 2 : 0);
     C.blocks = 0;
+  }
+  // a tuned shape is kept per class fingerprint (largest n, largest k, table
+  // floats, graph count, sum of n k) for the life of the process
+  using ShapeKey = std::tuple<int, int, int, int, int, int64_t, int>;
+  static std::map<ShapeKey, std::pair<int, int>> shape_cache;
+  static std::mutex shape_mu;
+  auto key_of = [&](int ci) {
+    const Cls &C = cls[ci];
+    return ShapeKey(ci, C.nmax, C.kmax, C.smax, C.count, C.work, nodes_per_lane);
+  };
+  bool tune = false;
+  for (int ci = 0; ci < kClasses; ++ci) {
+    Cls &C = cls[ci];
+    if (!C.count || (C.threads != 0 && C.npl != 0)) continue;
+    std::lock_guard<std::mutex> lk(shape_mu);
+    const auto it = shape_cache.find(key_of(ci));
+    if (it != shape_cache.end()) {
+      C.threads = it->second.first;
+      C.npl = it->second.second;
+    } else {
+      tune = true;
+    }
   }
   int64_t nodes = 0;
   for (int32_t i = 0; i < G; ++i) nodes = std::max<int64_t>(nodes, graphs[i].node_off + graphs[i].n);
@@ -450,55 +490,95 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     return X;
   };
 
-  note_launch(), k_batch_setup<<<G, 256, 0, s>>>(A);
-  SSM_TRY_CUDA(cudaGetLastError());
+  // each class's graphs carry its tile shape (pairs per tile) in their descriptors
+  auto set_class_ppt = [&](int ci, int npl) {
+    for (int q = cls[ci].first; q < cls[ci].first + cls[ci].count; ++q) dv[(size_t)order[(size_t)q]].ppt = 16 * npl;
+  };
+  auto upload_desc = [&]() -> int {
+    SSM_TRY_CUDA(cudaMemcpyAsync(w.desc, dv.data(), dv.size() * sizeof(BatchDev), cudaMemcpyHostToDevice, s));
+    return SSM_OK;
+  };
+  // the tiled copies of one class (or of every graph) for the shapes in dv
+  auto setup = [&](int ci, int do_stab) -> int {
+    if (ci < 0) {
+      note_launch(), k_batch_setup<<<G, 256, 0, s>>>(A, 0, do_stab);
+    } else {
+      note_launch(), k_batch_setup<<<cls[ci].count, 256, 0, s>>>(class_args(A, ci), 1, do_stab);
+    }
+    SSM_TRY_CUDA(cudaGetLastError());
+    return SSM_OK;
+  };
 
-  if (threads == 0) {
-    // tune the block size of every class on this batch: a few iterations
-    // per candidate on a scratch copy of the positions
-    SSM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (tune) {
+    // tune block size and nodes per lane of every class not fixed or cached:
+    // a few iterations per candidate on a scratch copy of the positions
     BatchArgs T = A;
     T.pos = w.scratch;
     T.iters = std::min(iters, 4);
     cudaEvent_t e0, e1;
     SSM_TRY_CUDA(cudaEventCreate(&e0));
     SSM_TRY_CUDA(cudaEventCreate(&e1));
-    for (int ci = 0; ci < kClasses; ++ci) {
+    int rc = SSM_OK;
+    bool stab_done = false;
+    for (int ci = 0; ci < kClasses && rc == SSM_OK; ++ci) {
       Cls &C = cls[ci];
-      if (!C.count) continue;
+      if (!C.count || (C.threads != 0 && C.npl != 0)) continue;
       const BatchArgs TC = class_args(T, ci);
       float best = 0.f;
-      C.threads = 0;
-      for (int cand : {128, 256, 512}) {
-        for (int rep = 0; rep < 2; ++rep) {  // the first run of a candidate warms it up
-          SSM_TRY_CUDA(cudaMemcpyAsync(w.scratch, pos, (size_t)nodes * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-          int blocks = 0;
-          int rc = batch_grid(cand, C.nmax, C.kmax, C.smax, C.count, &blocks);
-          if (rc) return rc;
-          SSM_TRY_CUDA(cudaEventRecord(e0, s));
-          rc = launch_batch_sweep(TC, cand, blocks, C.nmax, C.kmax, C.smax, s);
-          if (rc) return rc;
-          SSM_TRY_CUDA(cudaEventRecord(e1, s));
-          SSM_TRY_CUDA(cudaEventSynchronize(e1));
+      int bt = 0, bn = 0;
+      for (int npl : {2, 4}) {
+        if (C.npl != 0 && npl != C.npl) continue;
+        set_class_ppt(ci, npl);
+        if ((rc = upload_desc()) || (rc = setup(stab_done ? ci : -1, stab_done ? 0 : 1))) break;
+        stab_done = true;
+        for (int cand : {128, 256, 512}) {
+          if (C.threads != 0 && cand != C.threads) continue;
+          for (int rep = 0; rep < 2 && rc == SSM_OK; ++rep) {  // the first run of a candidate warms it up
+            SSM_TRY_CUDA(cudaMemcpyAsync(w.scratch, pos, (size_t)nodes * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+            int blocks = 0;
+            if ((rc = batch_grid(cand, npl, C.nmax, C.kmax, C.smax, C.count, &blocks))) break;
+            SSM_TRY_CUDA(cudaEventRecord(e0, s));
+            if ((rc = launch_batch_sweep(TC, cand, npl, blocks, C.nmax, C.kmax, C.smax, s))) break;
+            SSM_TRY_CUDA(cudaEventRecord(e1, s));
+            SSM_TRY_CUDA(cudaEventSynchronize(e1));
+          }
+          if (rc) break;
+          float ms = 0.f;
+          SSM_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (bt == 0 || ms < best) {
+            best = ms;
+            bt = cand;
+            bn = npl;
+          }
         }
-        float ms = 0.f;
-        SSM_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (C.threads == 0 || ms < best) {
-          best = ms;
-          C.threads = cand;
-        }
+        if (rc) break;
       }
+      if (rc) break;
+      C.threads = bt;
+      C.npl = bn;
+      std::lock_guard<std::mutex> lk(shape_mu);
+      shape_cache[key_of(ci)] = std::make_pair(bt, bn);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc) return rc;
   }
+  // the chosen shapes: descriptors, s tables and tiled copies of every graph
+  for (int ci = 0; ci < kClasses; ++ci)
+    if (cls[ci].count) set_class_ppt(ci, cls[ci].npl);
+  if (int rc = upload_desc()) return rc;
+  if (int rc = setup(-1, 1)) return rc;
   int heavy = 0;
   for (int ci = 0; ci < kClasses; ++ci)
     if (cls[ci].work > cls[heavy].work) heavy = ci;
-  if (threads_used) *threads_used = cls[heavy].threads;
+  if (shape_used) {
+    shape_used[0] = cls[heavy].threads;
+    shape_used[1] = cls[heavy].npl;
+  }
   for (int ci = 0; ci < kClasses; ++ci) {
     if (!cls[ci].count) continue;
-    const int rc = batch_grid(cls[ci].threads, cls[ci].nmax, cls[ci].kmax, cls[ci].smax, cls[ci].count, &cls[ci].blocks);
+    const int rc = batch_grid(cls[ci].threads, cls[ci].npl, cls[ci].nmax, cls[ci].kmax, cls[ci].smax, cls[ci].count,
+                              &cls[ci].blocks);
     if (rc) return rc;
   }
 
@@ -531,8 +611,8 @@ SSM_API int ssm_batch_iterate(int32_t G, const ssm_batch_graph *graphs, const in
     for (int ci = 0; ci < kClasses && rc == SSM_OK && e == cudaSuccess; ++ci) {
       if (!cls[ci].count) continue;
       if ((e = cudaStreamWaitEvent(cs[ci + 1], ev[kClasses], 0)) != cudaSuccess) break;
-      rc = launch_batch_sweep(class_args(A, ci), cls[ci].threads, cls[ci].blocks, cls[ci].nmax, cls[ci].kmax,
-                              cls[ci].smax, cs[ci + 1]);
+      rc = launch_batch_sweep(class_args(A, ci), cls[ci].threads, cls[ci].npl, cls[ci].blocks, cls[ci].nmax,
+                              cls[ci].kmax, cls[ci].smax, cs[ci + 1]);
       if (rc == SSM_OK) e = cudaEventRecord(ev[ci], cs[ci + 1]);
       if (rc == SSM_OK && e == cudaSuccess) e = cudaStreamWaitEvent(cs[0], ev[ci], 0);
     }

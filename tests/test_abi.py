@@ -64,22 +64,23 @@ def _batch_desc(specs):
     return desc
 
 
-@pytest.mark.parametrize("specs,threads,what", [
-    ([(12289, 10, 20)], 0, "n = 12289"),     # above the shared-memory positions limit
-    ([(100, 0, 20)], 0, "k = 0"),
-    ([(100, 101, 200)], 0, "k = 101"),       # more pivots than nodes
-    ([(100, 10, 5)], 0, "cnt_len < k"),
-    ([(100, 10, 20)], 192, "threads"),       # not a tuned block size
+@pytest.mark.parametrize("specs,threads,npl,what", [
+    ([(12289, 10, 20)], 0, 0, "n = 12289"),     # above the shared-memory positions limit
+    ([(100, 0, 20)], 0, 0, "k = 0"),
+    ([(100, 101, 200)], 0, 0, "k = 101"),       # more pivots than nodes
+    ([(100, 10, 5)], 0, 0, "cnt_len < k"),
+    ([(100, 10, 20)], 192, 0, "threads"),       # not a tuned block size
+    ([(100, 10, 20)], 256, 3, "nodes per lane"),  # not a tile shape
 ])
-def test_batch_arguments_rejected_on_host(specs, threads, what):
+def test_batch_arguments_rejected_on_host(specs, threads, npl, what):
     """ssm_batch_iterate checks every descriptor before touching the device
     (the dummy device pointers below are never dereferenced)."""
     L = ssm.lib()
     desc = _batch_desc(specs)
     dp = desc.ctypes.data_as(ctypes.c_void_p)
     fake = ctypes.c_void_p(256)
-    rc = L.ssm_batch_iterate(len(specs), dp, fake, fake, fake, fake, fake, fake, fake, 1, fake, threads, None, fake,
-                             fake, 1 << 20, None)
+    rc = L.ssm_batch_iterate(len(specs), dp, fake, fake, fake, fake, fake, fake, fake, 1, fake, threads, npl, None,
+                             fake, fake, 1 << 20, None)
     assert rc == -1
     assert len(L.ssm_last_error()) > 0
 
@@ -90,8 +91,8 @@ def test_batch_workspace_grows_with_the_batch():
     two = _batch_desc([(1000, 50, 1100), (4000, 100, 4200)])
     w1 = L.ssm_batch_iterate_workspace(1, one.ctypes.data_as(ctypes.c_void_p))
     w2 = L.ssm_batch_iterate_workspace(2, two.ctypes.data_as(ctypes.c_void_p))
-    # the tiled d_ip copy alone: 2 k n (rounded up to 64-node tiles) per graph
-    assert w1 >= 2 * 50 * 1024 and w2 >= w1 + 2 * 100 * 4032
+    # the tiled d_ip copy alone: 2 k n (rounded up to 128-node tiles, room for either tile shape) per graph
+    assert w1 >= 2 * 50 * 1024 and w2 >= w1 + 2 * 100 * 4096
 
 
 def test_gram_arguments_rejected_on_host():

@@ -47,7 +47,7 @@ def test_batch_step_matches_oracle(batch):
     for t in range(4):
         items = [(g, P, torch.from_numpy(x.astype(np.float32)).to(DEV)) for x, (_, g, P) in zip(xs, batch)]
         rel, used = ssm.ssm_batch_iterate(items, 1)
-        assert used in (128, 256, 512)
+        assert used[0] in (128, 256, 512) and used[1] in (2, 4)
         rel = rel.cpu().numpy()
         nxt = []
         for i, ((prep, _, _), (_, _, pos)) in enumerate(zip(batch, items)):
@@ -60,16 +60,37 @@ def test_batch_step_matches_oracle(batch):
         xs = nxt
 
 
-def test_batch_block_sizes_agree_bit_for_bit(batch):
-    res = []
-    for threads in (128, 256, 512):
-        items = [(g, P, torch.from_numpy(prep.pos0.astype(np.float32)).to(DEV)) for prep, g, P in batch]
-        rel, used = ssm.ssm_batch_iterate(items, 7, threads=threads)
-        assert used == threads
-        res.append(([p.cpu().numpy() for _, _, p in items], rel.cpu().numpy()))
-    for pos, rel in res[1:]:
-        assert all(np.array_equal(a, b) for a, b in zip(pos, res[0][0]))
-        assert np.array_equal(rel, res[0][1])
+def test_batch_shapes_agree_bit_for_bit(batch):
+    """Every block size and both tile shapes (64-node tiles with two nodes per
+    lane, 128-node tiles with four) give the same positions bit for bit: a
+    node's terms are added in the same order whatever the shape; the relative
+    change adds a lane's nodes in FP32 before the FP64 tile sums, so it agrees
+    bit for bit within a tile shape and to FP32 rounding across them."""
+    res = {}
+    for npl in (2, 4):
+        for threads in (128, 256, 512):
+            items = [(g, P, torch.from_numpy(prep.pos0.astype(np.float32)).to(DEV)) for prep, g, P in batch]
+            rel, used = ssm.ssm_batch_iterate(items, 7, threads=threads, nodes_per_lane=npl)
+            assert used == (threads, npl)
+            res[(threads, npl)] = ([p.cpu().numpy() for _, _, p in items], rel.cpu().numpy())
+    ref_pos, ref_rel = res[(128, 2)]
+    for (threads, npl), (pos, rel) in res.items():
+        assert all(np.array_equal(a, b) for a, b in zip(pos, ref_pos)), (threads, npl)
+        if npl == 2:
+            assert np.array_equal(rel, ref_rel)
+        else:
+            np.testing.assert_allclose(rel, ref_rel, rtol=1e-6)
+            assert np.array_equal(rel, res[(128, 4)][1])
+
+
+def test_batch_tuned_shape_is_kept(batch):
+    """The first call with threads = nodes_per_lane = 0 tunes; a second call on
+    a batch of the same shape takes the kept choice."""
+    items = [(g, P, torch.from_numpy(prep.pos0.astype(np.float32)).to(DEV)) for prep, g, P in batch]
+    _, first = ssm.ssm_batch_iterate(items, 3)
+    items = [(g, P, torch.from_numpy(prep.pos0.astype(np.float32)).to(DEV)) for prep, g, P in batch]
+    _, again = ssm.ssm_batch_iterate(items, 3)
+    assert first == again
 
 
 def test_batch_many_iterations_finite_and_converging(batch):
