@@ -319,20 +319,30 @@ __global__ void __launch_bounds__(256) k_pull_distances(PullArgs A) {
     reached[w][v] = any;
   }
   __syncthreads();
-  // warp: one source at a time, 32 consecutive nodes per store
+  // warp: one source at a time, the tile's 64 nodes in one store per lane (two
+  // consecutive distances in a 32-bit word when the rows are 4-byte aligned)
+  static_assert(kPullTile == 64, "two nodes per lane");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const bool pairs = (n % 2 == 0) && (reinterpret_cast<uintptr_t>(A.dist) & 3u) == 0;
   for (int sidx = warp; sidx < A.nsrc; sidx += nwarp) {
     const int w = sidx >> 5;
     const unsigned bit = 1u << (sidx & 31);
     uint16_t *row = A.dist + (size_t)(A.base + sidx) * n;
+    unsigned dd[2];
 #pragma unroll
-    for (int h = 0; h < kPullTile / 32; ++h) {
-      const int v = 32 * h + lane;
-      if (v0 + v >= n) continue;
+    for (int h = 0; h < 2; ++h) {
+      const int v = 2 * lane + h;
       unsigned d = 0;
 #pragma unroll
       for (int j = 0; j < kPullDistBits; ++j) d |= ((planes[w][j][v] & bit) ? 1u : 0u) << j;
-      row[v0 + v] = (reached[w][v] & bit) ? (uint16_t)d : (uint16_t)0xFFFFu;
+      dd[h] = (reached[w][v] & bit) ? d : 0xFFFFu;
+    }
+    const int v = v0 + 2 * lane;
+    if (pairs && v + 1 < n) {
+      *reinterpret_cast<unsigned *>(row + v) = dd[0] | (dd[1] << 16);
+    } else {
+      if (v < n) row[v] = (uint16_t)dd[0];
+      if (v + 1 < n) row[v + 1] = (uint16_t)dd[1];
     }
   }
 }

@@ -579,14 +579,19 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
 }
 
 // ------------------------------------------------------------- projection
-// two-float accumulation: (hi, lo) += a * (bh + bl), a exact in FP32
-__device__ __forceinline__ void ff_madd(float &hi, float &lo, float a, float bh, float bl) {
-  const float p = a * bh;
-  const float pe = fmaf(a, bh, -p);  // exact rounding error of the product
-  const float s = hi + p;
-  const float bp = s - hi;
-  const float e = (hi - (s - bp)) + (p - bp);  // exact rounding error of the sum
-  lo += e + fmaf(a, bl, pe);
+// two-float accumulation for the (x, y) pair at once, in packed FP32x2
+// arithmetic with every operation rounded on its own (no contraction):
+// (hi, lo) += a * (bh + bl), a exact in FP32; p + pe = a bh exactly, s + e =
+// hi + p exactly
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void ff_madd2(float2 &hi, float2 &lo, float a, float2 bh, float2 bl) {
+  const float2 a2 = make_float2(a, a);
+  const float2 p = __fmul2_rn(a2, bh);
+  const float2 pe = __ffma2_rn(a2, bh, neg2(p));
+  const float2 s = __fadd2_rn(hi, p);
+  const float2 bp = __fadd2_rn(s, neg2(hi));
+  const float2 e = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bp)))), __fadd2_rn(p, neg2(bp)));
+  lo = __fadd2_rn(lo, __fadd2_rn(e, __ffma2_rn(a2, bl, pe)));
   hi = s;
 }
 
@@ -596,17 +601,17 @@ __global__ void __launch_bounds__(256) k_project(int32_t n, int32_t k, const uin
                                                  const double *__restrict__ vv, const EigOut *__restrict__ eo,
                                                  const unsigned *__restrict__ dmax, void *__restrict__ pos,
                                                  int precision) {
-  extern __shared__ __align__(16) float4 sv[];  // per pivot: v0 hi, v0 lo, v1 hi, v1 lo
+  extern __shared__ __align__(16) float4 sv[];  // per pivot: (v0 hi, v1 hi), (v0 lo, v1 lo)
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     const double v0 = vv[a], v1 = vv[k + a];
     const float h0 = (float)v0, h1 = (float)v1;
-    sv[a] = make_float4(h0, (float)(v0 - (double)h0), h1, (float)(v1 - (double)h1));
+    sv[a] = make_float4(h0, h1, (float)(v0 - (double)h0), (float)(v1 - (double)h1));
   }
   __syncthreads();
   const double sig0 = eo->sigma[0], sig1 = eo->sigma[1], kap0 = eo->kappa[0], kap1 = eo->kappa[1];
   const bool BIG = (unsigned long long)(*dmax) * (*dmax) >= (1ull << 24);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+    float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);  // (x, y) two-float sums
     unsigned long long rs = 0;
     const uint16_t *col = dip + i;
     // eight pivots' distances in flight per thread, then added in pivot order
@@ -620,22 +625,18 @@ __global__ void __launch_bounds__(256) k_project(int32_t n, int32_t k, const uin
         const unsigned dd = dq[q] * dq[q];
         rs += dd;
         const float4 v = sv[a0 + q];
+        const float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
         if (!BIG) {
-          const float df = (float)dd;  // exact below 2^24
-          ff_madd(xh, xl, df, v.x, v.y);
-          ff_madd(yh, yl, df, v.z, v.w);
+          ff_madd2(hi, lo, (float)dd, vh, vl);  // dd exact below 2^24
         } else {
-          const float dh = (float)(dd & 0xFFFFF000u), dl = (float)(dd & 0xFFFu);  // both exact
-          ff_madd(xh, xl, dh, v.x, v.y);
-          ff_madd(xh, xl, dl, v.x, v.y);
-          ff_madd(yh, yl, dh, v.z, v.w);
-          ff_madd(yh, yl, dl, v.z, v.w);
+          ff_madd2(hi, lo, (float)(dd & 0xFFFFF000u), vh, vl);  // both parts exact
+          ff_madd2(hi, lo, (float)(dd & 0xFFFu), vh, vl);
         }
       }
     }
     const double rbar = (double)rs / (double)k;
-    const double x = -0.5 * (((double)xh + (double)xl) - rbar * sig0 - kap0);
-    const double y = -0.5 * (((double)yh + (double)yl) - rbar * sig1 - kap1);
+    const double x = -0.5 * (((double)hi.x + (double)lo.x) - rbar * sig0 - kap0);
+    const double y = -0.5 * (((double)hi.y + (double)lo.y) - rbar * sig1 - kap1);
     if (precision == 64) reinterpret_cast<double2 *>(pos)[i] = make_double2(x, y);
     else reinterpret_cast<float2 *>(pos)[i] = make_float2((float)x, (float)y);
   }

@@ -621,6 +621,35 @@ __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__
   constexpr int64_t P = kTileNodes / 2;
   const int64_t npairs = ((int64_t)(n + kTileNodes - 1) / kTileNodes) * P;
   const unsigned top = row > 0 ? (unsigned)row - 1u : 0u;
+  auto enc = [&](int a, unsigned lo, unsigned hi) -> unsigned {
+    if (row > 0) {
+      if (lo > top || hi > top) {
+        dev_fail(status, SSM_E_ARG);
+        lo = min(lo, top);
+        hi = min(hi, top);
+      }
+      lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
+      hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
+    }
+    return lo | (hi << 16);
+  };
+  if (pair_loads == 2) {
+    // n a multiple of 8, dip 16-byte aligned: four pairs (one 16-byte load,
+    // one 16-byte store of four consecutive words of a tile) per thread
+    const int64_t nquads = npairs / 4;
+    for (int a = blockIdx.y; a < k; a += gridDim.y) {
+      const uint4 *drow = reinterpret_cast<const uint4 *>(dip + (size_t)a * n);
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nquads; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = 4 * g;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (2 * p + 7 < n) v = __ldg(drow + g);  // else past the last node: zeros (n % 8 == 0: all or nothing)
+        const uint4 out = make_uint4(enc(a, v.x & 0xFFFFu, v.x >> 16), enc(a, v.y & 0xFFFFu, v.y >> 16),
+                                     enc(a, v.z & 0xFFFFu, v.z >> 16), enc(a, v.w & 0xFFFFu, v.w >> 16));
+        *reinterpret_cast<uint4 *>(dtile + ((p / P) * k + a) * P + (p % P)) = out;
+      }
+    }
+    return;
+  }
   for (int a = blockIdx.y; a < k; a += gridDim.y) {
     const uint16_t *drow = dip + (size_t)a * n;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * blockDim.x) {
@@ -634,16 +663,7 @@ __global__ void k_tile_dip(int32_t n, int32_t k, int32_t row, const uint16_t *__
         if (i < n) lo = (unsigned)__ldg(drow + i);
         if (i + 1 < n) hi = (unsigned)__ldg(drow + i + 1);
       }
-      if (row > 0) {
-        if (lo > top || hi > top) {
-          dev_fail(status, SSM_E_ARG);
-          lo = min(lo, top);
-          hi = min(hi, top);
-        }
-        lo = kTabEntryBytes * ((unsigned)a * (unsigned)row + lo);
-        hi = kTabEntryBytes * ((unsigned)a * (unsigned)row + hi);
-      }
-      dtile[((p / P) * k + a) * P + (p % P)] = lo | (hi << 16);
+      dtile[((p / P) * k + a) * P + (p % P)] = enc(a, lo, hi);
     }
   }
 }
@@ -962,7 +982,9 @@ SSM_API int ssm_iterate(int32_t n, int64_t m, const int32_t *rowptr, const int32
       const int64_t npairs = ((int64_t)n + kTileNodes - 1) / kTileNodes * (kTileNodes / 2);
       const int gy = std::min(k, 16);
       const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((npairs + 255) / 256, (int64_t)sms * 8 / gy + 1));
-      const int32_t pair_loads = (n % 2 == 0 && (reinterpret_cast<uintptr_t>(dip) & 3u) == 0) ? 1 : 0;
+      const int32_t pair_loads = (n % 8 == 0 && (reinterpret_cast<uintptr_t>(dip) & 15u) == 0)  ? 2
+                                 : (n % 2 == 0 && (reinterpret_cast<uintptr_t>(dip) & 3u) == 0) ? 1
+                                                                                                 : 0;
       note_launch(), k_tile_dip<<<dim3(gx, gy), 256, 0, s>>>(n, k, full ? (int32_t)dmax + 1 : 0, dip, w.dtile, status,
                                                            pair_loads);
     }
