@@ -13,7 +13,12 @@
 // accumulator is read out after at most kTcFlush chunks of 64 nodes (16384
 // nodes), so it holds an integer below 961 * 16384 < 2^24 -- exact in FP32.
 // D = ceil(bits(max d^2) / 5) comes from the largest distance on the device
-// (2 digits for small-world graphs, 4 for d <= 1023).
+// (2 digits for small-world graphs, 4 for d <= 1023).  When every squared
+// distance is below 2^7 (d <= 11) one 7-bit digit does instead: FP16 holds it
+// exactly, a product is at most 127^2, and an accumulator read out every
+// kTcFlush7 chunks (1024 nodes) stays below 2^24; those read-outs add into
+// 64-bit sums in shared memory (one per tile entry), and only the slice's
+// totals go to G.
 //
 // Work units are (output tile, digit block, chunk of 64 nodes): a 128 x 128
 // tile of pivots a (tile ta) by pivots b (tile tb >= ta, by symmetry), a
@@ -47,6 +52,8 @@ namespace ssm {
 constexpr int kTcThreads = 512;        // 16 warps, 8 pivot rows of each tile per warp
 constexpr int kTcChunk = 64;           // nodes per plane row (128 bytes of FP16, 4 MMAs of K = 16)
 constexpr int kTcFlush = 256;          // chunks per accumulator read-out (16384 nodes: below 2^24)
+constexpr int kTcFlush7 = 16;          // the same with one 7-bit digit (1024 nodes: 127^2 1024 < 2^24)
+constexpr unsigned kTcAccBytes = 128u * 128u * 8u;  // 64-bit sums of one tile (single-digit mode)
 constexpr int kTcDigBits = 5;          // digit width
 constexpr int kTcDigBlock = 2;         // digits per A block and per B block
 constexpr unsigned kTcPlaneBytes = 128u * kTcChunk * 2u;              // 128 pivots x 64 nodes, FP16
@@ -87,10 +94,12 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, unsigned phase) {
 
 // FP16 pair of digit p (bits 5p .. 5p + 4) of two squared distances s0, s1
 // (exact: (1024 + v) - 1024).  L packs bits 0..15 of both, M bits 15..30.
-__device__ __forceinline__ uint32_t tc_digits(uint32_t s0, uint32_t s1, uint32_t L, uint32_t M, int p) {
+// With mask 0x007F007F and p = 0 it is the single 7-bit digit.
+__device__ __forceinline__ uint32_t tc_digits(uint32_t s0, uint32_t s1, uint32_t L, uint32_t M, int p,
+                                              uint32_t mask = 0x001F001Fu) {
   uint32_t w;
   if (p < 3)
-    w = (L >> (kTcDigBits * p)) & 0x001F001Fu;
+    w = (L >> (kTcDigBits * p)) & mask;
   else if (p < 6)
     w = (M >> (kTcDigBits * (p - 3))) & 0x001F001Fu;
   else
@@ -177,6 +186,44 @@ __device__ __forceinline__ void tc_flush(const TcUnit &U, uint32_t tmem, int32_t
   }
 }
 
+// single-digit mode: add the one accumulator of the current unit into the
+// 64-bit tile sums acc[col][row] (column-major: a warp's lanes hit
+// consecutive words), each entry owned by one thread
+__device__ __forceinline__ void tc_acc_tmem(uint32_t tmem, int warp, int lane, unsigned long long *acc) {
+  const int q4 = warp & 3, row = 32 * q4 + lane;
+#pragma unroll 1
+  for (int part = 0; part < 4; ++part) {
+    const int cb = 32 * (warp >> 2) + 8 * part;
+    uint32_t v[8];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + (unsigned)cb;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[(cb + e) * 128 + row] += (unsigned long long)__uint_as_float(v[e]);
+  }
+}
+
+// single-digit mode: the tile sums of unit U into G (128-bit atomics), then cleared
+__device__ __forceinline__ void tc_acc_out(const TcUnit &U, int32_t k, int warp, int lane, unsigned long long *acc,
+                                           unsigned long long *__restrict__ Glo,
+                                           unsigned long long *__restrict__ Ghi) {
+  const int q4 = warp & 3, row = 32 * q4 + lane;
+  const int a = 128 * U.ta + row;
+  for (int c = 0; c < 32; ++c) {
+    const int col = 32 * (warp >> 2) + c;
+    const int b = 128 * U.tb + col;
+    unsigned long long &x = acc[col * 128 + row];
+    if (a < k && b < k && a <= b && x != 0ull) {
+      const size_t o = (size_t)a * k + b;
+      const unsigned long long old = atomicAdd(Glo + o, x);
+      if (old + x < old) atomicAdd(Ghi + o, 1ull);
+    }
+    x = 0ull;
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
                                                            int32_t wide, const unsigned *__restrict__ dmax,
                                                            unsigned long long *__restrict__ Glo,
@@ -191,7 +238,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   const unsigned long long s_max = (unsigned long long)dm * dm;
   int bits = 1;
   while (bits < 64 && (s_max >> bits) != 0ull) ++bits;
-  const int D = (bits + kTcDigBits - 1) / kTcDigBits;
+  const bool one = s_max < 128ull;  // single 7-bit digit
+  const int D = one ? 1 : (bits + kTcDigBits - 1) / kTcDigBits;
+  const int flush = one ? kTcFlush7 : kTcFlush;
+  const uint32_t dmask = one ? 0x007F007Fu : 0x001F001Fu;
+  const int ppo = one ? 1 : kTcDigBlock;  // planes per operand in a buffer
+  const unsigned buf_bytes = 2u * (unsigned)ppo * kTcPlaneBytes;
   const int nblk = (D + kTcDigBlock - 1) / kTcDigBlock;
   const int groups = nblk * nblk;
   const int T = (k + 127) / 128;
@@ -203,10 +255,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool wide4 = wide != 0;
 
-  // planes (1024-byte aligned for the swizzle): buffer u at base + u kTcBufBytes,
-  // A digit slot j at + j planes, B digit slot j at + (kTcDigBlock + j) planes
+  // planes (1024-byte aligned for the swizzle): buffer u at base + u buf_bytes,
+  // A digit slot j at + j planes, B digit slot j at + (ppo + j) planes
   const uint32_t base = (tc_smem(tc_raw) + 1023u) & ~1023u;
   unsigned char *const gbase = tc_raw + (base - tc_smem(tc_raw));
+  // single-digit mode: the tile sums after the two (smaller) buffers
+  unsigned long long *const acc = reinterpret_cast<unsigned long long *>(gbase + 2u * buf_bytes);
+  if (one)
+    for (unsigned t = tid; t < 128u * 128u; t += blockDim.x) acc[t] = 0ull;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc_smem(&s_tmem)));
@@ -244,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   int cur_tg = -1;
   TcUnit U{};
   for (int64_t idx = beg; idx < end; ++idx, ++it) {
-    if (cur_tg >= 0 && (tg != cur_tg || since == kTcFlush)) {
+    if (cur_tg >= 0 && (tg != cur_tg || since == flush)) {
       // drain the MMAs, then read the accumulators out
       const bool drained = tc_wait((it - 1) & 1 ? mbar1 : mbar0, (unsigned)((it - 1) >> 1) & 1u);
       if (!__syncthreads_and(drained ? 1 : 0)) {
@@ -252,7 +308,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      tc_flush(U, tmem, k, warp, lane, Glo, Ghi);
+      if (one) {
+        tc_acc_tmem(tmem, warp, lane, acc);
+        if (tg != cur_tg) tc_acc_out(U, k, warp, lane, acc, Glo, Ghi);  // each thread its own entries
+      } else {
+        tc_flush(U, tmem, k, warp, lane, Glo, Ghi);
+      }
       since = 0;
     }
     if (tg != cur_tg) {
@@ -268,7 +329,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
     // buffer u is free again once the MMAs of chunk it - 2 are done (the
     // verdict is made uniform at the barrier below)
     const bool freed = it < 2 || tc_wait(mb, (unsigned)((it - 2) >> 1) & 1u);
-    unsigned char *const buf = gbase + u * kTcBufBytes;
+    unsigned char *const buf = gbase + u * buf_bytes;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const uint32_t da = ca[r];
@@ -281,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
 #pragma unroll
       for (int j = 0; j < kTcDigBlock; ++j)
         if (j < U.npa)
-          *reinterpret_cast<uint32_t *>(buf + j * kTcPlaneBytes + off) = tc_digits(a0, a1, La, Ma, U.pa0 + j);
+          *reinterpret_cast<uint32_t *>(buf + j * kTcPlaneBytes + off) = tc_digits(a0, a1, La, Ma, U.pa0 + j, dmask);
       if (!share) {
         uint32_t b0 = a0, b1 = a1, Lb = La, Mb = Ma;
         if (!diag) {
@@ -294,8 +355,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
 #pragma unroll
         for (int j = 0; j < kTcDigBlock; ++j)
           if (j < U.nqb)
-            *reinterpret_cast<uint32_t *>(buf + (kTcDigBlock + j) * kTcPlaneBytes + off) =
-                tc_digits(b0, b1, Lb, Mb, U.qb0 + j);
+            *reinterpret_cast<uint32_t *>(buf + (ppo + j) * kTcPlaneBytes + off) =
+                tc_digits(b0, b1, Lb, Mb, U.qb0 + j, dmask);
       }
     }
     // the next chunk's distances, in flight while the MMAs are issued
@@ -322,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
       break;
     }
     if (tid == 0) {
-      const uint32_t bs = base + (unsigned)u * kTcBufBytes;
+      const uint32_t bs = base + (unsigned)u * buf_bytes;
       for (int ja = 0; ja < U.npa; ++ja)
         for (int jb = 0; jb < U.nqb; ++jb) {
           const uint32_t acc_col = tmem + 128u * (unsigned)(ja * kTcDigBlock + jb);
@@ -330,7 +391,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
           for (int st = 0; st < kTcChunk / 16; ++st) {
             // K slice st: bytes 32 st of every 128-byte row (the swizzle is applied by the hardware)
             const uint64_t da = tc_desc(bs + (unsigned)ja * kTcPlaneBytes + 32u * st);
-            const uint64_t db = tc_desc(bs + (unsigned)((share ? 0 : kTcDigBlock) + jb) * kTcPlaneBytes + 32u * st);
+            const uint64_t db = tc_desc(bs + (unsigned)((share ? 0 : ppo) + jb) * kTcPlaneBytes + 32u * st);
             const uint32_t acc = (since > 0 || st > 0) ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
@@ -351,7 +412,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   ok = __syncthreads_and(ok ? 1 : 0) != 0;  // uniform: the TMEM reads are warp-collective
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    tc_flush(U, tmem, k, warp, lane, Glo, Ghi);
+    if (one) {
+      tc_acc_tmem(tmem, warp, lane, acc);
+      tc_acc_out(U, k, warp, lane, acc, Glo, Ghi);
+    } else {
+      tc_flush(U, tmem, k, warp, lane, Glo, Ghi);
+    }
   } else {
     if (tid == 0) dev_fail(status, SSM_E_TIMEOUT);
     // let whatever is still in flight finish (bounded) before the TMEM goes
@@ -362,7 +428,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
-size_t gram_tc_smem() { return 2u * kTcBufBytes + 1024u; }
+// the larger of the two layouts: two-digit-block buffers, or single-digit
+// buffers and the tile sums
+size_t gram_tc_smem() { return std::max<size_t>(2u * kTcBufBytes, 2u * 2u * kTcPlaneBytes + kTcAccBytes) + 1024u; }
 
 int launch_gram_tc(int32_t n, int32_t k, const uint16_t *dip, const unsigned *dmax, unsigned long long *Glo,
                    unsigned long long *Ghi, int32_t *status, cudaStream_t s) {

@@ -926,7 +926,7 @@ static int launch_gram(int32_t n, int32_t k, const uint16_t *dip, unsigned *dmax
   SSM_TRY_CUDA(cudaMemsetAsync(Glo, 0, kk * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(Ghi, 0, kk * sizeof(unsigned long long), s));
   SSM_TRY_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned), s));
-  // the largest distance decides how many 4-bit digits the tensor-core Gram needs
+  // the largest distance decides how many digits the tensor-core Gram needs
   const int64_t cnt = (int64_t)k * n;
   note_launch(), k_dmax<<<std::min<int64_t>((cnt + 255) / 256, (int64_t)num_sms() * 8), 256, 0, s>>>(cnt, dip, dmax);
   SSM_TRY_CUDA(cudaGetLastError());

@@ -319,7 +319,9 @@ def _gram_u128(lo, hi):
 
 
 @pytest.mark.parametrize("k,n,dmax,offset", [
-    (200, 20001, 3, 0),        # one 4-bit digit, odd n (two-byte loads), ragged second tile
+    (200, 20001, 3, 0),        # one 7-bit digit, odd n (two-byte loads), ragged second tile
+    (300, 70001, 11, 0),       # one 7-bit digit at its largest (121): 69 read-outs into the tile sums
+    (300, 70000, 12, 0),       # the smallest squared distance that needs 5-bit digits (144)
     (200, 20001, 15, 0),       # two digits
     (130, 33000, 200, 0),      # four digits, even n (four-byte loads), three node ranges
     (130, 33000, 200, 1),      # the same table two bytes off a 4-byte boundary
