@@ -160,33 +160,92 @@ __global__ void __launch_bounds__(256) k_square_f64(int32_t k, const double *__r
   if (r < k && c < k) C[(size_t)r * k + c] = acc;
 }
 
-// block-wide sum of N doubles per thread (result broadcast to all threads).
 // GB300 runs FP64 at 1/64 of the FP32 rate and a warp instruction costs the
-// same with one lane as with 32, so the sum of the warp partials is formed
-// once, by thread 0, and broadcast through shared memory
+// same with one lane as with 32, so what the small k x P steps below cost is
+// their count of FP64 warp instructions.
+
+// N' = N rounded up to a power of two (N <= 32) and its log2
+template <int N>
+struct Halving {
+  static_assert(N >= 1 && N <= 32, "1..32 values");
+  static constexpr int LOG = N <= 1 ? 0 : N <= 2 ? 1 : N <= 4 ? 2 : N <= 8 ? 3 : N <= 16 ? 4 : 5;
+  static constexpr int NP = 1 << LOG;
+};
+
+// warp sum of N doubles per lane by recursive halving: at each of the first
+// log2 N' shuffle steps (offsets 16, 8, ...) a lane keeps one half of its
+// values -- the upper half where the offset's lane bit is set -- and adds the
+// partner's copy of that half; the single value left is summed over the
+// remaining offsets.  Lane l ends with the total of value l >> (5 - log2 N')
+// (N' - 1 + 5 - log2 N' adds per lane instead of 5 N).
+template <int N>
+__device__ __forceinline__ double warp_sum_halving(const double (&v)[N]) {
+  constexpr int LOG = Halving<N>::LOG, NP = Halving<N>::NP;
+  const int lane = threadIdx.x & 31;
+  double u[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) u[j] = j < N ? v[j] : 0.0;
+#pragma unroll
+  for (int st = 0; st < LOG; ++st) {
+    const int o = 16 >> st, h = NP >> (st + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double keep = up ? u[h + i] : u[i];
+      const double send = up ? u[i] : u[h + i];
+      u[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double t = u[0];
+#pragma unroll
+  for (int o = 16 >> LOG; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// block-wide sum of N doubles per thread (result broadcast to all threads):
+// the warps' totals by recursive halving, then lanes 0..N-1 of warp 0 add
+// the warps' partials of one value each, in warp order
 template <int N>
 __device__ void block_sum(double (&v)[N], double *scratch /* [(warps + 1) N] */) {
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int SH = 5 - Halving<N>::LOG;
+  const double t = warp_sum_halving<N>(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int j = 0; j < N; ++j) scratch[w * N + j] = v[j];
+  if ((lane & ((1 << SH) - 1)) == 0 && (lane >> SH) < N) scratch[w * N + (lane >> SH)] = t;
   __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      double t = 0.0;
-      for (int q = 0; q < nw; ++q) t += scratch[q * N + j];
-      scratch[nw * N + j] = t;
-    }
+  if (w == 0 && lane < N) {
+    double a = 0.0;
+    for (int q = 0; q < nw; ++q) a += scratch[q * N + lane];
+    scratch[nw * N + lane] = a;
+  }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < N; ++j) v[j] = scratch[nw * N + j];
   __syncthreads();
+}
+
+// (c, s) of the Jacobi rotation that zeroes h_pq.  Any t = tan(angle) gives
+// an exact rotation once c = (1 + t^2)^(-1/2) and s = t c hold in FP64, so t
+// comes from FP32 arithmetic (it leaves about 1e-7 of h_pq, which the next
+// sweep removes) and c from Newton's method for x^(-1/2), y <- y (3 - x y^2)/2,
+// twice from the FP32 reciprocal square root.  h_pq and h_qq - h_pp are
+// scaled by one power of two first, so that their FP32 copies neither
+// overflow nor lose h_pq (an h_pq below 2^-126 of the difference is far
+// under the convergence test's threshold).
+__device__ __forceinline__ void jacobi_rotation(double hpp, double hqq, double apq, double &c, double &sn) {
+  const double d = hqq - hpp;
+  const int ea = (__double2hiint(apq) >> 20) & 0x7FF, ed = (__double2hiint(d) >> 20) & 0x7FF;
+  const int e = min(max(ea, ed), 2045);                      // biased exponent of the larger
+  const double sc = __hiloint2double((2046 - e) << 20, 0);  // 2^(1023 - e): the larger to [1, 2)
+  const float af = (float)(apq * sc), df = (float)(d * sc);
+  const float th = df / (2.0f * af);
+  const float tf = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+  const double t = (double)tf, x = fma(t, t, 1.0), hx = 0.5 * x;
+  double y = (double)rsqrtf((float)x);
+  y *= fma(-hx * y, y, 1.5);
+  y *= fma(-hx * y, y, 1.5);
+  c = y;
+  sn = t * y;
 }
 
 // cyclic Jacobi on a tiny symmetric P x P matrix (P <= 4) by one warp: a
@@ -222,12 +281,7 @@ __device__ __forceinline__ void tiny_jacobi_warp(int P, double *H, double *Q) {
         const int p = pair_lo(r, lane), q = pair_hi(r, lane);
         if (q < P) {
           const double apq = H[p * P + q];
-          if (apq != 0.0) {
-            const double theta = (H[q * P + q] - H[p * P + p]) / (2.0 * apq);
-            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            sn = t * c;
-          }
+          if (apq != 0.0) jacobi_rotation(H[p * P + p], H[q * P + q], apq, c, sn);
         }
       }
       const double c0 = __shfl_sync(0xffffffffu, c, 0), s0 = __shfl_sync(0xffffffffu, sn, 0);
@@ -280,32 +334,53 @@ __device__ __forceinline__ void tiny_jacobi_warp(int P, double *H, double *Q) {
 // by a fixed pseudo-random vector.  (Cholesky-QR in two passes costs fewer
 // block sums but leaves the basis less aligned with the previous Ritz
 // vectors, and the Rayleigh-Ritz step after it then needs more Jacobi sweeps.)
+// The column's norm before the projections rides with the first pass's
+// dot products in one block sum; 1/||v|| is formed once, by thread 0.
 __device__ void orthonormalise(int k, int P, double *V, double *scratch, unsigned long long salt) {
+  __shared__ double s_inv;
   for (int j = 0; j < P; ++j) {
     for (int attempt = 0; attempt < 3; ++attempt) {
-      double nrm0[1] = {0.0};
-      for (int r = threadIdx.x; r < k; r += blockDim.x) nrm0[0] += V[r * P + j] * V[r * P + j];
-      block_sum<1>(nrm0, scratch);
-      for (int pass = 0; pass < 2; ++pass) {
-        double dots[kEigP];
+      double nrm0 = 0.0, nrm[1] = {0.0};
+      if (j == 0) {
+        for (int r = threadIdx.x; r < k; r += blockDim.x) nrm[0] += V[r * P + j] * V[r * P + j];
+        block_sum<1>(nrm, scratch);
+        nrm0 = nrm[0];
+      } else {
+        for (int pass = 0; pass < 2; ++pass) {
+          double dots[kEigP + 1];  // dots[q] = v_q . v_j (q < j); dots[kEigP] = ||v_j||^2 before the projections
 #pragma unroll
-        for (int q = 0; q < kEigP; ++q) dots[q] = 0.0;
-        for (int r = threadIdx.x; r < k; r += blockDim.x)
+          for (int q = 0; q <= kEigP; ++q) dots[q] = 0.0;
+          for (int r = threadIdx.x; r < k; r += blockDim.x) {
+            const double vj = V[r * P + j];
 #pragma unroll
-          for (int q = 0; q < kEigP; ++q)
-            if (q < j) dots[q] += V[r * P + q] * V[r * P + j];
-        block_sum<kEigP>(dots, scratch);
-        for (int r = threadIdx.x; r < k; r += blockDim.x)
+            for (int q = 0; q < kEigP; ++q)
+              if (q < j) dots[q] += V[r * P + q] * vj;
+            if (pass == 0) dots[kEigP] += vj * vj;
+          }
+          if (pass == 0) {
+            block_sum<kEigP + 1>(dots, scratch);
+            nrm0 = dots[kEigP];
+          } else {
+            double d4[kEigP];
 #pragma unroll
-          for (int q = 0; q < kEigP; ++q)
-            if (q < j) V[r * P + j] -= dots[q] * V[r * P + q];
-        __syncthreads();
+            for (int q = 0; q < kEigP; ++q) d4[q] = dots[q];
+            block_sum<kEigP>(d4, scratch);
+#pragma unroll
+            for (int q = 0; q < kEigP; ++q) dots[q] = d4[q];
+          }
+          for (int r = threadIdx.x; r < k; r += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < kEigP; ++q)
+              if (q < j) V[r * P + j] -= dots[q] * V[r * P + q];
+          __syncthreads();
+        }
+        for (int r = threadIdx.x; r < k; r += blockDim.x) nrm[0] += V[r * P + j] * V[r * P + j];
+        block_sum<1>(nrm, scratch);
       }
-      double nrm[1] = {0.0};
-      for (int r = threadIdx.x; r < k; r += blockDim.x) nrm[0] += V[r * P + j] * V[r * P + j];
-      block_sum<1>(nrm, scratch);
-      if (nrm[0] > 1e-24 * nrm0[0] && nrm[0] > 0.0) {
-        const double inv = 1.0 / sqrt(nrm[0]);
+      if (nrm[0] > 1e-24 * nrm0 && nrm[0] > 0.0) {
+        if (threadIdx.x == 0) s_inv = 1.0 / sqrt(nrm[0]);
+        __syncthreads();
+        const double inv = s_inv;
         for (int r = threadIdx.x; r < k; r += blockDim.x) V[r * P + j] *= inv;
         __syncthreads();
         break;
@@ -383,14 +458,11 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
         for (int q = 0; q < kEigP; ++q)
           if (q < ncols) acc[q] += av * V[c * P + q];
       }
-#pragma unroll
-      for (int q = 0; q < kEigP; ++q)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < kEigP; ++q)
-          if (q < ncols) yg[r * P + q] = acc[q];
+      // lane l holds the total of column l >> kSh
+      constexpr int kSh = 5 - Halving<kEigP>::LOG;
+      const double tot = warp_sum_halving<kEigP>(acc);
+      const int q = lane >> kSh;
+      if ((lane & ((1 << kSh) - 1)) == 0 && q < ncols) yg[r * P + q] = tot;
     }
     if (gridDim.x > 1) {
       if (!grid_barrier(bar, status)) return false;
@@ -405,7 +477,8 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
 
   // one Rayleigh-Ritz step with matrix A on span(V): V <- Ritz vectors,
   // Y <- A V, H diagonal <- Ritz values (descending); returns the relative
-  // residual max_{j<2} ||A v_j - h_j v_j|| / |h_0|, or -1 if a grid barrier gave up
+  // residual max_{j<2} ||A v_j - h_j v_j|| / |h_0| in thread 0 (0 in the
+  // others), or -1 in every thread if a grid barrier gave up
   auto rayleigh_ritz = [&](const double *__restrict__ A) -> double {
     if (!product(A, P)) return -1.0;
     double h[kEigP * (kEigP + 1) / 2];  // H = V^T Y, upper triangle
@@ -461,6 +534,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
         res[j] += e * e;
       }
     block_sum<2>(res, scratch);
+    if (threadIdx.x != 0) return 0.0;  // only thread 0 reads the residual
     const double h0 = fabs(H[0]);
     return h0 > 0.0 ? sqrt(fmax(res[0], res[1])) / h0 : 0.0;
   };
@@ -481,6 +555,7 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(int32_t n, int32_t k, con
         e[j] += d * d;
       }
     block_sum<2>(e, scratch);
+    if (threadIdx.x != 0) return 0.0;  // only thread 0 reads the residual
     const double q0 = fabs(q[0]);
     return q0 > 0.0 ? sqrt(fmax(e[0], e[1])) / q0 : 0.0;
   };
