@@ -262,8 +262,9 @@ int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_
  * on which ssm_pivotmds applies the double centring at the k x k level.
  * Writes g_lo[k*k], g_hi[k*k] (device, uint64): entry a*k + b holds the low
  * and high 64 bits of G[a][b] for a <= b; entries with a > b are zero.  The
- * call zeroes both arrays itself.  Runs on the tensor cores (5-bit digit
- * planes in FP16, FP32 accumulation of exact integers).  1 <= k <= 1024.
+ * call zeroes both arrays itself.  Runs on the tensor cores (digit planes in
+ * FP16 -- one 7-bit digit when every d^2 is below 128, 5-bit digits
+ * otherwise -- with FP32 accumulation of exact integers).  1 <= k <= 1024.
  * Device errors: SSM_E_TIMEOUT (a tensor-core wait ran out).
  * ------------------------------------------------------------------- */
 size_t ssm_gram_workspace(int32_t n, int32_t k);
