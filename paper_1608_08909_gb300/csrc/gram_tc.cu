@@ -16,9 +16,9 @@
 // (2 digits for small-world graphs, 4 for d <= 1023).  When every squared
 // distance is below 2^7 (d <= 11) one 7-bit digit does instead: FP16 holds it
 // exactly, a product is at most 127^2, and an accumulator read out every
-// kTcFlush7 chunks (1024 nodes) stays below 2^24; those read-outs add into
-// 64-bit sums in shared memory (one per tile entry), and only the slice's
-// totals go to G.
+// 2^18 / s_max^2 chunks (at least kTcFlush7: 1024 nodes) stays below 2^24;
+// those read-outs add into 64-bit sums in shared memory (one per tile
+// entry), and only the slice's totals go to G.
 //
 // Work units are (output tile, digit block, chunk of 64 nodes): a 128 x 128
 // tile of pivots a (tile ta) by pivots b (tile tb >= ta, by symmetry), a
@@ -52,7 +52,8 @@ namespace ssm {
 constexpr int kTcThreads = 512;        // 16 warps, 8 pivot rows of each tile per warp
 constexpr int kTcChunk = 64;           // nodes per plane row (128 bytes of FP16, 4 MMAs of K = 16)
 constexpr int kTcFlush = 256;          // chunks per accumulator read-out (16384 nodes: below 2^24)
-constexpr int kTcFlush7 = 16;          // the same with one 7-bit digit (1024 nodes: 127^2 1024 < 2^24)
+constexpr int kTcFlush7 = 16;          // the same with one 7-bit digit, at its largest (127^2 1024 < 2^24)
+static_assert((1 << 18) / (127 * 127) >= kTcFlush7, "one-digit read-out period");
 constexpr unsigned kTcAccBytes = 128u * 128u * 8u;  // 64-bit sums of one tile (single-digit mode)
 constexpr int kTcDigBits = 5;          // digit width
 constexpr int kTcDigBlock = 2;         // digits per A block and per B block
@@ -107,6 +108,16 @@ __device__ __forceinline__ uint32_t tc_digits(uint32_t s0, uint32_t s1, uint32_t
   w |= 0x64006400u;
   const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&w), __half2half2(__ushort_as_half(0x6400)));
   return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// single-digit mode: the FP16 pair (d0^2, d1^2) of two distances below 2^5
+// packed in 16-bit halves (1024 + d is exact in FP16, and so are its
+// difference with 1024 and that difference squared)
+__device__ __forceinline__ uint32_t tc_square_pair(uint32_t dd) {
+  uint32_t w = dd | 0x64006400u;
+  const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&w), __half2half2(__ushort_as_half(0x6400)));
+  const __half2 q = __hmul2(h, h);
+  return *reinterpret_cast<const uint32_t *>(&q);
 }
 
 // distances of nodes i, i + 1 of one pivot row packed in 16-bit halves (zero
@@ -240,7 +251,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
   while (bits < 64 && (s_max >> bits) != 0ull) ++bits;
   const bool one = s_max < 128ull;  // single 7-bit digit
   const int D = one ? 1 : (bits + kTcDigBits - 1) / kTcDigBits;
-  const int flush = one ? kTcFlush7 : kTcFlush;
+  // read-out period: with one digit every partial sum stays below
+  // 64 chunks s_max^2 <= 2^24 (at least kTcFlush7 chunks for s_max <= 127)
+  const int flush = one ? (int)min((unsigned long long)kTcFlush, (1ull << 18) / max(1ull, s_max * s_max)) : kTcFlush;
   const uint32_t dmask = one ? 0x007F007Fu : 0x001F001Fu;
   const int ppo = one ? 1 : kTcDigBlock;  // planes per operand in a buffer
   const unsigned buf_bytes = 2u * (unsigned)ppo * kTcPlaneBytes;
@@ -330,33 +343,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
     // verdict is made uniform at the barrier below)
     const bool freed = it < 2 || tc_wait(mb, (unsigned)((it - 2) >> 1) & 1u);
     unsigned char *const buf = gbase + u * buf_bytes;
+    if (one) {
+      // one digit: the planes hold the FP16 squares themselves
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const uint32_t da = ca[r];
-      const uint32_t a0 = (da & 0xFFFFu) * (da & 0xFFFFu), a1 = (da >> 16) * (da >> 16);
-      const uint32_t La = __byte_perm(a0, a1, 0x5410), Ma = needM ? __byte_perm(a0 >> 15, a1 >> 15, 0x5410) : 0u;
-      // row m = 8 warp + r: atom m / 8 = warp, row m mod 8 = r; 16-byte chunk
-      // lane / 4 swizzled by r, bytes 4 (lane mod 4) in it
-      const unsigned off = (unsigned)warp * 1024u + (unsigned)r * 128u + ((unsigned)((lane >> 2) ^ r) << 4) +
-                           ((unsigned)(lane & 3) << 2);
+      for (int r = 0; r < 8; ++r) {
+        const unsigned off = (unsigned)warp * 1024u + (unsigned)r * 128u + ((unsigned)((lane >> 2) ^ r) << 4) +
+                             ((unsigned)(lane & 3) << 2);
+        *reinterpret_cast<uint32_t *>(buf + off) = tc_square_pair(ca[r]);
+        if (!share) *reinterpret_cast<uint32_t *>(buf + kTcPlaneBytes + off) = tc_square_pair(cb[r]);
+      }
+    } else {
 #pragma unroll
-      for (int j = 0; j < kTcDigBlock; ++j)
-        if (j < U.npa)
-          *reinterpret_cast<uint32_t *>(buf + j * kTcPlaneBytes + off) = tc_digits(a0, a1, La, Ma, U.pa0 + j, dmask);
-      if (!share) {
-        uint32_t b0 = a0, b1 = a1, Lb = La, Mb = Ma;
-        if (!diag) {
-          const uint32_t db = cb[r];
-          b0 = (db & 0xFFFFu) * (db & 0xFFFFu);
-          b1 = (db >> 16) * (db >> 16);
-          Lb = __byte_perm(b0, b1, 0x5410);
-          Mb = needM ? __byte_perm(b0 >> 15, b1 >> 15, 0x5410) : 0u;
-        }
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t da = ca[r];
+        const uint32_t a0 = (da & 0xFFFFu) * (da & 0xFFFFu), a1 = (da >> 16) * (da >> 16);
+        const uint32_t La = __byte_perm(a0, a1, 0x5410), Ma = needM ? __byte_perm(a0 >> 15, a1 >> 15, 0x5410) : 0u;
+        // row m = 8 warp + r: atom m / 8 = warp, row m mod 8 = r; 16-byte chunk
+        // lane / 4 swizzled by r, bytes 4 (lane mod 4) in it
+        const unsigned off = (unsigned)warp * 1024u + (unsigned)r * 128u + ((unsigned)((lane >> 2) ^ r) << 4) +
+                             ((unsigned)(lane & 3) << 2);
 #pragma unroll
         for (int j = 0; j < kTcDigBlock; ++j)
-          if (j < U.nqb)
-            *reinterpret_cast<uint32_t *>(buf + (ppo + j) * kTcPlaneBytes + off) =
-                tc_digits(b0, b1, Lb, Mb, U.qb0 + j, dmask);
+          if (j < U.npa)
+            *reinterpret_cast<uint32_t *>(buf + j * kTcPlaneBytes + off) =
+                tc_digits(a0, a1, La, Ma, U.pa0 + j, dmask);
+        if (!share) {
+          uint32_t b0 = a0, b1 = a1, Lb = La, Mb = Ma;
+          if (!diag) {
+            const uint32_t db = cb[r];
+            b0 = (db & 0xFFFFu) * (db & 0xFFFFu);
+            b1 = (db >> 16) * (db >> 16);
+            Lb = __byte_perm(b0, b1, 0x5410);
+            Mb = needM ? __byte_perm(b0 >> 15, b1 >> 15, 0x5410) : 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < kTcDigBlock; ++j)
+            if (j < U.nqb)
+              *reinterpret_cast<uint32_t *>(buf + (ppo + j) * kTcPlaneBytes + off) =
+                  tc_digits(b0, b1, Lb, Mb, U.qb0 + j, dmask);
+        }
       }
     }
     // the next chunk's distances, in flight while the MMAs are issued
@@ -368,10 +393,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int32_t n, int32_t k,
     if (idx + 1 < end) {
       const TcUnit U1 = tg1 == tg ? U : tc_unit(tg1, groups, nblk, T, D);
       const int i = kTcChunk * ch1 + 2 * lane;
+      const int ra = 128 * U1.ta + 8 * warp, rb = 128 * U1.tb + 8 * warp;
+      if (wide4 && kTcChunk * (ch1 + 1) <= n) {
+        // the chunk lies inside the rows: 4-byte loads one row (n / 2 words) apart
+        const unsigned *pa = reinterpret_cast<const unsigned *>(dip) + ((size_t)ra * n + i) / 2;
+        const unsigned *pb = reinterpret_cast<const unsigned *>(dip) + ((size_t)rb * n + i) / 2;
+        const size_t row = (size_t)n / 2;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        ca[r] = tc_load_pair(dip, n, 128 * U1.ta + 8 * warp + r, k, i, wide4);
-        cb[r] = U1.ta == U1.tb ? 0u : tc_load_pair(dip, n, 128 * U1.tb + 8 * warp + r, k, i, wide4);
+        for (int r = 0; r < 8; ++r) {
+          ca[r] = ra + r < k ? __ldg(pa + r * row) : 0u;
+          cb[r] = (U1.ta != U1.tb && rb + r < k) ? __ldg(pb + r * row) : 0u;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          ca[r] = tc_load_pair(dip, n, ra + r, k, i, wide4);
+          cb[r] = U1.ta == U1.tb ? 0u : tc_load_pair(dip, n, rb + r, k, i, wide4);
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the planes are read by the tensor cores

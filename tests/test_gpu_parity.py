@@ -320,7 +320,10 @@ def _gram_u128(lo, hi):
 
 @pytest.mark.parametrize("k,n,dmax,offset", [
     (200, 20001, 3, 0),        # one 7-bit digit, odd n (two-byte loads), ragged second tile
-    (300, 70001, 11, 0),       # one 7-bit digit at its largest (121): 69 read-outs into the tile sums
+    (300, 70001, 11, 0),       # one 7-bit digit at its largest (121): read out every 17 chunks
+    (200, 300001, 2, 0),       # one digit read out every 256 chunks, odd n
+    (256, 150000, 8, 0),       # one digit read out every 64 chunks (d <= 8), full tiles, 4-byte loads
+    (150, 65538, 7, 0),        # one digit, even n with a ragged last chunk
     (300, 70000, 12, 0),       # the smallest squared distance that needs 5-bit digits (144)
     (200, 20001, 15, 0),       # two digits
     (130, 33000, 200, 0),      # four digits, even n (four-byte loads), three node ranges
