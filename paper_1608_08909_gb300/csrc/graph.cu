@@ -193,10 +193,16 @@ __global__ void k_compact(int32_t n, int64_t total, const int *__restrict__ off,
     rowptr[row] = pos[off[row]];
 }
 
-// ---- connectivity by union-find (no per-level latency): every input edge
-// links the root with the larger id under the one with the smaller id by
-// compare-and-swap; afterwards the graph is connected iff exactly one node is
-// its own root.
+// ---- connectivity by union-find (no per-level latency) with neighbour
+// sampling (Sutton, Ben-Nun and Barak, "Optimizing parallel graph
+// connectivity computation via subgraph sampling", 2018): every node first
+// links with its first two neighbours, the forest is compressed, the most
+// frequent root among kUfSamples evenly spaced nodes is taken for the large
+// component's, and only the nodes outside it link their remaining edges (an
+// edge between that component and another one is also in the row of its
+// other endpoint, which does not skip it).  A link hangs the root with the
+// larger id under the one with the smaller id by compare-and-swap; the graph
+// is connected iff exactly one node is its own root.
 __device__ __forceinline__ int uf_find(int *parent, int x) {
   int p = __ldcg(parent + x);
   while (p != x) {
@@ -213,18 +219,65 @@ __global__ void k_uf_init(int32_t n, int *__restrict__ parent) {
     parent[i] = (int)i;
 }
 
-// one thread per input edge (balanced whatever the degrees); self-loops and
-// repeated edges are harmless
-__global__ void k_uf_link(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int *parent) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    int a = uf_find(parent, __ldg(src + e)), b = uf_find(parent, __ldg(dst + e));
-    while (a != b) {
-      if (a > b) { const int t2 = a; a = b; b = t2; }
-      const int old = atomicCAS(parent + b, b, a);  // b is a root: hang it under a
-      if (old == b) break;
-      a = uf_find(parent, a);
-      b = uf_find(parent, old);
-    }
+// x and y in one tree; self-loops and repeated edges are harmless
+__device__ __forceinline__ void uf_link(int *parent, int x, int y) {
+  int a = uf_find(parent, x), b = uf_find(parent, y);
+  while (a != b) {
+    if (a > b) { const int t2 = a; a = b; b = t2; }
+    const int old = atomicCAS(parent + b, b, a);  // b is a root: hang it under a
+    if (old == b) break;
+    a = uf_find(parent, a);
+    b = uf_find(parent, old);
+  }
+}
+
+// every node links with its neighbour number r (rows are sorted, so the
+// smallest ids first)
+__global__ void k_uf_sample(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int r,
+                            int *parent) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int e = __ldg(rowptr + v) + r;
+    if (e < __ldg(rowptr + v + 1)) uf_link(parent, (int)v, __ldg(colidx + e));
+  }
+}
+
+// parent[v] = root of v (no links run meanwhile, so the roots hold still)
+__global__ void k_uf_compress(int32_t n, int *parent) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    parent[v] = uf_find(parent, (int)v);
+}
+
+// one block of kUfSamples threads: the most frequent root among the
+// compressed parents of kUfSamples evenly spaced nodes (ties: the smaller id)
+constexpr int kUfSamples = 256;
+__global__ void __launch_bounds__(kUfSamples) k_uf_guess(int32_t n, const int *__restrict__ parent,
+                                                         unsigned *__restrict__ big) {
+  __shared__ int root[kUfSamples];
+  __shared__ unsigned long long best[kUfSamples / 32];
+  const int t = threadIdx.x;
+  root[t] = __ldcg(parent + (int)((int64_t)t * n / kUfSamples));
+  __syncthreads();
+  unsigned cnt = 0;
+  for (int j = 0; j < kUfSamples; ++j) cnt += root[j] == root[t];
+  // largest count, then smallest root
+  unsigned long long key = ((unsigned long long)cnt << 32) | (unsigned)(0x7FFFFFFF - root[t]);
+  for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+  if ((t & 31) == 0) best[t >> 5] = key;
+  __syncthreads();
+  if (t == 0) {
+    for (int w = 1; w < kUfSamples / 32; ++w) key = max(key, best[w]);
+    *big = (unsigned)(0x7FFFFFFF - (int)(key & 0xFFFFFFFFu));
+  }
+}
+
+// nodes outside the guessed large component link their remaining edges
+__global__ void k_uf_finish(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                            const unsigned *__restrict__ big, int *parent) {
+  const int c = (int)__ldg(big);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (__ldcg(parent + v) == c) continue;
+    const int e1 = __ldg(rowptr + v + 1);
+    for (int e = __ldg(rowptr + v) + 2; e < e1; ++e) uf_link(parent, (int)v, __ldg(colidx + e));
   }
 }
 
@@ -313,10 +366,13 @@ SSM_API int ssm_build_graph(int32_t n, int64_t m_in, const int32_t *src, const i
   SSM_TRY_CUDA(cudaMemcpyAsync(&uniq, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SSM_TRY_CUDA(cudaStreamSynchronize(s));
   *m_out = uniq / 2;
-  // connectivity: union-find over the final CSR
+  // connectivity: union-find over the final CSR (roots[3]: the large component's root)
   SSM_TRY_CUDA(cudaMemsetAsync(w.roots, 0, 4 * sizeof(unsigned), s));
   note_launch(), k_uf_init<<<nblocks, 256, 0, s>>>(n, w.parent);
-  note_launch(), k_uf_link<<<eblocks, 256, 0, s>>>(m_in, src, dst, w.parent);
+  for (int r = 0; r < 2; ++r) note_launch(), k_uf_sample<<<nblocks, 256, 0, s>>>(n, rowptr, colidx, r, w.parent);
+  note_launch(), k_uf_compress<<<nblocks, 256, 0, s>>>(n, w.parent);
+  note_launch(), k_uf_guess<<<1, kUfSamples, 0, s>>>(n, w.parent, w.roots + 3);
+  note_launch(), k_uf_finish<<<nblocks, 256, 0, s>>>(n, rowptr, colidx, w.roots + 3, w.parent);
   note_launch(), k_uf_roots<<<nblocks, 256, 0, s>>>(n, w.parent, w.roots);
   // the sweep's row classes, read back with the component count
   if (row_classes) note_launch(), k_row_classes<<<nblocks, 256, 0, s>>>(n, rowptr, w.roots + 1);

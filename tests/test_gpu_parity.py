@@ -87,6 +87,33 @@ def test_build_graph_errors():
     assert e.value.code == -3
 
 
+@pytest.mark.parametrize("case", ["pieces", "crossed", "pairs"])
+def test_build_graph_counts_components(case):
+    """The connectivity check finds the exact number of components (named in
+    the error), also where each node's first two neighbours join little and
+    most nodes lie outside the largest component."""
+    if case == "pieces":  # a grid, a BA graph and 7 isolated nodes
+        n1, s1, d1 = I.grid(100, 100)
+        n2, s2, d2 = I.ba(5000, 2, 3)
+        n, want = n1 + n2 + 7, 9
+        s = np.concatenate([s1, s2 + n1]).astype(np.int32)
+        d = np.concatenate([d1, d2 + n1]).astype(np.int32)
+    elif case == "crossed":  # 40 cycles of 250 nodes, node ids dealt round-robin over the cycles
+        c, L = 40, 250
+        ids = np.arange(c * L, dtype=np.int64).reshape(L, c).T  # cycle j holds j, j + c, j + 2c, ...
+        s = ids.reshape(-1).astype(np.int32)
+        d = np.roll(ids, -1, axis=1).reshape(-1).astype(np.int32)
+        n, want = c * L, c
+    else:  # 1000 disjoint edges
+        n, want = 2000, 1000
+        s = np.arange(0, n, 2, dtype=np.int32)
+        d = s + 1
+    with pytest.raises(ssm.SSMError) as e:
+        _gpu_graph(n, s, d)
+    assert e.value.code == -3
+    assert f"{want} connected components" in str(e.value)
+
+
 # ------------------------------------------------------------------ a1 pivots
 
 @pytest.mark.parametrize("name,k,start", [("grid32", 50, 0), ("grid_ragged", 33, 5), ("path", 7, 150),
