@@ -152,6 +152,9 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // next one may start while the previous one drains; it waits here before it
 // touches anything the previous kernel writes (a no-op without that launch mode).
 __device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next kernel's blocks be scheduled as this kernel's blocks leave
+// (they still wait for its completion in wait_previous_kernel)
+__device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ float lds_f32(unsigned addr) {
   float v;
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(256) k_sweep_nbr(int32_t n, const int32_t *__r
                                                    int32_t nlong, const int32_t *__restrict__ long_rows, int32_t nmid,
                                                    const int32_t *__restrict__ mid_rows, float2 *__restrict__ nb,
                                                    const int32_t *__restrict__ stop) {
+  allow_next_kernel();
   wait_previous_kernel();
   if (__ldcg(stop)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -353,6 +357,10 @@ __global__ void __launch_bounds__(kSweepThreads, MODE == 2 ? SSM_SWEEP_FULL_MIN_
   uint2 *pidx = reinterpret_cast<uint2 *>(pxy + A.k);   // (table address base, clamp) per pivot
   float *stab = reinterpret_cast<float *>(pidx + A.k);  // s by d
   const int n = A.n, k = A.k;
+  // with pivot ranges split into tasks (graphs of few tiles) the next
+  // iteration's neighbour kernel may take the slots of finished blocks early;
+  // with whole tiles that measured slower, so there it is not let in
+  if (A.nsplit > 1) allow_next_kernel();
   // the weight tables do not depend on the previous kernels: load them first
   if (SMEM)
     for (int t = threadIdx.x; t < A.stab_len; t += blockDim.x) stab[t] = __ldg(A.stab + t);
