@@ -19,6 +19,12 @@
 // kPullMaxLevels levels, and reports it; the caller then runs the per-source
 // BFS.  Sources are taken in
 // passes of 256 (eight 32-bit words per node).
+//
+// Beside F_L a bitmap per level marks the nodes whose F_L word is not zero
+// (the frontier of level L); a node reads a neighbour's 32-byte frontier
+// words only when its bit is set.  At the first levels the frontier is a
+// small part of the graph and nearly every such read is saved; the bitmap
+// (n / 8 bytes) stays in L1.
 #include <algorithm>
 
 #include "bfs.cuh"
@@ -48,6 +54,8 @@ struct PullArgs {
   int32_t *status;
   uint4 *seen;      // [n][kPullW4] sources that reached the node
   uint4 *F;         // [kPullMaxLevels + 1][n][kPullW4] new bits of every level
+  unsigned *fb;     // [kPullMaxLevels + 1][fbw] bit v of level L: F_L[v] is not zero (zeroed by the caller)
+  size_t fbw;       // words per level bitmap (a multiple of 32: 128-byte rows)
   const int32_t *long_rows;  // nodes of degree above kPullLong
   const unsigned *nlong;     // how many (device)
   unsigned *nlev;   // levels with new bits (written when the pass completes)
@@ -88,6 +96,7 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
     unsigned *f = reinterpret_cast<unsigned *>(A.F + (size_t)v * kPullW4) + (a >> 5);
     atomicOr(s, bit);
     atomicOr(f, bit);
+    atomicOr(A.fb + (v >> 5), 1u << (v & 31u));
   }
   if (gtid == 0) {
     for (int i = 0; i < 6; ++i) A.flag[i] = 0u;
@@ -108,6 +117,10 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
     }
     const uint4 *fcur = A.F + (size_t)L * n * kPullW4;
     uint4 *fnext = A.F + (size_t)(L + 1u) * n * kPullW4;
+    // level L's bitmap was written (in L2, by atomics) during level L - 1 and is
+    // read only from this level on, so no cache holds an older copy of it
+    const unsigned *fbcur = A.fb + (size_t)L * A.fbw;
+    unsigned *fbnext = A.fb + (size_t)(L + 1u) * A.fbw;
     // the flags of level L+1 were last read right after the barrier of level
     // L-2, which every thread has passed since
     if (gtid == 0) {
@@ -141,6 +154,10 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
           unsigned u[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) u[e] = t + e < re ? (unsigned)__ldg(A.colidx + t + e) : 0xFFFFFFFFu;
+          // neighbours outside level L's frontier add nothing
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (u[e] != 0xFFFFFFFFu && ((fbcur[u[e] >> 5] >> (u[e] & 31u)) & 1u) == 0u) u[e] = 0xFFFFFFFFu;
           bool done = true;
 #pragma unroll
           for (int c = 0; c < kPullW4; ++c) {
@@ -167,6 +184,9 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
         got |= (nw[c].x | nw[c].y | nw[c].z | nw[c].w) != 0u;
         left |= (nw[c].x ^ miss[c].x) | (nw[c].y ^ miss[c].y) | (nw[c].z ^ miss[c].z) | (nw[c].w ^ miss[c].w);
       }
+      // this warp's 32 nodes in level L + 1's bitmap (a long row adds its bit later)
+      const unsigned fbits = __ballot_sync(0xffffffffu, live && !deferred && got);
+      if (lane == 0 && fbits != 0u) atomicOr(fbnext + (base >> 5), fbits);
       if (live && !deferred) {
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c) {
@@ -211,6 +231,9 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
 #pragma unroll
         for (int e = 0; e < kPullLongBatch; ++e)
           u[e] = t0 + 32 * e < he ? (unsigned)__ldg(A.colidx + t0 + 32 * e) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int e = 0; e < kPullLongBatch; ++e)
+          if (u[e] != 0xFFFFFFFFu && ((fbcur[u[e] >> 5] >> (u[e] & 31u)) & 1u) == 0u) u[e] = 0xFFFFFFFFu;
 #pragma unroll
         for (int c = 0; c < kPullW4; ++c)
 #pragma unroll
@@ -259,6 +282,7 @@ __global__ void __launch_bounds__(kPullThreads, 2) k_msbfs_pull(PullArgs A) {
         any_new |= got;
         unfinished |= left;
         if (L < kPullProbeLevel) pairs += np;
+        if (got) atomicOr(fbnext + (v >> 5), 1u << (v & 31u));
       }
     }
     if (__any_sync(0xffffffffu, any_new) && lane == 0) atomicOr(A.flag + L % 3u, 1u);
@@ -354,10 +378,14 @@ __global__ void k_pull_long_rows(int32_t n, const int32_t *__restrict__ rowptr, 
     if (__ldg(rowptr + v + 1) - __ldg(rowptr + v) > kPullLong) out[atomicAdd(count, 1u)] = v;
 }
 
+// words of one level's frontier bitmap, rounded to whole 128-byte rows
+static size_t pull_bitmap_words(int32_t n) { return (((size_t)n + 1023) / 1024) * 32; }
+
 size_t msbfs_pull_workspace(int32_t n) {
   Carver c(nullptr, 0);
   c.take<uint4>((size_t)n * kPullW4);
   c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  c.take<unsigned>(pull_bitmap_words(n) * (kPullMaxLevels + 1));
   c.take<int32_t>((size_t)n);
   c.take<unsigned>(1);
   c.take<unsigned>(1);
@@ -375,6 +403,8 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
   A.n = n; A.rowptr = rowptr; A.colidx = colidx; A.sources = sources; A.dist = dist; A.status = status;
   A.seen = c.take<uint4>((size_t)n * kPullW4);
   A.F = c.take<uint4>((size_t)n * kPullW4 * (kPullMaxLevels + 1));
+  A.fbw = pull_bitmap_words(n);
+  A.fb = c.take<unsigned>(A.fbw * (kPullMaxLevels + 1));
   int32_t *long_rows = c.take<int32_t>((size_t)n);
   unsigned *nlong = c.take<unsigned>(1);
   A.nlev = c.take<unsigned>(1);
@@ -397,6 +427,7 @@ int launch_msbfs_pull(int32_t n, const int32_t *rowptr, const int32_t *colidx, i
     A.nsrc = std::min(kPullSources, k - base);
     SSM_TRY_CUDA(cudaMemsetAsync(A.seen, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
     SSM_TRY_CUDA(cudaMemsetAsync(A.F, 0, (size_t)n * kPullW4 * sizeof(uint4), s));
+    SSM_TRY_CUDA(cudaMemsetAsync(A.fb, 0, A.fbw * (kPullMaxLevels + 1) * sizeof(unsigned), s));
     SSM_TRY_CUDA(cudaMemsetAsync(A.nlev, 0, sizeof(unsigned), s));
     if (int rc_ = reset_barrier(A.bar, s)) return rc_;
     void *args[] = {&A};
