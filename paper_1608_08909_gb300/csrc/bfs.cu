@@ -141,8 +141,14 @@ struct MaxMinArgs {
   unsigned long long *best;  // [2] packed (mind << 32 | ~node) maxima, by pivot parity
   BarrierState *bar;
   const unsigned *run_if;  // non-null: run only if *run_if != 0 (the cluster kernel gave the search up)
-  int32_t max_levels;      // > 0: stop the search at this depth and set *gave_up (the first search of a
-  unsigned *gave_up;       // cluster run: a deep graph is searched faster by the cluster itself)
+  // the first search of a cluster run (k_first_search): at most max_levels
+  // levels, else *gave_up (a deep graph is searched faster by the cluster itself)
+  int32_t max_levels;
+  unsigned *gave_up;
+  unsigned *fb;     // [kFirstSearchLevels + 1][fbw] frontier bitmaps, one per level (zeroed by the caller)
+  size_t fbw;       // words per bitmap (whole 128-byte rows)
+  unsigned *lcnt;   // [kFirstSearchLevels + 2] nodes first reached at each level (zeroed by the caller)
+  unsigned *nlong;  // rows above kFirstLong entries, listed in q0 (zeroed by the caller)
 };
 
 // Block 0 alone expands levels L, L+1, ... while the frontier has at most
@@ -167,7 +173,6 @@ __device__ void maxmin_solo(const MaxMinArgs &A, unsigned L, unsigned c, int2 (*
   for (int steps = 0; steps < kSoloLevels; ++steps) {
     const unsigned cc = s_cnt[cur];
     if (cc == 0 || cc > (unsigned)kSoloMax) break;
-    if (A.max_levels > 0 && L >= (unsigned)A.max_levels) break;
     const int nxt = cur ^ 1;
     unsigned *qout = ((L + 1) & 1) ? A.q1 : A.q0;
     const unsigned nd = L + 1;
@@ -239,10 +244,6 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
     for (unsigned L = __ldcg(A.level);;) {
       const unsigned c = __ldcg(A.qcnt + L % 3);
       if (c == 0) break;
-      if (A.max_levels > 0 && L >= (unsigned)A.max_levels) {  // every block reads the same L: uniform
-        if (gtid == 0) *A.gave_up = 1u;
-        return;
-      }
       if (c <= (unsigned)kSoloMax) {
         if (blockIdx.x == 0) maxmin_solo(A, L, c, sq, s_cnt, S);
         if (!grid_barrier(A.bar, A.status)) return;
@@ -299,6 +300,109 @@ __global__ void __launch_bounds__(kBfsThreads) k_maxmin(MaxMinArgs A) {
   }
 }
 
+// The first search of a cluster run (from start, over every node, at most
+// kFirstSearchLevels levels) as a BFS pulled level by level: every node not
+// reached yet scans its row for a neighbour in level L's frontier and stops
+// at the first one, so a level costs about one edge per new node where a
+// pushed expansion touches every edge of the frontier (small-world graphs:
+// levels of up to most of the graph).  The frontier of level L is a bitmap of
+// its own, written (by atomics, in L2) during level L - 1 and read from level
+// L on, so it can be read through L1.  Rows above kFirstLong entries are
+// scanned by a whole warp after the short rows of the level.  Writes mind
+// (= d(start, .)), pivots[0] = start and best[0] (the packed maximum), or sets
+// *gave_up when the search needs more levels, or when its first kFirstProbe
+// levels reached less than 1/64 of the nodes (a large diameter: the cluster
+// kernel, whose levels cost less, then searches from start itself).
+constexpr int kFirstLong = 64;
+constexpr unsigned kFirstProbe = 6;
+__global__ void __launch_bounds__(kBfsThreads) k_first_search(MaxMinArgs A) {
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gwarp = gtid >> 5, nwarps = nthreads >> 5;
+  const unsigned n = (unsigned)A.n, start = (unsigned)A.start;
+  for (unsigned base = gwarp * 32u; base < n; base += nwarps * 32u) {  // uniform per warp
+    const unsigned v = base + lane;
+    if (v < n) A.mind[v] = v == start ? 0u : kInf;
+    warp_append(v < n && __ldg(A.rowptr + v + 1) - __ldg(A.rowptr + v) > kFirstLong, v, A.q0, A.nlong);
+  }
+  if (gtid == 0) {
+    A.pivots[0] = (int32_t)start;
+    atomicOr(A.fb + (start >> 5), 1u << (start & 31u));
+    A.lcnt[0] = 1u;
+  }
+  if (!grid_barrier(A.bar, A.status)) return;
+  const unsigned nlong = __ldcg(A.nlong);
+  for (unsigned L = 0;; ++L) {
+    if (__ldcg(A.lcnt + L) == 0u) break;  // the same count in every thread: uniform
+    unsigned reached = 0;
+    if (L == kFirstProbe)
+      for (unsigned l = 0; l <= L; ++l) reached += __ldcg(A.lcnt + l);
+    if (L >= (unsigned)A.max_levels || (L == kFirstProbe && 64ull * reached < (unsigned long long)n)) {
+      if (gtid == 0) *A.gave_up = 1u;
+      return;
+    }
+    const unsigned *fbc = A.fb + (size_t)L * A.fbw;
+    unsigned *fbn = A.fb + (size_t)(L + 1u) * A.fbw;
+    unsigned found = 0;
+    for (unsigned base = gwarp * 32u; base < n; base += nwarps * 32u) {
+      const unsigned v = base + lane;
+      bool hit = false;
+      if (v < n && __ldcg(A.mind + v) == kInf) {
+        const int rb = __ldg(A.rowptr + v), re = __ldg(A.rowptr + v + 1);
+        if (re - rb <= kFirstLong)
+          for (int e = rb; e < re && !hit; e += 4) {
+            unsigned u[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u[q] = e + q < re ? (unsigned)__ldg(A.colidx + e + q) : kInf;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hit |= u[q] != kInf && ((fbc[u[q] >> 5] >> (u[q] & 31u)) & 1u);
+          }
+        if (hit) A.mind[v] = L + 1u;
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0 && bits) {
+        atomicOr(fbn + (base >> 5), bits);
+        found += __popc(bits);
+      }
+    }
+    // the long rows, a warp each, 32 entries at a time
+    for (unsigned li = gwarp; li < nlong; li += nwarps) {
+      const unsigned v = __ldcg(A.q0 + li);
+      if (__ldcg(A.mind + v) != kInf) continue;  // warp-uniform
+      const int rb = __ldg(A.rowptr + v), re = __ldg(A.rowptr + v + 1);
+      bool hit = false;
+      for (int e = rb; e < re && !hit; e += 32) {
+        const int t = e + (int)lane;
+        const unsigned u = t < re ? (unsigned)__ldg(A.colidx + t) : kInf;
+        hit = __any_sync(0xffffffffu, u != kInf && ((fbc[u >> 5] >> (u & 31u)) & 1u));
+      }
+      if (hit && lane == 0) {
+        A.mind[v] = L + 1u;
+        atomicOr(fbn + (v >> 5), 1u << (v & 31u));
+        ++found;
+      }
+    }
+    found = __reduce_add_sync(0xffffffffu, found);
+    if (lane == 0 && found) atomicAdd(A.lcnt + L + 1u, found);
+    if (!grid_barrier(A.bar, A.status)) return;
+  }
+  // argmax of mind, ties to the lowest node id
+  unsigned long long key = 0;
+  for (unsigned v = gtid; v < n; v += nthreads) {
+    const unsigned long long kk = ((unsigned long long)__ldcg(A.mind + v) << 32) | (unsigned long long)(~v);
+    key = kk > key ? kk : key;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, key, o);
+    key = t > key ? t : key;
+  }
+  if (lane == 0) atomicMax(A.best, key);
+  if (!grid_barrier(A.bar, A.status)) return;
+  if (gtid == 0 && (unsigned)(__ldcg(A.best) >> 32) == kInf) dev_fail(A.status, SSM_E_DISCONNECTED);
+}
+
 // adj[t] = (colidx[t], rowptr[colidx[t]], rowptr[colidx[t] + 1], 0)
 __global__ void k_expand_adj(int64_t m2, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                              int4 *__restrict__ adj) {
@@ -328,6 +432,10 @@ static void carve_maxmin(Carver &c, MaxMinArgs &A, unsigned **spill, int32_t n, 
   *spill = c.take<unsigned>(std::max<size_t>(1, maxmin_cluster_spill_entries(n)));
   A.run_if = c.take<unsigned>(1);
   A.gave_up = c.take<unsigned>(1);
+  A.fbw = (((size_t)n + 1023) / 1024) * 32;
+  A.fb = c.take<unsigned>(A.fbw * (kFirstSearchLevels + 1));
+  A.lcnt = c.take<unsigned>(kFirstSearchLevels + 2);
+  A.nlong = c.take<unsigned>(1);
 }
 
 // the cooperative grid kernel, after resetting its counters and barrier
@@ -345,8 +453,23 @@ static int launch_maxmin_grid(MaxMinArgs A, cudaStream_t s) {
   return SSM_OK;
 }
 
+// the first search of a cluster run (k_first_search), after zeroing its state
+static int launch_first_search(MaxMinArgs A, cudaStream_t s) {
+  SSM_TRY_CUDA(cudaMemsetAsync(A.best, 0, sizeof(unsigned long long), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.fb, 0, A.fbw * (kFirstSearchLevels + 1) * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.lcnt, 0, (kFirstSearchLevels + 2) * sizeof(unsigned), s));
+  SSM_TRY_CUDA(cudaMemsetAsync(A.nlong, 0, sizeof(unsigned), s));
+  if (int rc_ = reset_barrier(A.bar, s)) return rc_;
+  const int blocks = cooperative_blocks((const void *)k_first_search, kBfsThreads, 0, 2);
+  if (blocks < 1) return fail(SSM_E_CUDA, "max/min pivots: first search cannot be resident");
+  void *args[] = {&A};
+  note_launch();
+  SSM_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_first_search, dim3(blocks), dim3(kBfsThreads), args, 0, s));
+  return SSM_OK;
+}
+
 // Graphs whose mind fits a cluster: the first search (from start, over every
-// node) on the grid kernel, the other k - 1 searches (pruned, mostly small)
+// node) pulled on the whole grid, the other k - 1 searches (pruned, mostly small)
 // in the cluster; with a 2-byte mind the full grid selection is queued behind
 // them and runs only if the cluster handed over (a search deeper than 65534
 // levels).  Other graphs: the grid kernel alone.
@@ -372,7 +495,7 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
     first.k = 1;
     first.max_levels = kFirstSearchLevels;
     SSM_TRY_CUDA(cudaMemsetAsync(A.gave_up, 0, sizeof(unsigned), s));
-    if ((rc = launch_maxmin_grid(first, s))) return rc;
+    if ((rc = launch_first_search(first, s))) return rc;
     int mind_bytes = 0;
     rc = launch_maxmin_cluster(n, rowptr, A.adj, k, start, pivots, status, spill, fallback, A.mind, A.best,
                                A.gave_up, s, &mind_bytes);

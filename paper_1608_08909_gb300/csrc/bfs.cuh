@@ -21,9 +21,9 @@ int launch_maxmin(int32_t n, int64_t m2, const int32_t *rowptr, const int32_t *c
 // uses the grid kernel).  With 2 bytes the caller also queues the grid kernel
 // to run only if *fallback (device) was set: a search deeper than 65534
 // levels.  spill holds maxmin_cluster_spill_entries(n) entries.  With
-// init_mind / init_best (device; the grid kernel's mind and packed maximum
-// after a k = 1 run from start) the cluster starts at pivot 1, unless
-// *init_gaveup (device) says that run stopped early.
+// init_mind / init_best (device; mind and the packed maximum after the first
+// search, from start, on the whole grid) the cluster starts at pivot 1,
+// unless *init_gaveup (device) says that search stopped early.
 size_t maxmin_cluster_spill_entries(int32_t n);
 int maxmin_cluster_mind_bytes(int32_t n);  // 4 or 2 if the cluster kernel would run, else 0
 int launch_maxmin_cluster(int32_t n, const int32_t *rowptr, const int4 *adj, int32_t k, int32_t start,

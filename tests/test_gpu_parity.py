@@ -204,6 +204,26 @@ def test_select_pivots_large_ba_kernel():
     assert np.array_equal(got, O.maxmin(og, 24, 0))
 
 
+@pytest.mark.parametrize("case", ["ba_pair", "path_pair"])
+def test_select_pivots_disconnected(case):
+    """Max/min on a disconnected CSR reports SSM_E_DISCONNECTED, whether the
+    first search runs to its end (two small-world pieces) or hands the search
+    over to the cluster kernel (two paths, deeper than its level limit)."""
+    if case == "ba_pair":
+        n1, s1, d1 = I.ba(3000, 2, 5)
+        n = 2 * n1
+        s, d = np.concatenate([s1, s1 + n1]), np.concatenate([d1, d1 + n1])
+    else:
+        n, half = 80, 40
+        s = np.array(list(range(0, half - 1)) + list(range(half, n - 1)), np.int32)
+        d = s + 1
+    og = O.build_csr(n, s.astype(np.int32), d.astype(np.int32))
+    g = ssm.Graph(n, og.m, torch.from_numpy(og.rowptr).to(DEV), torch.from_numpy(og.colidx).to(DEV))
+    with pytest.raises(ssm.SSMError) as e:
+        ssm.ssm_select_pivots(g, 10, 0)
+    assert e.value.code == -3
+
+
 def test_select_pivots_deep_search_hands_over_to_the_grid_kernel():
     # a 900,000-node path: the 2-byte mind of the cluster kernel cannot hold
     # level 65535, so the grid kernel queued behind it redoes the selection
