@@ -299,28 +299,46 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
     }
 
     // argmax of mind over the cluster, ties to the lowest node id: a thread
-    // reads 16 bytes of slots at a time and keeps the first slot of the largest
-    // value it saw (slots ascending, so that is its lowest node id)
+    // takes 16 bytes of slots at a time, keeps the first chunk whose largest
+    // value (a packed maximum) beats what it saw, and then the first slot of
+    // that chunk holding it (chunks ascending, so that is its lowest node id);
+    // a chunk that runs past the last owned slot is taken slot by slot
     unsigned long long key = 0;
     {
       constexpr unsigned kPer = 16u / MB;  // slots per 16-byte load (slots is a multiple of 8)
-      unsigned bv = 0, bs = 0;
+      const uint4 *chunks = reinterpret_cast<const uint4 *>(mind);
+      auto slot_val = [&](const uint4 &w, unsigned e) -> unsigned {
+        const unsigned wd = e / (4u / MB) == 0 ? w.x : e / (4u / MB) == 1 ? w.y : e / (4u / MB) == 2 ? w.z : w.w;
+        return MB == 4 ? wd : (wd >> (16u * (e & 1u))) & 0xFFFFu;
+      };
+      unsigned bv = 0, bc = 0;
       bool any = false;
       for (unsigned c = tid; c * kPer < own; c += blockDim.x) {
-        const uint4 w = reinterpret_cast<const uint4 *>(mind)[c];
-        const unsigned wd[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (unsigned e = 0; e < kPer; ++e) {
-          const unsigned sl = c * kPer + e;
-          const unsigned val = MB == 4 ? wd[e] : (wd[e >> 1] >> (16u * (e & 1u))) & 0xFFFFu;
-          if (sl < own && (!any || val > bv)) {
-            bv = val;
-            bs = sl;
-            any = true;
+        const uint4 w = chunks[c];
+        unsigned v;
+        if ((c + 1u) * kPer <= own) {
+          if (MB == 2) {
+            const unsigned m = __vmaxu2(__vmaxu2(w.x, w.y), __vmaxu2(w.z, w.w));
+            v = max(m & 0xFFFFu, m >> 16);
+          } else {
+            v = max(max(w.x, w.y), max(w.z, w.w));
           }
+        } else {
+          v = 0;
+          for (unsigned e = 0; c * kPer + e < own; ++e) v = max(v, slot_val(w, e));
+        }
+        if (!any || v > bv) {
+          bv = v;
+          bc = c;
+          any = true;
         }
       }
-      if (any) key = ((unsigned long long)bv << 32) | (unsigned long long)(~(r + (bs << cs)));
+      if (any) {
+        const uint4 w = chunks[bc];
+        unsigned e = 0;
+        while (bc * kPer + e < own && slot_val(w, e) != bv) ++e;  // the value is in the chunk
+        key = ((unsigned long long)bv << 32) | (unsigned long long)(~(r + ((bc * kPer + e) << cs)));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
