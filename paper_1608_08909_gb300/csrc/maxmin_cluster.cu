@@ -239,6 +239,16 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
   const unsigned n = (unsigned)A.n;
   const unsigned own = n > r ? ((n - 1u - r) >> cs) + 1u : 0u;  // nodes r, r + C, ... below n
 
+  // the level counters of the next search, reset before the cluster barrier
+  // that precedes it: from that barrier on another CTA may push into this
+  // one's queue (level 0 publishes a total of 1: the pivot)
+  auto reset_search = [&]() {
+    if (tid < (unsigned)kMcMaxCluster) S.cnts[tid] = (tid == 0) ? 1u : 0u;
+    if (tid == 0) {
+      s_t3[0] = s_t3[1] = s_t3[2] = 0;
+      s_p3[0] = s_p3[1] = s_p3[2] = 0;
+    }
+  };
   unsigned p = (unsigned)A.start;
   int j0 = 0;
   if (A.init_mind && __ldcg(A.init_gaveup) == 0u) {
@@ -258,6 +268,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
   } else {
     for (unsigned s = tid; s < own; s += blockDim.x) mind[s] = (MindT)kInfM;
   }
+  reset_search();
   cluster_sync();  // every CTA of the cluster runs before any DSMEM access
 
   for (int j = j0; j < A.k; ++j) {
@@ -265,18 +276,15 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
     const bool last = (j == A.k - 1);
     if (last && j > 0) break;  // the final pivot needs no search
 
-    // level 0: the queue of p's owner holds p
-    if (tid < (unsigned)kMcMaxCluster) S.cnts[tid] = (tid == 0) ? 1u : 0u;
-    if (tid == 0) {
-      s_t3[0] = s_t3[1] = s_t3[2] = 0;
-      s_p3[0] = s_p3[1] = s_p3[2] = 0;
-      if (r == (p & cmask)) {
-        mind[p >> cs] = 0;
-        S.q[0] = make_int4((int)p, __ldg(A.rowptr + p), __ldg(A.rowptr + p + 1), 0);
-        s_t3[0] = 1;
-      }
+    // level 0: the queue of p's owner holds p.  Only the owner expands level 0,
+    // and every CTA finished reading mind (the last argmax) before the barrier
+    // that ended the previous search, so no cluster barrier is needed here
+    if (tid == 0 && r == (p & cmask)) {
+      mind[p >> cs] = 0;
+      S.q[0] = make_int4((int)p, __ldg(A.rowptr + p), __ldg(A.rowptr + p + 1), 0);
+      s_t3[0] = 1;
     }
-    cluster_sync();
+    __syncthreads();
 
     for (unsigned L = 0;; ++L) {
       unsigned tot = lane < C ? S.cnts[(L & 1u) * 16u + lane] : 0u;
@@ -356,6 +364,7 @@ __global__ void __launch_bounds__(kMcThreads, 1) k_maxmin_cluster(McArgs A) {
       }
       if (lane < C) dsmem_st_u64(dsmem_addr(bests + r, lane), key);
     }
+    reset_search();  // the level loop is over in every CTA (it ended at a cluster barrier)
     cluster_sync();
     key = 0;
     for (unsigned x = 0; x < C; ++x) key = bests[x] > key ? bests[x] : key;
