@@ -101,9 +101,12 @@ __global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__re
     B[t] = g - ((double)s[a] * (double)s[b]) * inv_n;
   }
   __syncthreads();
+  // row sums in column order: B is exactly symmetric (G from one triangle, the
+  // product s_a s_b commutes), so column a summed over rows 0..k-1 adds the
+  // same numbers in the same order as row a, and a warp's loads are coalesced
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     double acc = 0.0;
-    for (int b = 0; b < k; ++b) acc += B[(size_t)a * k + b];
+    for (int b = 0; b < k; ++b) acc += B[(size_t)b * k + a];
     rowmean[a] = acc / (double)k;
   }
   __syncthreads();
@@ -717,10 +720,22 @@ __global__ void __launch_bounds__(256) k_project(int32_t n, int32_t k, const uin
   }
 }
 
+// the largest entry: 16-byte loads of eight entries from the first 16-byte
+// boundary on (packed 16-bit maxima), the entries before it and past the
+// last whole load one at a time
 __global__ void k_dmax(int64_t count, const uint16_t *__restrict__ dip, unsigned *__restrict__ out) {
-  unsigned m = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
-    m = max(m, (unsigned)__ldg(dip + t));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t head = min(count, (int64_t)((16u - ((uintptr_t)dip & 15u)) & 15u) / 2);  // dip is 2-byte aligned
+  const int64_t nvec = (count - head) / 8;
+  const uint4 *v = reinterpret_cast<const uint4 *>(dip + head);
+  unsigned m2 = 0;  // two packed 16-bit maxima
+  for (int64_t t = gt; t < nvec; t += stride) {
+    const uint4 w = __ldg(v + t);
+    m2 = __vmaxu2(m2, __vmaxu2(__vmaxu2(w.x, w.y), __vmaxu2(w.z, w.w)));
+  }
+  unsigned m = max(m2 & 0xFFFFu, m2 >> 16);
+  for (int64_t t = gt; t < head; t += stride) m = max(m, (unsigned)__ldg(dip + t));
+  for (int64_t t = head + 8 * nvec + gt; t < count; t += stride) m = max(m, (unsigned)__ldg(dip + t));
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
@@ -1196,9 +1211,11 @@ __global__ void k_wgram_reduce(int32_t k, int64_t nchunks, const double *__restr
 // B = 1/4 (G' - rowmean_a - rowmean_b + grand mean), in place (one block)
 __global__ void k_center_b(int32_t k, double *__restrict__ B, double *__restrict__ rowmean) {
   __shared__ double red[32];
+  // G' is written symmetric (one value for both triangles): row sums taken
+  // down the columns, the same numbers in the same order, with coalesced loads
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     double acc = 0.0;
-    for (int b = 0; b < k; ++b) acc += B[(size_t)a * k + b];
+    for (int b = 0; b < k; ++b) acc += B[(size_t)b * k + a];
     rowmean[a] = acc / (double)k;
   }
   __syncthreads();
