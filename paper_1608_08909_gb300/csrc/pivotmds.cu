@@ -9,11 +9,14 @@
 //   k_dmax      largest d_ia (how many digits the Gram needs)
 //   k_gram_tc   G = Delta^T Delta on the tensor cores (gram_tc.cu)
 //   k_colsum    s_a
-//   k_prepare_b B = 1/4 J (G - s s^T/n) J
+//   k_prepare_b, k_row_means, k_center
+//               B = 1/4 J (G - s s^T/n) J
 //   k_square    M = (B / max|B|)^(2^kEigPowerLog2) by FP64 squarings (grid)
 //   k_eigen     top-2 eigenpairs of B: FP64 subspace iteration on M with
-//               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (one
-//               block), then a Rayleigh-Ritz step with B
+//               Rayleigh-Ritz and re-orthogonalised Gram-Schmidt (a
+//               cooperative grid: the k x k products over all blocks, the
+//               small steps on identical copies in every block), then a
+//               Rayleigh-Ritz step with B
 //   k_project   x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa),
 //               the sum in compensated (two-float) FP32 arithmetic
 //   k_edge_sum_* / k_rescale: scale so that sum_E ||x_i - x_j|| = m.
@@ -87,23 +90,31 @@ __global__ void k_colsum(int32_t n, int32_t k, const uint16_t *__restrict__ dip,
   }
 }
 
+// B = 1/4 J (G - s s^T / n) J in three steps, the element-wise ones spread
+// over the grid (FP64 runs at 1/64 of the FP32 rate, so one block spent
+// about 0.1 ms on the k^2 elements):
+//   k_prepare_b  B[a][b] = G[a][b] - s_a s_b / n (G from its upper triangle)
 __global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__restrict__ Glo,
                             const unsigned long long *__restrict__ Ghi, const unsigned long long *__restrict__ s,
-                            double *__restrict__ B, double *__restrict__ rowmean) {
-  __shared__ double red[32];
+                            double *__restrict__ B) {
   const double two64 = 18446744073709551616.0;
   const double inv_n = 1.0 / (double)n;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int a = t / k, b = t % k;
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < kk; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / k), b = (int)(t - (int64_t)a * k);
     const int lo_ = min(a, b), hi_ = max(a, b);
     const size_t o = (size_t)lo_ * k + hi_;
     const double g = (double)Ghi[o] * two64 + (double)Glo[o];
     B[t] = g - ((double)s[a] * (double)s[b]) * inv_n;
   }
-  __syncthreads();
-  // row sums in column order: B is exactly symmetric (G from one triangle, the
-  // product s_a s_b commutes), so column a summed over rows 0..k-1 adds the
-  // same numbers in the same order as row a, and a warp's loads are coalesced
+}
+
+//   k_row_means  rowmean[a] = mean of row a, rowmean[k] = their mean (one
+//                block of 1024 threads).  B is exactly symmetric (G from one
+//                triangle, s_a s_b commutes), so row a is summed down column
+//                a: the same numbers in the same order, with coalesced loads
+__global__ void k_row_means(int32_t k, const double *__restrict__ B, double *__restrict__ rowmean) {
+  __shared__ double red[32];
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     double acc = 0.0;
     for (int b = 0; b < k; ++b) acc += B[(size_t)b * k + a];
@@ -118,12 +129,16 @@ __global__ void k_prepare_b(int32_t n, int32_t k, const unsigned long long *__re
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
-    red[0] = t / (double)k;
+    rowmean[k] = t / (double)k;
   }
-  __syncthreads();
-  const double gm = red[0];
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int a = t / k, b = t % k;
+}
+
+//   k_center     B[a][b] = 1/4 (B[a][b] - rowmean[a] - rowmean[b] + rowmean[k])
+__global__ void k_center(int32_t k, double *__restrict__ B, const double *__restrict__ rowmean) {
+  const double gm = rowmean[k];
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < kk; t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / k), b = (int)(t - (int64_t)a * k);
     B[t] = 0.25 * (B[t] - rowmean[a] - rowmean[b] + gm);
   }
 }
@@ -933,7 +948,7 @@ static size_t carve_mds(Carver &c, MdsWs &w, int32_t n, int32_t k) {
   w.Btmp = c.take<double>(kk);
   w.M = c.take<double>(kk);
   w.bscale = c.take<double>(1);
-  w.rowmean = c.take<double>(k);
+  w.rowmean = c.take<double>((size_t)k + 1);  // the row means and their mean
   w.vv = c.take<double>(2 * (size_t)k);
   w.part = c.take<double>(8192);
   w.scale = c.take<double>(1);
@@ -1070,7 +1085,13 @@ SSM_API int ssm_pivotmds(int32_t n, const int32_t *rowptr, const int32_t *colidx
     const int64_t tasks = (int64_t)k * ((n + kColChunk - 1) / kColChunk);
     note_launch(), k_colsum<<<(unsigned)std::min<int64_t>(tasks, (int64_t)sms * 8), 256, 0, s>>>(n, k, dip, w.s);
   }
-  note_launch(), k_prepare_b<<<1, 1024, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B, w.rowmean);
+  {
+    const int64_t kk = (int64_t)k * k;
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((kk + 255) / 256, sms * 4));
+    note_launch(), k_prepare_b<<<gb, 256, 0, s>>>(n, k, w.Glo, w.Ghi, w.s, w.B);
+    note_launch(), k_row_means<<<1, 1024, 0, s>>>(k, w.B, w.rowmean);
+    note_launch(), k_center<<<gb, 256, 0, s>>>(k, w.B, w.rowmean);
+  }
   if (int rc = launch_eigen(n, k, w, w.s, eig, status, s)) return rc;
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   const size_t psm = (size_t)k * sizeof(float4);
@@ -1208,34 +1229,6 @@ __global__ void k_wgram_reduce(int32_t k, int64_t nchunks, const double *__restr
   }
 }
 
-// B = 1/4 (G' - rowmean_a - rowmean_b + grand mean), in place (one block)
-__global__ void k_center_b(int32_t k, double *__restrict__ B, double *__restrict__ rowmean) {
-  __shared__ double red[32];
-  // G' is written symmetric (one value for both triangles): row sums taken
-  // down the columns, the same numbers in the same order, with coalesced loads
-  for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    double acc = 0.0;
-    for (int b = 0; b < k; ++b) acc += B[(size_t)b * k + a];
-    rowmean[a] = acc / (double)k;
-  }
-  __syncthreads();
-  double g = 0.0;
-  for (int a = threadIdx.x; a < k; a += blockDim.x) g += rowmean[a];
-  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
-    red[0] = t / (double)k;
-  }
-  __syncthreads();
-  const double gm = red[0];
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int a = t / k, b = t % k;
-    B[t] = 0.25 * (B[t] - rowmean[a] - rowmean[b] + gm);
-  }
-}
 
 // x_i = C v = -1/2 (sum_a d_ia^2 v_a - rbar_i sigma - kappa), FP64
 __global__ void __launch_bounds__(256) k_wproject(int32_t n, int32_t k, const float *__restrict__ dist,
@@ -1312,7 +1305,10 @@ SSM_API int ssm_pivotmds_weighted(int32_t n, const int32_t *rowptr, const int32_
   const int64_t kk = (int64_t)k * k;
   note_launch(), k_wgram_reduce<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kk + 255) / 256, sms * 4)), 256, 0,
                                   s>>>(k, nch, x.partg, w.B);
-  note_launch(), k_center_b<<<1, 1024, 0, s>>>(k, w.B, w.rowmean);
+  // B = 1/4 (G' - rowmean_a - rowmean_b + grand mean)
+  note_launch(), k_row_means<<<1, 1024, 0, s>>>(k, w.B, w.rowmean);
+  note_launch(), k_center<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((kk + 255) / 256, sms * 4)), 256, 0, s>>>(
+      k, w.B, w.rowmean);
   if (int rc = launch_eigen(n, k, w, (const double *)x.colsum, eig, status, s)) return rc;
   const int pb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
   note_launch(), k_wproject<<<pb, 256, 2 * (size_t)k * sizeof(double), s>>>(n, k, dist, w.vv, w.eo, pos, precision);
